@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the bricked ray caster on the HI-survey workload.
+
+One step = one frame of the whole hot path at the next pose of a 120-pose orbit
+about the y axis: host plan (rendering rectangles, empty-space skipping, view
+order), ray march of every (brick, tile) item, sort-last 'over' composite.
+
+Workload (default): float32 cube 1024 x 1024 x 2048 (8 GiB; noise + 2000 line
+sources + 50 continuum sources), 128^3 bricks, 1920 x 1080 image, step 0.5
+voxel, 16-point transfer function TF-A, termination at alpha >= 0.99.  The cube
+is larger than L2, so no L2 flush is needed between frames.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the same workload instead (a bounded pixel sample per step).
+Multi-GPU (torchrun): each rank renders its own share of the orbit (no data
+exchange), the job time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ray samples/s & 1080p FPS vs HBM roofline; learned vs plain FPS @>=45 dB PSNR"
+UNIT = "ray samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=["hi", "tiny"], default="hi")
+    ap.add_argument("--tf", choices=["a", "b"], default="a")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    if args.config == "hi":
+        spec = dict(synth.HI)
+        tf = synth.tf_hi_a() if args.tf == "a" else synth.tf_hi_b()
+        poses = synth.orbit(spec["shape_xyz"], 120, 15.0, spec["width"], spec["height"])
+        desc = ("HI-survey cube 1024x1024x2048 f32 (noise + 2000 line + 50 continuum sources), "
+                f"128^3 bricks, 1920x1080, step 0.5, 16-point TF-{args.tf.upper()}, "
+                "tau 0.99, 120-pose orbit about y at 15 deg elevation")
+    else:
+        spec = dict(synth.TINY)
+        tf = synth.tf_tiny()
+        poses = synth.tiny_views()
+        desc = "tiny 64^3 cube, 32^3 bricks, 256x256, step 0.5, 8-point TF, 4 views"
+    return spec, tf, poses, desc
+
+
+def make_cube(spec):
+    if spec["name"] == "hi":
+        return synth.hi_cube()
+    return synth.tiny_cube()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "utilization.gpu",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3], parts[4:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        loaded = [r for r in rows if r[2] not in ("0", "[N/A]")] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in loaded for k, v in enumerate(r[3]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "samples_loaded": len(loaded)}
+
+
+# ------------------------------------------------------------------ roofline inputs
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("vr_kernels.cu", "vr_internal.cuh", "df.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1205_0282_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload_name):
+    """DRAM bytes per launch from a committed ncu capture, only if the kernel
+    source is unchanged since that capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel, {}).get(workload_name)
+    if not e or e.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_rate(cube, tf, poses, brick, seconds, crop=64):
+    """Samples/s of the FP64 oracle on centre crops of successive poses, for
+    about `seconds` of wall time (at least one crop)."""
+    import oracle
+    total = 0
+    t0 = time.perf_counter()
+    k = 0
+    crops = 0
+    while True:
+        cam = poses[k % len(poses)]
+        W, H = cam["width"], cam["height"]
+        x0, y0 = W // 2 - crop // 2, H // 2 - crop // 2
+        jj, ii = np.meshgrid(np.arange(y0, y0 + crop), np.arange(x0, x0 + crop), indexing="ij")
+        pix = (jj * W + ii).reshape(-1)
+        _, _, ns = oracle.render(cube, tf, cam, brick=brick, pixels=pix)
+        total += int(ns.sum())
+        crops += 1
+        k += 7
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return total / dt, dt, crops
+
+
+def cpu_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+# ------------------------------------------------------------------ main
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec, tf, poses, desc = workload(args)
+    cube = make_cube(spec)
+    brick = spec["brick"]
+    import oracle
+    oracle.build()
+    crop = 64 if spec["name"] == "hi" else 128
+    for k in range(args.warmup):
+        oracle_rate(cube, tf, poses[k:k + 1], brick, 0.0, crop=16)
+    total_samples, t = 0, 0.0
+    for k in range(args.steps):
+        rate, dt, _ = oracle_rate(cube, tf, poses[k % len(poses):] + poses, brick, 0.0, crop=crop)
+        total_samples += rate * dt
+        t += dt
+    value = total_samples / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sample": f"{crop}x{crop} centre crop of one pose per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{crop}x{crop} centre crop per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1205_0282_gb300 import VolumeRenderer
+
+    spec, tf, poses, desc = workload(args)
+    cube = make_cube(spec)
+    my_poses = poses[rank::world] if world > 1 else poses
+    W, H = spec["width"], spec["height"]
+
+    r = VolumeRenderer(local)
+    dcube = torch.from_numpy(cube).cuda()
+    r.load_cube(dcube)
+    del dcube
+    torch.cuda.empty_cache()
+    r.brick(*spec["brick"])
+    r.set_transfer_function(tf)
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def frame(k):
+        r.set_camera(my_poses[k % len(my_poses)])
+        r.render(out, stream)
+
+    for k in range(args.warmup):
+        frame(k)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    r.reset_stats()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = local
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(gpu_id) as clocks:
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for k in range(args.steps):
+            frame(k)
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    st = r.stats()
+    elapsed_ms = evs[0].elapsed_time(evs[-1])
+    frame_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    samples = st["samples"]
+    frames = st["frames"]
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        s = torch.tensor([samples, frames, st["launches"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        samples, frames, launches = int(s[0].item()), int(s[1].item()), int(s[2].item())
+    else:
+        launches = st["launches"]
+
+    # end to end: host output buffer, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True).numpy()
+        r.reset_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            r.set_camera(my_poses[k % len(my_poses)])
+            r.render(host)
+        t1 = time.perf_counter()
+        se = r.stats()
+        e2e_t = t1 - t0
+        if dist:
+            t = torch.tensor([e2e_t], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_t = float(t.item())
+            s = torch.tensor([se["samples"]], dtype=torch.float64, device="cuda")
+            dist.all_reduce(s, op=dist.ReduceOp.SUM)
+            e2e_samples = float(s.item())
+        else:
+            e2e_samples = se["samples"]
+        e2e = {"value": e2e_samples / e2e_t, "unit": UNIT,
+               "h2d_bytes_per_step": se["h2d_bytes"] // max(se["frames"], 1),
+               "d2h_bytes_per_step": se["d2h_bytes"] // max(se["frames"], 1),
+               "steps": args.e2e_steps,
+               "fps": args.e2e_steps * (world if dist else 1) / e2e_t}
+
+    if rank != 0:
+        r.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    avg_march_ms = st["march_ms"] / max(st["frames"], 1)
+    bytes_per_launch = st["touched_bytes"] / max(st["frames"], 1)
+    achieved = bytes_per_launch / (avg_march_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "march_kernel", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic("march_kernel", spec["name"]),
+                "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_ms": avg_march_ms,
+                "frame_bytes_per_step": bytes_per_launch + W * H * 16,
+                "frame_frac": (bytes_per_launch + W * H * 16) / (elapsed_ms / args.steps * 1e-3) / 1e9 / peak}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, secs, crops = oracle_rate(cube, tf, poses, spec["brick"], args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{crops} centre crops of 64x64 pixels on successive orbit poses, "
+                         f"{secs:.1f} s of FP64 CPU work"}
+
+    value = samples / (elapsed_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": desc, "cube_xyz": list(spec["shape_xyz"]),
+                       "brick": list(spec["brick"]), "image": [W, H], "step": 0.5,
+                       "tf": args.tf.upper(), "term_alpha": 0.99,
+                       "l2": "inputs larger than L2 (8 GiB cube), no flush",
+                       "parallelism": f"replicas x{world}: orbit poses split across ranks"},
+            "fps": frames / (elapsed_ms * 1e-3),
+            "frame_ms_p50": float(np.percentile(frame_ms, 50)),
+            "frame_ms_p75": float(np.percentile(frame_ms, 75)),
+            "samples_per_frame": samples / max(frames, 1),
+            "bricks_rendered_per_frame": st["bricks_rendered"] / max(st["frames"], 1),
+            "bricks_skipped_per_frame": st["bricks_skipped"] / max(st["frames"], 1),
+            "plan_ms_per_frame": st["plan_ms"] / max(st["frames"], 1),
+            "composite_ms_per_frame": st["composite_ms"] / max(st["frames"], 1),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks.summary(),
+            "device_errors": st["device_errors"]}
+    print(json.dumps(line), flush=True)
+    r.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * vr.h -- C ABI of the GB300 bricked volume ray caster.
+ *
+ * Renders a float32 data cube by per-pixel ray casting (tri-linear sampling,
+ * a 1D transfer function with step-size opacity correction, front-to-back
+ * compositing with early ray termination) and sort-last 'over' compositing of
+ * per-brick sub-images in view order, after Hassan, Fluke & Barnes, "A
+ * Distributed GPU-based Framework for real-time 3D Volume Rendering of Large
+ * Astronomical Data Cubes" (arXiv:1205.0282):
+ *   Section 2.3.1  data partitioning into sub-cubes, per-sub-cube min/max;
+ *   Section 2.3.2  ray casting: rendering rectangle from the projected sub-cube
+ *                  vertices, entry/exit with the bounding cube, tri-linear
+ *                  sampling, termination at exit or on opacity;
+ *   Section 2.3.3  composition of sub-images, associativity of alpha blending,
+ *                  maximum intensity projection with a colour map.
+ *
+ * Conventions for every call:
+ *   - Return value: VR_OK (0) or a negative VR_E* code; no exception crosses the
+ *     ABI.  vr_last_error() gives a message for the last failing call on a context.
+ *   - The library owns all device memory it allocates (released by vr_destroy).
+ *     Callers own every buffer they pass; the library never keeps a pointer to a
+ *     caller buffer after a call returns, except that a device output buffer
+ *     given to vr_render is written asynchronously on the given stream.
+ *   - Pointers may be host or device (CUDA unified addressing decides).
+ *   - Coordinates: voxel (i,j,k) of a cube float32[nz][ny][nx] (x fastest) sits
+ *     at the point (i,j,k); the domain is [0,nx-1] x [0,ny-1] x [0,nz-1]; all
+ *     distances are in voxel units.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef VR_H
+#define VR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VR_OK 0
+#define VR_EINVAL (-1)   /* bad argument */
+#define VR_ENOMEM (-2)   /* device or pinned-host allocation failed */
+#define VR_ECUDA (-3)    /* a CUDA runtime/driver call failed */
+#define VR_ESTATE (-4)   /* call out of order (e.g. render before cube/brick/TF/camera) */
+#define VR_ETIMEOUT (-5) /* a bounded device wait gave up; the frame is invalid */
+
+typedef struct vr_ctx vr_ctx;
+
+/*
+ * Pinhole camera (Section 2.3.2 passes the viewer's projection and view
+ * transforms; this is the equivalent look-at form).  Basis f = |target-eye|,
+ * r = |f x up|, u = r x f.  Pixel (i,j), row j = 0 at the top, is cast along
+ * |f + qx r + qy u| with qx = (2(i+0.5)/width - 1) tan(fovy/2) width/height and
+ * qy = (1 - 2(j+0.5)/height) tan(fovy/2).  Samples are taken every `step`
+ * voxels from the ray's entry into the domain (or from the eye if it is
+ * inside); compositing stops once the accumulated opacity reaches
+ * `term_alpha` (1.0 disables early termination).
+ */
+typedef struct {
+    double eye[3], target[3], up[3];
+    double fovy_deg;      /* vertical field of view, (0, 180) */
+    int32_t width, height;
+    double step;          /* sample spacing in voxels, [0.01, 1000] */
+    double term_alpha;    /* early-termination opacity, (0, 1] */
+} vr_camera;
+
+/* Render statistics (cumulative since vr_create or the last vr_reset_stats). */
+typedef struct {
+    int64_t frames;          /* completed vr_render calls */
+    int64_t samples;         /* samples composited (after termination, excluding skipped bricks) */
+    int64_t items;           /* (brick, pixel tile) work items launched */
+    int64_t fragments;       /* per-brick sub-image pixels written (items x tile pixels) */
+    int64_t bricks_rendered; /* bricks with at least one work item, summed over frames */
+    int64_t bricks_skipped;  /* bricks dropped because the TF opacity is zero on [min,max] */
+    int64_t touched_bytes;   /* sum over rendered bricks of their voxel bytes (no apron) */
+    double march_ms;         /* device time of the ray-march kernel (CUDA events) */
+    double composite_ms;     /* device time of the sort-last compositing kernel */
+    double frame_ms;         /* device time from plan upload to image written */
+    double plan_ms;          /* host time of the per-frame planner */
+    int64_t h2d_bytes;       /* host->device bytes copied by vr_render (plans, camera, TF) */
+    int64_t d2h_bytes;       /* device->host bytes copied by vr_render (counters, host images) */
+    int64_t launches;        /* kernels launched by vr_render */
+    int32_t device_errors;   /* OR of device-side error flags seen (0 = none) */
+    int32_t reserved;
+} vr_stats;
+
+/* Options for vr_set_option. */
+#define VR_OPT_SKIP_EMPTY 1  /* 1 (default): drop bricks whose TF opacity is 0 on [min,max] */
+#define VR_OPT_RECT_CULL 2   /* 1 (default): items only for tiles inside a brick's rendering
+                                rectangle (Section 2.3.2); 0: every tile for every brick */
+#define VR_OPT_MODE 3        /* 0 (default): emission-absorption compositing;
+                                1: maximum intensity projection + colour map (Section 2.3.3) */
+
+/*
+ * Create a context on CUDA device `device`.  *out receives the context.
+ * Errors: VR_EINVAL (null out, bad device), VR_ECUDA.
+ */
+int vr_create(vr_ctx** out, int32_t device);
+
+/* Destroy a context and free everything it owns; NULL is ignored.  Waits for
+ * the context's outstanding work first. */
+void vr_destroy(vr_ctx* ctx);
+
+/*
+ * Load the data cube (Section 2.3.1: the cube is moved into GPU memory).
+ * data: float32[nz][ny][nx], x fastest, host or device; the library copies it
+ * into memory it owns (the caller keeps ownership of `data`).  2 <= nx, ny, nz <= 65536.
+ * Invalidates any previous bricking.  Synchronous.
+ * Errors: VR_EINVAL, VR_ENOMEM, VR_ECUDA.
+ */
+int vr_load_cube(vr_ctx* ctx, const float* data, int64_t nx, int64_t ny, int64_t nz);
+
+/*
+ * Partition the loaded cube into bricks of bx x by x bz voxels (Section 2.3.1;
+ * the unit of sort-last compositing) and compute each brick's [min, max] over
+ * the voxels its samples can touch: along each axis brick b covers voxels
+ * [b*B, min((b+1)*B, n-1)] (its own plus a one-voxel apron on the high side).
+ * Bricks per axis: ceil((n-1)/B).  Sample p belongs to brick floor(p/B) per
+ * axis, the last brick being closed.  1 <= B <= 4096.  Synchronous.
+ * Errors: VR_EINVAL, VR_ESTATE (no cube), VR_ENOMEM, VR_ECUDA.
+ */
+int vr_brick(vr_ctx* ctx, int32_t bx, int32_t by, int32_t bz);
+
+/*
+ * Set the transfer function (Section 1.2): n >= 2 control points given as
+ * rows of 5 doubles (v, r, g, b, a), host memory, v strictly increasing,
+ * r, g, b, a in [0, 1]; a is the opacity per unit voxel of path.  Values
+ * between points are interpolated linearly, values outside take the end
+ * points.  Per sample alpha = 1 - (1 - a)^(step / 1 voxel).  n <= 256.
+ * Host-side only: takes effect for the next vr_render.  Errors: VR_EINVAL.
+ */
+int vr_set_transfer_function(vr_ctx* ctx, const double* points, int32_t n);
+
+/* Set the camera; see vr_camera.  width, height in [1, 16384].  Host-side
+ * only: takes effect for the next vr_render, frames already enqueued are not
+ * affected.  Errors: VR_EINVAL (degenerate basis, bad sizes). */
+int vr_set_camera(vr_ctx* ctx, const vr_camera* cam);
+
+/* Set an option (VR_OPT_*).  Errors: VR_EINVAL. */
+int vr_set_option(vr_ctx* ctx, int32_t option, int64_t value);
+
+/*
+ * Render one frame into out_rgba: float32[height][width][4], premultiplied
+ * (r, g, b, alpha), row 0 at the top, no background.  out_rgba may be device
+ * memory (written asynchronously on `cuda_stream`, a cudaStream_t or NULL for
+ * the legacy default stream) or host memory (the call then copies the image
+ * back and synchronises the stream).  Stream-ordered: the call returns after
+ * enqueueing work unless out_rgba is host memory.  Calls on different streams
+ * with one context must not overlap in time on the device.
+ * Errors: VR_ESTATE (missing cube/brick/TF/camera), VR_EINVAL, VR_ENOMEM,
+ * VR_ECUDA.
+ */
+int vr_render(vr_ctx* ctx, float* out_rgba, void* cuda_stream);
+
+/* Copy the statistics out (waits for the context's outstanding frames).
+ * Errors: VR_EINVAL, VR_ECUDA. */
+int vr_get_stats(vr_ctx* ctx, vr_stats* out);
+
+/* Zero the statistics (waits for outstanding frames).  Errors: VR_EINVAL, VR_ECUDA. */
+int vr_reset_stats(vr_ctx* ctx);
+
+/* Copy the per-brick [min, max] pairs (float32, n_bricks x 2, host memory,
+ * brick id = ix + nbx*(iy + nby*iz)) computed by vr_brick.
+ * Errors: VR_EINVAL (n_bricks mismatch), VR_ESTATE (no bricking), VR_ECUDA. */
+int vr_get_brick_minmax(vr_ctx* ctx, float* out, int64_t n_bricks);
+
+/*
+ * Host-only planner query, no device needed: the rendering rectangle of every
+ * brick (Section 2.3.2: the bounding rectangle of the brick's projected
+ * vertices, clipped to the image).  rects: int32[n_bricks][4] receiving
+ * (x0, y0, x1, y1) inclusive pixel bounds, or (0, 0, -1, -1) when the brick is
+ * off screen.  n_bricks must equal the brick count for the given sizes.
+ * Errors: VR_EINVAL.
+ */
+int vr_plan_brick_rects(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz,
+                        int32_t bx, int32_t by, int32_t bz, int32_t* rects, int64_t n_bricks);
+
+/* Message describing the last failing call on ctx (never NULL). */
+const char* vr_last_error(const vr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VR_H */

@@ -1,0 +1,20 @@
+"""GB300 bricked volume ray caster (after Hassan, Fluke & Barnes, arXiv:1205.0282).
+
+The rendering path lives in ``libvr.so`` (CUDA, sm_103a) behind the C ABI of
+``include/vr.h``; ``paper_1205_0282_gb300.vr`` is its Python binding.  The
+binding's names are loaded on first use, so ``paper_1205_0282_gb300.build`` can
+be imported (to compile the library) before the library exists.
+"""
+_EXPORTED = ("VolumeRenderer", "VRError", "VR_OPT_MODE", "VR_OPT_RECT_CULL", "VR_OPT_SKIP_EMPTY",
+             "vr_brick", "vr_create", "vr_destroy", "vr_get_brick_minmax", "vr_get_stats",
+             "vr_last_error", "vr_load_cube", "vr_plan_brick_rects", "vr_render",
+             "vr_reset_stats", "vr_set_camera", "vr_set_option", "vr_set_transfer_function")
+
+__all__ = list(_EXPORTED)
+
+
+def __getattr__(name):
+    if name in _EXPORTED:
+        from . import vr
+        return getattr(vr, name)
+    raise AttributeError(name)

@@ -1,0 +1,776 @@
+// Host side of the C ABI declared in include/vr.h: context, brick store, transfer
+// function and camera state, the per-frame planner (rendering rectangles, exact
+// empty-space skipping, view-order sort, work-list build; Sections 2.3.1-2.3.3 of
+// arXiv:1205.0282) and the stream-ordered frame pipeline.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vr.h"
+#include "vr_internal.cuh"
+
+using vr::df;
+
+namespace {
+
+constexpr int kSlots = 3;  // frames that may be in flight per context
+
+struct Slot {
+    vr::Item* h_items = nullptr;
+    int32_t* h_tile_start = nullptr;
+    size_t cap_items = 0, cap_tiles = 0;
+    vr::Item* d_items = nullptr;
+    int32_t* d_tile_start = nullptr;
+    size_t dcap_items = 0, dcap_tiles = 0;
+    float4* d_frags = nullptr;
+    size_t cap_frags = 0;  // float4 pixels
+    float4* d_img = nullptr;
+    size_t cap_img = 0;    // float4 pixels
+    unsigned char* h_frame = nullptr;  // camera tables + transfer function, pinned
+    unsigned char* d_frame = nullptr;
+    size_t cap_frame = 0, dcap_frame = 0;
+    vr::Stats* d_stats = nullptr;
+    vr::Stats* h_stats = nullptr;
+    cudaEvent_t ev_begin = nullptr, ev_march0 = nullptr, ev_march1 = nullptr, ev_end = nullptr;
+    bool pending = false;
+    // host-side facts of the frame in flight
+    int64_t items = 0, bricks_rendered = 0, bricks_skipped = 0, touched_bytes = 0;
+    int64_t h2d_bytes = 0, d2h_bytes = 0, launches = 0;
+    double plan_ms = 0.0;
+};
+
+struct Basis {
+    double f[3], r[3], u[3];
+    double tan_half, aspect;
+};
+
+bool make_basis(const vr_camera& c, Basis& b) {
+    double f[3], n = 0;
+    for (int a = 0; a < 3; ++a) {
+        f[a] = c.target[a] - c.eye[a];
+        n += f[a] * f[a];
+    }
+    n = std::sqrt(n);
+    if (!(n > 0)) return false;
+    for (int a = 0; a < 3; ++a) b.f[a] = f[a] / n;
+    double r[3] = {b.f[1] * c.up[2] - b.f[2] * c.up[1], b.f[2] * c.up[0] - b.f[0] * c.up[2],
+                   b.f[0] * c.up[1] - b.f[1] * c.up[0]};
+    n = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (!(n > 1e-300)) return false;
+    for (int a = 0; a < 3; ++a) b.r[a] = r[a] / n;
+    b.u[0] = b.r[1] * b.f[2] - b.r[2] * b.f[1];
+    b.u[1] = b.r[2] * b.f[0] - b.r[0] * b.f[2];
+    b.u[2] = b.r[0] * b.f[1] - b.r[1] * b.f[0];
+    b.tan_half = std::tan(c.fovy_deg * 3.14159265358979323846 / 360.0);
+    b.aspect = (double)c.width / (double)c.height;
+    return true;
+}
+
+bool camera_valid(const vr_camera& c) {
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return false;
+    if (!(c.fovy_deg > 0.0 && c.fovy_deg < 180.0)) return false;
+    // step >= 0.01 keeps every sample index below 2^24 (exact in FP32) for cubes up
+    // to 65536 voxels per axis
+    if (!(c.step >= 0.01 && c.step <= 1000.0)) return false;
+    if (!(c.term_alpha > 0.0 && c.term_alpha <= 1.0)) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(c.eye[a]) || !std::isfinite(c.target[a]) || !std::isfinite(c.up[a]))
+            return false;
+    return true;
+}
+
+int64_t bricks_along(int64_t n, int64_t B) { return (n - 1 + B - 1) / B; }
+
+// Rendering rectangle of the box [lo, hi] (Section 2.3.2: project the sub-cube's
+// vertices, take their bounding rectangle).  Pixel (i, j) has its centre at
+// ((i+.5)/W, (j+.5)/H) of the image; the rectangle is widened by one pixel so that
+// rounding can never drop a pixel whose ray touches the box.  Returns false if the
+// rectangle is empty after clipping.  A box reaching behind the eye plane maps to
+// the whole image.
+bool box_rect(const vr_camera& c, const Basis& b, const double lo[3], const double hi[3],
+              int32_t rect[4]) {
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    bool behind = false;
+    for (int k = 0; k < 8; ++k) {
+        double P[3] = {(k & 1) ? hi[0] : lo[0], (k & 2) ? hi[1] : lo[1], (k & 4) ? hi[2] : lo[2]};
+        double v[3] = {P[0] - c.eye[0], P[1] - c.eye[1], P[2] - c.eye[2]};
+        double zc = v[0] * b.f[0] + v[1] * b.f[1] + v[2] * b.f[2];
+        if (!(zc > 1e-9)) {
+            behind = true;
+            break;
+        }
+        double xc = v[0] * b.r[0] + v[1] * b.r[1] + v[2] * b.r[2];
+        double yc = v[0] * b.u[0] + v[1] * b.u[1] + v[2] * b.u[2];
+        double sx = xc / (zc * b.tan_half * b.aspect), sy = yc / (zc * b.tan_half);
+        double pi = (sx + 1.0) * 0.5 * c.width - 0.5;
+        double pj = (1.0 - sy) * 0.5 * c.height - 0.5;
+        xmin = std::min(xmin, pi);
+        xmax = std::max(xmax, pi);
+        ymin = std::min(ymin, pj);
+        ymax = std::max(ymax, pj);
+    }
+    if (behind) {
+        rect[0] = 0;
+        rect[1] = 0;
+        rect[2] = c.width - 1;
+        rect[3] = c.height - 1;
+        return true;
+    }
+    double x0 = std::floor(xmin) - 1, x1 = std::ceil(xmax) + 1;
+    double y0 = std::floor(ymin) - 1, y1 = std::ceil(ymax) + 1;
+    x0 = std::max(x0, 0.0);
+    y0 = std::max(y0, 0.0);
+    x1 = std::min(x1, (double)c.width - 1);
+    y1 = std::min(y1, (double)c.height - 1);
+    if (x1 < x0 || y1 < y0) {
+        rect[0] = rect[1] = 0;
+        rect[2] = rect[3] = -1;
+        return false;
+    }
+    rect[0] = (int32_t)x0;
+    rect[1] = (int32_t)y0;
+    rect[2] = (int32_t)x1;
+    rect[3] = (int32_t)y1;
+    return true;
+}
+
+// Sampling region of brick (ix, iy, iz): [b*B, min((b+1)*B, n-1)] per axis.
+void brick_box(const int64_t n[3], const int32_t B[3], const int64_t idx[3], double lo[3],
+               double hi[3]) {
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (double)(idx[a] * B[a]);
+        hi[a] = (double)std::min<int64_t>((idx[a] + 1) * B[a], n[a] - 1);
+    }
+}
+
+// Maximum of the piecewise-linear opacity over [lo, hi] (exact: endpoints and the
+// control points strictly inside).
+double tf_alpha_max(const std::vector<double>& tf, double lo, double hi) {
+    const int n = (int)(tf.size() / 5);
+    auto eval = [&](double v) {
+        if (v <= tf[0]) return tf[4];
+        if (v >= tf[5 * (n - 1)]) return tf[5 * (n - 1) + 4];
+        int s = 0;
+        while (!(v < tf[5 * (s + 1)])) ++s;
+        double w = (v - tf[5 * s]) / (tf[5 * (s + 1)] - tf[5 * s]);
+        return tf[5 * s + 4] + w * (tf[5 * (s + 1) + 4] - tf[5 * s + 4]);
+    };
+    double m = std::max(eval(lo), eval(hi));
+    for (int s = 0; s < n; ++s)
+        if (tf[5 * s] > lo && tf[5 * s] < hi) m = std::max(m, tf[5 * s + 4]);
+    return m;
+}
+
+// Q(a) = (1 - (1-a)^r) / a, with Q(0) = r.
+double alpha_over_a(double a, double r) {
+    if (a == 0.0) return r;
+    return -std::expm1(r * std::log1p(-a)) / a;
+}
+
+// Chebyshev interpolation of Q on [0, split], converted to powers of t = 2a/split - 1.
+// Chooses the lowest degree whose error on a dense grid is below 2e-10.
+int fit_alpha_poly(double r, double split, float* coeff) {
+    for (int deg = 1; deg < vr::kAlphaPolyMax; ++deg) {
+        const int m = deg + 1;
+        std::vector<double> c(m, 0.0);
+        for (int j = 0; j < m; ++j) {
+            double s = 0;
+            for (int k = 0; k < m; ++k) {
+                double th = M_PI * (k + 0.5) / m;
+                double a = (std::cos(th) + 1.0) * 0.5 * split;
+                s += alpha_over_a(a, r) * std::cos(j * th);
+            }
+            c[j] = 2.0 * s / m;
+        }
+        c[0] *= 0.5;
+        // Chebyshev -> monomial: T_0 = 1, T_1 = t, T_{k+1} = 2t T_k - T_{k-1}
+        std::vector<double> mono(m, 0.0), tkm1(m, 0.0), tk(m, 0.0), tkp1(m, 0.0);
+        tkm1[0] = 1.0;
+        if (m > 1) tk[1] = 1.0;
+        for (int j = 0; j < m; ++j) {
+            const std::vector<double>& T = (j == 0) ? tkm1 : tk;
+            for (int q = 0; q < m; ++q) mono[q] += c[j] * T[q];
+            if (j >= 1) {
+                std::fill(tkp1.begin(), tkp1.end(), 0.0);
+                for (int q = 0; q + 1 < m; ++q) tkp1[q + 1] += 2.0 * tk[q];
+                for (int q = 0; q < m; ++q) tkp1[q] -= tkm1[q];
+                tkm1 = tk;
+                tk = tkp1;
+            }
+        }
+        double err = 0;
+        for (int g = 0; g <= 4000; ++g) {
+            double a = split * g / 4000.0;
+            double t = 2.0 * a / split - 1.0, q = 0;
+            for (int k = m - 1; k >= 0; --k) q = q * t + mono[k];
+            err = std::max(err, std::fabs(q - alpha_over_a(a, r)));
+        }
+        if (err < 2e-10 || deg == vr::kAlphaPolyMax - 1) {
+            for (int k = 0; k < m; ++k) coeff[k] = (float)mono[k];
+            return m;
+        }
+    }
+    return 0;
+}
+
+}  // namespace
+
+struct vr_ctx {
+    int device = 0;
+    std::string err;
+    int sm_count = 0;
+
+    float* d_cube = nullptr;
+    int64_t n[3] = {0, 0, 0};
+
+    bool bricked = false;
+    int32_t B[3] = {0, 0, 0};
+    int32_t nb[3] = {0, 0, 0};
+    int64_t n_bricks = 0;
+    float2* d_minmax = nullptr;
+    std::vector<float2> h_minmax;
+
+    bool tf_set = false;
+    std::vector<double> tf;
+    std::vector<float4> tf_rgba;
+    std::vector<float> tf_v;
+    int tf_uniform = 0;
+    float tf_v0 = 0, tf_inv_dv = 0;
+
+    bool cam_set = false;
+    vr_camera cam{};
+    Basis basis{};
+    std::vector<df> q;  // qx (width entries) then qy (height entries)
+    float alpha_poly[vr::kAlphaPolyMax] = {};
+    int alpha_poly_n = 0;
+
+    bool skip_empty = true, rect_cull = true;
+    int mode = 0;
+
+    Slot slots[kSlots];
+    int next_slot = 0;
+    vr_stats acc{};
+
+    // planner scratch (host)
+    std::vector<int32_t> plan_count, plan_fill;
+    struct PB {
+        int32_t key, id, rect[4];
+    };
+    std::vector<PB> plan_bricks;
+};
+
+namespace {
+
+int fail(vr_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(vr_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, VR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define VR_CUDA(ctx, call)                                      \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+    } while (0)
+
+template <typename T>
+int grow_device(vr_ctx* c, T*& p, size_t& cap, size_t need) {
+    if (need <= cap && p) return VR_OK;
+    size_t n = std::max(need, cap + cap / 2);
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc((void**)&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, VR_ENOMEM, "device allocation failed");
+    }
+    cap = n;
+    return VR_OK;
+}
+
+template <typename T>
+int grow_pinned(vr_ctx* c, T*& p, size_t& cap, size_t need) {
+    if (need <= cap && p) return VR_OK;
+    size_t n = std::max(need, cap + cap / 2);
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMallocHost((void**)&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, VR_ENOMEM, "pinned host allocation failed");
+    }
+    cap = n;
+    return VR_OK;
+}
+
+// Wait for a slot's frame, fold its numbers into the statistics.
+int retire(vr_ctx* c, Slot& s) {
+    if (!s.pending) return VR_OK;
+    VR_CUDA(c, cudaEventSynchronize(s.ev_end));
+    float ms_march = 0, ms_frame = 0, ms_comp = 0;
+    VR_CUDA(c, cudaEventElapsedTime(&ms_march, s.ev_march0, s.ev_march1));
+    VR_CUDA(c, cudaEventElapsedTime(&ms_comp, s.ev_march1, s.ev_end));
+    VR_CUDA(c, cudaEventElapsedTime(&ms_frame, s.ev_begin, s.ev_end));
+    c->acc.frames += 1;
+    c->acc.samples += (int64_t)s.h_stats->samples;
+    c->acc.items += s.items;
+    c->acc.fragments += s.items * vr::kTilePixels;
+    c->acc.bricks_rendered += s.bricks_rendered;
+    c->acc.bricks_skipped += s.bricks_skipped;
+    c->acc.touched_bytes += s.touched_bytes;
+    c->acc.march_ms += ms_march;
+    c->acc.composite_ms += ms_comp;
+    c->acc.frame_ms += ms_frame;
+    c->acc.plan_ms += s.plan_ms;
+    c->acc.h2d_bytes += s.h2d_bytes;
+    c->acc.d2h_bytes += s.d2h_bytes;
+    c->acc.launches += s.launches;
+    c->acc.device_errors |= s.h_stats->errors;
+    s.pending = false;
+    return VR_OK;
+}
+
+int retire_all(vr_ctx* c) {
+    for (auto& s : c->slots) {
+        int rc = retire(c, s);
+        if (rc) return rc;
+    }
+    return VR_OK;
+}
+
+// Build the frame's work list into slot s (host).  Returns VR_OK.
+int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int64_t& n_items) {
+    const vr_camera& cam = c->cam;
+    tiles_x = (cam.width + vr::kTile - 1) / vr::kTile;
+    tiles_y = (cam.height + vr::kTile - 1) / vr::kTile;
+    const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
+
+    // eye's brick index per axis, -1 / nb when outside (view-order key, see below)
+    int64_t e[3];
+    for (int a = 0; a < 3; ++a) {
+        double E = cam.eye[a];
+        if (E < 0.0) e[a] = -1;
+        else if (E > (double)(c->n[a] - 1)) e[a] = c->nb[a];
+        else e[a] = std::min<int64_t>((int64_t)std::floor(E / c->B[a]), c->nb[a] - 1);
+    }
+
+    c->plan_bricks.clear();
+    s.bricks_skipped = 0;
+    s.touched_bytes = 0;
+    for (int64_t id = 0; id < c->n_bricks; ++id) {
+        int64_t idx[3] = {id % c->nb[0], (id / c->nb[0]) % c->nb[1], id / ((int64_t)c->nb[0] * c->nb[1])};
+        if (c->skip_empty && c->mode == 0) {
+            const float2 mm = c->h_minmax[id];
+            if (tf_alpha_max(c->tf, mm.x, mm.y) == 0.0) {
+                ++s.bricks_skipped;
+                continue;
+            }
+        }
+        vr_ctx::PB pb;
+        pb.id = (int32_t)id;
+        if (c->rect_cull) {
+            double lo[3], hi[3];
+            brick_box(c->n, c->B, idx, lo, hi);
+            if (!box_rect(cam, c->basis, lo, hi, pb.rect)) continue;
+        } else {
+            pb.rect[0] = pb.rect[1] = 0;
+            pb.rect[2] = cam.width - 1;
+            pb.rect[3] = cam.height - 1;
+        }
+        // Along any ray from the eye each axis index moves monotonically away from
+        // the eye's index, so sum |b - e| strictly increases from one brick to the
+        // next: sorting by it is a valid front-to-back order for every ray.
+        pb.key = 0;
+        for (int a = 0; a < 3; ++a) pb.key += (int32_t)std::llabs(idx[a] - e[a]);
+        c->plan_bricks.push_back(pb);
+        int64_t vox = 1;
+        for (int a = 0; a < 3; ++a) vox *= std::min<int64_t>(c->B[a], c->n[a] - idx[a] * c->B[a]);
+        s.touched_bytes += vox * (int64_t)sizeof(float);
+    }
+    std::stable_sort(c->plan_bricks.begin(), c->plan_bricks.end(),
+                     [](const vr_ctx::PB& x, const vr_ctx::PB& y) { return x.key < y.key; });
+    s.bricks_rendered = (int64_t)c->plan_bricks.size();
+
+    c->plan_count.assign(n_tiles + 1, 0);
+    n_items = 0;
+    for (const auto& pb : c->plan_bricks) {
+        const int tx0 = pb.rect[0] / vr::kTile, tx1 = pb.rect[2] / vr::kTile;
+        const int ty0 = pb.rect[1] / vr::kTile, ty1 = pb.rect[3] / vr::kTile;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) c->plan_count[(int64_t)ty * tiles_x + tx]++;
+        n_items += (int64_t)(tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    }
+    if (n_items > (int64_t)INT32_MAX / vr::kTilePixels) return fail(c, VR_ENOMEM, "frame too large");
+    int rc = grow_pinned(c, s.h_items, s.cap_items, (size_t)n_items);
+    if (rc) return rc;
+    rc = grow_pinned(c, s.h_tile_start, s.cap_tiles, (size_t)n_tiles + 1);
+    if (rc) return rc;
+    int32_t run = 0;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        s.h_tile_start[t] = run;
+        run += c->plan_count[t];
+    }
+    s.h_tile_start[n_tiles] = run;
+    c->plan_fill.assign(n_tiles, 0);
+    int64_t k = 0;
+    for (const auto& pb : c->plan_bricks) {
+        const int tx0 = pb.rect[0] / vr::kTile, tx1 = pb.rect[2] / vr::kTile;
+        const int ty0 = pb.rect[1] / vr::kTile, ty1 = pb.rect[3] / vr::kTile;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                const int64_t t = (int64_t)ty * tiles_x + tx;
+                vr::Item it;
+                it.brick = pb.id;
+                it.tile = (int32_t)t;
+                it.frag = s.h_tile_start[t] + c->plan_fill[t]++;
+                it.pad = 0;
+                s.h_items[k++] = it;
+            }
+    }
+    s.items = n_items;
+    return VR_OK;
+}
+
+}  // namespace
+
+// =============================================================================== ABI
+
+extern "C" {
+
+int vr_create(vr_ctx** out, int32_t device) {
+    if (!out) return VR_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return VR_ECUDA;
+    }
+    if (device < 0 || device >= count) return VR_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return VR_ECUDA;
+    vr_ctx* c = new vr_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    for (auto& s : c->slots) {
+        if (cudaEventCreate(&s.ev_begin) != cudaSuccess || cudaEventCreate(&s.ev_march0) != cudaSuccess ||
+            cudaEventCreate(&s.ev_march1) != cudaSuccess || cudaEventCreate(&s.ev_end) != cudaSuccess ||
+            cudaMalloc(&s.d_stats, sizeof(vr::Stats)) != cudaSuccess ||
+            cudaMallocHost(&s.h_stats, sizeof(vr::Stats)) != cudaSuccess) {
+            vr_destroy(c);
+            return VR_ECUDA;
+        }
+        std::memset(s.h_stats, 0, sizeof(vr::Stats));
+    }
+    *out = c;
+    return VR_OK;
+}
+
+void vr_destroy(vr_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (auto& s : c->slots) {
+        if (s.pending) cudaEventSynchronize(s.ev_end);
+        if (s.h_items) cudaFreeHost(s.h_items);
+        if (s.h_tile_start) cudaFreeHost(s.h_tile_start);
+        if (s.h_stats) cudaFreeHost(s.h_stats);
+        if (s.h_frame) cudaFreeHost(s.h_frame);
+        cudaFree(s.d_frame);
+        cudaFree(s.d_items);
+        cudaFree(s.d_tile_start);
+        cudaFree(s.d_frags);
+        cudaFree(s.d_img);
+        cudaFree(s.d_stats);
+        for (cudaEvent_t ev : {s.ev_begin, s.ev_march0, s.ev_march1, s.ev_end})
+            if (ev) cudaEventDestroy(ev);
+    }
+    cudaFree(c->d_cube);
+    cudaFree(c->d_minmax);
+    delete c;
+}
+
+const char* vr_last_error(const vr_ctx* c) {
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+int vr_load_cube(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int64_t nz) {
+    if (!c) return VR_EINVAL;
+    if (!data) return fail(c, VR_EINVAL, "null cube");
+    if (nx < 2 || ny < 2 || nz < 2 || nx > 65536 || ny > 65536 || nz > 65536)
+        return fail(c, VR_EINVAL, "cube sizes must be in [2, 65536]");
+    VR_CUDA(c, cudaSetDevice(c->device));
+    int rc = retire_all(c);
+    if (rc) return rc;
+    const size_t bytes = (size_t)nx * ny * nz * sizeof(float);
+    cudaFree(c->d_cube);
+    c->d_cube = nullptr;
+    c->bricked = false;
+    if (cudaMalloc((void**)&c->d_cube, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, VR_ENOMEM, "cannot allocate the cube on the device");
+    }
+    VR_CUDA(c, cudaMemcpy(c->d_cube, data, bytes, cudaMemcpyDefault));
+    c->n[0] = nx;
+    c->n[1] = ny;
+    c->n[2] = nz;
+    return VR_OK;
+}
+
+int vr_brick(vr_ctx* c, int32_t bx, int32_t by, int32_t bz) {
+    if (!c) return VR_EINVAL;
+    if (!c->d_cube) return fail(c, VR_ESTATE, "vr_brick before vr_load_cube");
+    int32_t B[3] = {bx, by, bz};
+    for (int a = 0; a < 3; ++a)
+        if (B[a] < 1 || B[a] > 4096) return fail(c, VR_EINVAL, "brick sizes must be in [1, 4096]");
+    VR_CUDA(c, cudaSetDevice(c->device));
+    int rc = retire_all(c);
+    if (rc) return rc;
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) {
+        c->B[a] = B[a];
+        c->nb[a] = (int32_t)bricks_along(c->n[a], B[a]);
+        total *= c->nb[a];
+    }
+    if (total > (1 << 26)) return fail(c, VR_EINVAL, "too many bricks");
+    c->n_bricks = total;
+    cudaFree(c->d_minmax);
+    c->d_minmax = nullptr;
+    if (cudaMalloc((void**)&c->d_minmax, total * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, VR_ENOMEM, "cannot allocate brick min/max");
+    }
+    int32_t n32[3] = {(int32_t)c->n[0], (int32_t)c->n[1], (int32_t)c->n[2]};
+    VR_CUDA(c, vr::launch_brick_minmax(c->d_cube, n32, c->B, c->nb, c->d_minmax, 0));
+    c->h_minmax.resize(total);
+    VR_CUDA(c, cudaMemcpy(c->h_minmax.data(), c->d_minmax, total * sizeof(float2), cudaMemcpyDeviceToHost));
+    c->bricked = true;
+    return VR_OK;
+}
+
+int vr_get_brick_minmax(vr_ctx* c, float* out, int64_t n_bricks) {
+    if (!c) return VR_EINVAL;
+    if (!c->bricked) return fail(c, VR_ESTATE, "no bricking");
+    if (!out || n_bricks != c->n_bricks) return fail(c, VR_EINVAL, "n_bricks mismatch");
+    std::memcpy(out, c->h_minmax.data(), n_bricks * sizeof(float2));
+    return VR_OK;
+}
+
+int vr_set_transfer_function(vr_ctx* c, const double* pts, int32_t n) {
+    if (!c) return VR_EINVAL;
+    if (!pts || n < 2 || n > vr::kMaxTfPoints) return fail(c, VR_EINVAL, "need 2..256 control points");
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < 5; ++k)
+            if (!std::isfinite(pts[5 * i + k])) return fail(c, VR_EINVAL, "non-finite control point");
+        for (int k = 1; k < 5; ++k)
+            if (pts[5 * i + k] < 0.0 || pts[5 * i + k] > 1.0)
+                return fail(c, VR_EINVAL, "colour and opacity must be in [0, 1]");
+        if (i > 0 && !(pts[5 * i] > pts[5 * (i - 1)]))
+            return fail(c, VR_EINVAL, "control values must increase strictly");
+    }
+    c->tf.assign(pts, pts + 5 * n);
+    c->tf_rgba.resize(n);
+    c->tf_v.resize(n);
+    for (int i = 0; i < n; ++i) {
+        c->tf_rgba[i] = make_float4((float)pts[5 * i + 1], (float)pts[5 * i + 2], (float)pts[5 * i + 3],
+                                    (float)pts[5 * i + 4]);
+        c->tf_v[i] = (float)pts[5 * i];
+    }
+    const double v0 = pts[0], dv = (pts[5 * (n - 1)] - pts[0]) / (n - 1);
+    bool uniform = true;
+    for (int i = 0; i < n; ++i)
+        if (std::fabs(pts[5 * i] - (v0 + i * dv)) > 1e-9 * std::max(1.0, std::fabs(pts[5 * i])))
+            uniform = false;
+    c->tf_uniform = uniform ? 1 : 0;
+    c->tf_v0 = (float)v0;
+    c->tf_inv_dv = (float)(1.0 / dv);
+    c->tf_set = true;
+    return VR_OK;
+}
+
+int vr_set_camera(vr_ctx* c, const vr_camera* cam) {
+    if (!c) return VR_EINVAL;
+    if (!cam || !camera_valid(*cam)) return fail(c, VR_EINVAL, "invalid camera");
+    Basis b;
+    if (!make_basis(*cam, b)) return fail(c, VR_EINVAL, "degenerate camera basis (eye == target or up parallel to view)");
+    c->q.resize((size_t)cam->width + cam->height);
+    for (int i = 0; i < cam->width; ++i)
+        c->q[i] = vr::df_from_double((2.0 * (i + 0.5) / cam->width - 1.0) * b.tan_half * b.aspect);
+    for (int j = 0; j < cam->height; ++j)
+        c->q[cam->width + j] = vr::df_from_double((1.0 - 2.0 * (j + 0.5) / cam->height) * b.tan_half);
+    if (!c->cam_set || cam->step != c->cam.step)
+        c->alpha_poly_n = fit_alpha_poly(cam->step / 1.0, 0.5, c->alpha_poly);
+    c->cam = *cam;
+    c->basis = b;
+    c->cam_set = true;
+    return VR_OK;
+}
+
+int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
+    if (!c) return VR_EINVAL;
+    switch (option) {
+        case VR_OPT_SKIP_EMPTY: c->skip_empty = value != 0; return VR_OK;
+        case VR_OPT_RECT_CULL: c->rect_cull = value != 0; return VR_OK;
+        case VR_OPT_MODE:
+            if (value != 0 && value != 1) return fail(c, VR_EINVAL, "mode must be 0 or 1");
+            c->mode = (int)value;
+            return VR_OK;
+        default: return fail(c, VR_EINVAL, "unknown option");
+    }
+}
+
+int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
+    if (!c) return VR_EINVAL;
+    if (!c->d_cube || !c->bricked || !c->tf_set || !c->cam_set)
+        return fail(c, VR_ESTATE, "vr_render needs vr_load_cube, vr_brick, vr_set_transfer_function and vr_set_camera first");
+    if (!out_rgba) return fail(c, VR_EINVAL, "null output");
+    VR_CUDA(c, cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)stream_ptr;
+    cudaPointerAttributes attr;
+    bool out_on_device = false;
+    if (cudaPointerGetAttributes(&attr, out_rgba) == cudaSuccess)
+        out_on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    else
+        cudaGetLastError();
+
+    Slot& s = c->slots[c->next_slot];
+    c->next_slot = (c->next_slot + 1) % kSlots;
+    int rc = retire(c, s);
+    if (rc) return rc;
+
+    auto t0 = std::chrono::steady_clock::now();
+    int32_t tiles_x, tiles_y;
+    int64_t n_items;
+    rc = plan_frame(c, s, tiles_x, tiles_y, n_items);
+    if (rc) return rc;
+    s.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
+    const size_t img_px = (size_t)c->cam.width * c->cam.height;
+
+    if ((rc = grow_device(c, s.d_items, s.dcap_items, (size_t)std::max<int64_t>(n_items, 1)))) return rc;
+    if ((rc = grow_device(c, s.d_tile_start, s.dcap_tiles, (size_t)n_tiles + 1))) return rc;
+    if ((rc = grow_device(c, s.d_frags, s.cap_frags,
+                          (size_t)std::max<int64_t>(n_items, 1) * vr::kTilePixels)))
+        return rc;
+    if (!out_on_device && (rc = grow_device(c, s.d_img, s.cap_img, img_px))) return rc;
+    // per-frame constants: camera tables (df) and the transfer function
+    const size_t q_bytes = c->q.size() * sizeof(df);
+    const size_t tf_rgba_off = (q_bytes + 15) / 16 * 16;
+    const size_t tf_v_off = tf_rgba_off + c->tf_rgba.size() * sizeof(float4);
+    const size_t frame_bytes = tf_v_off + c->tf_v.size() * sizeof(float);
+    if ((rc = grow_pinned(c, s.h_frame, s.cap_frame, frame_bytes))) return rc;
+    if ((rc = grow_device(c, s.d_frame, s.dcap_frame, frame_bytes))) return rc;
+    std::memcpy(s.h_frame, c->q.data(), q_bytes);
+    std::memcpy(s.h_frame + tf_rgba_off, c->tf_rgba.data(), c->tf_rgba.size() * sizeof(float4));
+    std::memcpy(s.h_frame + tf_v_off, c->tf_v.data(), c->tf_v.size() * sizeof(float));
+
+    vr::FrameParams p;
+    std::memset(&p, 0, sizeof(p));
+    for (int a = 0; a < 3; ++a) {
+        p.eye[a] = vr::df_from_double(c->cam.eye[a]);
+        p.f[a] = vr::df_from_double(c->basis.f[a]);
+        p.r[a] = vr::df_from_double(c->basis.r[a]);
+        p.u[a] = vr::df_from_double(c->basis.u[a]);
+        p.n[a] = (int32_t)c->n[a];
+        p.B[a] = c->B[a];
+        p.nb[a] = c->nb[a];
+    }
+    p.qx = reinterpret_cast<const df*>(s.d_frame);
+    p.qy = reinterpret_cast<const df*>(s.d_frame) + c->cam.width;
+    p.width = c->cam.width;
+    p.height = c->cam.height;
+    p.tiles_x = tiles_x;
+    p.tiles_y = tiles_y;
+    p.dt = vr::df_from_double(c->cam.step);
+    p.dt_f = (float)c->cam.step;
+    p.tau = (float)c->cam.term_alpha;
+    p.cube = c->d_cube;
+    p.stride_y = c->n[0];
+    p.stride_z = c->n[0] * c->n[1];
+    p.tf_rgba = reinterpret_cast<const float4*>(s.d_frame + tf_rgba_off);
+    p.tf_v = reinterpret_cast<const float*>(s.d_frame + tf_v_off);
+    p.tf_n = (int32_t)(c->tf.size() / 5);
+    p.tf_uniform = c->tf_uniform;
+    p.tf_v0 = c->tf_v0;
+    p.tf_inv_dv = c->tf_inv_dv;
+    std::memcpy(p.alpha_poly, c->alpha_poly, sizeof(p.alpha_poly));
+    p.alpha_poly_n = c->alpha_poly_n;
+    p.alpha_split = 0.5f;
+    p.poly_scale = 2.0f / 0.5f;
+    p.mode = c->mode;
+    p.items = s.d_items;
+    p.n_items = (int32_t)n_items;
+    p.tile_start = s.d_tile_start;
+    p.frags = s.d_frags;
+    p.out = out_on_device ? reinterpret_cast<float4*>(out_rgba) : s.d_img;
+    p.stats = s.d_stats;
+
+    VR_CUDA(c, cudaEventRecord(s.ev_begin, st));
+    VR_CUDA(c, cudaMemcpyAsync(s.d_frame, s.h_frame, frame_bytes, cudaMemcpyHostToDevice, st));
+    VR_CUDA(c, cudaMemcpyAsync(s.d_items, s.h_items, (size_t)n_items * sizeof(vr::Item),
+                               cudaMemcpyHostToDevice, st));
+    VR_CUDA(c, cudaMemcpyAsync(s.d_tile_start, s.h_tile_start, ((size_t)n_tiles + 1) * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+    VR_CUDA(c, cudaMemsetAsync(s.d_stats, 0, sizeof(vr::Stats), st));
+    VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
+    VR_CUDA(c, vr::launch_march(p, st));
+    VR_CUDA(c, cudaEventRecord(s.ev_march1, st));
+    VR_CUDA(c, vr::launch_composite(p, st));
+    VR_CUDA(c, cudaMemcpyAsync(s.h_stats, s.d_stats, sizeof(vr::Stats), cudaMemcpyDeviceToHost, st));
+    VR_CUDA(c, cudaEventRecord(s.ev_end, st));
+    s.pending = true;
+    s.launches = (n_items > 0 ? 1 : 0) + 1;
+    s.h2d_bytes = (int64_t)(frame_bytes + (size_t)n_items * sizeof(vr::Item) +
+                            ((size_t)n_tiles + 1) * sizeof(int32_t));
+    s.d2h_bytes = (int64_t)sizeof(vr::Stats) + (out_on_device ? 0 : (int64_t)(img_px * sizeof(float4)));
+    if (!out_on_device) {
+        VR_CUDA(c, cudaMemcpyAsync(out_rgba, s.d_img, img_px * sizeof(float4), cudaMemcpyDeviceToHost, st));
+        VR_CUDA(c, cudaStreamSynchronize(st));
+    }
+    return VR_OK;
+}
+
+int vr_get_stats(vr_ctx* c, vr_stats* out) {
+    if (!c) return VR_EINVAL;
+    if (!out) return fail(c, VR_EINVAL, "null stats");
+    VR_CUDA(c, cudaSetDevice(c->device));
+    int rc = retire_all(c);
+    if (rc) return rc;
+    *out = c->acc;
+    return VR_OK;
+}
+
+int vr_reset_stats(vr_ctx* c) {
+    if (!c) return VR_EINVAL;
+    VR_CUDA(c, cudaSetDevice(c->device));
+    int rc = retire_all(c);
+    if (rc) return rc;
+    std::memset(&c->acc, 0, sizeof(c->acc));
+    return VR_OK;
+}
+
+int vr_plan_brick_rects(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz, int32_t bx,
+                        int32_t by, int32_t bz, int32_t* rects, int64_t n_bricks) {
+    if (!cam || !rects || !camera_valid(*cam)) return VR_EINVAL;
+    if (nx < 2 || ny < 2 || nz < 2 || bx < 1 || by < 1 || bz < 1) return VR_EINVAL;
+    Basis b;
+    if (!make_basis(*cam, b)) return VR_EINVAL;
+    const int64_t n[3] = {nx, ny, nz};
+    const int32_t B[3] = {bx, by, bz};
+    const int64_t nb[3] = {bricks_along(nx, bx), bricks_along(ny, by), bricks_along(nz, bz)};
+    if (nb[0] * nb[1] * nb[2] != n_bricks) return VR_EINVAL;
+    for (int64_t id = 0; id < n_bricks; ++id) {
+        int64_t idx[3] = {id % nb[0], (id / nb[0]) % nb[1], id / (nb[0] * nb[1])};
+        double lo[3], hi[3];
+        brick_box(n, B, idx, lo, hi);
+        box_rect(*cam, b, lo, hi, rects + 4 * id);
+    }
+    return VR_OK;
+}
+
+}  // extern "C"

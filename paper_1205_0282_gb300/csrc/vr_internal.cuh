@@ -1,0 +1,80 @@
+// Structures shared by the host planner (vr_host.cu) and the kernels (vr_kernels.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "df.cuh"
+
+namespace vr {
+
+constexpr int kTile = 8;                    // pixel tile edge (items are brick x 8x8 tile)
+constexpr int kTilePixels = kTile * kTile;  // 64 rays per item, one per thread
+constexpr int kMaxTfPoints = 256;
+constexpr int kAlphaPolyMax = 17;           // coefficients of the opacity-correction polynomial
+
+// Device error flags (OR-ed into Stats::errors).
+constexpr int kErrBounds = 1;               // a sample index left its brick's voxel range
+
+// One work item: the rays of one pixel tile restricted to the samples one brick owns.
+struct Item {
+    int32_t brick;  // brick id = ix + nbx*(iy + nby*iz)
+    int32_t tile;   // tile id = tx + tiles_x*ty
+    int32_t frag;   // fragment slot: its 64 float4 sub-image pixels live at frag*64
+    int32_t pad;
+};
+
+// Per-frame device counters.
+struct Stats {
+    unsigned long long samples;
+    int errors;
+    int pad;
+};
+
+// Everything a frame's kernels need, passed by value.
+struct FrameParams {
+    // camera (double-float)
+    df eye[3];
+    df f[3], r[3], u[3];
+    const df* qx;  // per column: (2(i+.5)/W - 1) tan(fovy/2) W/H
+    const df* qy;  // per row:    (1 - 2(j+.5)/H) tan(fovy/2)
+    int32_t width, height, tiles_x, tiles_y;
+    df dt;          // step (voxels)
+    float dt_f;
+    float tau;      // termination opacity
+
+    // volume
+    const float* cube;
+    int32_t n[3];          // nx, ny, nz
+    int32_t B[3];          // brick size
+    int32_t nb[3];         // bricks per axis
+    int64_t stride_y, stride_z;
+
+    // transfer function: control points (r,g,b,a) and their values
+    const float4* tf_rgba;
+    const float* tf_v;
+    int32_t tf_n;
+    int32_t tf_uniform;    // 1: v_i = v0 + i*dv
+    float tf_v0, tf_inv_dv;
+    // opacity correction alpha(a) = 1 - (1-a)^dt as a * Q(a) for a <= alpha_split
+    float alpha_poly[kAlphaPolyMax];  // Q in powers of t = a * poly_scale - 1
+    int32_t alpha_poly_n;
+    float poly_scale;
+    float alpha_split;
+    int32_t mode;          // 0 = emission-absorption, 1 = MIP
+
+    // plan
+    const Item* items;
+    int32_t n_items;
+    const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
+    float4* frags;
+    float4* out;
+    Stats* stats;
+};
+
+// Launchers (vr_kernels.cu).
+cudaError_t launch_brick_minmax(const float* cube, const int32_t n[3], const int32_t B[3],
+                                const int32_t nb[3], float2* out, cudaStream_t s);
+cudaError_t launch_march(const FrameParams& p, cudaStream_t s);
+cudaError_t launch_composite(const FrameParams& p, cudaStream_t s);
+
+}  // namespace vr

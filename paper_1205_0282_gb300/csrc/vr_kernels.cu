@@ -1,0 +1,325 @@
+// Device code of the bricked ray caster (Hassan, Fluke & Barnes, arXiv:1205.0282).
+//
+//   brick_minmax_kernel   Section 2.3.1: per-sub-cube minimum and maximum, computed on
+//                         the GPU once the data is resident (used for exact empty-space
+//                         skipping of bricks whose transfer-function opacity is zero).
+//   march_kernel          Section 2.3.2: per-pixel ray casting restricted to one brick's
+//                         samples (entry/exit, tri-linear sampling, transfer function,
+//                         opacity correction, front-to-back compositing, termination).
+//                         One CTA renders one (brick, 8x8 pixel tile) work item into a
+//                         sub-image fragment.
+//   composite_kernel      Section 2.3.3: sort-last composition of the per-brick
+//                         sub-images with the associative 'over' operator, in view
+//                         order, stopping once the pixel is opaque; or, for maximum
+//                         intensity projection, the maximum then the colour map.
+#include <cfloat>
+#include <cstdint>
+
+#include "vr_internal.cuh"
+
+namespace vr {
+
+// ------------------------------------------------------------------ brick min/max
+
+__global__ void brick_minmax_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb,
+                                    float2* __restrict__ out) {
+    const int id = blockIdx.x;
+    const int bx = id % nb.x, by = (id / nb.x) % nb.y, bz = id / (nb.x * nb.y);
+    const int x0 = bx * B.x, y0 = by * B.y, z0 = bz * B.z;
+    const int x1 = min(x0 + B.x, n.x - 1), y1 = min(y0 + B.y, n.y - 1), z1 = min(z0 + B.z, n.z - 1);
+    const int ny_rows = y1 - y0 + 1, rows = ny_rows * (z1 - z0 + 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    float mn = FLT_MAX, mx = -FLT_MAX;
+    for (int r = warp; r < rows; r += nwarps) {
+        const int z = z0 + r / ny_rows, y = y0 + r % ny_rows;
+        const float* row = cube + ((int64_t)z * n.y + y) * (int64_t)n.x;
+        for (int x = x0 + lane; x <= x1; x += 32) {
+            float v = __ldg(row + x);
+            mn = fminf(mn, v);
+            mx = fmaxf(mx, v);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __shared__ float smn[32], smx[32];
+    if (lane == 0) {
+        smn[warp] = mn;
+        smx[warp] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nwarps; ++w) {
+            mn = fminf(mn, smn[w]);
+            mx = fmaxf(mx, smx[w]);
+        }
+        out[id] = make_float2(mn, mx);
+    }
+}
+
+cudaError_t launch_brick_minmax(const float* cube, const int32_t n[3], const int32_t B[3],
+                                const int32_t nb[3], float2* out, cudaStream_t s) {
+    const int total = nb[0] * nb[1] * nb[2];
+    brick_minmax_kernel<<<total, 256, 0, s>>>(cube, make_int3(n[0], n[1], n[2]),
+                                              make_int3(B[0], B[1], B[2]),
+                                              make_int3(nb[0], nb[1], nb[2]), out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ ray set-up
+
+// Ray of pixel (i, j) in double-float: unit direction d, entry point pe and the
+// sample count n = #{k >= 0 : k dt < t1 - t0}.  Returns false if the ray misses
+// the domain [0, n-1]^3.
+__device__ bool setup_ray(const FrameParams& p, int i, int j, df d[3], df pe[3], int& n_samples) {
+    const df qx = p.qx[i], qy = p.qy[j];
+    df dun[3];
+    for (int a = 0; a < 3; ++a) dun[a] = df_add(df_add(p.f[a], df_mul(qx, p.r[a])), df_mul(qy, p.u[a]));
+    df n2 = df_add(df_add(df_mul(dun[0], dun[0]), df_mul(dun[1], dun[1])), df_mul(dun[2], dun[2]));
+    df len = df_sqrt(n2);
+    for (int a = 0; a < 3; ++a) d[a] = df_div(dun[a], len);
+
+    df tn = df_make(-FLT_MAX), tf = df_make(FLT_MAX);
+    for (int a = 0; a < 3; ++a) {
+        const df hi = df_make((float)(p.n[a] - 1));
+        if (df_is_zero(d[a])) {
+            if (df_lt(p.eye[a], df_make(0.0f)) || df_gt(p.eye[a], hi)) return false;
+            continue;
+        }
+        df ta = df_div(df_neg(p.eye[a]), d[a]);
+        df tb = df_div(df_sub(hi, p.eye[a]), d[a]);
+        tn = df_max(tn, df_min(ta, tb));
+        tf = df_min(tf, df_max(ta, tb));
+    }
+    const df t0 = df_max(tn, df_make(0.0f));
+    if (!df_gt(tf, t0)) return false;
+    const df L = df_sub(tf, t0);
+    n_samples = (int)df_ceil(df_div(L, p.dt));
+    for (int a = 0; a < 3; ++a) pe[a] = df_add(p.eye[a], df_mul(t0, d[a]));
+    return n_samples > 0;
+}
+
+// Sample range [klo, khi) owned by brick bidx (sample p_k = pe + k dt d belongs to
+// brick floor(p/B) per axis, first and last bricks open towards the outside).
+__device__ void brick_range(const FrameParams& p, const int bidx[3], const df d[3], const df pe[3],
+                            int n_samples, int& klo, int& khi) {
+    float lo = 0.0f, hi = (float)n_samples;
+    for (int a = 0; a < 3; ++a) {
+        const df D = df_mul(p.dt, d[a]);
+        const float O = (float)(bidx[a] * p.B[a]);
+        const float OB = (float)(bidx[a] * p.B[a] + p.B[a]);
+        if (bidx[a] > 0) {
+            if (D.hi > 0.0f) {
+                lo = fmaxf(lo, df_ceil(df_div(df_sub(df_make(O), pe[a]), D)));
+            } else if (D.hi < 0.0f) {
+                hi = fminf(hi, df_floor(df_div(df_sub(df_make(O), pe[a]), D)) + 1.0f);
+            } else if (df_lt(pe[a], df_make(O))) {
+                hi = -1.0f;
+            }
+        }
+        if (bidx[a] < p.nb[a] - 1) {
+            if (D.hi > 0.0f) {
+                hi = fminf(hi, df_ceil(df_div(df_sub(df_make(OB), pe[a]), D)));
+            } else if (D.hi < 0.0f) {
+                lo = fmaxf(lo, df_floor(df_div(df_sub(df_make(OB), pe[a]), D)) + 1.0f);
+            } else if (!df_lt(pe[a], df_make(OB))) {
+                hi = -1.0f;
+            }
+        }
+    }
+    lo = fmaxf(lo, 0.0f);
+    hi = fminf(hi, (float)n_samples);
+    klo = (int)lo;
+    khi = hi > lo ? (int)hi : klo;
+}
+
+// ------------------------------------------------------------------ per-sample ops
+
+struct TfShared {
+    float4 rgba[kMaxTfPoints];
+    float v[kMaxTfPoints];
+};
+
+__device__ __forceinline__ float4 tf_lookup(const FrameParams& p, const TfShared& s, float v) {
+    int seg;
+    float w;
+    if (p.tf_uniform) {
+        float x = (v - p.tf_v0) * p.tf_inv_dv;
+        x = fminf(fmaxf(x, 0.0f), (float)(p.tf_n - 1));
+        seg = min((int)x, p.tf_n - 2);
+        w = x - (float)seg;
+    } else {
+        int lo = 0, hi = p.tf_n - 1;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (v >= s.v[mid]) lo = mid;
+            else hi = mid;
+        }
+        seg = lo;
+        w = (v - s.v[seg]) / (s.v[seg + 1] - s.v[seg]);
+        w = fminf(fmaxf(w, 0.0f), 1.0f);
+    }
+    const float4 c0 = s.rgba[seg], c1 = s.rgba[seg + 1];
+    return make_float4(fmaf(w, c1.x - c0.x, c0.x), fmaf(w, c1.y - c0.y, c0.y),
+                       fmaf(w, c1.z - c0.z, c0.z), fmaf(w, c1.w - c0.w, c0.w));
+}
+
+// alpha = 1 - (1 - a)^dt.  For a <= alpha_split: a * Q(t), Q a polynomial fit of
+// alpha(a)/a in t = a*scale - 1 (exactly 0 at a = 0, accurate to ~1e-9); above it
+// the exponential form.
+__device__ __forceinline__ float opacity_correct(const FrameParams& p, float a) {
+    if (a <= p.alpha_split) {
+        const float t = fmaf(a, p.poly_scale, -1.0f);
+        float q = p.alpha_poly[p.alpha_poly_n - 1];
+        for (int k = p.alpha_poly_n - 2; k >= 0; --k) q = fmaf(q, t, p.alpha_poly[k]);
+        return a * q;
+    }
+    return 1.0f - exp2f(p.dt_f * __log2f(1.0f - a));
+}
+
+// ------------------------------------------------------------------ ray march
+
+__global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p) {
+    __shared__ TfShared s_tf;
+    for (int k = threadIdx.x; k < p.tf_n; k += blockDim.x) {
+        s_tf.rgba[k] = p.tf_rgba[k];
+        s_tf.v[k] = p.tf_v[k];
+    }
+    __syncthreads();
+
+    const Item item = p.items[blockIdx.x];
+    const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+    const int tx = item.tile % p.tiles_x, ty = item.tile / p.tiles_x;
+    const int i = tx * kTile + lx, j = ty * kTile + ly;
+    int bidx[3];
+    bidx[0] = item.brick % p.nb[0];
+    bidx[1] = (item.brick / p.nb[0]) % p.nb[1];
+    bidx[2] = item.brick / (p.nb[0] * p.nb[1]);
+
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float vmax = -FLT_MAX;
+    int taken = 0;
+    df d[3], pe[3];
+    int n_samples = 0;
+    if (i < p.width && j < p.height && setup_ray(p, i, j, d, pe, n_samples)) {
+        int klo, khi;
+        brick_range(p, bidx, d, pe, n_samples, klo, khi);
+        if (khi > klo) {
+            int O[3], imax[3];
+            float qs[3], dq[3], qmax[3];
+            for (int a = 0; a < 3; ++a) {
+                O[a] = bidx[a] * p.B[a];
+                imax[a] = min(p.B[a] - 1, p.n[a] - 2 - O[a]);
+                qmax[a] = (float)min(p.B[a], p.n[a] - 1 - O[a]);
+                const df D = df_mul(p.dt, d[a]);
+                qs[a] = df_to_float(df_add_f(df_add(pe[a], df_mul_f(D, (float)klo)), -(float)O[a]));
+                dq[a] = df_to_float(D);
+            }
+            const float* __restrict__ base =
+                p.cube + (int64_t)O[2] * p.stride_z + (int64_t)O[1] * p.stride_y + O[0];
+            const int64_t sy = p.stride_y, sz = p.stride_z;
+            const int nk = khi - klo;
+            for (int kk = 0; kk < nk; ++kk) {
+                const float fk = (float)kk;
+                float c[3], f[3];
+                int ix[3];
+                for (int a = 0; a < 3; ++a) {
+                    c[a] = fminf(fmaxf(fmaf(fk, dq[a], qs[a]), 0.0f), qmax[a]);
+                    ix[a] = min((int)c[a], imax[a]);
+                    f[a] = c[a] - (float)ix[a];
+                }
+                const float* b = base + (int64_t)ix[2] * sz + (int64_t)ix[1] * sy + ix[0];
+                const float v000 = __ldg(b), v100 = __ldg(b + 1);
+                const float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
+                const float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
+                const float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
+                const float c00 = fmaf(f[0], v100 - v000, v000);
+                const float c10 = fmaf(f[0], v110 - v010, v010);
+                const float c01 = fmaf(f[0], v101 - v001, v001);
+                const float c11 = fmaf(f[0], v111 - v011, v011);
+                const float c0 = fmaf(f[1], c10 - c00, c00);
+                const float c1 = fmaf(f[1], c11 - c01, c01);
+                const float v = fmaf(f[2], c1 - c0, c0);
+                ++taken;
+                if (p.mode == 1) {
+                    vmax = fmaxf(vmax, v);
+                    continue;
+                }
+                const float4 col = tf_lookup(p, s_tf, v);
+                const float alpha = opacity_correct(p, col.w);
+                const float w = (1.0f - acc.w) * alpha;
+                acc.x = fmaf(w, col.x, acc.x);
+                acc.y = fmaf(w, col.y, acc.y);
+                acc.z = fmaf(w, col.z, acc.z);
+                acc.w += w;
+                if (acc.w >= p.tau) break;
+            }
+        }
+    }
+    if (p.mode == 1) acc = make_float4(vmax, taken > 0 ? 1.0f : 0.0f, 0.0f, 0.0f);
+    p.frags[(int64_t)item.frag * kTilePixels + threadIdx.x] = acc;
+
+    // sample count: warp reduction then one atomic per warp
+    unsigned long long t = (unsigned long long)taken;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(&p.stats->samples, t);
+}
+
+cudaError_t launch_march(const FrameParams& p, cudaStream_t s) {
+    if (p.n_items == 0) return cudaSuccess;
+    march_kernel<<<p.n_items, kTilePixels, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ composite
+
+__global__ void __launch_bounds__(kTilePixels) composite_kernel(const FrameParams p) {
+    __shared__ TfShared s_tf;
+    if (p.mode == 1) {
+        for (int k = threadIdx.x; k < p.tf_n; k += blockDim.x) {
+            s_tf.rgba[k] = p.tf_rgba[k];
+            s_tf.v[k] = p.tf_v[k];
+        }
+        __syncthreads();
+    }
+    const int t = blockIdx.x;
+    const int tx = t % p.tiles_x, ty = t / p.tiles_x;
+    const int i = tx * kTile + threadIdx.x % kTile, j = ty * kTile + threadIdx.x / kTile;
+    if (i >= p.width || j >= p.height) return;
+    const int f0 = p.tile_start[t], f1 = p.tile_start[t + 1];
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (p.mode == 0) {
+        for (int f = f0; f < f1; ++f) {
+            if (acc.w >= p.tau) break;
+            const float4 fr = p.frags[(int64_t)f * kTilePixels + threadIdx.x];
+            const float tr = 1.0f - acc.w;
+            acc.x = fmaf(tr, fr.x, acc.x);
+            acc.y = fmaf(tr, fr.y, acc.y);
+            acc.z = fmaf(tr, fr.z, acc.z);
+            acc.w = fmaf(tr, fr.w, acc.w);
+        }
+    } else {
+        float vmax = -FLT_MAX;
+        bool any = false;
+        for (int f = f0; f < f1; ++f) {
+            const float4 fr = p.frags[(int64_t)f * kTilePixels + threadIdx.x];
+            if (fr.y > 0.0f) {
+                vmax = fmaxf(vmax, fr.x);
+                any = true;
+            }
+        }
+        if (any) {
+            const float4 c = tf_lookup(p, s_tf, vmax);
+            acc = make_float4(c.x * c.w, c.y * c.w, c.z * c.w, c.w);
+        }
+    }
+    p.out[(int64_t)j * p.width + i] = acc;
+}
+
+cudaError_t launch_composite(const FrameParams& p, cudaStream_t s) {
+    composite_kernel<<<p.tiles_x * p.tiles_y, kTilePixels, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace vr

@@ -1,0 +1,290 @@
+"""Python binding of the C ABI in ``include/vr.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; all rendering
+work runs in ``libvr.so``'s CUDA kernels.  PyTorch is used only to hand over
+device buffers and streams.  There is no fallback: if ``libvr.so`` is missing
+the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libvr.so")
+
+VR_OK = 0
+VR_EINVAL = -1
+VR_ENOMEM = -2
+VR_ECUDA = -3
+VR_ESTATE = -4
+VR_ETIMEOUT = -5
+
+VR_OPT_SKIP_EMPTY = 1
+VR_OPT_RECT_CULL = 2
+VR_OPT_MODE = 3
+
+_ERR_NAMES = {VR_EINVAL: "VR_EINVAL", VR_ENOMEM: "VR_ENOMEM", VR_ECUDA: "VR_ECUDA",
+              VR_ESTATE: "VR_ESTATE", VR_ETIMEOUT: "VR_ETIMEOUT"}
+
+
+class VRError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class vr_camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_double * 3), ("target", ctypes.c_double * 3),
+                ("up", ctypes.c_double * 3), ("fovy_deg", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("step", ctypes.c_double), ("term_alpha", ctypes.c_double)]
+
+
+class vr_stats(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_int64), ("samples", ctypes.c_int64),
+                ("items", ctypes.c_int64), ("fragments", ctypes.c_int64),
+                ("bricks_rendered", ctypes.c_int64), ("bricks_skipped", ctypes.c_int64),
+                ("touched_bytes", ctypes.c_int64), ("march_ms", ctypes.c_double),
+                ("composite_ms", ctypes.c_double), ("frame_ms", ctypes.c_double),
+                ("plan_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("device_errors", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+# The exported symbols, in header order (tests check them against include/vr.h).
+EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_brick", "vr_set_transfer_function",
+           "vr_set_camera", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
+           "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_last_error"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1205_0282_gb300.build` "
+                          "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.vr_create.argtypes = [ctypes.POINTER(P), I32]
+    lib.vr_destroy.argtypes = [P]
+    lib.vr_destroy.restype = None
+    lib.vr_load_cube.argtypes = [P, P, I64, I64, I64]
+    lib.vr_brick.argtypes = [P, I32, I32, I32]
+    lib.vr_set_transfer_function.argtypes = [P, P, I32]
+    lib.vr_set_camera.argtypes = [P, ctypes.POINTER(vr_camera)]
+    lib.vr_set_option.argtypes = [P, I32, I64]
+    lib.vr_render.argtypes = [P, P, P]
+    lib.vr_get_stats.argtypes = [P, ctypes.POINTER(vr_stats)]
+    lib.vr_reset_stats.argtypes = [P]
+    lib.vr_get_brick_minmax.argtypes = [P, P, I64]
+    lib.vr_plan_brick_rects.argtypes = [ctypes.POINTER(vr_camera), I64, I64, I64, I32, I32, I32,
+                                        P, I64]
+    lib.vr_last_error.argtypes = [P]
+    lib.vr_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("vr_destroy", "vr_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(ctx, rc: int):
+    if rc != VR_OK:
+        msg = _lib.vr_last_error(ctx).decode() if ctx else ""
+        raise VRError(rc, msg)
+
+
+def make_camera(cam: dict) -> vr_camera:
+    c = vr_camera()
+    c.eye[:] = cam["eye"]
+    c.target[:] = cam["target"]
+    c.up[:] = cam["up"]
+    c.fovy_deg = cam["fovy_deg"]
+    c.width = cam["width"]
+    c.height = cam["height"]
+    c.step = cam["step"]
+    c.term_alpha = cam["term_alpha"]
+    return c
+
+
+def _ptr(buf):
+    """(address, keep-alive) of a numpy array or torch tensor."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return buf.ctypes.data, buf
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr(), buf
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------- C-ABI calls
+
+def vr_create(device: int = 0):
+    h = ctypes.c_void_p()
+    rc = _lib.vr_create(ctypes.byref(h), device)
+    _check(None, rc)
+    return h
+
+
+def vr_destroy(ctx) -> None:
+    _lib.vr_destroy(ctx)
+
+
+def vr_load_cube(ctx, cube) -> None:
+    """cube: float32 (nz, ny, nx), numpy (host) or torch (host or device)."""
+    if getattr(cube, "dtype", None) not in (np.float32,) and str(getattr(cube, "dtype", "")) != "torch.float32":
+        raise TypeError("cube must be float32")
+    nz, ny, nx = cube.shape
+    addr, keep = _ptr(cube)
+    _check(ctx, _lib.vr_load_cube(ctx, addr, nx, ny, nz))
+
+
+def vr_brick(ctx, bx: int, by: int, bz: int) -> None:
+    _check(ctx, _lib.vr_brick(ctx, bx, by, bz))
+
+
+def vr_set_transfer_function(ctx, points) -> None:
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 5)
+    _check(ctx, _lib.vr_set_transfer_function(ctx, pts.ctypes.data, len(pts)))
+
+
+def vr_set_camera(ctx, cam: dict) -> None:
+    c = make_camera(cam)
+    _check(ctx, _lib.vr_set_camera(ctx, ctypes.byref(c)))
+
+
+def vr_set_option(ctx, option: int, value: int) -> None:
+    _check(ctx, _lib.vr_set_option(ctx, option, int(value)))
+
+
+def vr_render(ctx, out, stream=None) -> None:
+    """Render into ``out`` (float32 (H, W, 4)): a CUDA tensor is written
+    asynchronously on ``stream`` (default: torch's current stream); a numpy
+    array or CPU tensor is filled synchronously."""
+    addr, keep = _ptr(out)
+    on_device = hasattr(out, "is_cuda") and out.is_cuda
+    _check(ctx, _lib.vr_render(ctx, addr, _stream_handle(stream) if on_device else None))
+
+
+def vr_get_stats(ctx) -> dict:
+    s = vr_stats()
+    _check(ctx, _lib.vr_get_stats(ctx, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in vr_stats._fields_ if name != "reserved"}
+
+
+def vr_reset_stats(ctx) -> None:
+    _check(ctx, _lib.vr_reset_stats(ctx))
+
+
+def vr_get_brick_minmax(ctx, n_bricks: int) -> np.ndarray:
+    out = np.zeros((n_bricks, 2), dtype=np.float32)
+    _check(ctx, _lib.vr_get_brick_minmax(ctx, out.ctypes.data, n_bricks))
+    return out
+
+
+def vr_plan_brick_rects(cam: dict, shape_xyz, brick) -> np.ndarray:
+    """Host-only: rendering rectangle (x0, y0, x1, y1) of every brick."""
+    nb = [(n - 1 + b - 1) // b for n, b in zip(shape_xyz, brick)]
+    n_bricks = nb[0] * nb[1] * nb[2]
+    rects = np.zeros((n_bricks, 4), dtype=np.int32)
+    c = make_camera(cam)
+    rc = _lib.vr_plan_brick_rects(ctypes.byref(c), *shape_xyz, *brick, rects.ctypes.data, n_bricks)
+    if rc != VR_OK:
+        raise VRError(rc, "vr_plan_brick_rects rejected its arguments")
+    return rects
+
+
+def vr_last_error(ctx) -> str:
+    return _lib.vr_last_error(ctx).decode()
+
+
+# ------------------------------------------------------------------ convenience
+
+class VolumeRenderer:
+    """Owns one context; methods call the entry points above."""
+
+    def __init__(self, device: int = 0):
+        self.ctx = vr_create(device)
+        self.shape_xyz = None
+        self.brick_size = None
+        self.camera = None
+
+    def close(self):
+        if self.ctx:
+            vr_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_cube(self, cube):
+        vr_load_cube(self.ctx, cube)
+        nz, ny, nx = cube.shape
+        self.shape_xyz = (nx, ny, nz)
+
+    def brick(self, bx, by, bz):
+        vr_brick(self.ctx, bx, by, bz)
+        self.brick_size = (bx, by, bz)
+
+    @property
+    def n_bricks(self):
+        nb = [(n - 1 + b - 1) // b for n, b in zip(self.shape_xyz, self.brick_size)]
+        return nb[0] * nb[1] * nb[2]
+
+    def set_transfer_function(self, tf):
+        vr_set_transfer_function(self.ctx, tf)
+
+    def set_camera(self, cam):
+        vr_set_camera(self.ctx, cam)
+        self.camera = dict(cam)
+
+    def set_option(self, option, value):
+        vr_set_option(self.ctx, option, value)
+
+    def render(self, out=None, stream=None):
+        """Render one frame; returns ``out`` (allocates a CUDA tensor if None)."""
+        if out is None:
+            import torch
+            out = torch.empty((self.camera["height"], self.camera["width"], 4),
+                              dtype=torch.float32, device="cuda")
+        vr_render(self.ctx, out, stream)
+        return out
+
+    def stats(self):
+        return vr_get_stats(self.ctx)
+
+    def reset_stats(self):
+        vr_reset_stats(self.ctx)
+
+    def brick_minmax(self):
+        return vr_get_brick_minmax(self.ctx, self.n_bricks)

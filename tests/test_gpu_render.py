@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element
+by element, on the same seeded inputs (tolerances in parity_util)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import AMB_ALPHA, AMB_STEPS, assert_parity, compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+@pytest.fixture(scope="module")
+def vr():
+    from paper_1205_0282_gb300 import vr
+    return vr
+
+
+def gpu_render(vr, torch, cube, tf, cam, brick, options=None, host_out=False):
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(np.ascontiguousarray(cube)).cuda())
+        r.brick(*brick)
+        r.set_transfer_function(tf)
+        r.set_camera(cam)
+        for k, v in (options or {}).items():
+            r.set_option(k, v)
+        if host_out:
+            out = np.zeros((cam["height"], cam["width"], 4), dtype=np.float32)
+            r.render(out)
+            img = out
+        else:
+            img = r.render().cpu().numpy()
+        st = r.stats()
+    assert st["device_errors"] == 0, st
+    return img.astype(np.float64), st
+
+
+def oracle_render(cube, tf, cam, brick, mode="ea"):
+    nz, ny, nx = cube.shape
+    b = None if all(bb >= n - 1 for bb, n in zip(brick, (nx, ny, nz))) else brick
+    return oracle.render(cube, tf, cam, brick=b, mode=mode, amb_alpha=AMB_ALPHA,
+                         amb_steps=AMB_STEPS)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.tiny_cube(), synth.tf_tiny()
+
+
+@pytest.mark.parametrize("view", range(4))
+def test_tiny_views_bricked(vr, torch, tiny, view):
+    cube, tf = tiny
+    cam = synth.tiny_views()[view]
+    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32))
+    ref, amb, ns = oracle_render(cube, tf, cam, (32, 32, 32))
+    assert_parity(img, ref, amb)
+    assert st["samples"] >= ns.sum() > 0
+
+
+@pytest.mark.parametrize("view", range(4))
+def test_tiny_views_monolithic(vr, torch, tiny, view):
+    cube, tf = tiny
+    cam = synth.tiny_views()[view]
+    img, _ = gpu_render(vr, torch, cube, tf, cam, (64, 64, 64))
+    ref, amb, _ = oracle_render(cube, tf, cam, (64, 64, 64))
+    assert_parity(img, ref, amb)
+
+
+RAGGED = [
+    # shape (nx, ny, nz), brick, camera, step, tau
+    ((61, 47, 53), (24, 16, 20), dict(az=2.2, el=-0.9, W=83, H=59), 0.35, 0.99),
+    ((64, 64, 64), (7, 9, 11), dict(az=0.7, el=0.3, W=100, H=41), 0.5, 0.99),
+    ((33, 70, 20), (32, 32, 32), dict(az=4.0, el=1.2, W=37, H=90), 1.0, 0.95),
+    ((48, 40, 56), (16, 16, 16), dict(az=1.3, el=0.1, W=64, H=64), 0.25, 1.0),
+]
+
+
+@pytest.mark.parametrize("shape,brick,camk,step,tau", RAGGED)
+def test_ragged_sizes(vr, torch, shape, brick, camk, step, tau):
+    nx, ny, nz = shape
+    cube = synth.hi_cube(seed=11, shape_xyz=shape, n_line=12, n_cont=2)
+    tf = synth.tf_tiny()
+    cam = synth.pose(shape, camk["az"], camk["el"], camk["W"], camk["H"], step=step, term_alpha=tau)
+    img, _ = gpu_render(vr, torch, cube, tf, cam, brick)
+    ref, amb, _ = oracle_render(cube, tf, cam, brick)
+    assert_parity(img, ref, amb)
+
+
+def test_eye_inside_cube(vr, torch, tiny):
+    cube, tf = tiny
+    for cam in [synth.camera((30, 33, 20), (60, 10, 50), (0, 1, 0), 70.0, 96, 72),
+                synth.camera((31.5, 31.5, 31.5), (0, 0, 0), (0, 0, 1), 90.0, 64, 64, step=0.3)]:
+        img, _ = gpu_render(vr, torch, cube, tf, cam, (16, 16, 16))
+        ref, amb, _ = oracle_render(cube, tf, cam, (16, 16, 16))
+        assert_parity(img, ref, amb)
+
+
+def test_opaque_tf_local_termination(vr, torch, tiny):
+    """Per-brick early termination active everywhere (an opaque transfer
+    function): the bricked semantics must match, not the monolithic one."""
+    cube, _ = tiny
+    tf = synth.make_tf([0.0, 0.0, 0.3, 0.6, 0.8, 0.9, 0.95, 0.99])
+    cam = synth.tiny_views(width=128, height=128)[0]
+    img, _ = gpu_render(vr, torch, cube, tf, cam, (8, 8, 8))
+    ref, amb, _ = oracle_render(cube, tf, cam, (8, 8, 8))
+    mono, _, _ = oracle_render(cube, tf, cam, (64, 64, 64))
+    assert_parity(img, ref, amb)
+    assert np.abs(ref - mono).max() > 1e-3   # the two semantics really differ here
+
+
+def test_nonuniform_tf(vr, torch, tiny):
+    cube, _ = tiny
+    tf = np.array([[-3.0, 0.0, 0.0, 1.0, 0.0], [0.8, 0.1, 0.2, 0.9, 0.0],
+                   [1.1, 0.2, 0.6, 0.8, 0.01], [2.9, 0.9, 0.9, 0.9, 0.05],
+                   [4.0, 1.0, 0.5, 0.1, 0.2], [9.5, 1.0, 0.0, 0.0, 0.7]])
+    cam = synth.tiny_views(width=128, height=96)[1]
+    img, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32))
+    ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32))
+    assert_parity(img, ref, amb)
+
+
+def test_mip_mode(vr, torch, tiny):
+    cube, tf = tiny
+    cam = synth.tiny_views(width=128, height=128)[2]
+    img, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_MODE: 1})
+    ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32), mode="mip")
+    assert_parity(img, ref, amb)
+
+
+def test_skip_and_cull_do_not_change_the_image(vr, torch):
+    """Exact empty-space skipping (Section 2.3.1 min/max) and rendering-rectangle
+    culling (Section 2.3.2) only drop work that contributes exactly zero."""
+    cube = synth.hi_cube(seed=5, shape_xyz=(96, 80, 112), n_line=20, n_cont=2)
+    tf = synth.tf_hi_b()
+    cam = synth.pose((96, 80, 112), 0.4, 0.26, 120, 90)
+    base, st = gpu_render(vr, torch, cube, tf, cam, (16, 16, 16))
+    assert st["bricks_skipped"] > 0
+    noskip, st2 = gpu_render(vr, torch, cube, tf, cam, (16, 16, 16), {vr.VR_OPT_SKIP_EMPTY: 0})
+    nocull, st3 = gpu_render(vr, torch, cube, tf, cam, (16, 16, 16), {vr.VR_OPT_RECT_CULL: 0})
+    assert st2["bricks_skipped"] == 0 and st3["items"] > st["items"]
+    np.testing.assert_array_equal(base, nocull)
+    np.testing.assert_allclose(base, noskip, rtol=0, atol=1e-7)
+    ref, amb, _ = oracle_render(cube, tf, cam, (16, 16, 16))
+    assert_parity(base, ref, amb, min_signal=0.01)
+
+
+def test_host_output_matches_device_output(vr, torch, tiny):
+    cube, tf = tiny
+    cam = synth.tiny_views(width=77, height=65)[3]
+    dev, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32))
+    host, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), host_out=True)
+    np.testing.assert_array_equal(dev, host)
+
+
+def test_sample_count_matches_oracle_without_termination(vr, torch, tiny):
+    cube, tf = tiny
+    cam = synth.tiny_views(width=96, height=96, term_alpha=1.0)[0]
+    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32))
+    ref, amb, ns = oracle_render(cube, tf, cam, (32, 32, 32))
+    n_amb = int((amb != 0).sum())
+    assert abs(st["samples"] - int(ns.sum())) <= n_amb
+    assert_parity(img, ref, amb)
+
+
+def test_brick_minmax_matches_oracle(vr, torch, tiny):
+    cube, _ = tiny
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(cube).cuda())
+        for brick in [(32, 32, 32), (24, 16, 40), (7, 9, 11)]:
+            r.brick(*brick)
+            np.testing.assert_array_equal(r.brick_minmax(), oracle.brick_minmax(cube, brick))
+
+
+def test_repeated_frames_and_streams(vr, torch, tiny):
+    """Several frames in flight on a side stream give the same images as one
+    synchronous frame each."""
+    cube, tf = tiny
+    views = synth.tiny_views(width=64, height=64)
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(cube).cuda())
+        r.brick(32, 32, 32)
+        r.set_transfer_function(tf)
+        singles = []
+        for cam in views:
+            r.set_camera(cam)
+            singles.append(r.render().cpu())
+        s = torch.cuda.Stream()
+        outs = []
+        with torch.cuda.stream(s):
+            for rep in range(3):
+                for cam in views:
+                    r.set_camera(cam)
+                    outs.append(r.render(stream=s))
+        s.synchronize()
+        for k, o in enumerate(outs):
+            assert torch.equal(o.cpu(), singles[k % 4])
+        assert r.stats()["frames"] == 16
+
+
+def test_error_codes(vr, torch, tiny):
+    cube, tf = tiny
+    r = vr.VolumeRenderer(0)
+    out = torch.empty((8, 8, 4), device="cuda")
+    with pytest.raises(vr.VRError) as e:
+        r.render(out)
+    assert e.value.code == vr.VR_ESTATE
+    with pytest.raises(vr.VRError) as e:
+        r.brick(8, 8, 8)
+    assert e.value.code == vr.VR_ESTATE
+    r.load_cube(torch.from_numpy(cube).cuda())
+    with pytest.raises(vr.VRError) as e:
+        r.brick(0, 8, 8)
+    assert e.value.code == vr.VR_EINVAL
+    bad = tf.copy()
+    bad[3, 0] = bad[2, 0]
+    with pytest.raises(vr.VRError) as e:
+        r.set_transfer_function(bad)
+    assert e.value.code == vr.VR_EINVAL
+    with pytest.raises(vr.VRError) as e:
+        r.set_camera(synth.camera((0, 0, 0), (0, 0, 0), (0, 1, 0)))
+    assert e.value.code == vr.VR_EINVAL
+    with pytest.raises(vr.VRError) as e:
+        r.set_option(99, 1)
+    assert e.value.code == vr.VR_EINVAL
+    r.close()
