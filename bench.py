@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["hi", "tiny"], default="hi")
+    ap.add_argument("--config", choices=["hi", "mid", "tiny"], default="hi")
     ap.add_argument("--tf", choices=["a", "b"], default="a")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -60,6 +60,12 @@ def workload(args):
         desc = ("HI-survey cube 1024x1024x2048 f32 (noise + 2000 line + 50 continuum sources), "
                 f"128^3 bricks, 1920x1080, step 0.5, 16-point TF-{args.tf.upper()}, "
                 "tau 0.99, 120-pose orbit about y at 15 deg elevation")
+    elif args.config == "mid":
+        spec = dict(synth.MID)
+        tf = synth.tf_hi_a() if args.tf == "a" else synth.tf_hi_b()
+        poses = synth.orbit(spec["shape_xyz"], 120, 15.0, spec["width"], spec["height"])
+        desc = ("mid-size HI-like cube 512x512x1024 f32 (1 GiB), 128^3 bricks, 1920x1080, "
+                f"step 0.5, 16-point TF-{args.tf.upper()}, profiling case")
     else:
         spec = dict(synth.TINY)
         tf = synth.tf_tiny()
@@ -71,6 +77,8 @@ def workload(args):
 def make_cube(spec):
     if spec["name"] == "hi":
         return synth.hi_cube()
+    if spec["name"] == "mid":
+        return synth.hi_cube(seed=4, shape_xyz=spec["shape_xyz"], n_line=250, n_cont=25)
     return synth.tiny_cube()
 
 
@@ -356,7 +364,8 @@ def run_ours(args):
             "config": {"workload": desc, "cube_xyz": list(spec["shape_xyz"]),
                        "brick": list(spec["brick"]), "image": [W, H], "step": 0.5,
                        "tf": args.tf.upper(), "term_alpha": 0.99,
-                       "l2": "inputs larger than L2 (8 GiB cube), no flush",
+                       "l2": ("inputs larger than L2, no flush" if spec["name"] != "tiny"
+                              else "tiny cube fits in L2 (not a bench line)"),
                        "parallelism": f"replicas x{world}: orbit poses split across ranks"},
             "fps": frames / (elapsed_ms * 1e-3),
             "frame_ms_p50": float(np.percentile(frame_ms, 50)),

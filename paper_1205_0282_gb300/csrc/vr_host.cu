@@ -171,11 +171,13 @@ double alpha_over_a(double a, double r) {
     return -std::expm1(r * std::log1p(-a)) / a;
 }
 
-// Chebyshev interpolation of Q on [0, split], converted to powers of t = 2a/split - 1.
-// Chooses the lowest degree whose error on a dense grid is below 2e-10.
-int fit_alpha_poly(double r, double split, float* coeff) {
-    for (int deg = 1; deg < vr::kAlphaPolyMax; ++deg) {
-        const int m = deg + 1;
+// Chebyshev interpolation of Q on [0, split] with kAlphaPolyTerms terms, converted
+// to powers of t = 2a/split - 1.  Returns the largest split in {0.5, 0.4, 0.3, 0.25,
+// 0.2} whose fit error on a dense grid is below 5e-10 (opacities above the split use
+// the exponential form on the device).
+double fit_alpha_poly(double r, float* coeff) {
+    const int m = vr::kAlphaPolyTerms;
+    for (double split : {0.5, 0.4, 0.3, 0.25, 0.2}) {
         std::vector<double> c(m, 0.0);
         for (int j = 0; j < m; ++j) {
             double s = 0;
@@ -190,7 +192,7 @@ int fit_alpha_poly(double r, double split, float* coeff) {
         // Chebyshev -> monomial: T_0 = 1, T_1 = t, T_{k+1} = 2t T_k - T_{k-1}
         std::vector<double> mono(m, 0.0), tkm1(m, 0.0), tk(m, 0.0), tkp1(m, 0.0);
         tkm1[0] = 1.0;
-        if (m > 1) tk[1] = 1.0;
+        tk[1] = 1.0;
         for (int j = 0; j < m; ++j) {
             const std::vector<double>& T = (j == 0) ? tkm1 : tk;
             for (int q = 0; q < m; ++q) mono[q] += c[j] * T[q];
@@ -209,12 +211,12 @@ int fit_alpha_poly(double r, double split, float* coeff) {
             for (int k = m - 1; k >= 0; --k) q = q * t + mono[k];
             err = std::max(err, std::fabs(q - alpha_over_a(a, r)));
         }
-        if (err < 2e-10 || deg == vr::kAlphaPolyMax - 1) {
+        if (err < 5e-10 || split == 0.2) {
             for (int k = 0; k < m; ++k) coeff[k] = (float)mono[k];
-            return m;
+            return split;
         }
     }
-    return 0;
+    return 0.2;
 }
 
 }  // namespace
@@ -245,8 +247,8 @@ struct vr_ctx {
     vr_camera cam{};
     Basis basis{};
     std::vector<df> q;  // qx (width entries) then qy (height entries)
-    float alpha_poly[vr::kAlphaPolyMax] = {};
-    int alpha_poly_n = 0;
+    float alpha_poly[vr::kAlphaPolyTerms] = {};
+    double alpha_split = 0.5;
 
     bool skip_empty = true, rect_cull = true;
     int mode = 0;
@@ -604,7 +606,7 @@ int vr_set_camera(vr_ctx* c, const vr_camera* cam) {
     for (int j = 0; j < cam->height; ++j)
         c->q[cam->width + j] = vr::df_from_double((1.0 - 2.0 * (j + 0.5) / cam->height) * b.tan_half);
     if (!c->cam_set || cam->step != c->cam.step)
-        c->alpha_poly_n = fit_alpha_poly(cam->step / 1.0, 0.5, c->alpha_poly);
+        c->alpha_split = fit_alpha_poly(cam->step / 1.0, c->alpha_poly);
     c->cam = *cam;
     c->basis = b;
     c->cam_set = true;
@@ -692,6 +694,8 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     p.cube = c->d_cube;
     p.stride_y = c->n[0];
     p.stride_z = c->n[0] * c->n[1];
+    p.offsets32 = ((int64_t)c->B[2] + 1) * p.stride_z + ((int64_t)c->B[1] + 1) * p.stride_y +
+                      c->B[0] + 1 < ((int64_t)1 << 32) ? 1 : 0;
     p.tf_rgba = reinterpret_cast<const float4*>(s.d_frame + tf_rgba_off);
     p.tf_v = reinterpret_cast<const float*>(s.d_frame + tf_v_off);
     p.tf_n = (int32_t)(c->tf.size() / 5);
@@ -699,9 +703,8 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     p.tf_v0 = c->tf_v0;
     p.tf_inv_dv = c->tf_inv_dv;
     std::memcpy(p.alpha_poly, c->alpha_poly, sizeof(p.alpha_poly));
-    p.alpha_poly_n = c->alpha_poly_n;
-    p.alpha_split = 0.5f;
-    p.poly_scale = 2.0f / 0.5f;
+    p.alpha_split = (float)c->alpha_split;
+    p.poly_scale = (float)(2.0 / c->alpha_split);
     p.mode = c->mode;
     p.items = s.d_items;
     p.n_items = (int32_t)n_items;

@@ -10,7 +10,7 @@ namespace vr {
 constexpr int kTile = 8;                    // pixel tile edge (items are brick x 8x8 tile)
 constexpr int kTilePixels = kTile * kTile;  // 64 rays per item, one per thread
 constexpr int kMaxTfPoints = 256;
-constexpr int kAlphaPolyMax = 17;           // coefficients of the opacity-correction polynomial
+constexpr int kAlphaPolyTerms = 11;         // coefficients of the opacity-correction polynomial
 
 // Device error flags (OR-ed into Stats::errors).
 constexpr int kErrBounds = 1;               // a sample index left its brick's voxel range
@@ -48,6 +48,7 @@ struct FrameParams {
     int32_t B[3];          // brick size
     int32_t nb[3];         // bricks per axis
     int64_t stride_y, stride_z;
+    int32_t offsets32;     // 1: (B+1) * stride_z < 2^31, brick-local offsets fit in 32 bits
 
     // transfer function: control points (r,g,b,a) and their values
     const float4* tf_rgba;
@@ -56,8 +57,7 @@ struct FrameParams {
     int32_t tf_uniform;    // 1: v_i = v0 + i*dv
     float tf_v0, tf_inv_dv;
     // opacity correction alpha(a) = 1 - (1-a)^dt as a * Q(a) for a <= alpha_split
-    float alpha_poly[kAlphaPolyMax];  // Q in powers of t = a * poly_scale - 1
-    int32_t alpha_poly_n;
+    float alpha_poly[kAlphaPolyTerms];  // Q in powers of t = a * poly_scale - 1
     float poly_scale;
     float alpha_split;
     int32_t mode;          // 0 = emission-absorption, 1 = MIP

@@ -141,10 +141,11 @@ struct TfShared {
     float v[kMaxTfPoints];
 };
 
+template <bool UNIFORM>
 __device__ __forceinline__ float4 tf_lookup(const FrameParams& p, const TfShared& s, float v) {
     int seg;
     float w;
-    if (p.tf_uniform) {
+    if (UNIFORM) {
         float x = (v - p.tf_v0) * p.tf_inv_dv;
         x = fminf(fmaxf(x, 0.0f), (float)(p.tf_n - 1));
         seg = min((int)x, p.tf_n - 2);
@@ -171,8 +172,9 @@ __device__ __forceinline__ float4 tf_lookup(const FrameParams& p, const TfShared
 __device__ __forceinline__ float opacity_correct(const FrameParams& p, float a) {
     if (a <= p.alpha_split) {
         const float t = fmaf(a, p.poly_scale, -1.0f);
-        float q = p.alpha_poly[p.alpha_poly_n - 1];
-        for (int k = p.alpha_poly_n - 2; k >= 0; --k) q = fmaf(q, t, p.alpha_poly[k]);
+        float q = p.alpha_poly[kAlphaPolyTerms - 1];
+#pragma unroll
+        for (int k = kAlphaPolyTerms - 2; k >= 0; --k) q = fmaf(q, t, p.alpha_poly[k]);
         return a * q;
     }
     return 1.0f - exp2f(p.dt_f * __log2f(1.0f - a));
@@ -180,6 +182,8 @@ __device__ __forceinline__ float opacity_correct(const FrameParams& p, float a) 
 
 // ------------------------------------------------------------------ ray march
 
+// Off: type of brick-local voxel offsets (uint32_t when (B+1) * nx * ny < 2^32).
+template <bool UNIFORM, int MODE, typename Off>
 __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p) {
     __shared__ TfShared s_tf;
     for (int k = threadIdx.x; k < p.tf_n; k += blockDim.x) {
@@ -207,46 +211,51 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
         brick_range(p, bidx, d, pe, n_samples, klo, khi);
         if (khi > klo) {
             int O[3], imax[3];
-            float qs[3], dq[3], qmax[3];
+            float qs[3], dq[3];
             for (int a = 0; a < 3; ++a) {
                 O[a] = bidx[a] * p.B[a];
                 imax[a] = min(p.B[a] - 1, p.n[a] - 2 - O[a]);
-                qmax[a] = (float)min(p.B[a], p.n[a] - 1 - O[a]);
                 const df D = df_mul(p.dt, d[a]);
                 qs[a] = df_to_float(df_add_f(df_add(pe[a], df_mul_f(D, (float)klo)), -(float)O[a]));
                 dq[a] = df_to_float(D);
             }
+            // Sample positions stay inside the brick's owned box up to rounding
+            // (ownership), so a truncating conversion plus an upper clamp keeps the
+            // eight corners inside the brick and its one-voxel apron.
             const float* __restrict__ base =
                 p.cube + (int64_t)O[2] * p.stride_z + (int64_t)O[1] * p.stride_y + O[0];
-            const int64_t sy = p.stride_y, sz = p.stride_z;
+            const Off sy = (Off)p.stride_y, sz = (Off)p.stride_z;
             const int nk = khi - klo;
             for (int kk = 0; kk < nk; ++kk) {
                 const float fk = (float)kk;
-                float c[3], f[3];
-                int ix[3];
-                for (int a = 0; a < 3; ++a) {
-                    c[a] = fminf(fmaxf(fmaf(fk, dq[a], qs[a]), 0.0f), qmax[a]);
-                    ix[a] = min((int)c[a], imax[a]);
-                    f[a] = c[a] - (float)ix[a];
-                }
-                const float* b = base + (int64_t)ix[2] * sz + (int64_t)ix[1] * sy + ix[0];
-                const float v000 = __ldg(b), v100 = __ldg(b + 1);
-                const float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
-                const float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
-                const float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
-                const float c00 = fmaf(f[0], v100 - v000, v000);
-                const float c10 = fmaf(f[0], v110 - v010, v010);
-                const float c01 = fmaf(f[0], v101 - v001, v001);
-                const float c11 = fmaf(f[0], v111 - v011, v011);
-                const float c0 = fmaf(f[1], c10 - c00, c00);
-                const float c1 = fmaf(f[1], c11 - c01, c01);
-                const float v = fmaf(f[2], c1 - c0, c0);
+                const float qx = fmaf(fk, dq[0], qs[0]);
+                const float qy = fmaf(fk, dq[1], qs[1]);
+                const float qz = fmaf(fk, dq[2], qs[2]);
+                const int ix = min(max(__float2int_rz(qx), 0), imax[0]);
+                const int iy = min(max(__float2int_rz(qy), 0), imax[1]);
+                const int iz = min(max(__float2int_rz(qz), 0), imax[2]);
+                const float fx = qx - (float)ix, fy = qy - (float)iy, fz = qz - (float)iz;
+                const float* __restrict__ r0 = base + ((Off)iz * sz + (Off)iy * sy + (Off)ix);
+                const float* __restrict__ r1 = r0 + sy;
+                const float* __restrict__ r2 = r0 + sz;
+                const float* __restrict__ r3 = r2 + sy;
+                const float v000 = __ldg(r0), v100 = __ldg(r0 + 1);
+                const float v010 = __ldg(r1), v110 = __ldg(r1 + 1);
+                const float v001 = __ldg(r2), v101 = __ldg(r2 + 1);
+                const float v011 = __ldg(r3), v111 = __ldg(r3 + 1);
+                const float c00 = fmaf(fx, v100 - v000, v000);
+                const float c10 = fmaf(fx, v110 - v010, v010);
+                const float c01 = fmaf(fx, v101 - v001, v001);
+                const float c11 = fmaf(fx, v111 - v011, v011);
+                const float c0 = fmaf(fy, c10 - c00, c00);
+                const float c1 = fmaf(fy, c11 - c01, c01);
+                const float v = fmaf(fz, c1 - c0, c0);
                 ++taken;
-                if (p.mode == 1) {
+                if (MODE == 1) {
                     vmax = fmaxf(vmax, v);
                     continue;
                 }
-                const float4 col = tf_lookup(p, s_tf, v);
+                const float4 col = tf_lookup<UNIFORM>(p, s_tf, v);
                 const float alpha = opacity_correct(p, col.w);
                 const float w = (1.0f - acc.w) * alpha;
                 acc.x = fmaf(w, col.x, acc.x);
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
             }
         }
     }
-    if (p.mode == 1) acc = make_float4(vmax, taken > 0 ? 1.0f : 0.0f, 0.0f, 0.0f);
+    if (MODE == 1) acc = make_float4(vmax, taken > 0 ? 1.0f : 0.0f, 0.0f, 0.0f);
     p.frags[(int64_t)item.frag * kTilePixels + threadIdx.x] = acc;
 
     // sample count: warp reduction then one atomic per warp
@@ -266,9 +275,23 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
     if ((threadIdx.x & 31) == 0 && t) atomicAdd(&p.stats->samples, t);
 }
 
+template <bool UNIFORM, int MODE>
+static void launch_march_t(const FrameParams& p, cudaStream_t s) {
+    if (p.offsets32)
+        march_kernel<UNIFORM, MODE, uint32_t><<<p.n_items, kTilePixels, 0, s>>>(p);
+    else
+        march_kernel<UNIFORM, MODE, int64_t><<<p.n_items, kTilePixels, 0, s>>>(p);
+}
+
 cudaError_t launch_march(const FrameParams& p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
-    march_kernel<<<p.n_items, kTilePixels, 0, s>>>(p);
+    if (p.mode == 1) {
+        if (p.tf_uniform) launch_march_t<true, 1>(p, s);
+        else launch_march_t<false, 1>(p, s);
+    } else {
+        if (p.tf_uniform) launch_march_t<true, 0>(p, s);
+        else launch_march_t<false, 0>(p, s);
+    }
     return cudaGetLastError();
 }
 
@@ -310,7 +333,7 @@ __global__ void __launch_bounds__(kTilePixels) composite_kernel(const FrameParam
             }
         }
         if (any) {
-            const float4 c = tf_lookup(p, s_tf, vmax);
+            const float4 c = p.tf_uniform ? tf_lookup<true>(p, s_tf, vmax) : tf_lookup<false>(p, s_tf, vmax);
             acc = make_float4(c.x * c.w, c.y * c.w, c.z * c.w, c.w);
         }
     }

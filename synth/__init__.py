@@ -229,5 +229,7 @@ def orbit(shape_xyz, n_poses=120, elevation_deg=15.0, width=1920, height=1080, *
 
 TINY = {"name": "tiny", "shape_xyz": (64, 64, 64), "brick": (32, 32, 32),
         "width": 256, "height": 256}
+MID = {"name": "mid", "shape_xyz": (512, 512, 1024), "brick": (128, 128, 128),
+       "width": 1920, "height": 1080}
 HI = {"name": "hi", "shape_xyz": (1024, 1024, 2048), "brick": (128, 128, 128),
       "width": 1920, "height": 1080}
