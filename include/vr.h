@@ -174,6 +174,36 @@ int vr_get_brick_minmax(vr_ctx* ctx, float* out, int64_t n_bricks);
 int vr_plan_brick_rects(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz,
                         int32_t bx, int32_t by, int32_t bz, int32_t* rects, int64_t n_bricks);
 
+/*
+ * Allocation-free render (the paper has no counterpart; this serves callers that
+ * may not allocate device memory while rendering: an application or plugin that
+ * owns the device-memory budget, a real-time loop that cannot take the implicit
+ * synchronisation of cudaMalloc/cudaFree, or an embedding with its own allocator).
+ * It renders the same image as vr_render (emission-absorption mode, every brick
+ * marched, rendering-rectangle culling on) but calls no cudaMalloc, cudaFree or
+ * other allocating routine and needs no context: its scratch (work list,
+ * per-brick sub-image fragments, counters) lives in one static device array of
+ * VR_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
+ * the process exits.
+ *   cube:      device memory, float32[nz][ny][nx], x fastest, 2 <= n <= 65536.
+ *   bx,by,bz:  brick size (>= 1), at most 4096 bricks.
+ *   tf_points: host memory, n_tf rows (v, r, g, b, a) as for vr_set_transfer_function.
+ *   cam:       as for vr_set_camera, with width and height <= 1024.
+ *   out_rgba:  device memory, float32[height][width][4], written on cuda_stream.
+ * Runs on the current CUDA device.  The first call on each device looks up the
+ * scratch array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the scratch, which keeps the last
+ * call's contents (the counters are cleared by each call, everything else is
+ * rewritten): calls that overlap on the GPU race, and the function must not be
+ * called from two host threads at once.
+ * Errors: VR_EINVAL (bad argument, host-memory cube or image, or a frame whose
+ * work list needs more than VR_NOALLOC_SCRATCH_BYTES), VR_ECUDA.
+ */
+#define VR_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t bx, int32_t by,
+                      int32_t bz, const double* tf_points, int32_t n_tf, const vr_camera* cam,
+                      float* out_rgba, void* cuda_stream);
+
 /* Message describing the last failing call on ctx (never NULL). */
 const char* vr_last_error(const vr_ctx* ctx);
 

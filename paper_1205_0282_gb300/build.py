@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libvr.so")
-SOURCES = ["vr_host.cu", "vr_kernels.cu"]
+SOURCES = ["vr_host.cu", "vr_kernels.cu", "vr_noalloc.cu"]
 HEADERS = ["df.cuh", "vr_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

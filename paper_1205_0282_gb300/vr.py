@@ -58,7 +58,7 @@ class vr_stats(ctypes.Structure):
 # The exported symbols, in header order (tests check them against include/vr.h).
 EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_brick", "vr_set_transfer_function",
            "vr_set_camera", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
-           "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_last_error"]
+           "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_render_noalloc", "vr_last_error"]
 
 
 def _load():
@@ -81,6 +81,8 @@ def _load():
     lib.vr_get_brick_minmax.argtypes = [P, P, I64]
     lib.vr_plan_brick_rects.argtypes = [ctypes.POINTER(vr_camera), I64, I64, I64, I32, I32, I32,
                                         P, I64]
+    lib.vr_render_noalloc.argtypes = [P, I64, I64, I64, I32, I32, I32, P, I32,
+                                      ctypes.POINTER(vr_camera), P, P]
     lib.vr_last_error.argtypes = [P]
     lib.vr_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -213,6 +215,21 @@ def vr_plan_brick_rects(cam: dict, shape_xyz, brick) -> np.ndarray:
     if rc != VR_OK:
         raise VRError(rc, "vr_plan_brick_rects rejected its arguments")
     return rects
+
+
+def vr_render_noalloc(cube, brick, points, cam: dict, out, stream=None) -> None:
+    """Allocation-free render: ``cube`` and ``out`` are CUDA tensors (float32
+    (nz, ny, nx) and (H, W, 4)); scratch lives in the library's static device
+    array, so calls that overlap on the GPU race."""
+    nz, ny, nx = cube.shape
+    caddr, ckeep = _ptr(cube)
+    oaddr, okeep = _ptr(out)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 5)
+    c = make_camera(cam)
+    rc = _lib.vr_render_noalloc(caddr, nx, ny, nz, *brick, pts.ctypes.data, len(pts),
+                                ctypes.byref(c), oaddr, _stream_handle(stream))
+    if rc != VR_OK:
+        raise VRError(rc, "vr_render_noalloc failed")
 
 
 def vr_last_error(ctx) -> str:
