@@ -79,7 +79,12 @@ typedef struct {
     int64_t h2d_bytes;       /* host->device bytes copied by vr_render (plans, camera, TF) */
     int64_t d2h_bytes;       /* device->host bytes copied by vr_render (counters, host images) */
     int64_t launches;        /* kernels launched by vr_render */
-    int32_t device_errors;   /* OR of device-side error flags seen (0 = none) */
+    int64_t chunks_staged;   /* TMA march: sample chunks read from TMA-staged shared memory */
+    int64_t chunks_direct;   /* TMA march: chunks whose footprint did not fit the staged box
+                                (read through L1 instead) */
+    int32_t device_errors;   /* OR of device-side error flags seen (0 = none; 1 = a sample
+                                outside its staged box was clamped; 2 = a bounded wait on a
+                                TMA copy gave up and the frame is invalid) */
     int32_t reserved;
 } vr_stats;
 
@@ -89,6 +94,14 @@ typedef struct {
                                 rectangle (Section 2.3.2); 0: every tile for every brick */
 #define VR_OPT_MODE 3        /* 0 (default): emission-absorption compositing;
                                 1: maximum intensity projection + colour map (Section 2.3.3) */
+#define VR_OPT_KERNEL 4      /* ray-march kernel for emission-absorption frames:
+                                VR_KERNEL_TMA (default): 16x16-pixel items, voxel boxes staged
+                                in shared memory by TMA; VR_KERNEL_DIRECT: 8x8-pixel items,
+                                trilinear corners read through the L1 cache.  MIP frames
+                                always use the direct kernel.  Both give the same image up to
+                                FP32 rounding. */
+#define VR_KERNEL_TMA 0
+#define VR_KERNEL_DIRECT 1
 
 /*
  * Create a context on CUDA device `device`.  *out receives the context.

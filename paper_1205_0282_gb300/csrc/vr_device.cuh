@@ -1,0 +1,133 @@
+// Device helpers shared by the ray-march kernels: double-float ray set-up,
+// per-brick sample ranges, transfer-function lookup and opacity correction.
+#pragma once
+#include <cfloat>
+#include <cstdint>
+
+#include "vr_internal.cuh"
+
+namespace vr {
+
+// ------------------------------------------------------------------ ray set-up
+
+// Ray of pixel (i, j) in double-float: unit direction d, entry point pe and the
+// sample count n = #{k >= 0 : k dt < t1 - t0}.  Returns false if the ray misses
+// the domain [0, n-1]^3.
+__device__ __forceinline__ bool setup_ray(const FrameParams& p, int i, int j, df d[3], df pe[3], int& n_samples) {
+    const df qx = p.qx[i], qy = p.qy[j];
+    df dun[3];
+    for (int a = 0; a < 3; ++a) dun[a] = df_add(df_add(p.f[a], df_mul(qx, p.r[a])), df_mul(qy, p.u[a]));
+    df n2 = df_add(df_add(df_mul(dun[0], dun[0]), df_mul(dun[1], dun[1])), df_mul(dun[2], dun[2]));
+    df len = df_sqrt(n2);
+    for (int a = 0; a < 3; ++a) d[a] = df_div(dun[a], len);
+
+    df tn = df_make(-FLT_MAX), tf = df_make(FLT_MAX);
+    for (int a = 0; a < 3; ++a) {
+        const df hi = df_make((float)(p.n[a] - 1));
+        if (df_is_zero(d[a])) {
+            if (df_lt(p.eye[a], df_make(0.0f)) || df_gt(p.eye[a], hi)) return false;
+            continue;
+        }
+        df ta = df_div(df_neg(p.eye[a]), d[a]);
+        df tb = df_div(df_sub(hi, p.eye[a]), d[a]);
+        tn = df_max(tn, df_min(ta, tb));
+        tf = df_min(tf, df_max(ta, tb));
+    }
+    const df t0 = df_max(tn, df_make(0.0f));
+    if (!df_gt(tf, t0)) return false;
+    const df L = df_sub(tf, t0);
+    n_samples = (int)df_ceil(df_div(L, p.dt));
+    for (int a = 0; a < 3; ++a) pe[a] = df_add(p.eye[a], df_mul(t0, d[a]));
+    return n_samples > 0;
+}
+
+// Sample range [klo, khi) owned by brick bidx (sample p_k = pe + k dt d belongs to
+// brick floor(p/B) per axis, first and last bricks open towards the outside).
+__device__ __forceinline__ void brick_range(const FrameParams& p, const int bidx[3], const df d[3], const df pe[3],
+                            int n_samples, int& klo, int& khi) {
+    float lo = 0.0f, hi = (float)n_samples;
+    for (int a = 0; a < 3; ++a) {
+        const df D = df_mul(p.dt, d[a]);
+        const float O = (float)(bidx[a] * p.B[a]);
+        const float OB = (float)(bidx[a] * p.B[a] + p.B[a]);
+        if (bidx[a] > 0) {
+            if (D.hi > 0.0f) {
+                lo = fmaxf(lo, df_ceil(df_div(df_sub(df_make(O), pe[a]), D)));
+            } else if (D.hi < 0.0f) {
+                hi = fminf(hi, df_floor(df_div(df_sub(df_make(O), pe[a]), D)) + 1.0f);
+            } else if (df_lt(pe[a], df_make(O))) {
+                hi = -1.0f;
+            }
+        }
+        if (bidx[a] < p.nb[a] - 1) {
+            if (D.hi > 0.0f) {
+                hi = fminf(hi, df_ceil(df_div(df_sub(df_make(OB), pe[a]), D)));
+            } else if (D.hi < 0.0f) {
+                lo = fmaxf(lo, df_floor(df_div(df_sub(df_make(OB), pe[a]), D)) + 1.0f);
+            } else if (!df_lt(pe[a], df_make(OB))) {
+                hi = -1.0f;
+            }
+        }
+    }
+    lo = fmaxf(lo, 0.0f);
+    hi = fminf(hi, (float)n_samples);
+    klo = (int)lo;
+    khi = hi > lo ? (int)hi : klo;
+}
+
+// ------------------------------------------------------------------ per-sample ops
+
+struct TfShared {
+    float4 rgba[kMaxTfPoints + 1];
+    float v[kMaxTfPoints];
+};
+
+template <bool UNIFORM>
+__device__ __forceinline__ float4 tf_lookup(const FrameParams& p, const float4* __restrict__ rgba,
+                                            const float* __restrict__ vals, float v) {
+    int seg;
+    float w;
+    if (UNIFORM) {
+        // rgba[tf_n] repeats the last point, so x = tf_n - 1 needs no segment clamp
+        float x = (v - p.tf_v0) * p.tf_inv_dv;
+        x = fminf(fmaxf(x, 0.0f), (float)(p.tf_n - 1));
+        seg = __float2int_rz(x);
+        w = x - (float)seg;
+    } else {
+        int lo = 0, hi = p.tf_n - 1;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (v >= vals[mid]) lo = mid;
+            else hi = mid;
+        }
+        seg = lo;
+        w = (v - vals[seg]) / (vals[seg + 1] - vals[seg]);
+        w = fminf(fmaxf(w, 0.0f), 1.0f);
+    }
+    const float4 c0 = rgba[seg], c1 = rgba[seg + 1];
+    return make_float4(fmaf(w, c1.x - c0.x, c0.x), fmaf(w, c1.y - c0.y, c0.y),
+                       fmaf(w, c1.z - c0.z, c0.z), fmaf(w, c1.w - c0.w, c0.w));
+}
+
+// alpha = 1 - (1 - a)^dt as a * Q(t): a short polynomial for small a (noise, the
+// common case), a long one up to alpha_split (both accurate to ~1e-10 in Q and
+// exactly 0 at a = 0), the exponential form above.
+__device__ __forceinline__ float opacity_correct(const FrameParams& p, float a) {
+    if (a <= p.small_split) {
+        const float t = fmaf(a, p.small_scale, -1.0f);
+        float q = p.alpha_small[kAlphaSmallTerms - 1];
+#pragma unroll
+        for (int k = kAlphaSmallTerms - 2; k >= 0; --k) q = fmaf(q, t, p.alpha_small[k]);
+        return a * q;
+    }
+    if (a <= p.alpha_split) {
+        const float t = fmaf(a, p.poly_scale, -1.0f);
+        float q = p.alpha_poly[kAlphaPolyTerms - 1];
+#pragma unroll
+        for (int k = kAlphaPolyTerms - 2; k >= 0; --k) q = fmaf(q, t, p.alpha_poly[k]);
+        return a * q;
+    }
+    return 1.0f - exp2f(p.dt_f * __log2f(1.0f - a));
+}
+
+}  // namespace vr

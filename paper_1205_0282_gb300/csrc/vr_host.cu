@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/vr.h"
+#include "vr_alpha_fit.h"
 #include "vr_internal.cuh"
 
 using vr::df;
@@ -39,7 +40,7 @@ struct Slot {
     bool pending = false;
     // host-side facts of the frame in flight
     int64_t items = 0, bricks_rendered = 0, bricks_skipped = 0, touched_bytes = 0;
-    int64_t h2d_bytes = 0, d2h_bytes = 0, launches = 0;
+    int64_t h2d_bytes = 0, d2h_bytes = 0, launches = 0, fragments = 0;
     double plan_ms = 0.0;
 };
 
@@ -165,60 +166,6 @@ double tf_alpha_max(const std::vector<double>& tf, double lo, double hi) {
     return m;
 }
 
-// Q(a) = (1 - (1-a)^r) / a, with Q(0) = r.
-double alpha_over_a(double a, double r) {
-    if (a == 0.0) return r;
-    return -std::expm1(r * std::log1p(-a)) / a;
-}
-
-// Chebyshev interpolation of Q on [0, split] with kAlphaPolyTerms terms, converted
-// to powers of t = 2a/split - 1.  Returns the largest split in {0.5, 0.4, 0.3, 0.25,
-// 0.2} whose fit error on a dense grid is below 5e-10 (opacities above the split use
-// the exponential form on the device).
-double fit_alpha_poly(double r, float* coeff) {
-    const int m = vr::kAlphaPolyTerms;
-    for (double split : {0.5, 0.4, 0.3, 0.25, 0.2}) {
-        std::vector<double> c(m, 0.0);
-        for (int j = 0; j < m; ++j) {
-            double s = 0;
-            for (int k = 0; k < m; ++k) {
-                double th = M_PI * (k + 0.5) / m;
-                double a = (std::cos(th) + 1.0) * 0.5 * split;
-                s += alpha_over_a(a, r) * std::cos(j * th);
-            }
-            c[j] = 2.0 * s / m;
-        }
-        c[0] *= 0.5;
-        // Chebyshev -> monomial: T_0 = 1, T_1 = t, T_{k+1} = 2t T_k - T_{k-1}
-        std::vector<double> mono(m, 0.0), tkm1(m, 0.0), tk(m, 0.0), tkp1(m, 0.0);
-        tkm1[0] = 1.0;
-        tk[1] = 1.0;
-        for (int j = 0; j < m; ++j) {
-            const std::vector<double>& T = (j == 0) ? tkm1 : tk;
-            for (int q = 0; q < m; ++q) mono[q] += c[j] * T[q];
-            if (j >= 1) {
-                std::fill(tkp1.begin(), tkp1.end(), 0.0);
-                for (int q = 0; q + 1 < m; ++q) tkp1[q + 1] += 2.0 * tk[q];
-                for (int q = 0; q < m; ++q) tkp1[q] -= tkm1[q];
-                tkm1 = tk;
-                tk = tkp1;
-            }
-        }
-        double err = 0;
-        for (int g = 0; g <= 4000; ++g) {
-            double a = split * g / 4000.0;
-            double t = 2.0 * a / split - 1.0, q = 0;
-            for (int k = m - 1; k >= 0; --k) q = q * t + mono[k];
-            err = std::max(err, std::fabs(q - alpha_over_a(a, r)));
-        }
-        if (err < 5e-10 || split == 0.2) {
-            for (int k = 0; k < m; ++k) coeff[k] = (float)mono[k];
-            return split;
-        }
-    }
-    return 0.2;
-}
-
 }  // namespace
 
 struct vr_ctx {
@@ -226,8 +173,13 @@ struct vr_ctx {
     std::string err;
     int sm_count = 0;
 
-    float* d_cube = nullptr;
+    float* d_cube = nullptr;     // [z][y][x], row pitch nx_pad floats (16-byte rows for TMA)
     int64_t n[3] = {0, 0, 0};
+    int64_t nx_pad = 0;
+    float* d_cube_xzy = nullptr; // transposed copy [x][z][y], row pitch ny_pad (sweeps along x)
+    int64_t ny_pad = 0;
+    vr::TmaMaps tmaps;
+    bool tma_ready = false;
 
     bool bricked = false;
     int32_t B[3] = {0, 0, 0};
@@ -249,16 +201,19 @@ struct vr_ctx {
     std::vector<df> q;  // qx (width entries) then qy (height entries)
     float alpha_poly[vr::kAlphaPolyTerms] = {};
     double alpha_split = 0.5;
+    float alpha_small[vr::kAlphaSmallTerms] = {};
+    double small_split = 0.1;
 
     bool skip_empty = true, rect_cull = true;
     int mode = 0;
+    int kernel = VR_KERNEL_TMA;
 
     Slot slots[kSlots];
     int next_slot = 0;
     vr_stats acc{};
 
     // planner scratch (host)
-    std::vector<int32_t> plan_count, plan_fill;
+    std::vector<int32_t> plan_count, plan_fill, plan_sweep;
     struct PB {
         int32_t key, id, rect[4];
     };
@@ -322,8 +277,10 @@ int retire(vr_ctx* c, Slot& s) {
     VR_CUDA(c, cudaEventElapsedTime(&ms_frame, s.ev_begin, s.ev_end));
     c->acc.frames += 1;
     c->acc.samples += (int64_t)s.h_stats->samples;
+    c->acc.chunks_staged += (int64_t)s.h_stats->chunks_staged;
+    c->acc.chunks_direct += (int64_t)s.h_stats->chunks_direct;
     c->acc.items += s.items;
-    c->acc.fragments += s.items * vr::kTilePixels;
+    c->acc.fragments += s.fragments;
     c->acc.bricks_rendered += s.bricks_rendered;
     c->acc.bricks_skipped += s.bricks_skipped;
     c->acc.touched_bytes += s.touched_bytes;
@@ -348,11 +305,31 @@ int retire_all(vr_ctx* c) {
 }
 
 // Build the frame's work list into slot s (host).  Returns VR_OK.
-int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int64_t& n_items) {
+bool use_tma(const vr_ctx* c) { return c->kernel == VR_KERNEL_TMA && c->mode == 0; }
+
+int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int32_t& T, int64_t& n_items) {
     const vr_camera& cam = c->cam;
-    tiles_x = (cam.width + vr::kTile - 1) / vr::kTile;
-    tiles_y = (cam.height + vr::kTile - 1) / vr::kTile;
+    T = use_tma(c) ? vr::kTileTma : vr::kTile;
+    tiles_x = (cam.width + T - 1) / T;
+    tiles_y = (cam.height + T - 1) / T;
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
+    // sweep axis of each tile for the TMA march: the dominant axis of the ray
+    // through the tile's centre pixel, and its sign
+    c->plan_sweep.assign(n_tiles, 0);
+    if (use_tma(c)) {
+        for (int ty = 0; ty < tiles_y; ++ty)
+            for (int tx = 0; tx < tiles_x; ++tx) {
+                const int i = std::min(tx * T + T / 2, cam.width - 1), j = std::min(ty * T + T / 2, cam.height - 1);
+                const double qx = (2.0 * (i + 0.5) / cam.width - 1.0) * c->basis.tan_half * c->basis.aspect;
+                const double qy = (1.0 - 2.0 * (j + 0.5) / cam.height) * c->basis.tan_half;
+                double d[3];
+                for (int a = 0; a < 3; ++a) d[a] = c->basis.f[a] + qx * c->basis.r[a] + qy * c->basis.u[a];
+                int ax = 0;
+                for (int a = 1; a < 3; ++a)
+                    if (std::fabs(d[a]) > std::fabs(d[ax])) ax = a;
+                c->plan_sweep[(int64_t)ty * tiles_x + tx] = ax | (d[ax] < 0.0 ? 4 : 0);
+            }
+    }
 
     // eye's brick index per axis, -1 / nb when outside (view-order key, see below)
     int64_t e[3];
@@ -403,13 +380,13 @@ int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int64_t& 
     c->plan_count.assign(n_tiles + 1, 0);
     n_items = 0;
     for (const auto& pb : c->plan_bricks) {
-        const int tx0 = pb.rect[0] / vr::kTile, tx1 = pb.rect[2] / vr::kTile;
-        const int ty0 = pb.rect[1] / vr::kTile, ty1 = pb.rect[3] / vr::kTile;
+        const int tx0 = pb.rect[0] / T, tx1 = pb.rect[2] / T;
+        const int ty0 = pb.rect[1] / T, ty1 = pb.rect[3] / T;
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) c->plan_count[(int64_t)ty * tiles_x + tx]++;
         n_items += (int64_t)(tx1 - tx0 + 1) * (ty1 - ty0 + 1);
     }
-    if (n_items > (int64_t)INT32_MAX / vr::kTilePixels) return fail(c, VR_ENOMEM, "frame too large");
+    if (n_items > (int64_t)INT32_MAX / (T * T)) return fail(c, VR_ENOMEM, "frame too large");
     int rc = grow_pinned(c, s.h_items, s.cap_items, (size_t)n_items);
     if (rc) return rc;
     rc = grow_pinned(c, s.h_tile_start, s.cap_tiles, (size_t)n_tiles + 1);
@@ -423,8 +400,8 @@ int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int64_t& 
     c->plan_fill.assign(n_tiles, 0);
     int64_t k = 0;
     for (const auto& pb : c->plan_bricks) {
-        const int tx0 = pb.rect[0] / vr::kTile, tx1 = pb.rect[2] / vr::kTile;
-        const int ty0 = pb.rect[1] / vr::kTile, ty1 = pb.rect[3] / vr::kTile;
+        const int tx0 = pb.rect[0] / T, tx1 = pb.rect[2] / T;
+        const int ty0 = pb.rect[1] / T, ty1 = pb.rect[3] / T;
         for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) {
                 const int64_t t = (int64_t)ty * tiles_x + tx;
@@ -432,7 +409,7 @@ int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int64_t& 
                 it.brick = pb.id;
                 it.tile = (int32_t)t;
                 it.frag = s.h_tile_start[t] + c->plan_fill[t]++;
-                it.pad = 0;
+                it.sweep = c->plan_sweep[t];
                 s.h_items[k++] = it;
             }
     }
@@ -492,6 +469,7 @@ void vr_destroy(vr_ctx* c) {
             if (ev) cudaEventDestroy(ev);
     }
     cudaFree(c->d_cube);
+    cudaFree(c->d_cube_xzy);
     cudaFree(c->d_minmax);
     delete c;
 }
@@ -509,15 +487,22 @@ int vr_load_cube(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int64_t n
     VR_CUDA(c, cudaSetDevice(c->device));
     int rc = retire_all(c);
     if (rc) return rc;
-    const size_t bytes = (size_t)nx * ny * nz * sizeof(float);
+    const int64_t nx_pad = (nx + 3) / 4 * 4;
+    const size_t bytes = (size_t)nx_pad * ny * nz * sizeof(float);
     cudaFree(c->d_cube);
+    cudaFree(c->d_cube_xzy);
     c->d_cube = nullptr;
+    c->d_cube_xzy = nullptr;
     c->bricked = false;
+    c->tma_ready = false;
     if (cudaMalloc((void**)&c->d_cube, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, VR_ENOMEM, "cannot allocate the cube on the device");
     }
-    VR_CUDA(c, cudaMemcpy(c->d_cube, data, bytes, cudaMemcpyDefault));
+    if (nx_pad != nx) VR_CUDA(c, cudaMemset(c->d_cube, 0, bytes));
+    VR_CUDA(c, cudaMemcpy2D(c->d_cube, nx_pad * sizeof(float), data, nx * sizeof(float), nx * sizeof(float),
+                            (size_t)ny * nz, cudaMemcpyDefault));
+    c->nx_pad = nx_pad;
     c->n[0] = nx;
     c->n[1] = ny;
     c->n[2] = nz;
@@ -548,12 +533,41 @@ int vr_brick(vr_ctx* c, int32_t bx, int32_t by, int32_t bz) {
         return fail(c, VR_ENOMEM, "cannot allocate brick min/max");
     }
     int32_t n32[3] = {(int32_t)c->n[0], (int32_t)c->n[1], (int32_t)c->n[2]};
-    VR_CUDA(c, vr::launch_brick_minmax(c->d_cube, n32, c->B, c->nb, c->d_minmax, 0));
+    VR_CUDA(c, vr::launch_brick_minmax(c->d_cube, c->nx_pad, n32, c->B, c->nb, c->d_minmax, 0));
     c->h_minmax.resize(total);
     VR_CUDA(c, cudaMemcpy(c->h_minmax.data(), c->d_minmax, total * sizeof(float2), cudaMemcpyDeviceToHost));
     c->bricked = true;
     return VR_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// Transposed copy and tensor maps for the TMA-staged march (built on first use).
+int prepare_tma(vr_ctx* c) {
+    if (c->tma_ready) return VR_OK;
+    const int64_t nx = c->n[0], ny = c->n[1], nz = c->n[2];
+    const int64_t ny_pad = (ny + 3) / 4 * 4;
+    if (!c->d_cube_xzy) {
+        const size_t bytes = (size_t)ny_pad * nz * nx * sizeof(float);
+        if (cudaMalloc((void**)&c->d_cube_xzy, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, VR_ENOMEM, "cannot allocate the transposed cube for the TMA march");
+        }
+        if (ny_pad != ny) VR_CUDA(c, cudaMemset(c->d_cube_xzy, 0, bytes));
+        VR_CUDA(c, vr::launch_transpose_xzy(c->d_cube, nx, ny, nz, c->nx_pad, c->d_cube_xzy, ny_pad, 0));
+        VR_CUDA(c, cudaDeviceSynchronize());
+    }
+    c->ny_pad = ny_pad;
+    VR_CUDA(c, vr::make_tma_maps(c->d_cube, nx, ny, nz, c->nx_pad, c->d_cube_xzy, ny_pad, &c->tmaps));
+    c->tma_ready = true;
+    return VR_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int vr_get_brick_minmax(vr_ctx* c, float* out, int64_t n_bricks) {
     if (!c) return VR_EINVAL;
@@ -576,13 +590,14 @@ int vr_set_transfer_function(vr_ctx* c, const double* pts, int32_t n) {
             return fail(c, VR_EINVAL, "control values must increase strictly");
     }
     c->tf.assign(pts, pts + 5 * n);
-    c->tf_rgba.resize(n);
+    c->tf_rgba.resize(n + 1);
     c->tf_v.resize(n);
     for (int i = 0; i < n; ++i) {
         c->tf_rgba[i] = make_float4((float)pts[5 * i + 1], (float)pts[5 * i + 2], (float)pts[5 * i + 3],
                                     (float)pts[5 * i + 4]);
         c->tf_v[i] = (float)pts[5 * i];
     }
+    c->tf_rgba[n] = c->tf_rgba[n - 1];
     const double v0 = pts[0], dv = (pts[5 * (n - 1)] - pts[0]) / (n - 1);
     bool uniform = true;
     for (int i = 0; i < n; ++i)
@@ -606,7 +621,12 @@ int vr_set_camera(vr_ctx* c, const vr_camera* cam) {
     for (int j = 0; j < cam->height; ++j)
         c->q[cam->width + j] = vr::df_from_double((1.0 - 2.0 * (j + 0.5) / cam->height) * b.tan_half);
     if (!c->cam_set || cam->step != c->cam.step)
-        c->alpha_split = fit_alpha_poly(cam->step / 1.0, c->alpha_poly);
+    {
+        static const double long_splits[] = {0.5, 0.4, 0.3, 0.25, 0.2};
+        static const double short_splits[] = {0.1, 0.08, 0.06, 0.04, 0.02};
+        c->alpha_split = vr::fit_alpha(cam->step / 1.0, long_splits, vr::kAlphaPolyTerms, c->alpha_poly, 5e-10);
+        c->small_split = vr::fit_alpha(cam->step / 1.0, short_splits, vr::kAlphaSmallTerms, c->alpha_small, 5e-10);
+    }
     c->cam = *cam;
     c->basis = b;
     c->cam_set = true;
@@ -621,6 +641,11 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
         case VR_OPT_MODE:
             if (value != 0 && value != 1) return fail(c, VR_EINVAL, "mode must be 0 or 1");
             c->mode = (int)value;
+            return VR_OK;
+        case VR_OPT_KERNEL:
+            if (value != VR_KERNEL_TMA && value != VR_KERNEL_DIRECT)
+                return fail(c, VR_EINVAL, "kernel must be VR_KERNEL_TMA or VR_KERNEL_DIRECT");
+            c->kernel = (int)value;
             return VR_OK;
         default: return fail(c, VR_EINVAL, "unknown option");
     }
@@ -646,9 +671,10 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     if (rc) return rc;
 
     auto t0 = std::chrono::steady_clock::now();
-    int32_t tiles_x, tiles_y;
+    int32_t tiles_x, tiles_y, T;
     int64_t n_items;
-    rc = plan_frame(c, s, tiles_x, tiles_y, n_items);
+    if (use_tma(c) && (rc = prepare_tma(c))) return rc;
+    rc = plan_frame(c, s, tiles_x, tiles_y, T, n_items);
     if (rc) return rc;
     s.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
@@ -656,8 +682,7 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
 
     if ((rc = grow_device(c, s.d_items, s.dcap_items, (size_t)std::max<int64_t>(n_items, 1)))) return rc;
     if ((rc = grow_device(c, s.d_tile_start, s.dcap_tiles, (size_t)n_tiles + 1))) return rc;
-    if ((rc = grow_device(c, s.d_frags, s.cap_frags,
-                          (size_t)std::max<int64_t>(n_items, 1) * vr::kTilePixels)))
+    if ((rc = grow_device(c, s.d_frags, s.cap_frags, (size_t)std::max<int64_t>(n_items, 1) * T * T)))
         return rc;
     if (!out_on_device && (rc = grow_device(c, s.d_img, s.cap_img, img_px))) return rc;
     // per-frame constants: camera tables (df) and the transfer function
@@ -688,12 +713,13 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     p.height = c->cam.height;
     p.tiles_x = tiles_x;
     p.tiles_y = tiles_y;
+    p.tile = T;
     p.dt = vr::df_from_double(c->cam.step);
     p.dt_f = (float)c->cam.step;
     p.tau = (float)c->cam.term_alpha;
     p.cube = c->d_cube;
-    p.stride_y = c->n[0];
-    p.stride_z = c->n[0] * c->n[1];
+    p.stride_y = c->nx_pad;
+    p.stride_z = c->nx_pad * c->n[1];
     p.offsets32 = ((int64_t)c->B[2] + 1) * p.stride_z + ((int64_t)c->B[1] + 1) * p.stride_y +
                       c->B[0] + 1 < ((int64_t)1 << 32) ? 1 : 0;
     p.tf_rgba = reinterpret_cast<const float4*>(s.d_frame + tf_rgba_off);
@@ -705,6 +731,9 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     std::memcpy(p.alpha_poly, c->alpha_poly, sizeof(p.alpha_poly));
     p.alpha_split = (float)c->alpha_split;
     p.poly_scale = (float)(2.0 / c->alpha_split);
+    std::memcpy(p.alpha_small, c->alpha_small, sizeof(p.alpha_small));
+    p.small_split = (float)c->small_split;
+    p.small_scale = (float)(2.0 / c->small_split);
     p.mode = c->mode;
     p.items = s.d_items;
     p.n_items = (int32_t)n_items;
@@ -721,13 +750,18 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
                                cudaMemcpyHostToDevice, st));
     VR_CUDA(c, cudaMemsetAsync(s.d_stats, 0, sizeof(vr::Stats), st));
     VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
-    VR_CUDA(c, vr::launch_march(p, st));
+    if (use_tma(c)) {
+        VR_CUDA(c, vr::launch_march_tma(p, c->tmaps, st));
+    } else {
+        VR_CUDA(c, vr::launch_march(p, st));
+    }
     VR_CUDA(c, cudaEventRecord(s.ev_march1, st));
     VR_CUDA(c, vr::launch_composite(p, st));
     VR_CUDA(c, cudaMemcpyAsync(s.h_stats, s.d_stats, sizeof(vr::Stats), cudaMemcpyDeviceToHost, st));
     VR_CUDA(c, cudaEventRecord(s.ev_end, st));
     s.pending = true;
     s.launches = (n_items > 0 ? 1 : 0) + 1;
+    s.fragments = n_items * T * T;
     s.h2d_bytes = (int64_t)(frame_bytes + (size_t)n_items * sizeof(vr::Item) +
                             ((size_t)n_tiles + 1) * sizeof(int32_t));
     s.d2h_bytes = (int64_t)sizeof(vr::Stats) + (out_on_device ? 0 : (int64_t)(img_px * sizeof(float4)));

@@ -1,31 +1,37 @@
 // Structures shared by the host planner (vr_host.cu) and the kernels (vr_kernels.cu).
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "df.cuh"
 
 namespace vr {
 
-constexpr int kTile = 8;                    // pixel tile edge (items are brick x 8x8 tile)
+constexpr int kTile = 8;                    // tile edge of the direct-gather march (8x8 items)
 constexpr int kTilePixels = kTile * kTile;  // 64 rays per item, one per thread
+constexpr int kTileTma = 16;                // tile edge of the TMA-staged march (16x16 items)
 constexpr int kMaxTfPoints = 256;
 constexpr int kAlphaPolyTerms = 11;         // coefficients of the opacity-correction polynomial
+constexpr int kAlphaSmallTerms = 6;         // ... and of its short form for small opacities
 
 // Device error flags (OR-ed into Stats::errors).
-constexpr int kErrBounds = 1;               // a sample index left its brick's voxel range
+constexpr int kErrBounds = 1;               // a sample fell outside its staged box (clamped)
+constexpr int kErrTimeout = 2;              // a bounded mbarrier wait gave up
 
 // One work item: the rays of one pixel tile restricted to the samples one brick owns.
 struct Item {
     int32_t brick;  // brick id = ix + nbx*(iy + nby*iz)
     int32_t tile;   // tile id = tx + tiles_x*ty
     int32_t frag;   // fragment slot: its 64 float4 sub-image pixels live at frag*64
-    int32_t pad;
+    int32_t sweep;  // TMA march: sweep axis (0 = x, 1 = y, 2 = z) | 4 if it runs towards -axis
 };
 
 // Per-frame device counters.
 struct Stats {
     unsigned long long samples;
+    unsigned long long chunks_staged;  // TMA march: chunks read from shared memory
+    unsigned long long chunks_direct;  // TMA march: chunks that fell back to global loads
     int errors;
     int pad;
 };
@@ -38,6 +44,7 @@ struct FrameParams {
     const df* qx;  // per column: (2(i+.5)/W - 1) tan(fovy/2) W/H
     const df* qy;  // per row:    (1 - 2(j+.5)/H) tan(fovy/2)
     int32_t width, height, tiles_x, tiles_y;
+    int32_t tile;   // tile edge in pixels (fragments hold tile*tile pixels)
     df dt;          // step (voxels)
     float dt_f;
     float tau;      // termination opacity
@@ -50,14 +57,18 @@ struct FrameParams {
     int64_t stride_y, stride_z;
     int32_t offsets32;     // 1: (B+1) * stride_z < 2^31, brick-local offsets fit in 32 bits
 
-    // transfer function: control points (r,g,b,a) and their values
+    // transfer function: control points (r,g,b,a) and their values; tf_rgba has
+    // tf_n + 1 entries, the last one repeating point tf_n - 1
     const float4* tf_rgba;
     const float* tf_v;
     int32_t tf_n;
     int32_t tf_uniform;    // 1: v_i = v0 + i*dv
     float tf_v0, tf_inv_dv;
-    // opacity correction alpha(a) = 1 - (1-a)^dt as a * Q(a) for a <= alpha_split
-    float alpha_poly[kAlphaPolyTerms];  // Q in powers of t = a * poly_scale - 1
+    // opacity correction alpha(a) = 1 - (1-a)^dt as a * Q(a): Q in powers of
+    // t = a * scale - 1, a short fit for a <= small_split, a long one up to alpha_split
+    float alpha_small[kAlphaSmallTerms];
+    float small_scale, small_split;
+    float alpha_poly[kAlphaPolyTerms];
     float poly_scale;
     float alpha_split;
     int32_t mode;          // 0 = emission-absorption, 1 = MIP
@@ -72,9 +83,18 @@ struct FrameParams {
 };
 
 // Launchers (vr_kernels.cu).
-cudaError_t launch_brick_minmax(const float* cube, const int32_t n[3], const int32_t B[3],
+cudaError_t launch_brick_minmax(const float* cube, int64_t pitch, const int32_t n[3], const int32_t B[3],
                                 const int32_t nb[3], float2* out, cudaStream_t s);
 cudaError_t launch_march(const FrameParams& p, cudaStream_t s);
+// Tensor maps of the TMA-staged march (3 sweep axes x 5 box classes), opaque here.
+struct TmaMaps {
+    CUtensorMap m[15];
+};
+cudaError_t launch_march_tma(const FrameParams& p, const TmaMaps& maps, cudaStream_t s);
+cudaError_t make_tma_maps(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
+                          const float* b, int64_t b_pitch, TmaMaps* maps);
+cudaError_t launch_transpose_xzy(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
+                                 float* b, int64_t b_pitch, cudaStream_t s);
 cudaError_t launch_composite(const FrameParams& p, cudaStream_t s);
 
 }  // namespace vr

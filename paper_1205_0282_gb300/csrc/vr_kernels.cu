@@ -15,14 +15,14 @@
 #include <cfloat>
 #include <cstdint>
 
-#include "vr_internal.cuh"
+#include "vr_device.cuh"
 
 namespace vr {
 
 // ------------------------------------------------------------------ brick min/max
 
-__global__ void brick_minmax_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb,
-                                    float2* __restrict__ out) {
+__global__ void brick_minmax_kernel(const float* __restrict__ cube, int64_t pitch, int3 n, int3 B,
+                                    int3 nb, float2* __restrict__ out) {
     const int id = blockIdx.x;
     const int bx = id % nb.x, by = (id / nb.x) % nb.y, bz = id / (nb.x * nb.y);
     const int x0 = bx * B.x, y0 = by * B.y, z0 = bz * B.z;
@@ -32,7 +32,7 @@ __global__ void brick_minmax_kernel(const float* __restrict__ cube, int3 n, int3
     float mn = FLT_MAX, mx = -FLT_MAX;
     for (int r = warp; r < rows; r += nwarps) {
         const int z = z0 + r / ny_rows, y = y0 + r % ny_rows;
-        const float* row = cube + ((int64_t)z * n.y + y) * (int64_t)n.x;
+        const float* row = cube + ((int64_t)z * n.y + y) * pitch;
         for (int x = x0 + lane; x <= x1; x += 32) {
             float v = __ldg(row + x);
             mn = fminf(mn, v);
@@ -58,137 +58,22 @@ __global__ void brick_minmax_kernel(const float* __restrict__ cube, int3 n, int3
     }
 }
 
-cudaError_t launch_brick_minmax(const float* cube, const int32_t n[3], const int32_t B[3],
+cudaError_t launch_brick_minmax(const float* cube, int64_t pitch, const int32_t n[3], const int32_t B[3],
                                 const int32_t nb[3], float2* out, cudaStream_t s) {
     const int total = nb[0] * nb[1] * nb[2];
-    brick_minmax_kernel<<<total, 256, 0, s>>>(cube, make_int3(n[0], n[1], n[2]),
+    brick_minmax_kernel<<<total, 256, 0, s>>>(cube, pitch, make_int3(n[0], n[1], n[2]),
                                               make_int3(B[0], B[1], B[2]),
                                               make_int3(nb[0], nb[1], nb[2]), out);
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ ray set-up
-
-// Ray of pixel (i, j) in double-float: unit direction d, entry point pe and the
-// sample count n = #{k >= 0 : k dt < t1 - t0}.  Returns false if the ray misses
-// the domain [0, n-1]^3.
-__device__ bool setup_ray(const FrameParams& p, int i, int j, df d[3], df pe[3], int& n_samples) {
-    const df qx = p.qx[i], qy = p.qy[j];
-    df dun[3];
-    for (int a = 0; a < 3; ++a) dun[a] = df_add(df_add(p.f[a], df_mul(qx, p.r[a])), df_mul(qy, p.u[a]));
-    df n2 = df_add(df_add(df_mul(dun[0], dun[0]), df_mul(dun[1], dun[1])), df_mul(dun[2], dun[2]));
-    df len = df_sqrt(n2);
-    for (int a = 0; a < 3; ++a) d[a] = df_div(dun[a], len);
-
-    df tn = df_make(-FLT_MAX), tf = df_make(FLT_MAX);
-    for (int a = 0; a < 3; ++a) {
-        const df hi = df_make((float)(p.n[a] - 1));
-        if (df_is_zero(d[a])) {
-            if (df_lt(p.eye[a], df_make(0.0f)) || df_gt(p.eye[a], hi)) return false;
-            continue;
-        }
-        df ta = df_div(df_neg(p.eye[a]), d[a]);
-        df tb = df_div(df_sub(hi, p.eye[a]), d[a]);
-        tn = df_max(tn, df_min(ta, tb));
-        tf = df_min(tf, df_max(ta, tb));
-    }
-    const df t0 = df_max(tn, df_make(0.0f));
-    if (!df_gt(tf, t0)) return false;
-    const df L = df_sub(tf, t0);
-    n_samples = (int)df_ceil(df_div(L, p.dt));
-    for (int a = 0; a < 3; ++a) pe[a] = df_add(p.eye[a], df_mul(t0, d[a]));
-    return n_samples > 0;
-}
-
-// Sample range [klo, khi) owned by brick bidx (sample p_k = pe + k dt d belongs to
-// brick floor(p/B) per axis, first and last bricks open towards the outside).
-__device__ void brick_range(const FrameParams& p, const int bidx[3], const df d[3], const df pe[3],
-                            int n_samples, int& klo, int& khi) {
-    float lo = 0.0f, hi = (float)n_samples;
-    for (int a = 0; a < 3; ++a) {
-        const df D = df_mul(p.dt, d[a]);
-        const float O = (float)(bidx[a] * p.B[a]);
-        const float OB = (float)(bidx[a] * p.B[a] + p.B[a]);
-        if (bidx[a] > 0) {
-            if (D.hi > 0.0f) {
-                lo = fmaxf(lo, df_ceil(df_div(df_sub(df_make(O), pe[a]), D)));
-            } else if (D.hi < 0.0f) {
-                hi = fminf(hi, df_floor(df_div(df_sub(df_make(O), pe[a]), D)) + 1.0f);
-            } else if (df_lt(pe[a], df_make(O))) {
-                hi = -1.0f;
-            }
-        }
-        if (bidx[a] < p.nb[a] - 1) {
-            if (D.hi > 0.0f) {
-                hi = fminf(hi, df_ceil(df_div(df_sub(df_make(OB), pe[a]), D)));
-            } else if (D.hi < 0.0f) {
-                lo = fmaxf(lo, df_floor(df_div(df_sub(df_make(OB), pe[a]), D)) + 1.0f);
-            } else if (!df_lt(pe[a], df_make(OB))) {
-                hi = -1.0f;
-            }
-        }
-    }
-    lo = fmaxf(lo, 0.0f);
-    hi = fminf(hi, (float)n_samples);
-    klo = (int)lo;
-    khi = hi > lo ? (int)hi : klo;
-}
-
-// ------------------------------------------------------------------ per-sample ops
-
-struct TfShared {
-    float4 rgba[kMaxTfPoints];
-    float v[kMaxTfPoints];
-};
-
-template <bool UNIFORM>
-__device__ __forceinline__ float4 tf_lookup(const FrameParams& p, const TfShared& s, float v) {
-    int seg;
-    float w;
-    if (UNIFORM) {
-        float x = (v - p.tf_v0) * p.tf_inv_dv;
-        x = fminf(fmaxf(x, 0.0f), (float)(p.tf_n - 1));
-        seg = min((int)x, p.tf_n - 2);
-        w = x - (float)seg;
-    } else {
-        int lo = 0, hi = p.tf_n - 1;
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (v >= s.v[mid]) lo = mid;
-            else hi = mid;
-        }
-        seg = lo;
-        w = (v - s.v[seg]) / (s.v[seg + 1] - s.v[seg]);
-        w = fminf(fmaxf(w, 0.0f), 1.0f);
-    }
-    const float4 c0 = s.rgba[seg], c1 = s.rgba[seg + 1];
-    return make_float4(fmaf(w, c1.x - c0.x, c0.x), fmaf(w, c1.y - c0.y, c0.y),
-                       fmaf(w, c1.z - c0.z, c0.z), fmaf(w, c1.w - c0.w, c0.w));
-}
-
-// alpha = 1 - (1 - a)^dt.  For a <= alpha_split: a * Q(t), Q a polynomial fit of
-// alpha(a)/a in t = a*scale - 1 (exactly 0 at a = 0, accurate to ~1e-9); above it
-// the exponential form.
-__device__ __forceinline__ float opacity_correct(const FrameParams& p, float a) {
-    if (a <= p.alpha_split) {
-        const float t = fmaf(a, p.poly_scale, -1.0f);
-        float q = p.alpha_poly[kAlphaPolyTerms - 1];
-#pragma unroll
-        for (int k = kAlphaPolyTerms - 2; k >= 0; --k) q = fmaf(q, t, p.alpha_poly[k]);
-        return a * q;
-    }
-    return 1.0f - exp2f(p.dt_f * __log2f(1.0f - a));
-}
-
-// ------------------------------------------------------------------ ray march
-
 // Off: type of brick-local voxel offsets (uint32_t when (B+1) * nx * ny < 2^32).
 template <bool UNIFORM, int MODE, typename Off>
 __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p) {
     __shared__ TfShared s_tf;
-    for (int k = threadIdx.x; k < p.tf_n; k += blockDim.x) {
+    for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
         s_tf.rgba[k] = p.tf_rgba[k];
-        s_tf.v[k] = p.tf_v[k];
+        if (k < p.tf_n) s_tf.v[k] = p.tf_v[k];
     }
     __syncthreads();
 
@@ -255,7 +140,7 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
                     vmax = fmaxf(vmax, v);
                     continue;
                 }
-                const float4 col = tf_lookup<UNIFORM>(p, s_tf, v);
+                const float4 col = tf_lookup<UNIFORM>(p, s_tf.rgba, s_tf.v, v);
                 const float alpha = opacity_correct(p, col.w);
                 const float w = (1.0f - acc.w) * alpha;
                 acc.x = fmaf(w, col.x, acc.x);
@@ -297,25 +182,26 @@ cudaError_t launch_march(const FrameParams& p, cudaStream_t s) {
 
 // ------------------------------------------------------------------ composite
 
-__global__ void __launch_bounds__(kTilePixels) composite_kernel(const FrameParams p) {
+__global__ void __launch_bounds__(256) composite_kernel(const FrameParams p) {
     __shared__ TfShared s_tf;
     if (p.mode == 1) {
-        for (int k = threadIdx.x; k < p.tf_n; k += blockDim.x) {
+        for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
             s_tf.rgba[k] = p.tf_rgba[k];
-            s_tf.v[k] = p.tf_v[k];
+            if (k < p.tf_n) s_tf.v[k] = p.tf_v[k];
         }
         __syncthreads();
     }
     const int t = blockIdx.x;
+    const int T = p.tile, TT = p.tile * p.tile;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
-    const int i = tx * kTile + threadIdx.x % kTile, j = ty * kTile + threadIdx.x / kTile;
+    const int i = tx * T + threadIdx.x % T, j = ty * T + threadIdx.x / T;
     if (i >= p.width || j >= p.height) return;
     const int f0 = p.tile_start[t], f1 = p.tile_start[t + 1];
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (p.mode == 0) {
         for (int f = f0; f < f1; ++f) {
             if (acc.w >= p.tau) break;
-            const float4 fr = p.frags[(int64_t)f * kTilePixels + threadIdx.x];
+            const float4 fr = p.frags[(int64_t)f * TT + threadIdx.x];
             const float tr = 1.0f - acc.w;
             acc.x = fmaf(tr, fr.x, acc.x);
             acc.y = fmaf(tr, fr.y, acc.y);
@@ -326,14 +212,15 @@ __global__ void __launch_bounds__(kTilePixels) composite_kernel(const FrameParam
         float vmax = -FLT_MAX;
         bool any = false;
         for (int f = f0; f < f1; ++f) {
-            const float4 fr = p.frags[(int64_t)f * kTilePixels + threadIdx.x];
+            const float4 fr = p.frags[(int64_t)f * TT + threadIdx.x];
             if (fr.y > 0.0f) {
                 vmax = fmaxf(vmax, fr.x);
                 any = true;
             }
         }
         if (any) {
-            const float4 c = p.tf_uniform ? tf_lookup<true>(p, s_tf, vmax) : tf_lookup<false>(p, s_tf, vmax);
+            const float4 c = p.tf_uniform ? tf_lookup<true>(p, s_tf.rgba, s_tf.v, vmax)
+                                         : tf_lookup<false>(p, s_tf.rgba, s_tf.v, vmax);
             acc = make_float4(c.x * c.w, c.y * c.w, c.z * c.w, c.w);
         }
     }
@@ -341,7 +228,7 @@ __global__ void __launch_bounds__(kTilePixels) composite_kernel(const FrameParam
 }
 
 cudaError_t launch_composite(const FrameParams& p, cudaStream_t s) {
-    composite_kernel<<<p.tiles_x * p.tiles_y, kTilePixels, 0, s>>>(p);
+    composite_kernel<<<p.tiles_x * p.tiles_y, p.tile * p.tile, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "../../include/vr.h"
+#include "vr_alpha_fit.h"
 #include "vr_internal.cuh"
 
 namespace {
@@ -130,49 +131,6 @@ bool rect_of(const vr_camera& c, const Basis& b, const double lo[3], const doubl
     return true;
 }
 
-double q_of(double a, double r) { return a == 0.0 ? r : -std::expm1(r * std::log1p(-a)) / a; }
-
-// Opacity-correction polynomial (same construction as the main path): Chebyshev
-// interpolation of (1-(1-a)^r)/a on [0, split] in powers of t = 2a/split - 1.
-double alpha_poly(double r, float* coeff) {
-    const int m = vr::kAlphaPolyTerms;
-    for (double split : {0.5, 0.4, 0.3, 0.25, 0.2}) {
-        double c[vr::kAlphaPolyTerms], mono[vr::kAlphaPolyTerms] = {};
-        double tkm1[vr::kAlphaPolyTerms] = {}, tk[vr::kAlphaPolyTerms] = {}, tkp1[vr::kAlphaPolyTerms];
-        for (int j = 0; j < m; ++j) {
-            double s = 0;
-            for (int k = 0; k < m; ++k) {
-                double th = M_PI * (k + 0.5) / m;
-                s += q_of((std::cos(th) + 1.0) * 0.5 * split, r) * std::cos(j * th);
-            }
-            c[j] = 2.0 * s / m;
-        }
-        c[0] *= 0.5;
-        tkm1[0] = 1.0;
-        tk[1] = 1.0;
-        for (int j = 0; j < m; ++j) {
-            const double* T = (j == 0) ? tkm1 : tk;
-            for (int q = 0; q < m; ++q) mono[q] += c[j] * T[q];
-            if (j >= 1) {
-                for (int q = 0; q < m; ++q) tkp1[q] = (q > 0 ? 2.0 * tk[q - 1] : 0.0) - tkm1[q];
-                std::memcpy(tkm1, tk, sizeof(tk));
-                std::memcpy(tk, tkp1, sizeof(tk));
-            }
-        }
-        double err = 0;
-        for (int g = 0; g <= 4000; ++g) {
-            double a = split * g / 4000.0, t = 2.0 * a / split - 1.0, q = 0;
-            for (int k = m - 1; k >= 0; --k) q = q * t + mono[k];
-            err = std::max(err, std::fabs(q - q_of(a, r)));
-        }
-        if (err < 5e-10 || split == 0.2) {
-            for (int k = 0; k < m; ++k) coeff[k] = (float)mono[k];
-            return split;
-        }
-    }
-    return 0.2;
-}
-
 }  // namespace
 
 extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int64_t nz,
@@ -264,7 +222,7 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
     // ---- frame constants (camera tables, transfer function) into the const block
     const size_t q_bytes = (size_t)(cam->width + cam->height) * sizeof(vr::df);
     const size_t tf_rgba_off = (q_bytes + 15) / 16 * 16;
-    const size_t tf_v_off = tf_rgba_off + (size_t)n_tf * sizeof(float4);
+    const size_t tf_v_off = tf_rgba_off + (size_t)(n_tf + 1) * sizeof(float4);
     const size_t const_bytes = tf_v_off + (size_t)n_tf * sizeof(float);
     if (const_bytes > kConstBytes) return VR_EINVAL;
     vr::df* hq = reinterpret_cast<vr::df*>(h_const);
@@ -278,6 +236,7 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
         hrgba[i] = make_float4((float)tf[5 * i + 1], (float)tf[5 * i + 2], (float)tf[5 * i + 3], (float)tf[5 * i + 4]);
         hv[i] = (float)tf[5 * i];
     }
+    hrgba[n_tf] = hrgba[n_tf - 1];  // the kernels read one entry past the last point
     const double v0 = tf[0], dv = (tf[5 * (n_tf - 1)] - tf[0]) / (n_tf - 1);
     bool uniform = true;
     for (int i = 0; i < n_tf; ++i)
@@ -309,6 +268,7 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
     p.height = cam->height;
     p.tiles_x = tiles_x;
     p.tiles_y = tiles_y;
+    p.tile = kTileSide;
     p.dt = vr::df_from_double(cam->step);
     p.dt_f = (float)cam->step;
     p.tau = (float)cam->term_alpha;
@@ -322,9 +282,14 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
     p.tf_uniform = uniform ? 1 : 0;
     p.tf_v0 = (float)v0;
     p.tf_inv_dv = (float)(1.0 / dv);
-    const double split = alpha_poly(cam->step, p.alpha_poly);
+    static const double long_splits[] = {0.5, 0.4, 0.3, 0.25, 0.2};
+    static const double short_splits[] = {0.1, 0.08, 0.06, 0.04, 0.02};
+    const double split = vr::fit_alpha(cam->step, long_splits, vr::kAlphaPolyTerms, p.alpha_poly, 5e-10);
     p.alpha_split = (float)split;
     p.poly_scale = (float)(2.0 / split);
+    const double small = vr::fit_alpha(cam->step, short_splits, vr::kAlphaSmallTerms, p.alpha_small, 5e-10);
+    p.small_split = (float)small;
+    p.small_scale = (float)(2.0 / small);
     p.mode = 0;
     p.items = reinterpret_cast<const vr::Item*>(d_items);
     p.n_items = (int32_t)n_items;

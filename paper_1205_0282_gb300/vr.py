@@ -25,6 +25,9 @@ VR_ETIMEOUT = -5
 VR_OPT_SKIP_EMPTY = 1
 VR_OPT_RECT_CULL = 2
 VR_OPT_MODE = 3
+VR_OPT_KERNEL = 4
+VR_KERNEL_TMA = 0
+VR_KERNEL_DIRECT = 1
 
 _ERR_NAMES = {VR_EINVAL: "VR_EINVAL", VR_ENOMEM: "VR_ENOMEM", VR_ECUDA: "VR_ECUDA",
               VR_ESTATE: "VR_ESTATE", VR_ETIMEOUT: "VR_ETIMEOUT"}
@@ -51,6 +54,7 @@ class vr_stats(ctypes.Structure):
                 ("composite_ms", ctypes.c_double), ("frame_ms", ctypes.c_double),
                 ("plan_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("chunks_staged", ctypes.c_int64), ("chunks_direct", ctypes.c_int64),
                 ("device_errors", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
