@@ -178,7 +178,8 @@ struct vr_ctx {
     int64_t nx_pad = 0;
     float* d_cube_xzy = nullptr; // transposed copy [x][z][y], row pitch ny_pad (sweeps along x)
     int64_t ny_pad = 0;
-    vr::TmaMaps tmaps;
+    CUtensorMap* d_tmaps = nullptr;  // tensor maps of the TMA march (device memory)
+    int tmaps_per_brick = 0;
     bool tma_ready = false;
 
     bool bricked = false;
@@ -470,6 +471,7 @@ void vr_destroy(vr_ctx* c) {
     }
     cudaFree(c->d_cube);
     cudaFree(c->d_cube_xzy);
+    cudaFree(c->d_tmaps);
     cudaFree(c->d_minmax);
     delete c;
 }
@@ -526,6 +528,7 @@ int vr_brick(vr_ctx* c, int32_t bx, int32_t by, int32_t bz) {
     }
     if (total > (1 << 26)) return fail(c, VR_EINVAL, "too many bricks");
     c->n_bricks = total;
+    c->tma_ready = false;  // tensor maps are per brick
     cudaFree(c->d_minmax);
     c->d_minmax = nullptr;
     if (cudaMalloc((void**)&c->d_minmax, total * sizeof(float2)) != cudaSuccess) {
@@ -560,7 +563,16 @@ int prepare_tma(vr_ctx* c) {
         VR_CUDA(c, cudaDeviceSynchronize());
     }
     c->ny_pad = ny_pad;
-    VR_CUDA(c, vr::make_tma_maps(c->d_cube, nx, ny, nz, c->nx_pad, c->d_cube_xzy, ny_pad, &c->tmaps));
+    std::vector<CUtensorMap> maps;
+    VR_CUDA(c, vr::make_tma_maps(c->d_cube, nx, ny, nz, c->nx_pad, c->d_cube_xzy, ny_pad, c->B, c->nb, maps,
+                                 c->tmaps_per_brick));
+    cudaFree(c->d_tmaps);
+    c->d_tmaps = nullptr;
+    if (cudaMalloc((void**)&c->d_tmaps, maps.size() * sizeof(CUtensorMap)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, VR_ENOMEM, "cannot allocate tensor maps");
+    }
+    VR_CUDA(c, cudaMemcpy(c->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     c->tma_ready = true;
     return VR_OK;
 }
@@ -737,6 +749,8 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     p.mode = c->mode;
     p.items = s.d_items;
     p.n_items = (int32_t)n_items;
+    p.tmaps = c->d_tmaps;
+    p.tmaps_per_brick = c->tmaps_per_brick;
     p.tile_start = s.d_tile_start;
     p.frags = s.d_frags;
     p.out = out_on_device ? reinterpret_cast<float4*>(out_rgba) : s.d_img;
@@ -751,7 +765,7 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     VR_CUDA(c, cudaMemsetAsync(s.d_stats, 0, sizeof(vr::Stats), st));
     VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
     if (use_tma(c)) {
-        VR_CUDA(c, vr::launch_march_tma(p, c->tmaps, st));
+        VR_CUDA(c, vr::launch_march_tma(p, st));
     } else {
         VR_CUDA(c, vr::launch_march(p, st));
     }

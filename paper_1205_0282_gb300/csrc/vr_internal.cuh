@@ -1,6 +1,7 @@
 // Structures shared by the host planner (vr_host.cu) and the kernels (vr_kernels.cu).
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -11,6 +12,7 @@ namespace vr {
 constexpr int kTile = 8;                    // tile edge of the direct-gather march (8x8 items)
 constexpr int kTilePixels = kTile * kTile;  // 64 rays per item, one per thread
 constexpr int kTileTma = 16;                // tile edge of the TMA-staged march (16x16 items)
+constexpr int kTmaClasses = 8;              // staged-box classes of the TMA march
 constexpr int kMaxTfPoints = 256;
 constexpr int kAlphaPolyTerms = 11;         // coefficients of the opacity-correction polynomial
 constexpr int kAlphaSmallTerms = 6;         // ... and of its short form for small opacities
@@ -76,6 +78,8 @@ struct FrameParams {
     // plan
     const Item* items;
     int32_t n_items;
+    const CUtensorMap* tmaps;   // TMA march: tensor maps in device memory
+    int32_t tmaps_per_brick;    // 1: one set per brick (brick-local coordinates)
     const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
     float4* frags;
     float4* out;
@@ -86,13 +90,10 @@ struct FrameParams {
 cudaError_t launch_brick_minmax(const float* cube, int64_t pitch, const int32_t n[3], const int32_t B[3],
                                 const int32_t nb[3], float2* out, cudaStream_t s);
 cudaError_t launch_march(const FrameParams& p, cudaStream_t s);
-// Tensor maps of the TMA-staged march (3 sweep axes x 5 box classes), opaque here.
-struct TmaMaps {
-    CUtensorMap m[15];
-};
-cudaError_t launch_march_tma(const FrameParams& p, const TmaMaps& maps, cudaStream_t s);
+cudaError_t launch_march_tma(const FrameParams& p, cudaStream_t s);
 cudaError_t make_tma_maps(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
-                          const float* b, int64_t b_pitch, TmaMaps* maps);
+                          const float* b, int64_t b_pitch, const int32_t B[3], const int32_t nb[3],
+                          std::vector<CUtensorMap>& out, int& per_brick);
 cudaError_t launch_transpose_xzy(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
                                  float* b, int64_t b_pitch, cudaStream_t s);
 cudaError_t launch_composite(const FrameParams& p, cudaStream_t s);

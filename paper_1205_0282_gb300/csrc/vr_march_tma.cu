@@ -4,14 +4,16 @@
 //
 // One CTA of 256 threads renders one (brick, 16x16 pixel tile) item, one ray per
 // thread.  The CTA sweeps the brick along the item's dominant ray axis ("sweep
-// axis") in chunks of kC sample planes.  For each chunk the voxels that the tile's
-// rays can touch -- a square box across the sweep axis and kC + 1 planes along it,
+// axis") in chunks of C sample planes.  For each chunk the voxels that the tile's
+// rays can touch -- a square box across the sweep axis and C + 1 planes along it,
 // placed from the tile's four corner rays -- are copied from HBM into shared memory
 // by one TMA bulk-tensor load (mbarrier transaction count, bounded wait), and the
 // eight trilinear corners of every sample are read from shared memory.  The box
-// side is chosen per item from five classes (24..56 voxels) to match the tile's
-// footprint, so little more than the voxels the rays need is moved.  Four CTAs
-// share an SM, so one CTA's copy overlaps the others' compute.
+// is chosen per item from eight classes that trade side (24..80 voxels) against
+// depth (8..2 planes) at about the same size, matching the tile's footprint; the
+// tensor maps cover one brick plus its apron each, so box parts outside the brick
+// are zero-filled without being read.  Four CTAs share an SM, so one CTA's copy
+// overlaps the others' compute.
 //
 // The box's innermost axis must be contiguous in memory and must not be the sweep
 // axis, so sweeps along y and z read the cube as stored ([z][y][x]) and sweeps
@@ -30,14 +32,24 @@ namespace tma {
 
 constexpr int kT = kTileTma;           // tile edge (pixels)
 constexpr int kThreads = kT * kT;      // one ray per thread
-constexpr int kC = 3;                  // sample planes per chunk
-constexpr int kD = kC + 1;             // planes per staged box
-constexpr int kClasses = 5;            // box sides 24, 32, 40, 48, 56 (multiples of 4)
-constexpr int kMaxSide = 24 + 8 * (kClasses - 1);
-constexpr int kMaxBoxFloats = kMaxSide * kMaxSide * kD;
 constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before a wait gives up
 
+// Box classes: side (across the sweep axis, a multiple of 4) and depth (planes along
+// it; a chunk covers depth - 1 sample planes).
 __host__ __device__ constexpr int class_side(int c) { return 24 + 8 * c; }
+__host__ __device__ constexpr int class_depth(int c) {
+    return c < 3 ? 8 : (c == 3 ? 5 : (c == 4 ? 4 : (c == 5 ? 3 : 2)));
+}
+constexpr int kMaxSide = class_side(kTmaClasses - 1);
+constexpr int kMaxBoxFloats = 12800;  // max over classes of side^2 * depth
+static_assert(class_side(0) * class_side(0) * class_depth(0) <= kMaxBoxFloats &&
+              class_side(2) * class_side(2) * class_depth(2) <= kMaxBoxFloats &&
+              class_side(3) * class_side(3) * class_depth(3) <= kMaxBoxFloats &&
+              class_side(4) * class_side(4) * class_depth(4) <= kMaxBoxFloats &&
+              class_side(5) * class_side(5) * class_depth(5) <= kMaxBoxFloats &&
+              class_side(6) * class_side(6) * class_depth(6) <= kMaxBoxFloats &&
+              class_side(7) * class_side(7) * class_depth(7) <= kMaxBoxFloats,
+              "box buffer too small");
 
 struct alignas(16) Shared {
     unsigned long long bar;
@@ -94,18 +106,18 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Footprint of chunk g (sample planes [g*kC, g*kC + kC] along the sweep axis) from
+// Footprint of chunk g (sample planes [g*C, g*C + C] along the sweep axis) from
 // the corner-ray coefficients: lower corner (u0, v0) of a box of side `side`, with
 // two voxels of margin on each side (the corner rays are evaluated in FP32 from the
 // eye, the samples in brick-local coordinates) and the global u start rounded down
 // to a multiple of 4 (16-byte TMA alignment of the innermost coordinate).  Returns
 // false if the footprint does not fit.
-__device__ __forceinline__ bool place_box(const float (*coef)[4], int g, int side, int Ou, int& u0,
+__device__ __forceinline__ bool place_box(const float (*coef)[4], int g, int C, int side, int Ou, int& u0,
                                           int& v0) {
     float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const float sig = (float)(g * kC + e * kC);
+        const float sig = (float)(g * C + e * C);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const float pu = fmaf(coef[c][1], sig, coef[c][0]);
@@ -130,8 +142,8 @@ struct Axes {
 };
 
 template <int S, bool DESC, bool UNIFORM, typename Off>
-__device__ __forceinline__ void march_item(const FrameParams& p, const TmaMaps& maps, const Item& item,
-                                           float* box, Shared& sh, const float4* s_rgba, const float* s_v) {
+__device__ __forceinline__ void march_item(const FrameParams& p, const Item& item, float* box, Shared& sh,
+                                           const float4* s_rgba, const float* s_v) {
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
     const int tid = threadIdx.x;
     const int tx = item.tile % p.tiles_x, ty = item.tile / p.tiles_x;
@@ -166,13 +178,13 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const TmaMaps& 
             }
         }
     }
-    // chunk range of this ray along the sweep axis, reduced over the tile
+    // sample-plane range of this ray along the sweep axis, reduced over the tile
     int g_lo = INT_MAX, g_hi = INT_MIN;
     if (nk > 0) {
         const int p0 = min(max(__float2int_rd(qs[S]), 0), imax[S]);
         const int p1 = min(max(__float2int_rd(fmaf((float)(nk - 1), dq[S], qs[S])), 0), imax[S]);
-        g_lo = min(p0, p1) / kC;
-        g_hi = max(p0, p1) / kC;
+        g_lo = min(p0, p1);
+        g_hi = max(p0, p1);
     }
     for (int o = 16; o > 0; o >>= 1) {
         g_lo = min(g_lo, __shfl_xor_sync(0xffffffffu, g_lo, o));
@@ -209,29 +221,30 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const TmaMaps& 
         g_lo = min(g_lo, sh.red[0][w]);
         g_hi = max(g_hi, sh.red[1][w]);
     }
-    const int nchunks = g_hi >= g_lo ? g_hi - g_lo + 1 : 0;
+    const int p_lo = g_lo, p_hi = g_hi;  // sample planes of the whole tile
     if (tid == 0) {
-        // box class: the smallest side holding the first and the last chunk (the
-        // footprint's extent is convex in the sweep coordinate, so every chunk in
-        // between fits as well).  Corner rays must run along the sweep direction
-        // and reach every plane in front of the eye; otherwise the item reads
-        // global memory.
+        // box class: the first (smallest) class whose box holds the first and the
+        // last chunk (the footprint's extent is convex in the sweep coordinate, so
+        // every chunk in between fits as well).  Corner rays must run along the
+        // sweep direction and reach every plane in front of the eye; otherwise the
+        // item reads global memory.
         int cls = -1;
-        if (nchunks > 0) {
+        if (p_hi >= p_lo) {
             const float e_s = (p.eye[S].hi - (float)O[S]) + p.eye[S].lo;
-            const float sig0 = (float)(g_lo * kC), sig1 = (float)(g_hi * kC + kC);
             bool front = sh.toward[0] && sh.toward[1] && sh.toward[2] && sh.toward[3];
-            front = front && (DESC ? (sig1 < e_s) : (sig0 > e_s));
-            for (int c = 0; front && c < kClasses; ++c) {
+            front = front && (DESC ? ((float)(p_hi + 1) < e_s) : ((float)p_lo > e_s));
+            for (int c = 0; front && c < kTmaClasses; ++c) {
+                const int C = class_depth(c) - 1;
                 int u0, v0;
-                if (place_box(sh.coef, g_lo, class_side(c), O[U], u0, v0) &&
-                    place_box(sh.coef, g_hi, class_side(c), O[U], u0, v0)) {
+                if (place_box(sh.coef, p_lo / C, C, class_side(c), O[U], u0, v0) &&
+                    place_box(sh.coef, p_hi / C, C, class_side(c), O[U], u0, v0)) {
                     cls = c;
                     break;
                 }
             }
+            const int C = cls >= 0 ? class_depth(cls) - 1 : 7;
             int u0 = 0, v0 = 0;
-            const bool ok = cls >= 0 && place_box(sh.coef, DESC ? g_hi : g_lo, class_side(cls), O[U], u0, v0);
+            const bool ok = cls >= 0 && place_box(sh.coef, (DESC ? p_hi : p_lo) / C, C, class_side(cls), O[U], u0, v0);
             sh.box[0][0] = u0;
             sh.box[0][1] = v0;
             sh.box[0][2] = ok ? 1 : 0;
@@ -242,13 +255,23 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const TmaMaps& 
     __syncthreads();
     const int cls = sh.cls;
     const int side = cls >= 0 ? class_side(cls) : kMaxSide;
+    const int depth = cls >= 0 ? class_depth(cls) : 8;
+    const int C = depth - 1;  // sample planes per chunk
+    g_lo = p_hi >= p_lo ? p_lo / C : 0;
+    g_hi = p_hi >= p_lo ? p_hi / C : -1;
+    const int nchunks = g_hi - g_lo + 1;
     // shared-memory strides of the staged box: u contiguous, then v, then the sweep
     // axis; a y-sweep box is stored [v][s][u]
-    const int SV = S == 1 ? side * kD : side;
+    const int SV = S == 1 ? side * depth : side;
     const int SP = S == 1 ? side : side * side;
-    const int max_off = side * side * kD - 1 - (SP + SV + 1);
-    const uint32_t box_bytes = (uint32_t)(side * side * kD * 4);
-    const CUtensorMap* map = &maps.m[S * kClasses + (cls >= 0 ? cls : 0)];
+    const int max_off = side * side * depth - 1 - (SP + SV + 1);
+    const uint32_t box_bytes = (uint32_t)(side * side * depth * 4);
+    // tensor maps: one set per brick (brick-local coordinates) or one for the cube
+    const CUtensorMap* map = p.tmaps + ((p.tmaps_per_brick ? item.brick * 3 : 0) + S) * kTmaClasses +
+                             (cls >= 0 ? cls : 0);
+    int corg[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) corg[a] = p.tmaps_per_brick ? 0 : O[a];
 
     const float* __restrict__ gbase =
         p.cube + (int64_t)O[2] * p.stride_z + (int64_t)O[1] * p.stride_y + O[0];
@@ -266,15 +289,15 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const TmaMaps& 
 
     for (int ci = 0; ci < nchunks; ++ci) {
         const int g = DESC ? g_hi - ci : g_lo + ci;
-        const int plo = g * kC, phi = plo + kC - 1;
+        const int plo = g * C, phi = plo + C - 1;
         const int u0 = sh.box[ci & 1][0], v0 = sh.box[ci & 1][1];
         const bool ok = sh.box[ci & 1][2] != 0;
         if (ok) {
             if (tid == 0) {
                 int c[3];
-                c[U] = O[U] + u0;
-                c[V] = O[V] + v0;
-                c[S] = O[S] + plo;
+                c[U] = corg[U] + u0;
+                c[V] = corg[V] + v0;
+                c[S] = corg[S] + plo;
                 // tensor-map coordinate order: (x, y, z) for the stored cube, (y, z, x)
                 // for the transposed copy
                 fence_proxy_async();
@@ -364,7 +387,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const TmaMaps& 
             // place the next chunk's box while the other threads finish this one
             if (ci + 1 < nchunks) {
                 int nu0 = 0, nv0 = 0;
-                const bool nok = cls >= 0 && place_box(sh.coef, DESC ? g - 1 : g + 1, side, O[U], nu0, nv0);
+                const bool nok = cls >= 0 && place_box(sh.coef, DESC ? g - 1 : g + 1, C, side, O[U], nu0, nv0);
                 sh.box[(ci + 1) & 1][0] = nu0;
                 sh.box[(ci + 1) & 1][1] = nv0;
                 sh.box[(ci + 1) & 1][2] = nok ? 1 : 0;
@@ -395,7 +418,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const TmaMaps& 
 }
 
 template <bool UNIFORM, typename Off>
-__global__ void __launch_bounds__(kThreads, 4) march_tma_kernel(const FrameParams p, const __grid_constant__ TmaMaps maps) {
+__global__ void __launch_bounds__(kThreads, 4) march_tma_kernel(const FrameParams p) {
     extern __shared__ __align__(128) unsigned char smem[];
     float* box = reinterpret_cast<float*>(smem);
     Shared& sh = *reinterpret_cast<Shared*>(smem + kMaxBoxFloats * 4);
@@ -412,25 +435,25 @@ __global__ void __launch_bounds__(kThreads, 4) march_tma_kernel(const FrameParam
     }
     const Item item = p.items[blockIdx.x];
     switch (item.sweep & 7) {
-        case 0: march_item<0, false, UNIFORM, Off>(p, maps, item, box, sh, s_rgba, s_v); break;
-        case 1: march_item<1, false, UNIFORM, Off>(p, maps, item, box, sh, s_rgba, s_v); break;
-        case 2: march_item<2, false, UNIFORM, Off>(p, maps, item, box, sh, s_rgba, s_v); break;
-        case 4: march_item<0, true, UNIFORM, Off>(p, maps, item, box, sh, s_rgba, s_v); break;
-        case 5: march_item<1, true, UNIFORM, Off>(p, maps, item, box, sh, s_rgba, s_v); break;
-        default: march_item<2, true, UNIFORM, Off>(p, maps, item, box, sh, s_rgba, s_v); break;
+        case 0: march_item<0, false, UNIFORM, Off>(p, item, box, sh, s_rgba, s_v); break;
+        case 1: march_item<1, false, UNIFORM, Off>(p, item, box, sh, s_rgba, s_v); break;
+        case 2: march_item<2, false, UNIFORM, Off>(p, item, box, sh, s_rgba, s_v); break;
+        case 4: march_item<0, true, UNIFORM, Off>(p, item, box, sh, s_rgba, s_v); break;
+        case 5: march_item<1, true, UNIFORM, Off>(p, item, box, sh, s_rgba, s_v); break;
+        default: march_item<2, true, UNIFORM, Off>(p, item, box, sh, s_rgba, s_v); break;
     }
 }
 
 }  // namespace tma
 
-cudaError_t launch_march_tma(const FrameParams& p, const TmaMaps& maps, cudaStream_t s) {
+cudaError_t launch_march_tma(const FrameParams& p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
     static_assert(sizeof(tma::Shared) % 16 == 0, "TF table alignment");
     const size_t smem = (size_t)tma::kMaxBoxFloats * 4 + sizeof(tma::Shared) +
                         (size_t)(p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
     auto launch = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<p.n_items, tma::kThreads, smem, s>>>(p, maps);
+        kern<<<p.n_items, tma::kThreads, smem, s>>>(p);
     };
     if (p.tf_uniform) {
         if (p.offsets32) launch(tma::march_tma_kernel<true, uint32_t>);
@@ -473,13 +496,22 @@ cudaError_t launch_transpose_xzy(const float* a, int64_t nx, int64_t ny, int64_t
 
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <vector>
+
 namespace vr {
 
-// Encode the tensor maps of the TMA march: maps->m[S * kClasses + c] loads boxes of
-// side class_side(c) for sweeps along axis S.  a: cube [z][y][x] with row pitch
-// a_pitch floats; b: transposed copy [x][z][y] with row pitch b_pitch.
+// Encode the tensor maps of the TMA march into `out`.  Per-brick maps (when the
+// brick origins keep the 16-byte alignment TMA needs: B_x and B_y multiples of 4)
+// cover one brick plus its one-voxel apron, so box parts outside the brick are
+// zero-filled without memory traffic; index ((brick * 3 + S) * kTmaClasses + c).
+// Otherwise one set covers the cube; index (S * kTmaClasses + c).  a: cube
+// [z][y][x] with row pitch a_pitch floats; b: transposed copy [x][z][y] with row
+// pitch b_pitch.  Sweeps along z and y read a (dims x, y, z; a y-sweep box is
+// u = x, sweep = y, v = z), sweeps along x read b (dims y, z, x).
 cudaError_t make_tma_maps(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
-                          const float* b, int64_t b_pitch, TmaMaps* maps) {
+                          const float* b, int64_t b_pitch, const int32_t B[3], const int32_t nb[3],
+                          std::vector<CUtensorMap>& out, int& per_brick) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -489,26 +521,40 @@ cudaError_t make_tma_maps(const float* a, int64_t nx, int64_t ny, int64_t nz, in
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    per_brick = (B[0] % 4 == 0 && B[1] % 4 == 0) ? 1 : 0;
+    const int64_t n_bricks = per_brick ? (int64_t)nb[0] * nb[1] * nb[2] : 1;
+    out.resize((size_t)n_bricks * 3 * kTmaClasses);
     const cuuint32_t estr[3] = {1, 1, 1};
-    const cuuint64_t dims_a[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t str_a[2] = {(cuuint64_t)a_pitch * 4, (cuuint64_t)(a_pitch * ny) * 4};
-    const cuuint64_t dims_b[3] = {(cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)nx};
     const cuuint64_t str_b[2] = {(cuuint64_t)b_pitch * 4, (cuuint64_t)(b_pitch * nz) * 4};
-    for (int S = 0; S < 3; ++S)
-        for (int c = 0; c < tma::kClasses; ++c) {
-            const cuuint32_t side = (cuuint32_t)tma::class_side(c);
-            // sweeps along z and y read the stored cube (dims x, y, z); a y-sweep box
-            // is (u = x, sweep = y, v = z); sweeps along x read the transposed copy
-            // (dims y, z, x)
-            cuuint32_t box[3] = {side, side, (cuuint32_t)tma::kD};
-            if (S == 1) box[1] = (cuuint32_t)tma::kD, box[2] = side;
-            const bool tr = S == 0;
-            CUresult r = encode(&maps->m[S * tma::kClasses + c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                                const_cast<float*>(tr ? b : a), tr ? dims_b : dims_a, tr ? str_b : str_a, box,
-                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    for (int64_t id = 0; id < n_bricks; ++id) {
+        int64_t O[3] = {0, 0, 0}, E[3] = {nx, ny, nz};
+        if (per_brick) {
+            const int64_t idx[3] = {id % nb[0], (id / nb[0]) % nb[1], id / ((int64_t)nb[0] * nb[1])};
+            const int64_t n[3] = {nx, ny, nz};
+            for (int k = 0; k < 3; ++k) {
+                O[k] = idx[k] * B[k];
+                E[k] = std::min<int64_t>(B[k] + 1, n[k] - O[k]);
+            }
         }
+        const float* base_a = a + (O[2] * ny + O[1]) * a_pitch + O[0];
+        const float* base_b = b + (O[0] * nz + O[2]) * b_pitch + O[1];
+        const cuuint64_t dims_a[3] = {(cuuint64_t)E[0], (cuuint64_t)E[1], (cuuint64_t)E[2]};
+        const cuuint64_t dims_b[3] = {(cuuint64_t)E[1], (cuuint64_t)E[2], (cuuint64_t)E[0]};
+        for (int S = 0; S < 3; ++S)
+            for (int c = 0; c < kTmaClasses; ++c) {
+                const cuuint32_t side = (cuuint32_t)tma::class_side(c), depth = (cuuint32_t)tma::class_depth(c);
+                cuuint32_t box[3] = {side, side, depth};
+                if (S == 1) box[1] = depth, box[2] = side;
+                const bool tr = S == 0;
+                CUresult r = encode(&out[(size_t)(id * 3 + S) * kTmaClasses + c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                                    const_cast<float*>(tr ? base_b : base_a), tr ? dims_b : dims_a,
+                                    tr ? str_b : str_a, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+            }
+    }
     return cudaSuccess;
 }
 
