@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["hi", "mid", "tiny"], default="hi")
     ap.add_argument("--tf", choices=["a", "b"], default="a")
+    ap.add_argument("--width", type=int, default=0, help="override the image width")
+    ap.add_argument("--height", type=int, default=0, help="override the image height")
+    ap.add_argument("--kernel", choices=["auto", "tma", "direct", "tex"], default="auto")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -53,6 +56,17 @@ def parse():
 
 
 def workload(args):
+    spec, tf, poses, desc = _workload(args)
+    if args.width or args.height:
+        W = args.width or spec["width"]
+        H = args.height or spec["height"]
+        spec["width"], spec["height"] = W, H
+        poses = [dict(c, width=W, height=H) for c in poses]
+        desc += f", image overridden to {W}x{H}"
+    return spec, tf, poses, desc
+
+
+def _workload(args):
     if args.config == "hi":
         spec = dict(synth.HI)
         tf = synth.tf_hi_a() if args.tf == "a" else synth.tf_hi_b()
@@ -258,6 +272,9 @@ def run_ours(args):
     torch.cuda.empty_cache()
     r.brick(*spec["brick"])
     r.set_transfer_function(tf)
+    from paper_1205_0282_gb300 import vr as vrmod
+    r.set_option(vrmod.VR_OPT_KERNEL, {"auto": vrmod.VR_KERNEL_AUTO, "tma": vrmod.VR_KERNEL_TMA,
+                                       "direct": vrmod.VR_KERNEL_DIRECT, "tex": vrmod.VR_KERNEL_TEX}[args.kernel])
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -338,9 +355,12 @@ def run_ours(args):
     avg_march_ms = st["march_ms"] / max(st["frames"], 1)
     bytes_per_launch = st["touched_bytes"] / max(st["frames"], 1)
     achieved = bytes_per_launch / (avg_march_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "march_kernel", "achieved": achieved, "peak": peak,
+    kname = {"tma": "march_tma_kernel", "direct": "march_kernel", "tex": "march_tex_kernel",
+             "auto": "march_tex_kernel" if st["chunks_staged"] == 0 else "march_tma_kernel"}[args.kernel]
+    roofline = {"bound": "hbm", "kernel": kname,
+                "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic("march_kernel", spec["name"]),
+                "traffic": recorded_traffic(kname, spec["name"]),
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": avg_march_ms,
@@ -376,6 +396,9 @@ def run_ours(args):
             "plan_ms_per_frame": st["plan_ms"] / max(st["frames"], 1),
             "composite_ms_per_frame": st["composite_ms"] / max(st["frames"], 1),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "march_kernel": args.kernel,
+            "chunks_staged_per_frame": st["chunks_staged"] / max(st["frames"], 1),
+            "chunks_direct_per_frame": st["chunks_direct"] / max(st["frames"], 1),
             "gpu_launches": launches, "clocks": clocks.summary(),
             "device_errors": st["device_errors"]}
     print(json.dumps(line), flush=True)

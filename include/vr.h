@@ -95,13 +95,20 @@ typedef struct {
 #define VR_OPT_MODE 3        /* 0 (default): emission-absorption compositing;
                                 1: maximum intensity projection + colour map (Section 2.3.3) */
 #define VR_OPT_KERNEL 4      /* ray-march kernel for emission-absorption frames:
-                                VR_KERNEL_TMA (default): 16x16-pixel items, voxel boxes staged
-                                in shared memory by TMA; VR_KERNEL_DIRECT: 8x8-pixel items,
-                                trilinear corners read through the L1 cache.  MIP frames
-                                always use the direct kernel.  Both give the same image up to
+                                VR_KERNEL_AUTO (default): VR_KERNEL_TEX when the cube fits the
+                                device's layered-texture limits, else VR_KERNEL_TMA;
+                                VR_KERNEL_TEX: 8x8-pixel items, corners gathered unfiltered
+                                (tld4) from three layered-texture copies of the cube (three
+                                times the cube's size in extra device memory);
+                                VR_KERNEL_TMA: 16x16-pixel items, voxel boxes staged in shared
+                                memory by TMA (one transposed copy extra); VR_KERNEL_DIRECT:
+                                8x8-pixel items, corners read through the L1 cache.  MIP frames
+                                always use the direct kernel.  All give the same image up to
                                 FP32 rounding. */
 #define VR_KERNEL_TMA 0
 #define VR_KERNEL_DIRECT 1
+#define VR_KERNEL_TEX 2
+#define VR_KERNEL_AUTO 3
 
 /*
  * Create a context on CUDA device `device`.  *out receives the context.

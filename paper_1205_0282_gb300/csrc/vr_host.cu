@@ -179,6 +179,9 @@ struct vr_ctx {
     float* d_cube_xzy = nullptr; // transposed copy [x][z][y], row pitch ny_pad (sweeps along x)
     int64_t ny_pad = 0;
     CUtensorMap* d_tmaps = nullptr;  // tensor maps of the TMA march (device memory)
+    cudaArray_t tex_arr[3] = {nullptr, nullptr, nullptr};  // texture march: layered copies
+    cudaTextureObject_t tex_obj[3] = {0, 0, 0};
+    bool tex_ready = false;
     int tmaps_per_brick = 0;
     bool tma_ready = false;
 
@@ -207,7 +210,8 @@ struct vr_ctx {
 
     bool skip_empty = true, rect_cull = true;
     int mode = 0;
-    int kernel = VR_KERNEL_TMA;
+    int kernel = VR_KERNEL_AUTO;
+    int tex_fits = -1;  // -1 unknown, 0/1: the cube fits the layered-texture limits
 
     Slot slots[kSlots];
     int next_slot = 0;
@@ -306,18 +310,51 @@ int retire_all(vr_ctx* c) {
 }
 
 // Build the frame's work list into slot s (host).  Returns VR_OK.
-bool use_tma(const vr_ctx* c) { return c->kernel == VR_KERNEL_TMA && c->mode == 0; }
+// Kernel selection for emission-absorption frames: VR_KERNEL_AUTO takes the
+// texture-gather march when the cube fits the device's layered-texture limits and
+// the TMA-staged march otherwise.
+bool tex_fits(vr_ctx* c) {
+    if (c->tex_fits < 0) {
+        int maxw = 0, maxh = 0, maxl = 0;
+        cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, c->device);
+        cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, c->device);
+        cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, c->device);
+        bool ok = c->n[1] <= 65535 && c->n[2] <= 65535;
+        for (int S = 0; S < 3; ++S) {
+            const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
+            ok = ok && c->n[U] <= maxw && c->n[V] <= maxh && c->n[S] <= maxl;
+        }
+        c->tex_fits = ok ? 1 : 0;
+    }
+    return c->tex_fits == 1;
+}
+bool use_tex(vr_ctx* c) {
+    return c->mode == 0 && (c->kernel == VR_KERNEL_TEX || (c->kernel == VR_KERNEL_AUTO && tex_fits(c)));
+}
+bool use_tma(vr_ctx* c) {
+    return c->mode == 0 && (c->kernel == VR_KERNEL_TMA || (c->kernel == VR_KERNEL_AUTO && !tex_fits(c)));
+}
+
+void free_tex(vr_ctx* c) {
+    for (int a = 0; a < 3; ++a) {
+        if (c->tex_obj[a]) cudaDestroyTextureObject(c->tex_obj[a]);
+        if (c->tex_arr[a]) cudaFreeArray(c->tex_arr[a]);
+        c->tex_obj[a] = 0;
+        c->tex_arr[a] = nullptr;
+    }
+    c->tex_ready = false;
+}
 
 int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int32_t& T, int64_t& n_items) {
     const vr_camera& cam = c->cam;
-    T = use_tma(c) ? vr::kTileTma : vr::kTile;
+    T = use_tma(c) ? vr::kTileTma : vr::kTile;  // the direct and texture marches use 8x8 tiles
     tiles_x = (cam.width + T - 1) / T;
     tiles_y = (cam.height + T - 1) / T;
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
     // sweep axis of each tile for the TMA march: the dominant axis of the ray
     // through the tile's centre pixel, and its sign
     c->plan_sweep.assign(n_tiles, 0);
-    if (use_tma(c)) {
+    if (use_tma(c) || use_tex(c)) {
         for (int ty = 0; ty < tiles_y; ++ty)
             for (int tx = 0; tx < tiles_x; ++tx) {
                 const int i = std::min(tx * T + T / 2, cam.width - 1), j = std::min(ty * T + T / 2, cam.height - 1);
@@ -472,6 +509,7 @@ void vr_destroy(vr_ctx* c) {
     cudaFree(c->d_cube);
     cudaFree(c->d_cube_xzy);
     cudaFree(c->d_tmaps);
+    free_tex(c);
     cudaFree(c->d_minmax);
     delete c;
 }
@@ -497,6 +535,8 @@ int vr_load_cube(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int64_t n
     c->d_cube_xzy = nullptr;
     c->bricked = false;
     c->tma_ready = false;
+    c->tex_fits = -1;
+    free_tex(c);
     if (cudaMalloc((void**)&c->d_cube, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, VR_ENOMEM, "cannot allocate the cube on the device");
@@ -574,6 +614,53 @@ int prepare_tma(vr_ctx* c) {
     }
     VR_CUDA(c, cudaMemcpy(c->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
     c->tma_ready = true;
+    return VR_OK;
+}
+
+// Layered texture copies for the texture-gather march (built on first use): the copy
+// for sweeps along axis S has layers along S and texels over the two other axes.
+int prepare_tex(vr_ctx* c) {
+    if (c->tex_ready) return VR_OK;
+    int maxw = 0, maxh = 0, maxl = 0;
+    VR_CUDA(c, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, c->device));
+    VR_CUDA(c, cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, c->device));
+    VR_CUDA(c, cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, c->device));
+    const int64_t* n = c->n;
+    if (n[1] > 65535 || n[2] > 65535) return fail(c, VR_EINVAL, "cube too large for the texture march");
+    for (int S = 0; S < 3; ++S) {
+        const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
+        if (n[U] > maxw || n[V] > maxh || n[S] > maxl)
+            return fail(c, VR_EINVAL, "cube exceeds the layered-texture limits of this device");
+    }
+    free_tex(c);
+    for (int S = 0; S < 3; ++S) {
+        const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
+        cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
+        if (cudaMalloc3DArray(&c->tex_arr[S], &ch, make_cudaExtent((size_t)n[U], (size_t)n[V], (size_t)n[S]),
+                              cudaArrayLayered | cudaArraySurfaceLoadStore) != cudaSuccess) {
+            cudaGetLastError();
+            free_tex(c);
+            return fail(c, VR_ENOMEM, "cannot allocate the layered textures");
+        }
+        cudaResourceDesc rd;
+        std::memset(&rd, 0, sizeof(rd));
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = c->tex_arr[S];
+        cudaSurfaceObject_t surf = 0;
+        VR_CUDA(c, cudaCreateSurfaceObject(&surf, &rd));
+        cudaError_t e = vr::fill_tex_layers(c->d_cube, n[0], n[1], n[2], c->nx_pad, S, surf, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaDestroySurfaceObject(surf);
+        if (e != cudaSuccess) return cuda_fail(c, e, "fill_tex_layers");
+        cudaTextureDesc td;
+        std::memset(&td, 0, sizeof(td));
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        VR_CUDA(c, cudaCreateTextureObject(&c->tex_obj[S], &rd, &td, nullptr));
+    }
+    c->tex_ready = true;
     return VR_OK;
 }
 
@@ -655,8 +742,9 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
             c->mode = (int)value;
             return VR_OK;
         case VR_OPT_KERNEL:
-            if (value != VR_KERNEL_TMA && value != VR_KERNEL_DIRECT)
-                return fail(c, VR_EINVAL, "kernel must be VR_KERNEL_TMA or VR_KERNEL_DIRECT");
+            if (value != VR_KERNEL_AUTO && value != VR_KERNEL_TMA && value != VR_KERNEL_DIRECT &&
+                value != VR_KERNEL_TEX)
+                return fail(c, VR_EINVAL, "unknown kernel");
             c->kernel = (int)value;
             return VR_OK;
         default: return fail(c, VR_EINVAL, "unknown option");
@@ -686,6 +774,7 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     int32_t tiles_x, tiles_y, T;
     int64_t n_items;
     if (use_tma(c) && (rc = prepare_tma(c))) return rc;
+    if (use_tex(c) && (rc = prepare_tex(c))) return rc;
     rc = plan_frame(c, s, tiles_x, tiles_y, T, n_items);
     if (rc) return rc;
     s.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -751,6 +840,7 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     p.n_items = (int32_t)n_items;
     p.tmaps = c->d_tmaps;
     p.tmaps_per_brick = c->tmaps_per_brick;
+    for (int a = 0; a < 3; ++a) p.tex[a] = c->tex_obj[a];
     p.tile_start = s.d_tile_start;
     p.frags = s.d_frags;
     p.out = out_on_device ? reinterpret_cast<float4*>(out_rgba) : s.d_img;
@@ -766,6 +856,8 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
     if (use_tma(c)) {
         VR_CUDA(c, vr::launch_march_tma(p, st));
+    } else if (use_tex(c)) {
+        VR_CUDA(c, vr::launch_march_tex(p, st));
     } else {
         VR_CUDA(c, vr::launch_march(p, st));
     }

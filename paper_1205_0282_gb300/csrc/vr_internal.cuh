@@ -80,6 +80,7 @@ struct FrameParams {
     int32_t n_items;
     const CUtensorMap* tmaps;   // TMA march: tensor maps in device memory
     int32_t tmaps_per_brick;    // 1: one set per brick (brick-local coordinates)
+    cudaTextureObject_t tex[3]; // texture march: layered copies with layers along x, y, z
     const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
     float4* frags;
     float4* out;
@@ -91,6 +92,9 @@ cudaError_t launch_brick_minmax(const float* cube, int64_t pitch, const int32_t 
                                 const int32_t nb[3], float2* out, cudaStream_t s);
 cudaError_t launch_march(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tma(const FrameParams& p, cudaStream_t s);
+cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s);
+cudaError_t fill_tex_layers(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch, int S,
+                            cudaSurfaceObject_t surf, cudaStream_t s);
 cudaError_t make_tma_maps(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
                           const float* b, int64_t b_pitch, const int32_t B[3], const int32_t nb[3],
                           std::vector<CUtensorMap>& out, int& per_brick);

@@ -28,6 +28,8 @@ VR_OPT_MODE = 3
 VR_OPT_KERNEL = 4
 VR_KERNEL_TMA = 0
 VR_KERNEL_DIRECT = 1
+VR_KERNEL_TEX = 2
+VR_KERNEL_AUTO = 3
 
 _ERR_NAMES = {VR_EINVAL: "VR_EINVAL", VR_ENOMEM: "VR_ENOMEM", VR_ECUDA: "VR_ECUDA",
               VR_ESTATE: "VR_ESTATE", VR_ETIMEOUT: "VR_ETIMEOUT"}

@@ -61,7 +61,6 @@ def test_tiny_views_bricked(vr, torch, tiny, view):
     ref, amb, ns = oracle_render(cube, tf, cam, (32, 32, 32))
     assert_parity(img, ref, amb)
     assert st["samples"] >= ns.sum() > 0
-    assert st["chunks_staged"] > 0
 
 
 @pytest.mark.parametrize("view", range(4))
@@ -244,10 +243,12 @@ def test_direct_gather_kernel(vr, torch, tiny, view):
     assert st["chunks_staged"] == 0
 
 
-def test_tma_kernel_stages_chunks(vr, torch, tiny):
+@pytest.mark.parametrize("view", range(4))
+def test_tma_kernel_stages_chunks(vr, torch, tiny, view):
+    """The TMA-staged march (16x16 items, boxes copied into shared memory)."""
     cube, tf = tiny
-    cam = synth.tiny_views()[1]
-    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32))
+    cam = synth.tiny_views()[view]
+    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_KERNEL: vr.VR_KERNEL_TMA})
     assert st["chunks_staged"] > 0
     ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32))
     assert_parity(img, ref, amb)
@@ -258,7 +259,7 @@ def test_tma_fallback_chunks(vr, torch, tiny):
     the staged box; those chunks read through L1 and the image still matches."""
     cube, tf = tiny
     cam = synth.tiny_views(width=20, height=18)[0]
-    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32))
+    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_KERNEL: vr.VR_KERNEL_TMA})
     assert st["chunks_direct"] > 0
     ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32))
     assert_parity(img, ref, amb)
@@ -270,7 +271,29 @@ def test_kernels_agree(vr, torch):
     for az in (0.3, 1.6, 3.9):
         cam = synth.pose((128, 96, 160), az, 0.26, 160, 120)
         a, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32))
-        b, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_KERNEL: vr.VR_KERNEL_DIRECT})
-        assert np.abs(a - b).max() < 1e-4
+        for k in (vr.VR_KERNEL_DIRECT, vr.VR_KERNEL_TMA, vr.VR_KERNEL_TEX):
+            b, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_KERNEL: k})
+            assert np.abs(a - b).max() < 1e-4
         ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32))
         assert_parity(a, ref, amb)
+
+
+@pytest.mark.parametrize("view", [0, 1, 2, 3])
+def test_texture_gather_kernel(vr, torch, tiny, view):
+    """The texture-gather march (unfiltered tld4 gathers from layered textures,
+    FP32 trilinear weights) against the oracle."""
+    cube, tf = tiny
+    cam = synth.tiny_views()[view]
+    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_KERNEL: vr.VR_KERNEL_TEX})
+    ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32))
+    assert_parity(img, ref, amb)
+
+
+@pytest.mark.parametrize("shape,brick,camk,step,tau", RAGGED[:2])
+def test_texture_gather_ragged(vr, torch, shape, brick, camk, step, tau):
+    cube = synth.hi_cube(seed=11, shape_xyz=shape, n_line=12, n_cont=2)
+    tf = synth.tf_tiny()
+    cam = synth.pose(shape, camk["az"], camk["el"], camk["W"], camk["H"], step=step, term_alpha=tau)
+    img, _ = gpu_render(vr, torch, cube, tf, cam, brick, {vr.VR_OPT_KERNEL: vr.VR_KERNEL_TEX})
+    ref, amb, _ = oracle_render(cube, tf, cam, brick)
+    assert_parity(img, ref, amb)
