@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--width", type=int, default=0, help="override the image width")
     ap.add_argument("--height", type=int, default=0, help="override the image height")
     ap.add_argument("--kernel", choices=["auto", "tma", "direct", "tex"], default="auto")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -165,9 +165,15 @@ def peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("vr_kernels.cu", "vr_march_tma.cu", "vr_march_tex.cu", "vr_device.cuh",
+                  "vr_internal.cuh", "df.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the device sources; a recorded ncu traffic figure is reported only
+    while this hash matches the one stored with it."""
     h = hashlib.sha256()
-    for f in ("vr_kernels.cu", "vr_internal.cuh", "df.cuh"):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1205_0282_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -216,6 +222,27 @@ def cpu_cores():
     return int(n) if n else (os.cpu_count() or 1)
 
 
+# ------------------------------------------------------------------ ranks
+
+def my_share(items, rank: int, world: int):
+    """The orbit poses this rank renders: every world-th pose from its rank
+    (replicas: each rank renders whole frames of its own, no data exchange)."""
+    return list(items[rank::world]) if world > 1 else list(items)
+
+
+def job_totals(dist, elapsed: float, counts, device="cpu"):
+    """Whole-job numbers over ranks: the slowest rank's time (max) and the summed
+    counts (samples, frames, launches ...).  dist is torch.distributed or None."""
+    if dist is None:
+        return elapsed, [int(c) for c in counts]
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), [int(round(x)) for x in c.tolist()]
+
+
 # ------------------------------------------------------------------ main
 
 def run_reference(args):
@@ -262,7 +289,7 @@ def run_ours(args):
 
     spec, tf, poses, desc = workload(args)
     cube = make_cube(spec)
-    my_poses = poses[rank::world] if world > 1 else poses
+    my_poses = my_share(poses, rank, world)
     W, H = spec["width"], spec["height"]
 
     r = VolumeRenderer(local)
@@ -305,17 +332,8 @@ def run_ours(args):
     st = r.stats()
     elapsed_ms = evs[0].elapsed_time(evs[-1])
     frame_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    samples = st["samples"]
-    frames = st["frames"]
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        s = torch.tensor([samples, frames, st["launches"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        samples, frames, launches = int(s[0].item()), int(s[1].item()), int(s[2].item())
-    else:
-        launches = st["launches"]
+    elapsed_ms, (samples, frames, launches) = job_totals(
+        dist, elapsed_ms, [st["samples"], st["frames"], st["launches"]], "cuda")
 
     # end to end: host output buffer, copies inside the timed region
     e2e = None
@@ -329,16 +347,7 @@ def run_ours(args):
             r.render(host)
         t1 = time.perf_counter()
         se = r.stats()
-        e2e_t = t1 - t0
-        if dist:
-            t = torch.tensor([e2e_t], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_t = float(t.item())
-            s = torch.tensor([se["samples"]], dtype=torch.float64, device="cuda")
-            dist.all_reduce(s, op=dist.ReduceOp.SUM)
-            e2e_samples = float(s.item())
-        else:
-            e2e_samples = se["samples"]
+        e2e_t, (e2e_samples,) = job_totals(dist, t1 - t0, [se["samples"]], "cuda")
         e2e = {"value": e2e_samples / e2e_t, "unit": UNIT,
                "h2d_bytes_per_step": se["h2d_bytes"] // max(se["frames"], 1),
                "d2h_bytes_per_step": se["d2h_bytes"] // max(se["frames"], 1),
