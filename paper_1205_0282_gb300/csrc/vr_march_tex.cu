@@ -136,10 +136,13 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
     if ((threadIdx.x & 31) == 0 && t) atomicAdd(&p.stats->samples, t);
 }
 
+// The transfer function lives in dynamic shared memory sized to the control points,
+// so that almost all of the SM's L1/shared array stays texture cache.
 template <bool UNIFORM>
 __global__ void __launch_bounds__(kTilePixels, 20) march_tex_kernel(const FrameParams p) {
-    __shared__ float4 s_rgba[kMaxTfPoints + 1];
-    __shared__ float s_v[kMaxTfPoints];
+    extern __shared__ float4 s_dyn[];
+    float4* s_rgba = s_dyn;
+    float* s_v = reinterpret_cast<float*>(s_dyn + p.tf_n + 1);
     for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
         s_rgba[k] = p.tf_rgba[k];
         if (k < p.tf_n) s_v[k] = p.tf_v[k];
@@ -172,8 +175,20 @@ __global__ void fill_layers_kernel(const float* __restrict__ a, int64_t nx, int6
 
 cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
-    if (p.tf_uniform) texm::march_tex_kernel<true><<<p.n_items, kTilePixels, 0, s>>>(p);
-    else texm::march_tex_kernel<false><<<p.n_items, kTilePixels, 0, s>>>(p);
+    const size_t smem = (size_t)(p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
+    // shared-memory carveout just large enough for 20 resident CTAs (each also
+    // reserves 1 KB); the rest of the SM's 256 KB array is L1/texture cache
+    const int pct = (int)((20 * (smem + 1024) * 100 + 233471) / 233472) + 2;
+    auto go = [&](auto kern) {
+        static int carveout = -1;
+        if (carveout != pct) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            carveout = pct;
+        }
+        kern<<<p.n_items, kTilePixels, smem, s>>>(p);
+    };
+    if (p.tf_uniform) go(texm::march_tex_kernel<true>);
+    else go(texm::march_tex_kernel<false>);
     return cudaGetLastError();
 }
 
