@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--width", type=int, default=0, help="override the image width")
     ap.add_argument("--height", type=int, default=0, help="override the image height")
     ap.add_argument("--kernel", choices=["auto", "tma", "direct", "tex"], default="auto")
+    ap.add_argument("--precision", choices=["f32", "f16", "f8"], default="f32",
+                    help="storage of the texture march's cube copies (FP32, FP16, FP8 E4M3 per-brick scale)")
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -193,28 +195,44 @@ def recorded_traffic(kernel, workload_name):
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_rate(cube, tf, poses, brick, seconds, crop=64):
+def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False):
     """Samples/s of the FP64 oracle on centre crops of successive poses, for
-    about `seconds` of wall time (at least one crop)."""
+    about `seconds` of wall time (at least one crop).  With keep, also returns
+    the crops as (camera, pixel indices, RGBA) for the image-quality check."""
     import oracle
     total = 0
     t0 = time.perf_counter()
     k = 0
-    crops = 0
+    crops = []
     while True:
         cam = poses[k % len(poses)]
         W, H = cam["width"], cam["height"]
         x0, y0 = W // 2 - crop // 2, H // 2 - crop // 2
         jj, ii = np.meshgrid(np.arange(y0, y0 + crop), np.arange(x0, x0 + crop), indexing="ij")
         pix = (jj * W + ii).reshape(-1)
-        _, _, ns = oracle.render(cube, tf, cam, brick=brick, pixels=pix)
+        ref, _, ns = oracle.render(cube, tf, cam, brick=brick, pixels=pix)
         total += int(ns.sum())
-        crops += 1
+        crops.append((cam, pix, ref) if keep else None)
         k += 7
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return total / dt, dt, crops
+    return (total / dt, dt, len(crops), crops) if keep else (total / dt, dt, len(crops))
+
+
+def image_quality(render_pose, crops):
+    """Per-pixel error of the GPU image against the FP64 oracle's crops (oracle
+    on the FP32 cube).  PSNR = 10 log10(1 / MSE) over the RGBA channels, whose
+    values lie in [0, 1]."""
+    errs = []
+    for cam, pix, ref in crops:
+        errs.append(render_pose(cam, pix).astype(np.float64) - ref.reshape(-1, 4))
+    e = np.concatenate(errs)
+    mse = float(np.mean(e * e))
+    return {"against": "FP64 oracle on the FP32 cube", "pixels": int(e.shape[0]),
+            "sub_views": f"the CPU-baseline crops: {len(crops)} poses",
+            "max_abs": float(np.abs(e).max()), "rms": mse ** 0.5,
+            "psnr_db": (10 * np.log10(1.0 / mse)) if mse > 0 else None}
 
 
 def cpu_cores():
@@ -302,6 +320,8 @@ def run_ours(args):
     from paper_1205_0282_gb300 import vr as vrmod
     r.set_option(vrmod.VR_OPT_KERNEL, {"auto": vrmod.VR_KERNEL_AUTO, "tma": vrmod.VR_KERNEL_TMA,
                                        "direct": vrmod.VR_KERNEL_DIRECT, "tex": vrmod.VR_KERNEL_TEX}[args.kernel])
+    r.set_option(vrmod.VR_OPT_PRECISION, {"f32": vrmod.VR_PRECISION_F32, "f16": vrmod.VR_PRECISION_F16,
+                                          "f8": vrmod.VR_PRECISION_F8}[args.precision])
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -360,6 +380,12 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
+    def render_pose(cam, pix):
+        """RGBA of pixels pix (flat indices) of the frame at pose cam."""
+        r.set_camera(cam)
+        r.render(out, stream)
+        return out.view(-1, 4)[torch.from_numpy(pix).cuda()].cpu().numpy()
+
     peak, peak_kind = peaks()
     avg_march_ms = st["march_ms"] / max(st["frames"], 1)
     bytes_per_launch = st["touched_bytes"] / max(st["frames"], 1)
@@ -369,21 +395,24 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": kname,
                 "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(kname, spec["name"]),
+                "traffic": recorded_traffic(kname, spec["name"] + ("" if args.precision == "f32"
+                                                                   else "_" + args.precision)),
                 "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_ms": avg_march_ms,
                 "frame_bytes_per_step": bytes_per_launch + W * H * 16,
                 "frame_frac": (bytes_per_launch + W * H * 16) / (elapsed_ms / args.steps * 1e-3) / 1e9 / peak}
 
-    cpu = None
+    cpu = quality = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        rate, secs, crops = oracle_rate(cube, tf, poses, spec["brick"], args.cpu_seconds)
+        rate, secs, n_crops, crops = oracle_rate(cube, tf, poses, spec["brick"], args.cpu_seconds, keep=True)
         cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"{crops} centre crops of 64x64 pixels on successive orbit poses, "
+               "sample": f"{n_crops} centre crops of 64x64 pixels on successive orbit poses, "
                          f"{secs:.1f} s of FP64 CPU work"}
+        # the same crops judge the GPU image (per-pixel error, PSNR)
+        quality = image_quality(render_pose, crops)
 
     value = samples / (elapsed_ms * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -393,6 +422,8 @@ def run_ours(args):
             "config": {"workload": desc, "cube_xyz": list(spec["shape_xyz"]),
                        "brick": list(spec["brick"]), "image": [W, H], "step": 0.5,
                        "tf": args.tf.upper(), "term_alpha": 0.99,
+                       "storage": {"f32": "FP32", "f16": "FP16",
+                                   "f8": "FP8 E4M3, per-brick absmax/448 scale"}[args.precision],
                        "l2": ("inputs larger than L2, no flush" if spec["name"] != "tiny"
                               else "tiny cube fits in L2 (not a bench line)"),
                        "parallelism": f"replicas x{world}: orbit poses split across ranks"},
@@ -405,6 +436,7 @@ def run_ours(args):
             "plan_ms_per_frame": st["plan_ms"] / max(st["frames"], 1),
             "composite_ms_per_frame": st["composite_ms"] / max(st["frames"], 1),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "quality": quality,
             "march_kernel": args.kernel,
             "chunks_staged_per_frame": st["chunks_staged"] / max(st["frames"], 1),
             "chunks_direct_per_frame": st["chunks_direct"] / max(st["frames"], 1),

@@ -109,6 +109,28 @@ typedef struct {
 #define VR_KERNEL_DIRECT 1
 #define VR_KERNEL_TEX 2
 #define VR_KERNEL_AUTO 3
+#define VR_OPT_PRECISION 5   /* storage of the texture march's copies of the cube (no
+                                counterpart in the paper, which samples FP32 sub-cubes):
+                                VR_PRECISION_F32 (default): the values as loaded;
+                                VR_PRECISION_F16: each value rounded to the nearest FP16
+                                (VR_EINVAL at render time if |value| > 65504);
+                                VR_PRECISION_F8: each value v of a voxel owned by brick b
+                                (voxel g lies in brick min(g / B, nb - 1) along each axis)
+                                stored as the E4M3 code nearest to v / s_b, saturated at
+                                448, with s_b = max|v| over the voxels b owns / 448 (1 for
+                                an all-zero brick); it reads back as code * s_b.
+                                Interpolation, transfer function and compositing stay in
+                                FP32; the image equals the FP32 render of the cube of
+                                read-back values, and empty-space skipping uses the
+                                read-back values' per-brick range.  F16 and F8 need the
+                                texture march (VR_OPT_MODE 0 and VR_KERNEL_TEX, or
+                                VR_KERNEL_AUTO on a cube within the texture limits):
+                                vr_render returns VR_EINVAL otherwise.  Changing it waits
+                                for frames in flight and rebuilds the copies on the next
+                                render (F8 also after vr_brick). */
+#define VR_PRECISION_F32 0
+#define VR_PRECISION_F16 1
+#define VR_PRECISION_F8 2
 
 /*
  * Create a context on CUDA device `device`.  *out receives the context.

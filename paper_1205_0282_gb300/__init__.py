@@ -6,7 +6,8 @@ binding's names are loaded on first use, so ``paper_1205_0282_gb300.build`` can
 be imported (to compile the library) before the library exists.
 """
 _EXPORTED = ("VolumeRenderer", "VRError", "VR_OPT_MODE", "VR_OPT_RECT_CULL", "VR_OPT_SKIP_EMPTY",
-             "VR_OPT_KERNEL", "VR_KERNEL_TMA", "VR_KERNEL_DIRECT", "VR_KERNEL_TEX", "VR_KERNEL_AUTO", "vr_render_noalloc",
+             "VR_OPT_KERNEL", "VR_KERNEL_TMA", "VR_KERNEL_DIRECT", "VR_KERNEL_TEX", "VR_KERNEL_AUTO",
+             "VR_OPT_PRECISION", "VR_PRECISION_F32", "VR_PRECISION_F16", "VR_PRECISION_F8", "vr_render_noalloc",
              "vr_brick", "vr_create", "vr_destroy", "vr_get_brick_minmax", "vr_get_stats",
              "vr_last_error", "vr_load_cube", "vr_plan_brick_rects", "vr_render",
              "vr_reset_stats", "vr_set_camera", "vr_set_option", "vr_set_transfer_function")

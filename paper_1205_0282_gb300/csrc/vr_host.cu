@@ -182,6 +182,9 @@ struct vr_ctx {
     cudaArray_t tex_arr[3] = {nullptr, nullptr, nullptr};  // texture march: layered copies
     cudaTextureObject_t tex_obj[3] = {0, 0, 0};
     bool tex_ready = false;
+    int precision = VR_PRECISION_F32;  // storage of the layered copies
+    float* d_brick_scale = nullptr;    // FP8 storage: per-brick scale
+    std::vector<float2> h_minmax_q;    // FP16/FP8 storage: per-brick [min, max] of the stored values
     int tmaps_per_brick = 0;
     bool tma_ready = false;
 
@@ -335,6 +338,10 @@ bool use_tma(vr_ctx* c) {
     return c->mode == 0 && (c->kernel == VR_KERNEL_TMA || (c->kernel == VR_KERNEL_AUTO && !tex_fits(c)));
 }
 
+int64_t precision_bytes(int precision) {
+    return precision == VR_PRECISION_F16 ? 2 : (precision == VR_PRECISION_F8 ? 1 : 4);
+}
+
 void free_tex(vr_ctx* c) {
     for (int a = 0; a < 3; ++a) {
         if (c->tex_obj[a]) cudaDestroyTextureObject(c->tex_obj[a]);
@@ -342,6 +349,8 @@ void free_tex(vr_ctx* c) {
         c->tex_obj[a] = 0;
         c->tex_arr[a] = nullptr;
     }
+    cudaFree(c->d_brick_scale);
+    c->d_brick_scale = nullptr;
     c->tex_ready = false;
 }
 
@@ -384,7 +393,7 @@ int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int32_t& 
     for (int64_t id = 0; id < c->n_bricks; ++id) {
         int64_t idx[3] = {id % c->nb[0], (id / c->nb[0]) % c->nb[1], id / ((int64_t)c->nb[0] * c->nb[1])};
         if (c->skip_empty && c->mode == 0) {
-            const float2 mm = c->h_minmax[id];
+            const float2 mm = (use_tex(c) && c->precision != VR_PRECISION_F32) ? c->h_minmax_q[id] : c->h_minmax[id];
             if (tf_alpha_max(c->tf, mm.x, mm.y) == 0.0) {
                 ++s.bricks_skipped;
                 continue;
@@ -409,7 +418,7 @@ int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int32_t& 
         c->plan_bricks.push_back(pb);
         int64_t vox = 1;
         for (int a = 0; a < 3; ++a) vox *= std::min<int64_t>(c->B[a], c->n[a] - idx[a] * c->B[a]);
-        s.touched_bytes += vox * (int64_t)sizeof(float);
+        s.touched_bytes += vox * (use_tex(c) ? precision_bytes(c->precision) : (int64_t)sizeof(float));
     }
     std::stable_sort(c->plan_bricks.begin(), c->plan_bricks.end(),
                      [](const vr_ctx::PB& x, const vr_ctx::PB& y) { return x.key < y.key; });
@@ -569,6 +578,7 @@ int vr_brick(vr_ctx* c, int32_t bx, int32_t by, int32_t bz) {
     if (total > (1 << 26)) return fail(c, VR_EINVAL, "too many bricks");
     c->n_bricks = total;
     c->tma_ready = false;  // tensor maps are per brick
+    if (c->precision == VR_PRECISION_F8) free_tex(c);  // so are the FP8 scales
     cudaFree(c->d_minmax);
     c->d_minmax = nullptr;
     if (cudaMalloc((void**)&c->d_minmax, total * sizeof(float2)) != cudaSuccess) {
@@ -632,10 +642,25 @@ int prepare_tex(vr_ctx* c) {
         if (n[U] > maxw || n[V] > maxh || n[S] > maxl)
             return fail(c, VR_EINVAL, "cube exceeds the layered-texture limits of this device");
     }
+    if (c->precision == VR_PRECISION_F16)
+        for (const float2& mm : c->h_minmax)
+            if (mm.x < -65504.0f || mm.y > 65504.0f)
+                return fail(c, VR_EINVAL, "FP16 storage: the cube has values beyond the FP16 range");
+    const int prec = c->precision == VR_PRECISION_F8 ? vr::kPrecF8
+                     : c->precision == VR_PRECISION_F16 ? vr::kPrecF16 : vr::kPrecF32;
     free_tex(c);
+    if (c->precision == VR_PRECISION_F8) {
+        if (cudaMalloc((void**)&c->d_brick_scale, c->n_bricks * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, VR_ENOMEM, "cannot allocate the brick scales");
+        }
+        VR_CUDA(c, vr::launch_brick_scale(c->d_cube, n[0], n[1], n[2], c->nx_pad, c->B, c->nb, c->d_brick_scale, 0));
+    }
     for (int S = 0; S < 3; ++S) {
         const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
-        cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
+        cudaChannelFormatDesc ch = c->precision == VR_PRECISION_F16 ? cudaCreateChannelDescHalf()
+                                   : c->precision == VR_PRECISION_F8 ? cudaCreateChannelDesc<unsigned char>()
+                                                                     : cudaCreateChannelDesc<float>();
         if (cudaMalloc3DArray(&c->tex_arr[S], &ch, make_cudaExtent((size_t)n[U], (size_t)n[V], (size_t)n[S]),
                               cudaArrayLayered | cudaArraySurfaceLoadStore) != cudaSuccess) {
             cudaGetLastError();
@@ -648,7 +673,8 @@ int prepare_tex(vr_ctx* c) {
         rd.res.array.array = c->tex_arr[S];
         cudaSurfaceObject_t surf = 0;
         VR_CUDA(c, cudaCreateSurfaceObject(&surf, &rd));
-        cudaError_t e = vr::fill_tex_layers(c->d_cube, n[0], n[1], n[2], c->nx_pad, S, surf, 0);
+        cudaError_t e = vr::fill_tex_layers(c->d_cube, n[0], n[1], n[2], c->nx_pad, S, prec, surf,
+                                            c->d_brick_scale, c->B, c->nb, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaDestroySurfaceObject(surf);
         if (e != cudaSuccess) return cuda_fail(c, e, "fill_tex_layers");
@@ -659,6 +685,22 @@ int prepare_tex(vr_ctx* c) {
         td.readMode = cudaReadModeElementType;
         td.normalizedCoords = 0;
         VR_CUDA(c, cudaCreateTextureObject(&c->tex_obj[S], &rd, &td, nullptr));
+    }
+    if (c->precision != VR_PRECISION_F32) {
+        float2* d_mm = nullptr;
+        if (cudaMalloc((void**)&d_mm, c->n_bricks * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            free_tex(c);
+            return fail(c, VR_ENOMEM, "cannot allocate the stored-value min/max");
+        }
+        const int32_t n32[3] = {(int32_t)n[0], (int32_t)n[1], (int32_t)n[2]};
+        cudaError_t e = vr::launch_stored_minmax(c->d_cube, c->nx_pad, n32, c->B, c->nb, prec, c->d_brick_scale,
+                                                 d_mm, 0);
+        c->h_minmax_q.resize(c->n_bricks);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->h_minmax_q.data(), d_mm, c->n_bricks * sizeof(float2), cudaMemcpyDeviceToHost);
+        cudaFree(d_mm);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stored min/max");
     }
     c->tex_ready = true;
     return VR_OK;
@@ -747,6 +789,16 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
                 return fail(c, VR_EINVAL, "unknown kernel");
             c->kernel = (int)value;
             return VR_OK;
+        case VR_OPT_PRECISION:
+            if (value != VR_PRECISION_F32 && value != VR_PRECISION_F16 && value != VR_PRECISION_F8)
+                return fail(c, VR_EINVAL, "unknown precision");
+            if ((int)value != c->precision) {
+                int rc = retire_all(c);  // frames in flight may read the old textures
+                if (rc) return rc;
+                free_tex(c);
+                c->precision = (int)value;
+            }
+            return VR_OK;
         default: return fail(c, VR_EINVAL, "unknown option");
     }
 }
@@ -773,6 +825,9 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     auto t0 = std::chrono::steady_clock::now();
     int32_t tiles_x, tiles_y, T;
     int64_t n_items;
+    if (c->precision != VR_PRECISION_F32 && !use_tex(c))
+        return fail(c, VR_EINVAL, "FP16/FP8 storage needs the texture march (emission-absorption mode, "
+                                  "VR_KERNEL_TEX or VR_KERNEL_AUTO on a cube within the texture limits)");
     if (use_tma(c) && (rc = prepare_tma(c))) return rc;
     if (use_tex(c) && (rc = prepare_tex(c))) return rc;
     rc = plan_frame(c, s, tiles_x, tiles_y, T, n_items);
@@ -841,6 +896,9 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     p.tmaps = c->d_tmaps;
     p.tmaps_per_brick = c->tmaps_per_brick;
     for (int a = 0; a < 3; ++a) p.tex[a] = c->tex_obj[a];
+    p.precision = c->precision == VR_PRECISION_F8 ? vr::kPrecF8
+                  : c->precision == VR_PRECISION_F16 ? vr::kPrecF16 : vr::kPrecF32;
+    p.brick_scale = c->d_brick_scale;
     p.tile_start = s.d_tile_start;
     p.frags = s.d_frags;
     p.out = out_on_device ? reinterpret_cast<float4*>(out_rgba) : s.d_img;

@@ -13,6 +13,7 @@ constexpr int kTile = 8;                    // tile edge of the direct-gather ma
 constexpr int kTilePixels = kTile * kTile;  // 64 rays per item, one per thread
 constexpr int kTileTma = 16;                // tile edge of the TMA-staged march (16x16 items)
 constexpr int kTmaClasses = 8;              // staged-box classes of the TMA march
+constexpr int kPrecF32 = 0, kPrecF16 = 1, kPrecF8 = 2;  // texture storage precisions
 constexpr int kMaxTfPoints = 256;
 constexpr int kAlphaPolyTerms = 11;         // coefficients of the opacity-correction polynomial
 constexpr int kAlphaSmallTerms = 6;         // ... and of its short form for small opacities
@@ -81,6 +82,8 @@ struct FrameParams {
     const CUtensorMap* tmaps;   // TMA march: tensor maps in device memory
     int32_t tmaps_per_brick;    // 1: one set per brick (brick-local coordinates)
     cudaTextureObject_t tex[3]; // texture march: layered copies with layers along x, y, z
+    int32_t precision;          // texture storage: kPrecF32, kPrecF16, kPrecF8
+    const float* brick_scale;   // FP8: per-brick scale (value = code * scale)
     const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
     float4* frags;
     float4* out;
@@ -94,7 +97,13 @@ cudaError_t launch_march(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tma(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s);
 cudaError_t fill_tex_layers(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch, int S,
-                            cudaSurfaceObject_t surf, cudaStream_t s);
+                            int precision, cudaSurfaceObject_t surf, const float* scale, const int32_t B[3],
+                            const int32_t nb[3], cudaStream_t s);
+cudaError_t launch_brick_scale(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
+                               const int32_t B[3], const int32_t nb[3], float* scale, cudaStream_t s);
+cudaError_t launch_stored_minmax(const float* a, int64_t pitch, const int32_t n[3], const int32_t B[3],
+                                 const int32_t nb[3], int precision, const float* scale, float2* out,
+                                 cudaStream_t s);
 cudaError_t make_tma_maps(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
                           const float* b, int64_t b_pitch, const int32_t B[3], const int32_t nb[3],
                           std::vector<CUtensorMap>& out, int& per_brick);

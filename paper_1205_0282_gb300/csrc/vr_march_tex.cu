@@ -11,6 +11,7 @@
 // rays of a warp sample one or two layers at a time and the gathers stay local in
 // the texture cache.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include <cfloat>
 #include <cstdint>
@@ -20,6 +21,10 @@
 namespace vr {
 
 namespace texm {
+
+// resident CTAs per SM the kernels are compiled for: 20 (48 registers a thread) for
+// FP32/FP16 storage; FP8 decoding needs a few more registers (16 CTAs, 64 registers)
+constexpr int tex_blocks_per_sm(int prec) { return prec == kPrecF8 ? 16 : 20; }
 
 // Layered texture of the sweep axis S: layer index = coordinate along S, texel
 // (x, y) = coordinates along (U, V) with U < V the two other axes.
@@ -45,7 +50,38 @@ __device__ __forceinline__ void gather4(cudaTextureObject_t t, int layer, float 
     c00 = r3;
 }
 
-template <int S, bool UNIFORM>
+// FP8 E4M3 storage: the texture returns the raw codes; two codes at a time are
+// widened by the hardware conversion e4m3x2 -> f16x2 and then to FP32.
+__device__ __forceinline__ void gather4_codes(cudaTextureObject_t t, int layer, float x, float y,
+                                              unsigned& c00, unsigned& c10, unsigned& c01, unsigned& c11) {
+    unsigned r0, r1, r2, r3;
+    asm("tld4.r.a2d.v4.u32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %8}];"
+        : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+        : "l"(t), "r"(layer), "f"(x), "f"(y), "f"(0.0f));
+    c01 = r0;
+    c11 = r1;
+    c10 = r2;
+    c00 = r3;
+}
+
+// (lo, hi) E4M3 codes -> their values (the code in the low byte of the packed pair
+// becomes the low half of the f16x2 result)
+__device__ __forceinline__ float2 e4m3_pair(unsigned lo, unsigned hi) {
+    const unsigned short packed = (unsigned short)((lo & 0xffu) | ((hi & 0xffu) << 8));
+    unsigned h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(packed));
+    const __half2 hh = *reinterpret_cast<const __half2*>(&h2);
+    return __half22float2(hh);
+}
+
+// E4M3 code of x (saturating to the largest finite value 448)
+__device__ __forceinline__ unsigned e4m3_code(float x) {
+    unsigned short d;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(0.0f), "f"(x));
+    return d & 0xffu;
+}
+
+template <int S, bool UNIFORM, int PREC>
 __device__ __forceinline__ void march_item(const FrameParams& p, const Item& item, const float4* s_rgba,
                                            const float* s_v) {
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
@@ -92,6 +128,22 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
         float c[8];  // (u, v, s) corners: c[0..3] in plane ps, c[4..7] in plane ps + 1
         float fu, fv, fs;
     };
+    // FP8: corners read back as code * scale of the brick that owns them; the +1
+    // corners on the brick's far faces belong to the next brick along that axis, if
+    // there is one (a rare case, whose scales are read when needed)
+    float sc0 = 1.0f;
+    bool next_u = false, next_v = false, next_s = false;
+    int step_u = 0, step_v = 0, step_s = 0;
+    if (PREC == kPrecF8) {
+        sc0 = p.brick_scale[item.brick];
+        const int step[3] = {1, p.nb[0], p.nb[0] * p.nb[1]};
+        next_u = bidx[U] + 1 < p.nb[U];
+        next_v = bidx[V] + 1 < p.nb[V];
+        next_s = bidx[S] + 1 < p.nb[S];
+        step_u = step[U];
+        step_v = step[V];
+        step_s = step[S];
+    }
     auto fetch = [&](float f, Corners& s) {
         const float qS = fmaf(f, dq[S], qs[S]);
         const float qU = fmaf(f, dq[U], qs[U]);
@@ -105,8 +157,35 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
         s.fu = qU - (float)iu;
         s.fv = qV - (float)iv;
         const float x = ou + (float)iu, y = ov + (float)iv;
-        gather4(tex, O[S] + ps, x, y, s.c[0], s.c[1], s.c[2], s.c[3]);
-        gather4(tex, O[S] + ps + 1, x, y, s.c[4], s.c[5], s.c[6], s.c[7]);
+        if (PREC != kPrecF8) {
+            // FP32 and FP16 textures both return FP32 values
+            gather4(tex, O[S] + ps, x, y, s.c[0], s.c[1], s.c[2], s.c[3]);
+            gather4(tex, O[S] + ps + 1, x, y, s.c[4], s.c[5], s.c[6], s.c[7]);
+        } else {
+            unsigned k[8];
+            gather4_codes(tex, O[S] + ps, x, y, k[0], k[1], k[2], k[3]);
+            gather4_codes(tex, O[S] + ps + 1, x, y, k[4], k[5], k[6], k[7]);
+#pragma unroll
+            for (int c = 0; c < 8; c += 2) {
+                const float2 v = e4m3_pair(k[c], k[c + 1]);
+                s.c[c] = v.x;
+                s.c[c + 1] = v.y;
+            }
+            const bool hu = next_u && iu + 1 == p.B[U];
+            const bool hv = next_v && iv + 1 == p.B[V];
+            const bool hs = next_s && ps + 1 == p.B[S];
+            if (hu || hv || hs) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int off = ((c & 1) && hu ? step_u : 0) + ((c & 2) && hv ? step_v : 0) +
+                                    ((c & 4) && hs ? step_s : 0);
+                    s.c[c] *= off ? __ldg(p.brick_scale + item.brick + off) : sc0;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) s.c[c] *= sc0;
+            }
+        }
     };
     Corners nxt;
     if (fk < fn) fetch(fk, nxt);
@@ -138,8 +217,8 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
 
 // The transfer function lives in dynamic shared memory sized to the control points,
 // so that almost all of the SM's L1/shared array stays texture cache.
-template <bool UNIFORM>
-__global__ void __launch_bounds__(kTilePixels, 20) march_tex_kernel(const FrameParams p) {
+template <bool UNIFORM, int PREC>
+__global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_kernel(const FrameParams p) {
     extern __shared__ float4 s_dyn[];
     float4* s_rgba = s_dyn;
     float* s_v = reinterpret_cast<float*>(s_dyn + p.tf_n + 1);
@@ -150,17 +229,20 @@ __global__ void __launch_bounds__(kTilePixels, 20) march_tex_kernel(const FrameP
     __syncthreads();
     const Item item = p.items[blockIdx.x];
     switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM>(p, item, s_rgba, s_v); break;
-        case 1: march_item<1, UNIFORM>(p, item, s_rgba, s_v); break;
-        default: march_item<2, UNIFORM>(p, item, s_rgba, s_v); break;
+        case 0: march_item<0, UNIFORM, PREC>(p, item, s_rgba, s_v); break;
+        case 1: march_item<1, UNIFORM, PREC>(p, item, s_rgba, s_v); break;
+        default: march_item<2, UNIFORM, PREC>(p, item, s_rgba, s_v); break;
     }
 }
 
 // Copy the stored cube a[z][y][x] (row pitch a_pitch floats) into the layered
-// array of sweep axis S through its surface: layer = coordinate along S.
-template <int S>
+// array of sweep axis S through its surface: layer = coordinate along S.  FP16
+// stores the nearest half; FP8 stores the E4M3 code of v / scale, the scale of the
+// brick that owns the voxel (voxel g belongs to brick min(g / B, nb - 1)).
+template <int S, int PREC>
 __global__ void fill_layers_kernel(const float* __restrict__ a, int64_t nx, int64_t ny, int64_t nz,
-                                   int64_t a_pitch, cudaSurfaceObject_t surf) {
+                                   int64_t a_pitch, cudaSurfaceObject_t surf, const float* __restrict__ scale,
+                                   int3 B, int3 nb) {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t y = blockIdx.y;
     const int64_t z = blockIdx.z;
@@ -168,7 +250,93 @@ __global__ void fill_layers_kernel(const float* __restrict__ a, int64_t nx, int6
     const float v = a[(z * ny + y) * a_pitch + x];
     const int64_t c[3] = {x, y, z};
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
-    surf2DLayeredwrite(v, surf, (int)(c[U] * sizeof(float)), (int)c[V], (int)c[S]);
+    const int cx = (int)(c[U] * (PREC == kPrecF32 ? 4 : (PREC == kPrecF16 ? 2 : 1)));
+    if (PREC == kPrecF32) {
+        surf2DLayeredwrite(v, surf, cx, (int)c[V], (int)c[S]);
+    } else if (PREC == kPrecF16) {
+        surf2DLayeredwrite(__half_as_ushort(__float2half_rn(v)), surf, cx, (int)c[V], (int)c[S]);
+    } else {
+        const int bx = min((int)(x / B.x), nb.x - 1), by = min((int)(y / B.y), nb.y - 1);
+        const int bz = min((int)(z / B.z), nb.z - 1);
+        const float sc = scale[bx + nb.x * (by + nb.y * bz)];
+        surf2DLayeredwrite((unsigned char)e4m3_code(v / sc), surf, cx, (int)c[V], (int)c[S]);
+    }
+}
+
+// Per-brick FP8 scale: the largest |value| over the voxels the brick owns, / 448
+// (the largest finite E4M3 value); 1 for an all-zero brick.
+__global__ void brick_scale_kernel(const float* __restrict__ a, int64_t nx, int64_t ny, int64_t nz,
+                                   int64_t a_pitch, int3 B, int3 nb, float* __restrict__ scale) {
+    const int id = blockIdx.x;
+    const int bx = id % nb.x, by = (id / nb.x) % nb.y, bz = id / (nb.x * nb.y);
+    const int x0 = bx * B.x, y0 = by * B.y, z0 = bz * B.z;
+    const int x1 = bx == nb.x - 1 ? (int)nx : x0 + B.x;
+    const int y1 = by == nb.y - 1 ? (int)ny : y0 + B.y;
+    const int z1 = bz == nb.z - 1 ? (int)nz : z0 + B.z;
+    const int rows_y = y1 - y0, rows = rows_y * (z1 - z0);
+    float m = 0.0f;
+    for (int r = threadIdx.x >> 5; r < rows; r += blockDim.x >> 5) {
+        const int64_t y = y0 + r % rows_y, z = z0 + r / rows_y;
+        const float* row = a + (z * ny + y) * a_pitch;
+        for (int x = x0 + (threadIdx.x & 31); x < x1; x += 32) m = fmaxf(m, fabsf(row[x]));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sm[w]);
+        scale[id] = m > 0.0f ? m / 448.0f : 1.0f;
+    }
+}
+
+// Per-brick [min, max] of the values the march reads back from reduced-precision
+// storage (the brick's voxels plus its +1 apron, each decoded with the scale of the
+// brick that owns it), so that empty-space skipping stays exact for that storage.
+template <int PREC>
+__global__ void stored_minmax_kernel(const float* __restrict__ a, int64_t pitch, int3 n, int3 B, int3 nb,
+                                     const float* __restrict__ scale, float2* __restrict__ out) {
+    const int id = blockIdx.x;
+    const int bx = id % nb.x, by = (id / nb.x) % nb.y, bz = id / (nb.x * nb.y);
+    const int x0 = bx * B.x, y0 = by * B.y, z0 = bz * B.z;
+    const int x1 = min(x0 + B.x, n.x - 1), y1 = min(y0 + B.y, n.y - 1), z1 = min(z0 + B.z, n.z - 1);
+    const int ny_rows = y1 - y0 + 1, rows = ny_rows * (z1 - z0 + 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    float mn = FLT_MAX, mx = -FLT_MAX;
+    for (int r = warp; r < rows; r += nwarps) {
+        const int z = z0 + r / ny_rows, y = y0 + r % ny_rows;
+        const float* row = a + ((int64_t)z * n.y + y) * pitch;
+        const int oyz = min(y / B.y, nb.y - 1) * nb.x + min(z / B.z, nb.z - 1) * nb.x * nb.y;
+        for (int x = x0 + lane; x <= x1; x += 32) {
+            const float v = row[x];
+            float q;
+            if (PREC == kPrecF16) {
+                q = __half2float(__float2half_rn(v));
+            } else {
+                const float sc = scale[oyz + min(x / B.x, nb.x - 1)];
+                q = e4m3_pair(e4m3_code(v / sc), 0).x * sc;
+            }
+            mn = fminf(mn, q);
+            mx = fmaxf(mx, q);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __shared__ float smn[32], smx[32];
+    if (lane == 0) {
+        smn[warp] = mn;
+        smx[warp] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nwarps; ++w) {
+            mn = fminf(mn, smn[w]);
+            mx = fmaxf(mx, smx[w]);
+        }
+        out[id] = make_float2(mn, mx);
+    }
 }
 
 }  // namespace texm
@@ -176,10 +344,12 @@ __global__ void fill_layers_kernel(const float* __restrict__ a, int64_t nx, int6
 cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
     const size_t smem = (size_t)(p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
-    // shared-memory carveout just large enough for 20 resident CTAs (each also
-    // reserves 1 KB); the rest of the SM's 256 KB array is L1/texture cache
-    const int pct = (int)((20 * (smem + 1024) * 100 + 233471) / 233472) + 2;
+    // shared-memory carveout just large enough for the resident CTAs the kernel is
+    // compiled for (each also reserves 1 KB); the rest of the SM's 256 KB array is
+    // L1/texture cache
     auto go = [&](auto kern) {
+        const int blocks = texm::tex_blocks_per_sm(p.precision == kPrecF8 ? kPrecF8 : kPrecF32);
+        const int pct = (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2;
         static int carveout = -1;
         if (carveout != pct) {
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
@@ -187,17 +357,56 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
         }
         kern<<<p.n_items, kTilePixels, smem, s>>>(p);
     };
-    if (p.tf_uniform) go(texm::march_tex_kernel<true>);
-    else go(texm::march_tex_kernel<false>);
+    if (p.precision == kPrecF8) {
+        if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF8>);
+        else go(texm::march_tex_kernel<false, kPrecF8>);
+    } else {  // FP32 and FP16 textures share the kernel
+        if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF32>);
+        else go(texm::march_tex_kernel<false, kPrecF32>);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t fill_tex_layers(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch, int S,
-                            cudaSurfaceObject_t surf, cudaStream_t s) {
+                            int precision, cudaSurfaceObject_t surf, const float* scale, const int32_t B[3],
+                            const int32_t nb[3], cudaStream_t s) {
     dim3 grid((unsigned)((nx + 255) / 256), (unsigned)ny, (unsigned)nz);
-    if (S == 0) texm::fill_layers_kernel<0><<<grid, 256, 0, s>>>(a, nx, ny, nz, a_pitch, surf);
-    else if (S == 1) texm::fill_layers_kernel<1><<<grid, 256, 0, s>>>(a, nx, ny, nz, a_pitch, surf);
-    else texm::fill_layers_kernel<2><<<grid, 256, 0, s>>>(a, nx, ny, nz, a_pitch, surf);
+    const int3 b3 = make_int3(B[0], B[1], B[2]), n3 = make_int3(nb[0], nb[1], nb[2]);
+    auto go = [&](auto kern) { kern<<<grid, 256, 0, s>>>(a, nx, ny, nz, a_pitch, surf, scale, b3, n3); };
+    if (precision == kPrecF16) {
+        if (S == 0) go(texm::fill_layers_kernel<0, kPrecF16>);
+        else if (S == 1) go(texm::fill_layers_kernel<1, kPrecF16>);
+        else go(texm::fill_layers_kernel<2, kPrecF16>);
+    } else if (precision == kPrecF8) {
+        if (S == 0) go(texm::fill_layers_kernel<0, kPrecF8>);
+        else if (S == 1) go(texm::fill_layers_kernel<1, kPrecF8>);
+        else go(texm::fill_layers_kernel<2, kPrecF8>);
+    } else {
+        if (S == 0) go(texm::fill_layers_kernel<0, kPrecF32>);
+        else if (S == 1) go(texm::fill_layers_kernel<1, kPrecF32>);
+        else go(texm::fill_layers_kernel<2, kPrecF32>);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_scale(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
+                               const int32_t B[3], const int32_t nb[3], float* scale, cudaStream_t s) {
+    texm::brick_scale_kernel<<<nb[0] * nb[1] * nb[2], 256, 0, s>>>(a, nx, ny, nz, a_pitch,
+                                                                   make_int3(B[0], B[1], B[2]),
+                                                                   make_int3(nb[0], nb[1], nb[2]), scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stored_minmax(const float* a, int64_t pitch, const int32_t n[3], const int32_t B[3],
+                                 const int32_t nb[3], int precision, const float* scale, float2* out,
+                                 cudaStream_t s) {
+    const int total = nb[0] * nb[1] * nb[2];
+    const int3 n3 = make_int3(n[0], n[1], n[2]), b3 = make_int3(B[0], B[1], B[2]);
+    const int3 nb3 = make_int3(nb[0], nb[1], nb[2]);
+    if (precision == kPrecF8)
+        texm::stored_minmax_kernel<kPrecF8><<<total, 256, 0, s>>>(a, pitch, n3, b3, nb3, scale, out);
+    else
+        texm::stored_minmax_kernel<kPrecF16><<<total, 256, 0, s>>>(a, pitch, n3, b3, nb3, scale, out);
     return cudaGetLastError();
 }
 

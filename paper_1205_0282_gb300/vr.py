@@ -30,6 +30,10 @@ VR_KERNEL_TMA = 0
 VR_KERNEL_DIRECT = 1
 VR_KERNEL_TEX = 2
 VR_KERNEL_AUTO = 3
+VR_OPT_PRECISION = 5
+VR_PRECISION_F32 = 0
+VR_PRECISION_F16 = 1
+VR_PRECISION_F8 = 2
 
 _ERR_NAMES = {VR_EINVAL: "VR_EINVAL", VR_ENOMEM: "VR_ENOMEM", VR_ECUDA: "VR_ECUDA",
               VR_ESTATE: "VR_ESTATE", VR_ETIMEOUT: "VR_ETIMEOUT"}

@@ -381,3 +381,112 @@ def test_tf_alpha_max_matches_dense_sampling():
         assert abs(oracle.tf_alpha_max(tf, lo, hi) - dense) < 1e-12
     assert oracle.tf_alpha_max(tf, -3.0, 6.5) == 0.0
     assert oracle.tf_alpha_max(tf, -3.0, 6.6) > 0.0
+
+
+# ------------------------------------------------------------ storage quantisers
+from oracle import quant  # noqa: E402
+
+
+def test_e4m3_table_fixed_points():
+    """Values the E4M3 definition fixes (1 sign, 4 exponent bits with bias 7, 3
+    mantissa bits, subnormals at exponent field 0, S.1111.111 = NaN)."""
+    v = quant.e4m3_values()
+    assert v[0x38] == 1.0 and v[0xB8] == -1.0
+    assert v[0x7E] == 448.0 and v[0xFE] == -448.0
+    assert v[0x01] == 2.0 ** -9 and v[0x07] == 7 * 2.0 ** -9
+    assert v[0x08] == 2.0 ** -6 and v[0x3F] == 1.875 and v[0x40] == 2.0
+    assert v[0x00] == 0.0 and np.signbit(v[0x80])
+    assert np.isnan(v[0x7F]) and np.isnan(v[0xFF])
+    assert np.isnan(v).sum() == 2
+    pos = v[:127]
+    assert np.all(np.diff(pos) > 0)  # codes 0..0x7e increase
+    assert np.allclose(v[128:255], -v[:127])
+
+
+def test_e4m3_round_trip_and_ties():
+    v = quant.e4m3_values()
+    finite = [c for c in range(256) if not np.isnan(v[c]) and c != 0x80]
+    assert list(quant.e4m3_encode(v[finite])) == finite
+    # exact midpoints go to the even code
+    assert quant.e4m3_encode(1.0625) == 0x38   # between 1.0 (0x38) and 1.125 (0x39)
+    assert quant.e4m3_encode(1.1875) == 0x3A   # between 1.125 (0x39) and 1.25 (0x3a)
+    assert quant.e4m3_encode(2.0 ** -10) == 0x00   # between 0 and 2^-9
+    assert quant.e4m3_encode(3 * 2.0 ** -10) == 0x02
+    assert quant.e4m3_encode(15 * 2.0 ** -10) == 0x08   # subnormal 7/8 2^-6 | normal 2^-6
+    assert quant.e4m3_encode(np.nextafter(np.float32(1.0625), np.float32(2))) == 0x39
+    # saturation
+    assert quant.e4m3_encode(464.0) == 0x7E and quant.e4m3_encode(1e30) == 0x7E
+    assert quant.e4m3_encode(-1e6) == 0xFE
+
+
+def test_e4m3_encode_is_the_nearest_value_brute_force():
+    rng = np.random.default_rng(5)
+    x = (rng.choice([-1, 1], 4000) * 2.0 ** rng.uniform(-12, 9.5, 4000)).astype(np.float32)
+    codes = quant.e4m3_encode(x)
+    v = quant.e4m3_values()
+    fin = np.array([c for c in range(256) if not np.isnan(v[c])])
+    for xi, c in zip(x.astype(np.float64), codes):
+        xs = np.clip(xi, -448, 448)
+        d = np.abs(v[fin] - xs)
+        best = fin[d == d.min()]
+        best_vals = set(v[best])
+        assert v[c] in best_vals or (v[c] == 0 and 0.0 in best_vals)
+        if len(best_vals) > 1:  # a tie: the even mantissa wins
+            assert c % 2 == 0
+
+
+def test_fp16_storage_fixed_points():
+    c = np.array([[[1 / 3, 65504.0, 2.0 ** -24, 1.0 + 2.0 ** -11]]], dtype=np.float32)
+    s = quant.stored_cube(c, "f16")
+    assert s[0, 0, 0] == np.float32(0.333251953125)
+    assert s[0, 0, 1] == 65504.0 and s[0, 0, 2] == 2.0 ** -24
+    assert s[0, 0, 3] == 1.0  # tie between 1 and 1 + 2^-10 goes to the even fraction
+
+
+def test_brick_ownership():
+    assert list(quant.owner_index(9, 4)) == [0, 0, 0, 0, 1, 1, 1, 1, 1]
+    assert list(quant.owner_index(10, 4)) == [0, 0, 0, 0, 1, 1, 1, 1, 2, 2]
+    assert list(quant.owner_index(5, 8)) == [0] * 5
+
+
+def fp8_lossless_cube(shape_xyz, brick, seed=7):
+    """A cube that FP8 storage holds exactly: per brick b a power-of-two scale 2^k_b,
+    every value a finite E4M3 value times 2^k_b, and one voxel of magnitude
+    448 * 2^k_b so that the brick's scale is exactly 2^k_b."""
+    nx, ny, nz = shape_xyz
+    cube = synth.hi_cube(seed=seed, shape_xyz=shape_xyz, n_line=12, n_cont=2)
+    ox, oy, oz = (quant.owner_index(n, b) for n, b in zip(shape_xyz, brick))
+    kb = -5 - ((ox[None, None, :] + oy[None, :, None] + oz[:, None, None]) % 3)
+    scale = np.ldexp(np.float32(1), kb).astype(np.float32)
+    q = quant.e4m3_decode(quant.e4m3_encode(cube / scale)).astype(np.float32) * scale
+    for k in range(oz.max() + 1):
+        for j in range(oy.max() + 1):
+            for i in range(ox.max() + 1):
+                z0, y0, x0 = np.argmax(oz == k), np.argmax(oy == j), np.argmax(ox == i)
+                q[z0, y0, x0] = 448.0 * scale[z0, y0, x0]
+    return q.astype(np.float32)
+
+
+def test_fp8_storage_of_a_representable_cube_is_exact():
+    for shape, brick in [((40, 33, 27), (16, 16, 8)), ((64, 64, 64), (32, 32, 32))]:
+        c = fp8_lossless_cube(shape, brick)
+        s = quant.brick_scales(c, brick)
+        assert np.all(np.log2(s) == np.round(np.log2(s)))
+        assert np.array_equal(quant.stored_cube(c, "f8", brick), c)
+
+
+def test_fp8_storage_error_bound():
+    """|read-back - v| <= 2^-4 |v| (3 mantissa bits, round to nearest) plus half
+    the subnormal spacing 2^-10 s_b, and each brick keeps its largest magnitude."""
+    c = synth.tiny_cube()
+    brick = (24, 20, 32)
+    q = quant.stored_cube(c, "f8", brick)
+    s = quant.brick_scales(c, brick)
+    nz, ny, nx = c.shape
+    sv = s[np.ix_(quant.owner_index(nz, brick[2]), quant.owner_index(ny, brick[1]),
+                  quant.owner_index(nx, brick[0]))]
+    err = np.abs(q.astype(np.float64) - c)
+    assert np.all(err <= 2.0 ** -4 * np.abs(c) + 2.0 ** -10 * sv + 1e-6 * np.abs(c))
+    assert err.max() > 0
+    # relative error of the normal range is well inside the bound on average
+    assert np.median(err / np.maximum(np.abs(c), 1e-30)) < 2.0 ** -5
