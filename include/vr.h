@@ -120,8 +120,10 @@ typedef struct {
                                 448, with s_b = max|v| over the voxels b owns / 448 (1 for
                                 an all-zero brick); it reads back as code * s_b.
                                 Interpolation, transfer function and compositing stay in
-                                FP32; the image equals the FP32 render of the cube of
-                                read-back values, and empty-space skipping uses the
+                                FP32; the image is the FP32 render of the cube of
+                                read-back values (up to FP32 rounding order: F8
+                                interpolates code values and applies the brick's scale
+                                once per sample), and empty-space skipping uses the
                                 read-back values' per-brick range.  F16 and F8 need the
                                 texture march (VR_OPT_MODE 0 and VR_KERNEL_TEX, or
                                 VR_KERNEL_AUTO on a cube within the texture limits):

@@ -659,7 +659,7 @@ int prepare_tex(vr_ctx* c) {
     for (int S = 0; S < 3; ++S) {
         const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
         cudaChannelFormatDesc ch = c->precision == VR_PRECISION_F16 ? cudaCreateChannelDescHalf()
-                                   : c->precision == VR_PRECISION_F8 ? cudaCreateChannelDesc<unsigned char>()
+                                   : c->precision == VR_PRECISION_F8 ? cudaCreateChannelDesc<signed char>()
                                                                      : cudaCreateChannelDesc<float>();
         if (cudaMalloc3DArray(&c->tex_arr[S], &ch, make_cudaExtent((size_t)n[U], (size_t)n[V], (size_t)n[S]),
                               cudaArrayLayered | cudaArraySurfaceLoadStore) != cudaSuccess) {

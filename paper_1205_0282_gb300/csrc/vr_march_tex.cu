@@ -22,9 +22,9 @@ namespace vr {
 
 namespace texm {
 
-// resident CTAs per SM the kernels are compiled for: 20 (48 registers a thread) for
-// FP32/FP16 storage; FP8 decoding needs a few more registers (16 CTAs, 64 registers)
-constexpr int tex_blocks_per_sm(int prec) { return prec == kPrecF8 ? 16 : 20; }
+// resident CTAs per SM the kernels are compiled for: 20 (48 registers a thread)
+// for FP32/FP16 storage, 18 (56 registers) for FP8, whose decode needs a few more
+constexpr int tex_blocks_per_sm(int prec) { return prec == kPrecF8 ? 18 : 20; }
 
 // Layered texture of the sweep axis S: layer index = coordinate along S, texel
 // (x, y) = coordinates along (U, V) with U < V the two other axes.
@@ -50,12 +50,12 @@ __device__ __forceinline__ void gather4(cudaTextureObject_t t, int layer, float 
     c00 = r3;
 }
 
-// FP8 E4M3 storage: the texture returns the raw codes; two codes at a time are
-// widened by the hardware conversion e4m3x2 -> f16x2 and then to FP32.
+// FP8 E4M3 storage: the codes sit in a signed 8-bit texture, so the gather
+// returns each code sign-extended to 32 bits.
 __device__ __forceinline__ void gather4_codes(cudaTextureObject_t t, int layer, float x, float y,
-                                              unsigned& c00, unsigned& c10, unsigned& c01, unsigned& c11) {
-    unsigned r0, r1, r2, r3;
-    asm("tld4.r.a2d.v4.u32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %8}];"
+                                              int& c00, int& c10, int& c01, int& c11) {
+    int r0, r1, r2, r3;
+    asm("tld4.r.a2d.v4.s32.f32 {%0, %1, %2, %3}, [%4, {%5, %6, %7, %8}];"
         : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
         : "l"(t), "r"(layer), "f"(x), "f"(y), "f"(0.0f));
     c01 = r0;
@@ -64,8 +64,19 @@ __device__ __forceinline__ void gather4_codes(cudaTextureObject_t t, int layer, 
     c00 = r3;
 }
 
-// (lo, hi) E4M3 codes -> their values (the code in the low byte of the packed pair
-// becomes the low half of the f16x2 result)
+// Value of a sign-extended E4M3 code r times 2^-120, by moving its fields into an
+// FP32 word: shifted left by 20, the code's sign lands in bit 31 (the sign
+// extension fills bits 27..30, which the mask clears) and its exponent e (bias 7)
+// and 3 mantissa bits in bits 26..20, i.e. in the low exponent bits and the top
+// of the FP32 mantissa.  A normal code then reads as 2^(e-127) (1 + m/8) and a
+// subnormal one (e = 0) as the FP32 denormal m 2^20 2^-149 = (m/8) 2^-6 2^-120:
+// both are the code's value times 2^-120, exactly.
+__device__ __forceinline__ float e4m3_times_2m120(int r) {
+    return __uint_as_float(((unsigned)r << 20) & 0x87f00000u);
+}
+
+// (lo, hi) E4M3 codes -> their values through the hardware conversion e4m3x2 ->
+// f16x2 (used by the per-brick range of the stored values)
 __device__ __forceinline__ float2 e4m3_pair(unsigned lo, unsigned hi) {
     const unsigned short packed = (unsigned short)((lo & 0xffu) | ((hi & 0xffu) << 8));
     unsigned h2;
@@ -79,6 +90,11 @@ __device__ __forceinline__ unsigned e4m3_code(float x) {
     unsigned short d;
     asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(0.0f), "f"(x));
     return d & 0xffu;
+}
+
+// Brick-index step along axis a.
+__device__ __forceinline__ int step_of(const FrameParams& p, int a) {
+    return a == 0 ? 1 : (a == 1 ? p.nb[0] : p.nb[0] * p.nb[1]);
 }
 
 template <int S, bool UNIFORM, int PREC>
@@ -126,23 +142,27 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
     // composited, so texture latency overlaps the arithmetic.
     struct Corners {
         float c[8];  // (u, v, s) corners: c[0..3] in plane ps, c[4..7] in plane ps + 1
+                     // (FP8: the raw codes, decoded when the sample is used, so that the
+                     // gathers stay in flight across one sample's compositing)
         float fu, fv, fs;
+        int halo;    // FP8: bit a set if the cell's +1 corners along U, V, S (a = 0, 1, 2)
+                     // lie in the next brick
     };
-    // FP8: corners read back as code * scale of the brick that owns them; the +1
-    // corners on the brick's far faces belong to the next brick along that axis, if
-    // there is one (a rare case, whose scales are read when needed)
-    float sc0 = 1.0f;
-    bool next_u = false, next_v = false, next_s = false;
-    int step_u = 0, step_v = 0, step_s = 0;
+    // FP8: corners read back as code * scale of the brick that owns them.  The
+    // interpolation runs on code values * 2^-120 and the result is multiplied once
+    // by k0 = 2^120 s_b (trilinear weights sum to one; the power of two is exact).
+    // The +1 corners on the brick's far faces belong to the next brick along that
+    // axis, if there is one (a rare case: those corners are rescaled by the ratio
+    // of the two bricks' scales).  lim_a is the cell index along axis a whose +1
+    // corner lies in the next brick (-1: none).
+    float k0 = 1.0f, s0 = 1.0f;
+    int lim_u = -1, lim_v = -1, lim_s = -1;
     if (PREC == kPrecF8) {
-        sc0 = p.brick_scale[item.brick];
-        const int step[3] = {1, p.nb[0], p.nb[0] * p.nb[1]};
-        next_u = bidx[U] + 1 < p.nb[U];
-        next_v = bidx[V] + 1 < p.nb[V];
-        next_s = bidx[S] + 1 < p.nb[S];
-        step_u = step[U];
-        step_v = step[V];
-        step_s = step[S];
+        s0 = p.brick_scale[item.brick];
+        k0 = s0 * 0x1p120f;
+        if (bidx[U] + 1 < p.nb[U]) lim_u = p.B[U] - 1;
+        if (bidx[V] + 1 < p.nb[V]) lim_v = p.B[V] - 1;
+        if (bidx[S] + 1 < p.nb[S]) lim_s = p.B[S] - 1;
     }
     auto fetch = [&](float f, Corners& s) {
         const float qS = fmaf(f, dq[S], qs[S]);
@@ -162,43 +182,44 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
             gather4(tex, O[S] + ps, x, y, s.c[0], s.c[1], s.c[2], s.c[3]);
             gather4(tex, O[S] + ps + 1, x, y, s.c[4], s.c[5], s.c[6], s.c[7]);
         } else {
-            unsigned k[8];
+            int k[8];
             gather4_codes(tex, O[S] + ps, x, y, k[0], k[1], k[2], k[3]);
             gather4_codes(tex, O[S] + ps + 1, x, y, k[4], k[5], k[6], k[7]);
 #pragma unroll
-            for (int c = 0; c < 8; c += 2) {
-                const float2 v = e4m3_pair(k[c], k[c + 1]);
-                s.c[c] = v.x;
-                s.c[c + 1] = v.y;
-            }
-            const bool hu = next_u && iu + 1 == p.B[U];
-            const bool hv = next_v && iv + 1 == p.B[V];
-            const bool hs = next_s && ps + 1 == p.B[S];
-            if (hu || hv || hs) {
+            for (int c = 0; c < 8; ++c) s.c[c] = __int_as_float(k[c]);
+            s.halo = (iu == lim_u ? 1 : 0) | (iv == lim_v ? 2 : 0) | (ps == lim_s ? 4 : 0);
+        }
+    };
+    // FP8 corners of a fetched sample: code value * 2^-120 (* s_owner / s_b on the
+    // far faces)
+    auto decode = [&](Corners& s) {
+        if (PREC != kPrecF8) return;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int off = ((c & 1) && hu ? step_u : 0) + ((c & 2) && hv ? step_v : 0) +
-                                    ((c & 4) && hs ? step_s : 0);
-                    s.c[c] *= off ? __ldg(p.brick_scale + item.brick + off) : sc0;
-                }
-            } else {
+        for (int c = 0; c < 8; ++c) s.c[c] = e4m3_times_2m120(__float_as_int(s.c[c]));
+        if (s.halo) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) s.c[c] *= sc0;
+            for (int c = 1; c < 8; ++c) {
+                const int off = ((c & 1) && (s.halo & 1) ? step_of(p, U) : 0) +
+                                ((c & 2) && (s.halo & 2) ? step_of(p, V) : 0) +
+                                ((c & 4) && (s.halo & 4) ? step_of(p, S) : 0);
+                if (off) s.c[c] *= __ldg(p.brick_scale + item.brick + off) / s0;
             }
         }
     };
     Corners nxt;
     if (fk < fn) fetch(fk, nxt);
     while (fk < fn) {
-        const Corners cur = nxt;
+        Corners cur = nxt;
         if (fk + 1.0f < fn) fetch(fk + 1.0f, nxt);
+        decode(cur);
         const float e00 = fmaf(cur.fu, cur.c[1] - cur.c[0], cur.c[0]);
         const float e10 = fmaf(cur.fu, cur.c[3] - cur.c[2], cur.c[2]);
         const float e01 = fmaf(cur.fu, cur.c[5] - cur.c[4], cur.c[4]);
         const float e11 = fmaf(cur.fu, cur.c[7] - cur.c[6], cur.c[6]);
         const float e0 = fmaf(cur.fv, e10 - e00, e00);
         const float e1 = fmaf(cur.fv, e11 - e01, e01);
-        const float val = fmaf(cur.fs, e1 - e0, e0);
+        float val = fmaf(cur.fs, e1 - e0, e0);
+        if (PREC == kPrecF8) val *= k0;
         const float4 col = tf_lookup<UNIFORM>(p, s_rgba, s_v, val);
         const float alpha = opacity_correct(p, col.w);
         const float w = (1.0f - acc.w) * alpha;
@@ -259,7 +280,7 @@ __global__ void fill_layers_kernel(const float* __restrict__ a, int64_t nx, int6
         const int bx = min((int)(x / B.x), nb.x - 1), by = min((int)(y / B.y), nb.y - 1);
         const int bz = min((int)(z / B.z), nb.z - 1);
         const float sc = scale[bx + nb.x * (by + nb.y * bz)];
-        surf2DLayeredwrite((unsigned char)e4m3_code(v / sc), surf, cx, (int)c[V], (int)c[S]);
+        surf2DLayeredwrite((signed char)e4m3_code(v / sc), surf, cx, (int)c[V], (int)c[S]);
     }
 }
 

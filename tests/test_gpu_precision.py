@@ -5,9 +5,10 @@ An FP16 or FP8 render is defined as the FP32 render of the cube of values that t
 storage reads back (oracle/quant.py builds that cube from the format definitions);
 so each form is compared element by element with the FP64 oracle run on the
 read-back cube, at the same tolerances as the FP32 path.  Cubes whose values the
-storage holds exactly must give the FP32 image bit for bit (this checks the code
-layout, the decode and the per-brick scale of every corner, including the corners
-a brick reads from its neighbours).
+storage holds exactly must give the FP32 image (FP16: bit for bit; FP8, which
+interpolates code values and applies the brick's scale once afterwards: up to
+FP32 rounding).  This checks the code layout, the decode and the per-brick scale
+of every corner, including the corners a brick reads from its neighbours.
 """
 import numpy as np
 import pytest
@@ -73,7 +74,8 @@ def test_fp8_exact_cube_gives_the_fp32_image(vr, torch, shape, brick):
         cam = synth.pose(shape, az, el, 96, 80, step=0.4)
         a, _ = tex_render(vr, torch, cube, tf, cam, brick, "f32")
         b, _ = tex_render(vr, torch, cube, tf, cam, brick, "f8")
-        assert np.array_equal(a, b)
+        assert np.abs(a - b).max() <= 2e-6
+        assert np.mean(a == b) > 0.9
         assert a[..., 3].max() > 0.3
 
 

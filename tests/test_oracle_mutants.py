@@ -3,17 +3,25 @@
 Each case plants one mistake in a copy of the oracle's C source (on the CPU,
 in a temporary directory), builds it, swaps it in for the real oracle library,
 and runs the pin tests of test_oracle_pins.py against it: at least one pin
-must fail.  The real oracle is untouched.
+must fail.  The real oracle is untouched.  The pins run in a child process, so
+that a mutant that reads out of bounds and crashes (which also counts as caught)
+cannot take the test session down.
 """
 import ctypes
+import json
 import os
 import subprocess
+import sys
 
 import numpy as np
 import pytest
 
-import oracle
-import test_oracle_pins as pins
+if __name__ == "__main__":
+    sys.path[:0] = [os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    os.path.dirname(os.path.abspath(__file__))]
+
+import oracle  # noqa: E402
+import test_oracle_pins as pins  # noqa: E402
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "vr_oracle.c")
 
@@ -55,43 +63,63 @@ def _pin_calls():
     return calls
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_mutant_is_caught(name, tmp_path, monkeypatch):
-    old, new = MUTANTS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation site for {name!r} not found exactly once"
-    mpath = tmp_path / "mutant.c"
-    mpath.write_text(src.replace(old, new))
-    so = tmp_path / "mutant.so"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                    "-std=c11", "-o", str(so), str(mpath), "-lm"], check=True)
+def _swap_in(so_path):
+    """Load the library at so_path with the real oracle's signatures and make the
+    oracle package use it."""
     real = oracle._load()
-    mlib = ctypes.CDLL(str(so))
-    for fn in ("orc_render", "orc_pixel_ray", "orc_pixel_bricks", "orc_brick_minmax",
-               "orc_tf_alpha_max"):
-        getattr(mlib, fn).argtypes = getattr(real, fn).argtypes
-        getattr(mlib, fn).restype = getattr(real, fn).restype
-    monkeypatch.setattr(oracle, "_lib", mlib)
-    caught = []
-    for pin_name, call in _pin_calls():
-        try:
-            call()
-        except AssertionError:
-            caught.append(pin_name)
-    assert caught, f"no pin caught the planted mistake {name!r}"
-
-
-def test_unmutated_copy_passes_all_pins(tmp_path, monkeypatch):
-    """Control: the same harness with the unchanged source fails nothing."""
-    so = tmp_path / "same.so"
-    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-                    "-std=c11", "-o", str(so), SRC, "-lm"], check=True)
-    real = oracle._load()
-    lib = ctypes.CDLL(str(so))
+    lib = ctypes.CDLL(str(so_path))
     for fn in ("orc_render", "orc_pixel_ray", "orc_pixel_bricks", "orc_brick_minmax",
                "orc_tf_alpha_max"):
         getattr(lib, fn).argtypes = getattr(real, fn).argtypes
         getattr(lib, fn).restype = getattr(real, fn).restype
-    monkeypatch.setattr(oracle, "_lib", lib)
-    for _, call in _pin_calls():
-        call()
+    oracle._lib = lib
+
+
+def _run_pins_in_child(so_path):
+    """(return code, names of the pins that failed) for the library at so_path."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), str(so_path)], cwd=here,
+                       capture_output=True, text=True, timeout=600)
+    caught = []
+    for line in r.stdout.splitlines():
+        if line.startswith("CAUGHT "):
+            caught = json.loads(line[len("CAUGHT "):])
+    return r.returncode, caught
+
+
+def _build(src_text, tmp_path, name):
+    cpath = tmp_path / f"{name}.c"
+    cpath.write_text(src_text)
+    so = tmp_path / f"{name}.so"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                    "-std=c11", "-o", str(so), str(cpath), "-lm"], check=True)
+    return so
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name!r} not found exactly once"
+    so = _build(src.replace(old, new), tmp_path, "mutant")
+    rc, caught = _run_pins_in_child(so)
+    assert rc != 0 or caught, f"no pin caught the planted mistake {name!r}"
+
+
+def test_unmutated_copy_passes_all_pins(tmp_path):
+    """Control: the same harness with the unchanged source fails nothing."""
+    so = _build(open(SRC).read(), tmp_path, "same")
+    rc, caught = _run_pins_in_child(so)
+    assert rc == 0 and caught == []
+
+
+if __name__ == "__main__":
+    # child: run every pin against the library given on the command line
+    _swap_in(sys.argv[1])
+    failed = []
+    for pin_name, call in _pin_calls():
+        try:
+            call()
+        except AssertionError:
+            failed.append(pin_name)
+    print("CAUGHT " + json.dumps(failed), flush=True)
