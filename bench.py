@@ -210,9 +210,10 @@ def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False):
         x0, y0 = W // 2 - crop // 2, H // 2 - crop // 2
         jj, ii = np.meshgrid(np.arange(y0, y0 + crop), np.arange(x0, x0 + crop), indexing="ij")
         pix = (jj * W + ii).reshape(-1)
-        ref, _, ns = oracle.render(cube, tf, cam, brick=brick, pixels=pix)
+        ref, amb, ns = oracle.render(cube, tf, cam, brick=brick, pixels=pix,
+                                     amb_alpha=QUALITY_AMB_ALPHA, amb_steps=QUALITY_AMB_STEPS)
         total += int(ns.sum())
-        crops.append((cam, pix, ref) if keep else None)
+        crops.append((cam, pix, ref, amb) if keep else None)
         k += 7
         if time.perf_counter() - t0 >= seconds:
             break
@@ -220,19 +221,36 @@ def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False):
     return (total / dt, dt, len(crops), crops) if keep else (total / dt, dt, len(crops))
 
 
+# A pixel is "ambiguous" for the image-quality figures when the oracle's compositing
+# alpha comes within this distance of the termination threshold, or a sample
+# position within QUALITY_AMB_STEPS voxel of the ray's exit: there a perturbation
+# of that size (FP16/FP8 storage moves voxel values by up to 2^-11 / 2^-4
+# relative) may legitimately stop the ray one sample earlier or later.
+QUALITY_AMB_ALPHA = 1e-3
+QUALITY_AMB_STEPS = 1e-4
+
+
 def image_quality(render_pose, crops):
     """Per-pixel error of the GPU image against the FP64 oracle's crops (oracle
     on the FP32 cube).  PSNR = 10 log10(1 / MSE) over the RGBA channels, whose
-    values lie in [0, 1]."""
-    errs = []
-    for cam, pix, ref in crops:
+    values lie in [0, 1]; max_abs over all pixels and over the unambiguous ones."""
+    errs, ambs = [], []
+    for cam, pix, ref, amb in crops:
         errs.append(render_pose(cam, pix).astype(np.float64) - ref.reshape(-1, 4))
+        ambs.append(amb.reshape(-1) != 0)
     e = np.concatenate(errs)
+    amb = np.concatenate(ambs)
     mse = float(np.mean(e * e))
+    per_px = np.abs(e).max(axis=1)
     return {"against": "FP64 oracle on the FP32 cube", "pixels": int(e.shape[0]),
             "sub_views": f"the CPU-baseline crops: {len(crops)} poses",
-            "max_abs": float(np.abs(e).max()), "rms": mse ** 0.5,
-            "psnr_db": (10 * np.log10(1.0 / mse)) if mse > 0 else None}
+            "max_abs": float(per_px.max()), "rms": mse ** 0.5,
+            "psnr_db": (10 * np.log10(1.0 / mse)) if mse > 0 else None,
+            "ambiguous_pixels": int(amb.sum()),
+            "ambiguity": f"oracle alpha within {QUALITY_AMB_ALPHA:g} of tau or a sample within "
+                         f"{QUALITY_AMB_STEPS:g} voxel of the exit",
+            "max_abs_unambiguous": float(per_px[~amb].max()) if (~amb).any() else None,
+            "pixels_over_1e-3": int((per_px > 1e-3).sum())}
 
 
 def cpu_cores():
