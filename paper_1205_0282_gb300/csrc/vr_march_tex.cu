@@ -187,9 +187,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
             gather4_codes(tex, O[S] + ps + 1, x, y, k[4], k[5], k[6], k[7]);
 #pragma unroll
             for (int c = 0; c < 8; ++c) s.c[c] = __int_as_float(k[c]);
-            s.halo = 0;
-            if (iu == lim_u || iv == lim_v || ps == lim_s)
-                s.halo = (iu == lim_u ? 1 : 0) | (iv == lim_v ? 2 : 0) | (ps == lim_s ? 4 : 0);
+            s.halo = (iu == lim_u ? 1 : 0) | (iv == lim_v ? 2 : 0) | (ps == lim_s ? 4 : 0);
         }
     };
     // FP8 corners of a fetched sample: code value * 2^-120 (* s_owner / s_b on the
