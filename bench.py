@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--kernel", choices=["auto", "tma", "direct", "tex"], default="auto")
     ap.add_argument("--precision", choices=["f32", "f16", "f8"], default="f32",
                     help="storage of the texture march's cube copies (FP32, FP16, FP8 E4M3 per-brick scale)")
+    ap.add_argument("--shard", type=int, default=1,
+                    help="render each frame as this many virtual ranks on one GPU (k-d leaves, one "
+                         "stream each, root fold of the rectangle-clipped sub-images)")
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -343,9 +346,39 @@ def run_ours(args):
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    if args.shard > 1:
+        from paper_1205_0282_gb300 import vr as vrm
+        leaves = vrm.vr_kd_partition(spec["shape_xyz"], spec["brick"], args.shard)
+        leaf_streams = [torch.cuda.Stream() for _ in range(args.shard)]
+        leaf_bufs = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(args.shard)]
+
     def frame(k):
-        r.set_camera(my_poses[k % len(my_poses)])
-        r.render(out, stream)
+        draw(my_poses[k % len(my_poses)])
+
+    def draw(cam):
+        r.set_camera(cam)
+        if args.shard <= 1:
+            r.render(out, stream)
+            return
+        # virtual ranks: leaf j on its own stream into a rectangle-sized buffer,
+        # then the root stream folds the sub-images in visibility order
+        subs, rects = [], []
+        for j in range(args.shard):
+            r.set_region(leaves[j, :3], leaves[j, 3:])
+            rect = r.region_rect()
+            n_px = max(int(rect[2] - rect[0] + 1), 0) * max(int(rect[3] - rect[1] + 1), 0)
+            leaf_streams[j].wait_stream(stream)
+            sub = None
+            if n_px:
+                sub = leaf_bufs[j].view(-1)[:n_px * 4].view(int(rect[3] - rect[1] + 1), int(rect[2] - rect[0] + 1), 4)
+                r.render_rect(rect, sub, leaf_streams[j])
+            subs.append(sub)
+            rects.append(rect)
+        for s_ in leaf_streams:
+            stream.wait_stream(s_)
+        order = vrm.vr_kd_order(spec["shape_xyz"], spec["brick"], args.shard, cam["eye"])
+        vrm.vr_composite_subimages(r.ctx, [subs[j] for j in order], np.stack([rects[j] for j in order]), out,
+                                   stream)
 
     for k in range(args.warmup):
         frame(k)
@@ -370,12 +403,14 @@ def run_ours(args):
     st = r.stats()
     elapsed_ms = evs[0].elapsed_time(evs[-1])
     frame_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    # the root fold of --shard is one more launch per frame
+    fold_launches = args.steps if args.shard > 1 else 0
     elapsed_ms, (samples, frames, launches) = job_totals(
-        dist, elapsed_ms, [st["samples"], st["frames"], st["launches"]], "cuda")
+        dist, elapsed_ms, [st["samples"], args.steps, st["launches"] + fold_launches], "cuda")
 
     # end to end: host output buffer, copies inside the timed region
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and args.shard <= 1:
         host = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True).numpy()
         r.reset_stats()
         torch.cuda.synchronize()
@@ -400,10 +435,10 @@ def run_ours(args):
 
     def render_pose(cam, pix):
         """RGBA of pixels pix (flat indices) of the frame at pose cam."""
-        r.set_camera(cam)
-        r.render(out, stream)
+        draw(cam)
         return out.view(-1, 4)[torch.from_numpy(pix).cuda()].cpu().numpy()
 
+    per_frame = max(st["frames"], 1) if args.shard <= 1 else args.steps   # stats count leaf renders
     peak, peak_kind = peaks()
     avg_march_ms = st["march_ms"] / max(st["frames"], 1)
     bytes_per_launch = st["touched_bytes"] / max(st["frames"], 1)
@@ -444,20 +479,22 @@ def run_ours(args):
                                    "f8": "FP8 E4M3, per-brick absmax/448 scale"}[args.precision],
                        "l2": ("inputs larger than L2, no flush" if spec["name"] != "tiny"
                               else "tiny cube fits in L2 (not a bench line)"),
-                       "parallelism": f"replicas x{world}: orbit poses split across ranks"},
+                       "parallelism": f"replicas x{world}: orbit poses split across ranks"
+                                      + (f"; each frame as {args.shard} virtual ranks (k-d leaves) on one GPU"
+                                         if args.shard > 1 else "")},
             "fps": frames / (elapsed_ms * 1e-3),
             "frame_ms_p50": float(np.percentile(frame_ms, 50)),
             "frame_ms_p75": float(np.percentile(frame_ms, 75)),
             "samples_per_frame": samples / max(frames, 1),
-            "bricks_rendered_per_frame": st["bricks_rendered"] / max(st["frames"], 1),
-            "bricks_skipped_per_frame": st["bricks_skipped"] / max(st["frames"], 1),
-            "plan_ms_per_frame": st["plan_ms"] / max(st["frames"], 1),
-            "composite_ms_per_frame": st["composite_ms"] / max(st["frames"], 1),
+            "bricks_rendered_per_frame": st["bricks_rendered"] / per_frame,
+            "bricks_skipped_per_frame": st["bricks_skipped"] / per_frame,
+            "plan_ms_per_frame": st["plan_ms"] / per_frame,
+            "composite_ms_per_frame": st["composite_ms"] / per_frame,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "quality": quality,
             "march_kernel": args.kernel,
-            "chunks_staged_per_frame": st["chunks_staged"] / max(st["frames"], 1),
-            "chunks_direct_per_frame": st["chunks_direct"] / max(st["frames"], 1),
+            "chunks_staged_per_frame": st["chunks_staged"] / per_frame,
+            "chunks_direct_per_frame": st["chunks_direct"] / per_frame,
             "gpu_launches": launches, "clocks": clocks.summary(),
             "device_errors": st["device_errors"]}
     print(json.dumps(line), flush=True)

@@ -218,6 +218,88 @@ int vr_get_brick_minmax(vr_ctx* ctx, float* out, int64_t n_bricks);
 int vr_plan_brick_rects(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz,
                         int32_t bx, int32_t by, int32_t bz, int32_t* rects, int64_t n_bricks);
 
+/* ---------------------------------------------------------------------------
+ * Sort-last distribution over ranks (Sections 2.3.1, 2.3.3, 2.3.4).  Each rank
+ * renders the bricks of its k-d leaf into a sub-image clipped to the leaf's
+ * rendering rectangle; the root folds the sub-images front to back with 'over'.
+ * A ray meets each leaf in one contiguous run (leaves are boxes), so with
+ * term_alpha = 1 the fold equals the single-context render; with term_alpha < 1
+ * each leaf stops at term_alpha on its own and the root stops once a pixel
+ * reaches it, as bricks do within one context.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Host-only, no device needed.  k-d partition of the brick grid of an nx x ny x nz
+ * cube with brick size B into n_parts boxes of bricks of near-equal volume
+ * (Section 2.3.1): each tree node cuts its longest axis (voxel extent; ties go to
+ * the lower axis; an axis of one brick is not cut), the low side taking
+ * floor(parts/2) of the node's parts and round(bricks * floor(parts/2) / parts)
+ * of its bricks along that axis (at least one brick a side).
+ *   ranges: int32[n_parts][6] receiving brick (lo x, y, z, hi x, y, z), hi
+ *           exclusive, leaves numbered depth first, low side first.
+ * Errors: VR_EINVAL (bad sizes, n_parts < 1 or more parts than bricks, or a node
+ * that cannot be cut).
+ */
+int vr_kd_partition(int64_t nx, int64_t ny, int64_t nz, const int32_t B[3], int32_t n_parts,
+                    int32_t* ranges);
+
+/*
+ * Host-only.  Front-to-back visibility order of the leaves of vr_kd_partition
+ * (same arguments) from eye (voxel coordinates): the tree is walked with the
+ * eye's side of each cut first (a cut at brick index k along axis a is the plane
+ * a = k * B[a]; an eye on the plane counts as the high side).
+ *   order: int32[n_parts] receiving leaf numbers, nearest first.
+ * Errors: VR_EINVAL.
+ */
+int vr_kd_order(int64_t nx, int64_t ny, int64_t nz, const int32_t B[3], int32_t n_parts,
+                const double eye[3], int32_t* order);
+
+/*
+ * Restrict this context's renders to the bricks [lo, hi) (brick indices per axis,
+ * 0 <= lo < hi <= bricks along the axis).  vr_brick resets it to all bricks.
+ * Errors: VR_EINVAL, VR_ESTATE (no bricking).
+ */
+int vr_set_region(vr_ctx* ctx, const int32_t lo[3], const int32_t hi[3]);
+
+/*
+ * Rendering rectangle of the current region for the current camera (Section
+ * 2.3.2), int32[4] = (x0, y0, x1, y1) inclusive, or (0, 0, -1, -1) when no pixel
+ * sees it.  Host-only computation.  Errors: VR_EINVAL, VR_ESTATE.
+ */
+int vr_region_rect(vr_ctx* ctx, int32_t rect[4]);
+
+/* Host-only: the same rectangle for the brick range [lo, hi) of a cube of the
+ * given sizes and brick size B, without a context.  Errors: VR_EINVAL. */
+int vr_plan_region_rect(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz, const int32_t B[3],
+                        const int32_t lo[3], const int32_t hi[3], int32_t rect[4]);
+
+/*
+ * vr_render restricted to the pixel rectangle rect = (x0, y0, x1, y1) inclusive
+ * (within the image): only those pixels are computed, and out_rgba receives them
+ * as float32[y1-y0+1][x1-x0+1][4] (device memory written on the stream, or host
+ * memory filled before return, as for vr_render).  An empty rect (x1 < x0 or
+ * y1 < y0) renders nothing and returns VR_OK.  The pixels equal those of
+ * vr_render.  Errors: as vr_render, VR_EINVAL (rect outside the image).
+ */
+int vr_render_rect(vr_ctx* ctx, const int32_t rect[4], float* out_rgba, void* cuda_stream);
+
+/*
+ * Root fold (Sections 2.3.3-2.3.4): out_rgba (float32[H][W][4] of the context's
+ * camera; device memory written on the stream, or host memory filled before
+ * return) receives, per pixel, the front-to-back 'over' fold of the sub-images
+ * whose rectangle holds it, in the order given, stopping once the pixel's alpha
+ * reaches term_alpha; pixels no sub-image covers are 0.
+ *   images: n device pointers, sub-image k = float32[rows][cols][4] of rects[k];
+ *   rects:  int32[n][4] (x0, y0, x1, y1) inclusive, within the image; an empty
+ *           rect (x1 < x0 or y1 < y0) is skipped and its pointer may be NULL.
+ *   n:      0 <= n <= 256.
+ * The sub-images must be complete on the device before the fold's stream reaches
+ * it (the caller orders streams).  Errors: VR_EINVAL, VR_ESTATE (no camera),
+ * VR_ENOMEM, VR_ECUDA.
+ */
+int vr_composite_subimages(vr_ctx* ctx, int32_t n, const float* const* images, const int32_t* rects,
+                           float* out_rgba, void* cuda_stream);
+
 /*
  * Allocation-free render (the paper has no counterpart; this serves callers that
  * may not allocate device memory while rendering: an application or plugin that

@@ -7,8 +7,10 @@ it and never calls it.
 ``vr_oracle.c`` is the plain FP64 ray caster (camera, slab entry/exit, fixed
 step sampling, tri-linear interpolation, piecewise-linear transfer function,
 opacity correction, front-to-back compositing with early termination, bricked
-mode with per-brick runs folded by 'over'; Sections 1.2, 2.3.2 and 2.3.3 of
-Hassan, Fluke & Barnes, arXiv:1205.0282).  ``brute.py`` is an independent
+mode with per-brick runs folded by 'over', and the two-level fold of per-region
+runs for sort-last distribution over ranks; Sections 1.2, 2.3.2-2.3.4 of
+Hassan, Fluke & Barnes, arXiv:1205.0282).  ``quant.py`` builds the cube that
+FP16 / FP8 storage reads back.  ``brute.py`` is an independent
 arbitrary-precision restatement used to pin it on tiny inputs.
 """
 from __future__ import annotations
@@ -64,6 +66,11 @@ def _load():
                                        P, I64, P, P, P, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int32]
             lib.orc_render.restype = ctypes.c_int
+            lib.orc_render_regions.argtypes = [P, I64, I64, I64, P, ctypes.c_int32,
+                                               ctypes.POINTER(OrcCamera), I64, I64, I64, P, I64,
+                                               P, I64, P, P, P, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_int32]
+            lib.orc_render_regions.restype = ctypes.c_int
             lib.orc_pixel_ray.argtypes = [ctypes.POINTER(OrcCamera), I64, I64, I64,
                                           ctypes.c_int32, ctypes.c_int32, P]
             lib.orc_pixel_ray.restype = ctypes.c_int
@@ -96,11 +103,15 @@ def _nbricks(shape_xyz, brick):
 
 
 def render(cube: np.ndarray, tf: np.ndarray, cam: dict, brick=None, mode: str = "ea",
-           pixels=None, amb_alpha: float = 1e-5, amb_steps: float = 1e-4, threads: int = 0):
+           pixels=None, amb_alpha: float = 1e-5, amb_steps: float = 1e-4, threads: int = 0,
+           regions=None):
     """Render with the FP64 oracle.
 
     cube: float32[nz][ny][nx].  brick: (bx, by, bz) or None for monolithic.
     pixels: None for the whole image, else an int array of j*W+i indices.
+    regions: None, or the region of every brick (brick id = ix + nbx*(iy + nby*iz);
+    -1 = not rendered) for the two-level sort-last fold (needs a bricking and
+    emission-absorption mode).
     Returns (rgba, ambiguous_flags, samples): rgba is float64 (H, W, 4) for the
     whole image or (npix, 4) for a pixel list, premultiplied.
     """
@@ -121,9 +132,18 @@ def render(cube: np.ndarray, tf: np.ndarray, cam: dict, brick=None, mode: str = 
     bx, by, bz = brick if brick is not None else (0, 0, 0)
     m = {"ea": 0, "mip": 1}[mode]
     oc = _cam(cam)
-    rc = _load().orc_render(cube.ctypes.data, nx, ny, nz, tfa.ctypes.data, len(tfa),
-                            ctypes.byref(oc), bx, by, bz, m, pix_ptr, npix, out.ctypes.data,
-                            amb.ctypes.data, samples.ctypes.data, amb_alpha, amb_steps, threads)
+    if regions is not None:
+        if brick is None or mode != "ea":
+            raise ValueError("regions need a bricking and emission-absorption mode")
+        reg = np.ascontiguousarray(regions, dtype=np.int32).reshape(-1)
+        rc = _load().orc_render_regions(cube.ctypes.data, nx, ny, nz, tfa.ctypes.data, len(tfa),
+                                        ctypes.byref(oc), bx, by, bz, reg.ctypes.data, len(reg),
+                                        pix_ptr, npix, out.ctypes.data, amb.ctypes.data,
+                                        samples.ctypes.data, amb_alpha, amb_steps, threads)
+    else:
+        rc = _load().orc_render(cube.ctypes.data, nx, ny, nz, tfa.ctypes.data, len(tfa),
+                                ctypes.byref(oc), bx, by, bz, m, pix_ptr, npix, out.ctypes.data,
+                                amb.ctypes.data, samples.ctypes.data, amb_alpha, amb_steps, threads)
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     if pixels is None:

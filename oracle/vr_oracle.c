@@ -177,6 +177,7 @@ typedef struct {
     int64_t nb[3];
     int mode;
     double amb_alpha, amb_steps;
+    const int32_t* region; /* NULL, or the region of each brick (-1: not rendered) */
 } job_t;
 
 static int64_t owner_of(const job_t* J, const double p[3]) {
@@ -195,6 +196,16 @@ static int64_t owner_of(const job_t* J, const double p[3]) {
 
 static void near_tau(const job_t* J, double A, int* amb) {
     if (fabs(A - J->cam->term_alpha) < J->amb_alpha) *amb |= ORC_AMB_TERM;
+}
+
+/* Front-to-back compositing of one sample (premultiplied): the sample's colour
+ * and opacity alpha enter through the transmittance 1 - seg[3] left so far. */
+static void accumulate(double seg[4], const double rgba[4], double alpha) {
+    double w = (1.0 - seg[3]) * alpha;
+    seg[0] += w * rgba[0];
+    seg[1] += w * rgba[1];
+    seg[2] += w * rgba[2];
+    seg[3] += w;
 }
 
 /* over: acc <- acc over seg */
@@ -249,6 +260,68 @@ static void render_pixel(const job_t* J, int i, int j, double out[4], int* amb_o
         goto done;
     }
 
+    if (J->region) {
+        /* Two-level sort-last fold (Sections 2.3.3-2.3.4): each brick's run is
+         * folded into the run of its region (a box of bricks, crossed by the ray
+         * in one piece), which stops taking runs once its opacity reaches tau;
+         * region runs are folded into the pixel, which stops at tau.  Bricks of
+         * region -1 are not rendered. */
+        double acc[4] = {0, 0, 0, 0}, racc[4] = {0, 0, 0, 0}, seg[4] = {0, 0, 0, 0};
+        int64_t cur = -1;
+        int32_t rcur = -1;
+        int seg_done = 0, stopped = 0;
+        for (int64_t k = 0;; ++k) {
+            double s = (double)k * dt;
+            int more = s < L;
+            int64_t b = -1;
+            double p[3];
+            if (more) {
+                for (int a = 0; a < 3; ++a) p[a] = pe[a] + s * d[a];
+                b = owner_of(J, p);
+            }
+            if (!more || b != cur) {
+                /* close the run of brick cur */
+                if (cur >= 0 && J->region[cur] >= 0) {
+                    const int32_t r = J->region[cur];
+                    if (r != rcur) {
+                        if (rcur >= 0) {
+                            near_tau(J, acc[3], &amb);
+                            if (acc[3] < tau) fold(acc, racc);
+                            near_tau(J, acc[3], &amb);
+                            if (acc[3] >= tau) {
+                                stopped = 1;
+                                break;
+                            }
+                        }
+                        racc[0] = racc[1] = racc[2] = racc[3] = 0.0;
+                        rcur = r;
+                    }
+                    near_tau(J, racc[3], &amb);
+                    if (racc[3] < tau) fold(racc, seg);
+                    near_tau(J, racc[3], &amb);
+                }
+                if (!more) break;
+                cur = b;
+                seg[0] = seg[1] = seg[2] = seg[3] = 0.0;
+                seg_done = 0;
+            }
+            if (seg_done || J->region[cur] < 0) continue;
+            double v = trilinear(cube, p);
+            double rgba[4];
+            tf_eval(J->tf, J->ntf, v, rgba);
+            accumulate(seg, rgba, opacity_correct(rgba[3], dt));
+            ++ns;
+            near_tau(J, seg[3], &amb);
+            if (seg[3] >= tau) seg_done = 1;
+        }
+        if (!stopped && rcur >= 0) {
+            near_tau(J, acc[3], &amb);
+            if (acc[3] < tau) fold(acc, racc);
+        }
+        memcpy(out, acc, sizeof(acc));
+        goto done;
+    }
+
     double acc[4] = {0, 0, 0, 0}, seg[4] = {0, 0, 0, 0};
     int64_t cur = -1;
     int seg_done = 0, stopped = 0;
@@ -276,12 +349,7 @@ static void render_pixel(const job_t* J, int i, int j, double out[4], int* amb_o
         double v = trilinear(cube, p);
         double rgba[4];
         tf_eval(J->tf, J->ntf, v, rgba);
-        double alpha = opacity_correct(rgba[3], dt);
-        double w = (1.0 - seg[3]) * alpha;
-        seg[0] += w * rgba[0];
-        seg[1] += w * rgba[1];
-        seg[2] += w * rgba[2];
-        seg[3] += w;
+        accumulate(seg, rgba, opacity_correct(rgba[3], dt));
         ++ns;
         near_tau(J, seg[3], &amb);
         if (seg[3] >= tau) seg_done = 1;
@@ -314,6 +382,7 @@ static void setup_job(job_t* J, const cube_t* cube, const double* tf, int ntf,
     J->mode = mode;
     J->amb_alpha = amb_alpha;
     J->amb_steps = amb_steps;
+    J->region = NULL;
 }
 
 /*
@@ -334,6 +403,44 @@ int orc_render(const float* cube_data, int64_t nx, int64_t ny, int64_t nz,
     int64_t brick[3] = {bx, by, bz};
     job_t J;
     setup_job(&J, &cube, tf, ntf, cam, brick, mode, amb_alpha, amb_steps);
+    const int64_t W = cam->width;
+    const int64_t total = pixels ? npix : W * cam->height;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < total; ++q) {
+        int64_t pix = pixels ? pixels[q] : q;
+        int i = (int)(pix % W), j = (int)(pix / W);
+        int amb = 0;
+        int64_t ns = 0;
+        render_pixel(&J, i, j, out_rgba + 4 * q, &amb, &ns);
+        if (ambiguous) ambiguous[q] = (uint8_t)amb;
+        if (samples) samples[q] = ns;
+    }
+    return 0;
+}
+
+/*
+ * orc_render with the two-level fold: region[b] is the region of brick b
+ * (-1: brick not rendered); n_bricks must match the bricking.  Emission-
+ * absorption only.  Returns 0, or -1 on bad arguments.
+ */
+int orc_render_regions(const float* cube_data, int64_t nx, int64_t ny, int64_t nz,
+                       const double* tf, int32_t ntf, const orc_camera* cam,
+                       int64_t bx, int64_t by, int64_t bz, const int32_t* region, int64_t n_bricks,
+                       const int64_t* pixels, int64_t npix,
+                       double* out_rgba, uint8_t* ambiguous, int64_t* samples,
+                       double amb_alpha, double amb_steps, int32_t nthreads) {
+    if (!cube_data || nx < 2 || ny < 2 || nz < 2 || !tf || ntf < 1 || !cam || !out_rgba || !region) return -1;
+    if (cam->width < 1 || cam->height < 1 || !(cam->step > 0.0)) return -1;
+    if (bx < 1 || by < 1 || bz < 1) return -1;
+    cube_t cube = {cube_data, {nx, ny, nz}};
+    int64_t brick[3] = {bx, by, bz};
+    job_t J;
+    setup_job(&J, &cube, tf, ntf, cam, brick, ORC_MODE_EA, amb_alpha, amb_steps);
+    if (J.nb[0] * J.nb[1] * J.nb[2] != n_bricks) return -1;
+    J.region = region;
     const int64_t W = cam->width;
     const int64_t total = pixels ? npix : W * cam->height;
 #ifdef _OPENMP

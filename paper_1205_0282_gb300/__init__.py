@@ -10,7 +10,9 @@ _EXPORTED = ("VolumeRenderer", "VRError", "VR_OPT_MODE", "VR_OPT_RECT_CULL", "VR
              "VR_OPT_PRECISION", "VR_PRECISION_F32", "VR_PRECISION_F16", "VR_PRECISION_F8", "vr_render_noalloc",
              "vr_brick", "vr_create", "vr_destroy", "vr_get_brick_minmax", "vr_get_stats",
              "vr_last_error", "vr_load_cube", "vr_plan_brick_rects", "vr_render",
-             "vr_reset_stats", "vr_set_camera", "vr_set_option", "vr_set_transfer_function")
+             "vr_reset_stats", "vr_set_camera", "vr_set_option", "vr_set_transfer_function",
+             "vr_kd_partition", "vr_kd_order", "vr_set_region", "vr_region_rect", "vr_plan_region_rect",
+             "vr_render_rect", "vr_composite_subimages")
 
 __all__ = list(_EXPORTED)
 

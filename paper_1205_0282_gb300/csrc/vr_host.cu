@@ -216,6 +216,11 @@ struct vr_ctx {
     int kernel = VR_KERNEL_AUTO;
     int tex_fits = -1;  // -1 unknown, 0/1: the cube fits the layered-texture limits
 
+    // sort-last distribution: the bricks this context renders, [region_lo, region_hi)
+    int32_t region_lo[3] = {0, 0, 0}, region_hi[3] = {0, 0, 0};
+    float4* d_comp = nullptr;  // root fold output when the caller passes a host buffer
+    size_t cap_comp = 0;
+
     Slot slots[kSlots];
     int next_slot = 0;
     vr_stats acc{};
@@ -354,7 +359,8 @@ void free_tex(vr_ctx* c) {
     c->tex_ready = false;
 }
 
-int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int32_t& T, int64_t& n_items) {
+int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32_t& tiles_y, int32_t& T,
+               int64_t& n_items) {
     const vr_camera& cam = c->cam;
     T = use_tma(c) ? vr::kTileTma : vr::kTile;  // the direct and texture marches use 8x8 tiles
     tiles_x = (cam.width + T - 1) / T;
@@ -392,6 +398,9 @@ int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int32_t& 
     s.touched_bytes = 0;
     for (int64_t id = 0; id < c->n_bricks; ++id) {
         int64_t idx[3] = {id % c->nb[0], (id / c->nb[0]) % c->nb[1], id / ((int64_t)c->nb[0] * c->nb[1])};
+        bool inside = true;
+        for (int a = 0; a < 3; ++a) inside = inside && idx[a] >= c->region_lo[a] && idx[a] < c->region_hi[a];
+        if (!inside) continue;
         if (c->skip_empty && c->mode == 0) {
             const float2 mm = (use_tex(c) && c->precision != VR_PRECISION_F32) ? c->h_minmax_q[id] : c->h_minmax[id];
             if (tf_alpha_max(c->tf, mm.x, mm.y) == 0.0) {
@@ -410,6 +419,12 @@ int plan_frame(vr_ctx* c, Slot& s, int32_t& tiles_x, int32_t& tiles_y, int32_t& 
             pb.rect[2] = cam.width - 1;
             pb.rect[3] = cam.height - 1;
         }
+        // only the output window's pixels are computed
+        pb.rect[0] = std::max(pb.rect[0], win[0]);
+        pb.rect[1] = std::max(pb.rect[1], win[1]);
+        pb.rect[2] = std::min(pb.rect[2], win[2]);
+        pb.rect[3] = std::min(pb.rect[3], win[3]);
+        if (pb.rect[2] < pb.rect[0] || pb.rect[3] < pb.rect[1]) continue;
         // Along any ray from the eye each axis index moves monotonically away from
         // the eye's index, so sum |b - e| strictly increases from one brick to the
         // next: sorting by it is a valid front-to-back order for every ray.
@@ -520,6 +535,7 @@ void vr_destroy(vr_ctx* c) {
     cudaFree(c->d_tmaps);
     free_tex(c);
     cudaFree(c->d_minmax);
+    cudaFree(c->d_comp);
     delete c;
 }
 
@@ -589,6 +605,10 @@ int vr_brick(vr_ctx* c, int32_t bx, int32_t by, int32_t bz) {
     VR_CUDA(c, vr::launch_brick_minmax(c->d_cube, c->nx_pad, n32, c->B, c->nb, c->d_minmax, 0));
     c->h_minmax.resize(total);
     VR_CUDA(c, cudaMemcpy(c->h_minmax.data(), c->d_minmax, total * sizeof(float2), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < 3; ++a) {
+        c->region_lo[a] = 0;
+        c->region_hi[a] = c->nb[a];
+    }
     c->bricked = true;
     return VR_OK;
 }
@@ -803,11 +823,13 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
     }
 }
 
-int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
-    if (!c) return VR_EINVAL;
-    if (!c->d_cube || !c->bricked || !c->tf_set || !c->cam_set)
-        return fail(c, VR_ESTATE, "vr_render needs vr_load_cube, vr_brick, vr_set_transfer_function and vr_set_camera first");
-    if (!out_rgba) return fail(c, VR_EINVAL, "null output");
+}  // extern "C"
+
+namespace {
+
+// One frame into the output window win = {x0, y0, x1, y1} (inclusive) of the image;
+// out_rgba holds the window's pixels row-major.
+int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[4]) {
     VR_CUDA(c, cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream_ptr;
     cudaPointerAttributes attr;
@@ -830,11 +852,11 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
                                   "VR_KERNEL_TEX or VR_KERNEL_AUTO on a cube within the texture limits)");
     if (use_tma(c) && (rc = prepare_tma(c))) return rc;
     if (use_tex(c) && (rc = prepare_tex(c))) return rc;
-    rc = plan_frame(c, s, tiles_x, tiles_y, T, n_items);
+    rc = plan_frame(c, s, win, tiles_x, tiles_y, T, n_items);
     if (rc) return rc;
     s.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
-    const size_t img_px = (size_t)c->cam.width * c->cam.height;
+    const size_t img_px = (size_t)(win[2] - win[0] + 1) * (size_t)(win[3] - win[1] + 1);
 
     if ((rc = grow_device(c, s.d_items, s.dcap_items, (size_t)std::max<int64_t>(n_items, 1)))) return rc;
     if ((rc = grow_device(c, s.d_tile_start, s.dcap_tiles, (size_t)n_tiles + 1))) return rc;
@@ -902,6 +924,10 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     p.tile_start = s.d_tile_start;
     p.frags = s.d_frags;
     p.out = out_on_device ? reinterpret_cast<float4*>(out_rgba) : s.d_img;
+    p.out_x0 = win[0];
+    p.out_y0 = win[1];
+    p.out_w = win[2] - win[0] + 1;
+    p.out_h = win[3] - win[1] + 1;
     p.stats = s.d_stats;
 
     VR_CUDA(c, cudaEventRecord(s.ev_begin, st));
@@ -931,6 +957,148 @@ int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
     s.d2h_bytes = (int64_t)sizeof(vr::Stats) + (out_on_device ? 0 : (int64_t)(img_px * sizeof(float4)));
     if (!out_on_device) {
         VR_CUDA(c, cudaMemcpyAsync(out_rgba, s.d_img, img_px * sizeof(float4), cudaMemcpyDeviceToHost, st));
+        VR_CUDA(c, cudaStreamSynchronize(st));
+    }
+    return VR_OK;
+}
+
+int render_checks(vr_ctx* c, const float* out_rgba) {
+    if (!c) return VR_EINVAL;
+    if (!c->d_cube || !c->bricked || !c->tf_set || !c->cam_set)
+        return fail(c, VR_ESTATE, "vr_render needs vr_load_cube, vr_brick, vr_set_transfer_function and vr_set_camera first");
+    if (!out_rgba) return fail(c, VR_EINVAL, "null output");
+    return VR_OK;
+}
+
+// Rendering rectangle of the brick range [lo, hi) (inclusive pixel bounds; x1 < x0
+// when no pixel can see it).
+void region_rect(const vr_camera& cam, const Basis& b, const int64_t n[3], const int32_t B[3],
+                 const int32_t lo[3], const int32_t hi[3], int32_t rect[4]) {
+    double blo[3], bhi[3];
+    for (int a = 0; a < 3; ++a) {
+        blo[a] = (double)lo[a] * B[a];
+        bhi[a] = std::min((double)hi[a] * B[a], (double)(n[a] - 1));
+    }
+    box_rect(cam, b, blo, bhi, rect);
+}
+
+}  // namespace
+
+extern "C" {
+
+int vr_render(vr_ctx* c, float* out_rgba, void* stream_ptr) {
+    int rc = render_checks(c, out_rgba);
+    if (rc) return rc;
+    const int32_t win[4] = {0, 0, c->cam.width - 1, c->cam.height - 1};
+    return render_impl(c, out_rgba, stream_ptr, win);
+}
+
+int vr_render_rect(vr_ctx* c, const int32_t rect[4], float* out_rgba, void* stream_ptr) {
+    int rc = render_checks(c, out_rgba);
+    if (rc) return rc;
+    if (!rect) return fail(c, VR_EINVAL, "null rect");
+    if (rect[2] < rect[0] || rect[3] < rect[1]) return VR_OK;  // empty: nothing to render
+    if (rect[0] < 0 || rect[1] < 0 || rect[2] >= c->cam.width || rect[3] >= c->cam.height)
+        return fail(c, VR_EINVAL, "rect outside the image");
+    return render_impl(c, out_rgba, stream_ptr, rect);
+}
+
+int vr_set_region(vr_ctx* c, const int32_t lo[3], const int32_t hi[3]) {
+    if (!c) return VR_EINVAL;
+    if (!c->bricked) return fail(c, VR_ESTATE, "vr_set_region needs vr_brick first");
+    if (!lo || !hi) return fail(c, VR_EINVAL, "null region");
+    for (int a = 0; a < 3; ++a)
+        if (lo[a] < 0 || hi[a] > c->nb[a] || lo[a] >= hi[a]) return fail(c, VR_EINVAL, "bad brick range");
+    for (int a = 0; a < 3; ++a) {
+        c->region_lo[a] = lo[a];
+        c->region_hi[a] = hi[a];
+    }
+    return VR_OK;
+}
+
+int vr_region_rect(vr_ctx* c, int32_t rect[4]) {
+    if (!c) return VR_EINVAL;
+    if (!c->bricked || !c->cam_set) return fail(c, VR_ESTATE, "vr_region_rect needs vr_brick and vr_set_camera first");
+    if (!rect) return fail(c, VR_EINVAL, "null rect");
+    region_rect(c->cam, c->basis, c->n, c->B, c->region_lo, c->region_hi, rect);
+    return VR_OK;
+}
+
+int vr_plan_region_rect(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz, const int32_t B[3],
+                        const int32_t lo[3], const int32_t hi[3], int32_t rect[4]) {
+    if (!cam || !B || !lo || !hi || !rect || !camera_valid(*cam)) return VR_EINVAL;
+    if (nx < 2 || ny < 2 || nz < 2 || B[0] < 1 || B[1] < 1 || B[2] < 1) return VR_EINVAL;
+    const int64_t n[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a)
+        if (lo[a] < 0 || lo[a] >= hi[a] || hi[a] > bricks_along(n[a], B[a])) return VR_EINVAL;
+    Basis b;
+    if (!make_basis(*cam, b)) return VR_EINVAL;
+    region_rect(*cam, b, n, B, lo, hi, rect);
+    return VR_OK;
+}
+
+int vr_kd_partition(int64_t nx, int64_t ny, int64_t nz, const int32_t B[3], int32_t n_parts,
+                    int32_t* ranges) {
+    if (!B || !ranges || n_parts < 1 || nx < 2 || ny < 2 || nz < 2 || B[0] < 1 || B[1] < 1 || B[2] < 1)
+        return VR_EINVAL;
+    const int64_t n[3] = {nx, ny, nz};
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) total *= bricks_along(n[a], B[a]);
+    if (n_parts > total) return VR_EINVAL;
+    return vr::kd_partition(n, B, n_parts, ranges) ? VR_OK : VR_EINVAL;
+}
+
+int vr_kd_order(int64_t nx, int64_t ny, int64_t nz, const int32_t B[3], int32_t n_parts, const double eye[3],
+                int32_t* order) {
+    if (!B || !eye || !order || n_parts < 1 || nx < 2 || ny < 2 || nz < 2 || B[0] < 1 || B[1] < 1 || B[2] < 1)
+        return VR_EINVAL;
+    const int64_t n[3] = {nx, ny, nz};
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) total *= bricks_along(n[a], B[a]);
+    if (n_parts > total) return VR_EINVAL;
+    return vr::kd_order(n, B, n_parts, eye, order) ? VR_OK : VR_EINVAL;
+}
+
+int vr_composite_subimages(vr_ctx* c, int32_t n, const float* const* images, const int32_t* rects,
+                           float* out_rgba, void* stream_ptr) {
+    if (!c) return VR_EINVAL;
+    if (!c->cam_set) return fail(c, VR_ESTATE, "vr_composite_subimages needs vr_set_camera first");
+    if (n < 0 || n > vr::kMaxSubimages) return fail(c, VR_EINVAL, "1..256 sub-images");
+    if (!out_rgba || (n > 0 && (!images || !rects))) return fail(c, VR_EINVAL, "null argument");
+    VR_CUDA(c, cudaSetDevice(c->device));
+    const int32_t W = c->cam.width, H = c->cam.height;
+    vr::SubimageList L;
+    std::memset(&L, 0, sizeof(L));
+    for (int32_t k = 0; k < n; ++k) {
+        const int32_t* r = rects + 4 * k;
+        if (r[2] < r[0] || r[3] < r[1]) continue;  // an empty sub-image
+        if (r[0] < 0 || r[1] < 0 || r[2] >= W || r[3] >= H) return fail(c, VR_EINVAL, "rect outside the image");
+        if (!images[k]) return fail(c, VR_EINVAL, "null sub-image");
+        vr::SubimageRef& e = L.s[L.n++];
+        e.data = reinterpret_cast<const float4*>(images[k]);
+        e.x0 = r[0];
+        e.y0 = r[1];
+        e.x1 = r[2];
+        e.y1 = r[3];
+    }
+    cudaStream_t st = (cudaStream_t)stream_ptr;
+    cudaPointerAttributes attr;
+    bool out_on_device = false;
+    if (cudaPointerGetAttributes(&attr, out_rgba) == cudaSuccess)
+        out_on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    else
+        cudaGetLastError();
+    const size_t px = (size_t)W * H;
+    float4* dst = reinterpret_cast<float4*>(out_rgba);
+    if (!out_on_device) {
+        int rc = retire_all(c);  // d_comp may still be read by an earlier call's copy
+        if (rc) return rc;
+        if ((rc = grow_device(c, c->d_comp, c->cap_comp, px))) return rc;
+        dst = c->d_comp;
+    }
+    VR_CUDA(c, vr::launch_subimage_composite(L, W, H, (float)c->cam.term_alpha, dst, st));
+    if (!out_on_device) {
+        VR_CUDA(c, cudaMemcpyAsync(out_rgba, dst, px * sizeof(float4), cudaMemcpyDeviceToHost, st));
         VR_CUDA(c, cudaStreamSynchronize(st));
     }
     return VR_OK;

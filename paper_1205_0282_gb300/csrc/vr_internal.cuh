@@ -86,8 +86,22 @@ struct FrameParams {
     const float* brick_scale;   // FP8: per-brick scale (value = code * scale)
     const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
     float4* frags;
-    float4* out;
+    float4* out;                // image window: pixel (i, j) of the frame goes to
+    int32_t out_x0, out_y0;     // out[(j - out_y0) * out_w + (i - out_x0)] if it lies in
+    int32_t out_w, out_h;       // [out_x0, out_x0 + out_w) x [out_y0, out_y0 + out_h)
     Stats* stats;
+};
+
+// Sub-images for the root's sort-last fold (vr_shard.cu): a rectangle
+// [x0, x1] x [y0, y1] of the frame, row-major RGBA.
+constexpr int kMaxSubimages = 256;
+struct SubimageRef {
+    const float4* data;
+    int32_t x0, y0, x1, y1;
+};
+struct SubimageList {
+    int32_t n;
+    SubimageRef s[kMaxSubimages];
 };
 
 // Launchers (vr_kernels.cu).
@@ -110,5 +124,12 @@ cudaError_t make_tma_maps(const float* a, int64_t nx, int64_t ny, int64_t nz, in
 cudaError_t launch_transpose_xzy(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
                                  float* b, int64_t b_pitch, cudaStream_t s);
 cudaError_t launch_composite(const FrameParams& p, cudaStream_t s);
+
+// k-d distribution and the root's fold (vr_shard.cu).  ranges: parts x 6 int32
+// (brick lo x, y, z then hi x, y, z, half-open), leaves in tree order.
+bool kd_partition(const int64_t n[3], const int32_t B[3], int32_t parts, int32_t* ranges);
+bool kd_order(const int64_t n[3], const int32_t B[3], int32_t parts, const double eye[3], int32_t* order);
+cudaError_t launch_subimage_composite(const SubimageList& L, int32_t width, int32_t height, float tau,
+                                      float4* out, cudaStream_t s);
 
 }  // namespace vr

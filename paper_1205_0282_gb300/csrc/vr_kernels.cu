@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(256) composite_kernel(const FrameParams p) {
             acc = make_float4(c.x * c.w, c.y * c.w, c.z * c.w, c.w);
         }
     }
-    p.out[(int64_t)j * p.width + i] = acc;
+    const int wi = i - p.out_x0, wj = j - p.out_y0;
+    if (wi >= 0 && wi < p.out_w && wj >= 0 && wj < p.out_h) p.out[(int64_t)wj * p.out_w + wi] = acc;
 }
 
 cudaError_t launch_composite(const FrameParams& p, cudaStream_t s) {

@@ -296,6 +296,9 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
     p.tile_start = reinterpret_cast<const int32_t*>(d_tiles);
     p.frags = reinterpret_cast<float4*>(d_frags);
     p.out = reinterpret_cast<float4*>(out_rgba);
+    p.out_x0 = p.out_y0 = 0;
+    p.out_w = p.width;
+    p.out_h = p.height;
     p.stats = reinterpret_cast<vr::Stats*>(d_stats);
 
     // The counters must start at zero; the rest of the scratch is fully rewritten.

@@ -68,7 +68,9 @@ class vr_stats(ctypes.Structure):
 # The exported symbols, in header order (tests check them against include/vr.h).
 EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_brick", "vr_set_transfer_function",
            "vr_set_camera", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
-           "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_render_noalloc", "vr_last_error"]
+           "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_kd_partition", "vr_kd_order",
+           "vr_set_region", "vr_region_rect", "vr_plan_region_rect", "vr_render_rect",
+           "vr_composite_subimages", "vr_render_noalloc", "vr_last_error"]
 
 
 def _load():
@@ -91,6 +93,13 @@ def _load():
     lib.vr_get_brick_minmax.argtypes = [P, P, I64]
     lib.vr_plan_brick_rects.argtypes = [ctypes.POINTER(vr_camera), I64, I64, I64, I32, I32, I32,
                                         P, I64]
+    lib.vr_kd_partition.argtypes = [I64, I64, I64, P, I32, P]
+    lib.vr_kd_order.argtypes = [I64, I64, I64, P, I32, P, P]
+    lib.vr_set_region.argtypes = [P, P, P]
+    lib.vr_region_rect.argtypes = [P, P]
+    lib.vr_plan_region_rect.argtypes = [ctypes.POINTER(vr_camera), I64, I64, I64, P, P, P, P]
+    lib.vr_render_rect.argtypes = [P, P, P, P]
+    lib.vr_composite_subimages.argtypes = [P, I32, P, P, P, P]
     lib.vr_render_noalloc.argtypes = [P, I64, I64, I64, I32, I32, I32, P, I32,
                                       ctypes.POINTER(vr_camera), P, P]
     lib.vr_last_error.argtypes = [P]
@@ -227,6 +236,85 @@ def vr_plan_brick_rects(cam: dict, shape_xyz, brick) -> np.ndarray:
     return rects
 
 
+def _i32(v, n):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int32).reshape(-1))
+    if a.size != n:
+        raise ValueError(f"expected {n} integers")
+    return a
+
+
+def vr_kd_partition(shape_xyz, brick, n_parts: int) -> np.ndarray:
+    """Host-only: int32 (n_parts, 6) brick ranges (lo xyz, hi xyz) of the k-d leaves."""
+    B = _i32(brick, 3)
+    out = np.zeros((n_parts, 6), dtype=np.int32)
+    rc = _lib.vr_kd_partition(*shape_xyz, B.ctypes.data, int(n_parts), out.ctypes.data)
+    if rc != VR_OK:
+        raise VRError(rc, "vr_kd_partition rejected its arguments")
+    return out
+
+
+def vr_kd_order(shape_xyz, brick, n_parts: int, eye) -> np.ndarray:
+    """Host-only: leaf numbers front to back as seen from ``eye``."""
+    B = _i32(brick, 3)
+    e = np.ascontiguousarray(np.asarray(eye, dtype=np.float64).reshape(3))
+    out = np.zeros(n_parts, dtype=np.int32)
+    rc = _lib.vr_kd_order(*shape_xyz, B.ctypes.data, int(n_parts), e.ctypes.data, out.ctypes.data)
+    if rc != VR_OK:
+        raise VRError(rc, "vr_kd_order rejected its arguments")
+    return out
+
+
+def vr_set_region(ctx, lo, hi) -> None:
+    lo_, hi_ = _i32(lo, 3), _i32(hi, 3)
+    _check(ctx, _lib.vr_set_region(ctx, lo_.ctypes.data, hi_.ctypes.data))
+
+
+def vr_region_rect(ctx) -> np.ndarray:
+    r = np.zeros(4, dtype=np.int32)
+    _check(ctx, _lib.vr_region_rect(ctx, r.ctypes.data))
+    return r
+
+
+def vr_plan_region_rect(cam: dict, shape_xyz, brick, lo, hi) -> np.ndarray:
+    """Host-only: rendering rectangle (x0, y0, x1, y1) of the brick range [lo, hi)."""
+    B, lo_, hi_ = _i32(brick, 3), _i32(lo, 3), _i32(hi, 3)
+    r = np.zeros(4, dtype=np.int32)
+    c = make_camera(cam)
+    rc = _lib.vr_plan_region_rect(ctypes.byref(c), *shape_xyz, B.ctypes.data, lo_.ctypes.data,
+                                  hi_.ctypes.data, r.ctypes.data)
+    if rc != VR_OK:
+        raise VRError(rc, "vr_plan_region_rect rejected its arguments")
+    return r
+
+
+def vr_render_rect(ctx, rect, out, stream=None) -> None:
+    """Render only the pixels of ``rect`` into ``out`` (float32 (rows, cols, 4))."""
+    r = _i32(rect, 4)
+    addr, keep = _ptr(out)
+    on_device = hasattr(out, "is_cuda") and out.is_cuda
+    _check(ctx, _lib.vr_render_rect(ctx, r.ctypes.data, addr, _stream_handle(stream) if on_device else None))
+
+
+def vr_composite_subimages(ctx, images, rects, out, stream=None) -> None:
+    """Front-to-back 'over' fold of sub-images (CUDA tensors, or None for an empty
+    rect) with their rects into ``out`` (float32 (H, W, 4))."""
+    n = len(images)
+    ptrs = (ctypes.c_void_p * max(n, 1))()
+    keep = []
+    for k, im in enumerate(images):
+        if im is None:
+            ptrs[k] = None
+            continue
+        a, kk = _ptr(im)
+        ptrs[k] = a
+        keep.append(kk)
+    R = np.ascontiguousarray(np.asarray(rects, dtype=np.int32).reshape(n, 4)) if n else np.zeros((1, 4), np.int32)
+    addr, keep_out = _ptr(out)
+    on_device = hasattr(out, "is_cuda") and out.is_cuda
+    _check(ctx, _lib.vr_composite_subimages(ctx, n, ctypes.cast(ptrs, ctypes.c_void_p), R.ctypes.data, addr,
+                                            _stream_handle(stream) if on_device else None))
+
+
 def vr_render_noalloc(cube, brick, points, cam: dict, out, stream=None) -> None:
     """Allocation-free render: ``cube`` and ``out`` are CUDA tensors (float32
     (nz, ny, nx) and (H, W, 4)); scratch lives in the library's static device
@@ -315,3 +403,30 @@ class VolumeRenderer:
 
     def brick_minmax(self):
         return vr_get_brick_minmax(self.ctx, self.n_bricks)
+
+    def set_region(self, lo, hi):
+        vr_set_region(self.ctx, lo, hi)
+
+    def region_rect(self):
+        return vr_region_rect(self.ctx)
+
+    def render_rect(self, rect, out=None, stream=None):
+        """Render the pixels of ``rect``; returns ``out`` (allocates a CUDA tensor
+        of the rect's size if None; None for an empty rect)."""
+        x0, y0, x1, y1 = (int(v) for v in rect)
+        if x1 < x0 or y1 < y0:
+            return None
+        if out is None:
+            import torch
+            out = torch.empty((y1 - y0 + 1, x1 - x0 + 1, 4), dtype=torch.float32, device="cuda")
+        vr_render_rect(self.ctx, rect, out, stream)
+        return out
+
+    def composite(self, images, rects, out=None, stream=None):
+        """Root fold of sub-images (front to back) into a full frame."""
+        if out is None:
+            import torch
+            out = torch.empty((self.camera["height"], self.camera["width"], 4),
+                              dtype=torch.float32, device="cuda")
+        vr_composite_subimages(self.ctx, images, rects, out, stream)
+        return out

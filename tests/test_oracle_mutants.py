@@ -45,6 +45,11 @@ MUTANTS = {
     "closed sampling interval": ("if (!(s < L)) break;\n        double p[3];\n        for (int a = 0; a < 3; ++a) p[a] = pe[a] + s * d[a];\n        int64_t b",
                                  "if (s > L) break;\n        double p[3];\n        for (int a = 0; a < 3; ++a) p[a] = pe[a] + s * d[a];\n        int64_t b"),
     "aspect ratio dropped": ("* b->tan_half * b->aspect;", "* b->tan_half;"),
+    "region runs folded past termination": ("if (racc[3] < tau) fold(racc, seg);", "fold(racc, seg);"),
+    "region run not restarted": ("racc[0] = racc[1] = racc[2] = racc[3] = 0.0;", "(void)racc;"),
+    "region folded behind the pixel": ("if (acc[3] < tau) fold(acc, racc);\n                            near_tau",
+                                       "if (acc[3] < tau) { double t_[4]; memcpy(t_, racc, sizeof(t_)); "
+                                       "fold(t_, acc); memcpy(acc, t_, sizeof(t_)); }\n                            near_tau"),
 }
 
 
@@ -59,6 +64,9 @@ def _pin_calls():
         ("opengl", pins.test_camera_matches_opengl_matrices),
         ("brute-mono", lambda: pins.test_brute_force_tiny(1, (4, 4, 4), None, 0.99, 0.6)),
         ("brute-brick", lambda: pins.test_brute_force_tiny(3, (4, 3, 4), (1, 2, 3), 0.99, 0.95)),
+        ("region-single", pins.test_region_fold_with_a_single_region_is_the_bricked_render),
+        ("region-over", lambda: pins.test_region_fold_is_the_over_of_the_region_renders(2)),
+        ("region-bound", pins.test_region_termination_bound),
     ]
     return calls
 
@@ -68,8 +76,8 @@ def _swap_in(so_path):
     oracle package use it."""
     real = oracle._load()
     lib = ctypes.CDLL(str(so_path))
-    for fn in ("orc_render", "orc_pixel_ray", "orc_pixel_bricks", "orc_brick_minmax",
-               "orc_tf_alpha_max"):
+    for fn in ("orc_render", "orc_render_regions", "orc_pixel_ray", "orc_pixel_bricks",
+               "orc_brick_minmax", "orc_tf_alpha_max"):
         getattr(lib, fn).argtypes = getattr(real, fn).argtypes
         getattr(lib, fn).restype = getattr(real, fn).restype
     oracle._lib = lib

@@ -490,3 +490,90 @@ def test_fp8_storage_error_bound():
     assert err.max() > 0
     # relative error of the normal range is well inside the bound on average
     assert np.median(err / np.maximum(np.abs(c), 1e-30)) < 2.0 ** -5
+
+
+# ------------------------------------------------------- two-level (region) fold
+
+def _region_map(nb, split_axis, split_at):
+    """Two regions of a brick grid nb (x, y, z), split at brick index split_at."""
+    ids = np.arange(nb[0] * nb[1] * nb[2])
+    idx = np.stack([ids % nb[0], (ids // nb[0]) % nb[1], ids // (nb[0] * nb[1])], axis=1)
+    return (idx[:, split_axis] >= split_at).astype(np.int32)
+
+
+def _over(images):
+    """Front-to-back 'over' fold of RGBA images (no termination)."""
+    acc = np.zeros_like(images[0])
+    for im in images:
+        acc = acc + (1.0 - acc[..., 3:4]) * im
+    return acc
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.99])
+def test_region_fold_with_one_region_per_brick_is_the_bricked_render(tau):
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    brick = (16, 16, 16)
+    nb = [(64 - 1 + 16 - 1) // 16] * 3
+    for cam in synth.tiny_views(width=40, height=36, term_alpha=tau)[:2]:
+        ref, amb_r, _ = oracle.render(cube, tf, cam, brick=brick)
+        got, amb_g, _ = oracle.render(cube, tf, cam, brick=brick,
+                                      regions=np.arange(nb[0] * nb[1] * nb[2], dtype=np.int32))
+        assert np.array_equal(got, ref) and np.array_equal(amb_g, amb_r)
+
+
+def test_region_fold_with_a_single_region_is_the_bricked_render():
+    cube = synth.tiny_cube()
+    tf = synth.make_tf([0.0, 0.0, 0.3, 0.6, 0.8, 0.9, 0.95, 0.99])   # opaque: termination active
+    brick = (8, 8, 8)
+    cam = synth.tiny_views(width=40, height=36)[0]
+    ref, _, _ = oracle.render(cube, tf, cam, brick=brick)
+    got, _, _ = oracle.render(cube, tf, cam, brick=brick, regions=np.zeros(8 ** 3, dtype=np.int32))
+    assert np.array_equal(got, ref)
+
+
+def _three_regions(nb, axis):
+    """Three slabs of a brick grid nb (x, y, z) along axis: bricks [0,1), [1,3), [3,...)."""
+    ids = np.arange(nb[0] * nb[1] * nb[2])
+    idx = np.stack([ids % nb[0], (ids // nb[0]) % nb[1], ids // (nb[0] * nb[1])], axis=1)[:, axis]
+    return np.where(idx < 1, 0, np.where(idx < 3, 1, 2)).astype(np.int32)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_region_fold_is_the_over_of_the_region_renders(axis):
+    """Termination off: rendering each of three slab regions alone (other bricks
+    excluded) and folding the images front to back equals the full render
+    (associativity, Section 2.3.3); the eye lies on the low side, so the low slab
+    is in front."""
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    brick = (16, 16, 16)
+    reg = _three_regions((4, 4, 4), axis)
+    eye = [31.5, 31.5, 31.5]
+    eye[axis] = -60.0
+    target = [31.5, 31.5, 31.5]
+    up = (0.0, 1.0, 0.0) if axis != 1 else (0.0, 0.0, 1.0)
+    cam = synth.camera(eye, target, up, 40.0, 40, 36, term_alpha=1.0)
+    full, _, _ = oracle.render(cube, tf, cam, brick=brick)
+    three, _, _ = oracle.render(cube, tf, cam, brick=brick, regions=reg)
+    parts = [oracle.render(cube, tf, cam, brick=brick, regions=np.where(reg == k, 0, -1))[0] for k in range(3)]
+    np.testing.assert_allclose(three, full, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(_over(parts), full, rtol=0, atol=1e-12)
+    assert np.abs(_over(parts[::-1]) - full).max() > 1e-3   # the order matters
+    assert min(p[..., 3].max() for p in parts) > 0.02   # every slab contributes
+
+
+def test_region_termination_bound():
+    """Termination at tau < 1: each region stops on its own, so the two-level
+    result differs from the bricked one by at most 1 - tau per channel, and the
+    difference is not vacuous for an opaque transfer function."""
+    cube = synth.tiny_cube()
+    tf = synth.make_tf([0.0, 0.0, 0.3, 0.6, 0.8, 0.9, 0.95, 0.99])
+    brick = (8, 8, 8)
+    reg = _region_map((8, 8, 8), 2, 3)
+    worst = 0.0
+    for cam in synth.tiny_views(width=40, height=36)[:3]:
+        ref, _, _ = oracle.render(cube, tf, cam, brick=brick)
+        got, _, _ = oracle.render(cube, tf, cam, brick=brick, regions=reg)
+        d = np.abs(got - ref)
+        assert d.max() <= 1.0 - cam["term_alpha"] + 1e-12
+        worst = max(worst, d.max())
+    assert worst > 1e-4
