@@ -198,10 +198,12 @@ def recorded_traffic(kernel, workload_name):
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False):
+def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False, regions=None):
     """Samples/s of the FP64 oracle on centre crops of successive poses, for
     about `seconds` of wall time (at least one crop).  With keep, also returns
-    the crops as (camera, pixel indices, RGBA) for the image-quality check."""
+    the crops as (camera, pixel indices, RGBA) for the image-quality check.
+    regions: the k-d leaf of every brick when frames are rendered as virtual
+    ranks (the oracle then folds per leaf first, as the ranks do)."""
     import oracle
     total = 0
     t0 = time.perf_counter()
@@ -214,7 +216,8 @@ def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False):
         jj, ii = np.meshgrid(np.arange(y0, y0 + crop), np.arange(x0, x0 + crop), indexing="ij")
         pix = (jj * W + ii).reshape(-1)
         ref, amb, ns = oracle.render(cube, tf, cam, brick=brick, pixels=pix,
-                                     amb_alpha=QUALITY_AMB_ALPHA, amb_steps=QUALITY_AMB_STEPS)
+                                     amb_alpha=QUALITY_AMB_ALPHA, amb_steps=QUALITY_AMB_STEPS,
+                                     regions=regions)
         total += int(ns.sum())
         crops.append((cam, pix, ref, amb) if keep else None)
         k += 7
@@ -460,7 +463,16 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        rate, secs, n_crops, crops = oracle_rate(cube, tf, poses, spec["brick"], args.cpu_seconds, keep=True)
+        regions = None
+        if args.shard > 1:
+            nb = [(n - 1 + b - 1) // b for n, b in zip(spec["shape_xyz"], spec["brick"])]
+            ids = np.arange(nb[0] * nb[1] * nb[2])
+            idx = np.stack([ids % nb[0], (ids // nb[0]) % nb[1], ids // (nb[0] * nb[1])], axis=1)
+            regions = np.zeros(len(ids), dtype=np.int32)
+            for j, lf in enumerate(leaves):
+                regions[((idx >= lf[:3]) & (idx < lf[3:])).all(axis=1)] = j
+        rate, secs, n_crops, crops = oracle_rate(cube, tf, poses, spec["brick"], args.cpu_seconds, keep=True,
+                                                 regions=regions)
         cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{n_crops} centre crops of 64x64 pixels on successive orbit poses, "
                          f"{secs:.1f} s of FP64 CPU work"}
