@@ -82,6 +82,9 @@ typedef struct {
     int64_t chunks_staged;   /* TMA march: sample chunks read from TMA-staged shared memory */
     int64_t chunks_direct;   /* TMA march: chunks whose footprint did not fit the staged box
                                 (read through L1 instead) */
+    int64_t bricks_uploaded; /* out-of-core: bricks copied host->device (their bytes are in
+                                h2d_bytes) */
+    int64_t bricks_cached;   /* out-of-core: rendered bricks found resident in the device cache */
     int32_t device_errors;   /* OR of device-side error flags seen (0 = none; 1 = a sample
                                 outside its staged box was clamped; 2 = a bounded wait on a
                                 TMA copy gave up and the frame is invalid) */
@@ -130,6 +133,14 @@ typedef struct {
                                 vr_render returns VR_EINVAL otherwise.  Changing it waits
                                 for frames in flight and rebuilds the copies on the next
                                 render (F8 also after vr_brick). */
+#define VR_OPT_DEVICE_BUDGET 6 /* out-of-core contexts (vr_load_cube_host): bytes of device
+                                memory for the brick cache, each brick taking
+                                (bx+1)(by+1)(bz+1) floats; default (and any value <= 0):
+                                room for every brick.  A frame whose rendered bricks fit
+                                keeps bricks resident across frames (least recently used
+                                evicted); a larger frame streams its bricks through the
+                                cache in two alternating halves.  Needs room for 2 bricks.
+                                Takes effect at the next vr_brick. */
 #define VR_PRECISION_F32 0
 #define VR_PRECISION_F16 1
 #define VR_PRECISION_F8 2
@@ -152,6 +163,22 @@ void vr_destroy(vr_ctx* ctx);
  * Errors: VR_EINVAL, VR_ENOMEM, VR_ECUDA.
  */
 int vr_load_cube(vr_ctx* ctx, const float* data, int64_t nx, int64_t ny, int64_t nz);
+
+/*
+ * Out-of-core load (no counterpart in the paper, which keeps the cube in GPU
+ * memory): the cube stays in host memory.  data: host memory, float32[nz][ny][nx];
+ * the context reads it at every vr_brick, so it must stay valid and unchanged
+ * until the context is destroyed or another cube is loaded.  vr_brick then copies
+ * it brick by brick into a pinned host brick store (brick b as a dense
+ * (bx+1)(by+1)(bz+1) block holding its voxels and apron, zero beyond the cube)
+ * and computes the brick ranges on the host; vr_render copies the bricks a frame
+ * needs into a device cache (VR_OPT_DEVICE_BUDGET) with cudaMemcpyAsync on a side
+ * stream, overlapped with the ray march of bricks already resident, and marches
+ * them with the direct kernel (the texture and TMA paths need the whole cube on
+ * the device).  Images are those of vr_load_cube with the same data.
+ * Errors: VR_EINVAL (bad sizes, device memory), VR_ECUDA.
+ */
+int vr_load_cube_host(vr_ctx* ctx, const float* data, int64_t nx, int64_t ny, int64_t nz);
 
 /*
  * Partition the loaded cube into bricks of bx x by x bz voxels (Section 2.3.1;

@@ -36,11 +36,15 @@ struct Slot {
     size_t cap_frame = 0, dcap_frame = 0;
     vr::Stats* d_stats = nullptr;
     vr::Stats* h_stats = nullptr;
+    int32_t* h_slot_of = nullptr;  // out-of-core: cache slot of each brick (pinned)
+    int32_t* d_slot_of = nullptr;
+    size_t cap_slot_of = 0, dcap_slot_of = 0;
     cudaEvent_t ev_begin = nullptr, ev_march0 = nullptr, ev_march1 = nullptr, ev_end = nullptr;
     bool pending = false;
     // host-side facts of the frame in flight
     int64_t items = 0, bricks_rendered = 0, bricks_skipped = 0, touched_bytes = 0;
     int64_t h2d_bytes = 0, d2h_bytes = 0, launches = 0, fragments = 0;
+    int64_t bricks_uploaded = 0, bricks_cached = 0;
     double plan_ms = 0.0;
 };
 
@@ -90,20 +94,21 @@ int64_t bricks_along(int64_t n, int64_t B) { return (n - 1 + B - 1) / B; }
 // vertices, take their bounding rectangle).  Pixel (i, j) has its centre at
 // ((i+.5)/W, (j+.5)/H) of the image; the rectangle is widened by one pixel so that
 // rounding can never drop a pixel whose ray touches the box.  Returns false if the
-// rectangle is empty after clipping.  A box reaching behind the eye plane maps to
-// the whole image.
+// rectangle is empty after clipping, or if the whole box lies behind the eye plane
+// (every ray leaves the eye forward along f).  A box reaching across the eye plane
+// maps to the whole image.
 bool box_rect(const vr_camera& c, const Basis& b, const double lo[3], const double hi[3],
               int32_t rect[4]) {
     double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
     bool behind = false;
+    int back = 0;
     for (int k = 0; k < 8; ++k) {
         double P[3] = {(k & 1) ? hi[0] : lo[0], (k & 2) ? hi[1] : lo[1], (k & 4) ? hi[2] : lo[2]};
         double v[3] = {P[0] - c.eye[0], P[1] - c.eye[1], P[2] - c.eye[2]};
         double zc = v[0] * b.f[0] + v[1] * b.f[1] + v[2] * b.f[2];
-        if (!(zc > 1e-9)) {
-            behind = true;
-            break;
-        }
+        if (zc < -1e-6) ++back;
+        if (!(zc > 1e-9)) behind = true;
+        if (behind) continue;
         double xc = v[0] * b.r[0] + v[1] * b.r[1] + v[2] * b.r[2];
         double yc = v[0] * b.u[0] + v[1] * b.u[1] + v[2] * b.u[2];
         double sx = xc / (zc * b.tan_half * b.aspect), sy = yc / (zc * b.tan_half);
@@ -113,6 +118,11 @@ bool box_rect(const vr_camera& c, const Basis& b, const double lo[3], const doub
         xmax = std::max(xmax, pi);
         ymin = std::min(ymin, pj);
         ymax = std::max(ymax, pj);
+    }
+    if (back == 8) {
+        rect[0] = rect[1] = 0;
+        rect[2] = rect[3] = -1;
+        return false;
     }
     if (behind) {
         rect[0] = 0;
@@ -216,6 +226,23 @@ struct vr_ctx {
     int kernel = VR_KERNEL_AUTO;
     int tex_fits = -1;  // -1 unknown, 0/1: the cube fits the layered-texture limits
 
+    // out-of-core mode (vr_load_cube_host): cube in host memory, bricks cached on the device
+    bool ooc = false;
+    const float* h_src = nullptr;      // the caller's cube
+    float* h_store = nullptr;          // pinned brick store, brick b at b * slot_floats
+    size_t store_bytes = 0;
+    int64_t slot_floats = 0;           // (Bx+1)(By+1)(Bz+1)
+    int64_t budget = 0;                // VR_OPT_DEVICE_BUDGET (<= 0: every brick)
+    float* d_pool = nullptr;           // device brick cache
+    vr::Residency res;
+    int64_t ooc_frame = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_march_done = nullptr;  // end of the last out-of-core frame's marching
+    cudaEvent_t ev_copy_done = nullptr;   // end of the last upload issued
+    std::vector<cudaEvent_t> ev_chunk, ev_chunk_march;
+    std::vector<int32_t> ooc_bricks, ooc_slot, ooc_up, ooc_item_off;
+    std::vector<vr::Item> ooc_items;
+
     // sort-last distribution: the bricks this context renders, [region_lo, region_hi)
     int32_t region_lo[3] = {0, 0, 0}, region_hi[3] = {0, 0, 0};
     float4* d_comp = nullptr;  // root fold output when the caller passes a host buffer
@@ -304,6 +331,8 @@ int retire(vr_ctx* c, Slot& s) {
     c->acc.h2d_bytes += s.h2d_bytes;
     c->acc.d2h_bytes += s.d2h_bytes;
     c->acc.launches += s.launches;
+    c->acc.bricks_uploaded += s.bricks_uploaded;
+    c->acc.bricks_cached += s.bricks_cached;
     c->acc.device_errors |= s.h_stats->errors;
     s.pending = false;
     return VR_OK;
@@ -337,10 +366,50 @@ bool tex_fits(vr_ctx* c) {
     return c->tex_fits == 1;
 }
 bool use_tex(vr_ctx* c) {
-    return c->mode == 0 && (c->kernel == VR_KERNEL_TEX || (c->kernel == VR_KERNEL_AUTO && tex_fits(c)));
+    return !c->ooc && c->mode == 0 && (c->kernel == VR_KERNEL_TEX || (c->kernel == VR_KERNEL_AUTO && tex_fits(c)));
 }
 bool use_tma(vr_ctx* c) {
-    return c->mode == 0 && (c->kernel == VR_KERNEL_TMA || (c->kernel == VR_KERNEL_AUTO && !tex_fits(c)));
+    return !c->ooc && c->mode == 0 && (c->kernel == VR_KERNEL_TMA || (c->kernel == VR_KERNEL_AUTO && !tex_fits(c)));
+}
+
+void free_ooc(vr_ctx* c) {
+    if (c->h_store) cudaFreeHost(c->h_store);
+    cudaFree(c->d_pool);
+    c->h_store = nullptr;
+    c->d_pool = nullptr;
+    c->store_bytes = 0;
+    c->res = vr::Residency();
+    c->h_src = nullptr;
+    c->ooc = false;
+}
+
+// Brick store and device cache of an out-of-core context (at vr_brick).
+int build_ooc_store(vr_ctx* c) {
+    if (c->h_store) cudaFreeHost(c->h_store);
+    cudaFree(c->d_pool);
+    c->h_store = nullptr;
+    c->d_pool = nullptr;
+    c->slot_floats = (int64_t)(c->B[0] + 1) * (c->B[1] + 1) * (c->B[2] + 1);
+    const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
+    c->store_bytes = slot_bytes * (size_t)c->n_bricks;
+    if (cudaHostAlloc((void**)&c->h_store, c->store_bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_store = nullptr;
+        return fail(c, VR_ENOMEM, "cannot allocate the pinned brick store");
+    }
+    vr::build_brick_store(c->h_src, c->n, c->B, c->nb, c->h_store, c->slot_floats, c->h_minmax.data());
+    int64_t slots = c->n_bricks;
+    if (c->budget > 0) slots = std::min<int64_t>(slots, c->budget / (int64_t)slot_bytes);
+    if (slots < 2) return fail(c, VR_EINVAL, "VR_OPT_DEVICE_BUDGET holds fewer than 2 bricks");
+    if (cudaMalloc((void**)&c->d_pool, slot_bytes * (size_t)slots) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_pool = nullptr;
+        return fail(c, VR_ENOMEM, "cannot allocate the device brick cache");
+    }
+    c->res.slot_of_brick.assign(c->n_bricks, -1);
+    c->res.brick_in_slot.assign(slots, -1);
+    c->res.last_used.assign(slots, -1);
+    return VR_OK;
 }
 
 int64_t precision_bytes(int precision) {
@@ -521,6 +590,8 @@ void vr_destroy(vr_ctx* c) {
         if (s.h_tile_start) cudaFreeHost(s.h_tile_start);
         if (s.h_stats) cudaFreeHost(s.h_stats);
         if (s.h_frame) cudaFreeHost(s.h_frame);
+        if (s.h_slot_of) cudaFreeHost(s.h_slot_of);
+        cudaFree(s.d_slot_of);
         cudaFree(s.d_frame);
         cudaFree(s.d_items);
         cudaFree(s.d_tile_start);
@@ -536,6 +607,12 @@ void vr_destroy(vr_ctx* c) {
     free_tex(c);
     cudaFree(c->d_minmax);
     cudaFree(c->d_comp);
+    free_ooc(c);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (cudaEvent_t ev : {c->ev_march_done, c->ev_copy_done})
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->ev_chunk) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->ev_chunk_march) cudaEventDestroy(ev);
     delete c;
 }
 
@@ -562,6 +639,7 @@ int vr_load_cube(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int64_t n
     c->tma_ready = false;
     c->tex_fits = -1;
     free_tex(c);
+    free_ooc(c);
     if (cudaMalloc((void**)&c->d_cube, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, VR_ENOMEM, "cannot allocate the cube on the device");
@@ -576,9 +654,46 @@ int vr_load_cube(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int64_t n
     return VR_OK;
 }
 
+int vr_load_cube_host(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int64_t nz) {
+    if (!c) return VR_EINVAL;
+    if (!data) return fail(c, VR_EINVAL, "null cube");
+    if (nx < 2 || ny < 2 || nz < 2 || nx > 65536 || ny > 65536 || nz > 65536)
+        return fail(c, VR_EINVAL, "cube sizes must be in [2, 65536]");
+    VR_CUDA(c, cudaSetDevice(c->device));
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, data) == cudaSuccess) {
+        if (attr.type == cudaMemoryTypeDevice) return fail(c, VR_EINVAL, "vr_load_cube_host needs host memory");
+    } else {
+        cudaGetLastError();
+    }
+    int rc = retire_all(c);
+    if (rc) return rc;
+    cudaFree(c->d_cube);
+    cudaFree(c->d_cube_xzy);
+    c->d_cube = nullptr;
+    c->d_cube_xzy = nullptr;
+    c->bricked = false;
+    c->tma_ready = false;
+    c->tex_fits = -1;
+    free_tex(c);
+    free_ooc(c);
+    if (!c->copy_stream) {
+        VR_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_march_done, cudaEventDisableTiming));
+        VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_copy_done, cudaEventDisableTiming));
+    }
+    c->ooc = true;
+    c->h_src = data;
+    c->nx_pad = nx;
+    c->n[0] = nx;
+    c->n[1] = ny;
+    c->n[2] = nz;
+    return VR_OK;
+}
+
 int vr_brick(vr_ctx* c, int32_t bx, int32_t by, int32_t bz) {
     if (!c) return VR_EINVAL;
-    if (!c->d_cube) return fail(c, VR_ESTATE, "vr_brick before vr_load_cube");
+    if (!c->d_cube && !c->ooc) return fail(c, VR_ESTATE, "vr_brick before vr_load_cube");
     int32_t B[3] = {bx, by, bz};
     for (int a = 0; a < 3; ++a)
         if (B[a] < 1 || B[a] > 4096) return fail(c, VR_EINVAL, "brick sizes must be in [1, 4096]");
@@ -597,14 +712,18 @@ int vr_brick(vr_ctx* c, int32_t bx, int32_t by, int32_t bz) {
     if (c->precision == VR_PRECISION_F8) free_tex(c);  // so are the FP8 scales
     cudaFree(c->d_minmax);
     c->d_minmax = nullptr;
-    if (cudaMalloc((void**)&c->d_minmax, total * sizeof(float2)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, VR_ENOMEM, "cannot allocate brick min/max");
-    }
-    int32_t n32[3] = {(int32_t)c->n[0], (int32_t)c->n[1], (int32_t)c->n[2]};
-    VR_CUDA(c, vr::launch_brick_minmax(c->d_cube, c->nx_pad, n32, c->B, c->nb, c->d_minmax, 0));
     c->h_minmax.resize(total);
-    VR_CUDA(c, cudaMemcpy(c->h_minmax.data(), c->d_minmax, total * sizeof(float2), cudaMemcpyDeviceToHost));
+    if (c->ooc) {
+        if ((rc = build_ooc_store(c))) return rc;
+    } else {
+        if (cudaMalloc((void**)&c->d_minmax, total * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, VR_ENOMEM, "cannot allocate brick min/max");
+        }
+        int32_t n32[3] = {(int32_t)c->n[0], (int32_t)c->n[1], (int32_t)c->n[2]};
+        VR_CUDA(c, vr::launch_brick_minmax(c->d_cube, c->nx_pad, n32, c->B, c->nb, c->d_minmax, 0));
+        VR_CUDA(c, cudaMemcpy(c->h_minmax.data(), c->d_minmax, total * sizeof(float2), cudaMemcpyDeviceToHost));
+    }
     for (int a = 0; a < 3; ++a) {
         c->region_lo[a] = 0;
         c->region_hi[a] = c->nb[a];
@@ -809,6 +928,7 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
                 return fail(c, VR_EINVAL, "unknown kernel");
             c->kernel = (int)value;
             return VR_OK;
+        case VR_OPT_DEVICE_BUDGET: c->budget = value; return VR_OK;
         case VR_OPT_PRECISION:
             if (value != VR_PRECISION_F32 && value != VR_PRECISION_F16 && value != VR_PRECISION_F8)
                 return fail(c, VR_EINVAL, "unknown precision");
@@ -826,6 +946,104 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
 }  // extern "C"
 
 namespace {
+
+// Out-of-core frame: cache slots for the frame's bricks, the slot table, and the
+// march launches, each a contiguous range of items with the bricks it must wait
+// for.  In cache mode the items of resident bricks come first (one launch, no
+// wait), then the missing bricks in groups of about 64 MiB; in streaming mode the
+// bricks go in groups of half the cache.
+struct OocLaunch {
+    int64_t lo, hi;             // items [lo, hi)
+    std::vector<int32_t> up;    // bricks (ids) to copy before the launch
+    std::vector<int32_t> slot;  // and their slots
+};
+
+int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocLaunch>& launches,
+                bool& streaming) {
+    const int32_t P = (int32_t)c->plan_bricks.size();
+    c->ooc_bricks.resize(P);
+    c->ooc_item_off.assign(P + 1, 0);
+    for (int32_t k = 0; k < P; ++k) {
+        const auto& pb = c->plan_bricks[k];
+        c->ooc_bricks[k] = pb.id;
+        const int64_t cnt = (int64_t)(pb.rect[2] / T - pb.rect[0] / T + 1) * (pb.rect[3] / T - pb.rect[1] / T + 1);
+        c->ooc_item_off[k + 1] = c->ooc_item_off[k] + (int32_t)cnt;
+    }
+    if (c->ooc_item_off[P] != n_items) return fail(c, VR_EINVAL, "internal: out-of-core item count mismatch");
+    const int H = vr::plan_residency(c->res, c->ooc_bricks, c->ooc_frame++, c->ooc_slot, c->ooc_up);
+    streaming = H > 0;
+    int rc = grow_pinned(c, s.h_slot_of, s.cap_slot_of, (size_t)c->n_bricks);
+    if (rc) return rc;
+    if ((rc = grow_device(c, s.d_slot_of, s.dcap_slot_of, (size_t)c->n_bricks))) return rc;
+    std::fill(s.h_slot_of, s.h_slot_of + c->n_bricks, -1);
+    for (int32_t k = 0; k < P; ++k) s.h_slot_of[c->ooc_bricks[k]] = c->ooc_slot[k];
+    launches.clear();
+    if (streaming) {
+        for (int32_t k0 = 0; k0 < P; k0 += H) {
+            const int32_t k1 = std::min<int32_t>(P, k0 + H);
+            OocLaunch L;
+            L.lo = c->ooc_item_off[k0];
+            L.hi = c->ooc_item_off[k1];
+            for (int32_t k = k0; k < k1; ++k) {
+                L.up.push_back(c->ooc_bricks[k]);
+                L.slot.push_back(c->ooc_slot[k]);
+            }
+            launches.push_back(std::move(L));
+        }
+        s.bricks_uploaded = P;
+        s.bricks_cached = 0;
+        return VR_OK;
+    }
+    // cache mode: reorder the items, resident bricks first
+    std::vector<char> missing(P, 0);
+    for (int32_t k : c->ooc_up) missing[k] = 1;
+    c->ooc_items.resize((size_t)n_items);
+    int64_t w = 0;
+    OocLaunch hits;
+    hits.lo = 0;
+    for (int32_t k = 0; k < P; ++k)
+        if (!missing[k])
+            for (int64_t i = c->ooc_item_off[k]; i < c->ooc_item_off[k + 1]; ++i) c->ooc_items[w++] = s.h_items[i];
+    hits.hi = w;
+    launches.push_back(std::move(hits));
+    const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
+    const size_t group = std::max<size_t>(1, ((size_t)64 << 20) / slot_bytes);
+    for (size_t g0 = 0; g0 < c->ooc_up.size(); g0 += group) {
+        OocLaunch L;
+        L.lo = w;
+        for (size_t g = g0; g < std::min(c->ooc_up.size(), g0 + group); ++g) {
+            const int32_t k = c->ooc_up[g];
+            for (int64_t i = c->ooc_item_off[k]; i < c->ooc_item_off[k + 1]; ++i) c->ooc_items[w++] = s.h_items[i];
+            L.up.push_back(c->ooc_bricks[k]);
+            L.slot.push_back(c->ooc_slot[k]);
+        }
+        L.hi = w;
+        launches.push_back(std::move(L));
+    }
+    std::copy(c->ooc_items.begin(), c->ooc_items.end(), s.h_items);
+    s.bricks_uploaded = (int64_t)c->ooc_up.size();
+    s.bricks_cached = P - s.bricks_uploaded;
+    return VR_OK;
+}
+
+// Copy bricks into their cache slots on the copy stream.
+int ooc_upload(vr_ctx* c, const OocLaunch& L) {
+    const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
+    for (size_t k = 0; k < L.up.size(); ++k)
+        VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
+                                   c->h_store + (size_t)L.up[k] * c->slot_floats, slot_bytes,
+                                   cudaMemcpyHostToDevice, c->copy_stream));
+    return VR_OK;
+}
+
+int ensure_events(vr_ctx* c, std::vector<cudaEvent_t>& ev, size_t n) {
+    while (ev.size() < n) {
+        cudaEvent_t e;
+        VR_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ev.push_back(e);
+    }
+    return VR_OK;
+}
 
 // One frame into the output window win = {x0, y0, x1, y1} (inclusive) of the image;
 // out_rgba holds the window's pixels row-major.
@@ -854,6 +1072,10 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     if (use_tex(c) && (rc = prepare_tex(c))) return rc;
     rc = plan_frame(c, s, win, tiles_x, tiles_y, T, n_items);
     if (rc) return rc;
+    std::vector<OocLaunch> ooc_launches;
+    bool ooc_streaming = false;
+    s.bricks_uploaded = s.bricks_cached = 0;
+    if (c->ooc && (rc = ooc_prepare(c, s, T, n_items, ooc_launches, ooc_streaming))) return rc;
     s.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
     const size_t img_px = (size_t)(win[2] - win[0] + 1) * (size_t)(win[3] - win[1] + 1);
@@ -896,6 +1118,13 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     p.dt_f = (float)c->cam.step;
     p.tau = (float)c->cam.term_alpha;
     p.cube = c->d_cube;
+    if (c->ooc) {
+        p.pool = c->d_pool;
+        p.slot_of = s.d_slot_of;
+        p.slot_stride = c->slot_floats;
+        p.pool_sy = c->B[0] + 1;
+        p.pool_sz = (c->B[0] + 1) * (c->B[1] + 1);
+    }
     p.stride_y = c->nx_pad;
     p.stride_z = c->nx_pad * c->n[1];
     p.offsets32 = ((int64_t)c->B[2] + 1) * p.stride_z + ((int64_t)c->B[1] + 1) * p.stride_y +
@@ -937,23 +1166,76 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     VR_CUDA(c, cudaMemcpyAsync(s.d_tile_start, s.h_tile_start, ((size_t)n_tiles + 1) * sizeof(int32_t),
                                cudaMemcpyHostToDevice, st));
     VR_CUDA(c, cudaMemsetAsync(s.d_stats, 0, sizeof(vr::Stats), st));
-    VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
-    if (use_tma(c)) {
-        VR_CUDA(c, vr::launch_march_tma(p, st));
-    } else if (use_tex(c)) {
-        VR_CUDA(c, vr::launch_march_tex(p, st));
+    int64_t march_launches = n_items > 0 ? 1 : 0;
+    size_t upload_bytes = 0;
+    if (c->ooc) {
+        p.offsets32 = c->slot_floats < ((int64_t)1 << 32) ? 1 : 0;  // offsets inside one slot
+        VR_CUDA(c, cudaMemcpyAsync(s.d_slot_of, s.h_slot_of, (size_t)c->n_bricks * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, st));
+        // uploads may overwrite slots the previous out-of-core frame still reads, and
+        // this frame reads bricks that earlier frames uploaded
+        VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_march_done, 0));
+        VR_CUDA(c, cudaStreamWaitEvent(st, c->ev_copy_done, 0));
+        const size_t nl = ooc_launches.size();
+        int rc2 = ensure_events(c, c->ev_chunk, nl);
+        if (!rc2) rc2 = ensure_events(c, c->ev_chunk_march, nl);
+        if (rc2) return rc2;
+        auto issue_upload = [&](size_t k) -> int {
+            if (ooc_launches[k].up.empty()) return VR_OK;
+            if (ooc_streaming && k >= 2)  // the half it fills was read by launch k - 2
+                VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_chunk_march[k - 2], 0));
+            int r = ooc_upload(c, ooc_launches[k]);
+            if (r) return r;
+            upload_bytes += ooc_launches[k].up.size() * (size_t)c->slot_floats * sizeof(float);
+            VR_CUDA(c, cudaEventRecord(c->ev_chunk[k], c->copy_stream));
+            return VR_OK;
+        };
+        // streaming: two launches' bricks ahead; cache: every missing brick at once
+        const size_t ahead = ooc_streaming ? std::min<size_t>(2, nl) : nl;
+        for (size_t k = 0; k < ahead; ++k)
+            if ((rc2 = issue_upload(k))) return rc2;
+        VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));
+        VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
+        march_launches = 0;
+        for (size_t k = 0; k < nl; ++k) {
+            const OocLaunch& L = ooc_launches[k];
+            if (!L.up.empty()) VR_CUDA(c, cudaStreamWaitEvent(st, c->ev_chunk[k], 0));
+            if (L.hi > L.lo) {
+                vr::FrameParams q = p;
+                q.items = s.d_items + L.lo;
+                q.n_items = (int32_t)(L.hi - L.lo);
+                VR_CUDA(c, vr::launch_march(q, st));
+                ++march_launches;
+            }
+            if (ooc_streaming) {
+                VR_CUDA(c, cudaEventRecord(c->ev_chunk_march[k], st));
+                if (k + 2 < nl) {
+                    if ((rc2 = issue_upload(k + 2))) return rc2;
+                    VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));
+                }
+            }
+        }
+        VR_CUDA(c, cudaEventRecord(c->ev_march_done, st));
     } else {
-        VR_CUDA(c, vr::launch_march(p, st));
+        VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
+        if (use_tma(c)) {
+            VR_CUDA(c, vr::launch_march_tma(p, st));
+        } else if (use_tex(c)) {
+            VR_CUDA(c, vr::launch_march_tex(p, st));
+        } else {
+            VR_CUDA(c, vr::launch_march(p, st));
+        }
     }
     VR_CUDA(c, cudaEventRecord(s.ev_march1, st));
     VR_CUDA(c, vr::launch_composite(p, st));
     VR_CUDA(c, cudaMemcpyAsync(s.h_stats, s.d_stats, sizeof(vr::Stats), cudaMemcpyDeviceToHost, st));
     VR_CUDA(c, cudaEventRecord(s.ev_end, st));
     s.pending = true;
-    s.launches = (n_items > 0 ? 1 : 0) + 1;
+    s.launches = march_launches + 1;
     s.fragments = n_items * T * T;
     s.h2d_bytes = (int64_t)(frame_bytes + (size_t)n_items * sizeof(vr::Item) +
-                            ((size_t)n_tiles + 1) * sizeof(int32_t));
+                            ((size_t)n_tiles + 1) * sizeof(int32_t) + upload_bytes +
+                            (c->ooc ? (size_t)c->n_bricks * sizeof(int32_t) : 0));
     s.d2h_bytes = (int64_t)sizeof(vr::Stats) + (out_on_device ? 0 : (int64_t)(img_px * sizeof(float4)));
     if (!out_on_device) {
         VR_CUDA(c, cudaMemcpyAsync(out_rgba, s.d_img, img_px * sizeof(float4), cudaMemcpyDeviceToHost, st));
@@ -964,7 +1246,7 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
 
 int render_checks(vr_ctx* c, const float* out_rgba) {
     if (!c) return VR_EINVAL;
-    if (!c->d_cube || !c->bricked || !c->tf_set || !c->cam_set)
+    if ((!c->d_cube && !c->ooc) || !c->bricked || !c->tf_set || !c->cam_set)
         return fail(c, VR_ESTATE, "vr_render needs vr_load_cube, vr_brick, vr_set_transfer_function and vr_set_camera first");
     if (!out_rgba) return fail(c, VR_EINVAL, "null output");
     return VR_OK;

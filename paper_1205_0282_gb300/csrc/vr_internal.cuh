@@ -85,6 +85,10 @@ struct FrameParams {
     int32_t precision;          // texture storage: kPrecF32, kPrecF16, kPrecF8
     const float* brick_scale;   // FP8: per-brick scale (value = code * scale)
     const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
+    const float* pool;          // out-of-core: device brick cache, or nullptr (read `cube`)
+    const int32_t* slot_of;     // out-of-core: cache slot of each brick rendered this frame
+    int64_t slot_stride;        // floats per slot, (Bx+1)(By+1)(Bz+1)
+    int32_t pool_sy, pool_sz;   // row and plane strides inside a slot
     float4* frags;
     float4* out;                // image window: pixel (i, j) of the frame goes to
     int32_t out_x0, out_y0;     // out[(j - out_y0) * out_w + (i - out_x0)] if it lies in
@@ -124,6 +128,20 @@ cudaError_t make_tma_maps(const float* a, int64_t nx, int64_t ny, int64_t nz, in
 cudaError_t launch_transpose_xzy(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
                                  float* b, int64_t b_pitch, cudaStream_t s);
 cudaError_t launch_composite(const FrameParams& p, cudaStream_t s);
+
+// Out-of-core residency (vr_ooc.cu).
+struct Residency {
+    std::vector<int32_t> slot_of_brick;  // per brick: its cache slot, -1 if not resident
+    std::vector<int32_t> brick_in_slot;  // per slot: its brick, -1 if free
+    std::vector<int64_t> last_used;      // per slot: last frame that rendered it
+};
+void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
+                       float* store, int64_t slot_floats, float2* minmax);
+// Slots for the frame's bricks (in render order).  Returns 0 in cache mode
+// (upload lists the positions, in `bricks`, of the bricks to copy), or H > 0 in
+// streaming mode (every brick is copied; brick k goes to half (k / H) % 2).
+int plan_residency(Residency& r, const std::vector<int32_t>& bricks, int64_t frame, std::vector<int32_t>& slot,
+                   std::vector<int32_t>& upload);
 
 // k-d distribution and the root's fold (vr_shard.cu).  ranges: parts x 6 int32
 // (brick lo x, y, z then hi x, y, z, half-open), leaves in tree order.

@@ -107,9 +107,11 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
             // Sample positions stay inside the brick's owned box up to rounding
             // (ownership), so a truncating conversion plus an upper clamp keeps the
             // eight corners inside the brick and its one-voxel apron.
+            // the brick's voxels: in the resident cube, or in its out-of-core cache slot
             const float* __restrict__ base =
-                p.cube + (int64_t)O[2] * p.stride_z + (int64_t)O[1] * p.stride_y + O[0];
-            const Off sy = (Off)p.stride_y, sz = (Off)p.stride_z;
+                p.pool ? p.pool + (int64_t)p.slot_of[item.brick] * p.slot_stride
+                       : p.cube + (int64_t)O[2] * p.stride_z + (int64_t)O[1] * p.stride_y + O[0];
+            const Off sy = (Off)(p.pool ? p.pool_sy : p.stride_y), sz = (Off)(p.pool ? p.pool_sz : p.stride_z);
             const int nk = khi - klo;
             for (int kk = 0; kk < nk; ++kk) {
                 const float fk = (float)kk;

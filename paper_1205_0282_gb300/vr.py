@@ -31,6 +31,7 @@ VR_KERNEL_DIRECT = 1
 VR_KERNEL_TEX = 2
 VR_KERNEL_AUTO = 3
 VR_OPT_PRECISION = 5
+VR_OPT_DEVICE_BUDGET = 6
 VR_PRECISION_F32 = 0
 VR_PRECISION_F16 = 1
 VR_PRECISION_F8 = 2
@@ -61,12 +62,13 @@ class vr_stats(ctypes.Structure):
                 ("plan_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("chunks_staged", ctypes.c_int64), ("chunks_direct", ctypes.c_int64),
+                ("bricks_uploaded", ctypes.c_int64), ("bricks_cached", ctypes.c_int64),
                 ("device_errors", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
 
 # The exported symbols, in header order (tests check them against include/vr.h).
-EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_brick", "vr_set_transfer_function",
+EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_brick", "vr_set_transfer_function",
            "vr_set_camera", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
            "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_kd_partition", "vr_kd_order",
            "vr_set_region", "vr_region_rect", "vr_plan_region_rect", "vr_render_rect",
@@ -83,6 +85,7 @@ def _load():
     lib.vr_destroy.argtypes = [P]
     lib.vr_destroy.restype = None
     lib.vr_load_cube.argtypes = [P, P, I64, I64, I64]
+    lib.vr_load_cube_host.argtypes = [P, P, I64, I64, I64]
     lib.vr_brick.argtypes = [P, I32, I32, I32]
     lib.vr_set_transfer_function.argtypes = [P, P, I32]
     lib.vr_set_camera.argtypes = [P, ctypes.POINTER(vr_camera)]
@@ -179,6 +182,17 @@ def vr_load_cube(ctx, cube) -> None:
     nz, ny, nx = cube.shape
     addr, keep = _ptr(cube)
     _check(ctx, _lib.vr_load_cube(ctx, addr, nx, ny, nz))
+
+
+def vr_load_cube_host(ctx, cube) -> None:
+    """Out-of-core load: cube is a float32 (nz, ny, nx) host array that must stay
+    alive and unchanged while the context uses it (the VolumeRenderer keeps a
+    reference)."""
+    if getattr(cube, "dtype", None) != np.float32 or not isinstance(cube, np.ndarray):
+        raise TypeError("cube must be a float32 numpy array")
+    nz, ny, nx = cube.shape
+    addr, keep = _ptr(cube)
+    _check(ctx, _lib.vr_load_cube_host(ctx, addr, nx, ny, nz))
 
 
 def vr_brick(ctx, bx: int, by: int, bz: int) -> None:
@@ -366,6 +380,15 @@ class VolumeRenderer:
         vr_load_cube(self.ctx, cube)
         nz, ny, nx = cube.shape
         self.shape_xyz = (nx, ny, nz)
+        self._host_cube = None
+
+    def load_cube_host(self, cube):
+        """Out-of-core: the cube stays in host memory (a reference is kept)."""
+        cube = np.ascontiguousarray(cube, dtype=np.float32)
+        vr_load_cube_host(self.ctx, cube)
+        nz, ny, nx = cube.shape
+        self.shape_xyz = (nx, ny, nz)
+        self._host_cube = cube
 
     def brick(self, bx, by, bz):
         vr_brick(self.ctx, bx, by, bz)

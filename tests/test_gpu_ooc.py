@@ -1,0 +1,162 @@
+"""GPU parity of the out-of-core path (vr_load_cube_host): the cube stays in host
+memory, bricks are copied into a device cache under a memory budget and marched
+from there.  Its images must equal the in-core direct march bit for bit (same
+voxels, same arithmetic) and match the FP64 oracle; the residency counters must
+show reuse when the frame fits the cache and streaming when it does not."""
+import numpy as np
+import pytest
+
+import synth
+from parity_util import assert_parity
+from test_gpu_render import RAGGED, oracle_render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+@pytest.fixture(scope="module")
+def vr():
+    from paper_1205_0282_gb300 import vr
+    return vr
+
+
+def _incore(vr, torch, cube, tf, cam, brick, mode=0):
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(np.ascontiguousarray(cube)).cuda())
+        r.brick(*brick)
+        r.set_transfer_function(tf)
+        r.set_camera(cam)
+        r.set_option(vr.VR_OPT_KERNEL, vr.VR_KERNEL_DIRECT)
+        r.set_option(vr.VR_OPT_MODE, mode)
+        return r.render().cpu().numpy()
+
+
+def _ooc(vr, cube, tf, brick, budget_bricks=0, mode=0):
+    r = vr.VolumeRenderer(0)
+    r.load_cube_host(cube)
+    if budget_bricks:
+        slot = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1) * 4
+        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_bricks * slot)
+    r.brick(*brick)
+    r.set_transfer_function(tf)
+    r.set_option(vr.VR_OPT_MODE, mode)
+    return r
+
+
+@pytest.mark.parametrize("budget", [0, 20, 9, 2])
+@pytest.mark.parametrize("view", [0, 2])
+def test_out_of_core_equals_in_core(vr, torch, budget, view):
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    brick = (16, 16, 16)    # 64 bricks
+    cam = synth.tiny_views(width=96, height=80)[view]
+    ref = _incore(vr, torch, cube, tf, cam, brick)
+    with _ooc(vr, cube, tf, brick, budget) as r:
+        r.set_camera(cam)
+        for _ in range(3):   # first frame uploads, later ones reuse or stream again
+            img = r.render().cpu().numpy()
+            assert np.array_equal(img, ref)
+        st = r.stats()
+    assert st["device_errors"] == 0
+    per_frame = st["bricks_rendered"] // 3
+    if budget == 0 or budget >= per_frame:
+        assert st["bricks_uploaded"] == per_frame          # once
+        assert st["bricks_cached"] == 2 * per_frame
+    else:
+        assert st["bricks_uploaded"] == 3 * per_frame      # streamed every frame
+        assert st["bricks_cached"] == 0
+
+
+def test_cache_evicts_least_recently_used(vr, torch):
+    """A cache that holds either view's bricks but not both: going back to the
+    first view re-uploads exactly the bricks the second view evicted."""
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    brick = (16, 16, 16)
+    # the eye inside the cube, looking at opposite corners: each view misses the
+    # bricks behind it
+    a = synth.camera((33.0, 31.0, 32.5), (63.0, 63.0, 63.0), (0, 1, 0), 40.0, 64, 64)
+    b = synth.camera((33.0, 31.0, 32.5), (0.0, 0.0, 0.0), (0, 1, 0), 40.0, 64, 64)
+    counts = {}
+    with _ooc(vr, cube, tf, brick) as r:     # every brick fits: learn each view's brick count
+        for name, cam in (("a", a), ("b", b)):
+            r.set_camera(cam)
+            r.reset_stats()
+            r.render()
+            counts[name] = r.stats()["bricks_rendered"]
+    budget = max(counts.values())
+    assert budget < 64
+    with _ooc(vr, cube, tf, brick, budget) as r:
+        ups = []
+        for cam in (a, b, a):
+            r.set_camera(cam)
+            r.reset_stats()
+            img = r.render().cpu().numpy()
+            st = r.stats()
+            ups.append(st["bricks_uploaded"])
+            assert st["bricks_uploaded"] + st["bricks_cached"] == st["bricks_rendered"]
+        assert np.array_equal(img, _incore(vr, torch, cube, tf, a, brick))
+    assert ups[0] == counts["a"]
+    assert 0 < ups[2] <= ups[1]          # evicted bricks come back, resident ones do not
+
+
+def test_out_of_core_matches_the_oracle(vr):
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    for view in range(4):
+        cam = synth.tiny_views()[view]
+        with _ooc(vr, cube, tf, (32, 32, 32), 3) as r:
+            r.set_camera(cam)
+            img = r.render().cpu().numpy().astype(np.float64)
+        ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32))
+        assert_parity(img, ref, amb)
+
+
+@pytest.mark.parametrize("shape,brick,camk,step,tau", RAGGED[:3])
+def test_out_of_core_ragged(vr, shape, brick, camk, step, tau):
+    cube = synth.hi_cube(seed=11, shape_xyz=shape, n_line=12, n_cont=2)
+    tf = synth.tf_tiny()
+    cam = synth.pose(shape, camk["az"], camk["el"], camk["W"], camk["H"], step=step, term_alpha=tau)
+    with _ooc(vr, cube, tf, brick, 5) as r:
+        r.set_camera(cam)
+        img = r.render().cpu().numpy().astype(np.float64)
+        host = np.zeros_like(img, dtype=np.float32)
+        r.render(host)
+    assert np.array_equal(host.astype(np.float64), img)
+    ref, amb, _ = oracle_render(cube, tf, cam, brick)
+    assert_parity(img, ref, amb)
+
+
+def test_out_of_core_mip(vr, torch):
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    cam = synth.tiny_views(width=80, height=72)[1]
+    ref = _incore(vr, torch, cube, tf, cam, (16, 16, 16), mode=1)
+    with _ooc(vr, cube, tf, (16, 16, 16), 6, mode=1) as r:
+        r.set_camera(cam)
+        assert np.array_equal(r.render().cpu().numpy(), ref)
+
+
+def test_out_of_core_errors(vr, torch):
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    with vr.VolumeRenderer(0) as r:
+        with pytest.raises(vr.VRError, match="VR_EINVAL"):
+            vr.vr_load_cube_host(r.ctx, np.zeros((1, 4, 4), np.float32))
+        r.load_cube_host(cube)
+        r.set_option(vr.VR_OPT_DEVICE_BUDGET, 17 ** 3 * 4)   # one brick: too small
+        with pytest.raises(vr.VRError, match="VR_EINVAL"):
+            r.brick(16, 16, 16)
+        r.set_option(vr.VR_OPT_DEVICE_BUDGET, 0)
+        r.brick(16, 16, 16)
+        r.set_transfer_function(tf)
+        r.set_camera(synth.tiny_views(width=32, height=32)[0])
+        r.set_option(vr.VR_OPT_PRECISION, vr.VR_PRECISION_F16)
+        with pytest.raises(vr.VRError, match="VR_EINVAL"):
+            r.render()   # reduced precision needs the texture march, which needs the cube on the device
+        r.set_option(vr.VR_OPT_PRECISION, vr.VR_PRECISION_F32)
+        r.render()
+        # switching back to an in-core cube
+        r.load_cube(torch.from_numpy(cube).cuda())
+        r.brick(16, 16, 16)
+        r.render()
