@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--shard", type=int, default=1,
                     help="render each frame as this many virtual ranks on one GPU (k-d leaves, one "
                          "stream each, root fold of the rectangle-clipped sub-images)")
+    ap.add_argument("--ooc", action="store_true",
+                    help="out-of-core: the cube stays in host memory, bricks stream into a device cache")
+    ap.add_argument("--budget-gib", type=float, default=0.0,
+                    help="device brick-cache budget for --ooc in GiB (0: every brick)")
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -335,11 +339,19 @@ def run_ours(args):
     W, H = spec["width"], spec["height"]
 
     r = VolumeRenderer(local)
-    dcube = torch.from_numpy(cube).cuda()
-    r.load_cube(dcube)
-    del dcube
-    torch.cuda.empty_cache()
+    from paper_1205_0282_gb300 import vr as vrmod
+    t_load = time.perf_counter()
+    if args.ooc:
+        r.load_cube_host(cube)
+        if args.budget_gib > 0:
+            r.set_option(vrmod.VR_OPT_DEVICE_BUDGET, int(args.budget_gib * 2 ** 30))
+    else:
+        dcube = torch.from_numpy(cube).cuda()
+        r.load_cube(dcube)
+        del dcube
+        torch.cuda.empty_cache()
     r.brick(*spec["brick"])
+    load_s = time.perf_counter() - t_load
     r.set_transfer_function(tf)
     from paper_1205_0282_gb300 import vr as vrmod
     r.set_option(vrmod.VR_OPT_KERNEL, {"auto": vrmod.VR_KERNEL_AUTO, "tma": vrmod.VR_KERNEL_TMA,
@@ -489,6 +501,9 @@ def run_ours(args):
                        "tf": args.tf.upper(), "term_alpha": 0.99,
                        "storage": {"f32": "FP32", "f16": "FP16",
                                    "f8": "FP8 E4M3, per-brick absmax/448 scale"}[args.precision],
+                       "residency": ("out-of-core: pinned host brick store, device brick cache of "
+                                     + (f"{args.budget_gib:g} GiB" if args.budget_gib > 0 else "every brick")
+                                     if args.ooc else "in-core: cube resident in HBM"),
                        "l2": ("inputs larger than L2, no flush" if spec["name"] != "tiny"
                               else "tiny cube fits in L2 (not a bench line)"),
                        "parallelism": f"replicas x{world}: orbit poses split across ranks"
@@ -508,6 +523,11 @@ def run_ours(args):
             "chunks_staged_per_frame": st["chunks_staged"] / per_frame,
             "chunks_direct_per_frame": st["chunks_direct"] / per_frame,
             "gpu_launches": launches, "clocks": clocks.summary(),
+            "load_and_brick_s": load_s,
+            "ooc": ({"bricks_uploaded_per_frame": st["bricks_uploaded"] / per_frame,
+                     "bricks_cached_per_frame": st["bricks_cached"] / per_frame,
+                     "upload_gb_per_s": (st["h2d_bytes"] / (elapsed_ms * 1e-3) / 1e9)}
+                    if args.ooc else None),
             "device_errors": st["device_errors"]}
     print(json.dumps(line), flush=True)
     r.close()

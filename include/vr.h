@@ -138,8 +138,11 @@ typedef struct {
                                 (bx+1)(by+1)(bz+1) floats; default (and any value <= 0):
                                 room for every brick.  A frame whose rendered bricks fit
                                 keeps bricks resident across frames (least recently used
-                                evicted); a larger frame streams its bricks through the
-                                cache in two alternating halves.  Needs room for 2 bricks.
+                                evicted); in a larger frame the last 2H slots (H = S/8
+                                clamped to [1, 32], S slots) form a ring of two halves that
+                                the bricks not resident stream through, each half refilled
+                                once its previous bricks are marched, while the other
+                                S - 2H slots stay resident.  Needs room for 2 bricks.
                                 Takes effect at the next vr_brick. */
 #define VR_PRECISION_F32 0
 #define VR_PRECISION_F16 1

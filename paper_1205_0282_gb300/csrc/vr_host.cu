@@ -239,7 +239,10 @@ struct vr_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_march_done = nullptr;  // end of the last out-of-core frame's marching
     cudaEvent_t ev_copy_done = nullptr;   // end of the last upload issued
-    std::vector<cudaEvent_t> ev_chunk, ev_chunk_march;
+    std::vector<cudaEvent_t> ev_chunk;
+    cudaEvent_t ev_half_read[2] = {nullptr, nullptr};  // last march that read each ring half
+    int32_t ring_first_half = 0;                       // ring half the next frame starts in
+    std::vector<int32_t> ooc_ring;
     std::vector<int32_t> ooc_bricks, ooc_slot, ooc_up, ooc_item_off;
     std::vector<vr::Item> ooc_items;
 
@@ -612,7 +615,8 @@ void vr_destroy(vr_ctx* c) {
     for (cudaEvent_t ev : {c->ev_march_done, c->ev_copy_done})
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : c->ev_chunk) cudaEventDestroy(ev);
-    for (cudaEvent_t ev : c->ev_chunk_march) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->ev_half_read)
+        if (ev) cudaEventDestroy(ev);
     delete c;
 }
 
@@ -681,6 +685,7 @@ int vr_load_cube_host(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int6
         VR_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_march_done, cudaEventDisableTiming));
         VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_copy_done, cudaEventDisableTiming));
+        for (cudaEvent_t& ev : c->ev_half_read) VR_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     c->ooc = true;
     c->h_src = data;
@@ -949,17 +954,17 @@ namespace {
 
 // Out-of-core frame: cache slots for the frame's bricks, the slot table, and the
 // march launches, each a contiguous range of items with the bricks it must wait
-// for.  In cache mode the items of resident bricks come first (one launch, no
-// wait), then the missing bricks in groups of about 64 MiB; in streaming mode the
-// bricks go in groups of half the cache.
+// for: first the items of resident bricks (no wait), then bricks copied into
+// resident slots in groups of about 64 MiB, then bricks streamed through the ring,
+// one launch per half-ring.
 struct OocLaunch {
     int64_t lo, hi;             // items [lo, hi)
     std::vector<int32_t> up;    // bricks (ids) to copy before the launch
     std::vector<int32_t> slot;  // and their slots
+    int32_t half = -1;          // ring half the bricks go to (-1: resident slots)
 };
 
-int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocLaunch>& launches,
-                bool& streaming) {
+int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocLaunch>& launches) {
     const int32_t P = (int32_t)c->plan_bricks.size();
     c->ooc_bricks.resize(P);
     c->ooc_item_off.assign(P + 1, 0);
@@ -970,40 +975,31 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocL
         c->ooc_item_off[k + 1] = c->ooc_item_off[k] + (int32_t)cnt;
     }
     if (c->ooc_item_off[P] != n_items) return fail(c, VR_EINVAL, "internal: out-of-core item count mismatch");
-    const int H = vr::plan_residency(c->res, c->ooc_bricks, c->ooc_frame++, c->ooc_slot, c->ooc_up);
-    streaming = H > 0;
+    const int32_t H = vr::plan_residency(c->res, c->ooc_bricks, c->ooc_frame++, c->ring_first_half, c->ooc_slot,
+                                         c->ooc_up, c->ooc_ring);
     int rc = grow_pinned(c, s.h_slot_of, s.cap_slot_of, (size_t)c->n_bricks);
     if (rc) return rc;
     if ((rc = grow_device(c, s.d_slot_of, s.dcap_slot_of, (size_t)c->n_bricks))) return rc;
     std::fill(s.h_slot_of, s.h_slot_of + c->n_bricks, -1);
     for (int32_t k = 0; k < P; ++k) s.h_slot_of[c->ooc_bricks[k]] = c->ooc_slot[k];
-    launches.clear();
-    if (streaming) {
-        for (int32_t k0 = 0; k0 < P; k0 += H) {
-            const int32_t k1 = std::min<int32_t>(P, k0 + H);
-            OocLaunch L;
-            L.lo = c->ooc_item_off[k0];
-            L.hi = c->ooc_item_off[k1];
-            for (int32_t k = k0; k < k1; ++k) {
-                L.up.push_back(c->ooc_bricks[k]);
-                L.slot.push_back(c->ooc_slot[k]);
-            }
-            launches.push_back(std::move(L));
-        }
-        s.bricks_uploaded = P;
-        s.bricks_cached = 0;
-        return VR_OK;
-    }
-    // cache mode: reorder the items, resident bricks first
-    std::vector<char> missing(P, 0);
-    for (int32_t k : c->ooc_up) missing[k] = 1;
+    // reorder the items: resident hits, then the uploads, then the ring
+    std::vector<char> moved(P, 0);
+    for (int32_t k : c->ooc_up) moved[k] = 1;
+    for (int32_t k : c->ooc_ring) moved[k] = 1;
     c->ooc_items.resize((size_t)n_items);
     int64_t w = 0;
+    auto take = [&](int32_t k, OocLaunch* L) {
+        for (int64_t i = c->ooc_item_off[k]; i < c->ooc_item_off[k + 1]; ++i) c->ooc_items[w++] = s.h_items[i];
+        if (L) {
+            L->up.push_back(c->ooc_bricks[k]);
+            L->slot.push_back(c->ooc_slot[k]);
+        }
+    };
+    launches.clear();
     OocLaunch hits;
     hits.lo = 0;
     for (int32_t k = 0; k < P; ++k)
-        if (!missing[k])
-            for (int64_t i = c->ooc_item_off[k]; i < c->ooc_item_off[k + 1]; ++i) c->ooc_items[w++] = s.h_items[i];
+        if (!moved[k]) take(k, nullptr);
     hits.hi = w;
     launches.push_back(std::move(hits));
     const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
@@ -1011,17 +1007,22 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocL
     for (size_t g0 = 0; g0 < c->ooc_up.size(); g0 += group) {
         OocLaunch L;
         L.lo = w;
-        for (size_t g = g0; g < std::min(c->ooc_up.size(), g0 + group); ++g) {
-            const int32_t k = c->ooc_up[g];
-            for (int64_t i = c->ooc_item_off[k]; i < c->ooc_item_off[k + 1]; ++i) c->ooc_items[w++] = s.h_items[i];
-            L.up.push_back(c->ooc_bricks[k]);
-            L.slot.push_back(c->ooc_slot[k]);
-        }
+        for (size_t g = g0; g < std::min(c->ooc_up.size(), g0 + group); ++g) take(c->ooc_up[g], &L);
         L.hi = w;
         launches.push_back(std::move(L));
     }
+    int32_t halves = 0;
+    for (size_t g0 = 0; g0 < c->ooc_ring.size(); g0 += (size_t)H, ++halves) {
+        OocLaunch L;
+        L.lo = w;
+        L.half = (c->ring_first_half + halves) % 2;
+        for (size_t g = g0; g < std::min(c->ooc_ring.size(), g0 + (size_t)H); ++g) take(c->ooc_ring[g], &L);
+        L.hi = w;
+        launches.push_back(std::move(L));
+    }
+    c->ring_first_half = (c->ring_first_half + halves) % 2;
     std::copy(c->ooc_items.begin(), c->ooc_items.end(), s.h_items);
-    s.bricks_uploaded = (int64_t)c->ooc_up.size();
+    s.bricks_uploaded = (int64_t)(c->ooc_up.size() + c->ooc_ring.size());
     s.bricks_cached = P - s.bricks_uploaded;
     return VR_OK;
 }
@@ -1073,9 +1074,8 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     rc = plan_frame(c, s, win, tiles_x, tiles_y, T, n_items);
     if (rc) return rc;
     std::vector<OocLaunch> ooc_launches;
-    bool ooc_streaming = false;
     s.bricks_uploaded = s.bricks_cached = 0;
-    if (c->ooc && (rc = ooc_prepare(c, s, T, n_items, ooc_launches, ooc_streaming))) return rc;
+    if (c->ooc && (rc = ooc_prepare(c, s, T, n_items, ooc_launches))) return rc;
     s.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
     const size_t img_px = (size_t)(win[2] - win[0] + 1) * (size_t)(win[3] - win[1] + 1);
@@ -1172,29 +1172,40 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
         p.offsets32 = c->slot_floats < ((int64_t)1 << 32) ? 1 : 0;  // offsets inside one slot
         VR_CUDA(c, cudaMemcpyAsync(s.d_slot_of, s.h_slot_of, (size_t)c->n_bricks * sizeof(int32_t),
                                    cudaMemcpyHostToDevice, st));
-        // uploads may overwrite slots the previous out-of-core frame still reads, and
-        // this frame reads bricks that earlier frames uploaded
-        VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_march_done, 0));
+        // this frame reads bricks that earlier frames copied into resident slots
         VR_CUDA(c, cudaStreamWaitEvent(st, c->ev_copy_done, 0));
         const size_t nl = ooc_launches.size();
         int rc2 = ensure_events(c, c->ev_chunk, nl);
-        if (!rc2) rc2 = ensure_events(c, c->ev_chunk_march, nl);
         if (rc2) return rc2;
         auto issue_upload = [&](size_t k) -> int {
-            if (ooc_launches[k].up.empty()) return VR_OK;
-            if (ooc_streaming && k >= 2)  // the half it fills was read by launch k - 2
-                VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_chunk_march[k - 2], 0));
-            int r = ooc_upload(c, ooc_launches[k]);
+            const OocLaunch& L = ooc_launches[k];
+            if (L.up.empty()) return VR_OK;
+            // a ring half is refilled once its last reader has marched (host issue
+            // order puts that reader's event record before this wait)
+            if (L.half >= 0) VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_half_read[L.half], 0));
+            int r = ooc_upload(c, L);
             if (r) return r;
-            upload_bytes += ooc_launches[k].up.size() * (size_t)c->slot_floats * sizeof(float);
+            upload_bytes += L.up.size() * (size_t)c->slot_floats * sizeof(float);
             VR_CUDA(c, cudaEventRecord(c->ev_chunk[k], c->copy_stream));
+            VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));
             return VR_OK;
         };
-        // streaming: two launches' bricks ahead; cache: every missing brick at once
-        const size_t ahead = ooc_streaming ? std::min<size_t>(2, nl) : nl;
-        for (size_t k = 0; k < ahead; ++k)
-            if ((rc2 = issue_upload(k))) return rc2;
-        VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));
+        // uploads into resident slots may overwrite bricks the previous frame still reads
+        bool resident_uploads = false;
+        for (const OocLaunch& L : ooc_launches) resident_uploads = resident_uploads || (L.half < 0 && !L.up.empty());
+        if (resident_uploads) VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_march_done, 0));
+        // every resident upload at once; the ring two launches ahead of the march
+        std::vector<size_t> ring_launches;
+        for (size_t k = 0; k < nl; ++k) {
+            if (ooc_launches[k].half < 0) {
+                if ((rc2 = issue_upload(k))) return rc2;
+            } else {
+                ring_launches.push_back(k);
+            }
+        }
+        size_t ring_issued = 0;
+        while (ring_issued < std::min<size_t>(2, ring_launches.size()))
+            if ((rc2 = issue_upload(ring_launches[ring_issued++]))) return rc2;
         VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
         march_launches = 0;
         for (size_t k = 0; k < nl; ++k) {
@@ -1207,12 +1218,10 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
                 VR_CUDA(c, vr::launch_march(q, st));
                 ++march_launches;
             }
-            if (ooc_streaming) {
-                VR_CUDA(c, cudaEventRecord(c->ev_chunk_march[k], st));
-                if (k + 2 < nl) {
-                    if ((rc2 = issue_upload(k + 2))) return rc2;
-                    VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));
-                }
+            if (L.half >= 0) {
+                VR_CUDA(c, cudaEventRecord(c->ev_half_read[L.half], st));
+                if (ring_issued < ring_launches.size())
+                    if ((rc2 = issue_upload(ring_launches[ring_issued++]))) return rc2;
             }
         }
         VR_CUDA(c, cudaEventRecord(c->ev_march_done, st));

@@ -137,11 +137,12 @@ struct Residency {
 };
 void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
                        float* store, int64_t slot_floats, float2* minmax);
-// Slots for the frame's bricks (in render order).  Returns 0 in cache mode
-// (upload lists the positions, in `bricks`, of the bricks to copy), or H > 0 in
-// streaming mode (every brick is copied; brick k goes to half (k / H) % 2).
-int plan_residency(Residency& r, const std::vector<int32_t>& bricks, int64_t frame, std::vector<int32_t>& slot,
-                   std::vector<int32_t>& upload);
+// Slots for the frame's bricks (in render order).  upload: positions (in
+// `bricks`) of bricks copied into resident slots; ring: positions of bricks that
+// stream through the ring, in order, the j-th into half (first_half + j / H) % 2.
+// Returns H (0 when every brick of the frame is resident).
+int plan_residency(Residency& r, const std::vector<int32_t>& bricks, int64_t frame, int32_t first_half,
+                   std::vector<int32_t>& slot, std::vector<int32_t>& upload, std::vector<int32_t>& ring);
 
 // k-d distribution and the root's fold (vr_shard.cu).  ranges: parts x 6 int32
 // (brick lo x, y, z then hi x, y, z, half-open), leaves in tree order.

@@ -9,9 +9,12 @@
 //                      brick's [min, max] over the same voxels (Section 2.3.1's
 //                      per-sub-cube range, used for empty-space skipping).
 //   plan_residency     assign a device slot to every brick a frame renders:
-//                      when they fit, resident bricks are reused and missing ones
-//                      take free or least recently used slots; otherwise the
-//                      bricks stream through two alternating halves of the cache.
+//                      resident bricks are reused and missing ones take free or
+//                      least recently used slots; when the frame needs more bricks
+//                      than the cache holds, the last 2H slots become a streaming
+//                      ring (two halves of H, alternating), the rest stays resident
+//                      across frames, and the bricks left over stream through the
+//                      ring.
 #include <algorithm>
 #include <cfloat>
 #include <cstring>
@@ -57,56 +60,63 @@ void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3],
     for (auto& th : pool) th.join();
 }
 
-int plan_residency(Residency& r, const std::vector<int32_t>& bricks, int64_t frame, std::vector<int32_t>& slot,
-                   std::vector<int32_t>& upload_chunks) {
+int plan_residency(Residency& r, const std::vector<int32_t>& bricks, int64_t frame, int32_t first_half,
+                   std::vector<int32_t>& slot, std::vector<int32_t>& upload, std::vector<int32_t>& ring) {
     const int32_t S = (int32_t)r.brick_in_slot.size();
     const int32_t P = (int32_t)bricks.size();
     slot.assign(P, -1);
-    upload_chunks.clear();
-    if (P <= S) {
-        // cache: mark this frame's resident bricks, then give every missing brick
-        // a free slot or the least recently used slot not needed by this frame
-        std::vector<char> needed(S, 0);
-        for (int32_t k = 0; k < P; ++k) {
-            const int32_t s = r.slot_of_brick[bricks[k]];
-            if (s >= 0) {
-                slot[k] = s;
-                needed[s] = 1;
-                r.last_used[s] = frame;
-            }
+    upload.clear();
+    ring.clear();
+    // Streaming ring for frames larger than the cache: two halves of H slots at the
+    // end of the cache; the first R = S - 2H slots stay resident across frames.
+    int32_t H = 0;
+    if (P > S) H = std::max<int32_t>(1, std::min<int32_t>(S / 8, 32));
+    const int32_t R = S - 2 * H;
+    // slots no longer resident (a smaller resident part than the last frame's)
+    for (int32_t s = R; s < S; ++s)
+        if (r.brick_in_slot[s] >= 0) {
+            r.slot_of_brick[r.brick_in_slot[s]] = -1;
+            r.brick_in_slot[s] = -1;
         }
-        std::vector<int32_t> victims;
-        for (int32_t s = 0; s < S; ++s)
-            if (!needed[s]) victims.push_back(s);
-        // free slots first (brick -1), then oldest use
-        std::sort(victims.begin(), victims.end(), [&](int32_t a, int32_t b) {
-            const bool fa = r.brick_in_slot[a] < 0, fb = r.brick_in_slot[b] < 0;
-            if (fa != fb) return fa;
-            return r.last_used[a] < r.last_used[b];
-        });
-        size_t v = 0;
-        for (int32_t k = 0; k < P; ++k) {
-            if (slot[k] >= 0) continue;
+    // resident hits, then free or least recently used resident slots for the rest
+    std::vector<char> needed(R, 0);
+    for (int32_t k = 0; k < P; ++k) {
+        const int32_t s = r.slot_of_brick[bricks[k]];
+        if (s >= 0) {
+            slot[k] = s;
+            needed[s] = 1;
+            r.last_used[s] = frame;
+        }
+    }
+    std::vector<int32_t> victims;
+    for (int32_t s = 0; s < R; ++s)
+        if (!needed[s]) victims.push_back(s);
+    std::sort(victims.begin(), victims.end(), [&](int32_t a, int32_t b) {
+        const bool fa = r.brick_in_slot[a] < 0, fb = r.brick_in_slot[b] < 0;
+        if (fa != fb) return fa;
+        return r.last_used[a] < r.last_used[b];
+    });
+    size_t v = 0;
+    int32_t streamed = 0;
+    for (int32_t k = 0; k < P; ++k) {
+        if (slot[k] >= 0) continue;
+        if (v < victims.size()) {
             const int32_t s = victims[v++];
             if (r.brick_in_slot[s] >= 0) r.slot_of_brick[r.brick_in_slot[s]] = -1;
             r.brick_in_slot[s] = bricks[k];
             r.slot_of_brick[bricks[k]] = s;
             r.last_used[s] = frame;
             slot[k] = s;
-            upload_chunks.push_back(k);
+            upload.push_back(k);
+        } else {
+            // through the ring: the j-th streamed brick goes to half (first_half + j / H) % 2
+            const int32_t half = (first_half + streamed / H) % 2;
+            slot[k] = R + half * H + streamed % H;
+            ring.push_back(k);
+            ++streamed;
         }
-        return 0;  // cache mode: upload_chunks lists the bricks to copy
     }
-    // streaming: drop the cache; chunk c (bricks [c*H, (c+1)*H)) uses half c % 2
-    std::fill(r.slot_of_brick.begin(), r.slot_of_brick.end(), -1);
-    std::fill(r.brick_in_slot.begin(), r.brick_in_slot.end(), -1);
-    const int32_t H = S / 2;
-    for (int32_t k = 0; k < P; ++k) {
-        const int32_t c = k / H;
-        slot[k] = (c % 2) * H + k % H;
-        upload_chunks.push_back(k);
-    }
-    return H;  // streaming mode: chunks of H bricks
+    return H;
 }
 
 }  // namespace vr
