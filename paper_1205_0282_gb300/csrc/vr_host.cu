@@ -237,6 +237,8 @@ struct vr_ctx {
     vr::Residency res;
     int64_t ooc_frame = 0;
     cudaStream_t copy_stream = nullptr;
+    cudaStream_t ring_stream = nullptr;   // marches of streamed bricks, beside the resident ones
+    cudaEvent_t ev_ring_start = nullptr, ev_ring_end = nullptr;
     cudaEvent_t ev_march_done = nullptr;  // end of the last out-of-core frame's marching
     cudaEvent_t ev_copy_done = nullptr;   // end of the last upload issued
     std::vector<cudaEvent_t> ev_chunk;
@@ -612,7 +614,8 @@ void vr_destroy(vr_ctx* c) {
     cudaFree(c->d_comp);
     free_ooc(c);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
-    for (cudaEvent_t ev : {c->ev_march_done, c->ev_copy_done})
+    if (c->ring_stream) cudaStreamDestroy(c->ring_stream);
+    for (cudaEvent_t ev : {c->ev_march_done, c->ev_copy_done, c->ev_ring_start, c->ev_ring_end})
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : c->ev_chunk) cudaEventDestroy(ev);
     for (cudaEvent_t ev : c->ev_half_read)
@@ -686,6 +689,13 @@ int vr_load_cube_host(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int6
         VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_march_done, cudaEventDisableTiming));
         VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_copy_done, cudaEventDisableTiming));
         for (cudaEvent_t& ev : c->ev_half_read) VR_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        // the ring's marches free its halves for the next copies: schedule their
+        // blocks ahead of the resident bricks' long launch
+        int lo_prio = 0, hi_prio = 0;
+        VR_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+        VR_CUDA(c, cudaStreamCreateWithPriority(&c->ring_stream, cudaStreamNonBlocking, hi_prio));
+        VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_start, cudaEventDisableTiming));
+        VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_end, cudaEventDisableTiming));
     }
     c->ooc = true;
     c->h_src = data;
@@ -1207,22 +1217,34 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
         while (ring_issued < std::min<size_t>(2, ring_launches.size()))
             if ((rc2 = issue_upload(ring_launches[ring_issued++]))) return rc2;
         VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
+        // the streamed bricks march on their own stream, beside the resident ones,
+        // so that waiting for a ring half never holds back the resident work
+        const bool ring = !ring_launches.empty();
+        if (ring) {
+            VR_CUDA(c, cudaEventRecord(c->ev_ring_start, st));
+            VR_CUDA(c, cudaStreamWaitEvent(c->ring_stream, c->ev_ring_start, 0));
+        }
         march_launches = 0;
         for (size_t k = 0; k < nl; ++k) {
             const OocLaunch& L = ooc_launches[k];
-            if (!L.up.empty()) VR_CUDA(c, cudaStreamWaitEvent(st, c->ev_chunk[k], 0));
+            cudaStream_t ms = L.half >= 0 ? c->ring_stream : st;
+            if (!L.up.empty()) VR_CUDA(c, cudaStreamWaitEvent(ms, c->ev_chunk[k], 0));
             if (L.hi > L.lo) {
                 vr::FrameParams q = p;
                 q.items = s.d_items + L.lo;
                 q.n_items = (int32_t)(L.hi - L.lo);
-                VR_CUDA(c, vr::launch_march(q, st));
+                VR_CUDA(c, vr::launch_march(q, ms));
                 ++march_launches;
             }
             if (L.half >= 0) {
-                VR_CUDA(c, cudaEventRecord(c->ev_half_read[L.half], st));
+                VR_CUDA(c, cudaEventRecord(c->ev_half_read[L.half], ms));
                 if (ring_issued < ring_launches.size())
                     if ((rc2 = issue_upload(ring_launches[ring_issued++]))) return rc2;
             }
+        }
+        if (ring) {
+            VR_CUDA(c, cudaEventRecord(c->ev_ring_end, c->ring_stream));
+            VR_CUDA(c, cudaStreamWaitEvent(st, c->ev_ring_end, 0));
         }
         VR_CUDA(c, cudaEventRecord(c->ev_march_done, st));
     } else {
