@@ -3,6 +3,7 @@
 // empty-space skipping, view-order sort, work-list build; Sections 2.3.1-2.3.3 of
 // arXiv:1205.0282) and the stream-ordered frame pipeline.
 #include <algorithm>
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -1152,6 +1153,8 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     p.small_split = (float)c->small_split;
     p.small_scale = (float)(2.0 / c->small_split);
     p.mode = c->mode;
+    p.gmax = FLT_MAX;
+    for (const float2& mm : c->h_minmax) p.gmax = p.gmax == FLT_MAX ? mm.y : std::max(p.gmax, mm.y);
     p.items = s.d_items;
     p.n_items = (int32_t)n_items;
     p.tmaps = c->d_tmaps;

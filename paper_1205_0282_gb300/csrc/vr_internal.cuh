@@ -74,7 +74,8 @@ struct FrameParams {
     float alpha_poly[kAlphaPolyTerms];
     float poly_scale;
     float alpha_split;
-    int32_t mode;          // 0 = emission-absorption, 1 = MIP
+    int32_t mode;               // 0 = emission-absorption, 1 = MIP
+    float gmax;                 // MIP: the cube's global maximum (rays stop on reaching it)
 
     // plan
     const Item* items;

@@ -140,6 +140,9 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
                 ++taken;
                 if (MODE == 1) {
                     vmax = fmaxf(vmax, v);
+                    // Section 2.3.2: a ray stops once it reaches the data's global
+                    // maximum (nothing later can exceed it)
+                    if (vmax >= p.gmax) break;
                     continue;
                 }
                 const float4 col = tf_lookup<UNIFORM>(p, s_tf.rgba, s_tf.v, v);

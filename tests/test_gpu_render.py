@@ -297,3 +297,17 @@ def test_texture_gather_ragged(vr, torch, shape, brick, camk, step, tau):
     img, _ = gpu_render(vr, torch, cube, tf, cam, brick, {vr.VR_OPT_KERNEL: vr.VR_KERNEL_TEX})
     ref, amb, _ = oracle_render(cube, tf, cam, brick)
     assert_parity(img, ref, amb)
+
+
+def test_mip_stops_at_the_global_maximum(vr, torch):
+    """Section 2.3.2: a MIP ray stops once it reaches the cube's global maximum.
+    On a cube clipped at its 90th percentile (large plateaus at the maximum) the
+    image is unchanged and fewer samples are taken than the oracle's full rays."""
+    cube = synth.tiny_cube()
+    cube = np.minimum(cube, np.percentile(cube, 90)).astype(np.float32)
+    tf = synth.tf_tiny()
+    cam = synth.tiny_views(width=96, height=96)[1]
+    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_MODE: 1})
+    ref, amb, ns = oracle_render(cube, tf, cam, (32, 32, 32), mode="mip")
+    assert_parity(img, ref, amb, min_signal=0.0)
+    assert st["samples"] < 0.7 * ns.sum()
