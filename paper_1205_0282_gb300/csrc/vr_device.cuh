@@ -13,10 +13,13 @@ namespace vr {
 // Ray of pixel (i, j) in double-float: unit direction d, entry point pe and the
 // sample count n = #{k >= 0 : k dt < t1 - t0}.  Returns false if the ray misses
 // the domain [0, n-1]^3.
-__device__ __forceinline__ bool setup_ray(const FrameParams& p, int i, int j, df d[3], df pe[3], int& n_samples) {
-    const df qx = p.qx[i], qy = p.qy[j];
+// Cam: FrameParams (one frame) or FrameCam (a frame of a batch): eye, f, r, u, qx, qy.
+template <class Cam>
+__device__ __forceinline__ bool setup_ray(const FrameParams& p, const Cam& cam, int i, int j, df d[3], df pe[3],
+                                          int& n_samples) {
+    const df qx = cam.qx[i], qy = cam.qy[j];
     df dun[3];
-    for (int a = 0; a < 3; ++a) dun[a] = df_add(df_add(p.f[a], df_mul(qx, p.r[a])), df_mul(qy, p.u[a]));
+    for (int a = 0; a < 3; ++a) dun[a] = df_add(df_add(cam.f[a], df_mul(qx, cam.r[a])), df_mul(qy, cam.u[a]));
     df n2 = df_add(df_add(df_mul(dun[0], dun[0]), df_mul(dun[1], dun[1])), df_mul(dun[2], dun[2]));
     df len = df_sqrt(n2);
     for (int a = 0; a < 3; ++a) d[a] = df_div(dun[a], len);
@@ -25,11 +28,11 @@ __device__ __forceinline__ bool setup_ray(const FrameParams& p, int i, int j, df
     for (int a = 0; a < 3; ++a) {
         const df hi = df_make((float)(p.n[a] - 1));
         if (df_is_zero(d[a])) {
-            if (df_lt(p.eye[a], df_make(0.0f)) || df_gt(p.eye[a], hi)) return false;
+            if (df_lt(cam.eye[a], df_make(0.0f)) || df_gt(cam.eye[a], hi)) return false;
             continue;
         }
-        df ta = df_div(df_neg(p.eye[a]), d[a]);
-        df tb = df_div(df_sub(hi, p.eye[a]), d[a]);
+        df ta = df_div(df_neg(cam.eye[a]), d[a]);
+        df tb = df_div(df_sub(hi, cam.eye[a]), d[a]);
         tn = df_max(tn, df_min(ta, tb));
         tf = df_min(tf, df_max(ta, tb));
     }
@@ -37,8 +40,12 @@ __device__ __forceinline__ bool setup_ray(const FrameParams& p, int i, int j, df
     if (!df_gt(tf, t0)) return false;
     const df L = df_sub(tf, t0);
     n_samples = (int)df_ceil(df_div(L, p.dt));
-    for (int a = 0; a < 3; ++a) pe[a] = df_add(p.eye[a], df_mul(t0, d[a]));
+    for (int a = 0; a < 3; ++a) pe[a] = df_add(cam.eye[a], df_mul(t0, d[a]));
     return n_samples > 0;
+}
+
+__device__ __forceinline__ bool setup_ray(const FrameParams& p, int i, int j, df d[3], df pe[3], int& n_samples) {
+    return setup_ray(p, p, i, j, d, pe, n_samples);
 }
 
 // Sample range [klo, khi) owned by brick bidx (sample p_k = pe + k dt d belongs to

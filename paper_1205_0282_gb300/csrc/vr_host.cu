@@ -2,318 +2,11 @@
 // function and camera state, the per-frame planner (rendering rectangles, exact
 // empty-space skipping, view-order sort, work-list build; Sections 2.3.1-2.3.3 of
 // arXiv:1205.0282) and the stream-ordered frame pipeline.
-#include <algorithm>
-#include <cfloat>
-#include <chrono>
-#include <cmath>
-#include <cstdio>
-#include <cstring>
-#include <string>
-#include <vector>
+#include "vr_ctx.cuh"
 
-#include "../../include/vr.h"
-#include "vr_alpha_fit.h"
-#include "vr_internal.cuh"
+using namespace vrh;
 
-using vr::df;
-
-namespace {
-
-constexpr int kSlots = 3;  // frames that may be in flight per context
-
-struct Slot {
-    vr::Item* h_items = nullptr;
-    int32_t* h_tile_start = nullptr;
-    size_t cap_items = 0, cap_tiles = 0;
-    vr::Item* d_items = nullptr;
-    int32_t* d_tile_start = nullptr;
-    size_t dcap_items = 0, dcap_tiles = 0;
-    float4* d_frags = nullptr;
-    size_t cap_frags = 0;  // float4 pixels
-    float4* d_img = nullptr;
-    size_t cap_img = 0;    // float4 pixels
-    unsigned char* h_frame = nullptr;  // camera tables + transfer function, pinned
-    unsigned char* d_frame = nullptr;
-    size_t cap_frame = 0, dcap_frame = 0;
-    vr::Stats* d_stats = nullptr;
-    vr::Stats* h_stats = nullptr;
-    int32_t* h_slot_of = nullptr;  // out-of-core: cache slot of each brick (pinned)
-    int32_t* d_slot_of = nullptr;
-    size_t cap_slot_of = 0, dcap_slot_of = 0;
-    cudaEvent_t ev_begin = nullptr, ev_march0 = nullptr, ev_march1 = nullptr, ev_end = nullptr;
-    bool pending = false;
-    // host-side facts of the frame in flight
-    int64_t items = 0, bricks_rendered = 0, bricks_skipped = 0, touched_bytes = 0;
-    int64_t h2d_bytes = 0, d2h_bytes = 0, launches = 0, fragments = 0;
-    int64_t bricks_uploaded = 0, bricks_cached = 0;
-    double plan_ms = 0.0;
-};
-
-struct Basis {
-    double f[3], r[3], u[3];
-    double tan_half, aspect;
-};
-
-bool make_basis(const vr_camera& c, Basis& b) {
-    double f[3], n = 0;
-    for (int a = 0; a < 3; ++a) {
-        f[a] = c.target[a] - c.eye[a];
-        n += f[a] * f[a];
-    }
-    n = std::sqrt(n);
-    if (!(n > 0)) return false;
-    for (int a = 0; a < 3; ++a) b.f[a] = f[a] / n;
-    double r[3] = {b.f[1] * c.up[2] - b.f[2] * c.up[1], b.f[2] * c.up[0] - b.f[0] * c.up[2],
-                   b.f[0] * c.up[1] - b.f[1] * c.up[0]};
-    n = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    if (!(n > 1e-300)) return false;
-    for (int a = 0; a < 3; ++a) b.r[a] = r[a] / n;
-    b.u[0] = b.r[1] * b.f[2] - b.r[2] * b.f[1];
-    b.u[1] = b.r[2] * b.f[0] - b.r[0] * b.f[2];
-    b.u[2] = b.r[0] * b.f[1] - b.r[1] * b.f[0];
-    b.tan_half = std::tan(c.fovy_deg * 3.14159265358979323846 / 360.0);
-    b.aspect = (double)c.width / (double)c.height;
-    return true;
-}
-
-bool camera_valid(const vr_camera& c) {
-    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return false;
-    if (!(c.fovy_deg > 0.0 && c.fovy_deg < 180.0)) return false;
-    // step >= 0.01 keeps every sample index below 2^24 (exact in FP32) for cubes up
-    // to 65536 voxels per axis
-    if (!(c.step >= 0.01 && c.step <= 1000.0)) return false;
-    if (!(c.term_alpha > 0.0 && c.term_alpha <= 1.0)) return false;
-    for (int a = 0; a < 3; ++a)
-        if (!std::isfinite(c.eye[a]) || !std::isfinite(c.target[a]) || !std::isfinite(c.up[a]))
-            return false;
-    return true;
-}
-
-int64_t bricks_along(int64_t n, int64_t B) { return (n - 1 + B - 1) / B; }
-
-// Rendering rectangle of the box [lo, hi] (Section 2.3.2: project the sub-cube's
-// vertices, take their bounding rectangle).  Pixel (i, j) has its centre at
-// ((i+.5)/W, (j+.5)/H) of the image; the rectangle is widened by one pixel so that
-// rounding can never drop a pixel whose ray touches the box.  Returns false if the
-// rectangle is empty after clipping, or if the whole box lies behind the eye plane
-// (every ray leaves the eye forward along f).  A box reaching across the eye plane
-// maps to the whole image.
-bool box_rect(const vr_camera& c, const Basis& b, const double lo[3], const double hi[3],
-              int32_t rect[4]) {
-    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
-    bool behind = false;
-    int back = 0;
-    for (int k = 0; k < 8; ++k) {
-        double P[3] = {(k & 1) ? hi[0] : lo[0], (k & 2) ? hi[1] : lo[1], (k & 4) ? hi[2] : lo[2]};
-        double v[3] = {P[0] - c.eye[0], P[1] - c.eye[1], P[2] - c.eye[2]};
-        double zc = v[0] * b.f[0] + v[1] * b.f[1] + v[2] * b.f[2];
-        if (zc < -1e-6) ++back;
-        if (!(zc > 1e-9)) behind = true;
-        if (behind) continue;
-        double xc = v[0] * b.r[0] + v[1] * b.r[1] + v[2] * b.r[2];
-        double yc = v[0] * b.u[0] + v[1] * b.u[1] + v[2] * b.u[2];
-        double sx = xc / (zc * b.tan_half * b.aspect), sy = yc / (zc * b.tan_half);
-        double pi = (sx + 1.0) * 0.5 * c.width - 0.5;
-        double pj = (1.0 - sy) * 0.5 * c.height - 0.5;
-        xmin = std::min(xmin, pi);
-        xmax = std::max(xmax, pi);
-        ymin = std::min(ymin, pj);
-        ymax = std::max(ymax, pj);
-    }
-    if (back == 8) {
-        rect[0] = rect[1] = 0;
-        rect[2] = rect[3] = -1;
-        return false;
-    }
-    if (behind) {
-        rect[0] = 0;
-        rect[1] = 0;
-        rect[2] = c.width - 1;
-        rect[3] = c.height - 1;
-        return true;
-    }
-    double x0 = std::floor(xmin) - 1, x1 = std::ceil(xmax) + 1;
-    double y0 = std::floor(ymin) - 1, y1 = std::ceil(ymax) + 1;
-    x0 = std::max(x0, 0.0);
-    y0 = std::max(y0, 0.0);
-    x1 = std::min(x1, (double)c.width - 1);
-    y1 = std::min(y1, (double)c.height - 1);
-    if (x1 < x0 || y1 < y0) {
-        rect[0] = rect[1] = 0;
-        rect[2] = rect[3] = -1;
-        return false;
-    }
-    rect[0] = (int32_t)x0;
-    rect[1] = (int32_t)y0;
-    rect[2] = (int32_t)x1;
-    rect[3] = (int32_t)y1;
-    return true;
-}
-
-// Sampling region of brick (ix, iy, iz): [b*B, min((b+1)*B, n-1)] per axis.
-void brick_box(const int64_t n[3], const int32_t B[3], const int64_t idx[3], double lo[3],
-               double hi[3]) {
-    for (int a = 0; a < 3; ++a) {
-        lo[a] = (double)(idx[a] * B[a]);
-        hi[a] = (double)std::min<int64_t>((idx[a] + 1) * B[a], n[a] - 1);
-    }
-}
-
-// Maximum of the piecewise-linear opacity over [lo, hi] (exact: endpoints and the
-// control points strictly inside).
-double tf_alpha_max(const std::vector<double>& tf, double lo, double hi) {
-    const int n = (int)(tf.size() / 5);
-    auto eval = [&](double v) {
-        if (v <= tf[0]) return tf[4];
-        if (v >= tf[5 * (n - 1)]) return tf[5 * (n - 1) + 4];
-        int s = 0;
-        while (!(v < tf[5 * (s + 1)])) ++s;
-        double w = (v - tf[5 * s]) / (tf[5 * (s + 1)] - tf[5 * s]);
-        return tf[5 * s + 4] + w * (tf[5 * (s + 1) + 4] - tf[5 * s + 4]);
-    };
-    double m = std::max(eval(lo), eval(hi));
-    for (int s = 0; s < n; ++s)
-        if (tf[5 * s] > lo && tf[5 * s] < hi) m = std::max(m, tf[5 * s + 4]);
-    return m;
-}
-
-}  // namespace
-
-struct vr_ctx {
-    int device = 0;
-    std::string err;
-    int sm_count = 0;
-
-    float* d_cube = nullptr;     // [z][y][x], row pitch nx_pad floats (16-byte rows for TMA)
-    int64_t n[3] = {0, 0, 0};
-    int64_t nx_pad = 0;
-    float* d_cube_xzy = nullptr; // transposed copy [x][z][y], row pitch ny_pad (sweeps along x)
-    int64_t ny_pad = 0;
-    CUtensorMap* d_tmaps = nullptr;  // tensor maps of the TMA march (device memory)
-    cudaArray_t tex_arr[3] = {nullptr, nullptr, nullptr};  // texture march: layered copies
-    cudaTextureObject_t tex_obj[3] = {0, 0, 0};
-    bool tex_ready = false;
-    int precision = VR_PRECISION_F32;  // storage of the layered copies
-    float* d_brick_scale = nullptr;    // FP8 storage: per-brick scale
-    std::vector<float2> h_minmax_q;    // FP16/FP8 storage: per-brick [min, max] of the stored values
-    int tmaps_per_brick = 0;
-    bool tma_ready = false;
-
-    bool bricked = false;
-    int32_t B[3] = {0, 0, 0};
-    int32_t nb[3] = {0, 0, 0};
-    int64_t n_bricks = 0;
-    float2* d_minmax = nullptr;
-    std::vector<float2> h_minmax;
-
-    bool tf_set = false;
-    std::vector<double> tf;
-    std::vector<float4> tf_rgba;
-    std::vector<float> tf_v;
-    int tf_uniform = 0;
-    float tf_v0 = 0, tf_inv_dv = 0;
-
-    bool cam_set = false;
-    vr_camera cam{};
-    Basis basis{};
-    std::vector<df> q;  // qx (width entries) then qy (height entries)
-    float alpha_poly[vr::kAlphaPolyTerms] = {};
-    double alpha_split = 0.5;
-    float alpha_small[vr::kAlphaSmallTerms] = {};
-    double small_split = 0.1;
-
-    bool skip_empty = true, rect_cull = true;
-    int mode = 0;
-    int kernel = VR_KERNEL_AUTO;
-    int tex_fits = -1;  // -1 unknown, 0/1: the cube fits the layered-texture limits
-
-    // out-of-core mode (vr_load_cube_host): cube in host memory, bricks cached on the device
-    bool ooc = false;
-    const float* h_src = nullptr;      // the caller's cube
-    float* h_store = nullptr;          // pinned brick store, brick b at b * slot_floats
-    size_t store_bytes = 0;
-    int64_t slot_floats = 0;           // (Bx+1)(By+1)(Bz+1)
-    int64_t budget = 0;                // VR_OPT_DEVICE_BUDGET (<= 0: every brick)
-    float* d_pool = nullptr;           // device brick cache
-    vr::Residency res;
-    int64_t ooc_frame = 0;
-    cudaStream_t copy_stream = nullptr;
-    cudaStream_t ring_stream = nullptr;   // marches of streamed bricks, beside the resident ones
-    cudaEvent_t ev_ring_start = nullptr, ev_ring_end = nullptr;
-    cudaEvent_t ev_march_done = nullptr;  // end of the last out-of-core frame's marching
-    cudaEvent_t ev_copy_done = nullptr;   // end of the last upload issued
-    std::vector<cudaEvent_t> ev_chunk;
-    cudaEvent_t ev_half_read[2] = {nullptr, nullptr};  // last march that read each ring half
-    int32_t ring_first_half = 0;                       // ring half the next frame starts in
-    std::vector<int32_t> ooc_ring;
-    std::vector<int32_t> ooc_bricks, ooc_slot, ooc_up, ooc_item_off;
-    std::vector<vr::Item> ooc_items;
-
-    // sort-last distribution: the bricks this context renders, [region_lo, region_hi)
-    int32_t region_lo[3] = {0, 0, 0}, region_hi[3] = {0, 0, 0};
-    float4* d_comp = nullptr;  // root fold output when the caller passes a host buffer
-    size_t cap_comp = 0;
-
-    Slot slots[kSlots];
-    int next_slot = 0;
-    vr_stats acc{};
-
-    // planner scratch (host)
-    std::vector<int32_t> plan_count, plan_fill, plan_sweep;
-    struct PB {
-        int32_t key, id, rect[4];
-    };
-    std::vector<PB> plan_bricks;
-};
-
-namespace {
-
-int fail(vr_ctx* c, int code, const std::string& msg) {
-    if (c) c->err = msg;
-    return code;
-}
-
-int cuda_fail(vr_ctx* c, cudaError_t e, const char* what) {
-    return fail(c, VR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-#define VR_CUDA(ctx, call)                                      \
-    do {                                                        \
-        cudaError_t _e = (call);                                \
-        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
-    } while (0)
-
-template <typename T>
-int grow_device(vr_ctx* c, T*& p, size_t& cap, size_t need) {
-    if (need <= cap && p) return VR_OK;
-    size_t n = std::max(need, cap + cap / 2);
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    if (cudaMalloc((void**)&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, VR_ENOMEM, "device allocation failed");
-    }
-    cap = n;
-    return VR_OK;
-}
-
-template <typename T>
-int grow_pinned(vr_ctx* c, T*& p, size_t& cap, size_t need) {
-    if (need <= cap && p) return VR_OK;
-    size_t n = std::max(need, cap + cap / 2);
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    cap = 0;
-    if (cudaMallocHost((void**)&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, VR_ENOMEM, "pinned host allocation failed");
-    }
-    cap = n;
-    return VR_OK;
-}
-
-// Wait for a slot's frame, fold its numbers into the statistics.
+namespace vrh {
 int retire(vr_ctx* c, Slot& s) {
     if (!s.pending) return VR_OK;
     VR_CUDA(c, cudaEventSynchronize(s.ev_end));
@@ -554,7 +247,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
     return VR_OK;
 }
 
-}  // namespace
+}  // namespace vrh
 
 // =============================================================================== ABI
 
@@ -750,7 +443,7 @@ int vr_brick(vr_ctx* c, int32_t bx, int32_t by, int32_t bz) {
 
 }  // extern "C"
 
-namespace {
+namespace vrh {
 
 // Transposed copy and tensor maps for the TMA-staged march (built on first use).
 int prepare_tma(vr_ctx* c) {
@@ -861,7 +554,7 @@ int prepare_tex(vr_ctx* c) {
     return VR_OK;
 }
 
-}  // namespace
+}  // namespace vrh
 
 extern "C" {
 
@@ -961,7 +654,46 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
 
 }  // extern "C"
 
-namespace {
+namespace vrh {
+
+// The frame parameters that do not depend on the camera or the frame's buffers:
+// cube, bricking, step, termination, transfer-function scalars, opacity-correction
+// fits, mode, storage.  Everything else is zero.
+void fill_common_params(vr_ctx* c, vr::FrameParams& p) {
+    std::memset(&p, 0, sizeof(p));
+    for (int a = 0; a < 3; ++a) {
+        p.n[a] = (int32_t)c->n[a];
+        p.B[a] = c->B[a];
+        p.nb[a] = c->nb[a];
+    }
+    p.dt = vr::df_from_double(c->cam.step);
+    p.dt_f = (float)c->cam.step;
+    p.tau = (float)c->cam.term_alpha;
+    p.cube = c->d_cube;
+    p.stride_y = c->nx_pad;
+    p.stride_z = c->nx_pad * c->n[1];
+    p.offsets32 = ((int64_t)c->B[2] + 1) * p.stride_z + ((int64_t)c->B[1] + 1) * p.stride_y +
+                      c->B[0] + 1 < ((int64_t)1 << 32) ? 1 : 0;
+    p.tf_n = (int32_t)(c->tf.size() / 5);
+    p.tf_uniform = c->tf_uniform;
+    p.tf_v0 = c->tf_v0;
+    p.tf_inv_dv = c->tf_inv_dv;
+    std::memcpy(p.alpha_poly, c->alpha_poly, sizeof(p.alpha_poly));
+    p.alpha_split = (float)c->alpha_split;
+    p.poly_scale = (float)(2.0 / c->alpha_split);
+    std::memcpy(p.alpha_small, c->alpha_small, sizeof(p.alpha_small));
+    p.small_split = (float)c->small_split;
+    p.small_scale = (float)(2.0 / c->small_split);
+    p.mode = c->mode;
+    p.gmax = FLT_MAX;
+    for (const float2& mm : c->h_minmax) p.gmax = p.gmax == FLT_MAX ? mm.y : std::max(p.gmax, mm.y);
+    p.tmaps = c->d_tmaps;
+    p.tmaps_per_brick = c->tmaps_per_brick;
+    for (int a = 0; a < 3; ++a) p.tex[a] = c->tex_obj[a];
+    p.precision = c->precision == VR_PRECISION_F8 ? vr::kPrecF8
+                  : c->precision == VR_PRECISION_F16 ? vr::kPrecF16 : vr::kPrecF32;
+    p.brick_scale = c->d_brick_scale;
+}
 
 // Out-of-core frame: cache slots for the frame's bricks, the slot table, and the
 // march launches, each a contiguous range of items with the bricks it must wait
@@ -1108,15 +840,12 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     std::memcpy(s.h_frame + tf_v_off, c->tf_v.data(), c->tf_v.size() * sizeof(float));
 
     vr::FrameParams p;
-    std::memset(&p, 0, sizeof(p));
+    fill_common_params(c, p);
     for (int a = 0; a < 3; ++a) {
         p.eye[a] = vr::df_from_double(c->cam.eye[a]);
         p.f[a] = vr::df_from_double(c->basis.f[a]);
         p.r[a] = vr::df_from_double(c->basis.r[a]);
         p.u[a] = vr::df_from_double(c->basis.u[a]);
-        p.n[a] = (int32_t)c->n[a];
-        p.B[a] = c->B[a];
-        p.nb[a] = c->nb[a];
     }
     p.qx = reinterpret_cast<const df*>(s.d_frame);
     p.qy = reinterpret_cast<const df*>(s.d_frame) + c->cam.width;
@@ -1125,10 +854,6 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     p.tiles_x = tiles_x;
     p.tiles_y = tiles_y;
     p.tile = T;
-    p.dt = vr::df_from_double(c->cam.step);
-    p.dt_f = (float)c->cam.step;
-    p.tau = (float)c->cam.term_alpha;
-    p.cube = c->d_cube;
     if (c->ooc) {
         p.pool = c->d_pool;
         p.slot_of = s.d_slot_of;
@@ -1136,33 +861,10 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
         p.pool_sy = c->B[0] + 1;
         p.pool_sz = (c->B[0] + 1) * (c->B[1] + 1);
     }
-    p.stride_y = c->nx_pad;
-    p.stride_z = c->nx_pad * c->n[1];
-    p.offsets32 = ((int64_t)c->B[2] + 1) * p.stride_z + ((int64_t)c->B[1] + 1) * p.stride_y +
-                      c->B[0] + 1 < ((int64_t)1 << 32) ? 1 : 0;
     p.tf_rgba = reinterpret_cast<const float4*>(s.d_frame + tf_rgba_off);
     p.tf_v = reinterpret_cast<const float*>(s.d_frame + tf_v_off);
-    p.tf_n = (int32_t)(c->tf.size() / 5);
-    p.tf_uniform = c->tf_uniform;
-    p.tf_v0 = c->tf_v0;
-    p.tf_inv_dv = c->tf_inv_dv;
-    std::memcpy(p.alpha_poly, c->alpha_poly, sizeof(p.alpha_poly));
-    p.alpha_split = (float)c->alpha_split;
-    p.poly_scale = (float)(2.0 / c->alpha_split);
-    std::memcpy(p.alpha_small, c->alpha_small, sizeof(p.alpha_small));
-    p.small_split = (float)c->small_split;
-    p.small_scale = (float)(2.0 / c->small_split);
-    p.mode = c->mode;
-    p.gmax = FLT_MAX;
-    for (const float2& mm : c->h_minmax) p.gmax = p.gmax == FLT_MAX ? mm.y : std::max(p.gmax, mm.y);
     p.items = s.d_items;
     p.n_items = (int32_t)n_items;
-    p.tmaps = c->d_tmaps;
-    p.tmaps_per_brick = c->tmaps_per_brick;
-    for (int a = 0; a < 3; ++a) p.tex[a] = c->tex_obj[a];
-    p.precision = c->precision == VR_PRECISION_F8 ? vr::kPrecF8
-                  : c->precision == VR_PRECISION_F16 ? vr::kPrecF16 : vr::kPrecF32;
-    p.brick_scale = c->d_brick_scale;
     p.tile_start = s.d_tile_start;
     p.frags = s.d_frags;
     p.out = out_on_device ? reinterpret_cast<float4*>(out_rgba) : s.d_img;
@@ -1298,7 +1000,7 @@ void region_rect(const vr_camera& cam, const Basis& b, const int64_t n[3], const
     box_rect(cam, b, blo, bhi, rect);
 }
 
-}  // namespace
+}  // namespace vrh
 
 extern "C" {
 

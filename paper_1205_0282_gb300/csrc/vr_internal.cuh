@@ -39,6 +39,21 @@ struct Stats {
     int pad;
 };
 
+// One frame of a batch (the serving loop): its camera, tiles and image.  The
+// frames of a batch share everything else in FrameParams (cube, transfer
+// function, step, termination, fragment buffer).
+struct FrameCam {
+    df eye[3];
+    df f[3], r[3], u[3];
+    const df* qx;
+    const df* qy;
+    int32_t width, height, tiles_x, tiles_y;
+    const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
+    float4* out;                // float4[height][width]
+    int32_t tile_base;          // first composite block of this frame in the batch
+    int32_t pad;
+};
+
 // Everything a frame's kernels need, passed by value.
 struct FrameParams {
     // camera (double-float)
@@ -91,6 +106,8 @@ struct FrameParams {
     int64_t slot_stride;        // floats per slot, (Bx+1)(By+1)(Bz+1)
     int32_t pool_sy, pool_sz;   // row and plane strides inside a slot
     float4* frags;
+    const FrameCam* cams;       // batch: per-frame cameras (items carry the frame in sweep >> 3)
+    int32_t n_cams;
     float4* out;                // image window: pixel (i, j) of the frame goes to
     int32_t out_x0, out_y0;     // out[(j - out_y0) * out_w + (i - out_x0)] if it lies in
     int32_t out_w, out_h;       // [out_x0, out_x0 + out_w) x [out_y0, out_y0 + out_h)
@@ -115,6 +132,10 @@ cudaError_t launch_brick_minmax(const float* cube, int64_t pitch, const int32_t 
 cudaError_t launch_march(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tma(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s);
+// Batch (vr_serve.cu): the texture march over items of several frames, and the
+// composite of every tile of every frame (p.n_cams frames, total_tiles blocks).
+cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s);
+cudaError_t launch_composite_batch(const FrameParams& p, int32_t total_tiles, cudaStream_t s);
 cudaError_t fill_tex_layers(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch, int S,
                             int precision, cudaSurfaceObject_t surf, const float* scale, const int32_t B[3],
                             const int32_t nb[3], cudaStream_t s);

@@ -233,6 +233,35 @@ __global__ void __launch_bounds__(256) composite_kernel(const FrameParams p) {
     if (wi >= 0 && wi < p.out_w && wj >= 0 && wj < p.out_h) p.out[(int64_t)wj * p.out_w + wi] = acc;
 }
 
+// Batch composite: block b is tile b - cams[k].tile_base of the frame k whose
+// blocks contain b (emission-absorption, 8x8 tiles).
+__global__ void __launch_bounds__(kTilePixels) composite_batch_kernel(const FrameParams p) {
+    int k = 0;
+    while (k + 1 < p.n_cams && (int)blockIdx.x >= p.cams[k + 1].tile_base) ++k;
+    const FrameCam& cam = p.cams[k];
+    const int t = blockIdx.x - cam.tile_base;
+    const int tx = t % cam.tiles_x, ty = t / cam.tiles_x;
+    const int i = tx * kTile + threadIdx.x % kTile, j = ty * kTile + threadIdx.x / kTile;
+    if (i >= cam.width || j >= cam.height) return;
+    const int f0 = cam.tile_start[t], f1 = cam.tile_start[t + 1];
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int f = f0; f < f1; ++f) {
+        if (acc.w >= p.tau) break;
+        const float4 fr = p.frags[(int64_t)f * kTilePixels + threadIdx.x];
+        const float tr = 1.0f - acc.w;
+        acc.x = fmaf(tr, fr.x, acc.x);
+        acc.y = fmaf(tr, fr.y, acc.y);
+        acc.z = fmaf(tr, fr.z, acc.z);
+        acc.w = fmaf(tr, fr.w, acc.w);
+    }
+    cam.out[(int64_t)j * cam.width + i] = acc;
+}
+
+cudaError_t launch_composite_batch(const FrameParams& p, int32_t total_tiles, cudaStream_t s) {
+    if (total_tiles > 0) composite_batch_kernel<<<total_tiles, kTilePixels, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_composite(const FrameParams& p, cudaStream_t s) {
     composite_kernel<<<p.tiles_x * p.tiles_y, p.tile * p.tile, 0, s>>>(p);
     return cudaGetLastError();

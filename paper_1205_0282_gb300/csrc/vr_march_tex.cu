@@ -97,13 +97,13 @@ __device__ __forceinline__ int step_of(const FrameParams& p, int a) {
     return a == 0 ? 1 : (a == 1 ? p.nb[0] : p.nb[0] * p.nb[1]);
 }
 
-template <int S, bool UNIFORM, int PREC>
-__device__ __forceinline__ void march_item(const FrameParams& p, const Item& item, const float4* s_rgba,
-                                           const float* s_v) {
+template <int S, bool UNIFORM, int PREC, class Cam>
+__device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam, const Item& item,
+                                           const float4* s_rgba, const float* s_v) {
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
     const cudaTextureObject_t tex = p.tex[S];
     const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
-    const int tx = item.tile % p.tiles_x, ty = item.tile / p.tiles_x;
+    const int tx = item.tile % cam.tiles_x, ty = item.tile / cam.tiles_x;
     const int i = tx * kTile + lx, j = ty * kTile + ly;
     int bidx[3], O[3], imax[3];
     bidx[0] = item.brick % p.nb[0];
@@ -120,7 +120,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
     {
         df d[3], pe[3];
         int n_samples = 0;
-        if (i < p.width && j < p.height && setup_ray(p, i, j, d, pe, n_samples)) {
+        if (i < cam.width && j < cam.height && setup_ray(p, cam, i, j, d, pe, n_samples)) {
             int klo, khi;
             brick_range(p, bidx, d, pe, n_samples, klo, khi);
             if (khi > klo) {
@@ -250,9 +250,30 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
     __syncthreads();
     const Item item = p.items[blockIdx.x];
     switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM, PREC>(p, item, s_rgba, s_v); break;
-        case 1: march_item<1, UNIFORM, PREC>(p, item, s_rgba, s_v); break;
-        default: march_item<2, UNIFORM, PREC>(p, item, s_rgba, s_v); break;
+        case 0: march_item<0, UNIFORM, PREC>(p, p, item, s_rgba, s_v); break;
+        case 1: march_item<1, UNIFORM, PREC>(p, p, item, s_rgba, s_v); break;
+        default: march_item<2, UNIFORM, PREC>(p, p, item, s_rgba, s_v); break;
+    }
+}
+
+// Batch of frames (the serving loop): the same march, each item's camera read
+// from the frame it belongs to (item.sweep >> 3).
+template <bool UNIFORM, int PREC>
+__global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_batch_kernel(const FrameParams p) {
+    extern __shared__ float4 s_dyn[];
+    float4* s_rgba = s_dyn;
+    float* s_v = reinterpret_cast<float*>(s_dyn + p.tf_n + 1);
+    for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
+        s_rgba[k] = p.tf_rgba[k];
+        if (k < p.tf_n) s_v[k] = p.tf_v[k];
+    }
+    __syncthreads();
+    const Item item = p.items[blockIdx.x];
+    const FrameCam& cam = p.cams[item.sweep >> 3];
+    switch (item.sweep & 3) {
+        case 0: march_item<0, UNIFORM, PREC>(p, cam, item, s_rgba, s_v); break;
+        case 1: march_item<1, UNIFORM, PREC>(p, cam, item, s_rgba, s_v); break;
+        default: march_item<2, UNIFORM, PREC>(p, cam, item, s_rgba, s_v); break;
     }
 }
 
@@ -384,6 +405,29 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
     } else {  // FP32 and FP16 textures share the kernel
         if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF32>);
         else go(texm::march_tex_kernel<false, kPrecF32>);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
+    if (p.n_items == 0) return cudaSuccess;
+    const size_t smem = (size_t)(p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
+    auto go = [&](auto kern) {
+        const int blocks = texm::tex_blocks_per_sm(p.precision == kPrecF8 ? kPrecF8 : kPrecF32);
+        const int pct = (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2;
+        static int carveout = -1;
+        if (carveout != pct) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            carveout = pct;
+        }
+        kern<<<p.n_items, kTilePixels, smem, s>>>(p);
+    };
+    if (p.precision == kPrecF8) {
+        if (p.tf_uniform) go(texm::march_tex_batch_kernel<true, kPrecF8>);
+        else go(texm::march_tex_batch_kernel<false, kPrecF8>);
+    } else {
+        if (p.tf_uniform) go(texm::march_tex_batch_kernel<true, kPrecF32>);
+        else go(texm::march_tex_batch_kernel<false, kPrecF32>);
     }
     return cudaGetLastError();
 }
