@@ -58,6 +58,12 @@ def parse():
                     help="out-of-core: the cube stays in host memory, bricks stream into a device cache")
     ap.add_argument("--budget-gib", type=float, default=0.0,
                     help="device brick-cache budget for --ooc in GiB (0: every brick)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving loop: Poisson arrivals of camera/TF/resolution requests, p50/p99 latency")
+    ap.add_argument("--rate", type=float, default=200.0, help="--serve: mean arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="--serve: length of the arrival window")
+    ap.add_argument("--arena-gib", type=float, default=16.0, help="--serve: device arena (two batch halves)")
+    ap.add_argument("--max-batch", type=int, default=32, help="--serve: frames per batch at most")
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -535,8 +541,120 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+SERVE_RESOLUTIONS = [(512, 512), (1280, 720), (1920, 1080), (3840, 2160)]
+
+
+def run_serve(args):
+    """Serving workload: requests arrive as a Poisson process (mean ``--rate`` per
+    second) for ``--serve-seconds``; each asks for an orbit pose at a resolution
+    drawn uniformly from 512x512, 1280x720, 1920x1080 and 3840x2160, and one in
+    ten switches the transfer function (TF-A <-> TF-B).  The cube is resident
+    (FP16 storage unless --precision says otherwise).  Latency = completion time
+    minus arrival time of each request."""
+    import threading
+
+    import torch
+    from paper_1205_0282_gb300 import vr as vrm
+
+    torch.cuda.set_device(0)
+    spec, tf, poses, desc = workload(args)
+    cube = make_cube(spec)
+    r = vrm.VolumeRenderer(0)
+    dcube = torch.from_numpy(cube).cuda()
+    r.load_cube(dcube)
+    del dcube
+    torch.cuda.empty_cache()
+    r.brick(*spec["brick"])
+    tfs = [synth.tf_hi_a(), synth.tf_hi_b()]
+    r.set_transfer_function(tfs[0])
+    r.set_camera(poses[0])
+    prec = {"f32": vrm.VR_PRECISION_F32, "f16": vrm.VR_PRECISION_F16, "f8": vrm.VR_PRECISION_F8}[
+        args.precision if args.precision != "f32" else "f16"]
+    r.set_option(vrm.VR_OPT_PRECISION, prec)
+    r.render()   # builds the layered copies
+    torch.cuda.synchronize()
+
+    rng = np.random.default_rng(7)
+    n = int(rng.poisson(args.rate * args.serve_seconds))
+    arrivals = np.sort(rng.uniform(0.0, args.serve_seconds, n))
+    res = [SERVE_RESOLUTIONS[k] for k in rng.integers(0, len(SERVE_RESOLUTIONS), n)]
+    tf_switch = rng.uniform(size=n) < 0.1
+    # output buffers: enough that none is reused while its request can be in flight
+    pool = {wh: [torch.empty((wh[1], wh[0], 4), dtype=torch.float32, device="cuda") for _ in range(48)]
+            for wh in SERVE_RESOLUTIONS}
+    used = {wh: 0 for wh in SERVE_RESOLUTIONS}
+
+    srv = vrm.Server(r, int(args.arena_gib * 2 ** 30), args.max_batch)
+    # warm the loop up (untimed): one request per resolution
+    for wh in SERVE_RESOLUTIONS:
+        cam = dict(poses[0], width=wh[0], height=wh[1])
+        srv.wait(srv.submit(cam, pool[wh][0]), 120.0)
+    st0 = srv.stats()
+    tickets = [None] * n
+    lat = [None] * n
+    done = threading.Event()
+
+    def waiter():
+        for k in range(n):
+            while tickets[k] is None:
+                time.sleep(0.0002)
+            lat[k] = srv.wait(tickets[k], 300.0)
+        done.set()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    tf_cur = 0
+    clocks_id = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    with ClockSampler(clocks_id) as clocks:
+        t0 = time.perf_counter()
+        for k in range(n):
+            dt = t0 + arrivals[k] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            wh = res[k]
+            cam = dict(poses[k % len(poses)], width=wh[0], height=wh[1])
+            buf = pool[wh][used[wh] % len(pool[wh])]
+            used[wh] += 1
+            new_tf = None
+            if tf_switch[k]:
+                tf_cur ^= 1
+                new_tf = tfs[tf_cur]
+            tickets[k] = srv.submit(cam, buf, new_tf)
+        done.wait()
+        t_end = time.perf_counter()
+    th.join()
+    st = srv.stats()
+    srv.close()
+    r.close()
+    wall = t_end - t0
+    lat = np.array(lat)
+    frames = st["completed"] - st0["completed"]
+    samples = st["samples"] - st0["samples"]
+    batches = st["batches"] - st0["batches"]
+    line = {"metric": METRIC, "value": samples / wall, "unit": UNIT, "n_gpus": 1, "steps": n,
+            "warmup": len(SERVE_RESOLUTIONS), "ms_per_step": 1e3 * wall / max(n, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc.split(", image overridden")[0] + "; serving: Poisson arrivals "
+                       f"{args.rate:g}/s for {args.serve_seconds:g} s, resolutions uniform over "
+                       "512x512/1280x720/1920x1080/3840x2160, 10% transfer-function switches (TF-A/TF-B)",
+                       "storage": {"f32": "FP16", "f16": "FP16", "f8": "FP8 E4M3, per-brick scale"}[args.precision],
+                       "arena_gib": args.arena_gib, "max_batch": args.max_batch,
+                       "l2": "inputs larger than L2, no flush"},
+            "serving": {"requests": n, "completed": frames, "failed": st["failed"] - st0["failed"],
+                        "fps": frames / wall, "wall_s": wall,
+                        "latency_ms_p50": float(np.percentile(lat, 50)),
+                        "latency_ms_p99": float(np.percentile(lat, 99)),
+                        "latency_ms_mean": float(lat.mean()), "latency_ms_max": float(lat.max()),
+                        "batches": batches, "mean_batch": (frames / batches) if batches else None},
+            "gpu_launches": 2 * batches, "clocks": clocks.summary(), "roofline": None, "cpu_baseline": None,
+            "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.serve and args.impl == "ours":
+        return run_serve(args)
     if args.impl == "reference":
         run_reference(args)
     else:

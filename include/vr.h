@@ -330,6 +330,65 @@ int vr_render_rect(vr_ctx* ctx, const int32_t rect[4], float* out_rgba, void* cu
 int vr_composite_subimages(vr_ctx* ctx, int32_t n, const float* const* images, const int32_t* rects,
                            float* out_rgba, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper): requests for frames arrive at any
+ * time and are rendered in batches, each batch one texture-march launch over the
+ * tiles of all its frames and one composite launch.
+ * ------------------------------------------------------------------------- */
+typedef struct vr_server vr_server;
+
+typedef struct {
+    int64_t submitted;       /* requests accepted by vr_server_submit */
+    int64_t completed;       /* requests rendered */
+    int64_t failed;          /* requests that could not be rendered (their wait returns the error) */
+    int64_t batches;         /* batches launched */
+    int64_t batched_frames;  /* frames in those batches (mean batch size = batched_frames / batches) */
+    int64_t samples;         /* samples composited by completed batches */
+    int64_t items;           /* (brick, tile) items marched by completed batches */
+} vr_server_stats;
+
+/*
+ * Start a serving loop on ctx, which must hold a loaded, bricked cube, a transfer
+ * function and a camera, in emission-absorption mode with the texture march
+ * (VR_KERNEL_TEX or VR_KERNEL_AUTO on a cube within the texture limits; any
+ * VR_OPT_PRECISION).  The loop owns ctx until vr_server_destroy: no other call
+ * may use ctx meanwhile.  It allocates arena_bytes of device memory (>= 64 MiB)
+ * in two halves, one per batch in flight, and pinned staging of the same size.
+ * A worker thread admits queued requests in arrival order into a batch while
+ * they share the transfer function, step and term_alpha, number at most
+ * max_batch, and their work lists and fragments fit one half; it plans the next
+ * batch while the GPU renders the current one.  A completion thread marks
+ * requests done when their batch's event fires.
+ * Errors: VR_EINVAL, VR_ESTATE, VR_ENOMEM, VR_ECUDA.
+ */
+int vr_server_create(vr_ctx* ctx, int64_t arena_bytes, int32_t max_batch, vr_server** out);
+
+/*
+ * Queue a frame.  cam: its camera (any resolution, step, term_alpha);
+ * tf_points: NULL for the transfer function in force, else n_tf rows (v, r, g, b,
+ * a) that take effect from this request on; out_rgba: device memory,
+ * float32[height][width][4], written when the request completes (keep it
+ * allocated until vr_server_wait returns).  *ticket identifies the request.
+ * Errors: VR_EINVAL, VR_ESTATE (the loop has stopped after a CUDA error).
+ */
+int vr_server_submit(vr_server* srv, const vr_camera* cam, const double* tf_points, int32_t n_tf,
+                     float* out_rgba, int64_t* ticket);
+
+/*
+ * Wait for a request: at most timeout_s seconds (< 0: no limit; VR_ETIMEOUT when
+ * it runs out, the ticket staying valid).  On return the ticket is released and
+ * *latency_ms (nullable) holds the time from submission to completion.  Returns
+ * the request's status: VR_OK, VR_ENOMEM (its frame does not fit half the arena),
+ * VR_EINVAL, VR_ECUDA.
+ */
+int vr_server_wait(vr_server* srv, int64_t ticket, double timeout_s, double* latency_ms);
+
+/* Counters since vr_server_create.  Errors: VR_EINVAL. */
+int vr_server_get_stats(vr_server* srv, vr_server_stats* out);
+
+/* Finish every queued request, stop the threads and free the loop; NULL is ignored. */
+void vr_server_destroy(vr_server* srv);
+
 /*
  * Allocation-free render (the paper has no counterpart; this serves callers that
  * may not allocate device memory while rendering: an application or plugin that

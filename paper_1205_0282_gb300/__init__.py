@@ -12,7 +12,9 @@ _EXPORTED = ("VolumeRenderer", "VRError", "VR_OPT_MODE", "VR_OPT_RECT_CULL", "VR
              "vr_last_error", "vr_load_cube", "vr_plan_brick_rects", "vr_render",
              "vr_reset_stats", "vr_set_camera", "vr_set_option", "vr_set_transfer_function",
              "vr_kd_partition", "vr_kd_order", "vr_set_region", "vr_region_rect", "vr_plan_region_rect",
-             "vr_render_rect", "vr_composite_subimages", "vr_load_cube_host", "VR_OPT_DEVICE_BUDGET")
+             "vr_render_rect", "vr_composite_subimages", "vr_load_cube_host", "VR_OPT_DEVICE_BUDGET",
+             "Server", "vr_server_create", "vr_server_submit", "vr_server_wait", "vr_server_get_stats",
+             "vr_server_destroy")
 
 __all__ = list(_EXPORTED)
 

@@ -72,7 +72,14 @@ EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_b
            "vr_set_camera", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
            "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_kd_partition", "vr_kd_order",
            "vr_set_region", "vr_region_rect", "vr_plan_region_rect", "vr_render_rect",
-           "vr_composite_subimages", "vr_render_noalloc", "vr_last_error"]
+           "vr_composite_subimages", "vr_server_create", "vr_server_submit", "vr_server_wait",
+           "vr_server_get_stats", "vr_server_destroy", "vr_render_noalloc", "vr_last_error"]
+
+
+class vr_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("batched_frames", ctypes.c_int64), ("samples", ctypes.c_int64),
+                ("items", ctypes.c_int64)]
 
 
 def _load():
@@ -84,6 +91,7 @@ def _load():
     lib.vr_create.argtypes = [ctypes.POINTER(P), I32]
     lib.vr_destroy.argtypes = [P]
     lib.vr_destroy.restype = None
+    lib.vr_server_destroy.restype = None
     lib.vr_load_cube.argtypes = [P, P, I64, I64, I64]
     lib.vr_load_cube_host.argtypes = [P, P, I64, I64, I64]
     lib.vr_brick.argtypes = [P, I32, I32, I32]
@@ -103,12 +111,17 @@ def _load():
     lib.vr_plan_region_rect.argtypes = [ctypes.POINTER(vr_camera), I64, I64, I64, P, P, P, P]
     lib.vr_render_rect.argtypes = [P, P, P, P]
     lib.vr_composite_subimages.argtypes = [P, I32, P, P, P, P]
+    lib.vr_server_create.argtypes = [P, I64, I32, ctypes.POINTER(P)]
+    lib.vr_server_submit.argtypes = [P, ctypes.POINTER(vr_camera), P, I32, P, ctypes.POINTER(I64)]
+    lib.vr_server_wait.argtypes = [P, I64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.vr_server_get_stats.argtypes = [P, ctypes.POINTER(vr_server_stats)]
+    lib.vr_server_destroy.argtypes = [P]
     lib.vr_render_noalloc.argtypes = [P, I64, I64, I64, I32, I32, I32, P, I32,
                                       ctypes.POINTER(vr_camera), P, P]
     lib.vr_last_error.argtypes = [P]
     lib.vr_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("vr_destroy", "vr_last_error"):
+        if name not in ("vr_destroy", "vr_last_error", "vr_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -327,6 +340,77 @@ def vr_composite_subimages(ctx, images, rects, out, stream=None) -> None:
     on_device = hasattr(out, "is_cuda") and out.is_cuda
     _check(ctx, _lib.vr_composite_subimages(ctx, n, ctypes.cast(ptrs, ctypes.c_void_p), R.ctypes.data, addr,
                                             _stream_handle(stream) if on_device else None))
+
+
+def vr_server_create(ctx, arena_bytes: int, max_batch: int = 64):
+    h = ctypes.c_void_p()
+    _check(ctx, _lib.vr_server_create(ctx, int(arena_bytes), int(max_batch), ctypes.byref(h)))
+    return h
+
+
+def vr_server_submit(srv, ctx, cam: dict, out, tf=None) -> int:
+    """Queue a frame into ``out`` (CUDA float32 (H, W, 4)); ``tf`` None keeps the
+    transfer function in force.  Returns the ticket.  ``ctx`` is the served
+    context (for error messages)."""
+    c = make_camera(cam)
+    addr, keep = _ptr(out)
+    t = ctypes.c_int64()
+    if tf is None:
+        rc = _lib.vr_server_submit(srv, ctypes.byref(c), None, 0, addr, ctypes.byref(t))
+    else:
+        pts = np.ascontiguousarray(tf, dtype=np.float64).reshape(-1, 5)
+        rc = _lib.vr_server_submit(srv, ctypes.byref(c), pts.ctypes.data, len(pts), addr, ctypes.byref(t))
+    _check(ctx, rc)
+    return t.value
+
+
+def vr_server_wait(srv, ctx, ticket: int, timeout_s: float = -1.0) -> float:
+    """Wait for a request; returns its latency in ms (submission to completion)."""
+    lat = ctypes.c_double()
+    rc = _lib.vr_server_wait(srv, int(ticket), float(timeout_s), ctypes.byref(lat))
+    if rc != VR_OK:
+        raise VRError(rc, f"request {ticket} failed")
+    return lat.value
+
+
+def vr_server_get_stats(srv) -> dict:
+    s = vr_server_stats()
+    rc = _lib.vr_server_get_stats(srv, ctypes.byref(s))
+    if rc != VR_OK:
+        raise VRError(rc, "vr_server_get_stats")
+    return {name: getattr(s, name) for name, _ in vr_server_stats._fields_}
+
+
+def vr_server_destroy(srv) -> None:
+    _lib.vr_server_destroy(srv)
+
+
+class Server:
+    """A serving loop on a VolumeRenderer (which it owns until closed)."""
+
+    def __init__(self, renderer, arena_bytes: int, max_batch: int = 64):
+        self.r = renderer
+        self.h = vr_server_create(renderer.ctx, arena_bytes, max_batch)
+
+    def submit(self, cam: dict, out, tf=None) -> int:
+        return vr_server_submit(self.h, self.r.ctx, cam, out, tf)
+
+    def wait(self, ticket: int, timeout_s: float = -1.0) -> float:
+        return vr_server_wait(self.h, self.r.ctx, ticket, timeout_s)
+
+    def stats(self) -> dict:
+        return vr_server_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            vr_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def vr_render_noalloc(cube, brick, points, cam: dict, out, stream=None) -> None:
