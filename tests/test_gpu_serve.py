@@ -102,10 +102,10 @@ def test_admission_by_memory(vr, torch):
     shape, brick = (64, 64, 64), (32, 32, 32)
     cube, tf = synth.tiny_cube(), synth.tf_tiny()
     small = synth.pose(shape, 0.5, 0.3, 64, 64)
-    big = synth.pose(shape, 0.5, 0.3, 1024, 1024)   # 8 bricks x 16k tiles x 1 KB of fragments
+    big = synth.pose(shape, 0.5, 0.3, 2048, 2048)   # ~100k items x 1 KB of fragments > 32 MiB
     r = _renderer(vr, torch, cube, tf, small, brick)
     o1 = torch.empty((64, 64, 4), dtype=torch.float32, device="cuda")
-    o2 = torch.empty((1024, 1024, 4), dtype=torch.float32, device="cuda")
+    o2 = torch.empty((2048, 2048, 4), dtype=torch.float32, device="cuda")
     o3 = torch.empty((64, 64, 4), dtype=torch.float32, device="cuda")
     with vr.Server(r, 64 << 20) as srv:
         t1, t2, t3 = srv.submit(small, o1), srv.submit(big, o2), srv.submit(small, o3)
