@@ -301,10 +301,12 @@ def test_texture_gather_ragged(vr, torch, shape, brick, camk, step, tau):
 
 def test_mip_stops_at_the_global_maximum(vr, torch):
     """Section 2.3.2: a MIP ray stops once it reaches the cube's global maximum.
-    On a cube clipped at its 90th percentile (large plateaus at the maximum) the
+    On a cube clipped low (large plateaus at the maximum) the
     image is unchanged and fewer samples are taken than the oracle's full rays."""
     cube = synth.tiny_cube()
-    cube = np.minimum(cube, np.percentile(cube, 90)).astype(np.float32)
+    # clipped at its 30th percentile: 70% of the voxels sit at the maximum, so many
+    # cells have all eight corners there and a ray soon samples the maximum exactly
+    cube = np.minimum(cube, np.percentile(cube, 30)).astype(np.float32)
     tf = synth.tf_tiny()
     cam = synth.tiny_views(width=96, height=96)[1]
     img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_MODE: 1})
