@@ -307,7 +307,7 @@ def test_mip_stops_at_the_global_maximum(vr, torch):
     # clipped at its 30th percentile: 70% of the voxels sit at the maximum, so many
     # cells have all eight corners there and a ray soon samples the maximum exactly
     cube = np.minimum(cube, np.percentile(cube, 30)).astype(np.float32)
-    tf = synth.tf_tiny()
+    tf = synth.make_tf([0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8], lo=float(cube.min()), hi=float(cube.max()))
     cam = synth.tiny_views(width=96, height=96)[1]
     img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_MODE: 1})
     ref, amb, ns = oracle_render(cube, tf, cam, (32, 32, 32), mode="mip")
