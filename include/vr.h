@@ -390,6 +390,19 @@ int vr_server_get_stats(vr_server* srv, vr_server_stats* out);
 void vr_server_destroy(vr_server* srv);
 
 /*
+ * Diagnostic of the tensor-core path used by the learned brick codec (no
+ * counterpart in the paper): D = A * B^T on one CTA with tcgen05.mma (BF16
+ * operands staged in shared memory K-major, or MN-major when *_mn_major is 1;
+ * FP32 accumulation in tensor memory; read back with tcgen05.ld).
+ *   a_bf16: host, 128 x K BF16 bit patterns, row-major; b_bf16: host, N x K;
+ *   16 <= K <= 64 and 16 <= N <= 64, multiples of 16; d_out: host, 128 x N FP32.
+ * Runs on the current CUDA device.  Errors: VR_EINVAL, VR_ENOMEM, VR_ECUDA,
+ * VR_ETIMEOUT (the kernel's bounded wait for the MMA gave up).
+ */
+int vr_codec_gemm_check(const uint16_t* a_bf16, const uint16_t* b_bf16, int32_t K, int32_t N,
+                        int32_t a_mn_major, int32_t b_mn_major, float* d_out);
+
+/*
  * Allocation-free render (the paper has no counterpart; this serves callers that
  * may not allocate device memory while rendering: an application or plugin that
  * owns the device-memory budget, a real-time loop that cannot take the implicit

@@ -15,8 +15,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libvr.so")
-SOURCES = ["vr_host.cu", "vr_kernels.cu", "vr_march_tma.cu", "vr_march_tex.cu", "vr_noalloc.cu", "vr_shard.cu", "vr_ooc.cu", "vr_serve.cu"]
-HEADERS = ["df.cuh", "vr_internal.cuh", "vr_device.cuh", "vr_alpha_fit.h", "vr_ctx.cuh"]
+SOURCES = ["vr_host.cu", "vr_kernels.cu", "vr_march_tma.cu", "vr_march_tex.cu", "vr_noalloc.cu", "vr_shard.cu", "vr_ooc.cu", "vr_serve.cu", "vr_codec.cu"]
+HEADERS = ["df.cuh", "vr_internal.cuh", "vr_device.cuh", "vr_alpha_fit.h", "vr_ctx.cuh", "tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

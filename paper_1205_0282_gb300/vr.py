@@ -73,7 +73,8 @@ EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_b
            "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_kd_partition", "vr_kd_order",
            "vr_set_region", "vr_region_rect", "vr_plan_region_rect", "vr_render_rect",
            "vr_composite_subimages", "vr_server_create", "vr_server_submit", "vr_server_wait",
-           "vr_server_get_stats", "vr_server_destroy", "vr_render_noalloc", "vr_last_error"]
+           "vr_server_get_stats", "vr_server_destroy", "vr_codec_gemm_check", "vr_render_noalloc",
+           "vr_last_error"]
 
 
 class vr_server_stats(ctypes.Structure):
@@ -116,6 +117,7 @@ def _load():
     lib.vr_server_wait.argtypes = [P, I64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.vr_server_get_stats.argtypes = [P, ctypes.POINTER(vr_server_stats)]
     lib.vr_server_destroy.argtypes = [P]
+    lib.vr_codec_gemm_check.argtypes = [P, P, I32, I32, I32, I32, P]
     lib.vr_render_noalloc.argtypes = [P, I64, I64, I64, I32, I32, I32, P, I32,
                                       ctypes.POINTER(vr_camera), P, P]
     lib.vr_last_error.argtypes = [P]
@@ -383,6 +385,30 @@ def vr_server_get_stats(srv) -> dict:
 
 def vr_server_destroy(srv) -> None:
     _lib.vr_server_destroy(srv)
+
+
+def to_bf16_bits(x) -> np.ndarray:
+    """float32 values -> BF16 bit patterns (uint16), round to nearest even."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def bf16_bits_to_float(h) -> np.ndarray:
+    return (np.asarray(h, dtype=np.uint32) << 16).view(np.float32)
+
+
+def vr_codec_gemm_check(a_bf16, b_bf16, a_mn_major=0, b_mn_major=0) -> np.ndarray:
+    """D = A B^T on the tensor cores (diagnostic): A (128, K), B (N, K) BF16 bits."""
+    A = np.ascontiguousarray(a_bf16, dtype=np.uint16)
+    B = np.ascontiguousarray(b_bf16, dtype=np.uint16)
+    K, N = A.shape[1], B.shape[0]
+    D = np.zeros((128, N), dtype=np.float32)
+    rc = _lib.vr_codec_gemm_check(A.ctypes.data, B.ctypes.data, K, N, int(a_mn_major), int(b_mn_major),
+                                  D.ctypes.data)
+    if rc != VR_OK:
+        raise VRError(rc, "vr_codec_gemm_check")
+    return D
 
 
 class Server:
