@@ -402,6 +402,63 @@ void vr_server_destroy(vr_server* srv);
 int vr_codec_gemm_check(const uint16_t* a_bf16, const uint16_t* b_bf16, int32_t K, int32_t N,
                         int32_t a_mn_major, int32_t b_mn_major, float* d_out);
 
+/* ---------------------------------------------------------------------------
+ * Learned brick codec (no counterpart in the paper): brick b is stored as a
+ * latent grid of 8 x 8 x 8 nodes x 16 channels and decoded by an MLP shared by
+ * all bricks.  The value at local voxel position u in [0, B]^3 is
+ *   x = u / B;  z = trilinear interpolation of the latents at 7 x;
+ *   in = [z (16), sin(pi x_a), cos(pi x_a), sin(2 pi x_a), cos(2 pi x_a) for
+ *         a = x, y, z (12), 0 (4)];
+ *   h1 = silu(W1 in + b1) (64);  h2 = silu(W2 h1 + b2) (64);
+ *   v = (w3 . h2 + b3) s_b + m_b,   silu(t) = t / (1 + exp(-t)).
+ * The MLP runs on the tensor cores (tcgen05.mma, BF16 operands: in, W1, W2,
+ * h1, w3 rounded to BF16; FP32 accumulation in tensor memory; biases FP32), 128
+ * points per CTA tile; training runs forward and backward in one kernel (the
+ * weight gradients accumulate in tensor memory across a CTA's tiles) and Adam.
+ *
+ * Parameter vector (FP32, vr_codec_param_count entries): W1 [64][32] (columns
+ * 28..31 unused), b1 [64], W2 [64][64], b2 [64], w3 [64], b3 [1], then the
+ * latents [brick][z][y][x][16].  m and s: per-brick offset and scale.
+ * Every call runs on the CUDA device current at vr_codec_create and blocks until
+ * done, except vr_codec_decode_bricks (asynchronous on its stream).
+ * ------------------------------------------------------------------------- */
+typedef struct vr_codec vr_codec;
+
+/* A codec for n_bricks bricks of size B (parameters zero).  Errors: VR_EINVAL, VR_ENOMEM. */
+int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out);
+void vr_codec_destroy(vr_codec* codec);
+int64_t vr_codec_param_count(const vr_codec* codec);
+
+/* Host copies of the parameters (set also resets the optimiser).  Errors: VR_EINVAL, VR_ECUDA. */
+int vr_codec_set_params(vr_codec* codec, const float* theta, const float* m, const float* s);
+int vr_codec_get_params(vr_codec* codec, float* theta, float* m, float* s);
+
+/* Decoded values of n points (host float32[n][4]: u_x, u_y, u_z, brick index as
+ * the bit pattern of an int32) into host values[n].  Errors: VR_EINVAL, VR_ENOMEM,
+ * VR_ECUDA, VR_ETIMEOUT (a bounded wait for the tensor cores gave up). */
+int vr_codec_forward(vr_codec* codec, const float* points, int64_t n, float* values);
+
+/* Loss mean((v - target)^2) over n points and its gradient (host float32 in the
+ * parameter layout; zero for latents no point touches).  Errors: as forward. */
+int vr_codec_gradient(vr_codec* codec, const float* points, const float* targets, int64_t n, float* grad,
+                      double* loss);
+
+/* m_b, s_b = mean and standard deviation (>= 1e-3) of each brick's voxels and
+ * apron in a device cube float32[nz][ny][nx] bricked by B.  Errors: VR_EINVAL, VR_ECUDA. */
+int vr_codec_fit_stats(vr_codec* codec, const float* cube, int64_t nx, int64_t ny, int64_t nz);
+
+/* `steps` Adam steps (lr; betas 0.9, 0.999; eps 1e-8) on `batch` voxels drawn per
+ * step (uniform brick, uniform voxel of its block clipped to the cube; counter-
+ * based generator seeded by seed) from the device cube; *last_loss = the last
+ * step's loss.  Errors: as forward. */
+int vr_codec_train(vr_codec* codec, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps,
+                   int32_t batch, float lr, uint64_t seed, double* last_loss);
+
+/* Decode the blocks of n bricks (device list) into device memory out, brick k's
+ * (bx+1)(by+1)(bz+1) values at out + k * that (x fastest), on `stream`.
+ * Errors: VR_EINVAL, VR_ECUDA. */
+int vr_codec_decode_bricks(vr_codec* codec, const int32_t* bricks, int32_t n, float* out, void* stream);
+
 /*
  * Allocation-free render (the paper has no counterpart; this serves callers that
  * may not allocate device memory while rendering: an application or plugin that

@@ -6,7 +6,10 @@
 // tensor-memory reads that the codec's kernels use.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "../../include/vr.h"
 #include "tc.cuh"
@@ -118,3 +121,768 @@ extern "C" int vr_codec_gemm_check(const uint16_t* a_bf16, const uint16_t* b_bf1
     cudaFree(err);
     return rc;
 }
+
+// ============================================================================ codec
+
+namespace vr {
+namespace codec {
+
+constexpr int kLatent = 16, kNodes = 8, kHidden = 64, kIn = 32, kTileP = 128;
+
+// Device state of the codec's MLP and latents.
+struct Net {
+    const __nv_bfloat16* lat;  // [brick][z][y][x][16] BF16
+    const __nv_bfloat16* W1;   // [64][32] BF16 (inputs 28..31 zero)
+    const __nv_bfloat16* W2;   // [64][64] BF16
+    const float* b1;           // [64]
+    const float* b2;           // [64]
+    const float* w3;           // [64] (BF16 values)
+    const float* b3;           // [1]
+    const float* m;            // per-brick offset
+    const float* s;            // per-brick scale
+    float inv_b[3];            // 1 / brick size
+};
+
+// Gradient accumulators of a training step (FP32, zeroed by the caller).
+struct Grads {
+    float* W1;   // [64][32]
+    float* W2;   // [64][64]
+    float* b1;   // [64]
+    float* b2;   // [64]
+    float* w3;   // [64]
+    float* b3;   // [1]
+    float* lat;  // like Net::lat
+    double* loss;
+    float dy_scale;  // 2 / (number of points of the step)
+};
+
+// Shared-memory layout of the step kernel (bytes).  G2 is followed by G1 and G1
+// by Z1: the padded weight-gradient products read up to 1 KiB past either.
+// Inference asks for 56 KiB so that at most 4 CTAs (128 tensor-memory columns
+// each) share an SM.
+constexpr uint32_t kOffW1 = 0, kOffW2 = 4096, kOffIN = 12288, kOffH1 = 20480, kOffG2 = 36864, kOffG1 = 53248,
+                   kOffZ1 = 69632, kSmemInfer = 57344, kSmemTrain = 102400;
+
+__device__ __forceinline__ float silu(float t) { return t / (1.0f + expf(-t)); }
+__device__ __forceinline__ float silu_grad(float t) {
+    const float s = 1.0f / (1.0f + expf(-t));
+    return s * (1.0f + t * (1.0f - s));
+}
+
+__device__ __forceinline__ void store_bf16(unsigned char* base, uint32_t off, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+// Point p: brick (bits of .w) and local voxel position (.x, .y, .z) in [0, B].
+// Builds its input row in IN_s and returns the interpolation corners.
+struct Corner {
+    int node[8];
+    float w[8];
+};
+
+__device__ __forceinline__ void build_input(const Net& net, float4 pt, bool valid, int row, unsigned char* in_s,
+                                            int& brick, Corner& cr) {
+    float in[kIn];
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) in[i] = 0.0f;
+    brick = __float_as_int(pt.w);
+    if (valid) {
+        const float x[3] = {pt.x * net.inv_b[0], pt.y * net.inv_b[1], pt.z * net.inv_b[2]};
+        int i0[3];
+        float f[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float g = x[a] * (float)(kNodes - 1);
+            i0[a] = min(max((int)floorf(g), 0), kNodes - 2);
+            f[a] = g - (float)i0[a];
+        }
+        const __nv_bfloat16* L = net.lat + (int64_t)brick * kNodes * kNodes * kNodes * kLatent;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+            const float w = (cx ? f[0] : 1.0f - f[0]) * (cy ? f[1] : 1.0f - f[1]) * (cz ? f[2] : 1.0f - f[2]);
+            const int node = ((i0[2] + cz) * kNodes + (i0[1] + cy)) * kNodes + (i0[0] + cx);
+            cr.node[c] = node;
+            cr.w[c] = w;
+            const uint4* src = reinterpret_cast<const uint4*>(L + node * kLatent);
+            const uint4 q0 = __ldg(src), q1 = __ldg(src + 1);
+            const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&q0);
+            const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&q1);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 a0 = __bfloat1622float2(h0[k]), a1 = __bfloat1622float2(h1[k]);
+                in[2 * k] = fmaf(w, a0.x, in[2 * k]);
+                in[2 * k + 1] = fmaf(w, a0.y, in[2 * k + 1]);
+                in[8 + 2 * k] = fmaf(w, a1.x, in[8 + 2 * k]);
+                in[8 + 2 * k + 1] = fmaf(w, a1.y, in[8 + 2 * k + 1]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            in[16 + 4 * a] = sinpif(x[a]);
+            in[17 + 4 * a] = cospif(x[a]);
+            in[18 + 4 * a] = sinpif(2.0f * x[a]);
+            in[19 + 4 * a] = cospif(2.0f * x[a]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kIn; i += 2)
+        *reinterpret_cast<__nv_bfloat162*>(in_s + tc::kmajor_offset(row, i, kIn)) =
+            __floats2bfloat162_rn(in[i], in[i + 1]);
+}
+
+// Issue a chain of K = 16 MMAs (nk of them) and leave the commit to the caller.
+__device__ __forceinline__ void mma_chain(uint32_t d_tmem, uint32_t a_start, uint32_t a_step, uint32_t a_lbo,
+                                          uint32_t a_sbo, uint32_t b_start, uint32_t b_step, uint32_t b_lbo,
+                                          uint32_t b_sbo, uint32_t idesc, int nk, bool accumulate) {
+    for (int j = 0; j < nk; ++j)
+        tc::mma_bf16(d_tmem, tc::make_desc(a_start + j * a_step, a_lbo, a_sbo),
+                     tc::make_desc(b_start + j * b_step, b_lbo, b_sbo), idesc, (accumulate || j > 0) ? 1u : 0u);
+}
+
+// One CTA of 128 threads processes tiles of 128 points (tile t, t + gridDim.x, ...).
+// TRAIN = false: out[p] = decoded value.  TRAIN = true: the step's loss and
+// gradients (targets in tgt) are accumulated into g.
+// Points come from pts, or (pts == nullptr) from the voxel grids of the bricks
+// listed in grid_bricks: point q is voxel (q % V) of brick grid_bricks[q / V], V =
+// (Bx+1)(By+1)(Bz+1) voxels x fastest, and out[q] is its slot-layout value.
+struct Grid {
+    const int32_t* bricks;
+    int32_t dims[3];  // B + 1 per axis
+};
+
+template <bool TRAIN>
+__global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const float4* __restrict__ pts,
+                                                       const Grid grid, const float* __restrict__ tgt,
+                                                       int64_t n_points, float* __restrict__ out, const Grads g,
+                                                       int* err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ float s_db1[kHidden], s_db2[kHidden], s_dw3[kHidden], s_db3;
+    __shared__ double s_loss;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t tcols = TRAIN ? 256 : 128;
+    // weights into shared memory (K-major, rows = outputs)
+    for (int i = tid; i < kHidden * kIn; i += kTileP)
+        *reinterpret_cast<__nv_bfloat16*>(sm + kOffW1 + tc::kmajor_offset(i / kIn, i % kIn, kIn)) = net.W1[i];
+    for (int i = tid; i < kHidden * kHidden; i += kTileP)
+        *reinterpret_cast<__nv_bfloat16*>(sm + kOffW2 + tc::kmajor_offset(i / kHidden, i % kHidden, kHidden)) =
+            net.W2[i];
+    if (TRAIN) {
+        for (int i = tid; i < kHidden; i += kTileP) s_db1[i] = s_db2[i] = s_dw3[i] = 0.0f;
+        // the bytes the padded gradient products read beyond G1 must be initialised
+        for (int i = tid; i < (int)(kSmemTrain - kOffG2) / 16; i += kTileP)
+            reinterpret_cast<uint4*>(sm + kOffG2)[i] = make_uint4(0, 0, 0, 0);
+        if (tid == 0) {
+            s_db3 = 0.0f;
+            s_loss = 0.0;
+        }
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, tcols);
+    if (tid == 0) tc::bar_init(&bar, 1);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t sbase = tc::smem_addr(sm);
+    const uint32_t T_D1 = tmem, T_D2 = tmem + 64, T_DW2 = tmem + 128, T_DW1 = tmem + 192, T_DIN = tmem + 224;
+    const uint32_t id_64 = tc::make_idesc_bf16(128, 64, 0, 0);
+    uint32_t phase = 0;
+    bool ok = true;
+    int tiles_done = 0;
+    // every thread waits for the MMAs; the block then agrees on the outcome, so that
+    // a wait that gave up in one thread stops the whole block at the same point
+    auto wait_mma = [&]() {
+        const bool mine = tc::bar_wait(&bar, phase, kWaitLimit);
+        phase ^= 1u;
+        ok = __syncthreads_and(mine ? 1 : 0) != 0;
+        if (!ok && tid == 0) atomicOr(err, 1);
+        tc::fence_after_sync();
+    };
+    const int64_t n_tiles = (n_points + kTileP - 1) / kTileP;
+    for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int64_t idx = t * kTileP + tid;
+        const bool valid = idx < n_points;
+        float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            if (pts) {
+                pt = pts[idx];
+            } else {
+                const int64_t V = (int64_t)grid.dims[0] * grid.dims[1] * grid.dims[2];
+                const int64_t q = idx % V;
+                pt = make_float4((float)(q % grid.dims[0]), (float)((q / grid.dims[0]) % grid.dims[1]),
+                                 (float)(q / ((int64_t)grid.dims[0] * grid.dims[1])),
+                                 __int_as_float(grid.bricks[idx / V]));
+            }
+        }
+        int brick = 0;
+        Corner cr;
+        build_input(net, pt, valid, tid, sm + kOffIN, brick, cr);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // layer 1: D1 = IN W1^T (M 128, N 64, K 32)
+        if (tid == 0) {
+            mma_chain(T_D1, sbase + kOffIN, 256, 128, 512, sbase + kOffW1, 256, 128, 512, id_64, 2, false);
+            tc::mma_commit(&bar);
+        }
+        wait_mma();
+#pragma unroll 1
+        for (int c = 0; c < kHidden; c += 16) {
+            float d[16];
+            tc::tmem_ld16(T_D1 + lane_base + c, d);
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                const float z0 = d[i] + net.b1[c + i], z1 = d[i + 1] + net.b1[c + i + 1];
+                if (TRAIN) {
+                    float* zr = reinterpret_cast<float*>(sm + kOffZ1) + tid * kHidden + c + i;
+                    zr[0] = z0;
+                    zr[1] = z1;
+                }
+                *reinterpret_cast<__nv_bfloat162*>(sm + kOffH1 + tc::kmajor_offset(tid, c + i, kHidden)) =
+                    __floats2bfloat162_rn(silu(z0), silu(z1));
+            }
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // layer 2: D2 = H1 W2^T (K 64)
+        if (tid == 0) {
+            mma_chain(T_D2, sbase + kOffH1, 256, 128, 1024, sbase + kOffW2, 256, 128, 1024, id_64, 4, false);
+            tc::mma_commit(&bar);
+        }
+        wait_mma();
+        float y = net.b3[0];
+#pragma unroll 1
+        for (int c = 0; c < kHidden; c += 16) {
+            float d[16];
+            tc::tmem_ld16(T_D2 + lane_base + c, d);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) y = fmaf(silu(d[i] + net.b2[c + i]), net.w3[c + i], y);
+        }
+        const float sb = valid ? net.s[brick] : 0.0f;
+        const float v = valid ? fmaf(y, sb, net.m[brick]) : 0.0f;
+        if (!TRAIN) {
+            if (valid) out[idx] = v;
+            tc::fence_before_sync();
+            __syncthreads();  // D1 / D2 and the operand tiles are reused by the next tile
+            tc::fence_after_sync();
+            ++tiles_done;
+            continue;
+        }
+        // ---- backward
+        const float r = valid ? v - tgt[idx] : 0.0f;
+        const float dy = r * sb * g.dy_scale;
+        {
+            double l = (double)r * (double)r;
+            for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+            if ((tid & 31) == 0 && l != 0.0) atomicAdd(&s_loss, l);
+            float d3 = dy;
+            for (int o = 16; o > 0; o >>= 1) d3 += __shfl_xor_sync(0xffffffffu, d3, o);
+            if ((tid & 31) == 0 && d3 != 0.0f) atomicAdd(&s_db3, d3);
+        }
+#pragma unroll 1
+        for (int c = 0; c < kHidden; c += 16) {
+            float d[16];
+            tc::tmem_ld16(T_D2 + lane_base + c, d);
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                float gg[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const float z2 = d[i + e] + net.b2[c + i + e];
+                    gg[e] = dy * net.w3[c + i + e] * silu_grad(z2);
+                    if (dy != 0.0f) {
+                        atomicAdd(&s_db2[c + i + e], gg[e]);
+                        atomicAdd(&s_dw3[c + i + e], dy * silu(z2));
+                    }
+                }
+                *reinterpret_cast<__nv_bfloat162*>(sm + kOffG2 + tc::kmajor_offset(tid, c + i, kHidden)) =
+                    __floats2bfloat162_rn(gg[0], gg[1]);
+            }
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            // dH1 = G2 W2: A = G2 (K-major, K = o), B = W2 read MN-major (K = o, N = i)
+            mma_chain(T_D1, sbase + kOffG2, 256, 128, 1024, sbase + kOffW2, 2048, 1024, 128,
+                      tc::make_idesc_bf16(128, 64, 0, 1), 4, false);
+            // dW2 += G2^T H1: A = G2 read MN-major (K = p, M = o, padded to 128),
+            // B = H1 read MN-major (K = p, N = i)
+            mma_chain(T_DW2, sbase + kOffG2, 2048, 1024, 128, sbase + kOffH1, 2048, 1024, 128,
+                      tc::make_idesc_bf16(128, 64, 1, 1), 8, tiles_done > 0);
+            tc::mma_commit(&bar);
+        }
+        wait_mma();
+#pragma unroll 1
+        for (int c = 0; c < kHidden; c += 16) {
+            float d[16];
+            tc::tmem_ld16(T_D1 + lane_base + c, d);
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+                float gg[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const float z1 = reinterpret_cast<const float*>(sm + kOffZ1)[tid * kHidden + c + i + e];
+                    gg[e] = d[i + e] * silu_grad(z1);
+                    if (dy != 0.0f) atomicAdd(&s_db1[c + i + e], gg[e]);
+                }
+                *reinterpret_cast<__nv_bfloat162*>(sm + kOffG1 + tc::kmajor_offset(tid, c + i, kHidden)) =
+                    __floats2bfloat162_rn(gg[0], gg[1]);
+            }
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            // dIN = G1 W1: A = G1 (K-major, K = o), B = W1 read MN-major (K = o, N = i 32)
+            mma_chain(T_DIN, sbase + kOffG1, 256, 128, 1024, sbase + kOffW1, 1024, 512, 128,
+                      tc::make_idesc_bf16(128, 32, 0, 1), 4, false);
+            // dW1 += G1^T IN: A = G1 read MN-major (K = p, M = o padded), B = IN read MN-major (K = p, N = i)
+            mma_chain(T_DW1, sbase + kOffG1, 2048, 1024, 128, sbase + kOffIN, 1024, 512, 128,
+                      tc::make_idesc_bf16(128, 32, 1, 1), 8, tiles_done > 0);
+            tc::mma_commit(&bar);
+        }
+        wait_mma();
+        {
+            float d[16];
+            tc::tmem_ld16(T_DIN + lane_base, d);
+            if (dy != 0.0f) {
+                float* gl = g.lat + (int64_t)brick * kNodes * kNodes * kNodes * kLatent;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    float* dst = gl + cr.node[k] * kLatent;
+#pragma unroll
+                    for (int ch = 0; ch < kLatent; ++ch) atomicAdd(dst + ch, cr.w[k] * d[ch]);
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        ++tiles_done;
+    }
+    if (TRAIN && ok && tiles_done > 0) {
+        // rows 0..63 of the weight-gradient accumulators hold dW2 and dW1
+        if (tid < kHidden) {
+            for (int c = 0; c < kHidden; c += 16) {
+                float d[16];
+                tc::tmem_ld16(T_DW2 + lane_base + c, d);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) atomicAdd(g.W2 + tid * kHidden + c + i, d[i]);
+            }
+            for (int c = 0; c < kIn; c += 16) {
+                float d[16];
+                tc::tmem_ld16(T_DW1 + lane_base + c, d);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) atomicAdd(g.W1 + tid * kIn + c + i, d[i]);
+            }
+        } else {
+            // the other warps of the pair must take part in the aligned loads
+            float d[16];
+            for (int c = 0; c < kHidden; c += 16) tc::tmem_ld16(T_DW2 + lane_base + c, d);
+            for (int c = 0; c < kIn; c += 16) tc::tmem_ld16(T_DW1 + lane_base + c, d);
+        }
+        __syncthreads();
+        for (int i = tid; i < kHidden; i += kTileP) {
+            atomicAdd(g.b1 + i, s_db1[i]);
+            atomicAdd(g.b2 + i, s_db2[i]);
+            atomicAdd(g.w3 + i, s_dw3[i]);
+        }
+        if (tid == 0) {
+            atomicAdd(g.b3, s_db3);
+            atomicAdd(g.loss, s_loss);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, tcols);
+}
+
+}  // namespace codec
+}  // namespace vr
+
+// ============================================================================ host side
+
+namespace vr {
+namespace codec {
+
+// Parameter vector layout (FP32): W1 [64][32], b1 [64], W2 [64][64], b2 [64],
+// w3 [64], b3 [1], then the latents [brick][8][8][8][16].
+constexpr int64_t kOfsW1 = 0, kOfsB1 = kOfsW1 + kHidden * kIn, kOfsW2 = kOfsB1 + kHidden,
+                  kOfsB2 = kOfsW2 + kHidden * kHidden, kOfsW3 = kOfsB2 + kHidden, kOfsB3 = kOfsW3 + kHidden,
+                  kOfsLat = kOfsB3 + 1;
+constexpr int64_t kLatPerBrick = (int64_t)kNodes * kNodes * kNodes * kLatent;
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+__global__ void round_bf16_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __bfloat162float(__float2bfloat16_rn(src[i]));
+}
+
+// Adam (bias-corrected), one step over the whole parameter vector.
+__global__ void adam_kernel(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m1,
+                            float* __restrict__ m2, int64_t n, float lr, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float a = m1[i] = 0.9f * m1[i] + 0.1f * gi;
+        const float b = m2[i] = 0.999f * m2[i] + 0.001f * gi * gi;
+        th[i] -= lr * (a * c1) / (sqrtf(b * c2) + 1e-8f);
+    }
+}
+
+// splitmix64 (a counter-based generator): 64 random bits of counter x.
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Training points: uniform brick, uniform voxel of its (B+1)^3 block clipped to
+// the cube; target = the cube's value there.
+__global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, int64_t n_points,
+                              uint64_t seed, float4* __restrict__ pts, float* __restrict__ tgt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_points) return;
+    const uint64_t r0 = mix64(seed ^ (uint64_t)(2 * i)), r1 = mix64(seed ^ (uint64_t)(2 * i + 1));
+    const int nbt = nb.x * nb.y * nb.z;
+    const int b = (int)(r0 % (uint64_t)nbt);
+    const int bx = b % nb.x, by = (b / nb.x) % nb.y, bz = b / (nb.x * nb.y);
+    const int ux = (int)((r1 & 0xFFFFF) % (uint64_t)(B.x + 1));
+    const int uy = (int)(((r1 >> 20) & 0xFFFFF) % (uint64_t)(B.y + 1));
+    const int uz = (int)(((r1 >> 40) & 0xFFFFF) % (uint64_t)(B.z + 1));
+    const int gx = min(bx * B.x + ux, n.x - 1), gy = min(by * B.y + uy, n.y - 1), gz = min(bz * B.z + uz, n.z - 1);
+    pts[i] = make_float4((float)(gx - bx * B.x), (float)(gy - by * B.y), (float)(gz - bz * B.z), __int_as_float(b));
+    tgt[i] = cube[((int64_t)gz * n.y + gy) * n.x + gx];
+}
+
+// Per-brick offset and scale: mean and standard deviation (at least 1e-3) over
+// the brick's voxels and apron.
+__global__ void brick_stats_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, float* m, float* s) {
+    const int b = blockIdx.x;
+    const int bx = b % nb.x, by = (b / nb.x) % nb.y, bz = b / (nb.x * nb.y);
+    const int x0 = bx * B.x, y0 = by * B.y, z0 = bz * B.z;
+    const int x1 = min(x0 + B.x, n.x - 1), y1 = min(y0 + B.y, n.y - 1), z1 = min(z0 + B.z, n.z - 1);
+    double s1 = 0, s2 = 0;
+    const int64_t cnt = (int64_t)(x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1);
+    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int x = x0 + (int)(q % (x1 - x0 + 1));
+        const int y = y0 + (int)((q / (x1 - x0 + 1)) % (y1 - y0 + 1));
+        const int z = z0 + (int)(q / ((int64_t)(x1 - x0 + 1) * (y1 - y0 + 1)));
+        const double v = cube[((int64_t)z * n.y + y) * n.x + x];
+        s1 += v;
+        s2 += v * v;
+    }
+    __shared__ double a1[256], a2[256];
+    a1[threadIdx.x] = s1;
+    a2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            a1[threadIdx.x] += a1[threadIdx.x + o];
+            a2[threadIdx.x] += a2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = a1[0] / (double)cnt;
+        const double var = fmax(a2[0] / (double)cnt - mean * mean, 0.0);
+        m[b] = (float)mean;
+        s[b] = (float)fmax(sqrt(var), 1e-3);
+    }
+}
+
+}  // namespace codec
+}  // namespace vr
+
+struct vr_codec {
+    int device = 0;
+    int32_t n_bricks = 0;
+    int32_t B[3] = {0, 0, 0};
+    int64_t n_params = 0;
+    float* theta = nullptr;  // FP32 parameters
+    float* grad = nullptr;
+    float* adam1 = nullptr;
+    float* adam2 = nullptr;
+    __nv_bfloat16* W1h = nullptr;
+    __nv_bfloat16* W2h = nullptr;
+    __nv_bfloat16* lath = nullptr;
+    float* w3r = nullptr;  // w3 rounded to BF16 values
+    float* m = nullptr;
+    float* s = nullptr;
+    double* loss = nullptr;
+    int* err = nullptr;
+    float4* pts = nullptr;
+    float* tgt = nullptr;
+    int64_t cap_pts = 0;
+    int64_t adam_t = 0;
+    int sm_count = 0;
+};
+
+namespace {
+
+using vr::codec::Net;
+
+uint64_t mix64_host(uint64_t seed, uint64_t step) {
+    uint64_t x = seed + 0x9E3779B97F4A7C15ull * (step + 1);
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+int codec_cuda(cudaError_t e) { return e == cudaSuccess ? VR_OK : (cudaGetLastError(), VR_ECUDA); }
+#define CODEC_CUDA(call)                        \
+    do {                                        \
+        int _rc = codec_cuda(call);             \
+        if (_rc) return _rc;                    \
+    } while (0)
+
+// Refresh the BF16 operand copies from the FP32 parameters.
+int sync_bf16(vr_codec* c) {
+    using namespace vr::codec;
+    to_bf16_kernel<<<64, 256>>>(c->theta + kOfsW1, c->W1h, kHidden * kIn);
+    to_bf16_kernel<<<64, 256>>>(c->theta + kOfsW2, c->W2h, kHidden * kHidden);
+    round_bf16_kernel<<<1, 64>>>(c->theta + kOfsW3, c->w3r, kHidden);
+    to_bf16_kernel<<<1024, 256>>>(c->theta + kOfsLat, c->lath, (int64_t)c->n_bricks * kLatPerBrick);
+    return codec_cuda(cudaGetLastError());
+}
+
+Net make_net(const vr_codec* c) {
+    using namespace vr::codec;
+    Net n;
+    n.lat = c->lath;
+    n.W1 = c->W1h;
+    n.W2 = c->W2h;
+    n.b1 = c->theta + kOfsB1;
+    n.b2 = c->theta + kOfsB2;
+    n.w3 = c->w3r;
+    n.b3 = c->theta + kOfsB3;
+    n.m = c->m;
+    n.s = c->s;
+    for (int a = 0; a < 3; ++a) n.inv_b[a] = 1.0f / (float)c->B[a];
+    return n;
+}
+
+int grow_points(vr_codec* c, int64_t n) {
+    if (n <= c->cap_pts) return VR_OK;
+    cudaFree(c->pts);
+    cudaFree(c->tgt);
+    c->pts = nullptr;
+    c->tgt = nullptr;
+    c->cap_pts = 0;
+    if (cudaMalloc(&c->pts, n * sizeof(float4)) != cudaSuccess || cudaMalloc(&c->tgt, n * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return VR_ENOMEM;
+    }
+    c->cap_pts = n;
+    return VR_OK;
+}
+
+template <bool TRAIN>
+int launch_codec(vr_codec* c, const float4* pts, vr::codec::Grid grid, const float* tgt, int64_t n, float* out,
+                 cudaStream_t st) {
+    using namespace vr::codec;
+    if (n == 0) return VR_OK;
+    const int smem = TRAIN ? (int)kSmemTrain : (int)kSmemInfer;
+    static bool attr = false;
+    if (!attr) {
+        CODEC_CUDA(cudaFuncSetAttribute(codec_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr = true;
+    }
+    Grads g{};
+    if (TRAIN) {
+        g.W1 = c->grad + kOfsW1;
+        g.W2 = c->grad + kOfsW2;
+        g.b1 = c->grad + kOfsB1;
+        g.b2 = c->grad + kOfsB2;
+        g.w3 = c->grad + kOfsW3;
+        g.b3 = c->grad + kOfsB3;
+        g.lat = c->grad + kOfsLat;
+        g.loss = c->loss;
+        g.dy_scale = 2.0f / (float)n;
+    }
+    const int64_t tiles = (n + kTileP - 1) / kTileP;
+    const int64_t grid_ctas = std::min<int64_t>(tiles, (int64_t)c->sm_count * (TRAIN ? 2 : 4));
+    codec_kernel<TRAIN><<<(unsigned)grid_ctas, kTileP, smem, st>>>(make_net(c), pts, grid, tgt, n, out, g, c->err);
+    return codec_cuda(cudaGetLastError());
+}
+
+int check_err(vr_codec* c) {
+    int h = 0;
+    CODEC_CUDA(cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    return h ? VR_ETIMEOUT : VR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
+    using namespace vr::codec;
+    if (!out || !B || n_bricks < 1 || B[0] < 1 || B[1] < 1 || B[2] < 1) return VR_EINVAL;
+    *out = nullptr;
+    vr_codec* c = new vr_codec();
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    c->n_bricks = n_bricks;
+    for (int a = 0; a < 3; ++a) c->B[a] = B[a];
+    c->n_params = kOfsLat + (int64_t)n_bricks * kLatPerBrick;
+    const size_t pb = (size_t)c->n_params * sizeof(float);
+    bool ok = cudaMalloc(&c->theta, pb) == cudaSuccess && cudaMalloc(&c->grad, pb) == cudaSuccess &&
+              cudaMalloc(&c->adam1, pb) == cudaSuccess && cudaMalloc(&c->adam2, pb) == cudaSuccess &&
+              cudaMalloc(&c->W1h, kHidden * kIn * 2) == cudaSuccess &&
+              cudaMalloc(&c->W2h, kHidden * kHidden * 2) == cudaSuccess &&
+              cudaMalloc(&c->lath, (size_t)n_bricks * kLatPerBrick * 2) == cudaSuccess &&
+              cudaMalloc(&c->w3r, kHidden * 4) == cudaSuccess && cudaMalloc(&c->m, n_bricks * 4) == cudaSuccess &&
+              cudaMalloc(&c->s, n_bricks * 4) == cudaSuccess && cudaMalloc(&c->loss, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->err, sizeof(int)) == cudaSuccess;
+    if (ok) ok = cudaMemset(c->theta, 0, pb) == cudaSuccess && cudaMemset(c->adam1, 0, pb) == cudaSuccess &&
+                 cudaMemset(c->adam2, 0, pb) == cudaSuccess && cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        vr_codec_destroy(c);
+        return VR_ENOMEM;
+    }
+    *out = c;
+    return VR_OK;
+}
+
+void vr_codec_destroy(vr_codec* c) {
+    if (!c) return;
+    for (void* p : {(void*)c->theta, (void*)c->grad, (void*)c->adam1, (void*)c->adam2, (void*)c->W1h, (void*)c->W2h,
+                    (void*)c->lath, (void*)c->w3r, (void*)c->m, (void*)c->s, (void*)c->loss, (void*)c->err,
+                    (void*)c->pts, (void*)c->tgt})
+        cudaFree(p);
+    delete c;
+}
+
+int64_t vr_codec_param_count(const vr_codec* c) { return c ? c->n_params : -1; }
+
+int vr_codec_set_params(vr_codec* c, const float* theta, const float* m, const float* s) {
+    if (!c || !theta || !m || !s) return VR_EINVAL;
+    CODEC_CUDA(cudaMemcpy(c->theta, theta, (size_t)c->n_params * 4, cudaMemcpyHostToDevice));
+    CODEC_CUDA(cudaMemcpy(c->m, m, (size_t)c->n_bricks * 4, cudaMemcpyHostToDevice));
+    CODEC_CUDA(cudaMemcpy(c->s, s, (size_t)c->n_bricks * 4, cudaMemcpyHostToDevice));
+    c->adam_t = 0;
+    CODEC_CUDA(cudaMemset(c->adam1, 0, (size_t)c->n_params * 4));
+    CODEC_CUDA(cudaMemset(c->adam2, 0, (size_t)c->n_params * 4));
+    return sync_bf16(c);
+}
+
+int vr_codec_get_params(vr_codec* c, float* theta, float* m, float* s) {
+    if (!c || !theta) return VR_EINVAL;
+    CODEC_CUDA(cudaMemcpy(theta, c->theta, (size_t)c->n_params * 4, cudaMemcpyDeviceToHost));
+    if (m) CODEC_CUDA(cudaMemcpy(m, c->m, (size_t)c->n_bricks * 4, cudaMemcpyDeviceToHost));
+    if (s) CODEC_CUDA(cudaMemcpy(s, c->s, (size_t)c->n_bricks * 4, cudaMemcpyDeviceToHost));
+    return VR_OK;
+}
+
+// Every point names an existing brick.
+bool points_valid(const vr_codec* c, const float* points, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t b;
+        std::memcpy(&b, points + 4 * i + 3, 4);
+        if (b < 0 || b >= c->n_bricks) return false;
+    }
+    return true;
+}
+
+int vr_codec_forward(vr_codec* c, const float* points, int64_t n, float* values) {
+    if (!c || !points || !values || n < 0 || !points_valid(c, points, n)) return VR_EINVAL;
+    int rc = grow_points(c, std::max<int64_t>(n, 1));
+    if (rc) return rc;
+    float* d_out = nullptr;
+    CODEC_CUDA(cudaMalloc(&d_out, std::max<int64_t>(n, 1) * 4));
+    CODEC_CUDA(cudaMemcpy(c->pts, points, n * 16, cudaMemcpyHostToDevice));
+    rc = launch_codec<false>(c, c->pts, vr::codec::Grid{}, nullptr, n, d_out, 0);
+    if (!rc) rc = codec_cuda(cudaDeviceSynchronize());
+    if (!rc) rc = check_err(c);
+    if (!rc) rc = codec_cuda(cudaMemcpy(values, d_out, n * 4, cudaMemcpyDeviceToHost));
+    cudaFree(d_out);
+    return rc;
+}
+
+int vr_codec_gradient(vr_codec* c, const float* points, const float* targets, int64_t n, float* grad, double* loss) {
+    if (!c || !points || !targets || !grad || n < 1 || !points_valid(c, points, n)) return VR_EINVAL;
+    int rc = grow_points(c, n);
+    if (rc) return rc;
+    CODEC_CUDA(cudaMemcpy(c->pts, points, n * 16, cudaMemcpyHostToDevice));
+    CODEC_CUDA(cudaMemcpy(c->tgt, targets, n * 4, cudaMemcpyHostToDevice));
+    CODEC_CUDA(cudaMemset(c->grad, 0, (size_t)c->n_params * 4));
+    CODEC_CUDA(cudaMemset(c->loss, 0, sizeof(double)));
+    if ((rc = launch_codec<true>(c, c->pts, vr::codec::Grid{}, c->tgt, n, nullptr, 0))) return rc;
+    CODEC_CUDA(cudaDeviceSynchronize());
+    if ((rc = check_err(c))) return rc;
+    CODEC_CUDA(cudaMemcpy(grad, c->grad, (size_t)c->n_params * 4, cudaMemcpyDeviceToHost));
+    double l = 0;
+    CODEC_CUDA(cudaMemcpy(&l, c->loss, sizeof(double), cudaMemcpyDeviceToHost));
+    if (loss) *loss = l / (double)n;
+    return VR_OK;
+}
+
+int vr_codec_fit_stats(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64_t nz) {
+    using namespace vr::codec;
+    if (!c || !cube) return VR_EINVAL;
+    const int3 n = make_int3((int)nx, (int)ny, (int)nz), B = make_int3(c->B[0], c->B[1], c->B[2]);
+    const int3 nb = make_int3((int)((nx - 2 + B.x) / B.x), (int)((ny - 2 + B.y) / B.y), (int)((nz - 2 + B.z) / B.z));
+    if ((int64_t)nb.x * nb.y * nb.z != c->n_bricks) return VR_EINVAL;
+    brick_stats_kernel<<<c->n_bricks, 256>>>(cube, n, B, nb, c->m, c->s);
+    CODEC_CUDA(cudaGetLastError());
+    return codec_cuda(cudaDeviceSynchronize());
+}
+
+int vr_codec_train(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps, int32_t batch,
+                   float lr, uint64_t seed, double* last_loss) {
+    using namespace vr::codec;
+    if (!c || !cube || steps < 0 || batch < 1) return VR_EINVAL;
+    const int3 n = make_int3((int)nx, (int)ny, (int)nz), B = make_int3(c->B[0], c->B[1], c->B[2]);
+    const int3 nb = make_int3((int)((nx - 2 + B.x) / B.x), (int)((ny - 2 + B.y) / B.y), (int)((nz - 2 + B.z) / B.z));
+    if ((int64_t)nb.x * nb.y * nb.z != c->n_bricks) return VR_EINVAL;
+    int rc = grow_points(c, batch);
+    if (rc) return rc;
+    for (int32_t it = 0; it < steps; ++it) {
+        sample_kernel<<<(batch + 255) / 256, 256>>>(cube, n, B, nb, batch, mix64_host(seed, it), c->pts, c->tgt);
+        CODEC_CUDA(cudaMemsetAsync(c->grad, 0, (size_t)c->n_params * 4));
+        CODEC_CUDA(cudaMemsetAsync(c->loss, 0, sizeof(double)));
+        if ((rc = launch_codec<true>(c, c->pts, Grid{}, c->tgt, batch, nullptr, 0))) return rc;
+        ++c->adam_t;
+        const float c1 = 1.0f / (1.0f - powf(0.9f, (float)c->adam_t));
+        const float c2 = 1.0f / (1.0f - powf(0.999f, (float)c->adam_t));
+        adam_kernel<<<1024, 256>>>(c->theta, c->grad, c->adam1, c->adam2, c->n_params, lr, c1, c2);
+        if ((rc = sync_bf16(c))) return rc;
+    }
+    CODEC_CUDA(cudaDeviceSynchronize());
+    if ((rc = check_err(c))) return rc;
+    if (last_loss) {
+        double l = 0;
+        CODEC_CUDA(cudaMemcpy(&l, c->loss, sizeof(double), cudaMemcpyDeviceToHost));
+        *last_loss = l / (double)batch;
+    }
+    return VR_OK;
+}
+
+int vr_codec_decode_bricks(vr_codec* c, const int32_t* bricks, int32_t n, float* out, void* stream) {
+    using namespace vr::codec;
+    if (!c || (!bricks && n > 0) || !out || n < 0) return VR_EINVAL;
+    if (n == 0) return VR_OK;
+    Grid grid;
+    grid.bricks = bricks;
+    for (int a = 0; a < 3; ++a) grid.dims[a] = c->B[a] + 1;
+    const int64_t pts = (int64_t)n * grid.dims[0] * grid.dims[1] * grid.dims[2];
+    return launch_codec<false>(c, nullptr, grid, nullptr, pts, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -73,8 +73,10 @@ EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_b
            "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_kd_partition", "vr_kd_order",
            "vr_set_region", "vr_region_rect", "vr_plan_region_rect", "vr_render_rect",
            "vr_composite_subimages", "vr_server_create", "vr_server_submit", "vr_server_wait",
-           "vr_server_get_stats", "vr_server_destroy", "vr_codec_gemm_check", "vr_render_noalloc",
-           "vr_last_error"]
+           "vr_server_get_stats", "vr_server_destroy", "vr_codec_gemm_check", "vr_codec_create",
+           "vr_codec_destroy", "vr_codec_param_count", "vr_codec_set_params", "vr_codec_get_params",
+           "vr_codec_forward", "vr_codec_gradient", "vr_codec_fit_stats", "vr_codec_train",
+           "vr_codec_decode_bricks", "vr_render_noalloc", "vr_last_error"]
 
 
 class vr_server_stats(ctypes.Structure):
@@ -93,6 +95,7 @@ def _load():
     lib.vr_destroy.argtypes = [P]
     lib.vr_destroy.restype = None
     lib.vr_server_destroy.restype = None
+    lib.vr_codec_param_count.restype = ctypes.c_int64
     lib.vr_load_cube.argtypes = [P, P, I64, I64, I64]
     lib.vr_load_cube_host.argtypes = [P, P, I64, I64, I64]
     lib.vr_brick.argtypes = [P, I32, I32, I32]
@@ -118,12 +121,25 @@ def _load():
     lib.vr_server_get_stats.argtypes = [P, ctypes.POINTER(vr_server_stats)]
     lib.vr_server_destroy.argtypes = [P]
     lib.vr_codec_gemm_check.argtypes = [P, P, I32, I32, I32, I32, P]
+    lib.vr_codec_create.argtypes = [I32, P, ctypes.POINTER(P)]
+    lib.vr_codec_destroy.argtypes = [P]
+    lib.vr_codec_destroy.restype = None
+    lib.vr_codec_param_count.argtypes = [P]
+    lib.vr_codec_set_params.argtypes = [P, P, P, P]
+    lib.vr_codec_get_params.argtypes = [P, P, P, P]
+    lib.vr_codec_forward.argtypes = [P, P, I64, P]
+    lib.vr_codec_gradient.argtypes = [P, P, P, I64, P, ctypes.POINTER(ctypes.c_double)]
+    lib.vr_codec_fit_stats.argtypes = [P, P, I64, I64, I64]
+    lib.vr_codec_train.argtypes = [P, P, I64, I64, I64, I32, I32, ctypes.c_float, ctypes.c_uint64,
+                                   ctypes.POINTER(ctypes.c_double)]
+    lib.vr_codec_decode_bricks.argtypes = [P, P, I32, P, P]
     lib.vr_render_noalloc.argtypes = [P, I64, I64, I64, I32, I32, I32, P, I32,
                                       ctypes.POINTER(vr_camera), P, P]
     lib.vr_last_error.argtypes = [P]
     lib.vr_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("vr_destroy", "vr_last_error", "vr_server_destroy"):
+        if name not in ("vr_destroy", "vr_last_error", "vr_server_destroy", "vr_codec_destroy",
+                        "vr_codec_param_count"):
             getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -409,6 +425,109 @@ def vr_codec_gemm_check(a_bf16, b_bf16, a_mn_major=0, b_mn_major=0) -> np.ndarra
     if rc != VR_OK:
         raise VRError(rc, "vr_codec_gemm_check")
     return D
+
+
+class Codec:
+    """Learned brick codec (see include/vr.h): latents + shared MLP on the tensor cores."""
+
+    HIDDEN, K_IN, LATENT, NODES = 64, 32, 16, 8
+
+    def __init__(self, n_bricks: int, brick):
+        h = ctypes.c_void_p()
+        B = _i32(brick, 3)
+        rc = _lib.vr_codec_create(int(n_bricks), B.ctypes.data, ctypes.byref(h))
+        if rc != VR_OK:
+            raise VRError(rc, "vr_codec_create")
+        self.h, self.n_bricks, self.brick = h, int(n_bricks), tuple(int(b) for b in brick)
+        self.n_params = int(_lib.vr_codec_param_count(h))
+
+    def close(self):
+        if self.h:
+            _lib.vr_codec_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _rc(self, rc, what):
+        if rc != VR_OK:
+            raise VRError(rc, what)
+
+    # parameter vector <-> dict of arrays (layout of include/vr.h)
+    def pack(self, p: dict, lat) -> np.ndarray:
+        parts = [np.asarray(p["W1"], np.float32).reshape(-1), np.asarray(p["b1"], np.float32).reshape(-1),
+                 np.asarray(p["W2"], np.float32).reshape(-1), np.asarray(p["b2"], np.float32).reshape(-1),
+                 np.asarray(p["w3"], np.float32).reshape(-1), np.asarray(p["b3"], np.float32).reshape(-1),
+                 np.asarray(lat, np.float32).reshape(-1)]
+        th = np.concatenate(parts)
+        assert th.size == self.n_params
+        return th
+
+    def unpack(self, th) -> dict:
+        H, K = self.HIDDEN, self.K_IN
+        o = 0
+        out = {}
+        for name, shape in (("W1", (H, K)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", (1,))):
+            n = int(np.prod(shape))
+            out[name] = np.asarray(th[o:o + n]).reshape(shape)
+            o += n
+        out["lat"] = np.asarray(th[o:]).reshape(self.n_bricks, 8, 8, 8, 16)
+        return out
+
+    def set_params(self, theta, m, s):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        mm = np.ascontiguousarray(m, dtype=np.float32)
+        ss = np.ascontiguousarray(s, dtype=np.float32)
+        self._rc(_lib.vr_codec_set_params(self.h, th.ctypes.data, mm.ctypes.data, ss.ctypes.data),
+                 "vr_codec_set_params")
+
+    def get_params(self):
+        th = np.zeros(self.n_params, np.float32)
+        m = np.zeros(self.n_bricks, np.float32)
+        s = np.zeros(self.n_bricks, np.float32)
+        self._rc(_lib.vr_codec_get_params(self.h, th.ctypes.data, m.ctypes.data, s.ctypes.data), "vr_codec_get_params")
+        return th, m, s
+
+    @staticmethod
+    def points(bricks, u) -> np.ndarray:
+        """float32 (n, 4) point records: u (n, 3) local positions, brick index bits."""
+        pts = np.zeros((len(bricks), 4), np.float32)
+        pts[:, :3] = u
+        pts[:, 3] = np.asarray(bricks, np.int32).view(np.float32)
+        return pts
+
+    def forward(self, pts) -> np.ndarray:
+        pts = np.ascontiguousarray(pts, np.float32)
+        out = np.zeros(len(pts), np.float32)
+        self._rc(_lib.vr_codec_forward(self.h, pts.ctypes.data, len(pts), out.ctypes.data), "vr_codec_forward")
+        return out
+
+    def gradient(self, pts, targets):
+        pts = np.ascontiguousarray(pts, np.float32)
+        t = np.ascontiguousarray(targets, np.float32)
+        g = np.zeros(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        self._rc(_lib.vr_codec_gradient(self.h, pts.ctypes.data, t.ctypes.data, len(pts), g.ctypes.data,
+                                        ctypes.byref(loss)), "vr_codec_gradient")
+        return loss.value, g
+
+    def fit_stats(self, cube_dev):
+        nz, ny, nx = cube_dev.shape
+        self._rc(_lib.vr_codec_fit_stats(self.h, cube_dev.data_ptr(), nx, ny, nz), "vr_codec_fit_stats")
+
+    def train(self, cube_dev, steps: int, batch: int, lr: float, seed: int = 1) -> float:
+        nz, ny, nx = cube_dev.shape
+        loss = ctypes.c_double()
+        self._rc(_lib.vr_codec_train(self.h, cube_dev.data_ptr(), nx, ny, nz, int(steps), int(batch), float(lr),
+                                     int(seed), ctypes.byref(loss)), "vr_codec_train")
+        return loss.value
+
+    def decode_bricks(self, bricks_dev, out_dev, stream=None):
+        self._rc(_lib.vr_codec_decode_bricks(self.h, bricks_dev.data_ptr(), int(bricks_dev.numel()),
+                                             out_dev.data_ptr(), _stream_handle(stream)), "vr_codec_decode_bricks")
 
 
 class Server:

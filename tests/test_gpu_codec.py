@@ -25,3 +25,113 @@ def test_tensor_core_product(vr, a_mn, b_mn, K, N):
     ref = a @ b.T
     scale = np.abs(a) @ np.abs(b).T
     assert np.all(np.abs(D - ref) <= 1e-6 * scale + 1e-30)
+
+
+# ------------------------------------------------------------------ the codec MLP
+
+from oracle import codec as ref   # noqa: E402
+
+
+def _setup(vr, n_bricks=3, brick=(16, 16, 16), seed=5):
+    rng = np.random.default_rng(seed)
+    params, lat = ref.init_params(n_bricks, seed=seed, brick_mean=rng.normal(size=n_bricks),
+                                  brick_scale=rng.uniform(0.5, 2.0, n_bricks))
+    params["b1"] = rng.normal(0, 0.2, 64)
+    params["b2"] = rng.normal(0, 0.2, 64)
+    params["b3"] = np.array(0.3)
+    lat = rng.normal(0, 0.5, lat.shape)
+    c = vr.Codec(n_bricks, brick)
+    c.set_params(c.pack(params, lat), params["m"], params["s"])
+    # the codec keeps FP32 parameters: compare against their FP32 values
+    th, m, s = c.get_params()
+    p = c.unpack(th.astype(np.float64))
+    p["b3"] = p["b3"].reshape(())
+    p["m"], p["s"] = m.astype(np.float64), s.astype(np.float64)
+    return c, p, p["lat"], rng
+
+
+def _points(rng, n, n_bricks, brick):
+    bricks = rng.integers(0, n_bricks, n)
+    u = rng.uniform(0, 1, (n, 3)) * np.array(brick)
+    u[: n // 8] = np.round(u[: n // 8])          # lattice points too
+    return bricks, u
+
+
+def test_codec_forward_matches_the_oracle(vr):
+    """Values of the tensor-core MLP against the FP64 definition with the same
+    BF16 rounding points.  The GPU forms the pre-rounding values in FP32, so a
+    rounding decision can land one BF16 step away from the FP64 one for a few
+    points: 99% agree to 1e-4, all to 1e-2 (relative to 1 + |v|)."""
+    c, p, lat, rng = _setup(vr)
+    bricks, u = _points(rng, 3000, 3, (16, 16, 16))
+    got = c.forward(c.points(bricks, u)).astype(np.float64)
+    want, _ = ref.forward(p, lat, bricks, u / 16.0, bf=True)
+    c.close()
+    e = np.abs(got - want) / (1.0 + np.abs(want))
+    assert np.quantile(e, 0.99) < 1e-4, np.quantile(e, [0.5, 0.99, 1.0])
+    assert e.max() < 1e-2
+    assert np.std(want) > 0.1
+
+
+def test_codec_gradient_matches_the_oracle(vr):
+    c, p, lat, rng = _setup(vr)
+    bricks, u = _points(rng, 4096, 3, (16, 16, 16))
+    targets = rng.normal(size=len(bricks))
+    loss, g = c.gradient(c.points(bricks, u), targets)
+    want_loss, want = ref.backward(p, lat, bricks, u / 16.0, targets, bf=True)
+    c.close()
+    got = c.unpack(g.astype(np.float64))
+    assert abs(loss - want_loss) <= 1e-4 * want_loss
+    for name in ("W1", "b1", "W2", "b2", "w3", "b3", "lat"):
+        a, b = got[name].reshape(-1), np.asarray(want[name]).reshape(-1)
+        if name == "W1":
+            a, b = got[name][:, :28].reshape(-1), want[name][:, :28].reshape(-1)
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel < 2e-3, (name, rel)
+    assert np.abs(got["W1"][:, 28:]).max() == 0.0   # the padded inputs are zero
+
+
+def test_codec_decodes_brick_blocks(vr):
+    import torch
+    brick = (8, 12, 10)
+    c, p, lat, rng = _setup(vr, n_bricks=4, brick=brick)
+    ids = torch.tensor([2, 0], dtype=torch.int32, device="cuda")
+    V = 9 * 13 * 11
+    out = torch.zeros(2 * V, dtype=torch.float32, device="cuda")
+    c.decode_bricks(ids, out)
+    torch.cuda.synchronize()
+    q = np.arange(V)
+    u = np.stack([q % 9, (q // 9) % 13, q // (9 * 13)], axis=1).astype(np.float64)
+    for k, b in enumerate([2, 0]):
+        direct = c.forward(c.points(np.full(V, b), u))
+        assert np.array_equal(out[k * V:(k + 1) * V].cpu().numpy(), direct)
+    c.close()
+
+
+def test_codec_training_fits_a_cube(vr):
+    """Adam on voxels of a smooth synthetic cube lowers the loss by 10x."""
+    import torch
+
+    import synth
+    cube = synth.hi_cube(seed=21, shape_xyz=(33, 33, 33), n_line=6, n_cont=1)
+    brick = (16, 16, 16)
+    nb = 2 * 2 * 2
+    dev = torch.from_numpy(cube).cuda()
+    p, lat = ref.init_params(nb, seed=3)
+    with vr.Codec(nb, brick) as c:
+        c.set_params(c.pack(p, lat), np.zeros(nb), np.ones(nb))
+        c.fit_stats(dev)
+        th, m, s = c.get_params()
+        c.set_params(th, m, s)
+        rng = np.random.default_rng(0)
+        bricks, u = _points(rng, 4096, nb, brick)
+        bi = np.asarray(bricks)
+        gx = np.minimum((bi % 2) * 16 + np.round(u[:, 0]).astype(int), 32)
+        gy = np.minimum(((bi // 2) % 2) * 16 + np.round(u[:, 1]).astype(int), 32)
+        gz = np.minimum((bi // 4) * 16 + np.round(u[:, 2]).astype(int), 32)
+        u = np.stack([gx - (bi % 2) * 16, gy - ((bi // 2) % 2) * 16, gz - (bi // 4) * 16], axis=1)
+        target = cube[gz, gy, gx]
+        before = np.mean((c.forward(c.points(bricks, u)) - target) ** 2)
+        c.train(dev, steps=300, batch=8192, lr=3e-3, seed=9)
+        after = np.mean((c.forward(c.points(bricks, u)) - target) ** 2)
+    assert after < 0.1 * before, (before, after)
