@@ -443,21 +443,45 @@ int vr_codec_forward(vr_codec* codec, const float* points, int64_t n, float* val
 int vr_codec_gradient(vr_codec* codec, const float* points, const float* targets, int64_t n, float* grad,
                       double* loss);
 
-/* m_b, s_b = mean and standard deviation (>= 1e-3) of each brick's voxels and
- * apron in a device cube float32[nz][ny][nx] bricked by B.  Errors: VR_EINVAL, VR_ECUDA. */
-int vr_codec_fit_stats(vr_codec* codec, const float* cube, int64_t nx, int64_t ny, int64_t nz);
+/* Fit the codec's per-brick data to a device cube float32[nz][ny][nx] bricked by
+ * B: m_b, s_b = mean and standard deviation (>= 1e-3) of max(value, floor_v) over
+ * each brick's voxels and apron, and the brick's [min, max] of the values (for
+ * empty-space skipping when rendering the codec).  floor_v: training targets are
+ * max(value, floor_v) (-FLT_MAX: the values themselves); choose a value below
+ * which the transfer function is transparent, so that the codec spends nothing
+ * on invisible noise.  Errors: VR_EINVAL, VR_ECUDA. */
+int vr_codec_fit_stats(vr_codec* codec, const float* cube, int64_t nx, int64_t ny, int64_t nz, float floor_v);
+
+/* The per-brick [min, max] recorded by vr_codec_fit_stats (host float32[n][2]). */
+int vr_codec_get_minmax(vr_codec* codec, float* out);
+int32_t vr_codec_brick_count(const vr_codec* codec);
+void vr_codec_brick_size(const vr_codec* codec, int32_t B[3]);
 
 /* `steps` Adam steps (lr; betas 0.9, 0.999; eps 1e-8) on `batch` voxels drawn per
  * step (uniform brick, uniform voxel of its block clipped to the cube; counter-
- * based generator seeded by seed) from the device cube; *last_loss = the last
- * step's loss.  Errors: as forward. */
+ * based generator seeded by seed) from the device cube, targets max(value,
+ * floor_v) of vr_codec_fit_stats; *last_loss = the last step's loss.
+ * Errors: as forward. */
 int vr_codec_train(vr_codec* codec, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps,
                    int32_t batch, float lr, uint64_t seed, double* last_loss);
 
-/* Decode the blocks of n bricks (device list) into device memory out, brick k's
- * (bx+1)(by+1)(bz+1) values at out + k * that (x fastest), on `stream`.
+/* Decode the blocks of n bricks (device list of valid brick indices) into device
+ * memory: brick k's V = (bx+1)(by+1)(bz+1) values (x fastest) go to out + k V, or
+ * to out + slots[k] V when slots (device) is not NULL; on `stream`.
  * Errors: VR_EINVAL, VR_ECUDA. */
-int vr_codec_decode_bricks(vr_codec* codec, const int32_t* bricks, int32_t n, float* out, void* stream);
+int vr_codec_decode_bricks(vr_codec* codec, const int32_t* bricks, const int32_t* slots, int32_t n, float* out,
+                           void* stream);
+
+/*
+ * Render from a codec instead of a cube (no counterpart in the paper): like
+ * vr_load_cube_host, the context keeps a device brick cache (VR_OPT_DEVICE_BUDGET)
+ * and marches bricks from it with the direct kernel, but fills a slot by decoding
+ * the brick on the tensor cores instead of copying it from host memory.  Empty-
+ * space skipping uses the ranges recorded by vr_codec_fit_stats.  The codec must
+ * outlive the context's use of it; vr_brick must give the codec's brick size.
+ * Errors: VR_EINVAL (sizes or bricking do not match the codec), VR_ECUDA.
+ */
+int vr_load_cube_codec(vr_ctx* ctx, vr_codec* codec, int64_t nx, int64_t ny, int64_t nz);
 
 /*
  * Allocation-free render (the paper has no counterpart; this serves callers that

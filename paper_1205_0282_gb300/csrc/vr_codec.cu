@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cfloat>
 #include <cstring>
 
 #include "../../include/vr.h"
@@ -244,11 +245,13 @@ __device__ __forceinline__ void mma_chain(uint32_t d_tmem, uint32_t a_start, uin
 // TRAIN = false: out[p] = decoded value.  TRAIN = true: the step's loss and
 // gradients (targets in tgt) are accumulated into g.
 // Points come from pts, or (pts == nullptr) from the voxel grids of the bricks
-// listed in grid_bricks: point q is voxel (q % V) of brick grid_bricks[q / V], V =
-// (Bx+1)(By+1)(Bz+1) voxels x fastest, and out[q] is its slot-layout value.
+// listed in grid.bricks: point q is voxel (q % V) of brick grid.bricks[q / V], V =
+// (Bx+1)(By+1)(Bz+1) voxels x fastest, written to out[q] (or, with grid.slots, to
+// out[grid.slots[q / V] * V + q % V]).
 struct Grid {
     const int32_t* bricks;
-    int32_t dims[3];  // B + 1 per axis
+    const int32_t* slots;  // nullptr: brick k's block at k * V; else at slots[k] * V
+    int32_t dims[3];       // B + 1 per axis
 };
 
 template <bool TRAIN>
@@ -368,7 +371,14 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
         const float sb = valid ? net.s[brick] : 0.0f;
         const float v = valid ? fmaf(y, sb, net.m[brick]) : 0.0f;
         if (!TRAIN) {
-            if (valid) out[idx] = v;
+            if (valid) {
+                int64_t o = idx;
+                if (!pts && grid.slots) {
+                    const int64_t V = (int64_t)grid.dims[0] * grid.dims[1] * grid.dims[2];
+                    o = (int64_t)grid.slots[idx / V] * V + idx % V;
+                }
+                out[o] = v;
+            }
             tc::fence_before_sync();
             __syncthreads();  // D1 / D2 and the operand tiles are reused by the next tile
             tc::fence_after_sync();
@@ -554,7 +564,7 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 // Training points: uniform brick, uniform voxel of its (B+1)^3 block clipped to
 // the cube; target = the cube's value there.
 __global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, int64_t n_points,
-                              uint64_t seed, float4* __restrict__ pts, float* __restrict__ tgt) {
+                              uint64_t seed, float floor_v, float4* __restrict__ pts, float* __restrict__ tgt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_points) return;
     const uint64_t r0 = mix64(seed ^ (uint64_t)(2 * i)), r1 = mix64(seed ^ (uint64_t)(2 * i + 1));
@@ -566,34 +576,44 @@ __global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, in
     const int uz = (int)(((r1 >> 40) & 0xFFFFF) % (uint64_t)(B.z + 1));
     const int gx = min(bx * B.x + ux, n.x - 1), gy = min(by * B.y + uy, n.y - 1), gz = min(bz * B.z + uz, n.z - 1);
     pts[i] = make_float4((float)(gx - bx * B.x), (float)(gy - by * B.y), (float)(gz - bz * B.z), __int_as_float(b));
-    tgt[i] = cube[((int64_t)gz * n.y + gy) * n.x + gx];
+    tgt[i] = fmaxf(cube[((int64_t)gz * n.y + gy) * n.x + gx], floor_v);
 }
 
 // Per-brick offset and scale: mean and standard deviation (at least 1e-3) over
 // the brick's voxels and apron.
-__global__ void brick_stats_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, float* m, float* s) {
+__global__ void brick_stats_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, float floor_v, float* m,
+                                   float* s, float2* mm) {
     const int b = blockIdx.x;
     const int bx = b % nb.x, by = (b / nb.x) % nb.y, bz = b / (nb.x * nb.y);
     const int x0 = bx * B.x, y0 = by * B.y, z0 = bz * B.z;
     const int x1 = min(x0 + B.x, n.x - 1), y1 = min(y0 + B.y, n.y - 1), z1 = min(z0 + B.z, n.z - 1);
     double s1 = 0, s2 = 0;
+    float lo = FLT_MAX, hi = -FLT_MAX;
     const int64_t cnt = (int64_t)(x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1);
     for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
         const int x = x0 + (int)(q % (x1 - x0 + 1));
         const int y = y0 + (int)((q / (x1 - x0 + 1)) % (y1 - y0 + 1));
         const int z = z0 + (int)(q / ((int64_t)(x1 - x0 + 1) * (y1 - y0 + 1)));
-        const double v = cube[((int64_t)z * n.y + y) * n.x + x];
+        const float raw = cube[((int64_t)z * n.y + y) * n.x + x];
+        lo = fminf(lo, raw);
+        hi = fmaxf(hi, raw);
+        const double v = fmaxf(raw, floor_v);
         s1 += v;
         s2 += v * v;
     }
     __shared__ double a1[256], a2[256];
+    __shared__ float l1[256], h1[256];
     a1[threadIdx.x] = s1;
     a2[threadIdx.x] = s2;
+    l1[threadIdx.x] = lo;
+    h1[threadIdx.x] = hi;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) {
             a1[threadIdx.x] += a1[threadIdx.x + o];
             a2[threadIdx.x] += a2[threadIdx.x + o];
+            l1[threadIdx.x] = fminf(l1[threadIdx.x], l1[threadIdx.x + o]);
+            h1[threadIdx.x] = fmaxf(h1[threadIdx.x], h1[threadIdx.x + o]);
         }
         __syncthreads();
     }
@@ -602,6 +622,7 @@ __global__ void brick_stats_kernel(const float* __restrict__ cube, int3 n, int3 
         const double var = fmax(a2[0] / (double)cnt - mean * mean, 0.0);
         m[b] = (float)mean;
         s[b] = (float)fmax(sqrt(var), 1e-3);
+        mm[b] = make_float2(l1[0], h1[0]);
     }
 }
 
@@ -623,6 +644,8 @@ struct vr_codec {
     float* w3r = nullptr;  // w3 rounded to BF16 values
     float* m = nullptr;
     float* s = nullptr;
+    float2* minmax = nullptr;  // per-brick range of the data the codec was fitted to
+    float floor_v = -FLT_MAX;  // training targets are max(value, floor_v)
     double* loss = nullptr;
     int* err = nullptr;
     float4* pts = nullptr;
@@ -747,7 +770,8 @@ int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
               cudaMalloc(&c->W2h, kHidden * kHidden * 2) == cudaSuccess &&
               cudaMalloc(&c->lath, (size_t)n_bricks * kLatPerBrick * 2) == cudaSuccess &&
               cudaMalloc(&c->w3r, kHidden * 4) == cudaSuccess && cudaMalloc(&c->m, n_bricks * 4) == cudaSuccess &&
-              cudaMalloc(&c->s, n_bricks * 4) == cudaSuccess && cudaMalloc(&c->loss, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->s, n_bricks * 4) == cudaSuccess && cudaMalloc(&c->minmax, n_bricks * 8) == cudaSuccess &&
+              cudaMalloc(&c->loss, sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->err, sizeof(int)) == cudaSuccess;
     if (ok) ok = cudaMemset(c->theta, 0, pb) == cudaSuccess && cudaMemset(c->adam1, 0, pb) == cudaSuccess &&
                  cudaMemset(c->adam2, 0, pb) == cudaSuccess && cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess;
@@ -763,7 +787,8 @@ int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
 void vr_codec_destroy(vr_codec* c) {
     if (!c) return;
     for (void* p : {(void*)c->theta, (void*)c->grad, (void*)c->adam1, (void*)c->adam2, (void*)c->W1h, (void*)c->W2h,
-                    (void*)c->lath, (void*)c->w3r, (void*)c->m, (void*)c->s, (void*)c->loss, (void*)c->err,
+                    (void*)c->lath, (void*)c->w3r, (void*)c->m, (void*)c->s, (void*)c->minmax, (void*)c->loss,
+                    (void*)c->err,
                     (void*)c->pts, (void*)c->tgt})
         cudaFree(p);
     delete c;
@@ -833,15 +858,21 @@ int vr_codec_gradient(vr_codec* c, const float* points, const float* targets, in
     return VR_OK;
 }
 
-int vr_codec_fit_stats(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64_t nz) {
+int vr_codec_fit_stats(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64_t nz, float floor_v) {
     using namespace vr::codec;
     if (!c || !cube) return VR_EINVAL;
     const int3 n = make_int3((int)nx, (int)ny, (int)nz), B = make_int3(c->B[0], c->B[1], c->B[2]);
     const int3 nb = make_int3((int)((nx - 2 + B.x) / B.x), (int)((ny - 2 + B.y) / B.y), (int)((nz - 2 + B.z) / B.z));
     if ((int64_t)nb.x * nb.y * nb.z != c->n_bricks) return VR_EINVAL;
-    brick_stats_kernel<<<c->n_bricks, 256>>>(cube, n, B, nb, c->m, c->s);
+    c->floor_v = floor_v;
+    brick_stats_kernel<<<c->n_bricks, 256>>>(cube, n, B, nb, floor_v, c->m, c->s, c->minmax);
     CODEC_CUDA(cudaGetLastError());
     return codec_cuda(cudaDeviceSynchronize());
+}
+
+int vr_codec_get_minmax(vr_codec* c, float* out) {
+    if (!c || !out) return VR_EINVAL;
+    return codec_cuda(cudaMemcpy(out, c->minmax, (size_t)c->n_bricks * 8, cudaMemcpyDeviceToHost));
 }
 
 int vr_codec_train(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps, int32_t batch,
@@ -854,7 +885,8 @@ int vr_codec_train(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64
     int rc = grow_points(c, batch);
     if (rc) return rc;
     for (int32_t it = 0; it < steps; ++it) {
-        sample_kernel<<<(batch + 255) / 256, 256>>>(cube, n, B, nb, batch, mix64_host(seed, it), c->pts, c->tgt);
+        sample_kernel<<<(batch + 255) / 256, 256>>>(cube, n, B, nb, batch, mix64_host(seed, it), c->floor_v, c->pts,
+                                                    c->tgt);
         CODEC_CUDA(cudaMemsetAsync(c->grad, 0, (size_t)c->n_params * 4));
         CODEC_CUDA(cudaMemsetAsync(c->loss, 0, sizeof(double)));
         if ((rc = launch_codec<true>(c, c->pts, Grid{}, c->tgt, batch, nullptr, 0))) return rc;
@@ -874,15 +906,22 @@ int vr_codec_train(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64
     return VR_OK;
 }
 
-int vr_codec_decode_bricks(vr_codec* c, const int32_t* bricks, int32_t n, float* out, void* stream) {
+int vr_codec_decode_bricks(vr_codec* c, const int32_t* bricks, const int32_t* slots, int32_t n, float* out,
+                           void* stream) {
     using namespace vr::codec;
     if (!c || (!bricks && n > 0) || !out || n < 0) return VR_EINVAL;
     if (n == 0) return VR_OK;
     Grid grid;
     grid.bricks = bricks;
+    grid.slots = slots;
     for (int a = 0; a < 3; ++a) grid.dims[a] = c->B[a] + 1;
     const int64_t pts = (int64_t)n * grid.dims[0] * grid.dims[1] * grid.dims[2];
     return launch_codec<false>(c, nullptr, grid, nullptr, pts, out, (cudaStream_t)stream);
+}
+
+int32_t vr_codec_brick_count(const vr_codec* c) { return c ? c->n_bricks : -1; }
+void vr_codec_brick_size(const vr_codec* c, int32_t B[3]) {
+    for (int a = 0; a < 3; ++a) B[a] = c ? c->B[a] : 0;
 }
 
 }  // extern "C"

@@ -40,6 +40,9 @@ struct Slot {
     int32_t* h_slot_of = nullptr;  // out-of-core: cache slot of each brick (pinned)
     int32_t* d_slot_of = nullptr;
     size_t cap_slot_of = 0, dcap_slot_of = 0;
+    int32_t* h_decode = nullptr;  // learned residency: (brick, slot) lists of the frame's decodes
+    int32_t* d_decode = nullptr;
+    size_t cap_decode = 0, dcap_decode = 0;
     cudaEvent_t ev_begin = nullptr, ev_march0 = nullptr, ev_march1 = nullptr, ev_end = nullptr;
     bool pending = false;
     // host-side facts of the frame in flight
@@ -233,6 +236,7 @@ struct vr_ctx {
     // out-of-core mode (vr_load_cube_host): cube in host memory, bricks cached on the device
     bool ooc = false;
     const float* h_src = nullptr;      // the caller's cube
+    vr_codec* codec = nullptr;         // learned residency: slots are filled by decoding
     float* h_store = nullptr;          // pinned brick store, brick b at b * slot_floats
     size_t store_bytes = 0;
     int64_t slot_floats = 0;           // (Bx+1)(By+1)(Bz+1)

@@ -79,7 +79,25 @@ void free_ooc(vr_ctx* c) {
     c->store_bytes = 0;
     c->res = vr::Residency();
     c->h_src = nullptr;
+    c->codec = nullptr;
     c->ooc = false;
+}
+
+// Side streams and events of the out-of-core pipeline (created once per context).
+int ensure_ooc_streams(vr_ctx* c) {
+    if (c->copy_stream) return VR_OK;
+    VR_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_march_done, cudaEventDisableTiming));
+    VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_copy_done, cudaEventDisableTiming));
+    for (cudaEvent_t& ev : c->ev_half_read) VR_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    // the ring's marches free its halves for the next copies: schedule their
+    // blocks ahead of the resident bricks' long launch
+    int lo_prio = 0, hi_prio = 0;
+    VR_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    VR_CUDA(c, cudaStreamCreateWithPriority(&c->ring_stream, cudaStreamNonBlocking, hi_prio));
+    VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_start, cudaEventDisableTiming));
+    VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_end, cudaEventDisableTiming));
+    return VR_OK;
 }
 
 // Brick store and device cache of an out-of-core context (at vr_brick).
@@ -90,13 +108,22 @@ int build_ooc_store(vr_ctx* c) {
     c->d_pool = nullptr;
     c->slot_floats = (int64_t)(c->B[0] + 1) * (c->B[1] + 1) * (c->B[2] + 1);
     const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
-    c->store_bytes = slot_bytes * (size_t)c->n_bricks;
-    if (cudaHostAlloc((void**)&c->h_store, c->store_bytes, cudaHostAllocDefault) != cudaSuccess) {
-        cudaGetLastError();
-        c->h_store = nullptr;
-        return fail(c, VR_ENOMEM, "cannot allocate the pinned brick store");
+    if (c->codec) {
+        int32_t cb[3];
+        vr_codec_brick_size(c->codec, cb);
+        if (cb[0] != c->B[0] || cb[1] != c->B[1] || cb[2] != c->B[2] || vr_codec_brick_count(c->codec) != c->n_bricks)
+            return fail(c, VR_EINVAL, "the bricking does not match the codec's");
+        if (vr_codec_get_minmax(c->codec, reinterpret_cast<float*>(c->h_minmax.data())))
+            return fail(c, VR_ECUDA, "cannot read the codec's brick ranges");
+    } else {
+        c->store_bytes = slot_bytes * (size_t)c->n_bricks;
+        if (cudaHostAlloc((void**)&c->h_store, c->store_bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            c->h_store = nullptr;
+            return fail(c, VR_ENOMEM, "cannot allocate the pinned brick store");
+        }
+        vr::build_brick_store(c->h_src, c->n, c->B, c->nb, c->h_store, c->slot_floats, c->h_minmax.data());
     }
-    vr::build_brick_store(c->h_src, c->n, c->B, c->nb, c->h_store, c->slot_floats, c->h_minmax.data());
     int64_t slots = c->n_bricks;
     if (c->budget > 0) slots = std::min<int64_t>(slots, c->budget / (int64_t)slot_bytes);
     if (slots < 2) return fail(c, VR_EINVAL, "VR_OPT_DEVICE_BUDGET holds fewer than 2 bricks");
@@ -291,6 +318,8 @@ void vr_destroy(vr_ctx* c) {
         if (s.h_frame) cudaFreeHost(s.h_frame);
         if (s.h_slot_of) cudaFreeHost(s.h_slot_of);
         cudaFree(s.d_slot_of);
+        if (s.h_decode) cudaFreeHost(s.h_decode);
+        cudaFree(s.d_decode);
         cudaFree(s.d_frame);
         cudaFree(s.d_items);
         cudaFree(s.d_tile_start);
@@ -378,21 +407,36 @@ int vr_load_cube_host(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int6
     c->tex_fits = -1;
     free_tex(c);
     free_ooc(c);
-    if (!c->copy_stream) {
-        VR_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-        VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_march_done, cudaEventDisableTiming));
-        VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_copy_done, cudaEventDisableTiming));
-        for (cudaEvent_t& ev : c->ev_half_read) VR_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        // the ring's marches free its halves for the next copies: schedule their
-        // blocks ahead of the resident bricks' long launch
-        int lo_prio = 0, hi_prio = 0;
-        VR_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
-        VR_CUDA(c, cudaStreamCreateWithPriority(&c->ring_stream, cudaStreamNonBlocking, hi_prio));
-        VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_start, cudaEventDisableTiming));
-        VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_end, cudaEventDisableTiming));
-    }
+    if ((rc = ensure_ooc_streams(c))) return rc;
     c->ooc = true;
     c->h_src = data;
+    c->nx_pad = nx;
+    c->n[0] = nx;
+    c->n[1] = ny;
+    c->n[2] = nz;
+    return VR_OK;
+}
+
+int vr_load_cube_codec(vr_ctx* c, vr_codec* codec, int64_t nx, int64_t ny, int64_t nz) {
+    if (!c) return VR_EINVAL;
+    if (!codec) return fail(c, VR_EINVAL, "null codec");
+    if (nx < 2 || ny < 2 || nz < 2 || nx > 65536 || ny > 65536 || nz > 65536)
+        return fail(c, VR_EINVAL, "cube sizes must be in [2, 65536]");
+    VR_CUDA(c, cudaSetDevice(c->device));
+    int rc = retire_all(c);
+    if (rc) return rc;
+    cudaFree(c->d_cube);
+    cudaFree(c->d_cube_xzy);
+    c->d_cube = nullptr;
+    c->d_cube_xzy = nullptr;
+    c->bricked = false;
+    c->tma_ready = false;
+    c->tex_fits = -1;
+    free_tex(c);
+    free_ooc(c);
+    if ((rc = ensure_ooc_streams(c))) return rc;
+    c->ooc = true;
+    c->codec = codec;
     c->nx_pad = nx;
     c->n[0] = nx;
     c->n[1] = ny;
@@ -770,9 +814,22 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocL
     return VR_OK;
 }
 
-// Copy bricks into their cache slots on the copy stream.
-int ooc_upload(vr_ctx* c, const OocLaunch& L) {
+// Fill the bricks' cache slots on the copy stream: copy them from the pinned
+// store, or decode them (learned residency; list_off: where this launch's
+// (brick, slot) lists sit in the frame's list buffers).
+int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off) {
     const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
+    if (c->codec) {
+        const size_t n = L.up.size();
+        std::memcpy(s.h_decode + list_off, L.up.data(), n * sizeof(int32_t));
+        std::memcpy(s.h_decode + list_off + n, L.slot.data(), n * sizeof(int32_t));
+        VR_CUDA(c, cudaMemcpyAsync(s.d_decode + list_off, s.h_decode + list_off, 2 * n * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, c->copy_stream));
+        const int rc = vr_codec_decode_bricks(c->codec, s.d_decode + list_off, s.d_decode + list_off + n, (int32_t)n,
+                                              c->d_pool, c->copy_stream);
+        if (rc) return fail(c, rc, "brick decode failed");
+        return VR_OK;
+    }
     for (size_t k = 0; k < L.up.size(); ++k)
         VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
                                    c->h_store + (size_t)L.up[k] * c->slot_floats, slot_bytes,
@@ -892,15 +949,22 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
         const size_t nl = ooc_launches.size();
         int rc2 = ensure_events(c, c->ev_chunk, nl);
         if (rc2) return rc2;
+        // learned residency: room for every launch's (brick, slot) lists
+        std::vector<size_t> list_off(nl + 1, 0);
+        for (size_t k = 0; k < nl; ++k) list_off[k + 1] = list_off[k] + 2 * ooc_launches[k].up.size();
+        if (c->codec) {
+            if ((rc2 = grow_pinned(c, s.h_decode, s.cap_decode, std::max<size_t>(list_off[nl], 1)))) return rc2;
+            if ((rc2 = grow_device(c, s.d_decode, s.dcap_decode, std::max<size_t>(list_off[nl], 1)))) return rc2;
+        }
         auto issue_upload = [&](size_t k) -> int {
             const OocLaunch& L = ooc_launches[k];
             if (L.up.empty()) return VR_OK;
             // a ring half is refilled once its last reader has marched (host issue
             // order puts that reader's event record before this wait)
             if (L.half >= 0) VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_half_read[L.half], 0));
-            int r = ooc_upload(c, L);
+            int r = ooc_upload(c, s, L, list_off[k]);
             if (r) return r;
-            upload_bytes += L.up.size() * (size_t)c->slot_floats * sizeof(float);
+            if (!c->codec) upload_bytes += L.up.size() * (size_t)c->slot_floats * sizeof(float);
             VR_CUDA(c, cudaEventRecord(c->ev_chunk[k], c->copy_stream));
             VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));
             return VR_OK;

@@ -76,7 +76,8 @@ EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_b
            "vr_server_get_stats", "vr_server_destroy", "vr_codec_gemm_check", "vr_codec_create",
            "vr_codec_destroy", "vr_codec_param_count", "vr_codec_set_params", "vr_codec_get_params",
            "vr_codec_forward", "vr_codec_gradient", "vr_codec_fit_stats", "vr_codec_train",
-           "vr_codec_decode_bricks", "vr_render_noalloc", "vr_last_error"]
+           "vr_codec_decode_bricks", "vr_codec_get_minmax", "vr_codec_brick_count", "vr_codec_brick_size",
+           "vr_load_cube_codec", "vr_render_noalloc", "vr_last_error"]
 
 
 class vr_server_stats(ctypes.Structure):
@@ -129,17 +130,23 @@ def _load():
     lib.vr_codec_get_params.argtypes = [P, P, P, P]
     lib.vr_codec_forward.argtypes = [P, P, I64, P]
     lib.vr_codec_gradient.argtypes = [P, P, P, I64, P, ctypes.POINTER(ctypes.c_double)]
-    lib.vr_codec_fit_stats.argtypes = [P, P, I64, I64, I64]
+    lib.vr_codec_fit_stats.argtypes = [P, P, I64, I64, I64, ctypes.c_float]
+    lib.vr_codec_get_minmax.argtypes = [P, P]
+    lib.vr_codec_brick_count.argtypes = [P]
+    lib.vr_codec_brick_count.restype = I32
+    lib.vr_codec_brick_size.argtypes = [P, P]
+    lib.vr_codec_brick_size.restype = None
+    lib.vr_load_cube_codec.argtypes = [P, P, I64, I64, I64]
     lib.vr_codec_train.argtypes = [P, P, I64, I64, I64, I32, I32, ctypes.c_float, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_double)]
-    lib.vr_codec_decode_bricks.argtypes = [P, P, I32, P, P]
+    lib.vr_codec_decode_bricks.argtypes = [P, P, P, I32, P, P]
     lib.vr_render_noalloc.argtypes = [P, I64, I64, I64, I32, I32, I32, P, I32,
                                       ctypes.POINTER(vr_camera), P, P]
     lib.vr_last_error.argtypes = [P]
     lib.vr_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("vr_destroy", "vr_last_error", "vr_server_destroy", "vr_codec_destroy",
-                        "vr_codec_param_count"):
+                        "vr_codec_param_count", "vr_codec_brick_count", "vr_codec_brick_size"):
             getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -514,9 +521,15 @@ class Codec:
                                         ctypes.byref(loss)), "vr_codec_gradient")
         return loss.value, g
 
-    def fit_stats(self, cube_dev):
+    def fit_stats(self, cube_dev, floor=-3.4e38):
         nz, ny, nx = cube_dev.shape
-        self._rc(_lib.vr_codec_fit_stats(self.h, cube_dev.data_ptr(), nx, ny, nz), "vr_codec_fit_stats")
+        self._rc(_lib.vr_codec_fit_stats(self.h, cube_dev.data_ptr(), nx, ny, nz, float(floor)),
+                 "vr_codec_fit_stats")
+
+    def minmax(self) -> np.ndarray:
+        out = np.zeros((self.n_bricks, 2), np.float32)
+        self._rc(_lib.vr_codec_get_minmax(self.h, out.ctypes.data), "vr_codec_get_minmax")
+        return out
 
     def train(self, cube_dev, steps: int, batch: int, lr: float, seed: int = 1) -> float:
         nz, ny, nx = cube_dev.shape
@@ -525,9 +538,11 @@ class Codec:
                                      int(seed), ctypes.byref(loss)), "vr_codec_train")
         return loss.value
 
-    def decode_bricks(self, bricks_dev, out_dev, stream=None):
-        self._rc(_lib.vr_codec_decode_bricks(self.h, bricks_dev.data_ptr(), int(bricks_dev.numel()),
-                                             out_dev.data_ptr(), _stream_handle(stream)), "vr_codec_decode_bricks")
+    def decode_bricks(self, bricks_dev, out_dev, slots_dev=None, stream=None):
+        self._rc(_lib.vr_codec_decode_bricks(self.h, bricks_dev.data_ptr(),
+                                             None if slots_dev is None else slots_dev.data_ptr(),
+                                             int(bricks_dev.numel()), out_dev.data_ptr(), _stream_handle(stream)),
+                 "vr_codec_decode_bricks")
 
 
 class Server:
@@ -610,6 +625,12 @@ class VolumeRenderer:
         nz, ny, nx = cube.shape
         self.shape_xyz = (nx, ny, nz)
         self._host_cube = None
+
+    def load_cube_codec(self, codec, shape_xyz):
+        """Render from a learned codec (bricks decoded into the device cache)."""
+        _check(self.ctx, _lib.vr_load_cube_codec(self.ctx, codec.h, *shape_xyz))
+        self.shape_xyz = tuple(int(v) for v in shape_xyz)
+        self._host_cube = codec
 
     def load_cube_host(self, cube):
         """Out-of-core: the cube stays in host memory (a reference is kept)."""
