@@ -64,6 +64,12 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="--serve: length of the arrival window")
     ap.add_argument("--arena-gib", type=float, default=16.0, help="--serve: device arena (two batch halves)")
     ap.add_argument("--max-batch", type=int, default=32, help="--serve: frames per batch at most")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned brick codec: train latents + MLP on the cube, render from decoded bricks, PSNR")
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--train-batch", type=int, default=262144)
+    ap.add_argument("--train-lr", type=float, default=3e-3)
+    ap.add_argument("--psnr-poses", type=int, default=12)
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -541,6 +547,151 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def tf_floor(tf):
+    """The largest value below which the transfer function's opacity is zero
+    (its first control point with nonzero opacity, or the one before it)."""
+    tf = np.asarray(tf, dtype=np.float64).reshape(-1, 5)
+    first = int(np.argmax(tf[:, 4] > 0))
+    return float(tf[max(first - 1, 0), 0]) if tf[first, 4] > 0 else float(tf[-1, 0])
+
+
+def run_learned(args):
+    """Learned brick codec on the workload's cube: per brick an 8^3 x 16 latent grid
+    and one shared MLP (28 inputs, two hidden layers of 64, SiLU) trained on the
+    GPU by the tensor-core kernels on voxels clipped below the transfer
+    function's transparent floor; frames rendered from bricks decoded into the
+    device cache; PSNR against the plain (in-core FP32) render of the same poses."""
+    import torch
+
+    from paper_1205_0282_gb300 import vr as vrm
+
+    torch.cuda.set_device(0)
+    spec, tf, poses, desc = workload(args)
+    cube = make_cube(spec)
+    shape, brick = spec["shape_xyz"], spec["brick"]
+    nb = int(np.prod([(n - 1 + b - 1) // b for n, b in zip(shape, brick)]))
+    dcube = torch.from_numpy(cube).cuda()
+    W, H = spec["width"], spec["height"]
+    q = max(1, len(poses) // args.psnr_poses)
+    psnr_poses = poses[::q][:args.psnr_poses]
+    # plain reference images (in-core, FP32 texture path)
+    plain = []
+    with vrm.VolumeRenderer(0) as r:
+        r.load_cube(dcube)
+        r.brick(*brick)
+        r.set_transfer_function(tf)
+        for cam in psnr_poses:
+            r.set_camera(cam)
+            plain.append(r.render().cpu().numpy().astype(np.float64))
+    # train
+    floor = tf_floor(tf)
+    codec = vrm.Codec(nb, brick)
+    rng = np.random.default_rng(3)
+    H_, K_ = vrm.Codec.HIDDEN, vrm.Codec.K_IN
+    W1 = rng.uniform(-1, 1, (H_, K_)) / np.sqrt(28.0)
+    W1[:, 28:] = 0.0
+    params = {"W1": W1, "b1": np.zeros(H_), "W2": rng.uniform(-1, 1, (H_, H_)) / np.sqrt(H_),
+              "b2": np.zeros(H_), "w3": rng.uniform(-1, 1, H_) / np.sqrt(H_), "b3": np.zeros(1)}
+    lat = rng.normal(0.0, 0.1, (nb, 8, 8, 8, 16))
+    codec.set_params(codec.pack(params, lat), np.zeros(nb), np.ones(nb))
+    codec.fit_stats(dcube, floor)
+    th, m, s = codec.get_params()
+    codec.set_params(th, m, s)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    chunk = 250
+    losses = []
+    done = 0
+    while done < args.train_steps:
+        k = min(chunk, args.train_steps - done)
+        lr = args.train_lr * (0.1 if done >= 0.8 * args.train_steps else 1.0)
+        losses.append(codec.train(dcube, k, args.train_batch, lr, seed=1000 + done))
+        done += k
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # decode throughput: every brick once (tensor-core MLP at every voxel)
+    V = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1)
+    ids = torch.arange(nb, dtype=torch.int32, device="cuda")
+    dec_batch = min(nb, 256)
+    blocks = torch.empty(dec_batch * V, dtype=torch.float32, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    codec.decode_bricks(ids[:dec_batch], blocks)      # warm-up
+    ev0.record()
+    for b0 in range(0, nb, dec_batch):
+        codec.decode_bricks(ids[b0:b0 + dec_batch], blocks)
+    ev1.record()
+    torch.cuda.synchronize()
+    dec_ms = ev0.elapsed_time(ev1)
+    del blocks
+    points = nb * V
+    mac_tensor = 32 * 64 + 64 * 64           # per point, on the tensor cores
+    dec_tflops = points * 2 * mac_tensor / (dec_ms * 1e-3) / 1e12
+    del dcube
+    torch.cuda.empty_cache()
+
+    def render_learned(budget_gib, steps):
+        r = vrm.VolumeRenderer(0)
+        r.load_cube_codec(codec, shape)
+        if budget_gib > 0:
+            r.set_option(vrm.VR_OPT_DEVICE_BUDGET, int(budget_gib * 2 ** 30))
+        r.brick(*brick)
+        r.set_transfer_function(tf)
+        imgs = []
+        for cam in psnr_poses:
+            r.set_camera(cam)
+            imgs.append(r.render().cpu().numpy().astype(np.float64))
+        out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        for k in range(args.warmup):
+            r.set_camera(poses[k % len(poses)])
+            r.render(out)
+        torch.cuda.synchronize()
+        r.reset_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(steps):
+            r.set_camera(poses[k % len(poses)])
+            r.render(out)
+        e1.record()
+        torch.cuda.synchronize()
+        st = r.stats()
+        r.close()
+        ms = e0.elapsed_time(e1)
+        return imgs, st, ms
+
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    with ClockSampler(gpu_id) as clocks:
+        imgs, st, ms = render_learned(args.budget_gib, args.steps)
+    mse = float(np.mean([np.mean((a - b) ** 2) for a, b in zip(imgs, plain)]))
+    psnr = 10 * np.log10(1.0 / mse) if mse > 0 else None
+    maxerr = float(max(np.abs(a - b).max() for a, b in zip(imgs, plain)))
+    codec.close()
+    frames = args.steps
+    line = {"metric": METRIC, "value": st["samples"] / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / frames, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (decoder bf16 x bf16 -> f32)", "data": "synthetic",
+            "config": {"workload": desc, "form": "learned: 8^3 x 16 BF16 latents per brick + shared MLP "
+                       "(28 -> 64 -> 64 -> 1, SiLU), bricks decoded on the tensor cores into the device cache",
+                       "device_budget_gib": args.budget_gib or "every brick",
+                       "train": {"steps": args.train_steps, "batch": args.train_batch, "lr": args.train_lr,
+                                 "floor": floor}},
+            "fps": frames / (ms * 1e-3),
+            "learned": {"psnr_db_vs_plain": psnr, "max_abs_vs_plain": maxerr, "psnr_poses": len(psnr_poses),
+                        "train_s": train_s, "loss_trace": losses,
+                        "latent_bytes": nb * 8 * 8 * 8 * 16 * 2, "cube_bytes": int(cube.nbytes),
+                        "compression": cube.nbytes / (nb * 8 * 8 * 8 * 16 * 2),
+                        "decode_ms_all_bricks": dec_ms, "decode_points_per_s": points / (dec_ms * 1e-3),
+                        "decode_tensor_tflops": dec_tflops,
+                        "bricks_decoded_per_frame": st["bricks_uploaded"] / max(st["frames"], 1),
+                        "bricks_cached_per_frame": st["bricks_cached"] / max(st["frames"], 1)},
+            "roofline": {"bound": "tensor", "kernel": "codec_kernel (decode)", "achieved": dec_tflops,
+                         "peak": json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+                         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0,
+                         "unit": "TFLOP/s", "traffic": None},
+            "gpu_launches": st["launches"], "clocks": clocks.summary(), "cpu_baseline": None, "e2e": None}
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+    print(json.dumps(line), flush=True)
+
+
 SERVE_RESOLUTIONS = [(512, 512), (1280, 720), (1920, 1080), (3840, 2160)]
 
 
@@ -655,6 +806,8 @@ def main():
     args = parse()
     if args.serve and args.impl == "ours":
         return run_serve(args)
+    if args.learned and args.impl == "ours":
+        return run_learned(args)
     if args.impl == "reference":
         run_reference(args)
     else:
