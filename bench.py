@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--train-batch", type=int, default=262144)
     ap.add_argument("--train-lr", type=float, default=3e-3)
     ap.add_argument("--psnr-poses", type=int, default=12)
+    ap.add_argument("--active-frac", type=float, default=0.5,
+                    help="--learned: share of training points drawn from voxels the transfer function can show")
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -605,7 +607,7 @@ def run_learned(args):
     while done < args.train_steps:
         k = min(chunk, args.train_steps - done)
         lr = args.train_lr * (0.1 if done >= 0.8 * args.train_steps else 1.0)
-        losses.append(codec.train(dcube, k, args.train_batch, lr, seed=1000 + done))
+        losses.append(codec.train(dcube, k, args.train_batch, lr, seed=1000 + done, active_frac=args.active_frac))
         done += k
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
@@ -673,7 +675,7 @@ def run_learned(args):
                        "(28 -> 64 -> 64 -> 1, SiLU), bricks decoded on the tensor cores into the device cache",
                        "device_budget_gib": args.budget_gib or "every brick",
                        "train": {"steps": args.train_steps, "batch": args.train_batch, "lr": args.train_lr,
-                                 "floor": floor}},
+                                 "floor": floor, "active_frac": args.active_frac}},
             "fps": frames / (ms * 1e-3),
             "learned": {"psnr_db_vs_plain": psnr, "max_abs_vs_plain": maxerr, "psnr_poses": len(psnr_poses),
                         "train_s": train_s, "loss_trace": losses,

@@ -458,12 +458,13 @@ int32_t vr_codec_brick_count(const vr_codec* codec);
 void vr_codec_brick_size(const vr_codec* codec, int32_t B[3]);
 
 /* `steps` Adam steps (lr; betas 0.9, 0.999; eps 1e-8) on `batch` voxels drawn per
- * step (uniform brick, uniform voxel of its block clipped to the cube; counter-
- * based generator seeded by seed) from the device cube, targets max(value,
- * floor_v) of vr_codec_fit_stats; *last_loss = the last step's loss.
- * Errors: as forward. */
+ * step from the device cube (counter-based generator seeded by seed): with
+ * probability active_frac a voxel above floor_v (listed by vr_codec_fit_stats,
+ * cubes of up to 2^32 voxels) in the brick that owns it, otherwise a uniform
+ * brick and a uniform voxel of its block clipped to the cube; targets
+ * max(value, floor_v); *last_loss = the last step's loss.  Errors: as forward. */
 int vr_codec_train(vr_codec* codec, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps,
-                   int32_t batch, float lr, uint64_t seed, double* last_loss);
+                   int32_t batch, float lr, float active_frac, uint64_t seed, double* last_loss);
 
 /* Decode the blocks of n bricks (device list of valid brick indices) into device
  * memory: brick k's V = (bx+1)(by+1)(bz+1) values (x fastest) go to out + k V, or

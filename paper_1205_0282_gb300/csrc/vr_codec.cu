@@ -566,19 +566,58 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 // Training points: uniform brick, uniform voxel of its (B+1)^3 block clipped to
 // the cube; target = the cube's value there.
 __global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, int64_t n_points,
-                              uint64_t seed, float floor_v, float4* __restrict__ pts, float* __restrict__ tgt) {
+                              uint64_t seed, float floor_v, const uint32_t* __restrict__ active, uint64_t n_active,
+                              float active_frac, float4* __restrict__ pts, float* __restrict__ tgt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_points) return;
-    const uint64_t r0 = mix64(seed ^ (uint64_t)(2 * i)), r1 = mix64(seed ^ (uint64_t)(2 * i + 1));
-    const int nbt = nb.x * nb.y * nb.z;
-    const int b = (int)(r0 % (uint64_t)nbt);
-    const int bx = b % nb.x, by = (b / nb.x) % nb.y, bz = b / (nb.x * nb.y);
-    const int ux = (int)((r1 & 0xFFFFF) % (uint64_t)(B.x + 1));
-    const int uy = (int)(((r1 >> 20) & 0xFFFFF) % (uint64_t)(B.y + 1));
-    const int uz = (int)(((r1 >> 40) & 0xFFFFF) % (uint64_t)(B.z + 1));
-    const int gx = min(bx * B.x + ux, n.x - 1), gy = min(by * B.y + uy, n.y - 1), gz = min(bz * B.z + uz, n.z - 1);
+    const uint64_t r0 = mix64(seed ^ (uint64_t)(3 * i)), r1 = mix64(seed ^ (uint64_t)(3 * i + 1));
+    const uint64_t r2 = mix64(seed ^ (uint64_t)(3 * i + 2));
+    int b, gx, gy, gz, bx, by, bz;
+    if (n_active > 0 && (float)(r2 >> 40) * (1.0f / 16777216.0f) < active_frac) {
+        // a voxel the transfer function can show, in the brick that owns it
+        const uint64_t v = active[r0 % n_active];
+        gx = (int)(v % (uint64_t)n.x);
+        gy = (int)((v / (uint64_t)n.x) % (uint64_t)n.y);
+        gz = (int)(v / ((uint64_t)n.x * (uint64_t)n.y));
+        bx = min(gx / B.x, nb.x - 1);
+        by = min(gy / B.y, nb.y - 1);
+        bz = min(gz / B.z, nb.z - 1);
+        b = (bz * nb.y + by) * nb.x + bx;
+    } else {
+        const int nbt = nb.x * nb.y * nb.z;
+        b = (int)(r0 % (uint64_t)nbt);
+        bx = b % nb.x;
+        by = (b / nb.x) % nb.y;
+        bz = b / (nb.x * nb.y);
+        const int ux = (int)((r1 & 0xFFFFF) % (uint64_t)(B.x + 1));
+        const int uy = (int)(((r1 >> 20) & 0xFFFFF) % (uint64_t)(B.y + 1));
+        const int uz = (int)(((r1 >> 40) & 0xFFFFF) % (uint64_t)(B.z + 1));
+        gx = min(bx * B.x + ux, n.x - 1);
+        gy = min(by * B.y + uy, n.y - 1);
+        gz = min(bz * B.z + uz, n.z - 1);
+    }
     pts[i] = make_float4((float)(gx - bx * B.x), (float)(gy - by * B.y), (float)(gz - bz * B.z), __int_as_float(b));
     tgt[i] = fmaxf(cube[((int64_t)gz * n.y + gy) * n.x + gx], floor_v);
+}
+
+// Voxels above the floor (the ones the transfer function can show): count, then
+// list (global linear indices; order unspecified).
+__global__ void active_kernel(const float* __restrict__ cube, int64_t n, float floor_v, unsigned long long* count,
+                              uint32_t* __restrict__ list, unsigned long long cap) {
+    // every warp runs the same number of iterations (the ballot needs all its lanes)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_round = (n + stride - 1) / stride * stride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_round; i += stride) {
+        const bool a = i < n && cube[i] > floor_v;
+        const unsigned mask = __ballot_sync(0xffffffffu, a);
+        unsigned long long base = 0;
+        if ((threadIdx.x & 31) == 0 && mask) base = atomicAdd(count, (unsigned long long)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (list && a) {
+            const unsigned long long k = base + __popc(mask & ((1u << (threadIdx.x & 31)) - 1u));
+            if (k < cap) list[k] = (uint32_t)i;
+        }
+    }
 }
 
 // Per-brick offset and scale: mean and standard deviation (at least 1e-3) over
@@ -648,6 +687,9 @@ struct vr_codec {
     float* s = nullptr;
     float2* minmax = nullptr;  // per-brick range of the data the codec was fitted to
     float floor_v = -FLT_MAX;  // training targets are max(value, floor_v)
+    uint32_t* active = nullptr;  // voxels above the floor (global linear indices)
+    uint64_t n_active = 0;
+    unsigned long long* d_count = nullptr;
     double* loss = nullptr;
     int* err = nullptr;
     float4* pts = nullptr;
@@ -790,7 +832,7 @@ void vr_codec_destroy(vr_codec* c) {
     if (!c) return;
     for (void* p : {(void*)c->theta, (void*)c->grad, (void*)c->adam1, (void*)c->adam2, (void*)c->W1h, (void*)c->W2h,
                     (void*)c->lath, (void*)c->w3r, (void*)c->m, (void*)c->s, (void*)c->minmax, (void*)c->loss,
-                    (void*)c->err,
+                    (void*)c->err, (void*)c->active, (void*)c->d_count,
                     (void*)c->pts, (void*)c->tgt})
         cudaFree(p);
     delete c;
@@ -869,6 +911,25 @@ int vr_codec_fit_stats(vr_codec* c, const float* cube, int64_t nx, int64_t ny, i
     c->floor_v = floor_v;
     brick_stats_kernel<<<c->n_bricks, 256>>>(cube, n, B, nb, floor_v, c->m, c->s, c->minmax);
     CODEC_CUDA(cudaGetLastError());
+    // the voxels above the floor, for importance sampling in training
+    cudaFree(c->active);
+    c->active = nullptr;
+    c->n_active = 0;
+    if (!c->d_count) CODEC_CUDA(cudaMalloc(&c->d_count, sizeof(unsigned long long)));
+    const int64_t nv = nx * ny * nz;
+    unsigned long long cnt = 0;
+    CODEC_CUDA(cudaMemset(c->d_count, 0, sizeof(cnt)));
+    active_kernel<<<4096, 256>>>(cube, nv, floor_v, c->d_count, nullptr, 0);
+    CODEC_CUDA(cudaMemcpy(&cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
+    if (cnt > 0 && nv <= 0xFFFFFFFFll) {
+        if (cudaMalloc(&c->active, cnt * sizeof(uint32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return VR_ENOMEM;
+        }
+        CODEC_CUDA(cudaMemset(c->d_count, 0, sizeof(cnt)));
+        active_kernel<<<4096, 256>>>(cube, nv, floor_v, c->d_count, c->active, cnt);
+        c->n_active = cnt;
+    }
     return codec_cuda(cudaDeviceSynchronize());
 }
 
@@ -878,7 +939,7 @@ int vr_codec_get_minmax(vr_codec* c, float* out) {
 }
 
 int vr_codec_train(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps, int32_t batch,
-                   float lr, uint64_t seed, double* last_loss) {
+                   float lr, float active_frac, uint64_t seed, double* last_loss) {
     using namespace vr::codec;
     if (!c || !cube || steps < 0 || batch < 1) return VR_EINVAL;
     const int3 n = make_int3((int)nx, (int)ny, (int)nz), B = make_int3(c->B[0], c->B[1], c->B[2]);
@@ -887,8 +948,8 @@ int vr_codec_train(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64
     int rc = grow_points(c, batch);
     if (rc) return rc;
     for (int32_t it = 0; it < steps; ++it) {
-        sample_kernel<<<(batch + 255) / 256, 256>>>(cube, n, B, nb, batch, mix64_host(seed, it), c->floor_v, c->pts,
-                                                    c->tgt);
+        sample_kernel<<<(batch + 255) / 256, 256>>>(cube, n, B, nb, batch, mix64_host(seed, it), c->floor_v,
+                                                    c->active, c->n_active, active_frac, c->pts, c->tgt);
         CODEC_CUDA(cudaMemsetAsync(c->grad, 0, (size_t)c->n_params * 4));
         CODEC_CUDA(cudaMemsetAsync(c->loss, 0, sizeof(double)));
         if ((rc = launch_codec<true>(c, c->pts, Grid{}, c->tgt, batch, nullptr, 0))) return rc;

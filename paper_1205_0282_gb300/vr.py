@@ -137,7 +137,7 @@ def _load():
     lib.vr_codec_brick_size.argtypes = [P, P]
     lib.vr_codec_brick_size.restype = None
     lib.vr_load_cube_codec.argtypes = [P, P, I64, I64, I64]
-    lib.vr_codec_train.argtypes = [P, P, I64, I64, I64, I32, I32, ctypes.c_float, ctypes.c_uint64,
+    lib.vr_codec_train.argtypes = [P, P, I64, I64, I64, I32, I32, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_double)]
     lib.vr_codec_decode_bricks.argtypes = [P, P, P, I32, P, P]
     lib.vr_render_noalloc.argtypes = [P, I64, I64, I64, I32, I32, I32, P, I32,
@@ -531,11 +531,11 @@ class Codec:
         self._rc(_lib.vr_codec_get_minmax(self.h, out.ctypes.data), "vr_codec_get_minmax")
         return out
 
-    def train(self, cube_dev, steps: int, batch: int, lr: float, seed: int = 1) -> float:
+    def train(self, cube_dev, steps: int, batch: int, lr: float, seed: int = 1, active_frac: float = 0.0) -> float:
         nz, ny, nx = cube_dev.shape
         loss = ctypes.c_double()
         self._rc(_lib.vr_codec_train(self.h, cube_dev.data_ptr(), nx, ny, nz, int(steps), int(batch), float(lr),
-                                     int(seed), ctypes.byref(loss)), "vr_codec_train")
+                                     float(active_frac), int(seed), ctypes.byref(loss)), "vr_codec_train")
         return loss.value
 
     def decode_bricks(self, bricks_dev, out_dev, slots_dev=None, stream=None):
