@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--train-batch", type=int, default=262144)
     ap.add_argument("--train-lr", type=float, default=3e-3)
     ap.add_argument("--psnr-poses", type=int, default=12)
+    ap.add_argument("--codec-brick", type=int, default=0,
+                    help="--learned: brick edge of the codec and of the learned render (0: the workload's)")
     ap.add_argument("--active-frac", type=float, default=0.5,
                     help="--learned: share of training points drawn from voxels the transfer function can show")
     ap.add_argument("--e2e-steps", type=int, default=120)
@@ -570,13 +572,14 @@ def run_learned(args):
     torch.cuda.set_device(0)
     spec, tf, poses, desc = workload(args)
     cube = make_cube(spec)
-    shape, brick = spec["shape_xyz"], spec["brick"]
+    shape = spec["shape_xyz"]
+    brick = (args.codec_brick,) * 3 if args.codec_brick else spec["brick"]
     nb = int(np.prod([(n - 1 + b - 1) // b for n, b in zip(shape, brick)]))
     dcube = torch.from_numpy(cube).cuda()
     W, H = spec["width"], spec["height"]
     q = max(1, len(poses) // args.psnr_poses)
     psnr_poses = poses[::q][:args.psnr_poses]
-    # plain reference images (in-core, FP32 texture path)
+    # plain reference images (in-core, FP32 texture path, the same bricking)
     plain = []
     with vrm.VolumeRenderer(0) as r:
         r.load_cube(dcube)
@@ -671,7 +674,8 @@ def run_learned(args):
     line = {"metric": METRIC, "value": st["samples"] / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / frames, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (decoder bf16 x bf16 -> f32)", "data": "synthetic",
-            "config": {"workload": desc, "form": "learned: 8^3 x 16 BF16 latents per brick + shared MLP "
+            "config": {"workload": desc, "codec_brick": list(brick),
+                       "form": "learned: 8^3 x 16 BF16 latents per brick + shared MLP "
                        "(28 -> 64 -> 64 -> 1, SiLU), bricks decoded on the tensor cores into the device cache",
                        "device_budget_gib": args.budget_gib or "every brick",
                        "train": {"steps": args.train_steps, "batch": args.train_batch, "lr": args.train_lr,
