@@ -461,7 +461,9 @@ void vr_codec_brick_size(const vr_codec* codec, int32_t B[3]);
  * step from the device cube (counter-based generator seeded by seed): with
  * probability active_frac a voxel above floor_v (listed by vr_codec_fit_stats,
  * cubes of up to 2^32 voxels) in the brick that owns it, otherwise a uniform
- * brick and a uniform voxel of its block clipped to the cube; targets
+ * brick among those holding values above floor_v (all bricks when the floor is
+ * -FLT_MAX; the others render empty) and a uniform voxel of its block clipped to
+ * the cube; targets
  * max(value, floor_v); *last_loss = the last step's loss.  Errors: as forward. */
 int vr_codec_train(vr_codec* codec, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps,
                    int32_t batch, float lr, float active_frac, uint64_t seed, double* last_loss);

@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cfloat>
 #include <cstring>
+#include <vector>
 
 #include "../../include/vr.h"
 #include "tc.cuh"
@@ -567,7 +568,8 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 // the cube; target = the cube's value there.
 __global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, int64_t n_points,
                               uint64_t seed, float floor_v, const uint32_t* __restrict__ active, uint64_t n_active,
-                              float active_frac, float4* __restrict__ pts, float* __restrict__ tgt) {
+                              float active_frac, const int32_t* __restrict__ shown, int32_t n_shown,
+                              float4* __restrict__ pts, float* __restrict__ tgt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_points) return;
     const uint64_t r0 = mix64(seed ^ (uint64_t)(3 * i)), r1 = mix64(seed ^ (uint64_t)(3 * i + 1));
@@ -584,8 +586,10 @@ __global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, in
         bz = min(gz / B.z, nb.z - 1);
         b = (bz * nb.y + by) * nb.x + bx;
     } else {
+        // a uniform brick among those the transfer function can show (all bricks
+        // when none is listed), then a uniform voxel of its block
         const int nbt = nb.x * nb.y * nb.z;
-        b = (int)(r0 % (uint64_t)nbt);
+        b = n_shown > 0 ? shown[r0 % (uint64_t)n_shown] : (int)(r0 % (uint64_t)nbt);
         bx = b % nb.x;
         by = (b / nb.x) % nb.y;
         bz = b / (nb.x * nb.y);
@@ -689,6 +693,8 @@ struct vr_codec {
     float floor_v = -FLT_MAX;  // training targets are max(value, floor_v)
     uint32_t* active = nullptr;  // voxels above the floor (global linear indices)
     uint64_t n_active = 0;
+    int32_t* shown = nullptr;    // bricks with values above the floor (the others render empty)
+    int32_t n_shown = 0;
     unsigned long long* d_count = nullptr;
     double* loss = nullptr;
     int* err = nullptr;
@@ -832,7 +838,7 @@ void vr_codec_destroy(vr_codec* c) {
     if (!c) return;
     for (void* p : {(void*)c->theta, (void*)c->grad, (void*)c->adam1, (void*)c->adam2, (void*)c->W1h, (void*)c->W2h,
                     (void*)c->lath, (void*)c->w3r, (void*)c->m, (void*)c->s, (void*)c->minmax, (void*)c->loss,
-                    (void*)c->err, (void*)c->active, (void*)c->d_count,
+                    (void*)c->err, (void*)c->active, (void*)c->d_count, (void*)c->shown,
                     (void*)c->pts, (void*)c->tgt})
         cudaFree(p);
     delete c;
@@ -911,6 +917,24 @@ int vr_codec_fit_stats(vr_codec* c, const float* cube, int64_t nx, int64_t ny, i
     c->floor_v = floor_v;
     brick_stats_kernel<<<c->n_bricks, 256>>>(cube, n, B, nb, floor_v, c->m, c->s, c->minmax);
     CODEC_CUDA(cudaGetLastError());
+    // the bricks with values above the floor: training samples only those (the
+    // others are skipped by the renderer's empty-space test whenever the transfer
+    // function is transparent up to the floor)
+    {
+        std::vector<float2> mm(c->n_bricks);
+        CODEC_CUDA(cudaMemcpy(mm.data(), c->minmax, (size_t)c->n_bricks * 8, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> shown;
+        for (int32_t b = 0; b < c->n_bricks; ++b)
+            if (mm[b].y > floor_v) shown.push_back(b);
+        cudaFree(c->shown);
+        c->shown = nullptr;
+        c->n_shown = 0;
+        if (!shown.empty() && floor_v > -FLT_MAX) {
+            CODEC_CUDA(cudaMalloc(&c->shown, shown.size() * sizeof(int32_t)));
+            CODEC_CUDA(cudaMemcpy(c->shown, shown.data(), shown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            c->n_shown = (int32_t)shown.size();
+        }
+    }
     // the voxels above the floor, for importance sampling in training
     cudaFree(c->active);
     c->active = nullptr;
@@ -949,7 +973,8 @@ int vr_codec_train(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64
     if (rc) return rc;
     for (int32_t it = 0; it < steps; ++it) {
         sample_kernel<<<(batch + 255) / 256, 256>>>(cube, n, B, nb, batch, mix64_host(seed, it), c->floor_v,
-                                                    c->active, c->n_active, active_frac, c->pts, c->tgt);
+                                                    c->active, c->n_active, active_frac, c->shown, c->n_shown,
+                                                    c->pts, c->tgt);
         CODEC_CUDA(cudaMemsetAsync(c->grad, 0, (size_t)c->n_params * 4));
         CODEC_CUDA(cudaMemsetAsync(c->loss, 0, sizeof(double)));
         if ((rc = launch_codec<true>(c, c->pts, Grid{}, c->tgt, batch, nullptr, 0))) return rc;
