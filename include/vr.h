@@ -144,6 +144,15 @@ typedef struct {
                                 once its previous bricks are marched, while the other
                                 S - 2H slots stay resident.  Needs room for 2 bricks.
                                 Takes effect at the next vr_brick. */
+#define VR_OPT_STEP_MODE 7   /* 0 (default): samples every cam.step voxels along each ray;
+                                1: dynamic step (Section 2.3.2: discrete ray casting, at
+                                least one sample per voxel crossed along the ray's
+                                dominant axis): a ray with unit direction d samples every
+                                cam.step / max_a |d_a| voxels, i.e. every cam.step voxels
+                                along its dominant axis, the opacity correction using that
+                                spacing.  The lattice stays anchored at the ray's entry.
+                                Rendered by the texture or the direct march (VR_KERNEL_TMA
+                                with it: VR_EINVAL at render time). */
 #define VR_PRECISION_F32 0
 #define VR_PRECISION_F16 1
 #define VR_PRECISION_F8 2

@@ -63,7 +63,7 @@ def _load():
             I64 = ctypes.c_int64
             lib.orc_render.argtypes = [P, I64, I64, I64, P, ctypes.c_int32,
                                        ctypes.POINTER(OrcCamera), I64, I64, I64, ctypes.c_int32,
-                                       P, I64, P, P, P, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int32, P, I64, P, P, P, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int32]
             lib.orc_render.restype = ctypes.c_int
             lib.orc_render_regions.argtypes = [P, I64, I64, I64, P, ctypes.c_int32,
@@ -104,7 +104,7 @@ def _nbricks(shape_xyz, brick):
 
 def render(cube: np.ndarray, tf: np.ndarray, cam: dict, brick=None, mode: str = "ea",
            pixels=None, amb_alpha: float = 1e-5, amb_steps: float = 1e-4, threads: int = 0,
-           regions=None):
+           regions=None, step_mode: int = 0):
     """Render with the FP64 oracle.
 
     cube: float32[nz][ny][nx].  brick: (bx, by, bz) or None for monolithic.
@@ -112,6 +112,8 @@ def render(cube: np.ndarray, tf: np.ndarray, cam: dict, brick=None, mode: str = 
     regions: None, or the region of every brick (brick id = ix + nbx*(iy + nby*iz);
     -1 = not rendered) for the two-level sort-last fold (needs a bricking and
     emission-absorption mode).
+    step_mode: 0 fixed step; 1 dynamic step (samples cam["step"] voxels apart along
+    each ray's dominant axis; not with regions).
     Returns (rgba, ambiguous_flags, samples): rgba is float64 (H, W, 4) for the
     whole image or (npix, 4) for a pixel list, premultiplied.
     """
@@ -133,7 +135,7 @@ def render(cube: np.ndarray, tf: np.ndarray, cam: dict, brick=None, mode: str = 
     m = {"ea": 0, "mip": 1}[mode]
     oc = _cam(cam)
     if regions is not None:
-        if brick is None or mode != "ea":
+        if brick is None or mode != "ea" or step_mode:
             raise ValueError("regions need a bricking and emission-absorption mode")
         reg = np.ascontiguousarray(regions, dtype=np.int32).reshape(-1)
         rc = _load().orc_render_regions(cube.ctypes.data, nx, ny, nz, tfa.ctypes.data, len(tfa),
@@ -142,7 +144,7 @@ def render(cube: np.ndarray, tf: np.ndarray, cam: dict, brick=None, mode: str = 
                                         samples.ctypes.data, amb_alpha, amb_steps, threads)
     else:
         rc = _load().orc_render(cube.ctypes.data, nx, ny, nz, tfa.ctypes.data, len(tfa),
-                                ctypes.byref(oc), bx, by, bz, m, pix_ptr, npix, out.ctypes.data,
+                                ctypes.byref(oc), bx, by, bz, m, int(step_mode), pix_ptr, npix, out.ctypes.data,
                                 amb.ctypes.data, samples.ctypes.data, amb_alpha, amb_steps, threads)
     if rc != 0:
         raise ValueError("oracle rejected its arguments")

@@ -178,6 +178,7 @@ typedef struct {
     int mode;
     double amb_alpha, amb_steps;
     const int32_t* region; /* NULL, or the region of each brick (-1: not rendered) */
+    int step_mode;         /* 0: fixed step; 1: dynamic step (see render_pixel) */
 } job_t;
 
 static int64_t owner_of(const job_t* J, const double p[3]) {
@@ -229,7 +230,12 @@ static void render_pixel(const job_t* J, int i, int j, double out[4], int* amb_o
     if (!slab(cam->eye, d, lo, hi, &tn, &tf)) goto done;
     double t0 = tn > 0.0 ? tn : 0.0, t1 = tf;
     if (!(t1 > t0)) goto done;
-    const double L = t1 - t0, dt = cam->step, tau = cam->term_alpha;
+    /* Dynamic step (Section 2.3.2, discrete ray casting with at least one sample
+     * per voxel crossed): successive samples are cam->step voxels apart along the
+     * ray's dominant axis, i.e. cam->step / max_a |d_a| apart along the ray. */
+    double dmax = 0.0;
+    for (int a = 0; a < 3; ++a) dmax = fabs(d[a]) > dmax ? fabs(d[a]) : dmax;
+    const double L = t1 - t0, dt = J->step_mode ? cam->step / dmax : cam->step, tau = cam->term_alpha;
     {
         double x = L / dt;
         if (fabs(x - nearbyint(x)) < J->amb_steps) amb |= ORC_AMB_STEPS;
@@ -383,6 +389,7 @@ static void setup_job(job_t* J, const cube_t* cube, const double* tf, int ntf,
     J->amb_alpha = amb_alpha;
     J->amb_steps = amb_steps;
     J->region = NULL;
+    J->step_mode = 0;
 }
 
 /*
@@ -393,7 +400,7 @@ static void setup_job(job_t* J, const cube_t* cube, const double* tf, int ntf,
  */
 int orc_render(const float* cube_data, int64_t nx, int64_t ny, int64_t nz,
                const double* tf, int32_t ntf, const orc_camera* cam,
-               int64_t bx, int64_t by, int64_t bz, int32_t mode,
+               int64_t bx, int64_t by, int64_t bz, int32_t mode, int32_t step_mode,
                const int64_t* pixels, int64_t npix,
                double* out_rgba, uint8_t* ambiguous, int64_t* samples,
                double amb_alpha, double amb_steps, int32_t nthreads) {
@@ -403,6 +410,7 @@ int orc_render(const float* cube_data, int64_t nx, int64_t ny, int64_t nz,
     int64_t brick[3] = {bx, by, bz};
     job_t J;
     setup_job(&J, &cube, tf, ntf, cam, brick, mode, amb_alpha, amb_steps);
+    J.step_mode = step_mode;
     const int64_t W = cam->width;
     const int64_t total = pixels ? npix : W * cam->height;
 #ifdef _OPENMP

@@ -14,7 +14,7 @@ _EXPORTED = ("VolumeRenderer", "VRError", "VR_OPT_MODE", "VR_OPT_RECT_CULL", "VR
              "vr_kd_partition", "vr_kd_order", "vr_set_region", "vr_region_rect", "vr_plan_region_rect",
              "vr_render_rect", "vr_composite_subimages", "vr_load_cube_host", "VR_OPT_DEVICE_BUDGET",
              "Server", "vr_server_create", "vr_server_submit", "vr_server_wait", "vr_server_get_stats",
-             "vr_server_destroy", "Codec", "vr_load_cube_codec")
+             "vr_server_destroy", "Codec", "vr_load_cube_codec", "VR_OPT_STEP_MODE")
 
 __all__ = list(_EXPORTED)
 

@@ -230,6 +230,7 @@ struct vr_ctx {
 
     bool skip_empty = true, rect_cull = true;
     int mode = 0;
+    int step_mode = 0;  // VR_OPT_STEP_MODE
     int kernel = VR_KERNEL_AUTO;
     int tex_fits = -1;  // -1 unknown, 0/1: the cube fits the layered-texture limits
 

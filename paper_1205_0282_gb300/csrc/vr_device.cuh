@@ -14,9 +14,12 @@ namespace vr {
 // sample count n = #{k >= 0 : k dt < t1 - t0}.  Returns false if the ray misses
 // the domain [0, n-1]^3.
 // Cam: FrameParams (one frame) or FrameCam (a frame of a batch): eye, f, r, u, qx, qy.
-template <class Cam>
+// dt: the ray's sample spacing, p.dt, or with the dynamic step (p.step_mode 1,
+// Section 2.3.2's discrete ray casting) p.dt / max_a |d_a|, so that successive
+// samples are p.dt voxels apart along the ray's dominant axis.
+template <bool DYN = false, class Cam = FrameParams>
 __device__ __forceinline__ bool setup_ray(const FrameParams& p, const Cam& cam, int i, int j, df d[3], df pe[3],
-                                          int& n_samples) {
+                                          int& n_samples, df& dt) {
     const df qx = cam.qx[i], qy = cam.qy[j];
     df dun[3];
     for (int a = 0; a < 3; ++a) dun[a] = df_add(df_add(cam.f[a], df_mul(qx, cam.r[a])), df_mul(qy, cam.u[a]));
@@ -39,22 +42,32 @@ __device__ __forceinline__ bool setup_ray(const FrameParams& p, const Cam& cam, 
     const df t0 = df_max(tn, df_make(0.0f));
     if (!df_gt(tf, t0)) return false;
     const df L = df_sub(tf, t0);
-    n_samples = (int)df_ceil(df_div(L, p.dt));
+    dt = p.dt;
+    if (DYN) {
+        // |d| along the dominant axis (selects, no indexed access)
+        df dm = d[0];
+        if (fabsf(d[1].hi) > fabsf(dm.hi)) dm = d[1];
+        if (fabsf(d[2].hi) > fabsf(dm.hi)) dm = d[2];
+        dt = df_div(p.dt, dm.hi < 0.0f ? df_neg(dm) : dm);
+    }
+    n_samples = (int)df_ceil(df_div(L, dt));
     for (int a = 0; a < 3; ++a) pe[a] = df_add(cam.eye[a], df_mul(t0, d[a]));
     return n_samples > 0;
 }
 
-__device__ __forceinline__ bool setup_ray(const FrameParams& p, int i, int j, df d[3], df pe[3], int& n_samples) {
-    return setup_ray(p, p, i, j, d, pe, n_samples);
+template <bool DYN = false>
+__device__ __forceinline__ bool setup_ray(const FrameParams& p, int i, int j, df d[3], df pe[3], int& n_samples,
+                                          df& dt) {
+    return setup_ray<DYN>(p, p, i, j, d, pe, n_samples, dt);
 }
 
 // Sample range [klo, khi) owned by brick bidx (sample p_k = pe + k dt d belongs to
 // brick floor(p/B) per axis, first and last bricks open towards the outside).
 __device__ __forceinline__ void brick_range(const FrameParams& p, const int bidx[3], const df d[3], const df pe[3],
-                            int n_samples, int& klo, int& khi) {
+                            int n_samples, const df& dt, int& klo, int& khi) {
     float lo = 0.0f, hi = (float)n_samples;
     for (int a = 0; a < 3; ++a) {
-        const df D = df_mul(p.dt, d[a]);
+        const df D = df_mul(dt, d[a]);
         const float O = (float)(bidx[a] * p.B[a]);
         const float OB = (float)(bidx[a] * p.B[a] + p.B[a]);
         if (bidx[a] > 0) {
@@ -119,6 +132,11 @@ __device__ __forceinline__ float4 tf_lookup(const FrameParams& p, const float4* 
 // alpha = 1 - (1 - a)^dt as a * Q(t): a short polynomial for small a (noise, the
 // common case), a long one up to alpha_split (both accurate to ~1e-10 in Q and
 // exactly 0 at a = 0), the exponential form above.
+// Opacity correction for a per-ray step of dt voxels (the dynamic step).
+__device__ __forceinline__ float opacity_correct_dt(float a, float dt) {
+    return a >= 1.0f ? 1.0f : 1.0f - exp2f(dt * __log2f(1.0f - a));
+}
+
 __device__ __forceinline__ float opacity_correct(const FrameParams& p, float a) {
     if (a <= p.small_split) {
         const float t = fmaf(a, p.small_scale, -1.0f);

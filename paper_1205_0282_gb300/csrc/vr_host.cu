@@ -68,7 +68,7 @@ bool use_tex(vr_ctx* c) {
     return !c->ooc && c->mode == 0 && (c->kernel == VR_KERNEL_TEX || (c->kernel == VR_KERNEL_AUTO && tex_fits(c)));
 }
 bool use_tma(vr_ctx* c) {
-    return !c->ooc && c->mode == 0 && (c->kernel == VR_KERNEL_TMA || (c->kernel == VR_KERNEL_AUTO && !tex_fits(c)));
+    return !c->ooc && c->mode == 0 && c->step_mode == 0 && (c->kernel == VR_KERNEL_TMA || (c->kernel == VR_KERNEL_AUTO && !tex_fits(c)));
 }
 
 void free_ooc(vr_ctx* c) {
@@ -682,6 +682,10 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
             c->kernel = (int)value;
             return VR_OK;
         case VR_OPT_DEVICE_BUDGET: c->budget = value; return VR_OK;
+        case VR_OPT_STEP_MODE:
+            if (value != 0 && value != 1) return fail(c, VR_EINVAL, "step mode must be 0 or 1");
+            c->step_mode = (int)value;
+            return VR_OK;
         case VR_OPT_PRECISION:
             if (value != VR_PRECISION_F32 && value != VR_PRECISION_F16 && value != VR_PRECISION_F8)
                 return fail(c, VR_EINVAL, "unknown precision");
@@ -712,6 +716,7 @@ void fill_common_params(vr_ctx* c, vr::FrameParams& p) {
     }
     p.dt = vr::df_from_double(c->cam.step);
     p.dt_f = (float)c->cam.step;
+    p.step_mode = c->step_mode;
     p.tau = (float)c->cam.term_alpha;
     p.cube = c->d_cube;
     p.stride_y = c->nx_pad;
@@ -866,6 +871,8 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     auto t0 = std::chrono::steady_clock::now();
     int32_t tiles_x, tiles_y, T;
     int64_t n_items;
+    if (c->step_mode && c->kernel == VR_KERNEL_TMA)
+        return fail(c, VR_EINVAL, "the dynamic step needs the texture or the direct march");
     if (c->precision != VR_PRECISION_F32 && !use_tex(c))
         return fail(c, VR_EINVAL, "FP16/FP8 storage needs the texture march (emission-absorption mode, "
                                   "VR_KERNEL_TEX or VR_KERNEL_AUTO on a cube within the texture limits)");

@@ -68,7 +68,7 @@ cudaError_t launch_brick_minmax(const float* cube, int64_t pitch, const int32_t 
 }
 
 // Off: type of brick-local voxel offsets (uint32_t when (B+1) * nx * ny < 2^32).
-template <bool UNIFORM, int MODE, typename Off>
+template <bool UNIFORM, int MODE, typename Off, bool DYN>
 __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p) {
     __shared__ TfShared s_tf;
     for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
@@ -89,18 +89,19 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float vmax = -FLT_MAX;
     int taken = 0;
-    df d[3], pe[3];
+    df d[3], pe[3], dt;
     int n_samples = 0;
-    if (i < p.width && j < p.height && setup_ray(p, i, j, d, pe, n_samples)) {
+    if (i < p.width && j < p.height && setup_ray<DYN>(p, i, j, d, pe, n_samples, dt)) {
         int klo, khi;
-        brick_range(p, bidx, d, pe, n_samples, klo, khi);
+        brick_range(p, bidx, d, pe, n_samples, dt, klo, khi);
+        const float dt_ray = df_to_float(dt);
         if (khi > klo) {
             int O[3], imax[3];
             float qs[3], dq[3];
             for (int a = 0; a < 3; ++a) {
                 O[a] = bidx[a] * p.B[a];
                 imax[a] = min(p.B[a] - 1, p.n[a] - 2 - O[a]);
-                const df D = df_mul(p.dt, d[a]);
+                const df D = df_mul(dt, d[a]);
                 qs[a] = df_to_float(df_add_f(df_add(pe[a], df_mul_f(D, (float)klo)), -(float)O[a]));
                 dq[a] = df_to_float(D);
             }
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
                     continue;
                 }
                 const float4 col = tf_lookup<UNIFORM>(p, s_tf.rgba, s_tf.v, v);
-                const float alpha = opacity_correct(p, col.w);
+                const float alpha = DYN ? opacity_correct_dt(col.w, dt_ray) : opacity_correct(p, col.w);
                 const float w = (1.0f - acc.w) * alpha;
                 acc.x = fmaf(w, col.x, acc.x);
                 acc.y = fmaf(w, col.y, acc.y);
@@ -165,22 +166,31 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
     if ((threadIdx.x & 31) == 0 && t) atomicAdd(&p.stats->samples, t);
 }
 
-template <bool UNIFORM, int MODE>
+template <bool UNIFORM, int MODE, bool DYN>
 static void launch_march_t(const FrameParams& p, cudaStream_t s) {
     if (p.offsets32)
-        march_kernel<UNIFORM, MODE, uint32_t><<<p.n_items, kTilePixels, 0, s>>>(p);
+        march_kernel<UNIFORM, MODE, uint32_t, DYN><<<p.n_items, kTilePixels, 0, s>>>(p);
     else
-        march_kernel<UNIFORM, MODE, int64_t><<<p.n_items, kTilePixels, 0, s>>>(p);
+        march_kernel<UNIFORM, MODE, int64_t, DYN><<<p.n_items, kTilePixels, 0, s>>>(p);
 }
 
 cudaError_t launch_march(const FrameParams& p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
+    // (MIP needs no opacity correction: there the dynamic step only moves the samples)
     if (p.mode == 1) {
-        if (p.tf_uniform) launch_march_t<true, 1>(p, s);
-        else launch_march_t<false, 1>(p, s);
+        if (p.step_mode) {
+            if (p.tf_uniform) launch_march_t<true, 1, true>(p, s);
+            else launch_march_t<false, 1, true>(p, s);
+        } else {
+            if (p.tf_uniform) launch_march_t<true, 1, false>(p, s);
+            else launch_march_t<false, 1, false>(p, s);
+        }
+    } else if (p.step_mode) {
+        if (p.tf_uniform) launch_march_t<true, 0, true>(p, s);
+        else launch_march_t<false, 0, true>(p, s);
     } else {
-        if (p.tf_uniform) launch_march_t<true, 0>(p, s);
-        else launch_march_t<false, 0>(p, s);
+        if (p.tf_uniform) launch_march_t<true, 0, false>(p, s);
+        else launch_march_t<false, 0, false>(p, s);
     }
     return cudaGetLastError();
 }

@@ -23,8 +23,8 @@ namespace vr {
 namespace texm {
 
 // resident CTAs per SM the kernels are compiled for: 20 (48 registers a thread)
-// for FP32/FP16 storage, 18 (56 registers) for FP8, whose decode needs a few more
-constexpr int tex_blocks_per_sm(int prec) { return prec == kPrecF8 ? 18 : 20; }
+// for FP32/FP16 storage, 16 (64 registers) for FP8, whose decode needs a few more
+constexpr int tex_blocks_per_sm(int prec) { return prec == kPrecF8 ? 16 : 20; }
 
 // Layered texture of the sweep axis S: layer index = coordinate along S, texel
 // (x, y) = coordinates along (U, V) with U < V the two other axes.
@@ -97,7 +97,7 @@ __device__ __forceinline__ int step_of(const FrameParams& p, int a) {
     return a == 0 ? 1 : (a == 1 ? p.nb[0] : p.nb[0] * p.nb[1]);
 }
 
-template <int S, bool UNIFORM, int PREC, class Cam>
+template <int S, bool UNIFORM, int PREC, bool DYN, class Cam>
 __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam, const Item& item,
                                            const float4* s_rgba, const float* s_v) {
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
@@ -117,17 +117,19 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float fk = 0.0f, fn = 0.0f;
     float qs[3] = {0, 0, 0}, dq[3] = {0, 0, 0};
+    float dt_ray = 0.0f;  // dynamic step: this ray's spacing (voxels)
     {
-        df d[3], pe[3];
+        df d[3], pe[3], dt;
         int n_samples = 0;
-        if (i < cam.width && j < cam.height && setup_ray(p, cam, i, j, d, pe, n_samples)) {
+        if (i < cam.width && j < cam.height && setup_ray<DYN>(p, cam, i, j, d, pe, n_samples, dt)) {
             int klo, khi;
-            brick_range(p, bidx, d, pe, n_samples, klo, khi);
+            brick_range(p, bidx, d, pe, n_samples, dt, klo, khi);
+            if (DYN) dt_ray = df_to_float(dt);
             if (khi > klo) {
                 fn = (float)(khi - klo);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const df D = df_mul(p.dt, d[a]);
+                    const df D = df_mul(dt, d[a]);
                     qs[a] = df_to_float(df_add_f(df_add(pe[a], df_mul_f(D, (float)klo)), -(float)O[a]));
                     dq[a] = df_to_float(D);
                 }
@@ -221,7 +223,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         float val = fmaf(cur.fs, e1 - e0, e0);
         if (PREC == kPrecF8) val *= k0;
         const float4 col = tf_lookup<UNIFORM>(p, s_rgba, s_v, val);
-        const float alpha = opacity_correct(p, col.w);
+        const float alpha = DYN ? opacity_correct_dt(col.w, dt_ray) : opacity_correct(p, col.w);
         const float w = (1.0f - acc.w) * alpha;
         acc.x = fmaf(w, col.x, acc.x);
         acc.y = fmaf(w, col.y, acc.y);
@@ -238,7 +240,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
 
 // The transfer function lives in dynamic shared memory sized to the control points,
 // so that almost all of the SM's L1/shared array stays texture cache.
-template <bool UNIFORM, int PREC>
+template <bool UNIFORM, int PREC, bool DYN>
 __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_kernel(const FrameParams p) {
     extern __shared__ float4 s_dyn[];
     float4* s_rgba = s_dyn;
@@ -250,9 +252,9 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
     __syncthreads();
     const Item item = p.items[blockIdx.x];
     switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM, PREC>(p, p, item, s_rgba, s_v); break;
-        case 1: march_item<1, UNIFORM, PREC>(p, p, item, s_rgba, s_v); break;
-        default: march_item<2, UNIFORM, PREC>(p, p, item, s_rgba, s_v); break;
+        case 0: march_item<0, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_v); break;
+        case 1: march_item<1, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_v); break;
+        default: march_item<2, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_v); break;
     }
 }
 
@@ -271,9 +273,9 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
     const Item item = p.items[blockIdx.x];
     const FrameCam& cam = p.cams[item.sweep >> 3];
     switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM, PREC>(p, cam, item, s_rgba, s_v); break;
-        case 1: march_item<1, UNIFORM, PREC>(p, cam, item, s_rgba, s_v); break;
-        default: march_item<2, UNIFORM, PREC>(p, cam, item, s_rgba, s_v); break;
+        case 0: march_item<0, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_v); break;
+        case 1: march_item<1, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_v); break;
+        default: march_item<2, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_v); break;
     }
 }
 
@@ -399,12 +401,20 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
         }
         kern<<<p.n_items, kTilePixels, smem, s>>>(p);
     };
-    if (p.precision == kPrecF8) {
-        if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF8>);
-        else go(texm::march_tex_kernel<false, kPrecF8>);
+    if (p.step_mode) {  // the dynamic step (any storage; uniform or not)
+        if (p.precision == kPrecF8) {
+            if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF8, true>);
+            else go(texm::march_tex_kernel<false, kPrecF8, true>);
+        } else {
+            if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF32, true>);
+            else go(texm::march_tex_kernel<false, kPrecF32, true>);
+        }
+    } else if (p.precision == kPrecF8) {
+        if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF8, false>);
+        else go(texm::march_tex_kernel<false, kPrecF8, false>);
     } else {  // FP32 and FP16 textures share the kernel
-        if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF32>);
-        else go(texm::march_tex_kernel<false, kPrecF32>);
+        if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF32, false>);
+        else go(texm::march_tex_kernel<false, kPrecF32, false>);
     }
     return cudaGetLastError();
 }

@@ -164,14 +164,15 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
     {
         df d[3], pe[3];
         int n_samples = 0;
-        if (i < p.width && j < p.height && setup_ray(p, i, j, d, pe, n_samples)) {
+        df dt;
+        if (i < p.width && j < p.height && setup_ray(p, i, j, d, pe, n_samples, dt)) {
             int klo, khi;
-            brick_range(p, bidx, d, pe, n_samples, klo, khi);
+            brick_range(p, bidx, d, pe, n_samples, dt, klo, khi);
             nk = khi - klo;
             if (nk > 0) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const df D = df_mul(p.dt, d[a]);
+                    const df D = df_mul(dt, d[a]);
                     qs[a] = df_to_float(df_add_f(df_add(pe[a], df_mul_f(D, (float)klo)), -(float)O[a]));
                     dq[a] = df_to_float(D);
                 }

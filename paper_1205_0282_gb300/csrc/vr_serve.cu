@@ -334,8 +334,9 @@ int vr_server_create(vr_ctx* c, int64_t arena_bytes, int32_t max_batch, vr_serve
         return fail(c, VR_EINVAL, "arena of at least 64 MiB and 1 <= max_batch");
     if (!c->d_cube || !c->bricked || !c->tf_set || !c->cam_set)
         return fail(c, VR_ESTATE, "vr_server_create needs a loaded, bricked cube, a transfer function and a camera");
-    if (c->mode != 0 || !use_tex(c))
-        return fail(c, VR_EINVAL, "the serving loop renders emission-absorption frames with the texture march");
+    if (c->mode != 0 || c->step_mode != 0 || !use_tex(c))
+        return fail(c, VR_EINVAL,
+                    "the serving loop renders emission-absorption frames with a fixed step and the texture march");
     VR_CUDA(c, cudaSetDevice(c->device));
     int rc = retire_all(c);
     if (rc) return rc;

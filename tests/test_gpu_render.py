@@ -313,3 +313,60 @@ def test_mip_stops_at_the_global_maximum(vr, torch):
     ref, amb, ns = oracle_render(cube, tf, cam, (32, 32, 32), mode="mip")
     assert_parity(img, ref, amb, min_signal=0.0)
     assert st["samples"] < 0.7 * ns.sum()
+
+
+# ------------------------------------------------------------------ dynamic step
+
+@pytest.mark.parametrize("view", range(4))
+def test_dynamic_step_texture_march(vr, torch, tiny, view):
+    """Section 2.3.2's dynamic step (samples `step` voxels apart along each ray's
+    dominant axis) on the default texture march, against the oracle."""
+    cube, tf = tiny
+    cam = synth.tiny_views()[view]
+    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_STEP_MODE: 1})
+    ref, amb, ns = oracle.render(cube, tf, cam, brick=(32, 32, 32), amb_alpha=AMB_ALPHA, amb_steps=AMB_STEPS,
+                                 step_mode=1)
+    assert_parity(img, ref, amb)
+    fixed, _, nf = oracle.render(cube, tf, cam, brick=(32, 32, 32))
+    assert np.abs(ref - fixed).max() > 1e-3      # the variant does change the image
+
+
+@pytest.mark.parametrize("kernel,mode", [(1, 0), (1, 1)])
+def test_dynamic_step_direct_march_and_mip(vr, torch, tiny, kernel, mode):
+    cube, tf = tiny
+    cam = synth.tiny_views(width=120, height=100)[2]
+    img, _ = gpu_render(vr, torch, cube, tf, cam, (16, 16, 16),
+                        {vr.VR_OPT_STEP_MODE: 1, vr.VR_OPT_KERNEL: kernel, vr.VR_OPT_MODE: mode})
+    ref, amb, _ = oracle.render(cube, tf, cam, brick=(16, 16, 16), mode="mip" if mode else "ea",
+                                amb_alpha=AMB_ALPHA, amb_steps=AMB_STEPS, step_mode=1)
+    assert_parity(img, ref, amb)
+
+
+@pytest.mark.parametrize("shape,brick,camk,step,tau", RAGGED[:2])
+def test_dynamic_step_ragged(vr, torch, shape, brick, camk, step, tau):
+    cube = synth.hi_cube(seed=11, shape_xyz=shape, n_line=12, n_cont=2)
+    tf = synth.tf_tiny()
+    cam = synth.pose(shape, camk["az"], camk["el"], camk["W"], camk["H"], step=step, term_alpha=tau)
+    img, _ = gpu_render(vr, torch, cube, tf, cam, brick, {vr.VR_OPT_STEP_MODE: 1})
+    ref, amb, _ = oracle.render(cube, tf, cam, brick=brick, amb_alpha=AMB_ALPHA, amb_steps=AMB_STEPS, step_mode=1)
+    assert_parity(img, ref, amb)
+
+
+def test_dynamic_step_errors(vr, torch, tiny):
+    cube, tf = tiny
+    cam = synth.tiny_views(width=32, height=32)[0]
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(cube).cuda())
+        r.brick(32, 32, 32)
+        r.set_transfer_function(tf)
+        r.set_camera(cam)
+        with pytest.raises(vr.VRError, match="VR_EINVAL"):
+            r.set_option(vr.VR_OPT_STEP_MODE, 2)
+        r.set_option(vr.VR_OPT_STEP_MODE, 1)
+        r.set_option(vr.VR_OPT_KERNEL, vr.VR_KERNEL_TMA)
+        with pytest.raises(vr.VRError, match="VR_EINVAL"):
+            r.render()
+        r.set_option(vr.VR_OPT_KERNEL, vr.VR_KERNEL_AUTO)
+        r.render()
+        with pytest.raises(vr.VRError, match="VR_EINVAL"):
+            vr.Server(r, 128 << 20)

@@ -577,3 +577,50 @@ def test_region_termination_bound():
         assert d.max() <= 1.0 - cam["term_alpha"] + 1e-12
         worst = max(worst, d.max())
     assert worst > 1e-4
+
+
+# ------------------------------------------------------------------ dynamic step
+
+def test_dynamic_step_is_the_fixed_step_on_an_axis_aligned_ray():
+    """The centre pixel of an odd-sized image looks exactly along f; with f along
+    z the dominant component is 1 and the dynamic spacing equals the fixed one."""
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    cam = synth.camera((31.3, 30.7, -40.0), (31.3, 30.7, 10.0), (0, 1, 0), 20.0, 9, 7, step=0.7)
+    pix = np.array([3 * 9 + 4])
+    a, _, na = oracle.render(cube, tf, cam, pixels=pix)
+    b, _, nb = oracle.render(cube, tf, cam, pixels=pix, step_mode=1)
+    assert np.array_equal(a, b) and na[0] == nb[0] > 0
+
+
+@pytest.mark.parametrize("step", [0.5, 1.0])
+def test_dynamic_step_closed_form_on_a_constant_cube(step):
+    """Constant cube, termination off: after n samples spaced dt = step / max|d_a|
+    the opacity is 1 - (1 - a)^(n dt) with n = ceil(L / dt) (Section 2.3.2's
+    discrete ray casting: one sample per `step` voxels along the dominant axis)."""
+    cube = np.full((20, 20, 20), 2.0, dtype=np.float32)
+    a_tf = 0.07
+    tf = np.array([[0.0, 0.2, 0.4, 0.6, a_tf], [4.0, 0.2, 0.4, 0.6, a_tf]])
+    cam = synth.camera((-15.0, 33.0, -9.0), (9.5, 9.5, 9.5), (0, 1, 0), 40.0, 17, 13, step=step,
+                       term_alpha=1.0)
+    rgba, _, ns = oracle.render(cube, tf, cam, step_mode=1)
+    checked = 0
+    for j in range(13):
+        for i in range(17):
+            ray = oracle.pixel_ray(cam, (20, 20, 20), i, j)
+            if ray["n"] == 0:
+                continue
+            d = np.array(ray["d"])
+            L = ray["t1"] - ray["t0"]
+            dt = step / np.abs(d).max()
+            n = 0
+            while n * dt < L:    # samples k dt < L, k = 0, 1, ... (reading 4)
+                n += 1
+            assert ns[j, i] == n
+            A = 1.0 - (1.0 - a_tf) ** (n * dt)
+            assert abs(rgba[j, i, 3] - A) < 1e-12
+            assert abs(rgba[j, i, 0] - 0.2 * A) < 1e-12
+            checked += 1
+    assert checked > 50
+    # a diagonal view really takes fewer samples than the fixed step would
+    _, _, nf = oracle.render(cube, tf, cam)
+    assert ns.sum() < nf.sum()
