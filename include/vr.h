@@ -150,7 +150,9 @@ typedef struct {
                                 dominant axis): a ray with unit direction d samples every
                                 cam.step / max_a |d_a| voxels, i.e. every cam.step voxels
                                 along its dominant axis, the opacity correction using that
-                                spacing.  The lattice stays anchored at the ray's entry.
+                                spacing; the first sample sits half a step after the
+                                ray's entry (a ray crossing whole voxel slabs samples their
+                                middles, never their faces).
                                 Rendered by the texture or the direct march (VR_KERNEL_TMA
                                 with it: VR_EINVAL at render time). */
 #define VR_PRECISION_F32 0

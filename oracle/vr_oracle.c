@@ -232,10 +232,17 @@ static void render_pixel(const job_t* J, int i, int j, double out[4], int* amb_o
     if (!(t1 > t0)) goto done;
     /* Dynamic step (Section 2.3.2, discrete ray casting with at least one sample
      * per voxel crossed): successive samples are cam->step voxels apart along the
-     * ray's dominant axis, i.e. cam->step / max_a |d_a| apart along the ray. */
+     * ray's dominant axis, i.e. cam->step / max_a |d_a| apart along the ray, and
+     * the first sits half a step after the entry (so a ray crossing whole voxel
+     * slabs samples their middles, never a face). */
     double dmax = 0.0;
     for (int a = 0; a < 3; ++a) dmax = fabs(d[a]) > dmax ? fabs(d[a]) : dmax;
-    const double L = t1 - t0, dt = J->step_mode ? cam->step / dmax : cam->step, tau = cam->term_alpha;
+    const double dt = J->step_mode ? cam->step / dmax : cam->step, tau = cam->term_alpha;
+    if (J->step_mode) {
+        t0 += 0.5 * dt;
+        if (!(t1 > t0)) goto done;
+    }
+    const double L = t1 - t0;
     {
         double x = L / dt;
         if (fabs(x - nearbyint(x)) < J->amb_steps) amb |= ORC_AMB_STEPS;

@@ -14,9 +14,10 @@ namespace vr {
 // sample count n = #{k >= 0 : k dt < t1 - t0}.  Returns false if the ray misses
 // the domain [0, n-1]^3.
 // Cam: FrameParams (one frame) or FrameCam (a frame of a batch): eye, f, r, u, qx, qy.
-// dt: the ray's sample spacing, p.dt, or with the dynamic step (p.step_mode 1,
-// Section 2.3.2's discrete ray casting) p.dt / max_a |d_a|, so that successive
-// samples are p.dt voxels apart along the ray's dominant axis.
+// dt: the ray's sample spacing, p.dt, or with the dynamic step (DYN, Section
+// 2.3.2's discrete ray casting) p.dt / max_a |d_a|, so that successive samples
+// are p.dt voxels apart along the ray's dominant axis, the first half a step
+// after the entry.
 template <bool DYN = false, class Cam = FrameParams>
 __device__ __forceinline__ bool setup_ray(const FrameParams& p, const Cam& cam, int i, int j, df d[3], df pe[3],
                                           int& n_samples, df& dt) {
@@ -39,17 +40,20 @@ __device__ __forceinline__ bool setup_ray(const FrameParams& p, const Cam& cam, 
         tn = df_max(tn, df_min(ta, tb));
         tf = df_min(tf, df_max(ta, tb));
     }
-    const df t0 = df_max(tn, df_make(0.0f));
+    df t0 = df_max(tn, df_make(0.0f));
     if (!df_gt(tf, t0)) return false;
-    const df L = df_sub(tf, t0);
     dt = p.dt;
     if (DYN) {
-        // |d| along the dominant axis (selects, no indexed access)
+        // |d| along the dominant axis (selects, no indexed access); the first
+        // sample sits half a step after the entry
         df dm = d[0];
         if (fabsf(d[1].hi) > fabsf(dm.hi)) dm = d[1];
         if (fabsf(d[2].hi) > fabsf(dm.hi)) dm = d[2];
         dt = df_div(p.dt, dm.hi < 0.0f ? df_neg(dm) : dm);
+        t0 = df_add(t0, df_mul_f(dt, 0.5f));
+        if (!df_gt(tf, t0)) return false;
     }
+    const df L = df_sub(tf, t0);
     n_samples = (int)df_ceil(df_div(L, dt));
     for (int a = 0; a < 3; ++a) pe[a] = df_add(cam.eye[a], df_mul(t0, d[a]));
     return n_samples > 0;

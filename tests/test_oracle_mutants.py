@@ -49,6 +49,7 @@ MUTANTS = {
     "region run not restarted": ("racc[0] = racc[1] = racc[2] = racc[3] = 0.0;", "(void)racc;"),
     "dynamic step scaled the wrong way": ("dt = J->step_mode ? cam->step / dmax : cam->step",
                                           "dt = J->step_mode ? cam->step * dmax : cam->step"),
+    "dynamic step from the entry": ("        t0 += 0.5 * dt;\n", "        t0 += 0.0 * dt;\n"),
     "region folded behind the pixel": ("if (acc[3] < tau) fold(acc, racc);\n                            near_tau",
                                        "if (acc[3] < tau) { double t_[4]; memcpy(t_, racc, sizeof(t_)); "
                                        "fold(t_, acc); memcpy(acc, t_, sizeof(t_)); }\n                            near_tau"),
@@ -69,7 +70,7 @@ def _pin_calls():
         ("region-single", pins.test_region_fold_with_a_single_region_is_the_bricked_render),
         ("region-over", lambda: pins.test_region_fold_is_the_over_of_the_region_renders(2)),
         ("region-bound", pins.test_region_termination_bound),
-        ("dynamic-axis", pins.test_dynamic_step_is_the_fixed_step_on_an_axis_aligned_ray),
+        ("dynamic-axis", pins.test_dynamic_step_samples_the_middles_of_voxel_slabs),
         ("dynamic-closed", lambda: pins.test_dynamic_step_closed_form_on_a_constant_cube(1.0)),
     ]
     return calls

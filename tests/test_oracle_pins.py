@@ -581,22 +581,34 @@ def test_region_termination_bound():
 
 # ------------------------------------------------------------------ dynamic step
 
-def test_dynamic_step_is_the_fixed_step_on_an_axis_aligned_ray():
-    """The centre pixel of an odd-sized image looks exactly along f; with f along
-    z the dominant component is 1 and the dynamic spacing equals the fixed one."""
-    cube, tf = synth.tiny_cube(), synth.tf_tiny()
-    cam = synth.camera((31.3, 30.7, -40.0), (31.3, 30.7, 10.0), (0, 1, 0), 20.0, 9, 7, step=0.7)
+def test_dynamic_step_samples_the_middles_of_voxel_slabs():
+    """An axis-aligned ray (the centre pixel of an odd-sized image looking along
+    +z) through the affine field v = z: with step 1 the dynamic samples sit at
+    z = 0.5, 1.5, ..., n - 1.5 (the middles of the voxel slabs), the fixed ones at
+    z = 0, 1, ..., n - 2; MIP returns the last sample's value."""
+    n = 20
+    z = np.arange(n, dtype=np.float32)
+    cube = np.ascontiguousarray(np.broadcast_to(z[:, None, None], (n, n, n)))
+    tf = np.array([[0.0, 1.0, 1.0, 1.0, 0.5], [40.0, 1.0, 1.0, 1.0, 0.5]])   # colour map of the MIP value
+    cam = synth.camera((9.3, 8.7, -30.0), (9.3, 8.7, 10.0), (0, 1, 0), 20.0, 9, 7, step=1.0, term_alpha=1.0)
     pix = np.array([3 * 9 + 4])
-    a, _, na = oracle.render(cube, tf, cam, pixels=pix)
-    b, _, nb = oracle.render(cube, tf, cam, pixels=pix, step_mode=1)
-    assert np.array_equal(a, b) and na[0] == nb[0] > 0
+    _, _, nd = oracle.render(cube, tf, cam, pixels=pix, step_mode=1)
+    _, _, nf = oracle.render(cube, tf, cam, pixels=pix)
+    assert nd[0] == n - 1 and nf[0] == n - 1
+    lo = np.array([[0.0, 0.0, 0.0, 0.0, 0.0], [40.0, 1.0, 0.0, 0.0, 1.0]])   # red = opacity = value / 40
+    md, _, _ = oracle.render(cube, lo, cam, pixels=pix, mode="mip", step_mode=1)
+    mf, _, _ = oracle.render(cube, lo, cam, pixels=pix, mode="mip")
+    # premultiplied: red = (v / 40) * (v / 40)
+    assert abs(md[0, 0] - ((n - 1.5) / 40.0) ** 2) < 1e-12
+    assert abs(mf[0, 0] - ((n - 2.0) / 40.0) ** 2) < 1e-12
 
 
 @pytest.mark.parametrize("step", [0.5, 1.0])
 def test_dynamic_step_closed_form_on_a_constant_cube(step):
     """Constant cube, termination off: after n samples spaced dt = step / max|d_a|
-    the opacity is 1 - (1 - a)^(n dt) with n = ceil(L / dt) (Section 2.3.2's
-    discrete ray casting: one sample per `step` voxels along the dominant axis)."""
+    from half a step after the entry the opacity is 1 - (1 - a)^(n dt), n = the
+    count of (k + 1/2) dt < L (Section 2.3.2's discrete ray casting: one sample
+    per `step` voxels along the dominant axis)."""
     cube = np.full((20, 20, 20), 2.0, dtype=np.float32)
     a_tf = 0.07
     tf = np.array([[0.0, 0.2, 0.4, 0.6, a_tf], [4.0, 0.2, 0.4, 0.6, a_tf]])
@@ -613,7 +625,7 @@ def test_dynamic_step_closed_form_on_a_constant_cube(step):
             L = ray["t1"] - ray["t0"]
             dt = step / np.abs(d).max()
             n = 0
-            while n * dt < L:    # samples k dt < L, k = 0, 1, ... (reading 4)
+            while (n + 0.5) * dt < L:    # samples at (k + 1/2) dt < L
                 n += 1
             assert ns[j, i] == n
             A = 1.0 - (1.0 - a_tf) ** (n * dt)
