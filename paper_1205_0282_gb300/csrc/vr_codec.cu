@@ -160,10 +160,11 @@ struct Grads {
 
 // Shared-memory layout of the step kernel (bytes).  G2 is followed by G1 and G1
 // by Z1: the padded weight-gradient products read up to 1 KiB past either.
-// Inference asks for 56 KiB so that at most 4 CTAs (128 tensor-memory columns
-// each) share an SM.
+// Inference keeps H1 where IN was (IN is consumed by the first product before
+// H1 is written) and uses 28 KiB: 7 CTAs of 64 tensor-memory columns per SM.
 constexpr uint32_t kOffW1 = 0, kOffW2 = 4096, kOffIN = 12288, kOffH1 = 20480, kOffG2 = 36864, kOffG1 = 53248,
-                   kOffZ1 = 69632, kSmemInfer = 57344, kSmemTrain = 102400;
+                   kOffZ1 = 69632, kSmemInfer = 28672, kSmemTrain = 102400;
+constexpr int kCtasInfer = 7, kCtasTrain = 2;
 
 // SiLU with the hardware exponential (relative error ~2^-21, far below the BF16
 // rounding the MLP's operands take).
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
     __shared__ float s_db1[kHidden], s_db2[kHidden], s_dw3[kHidden], s_db3;
     __shared__ double s_loss;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t tcols = TRAIN ? 256 : 128;
+    const uint32_t tcols = TRAIN ? 256 : 64;
+    constexpr uint32_t kH1 = TRAIN ? kOffH1 : kOffIN;  // inference: H1 over IN
     // weights into shared memory (K-major, rows = outputs)
     for (int i = tid; i < kHidden * kIn; i += kTileP)
         *reinterpret_cast<__nv_bfloat16*>(sm + kOffW1 + tc::kmajor_offset(i / kIn, i % kIn, kIn)) = net.W1[i];
@@ -294,7 +296,9 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
     const uint32_t tmem = tmem_slot;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint32_t sbase = tc::smem_addr(sm);
-    const uint32_t T_D1 = tmem, T_D2 = tmem + 64, T_DW2 = tmem + 128, T_DW1 = tmem + 192, T_DIN = tmem + 224;
+    // inference: D2 reuses D1's columns (D1 is read out before the second product)
+    const uint32_t T_D1 = tmem, T_D2 = TRAIN ? tmem + 64 : tmem, T_DW2 = tmem + 128, T_DW1 = tmem + 192,
+                   T_DIN = tmem + 224;
     const uint32_t id_64 = tc::make_idesc_bf16(128, 64, 0, 0);
     uint32_t phase = 0;
     bool ok = true;
@@ -338,18 +342,18 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
         }
         wait_mma();
 #pragma unroll 1
-        for (int c = 0; c < kHidden; c += 16) {
-            float d[16];
-            tc::tmem_ld16(T_D1 + lane_base + c, d);
+        for (int c = 0; c < kHidden; c += 32) {
+            float d[32];
+            tc::tmem_ld32(T_D1 + lane_base + c, d);
 #pragma unroll
-            for (int i = 0; i < 16; i += 2) {
+            for (int i = 0; i < 32; i += 2) {
                 const float z0 = d[i] + net.b1[c + i], z1 = d[i + 1] + net.b1[c + i + 1];
                 if (TRAIN) {
                     float* zr = reinterpret_cast<float*>(sm + kOffZ1) + tid * kHidden + c + i;
                     zr[0] = z0;
                     zr[1] = z1;
                 }
-                *reinterpret_cast<__nv_bfloat162*>(sm + kOffH1 + tc::kmajor_offset(tid, c + i, kHidden)) =
+                *reinterpret_cast<__nv_bfloat162*>(sm + kH1 + tc::kmajor_offset(tid, c + i, kHidden)) =
                     __floats2bfloat162_rn(silu(z0), silu(z1));
             }
         }
@@ -359,17 +363,17 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
         tc::fence_after_sync();
         // layer 2: D2 = H1 W2^T (K 64)
         if (tid == 0) {
-            mma_chain(T_D2, sbase + kOffH1, 256, 128, 1024, sbase + kOffW2, 256, 128, 1024, id_64, 4, false);
+            mma_chain(T_D2, sbase + kH1, 256, 128, 1024, sbase + kOffW2, 256, 128, 1024, id_64, 4, false);
             tc::mma_commit(&bar);
         }
         wait_mma();
         float y = net.b3[0];
 #pragma unroll 1
-        for (int c = 0; c < kHidden; c += 16) {
-            float d[16];
-            tc::tmem_ld16(T_D2 + lane_base + c, d);
+        for (int c = 0; c < kHidden; c += 32) {
+            float d[32];
+            tc::tmem_ld32(T_D2 + lane_base + c, d);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) y = fmaf(silu(d[i] + net.b2[c + i]), net.w3[c + i], y);
+            for (int i = 0; i < 32; ++i) y = fmaf(silu(d[i] + net.b2[c + i]), net.w3[c + i], y);
         }
         const float sb = valid ? net.s[brick] : 0.0f;
         const float v = valid ? fmaf(y, sb, net.m[brick]) : 0.0f;
@@ -788,7 +792,7 @@ int launch_codec(vr_codec* c, const float4* pts, vr::codec::Grid grid, const flo
         g.dy_scale = 2.0f / (float)n;
     }
     const int64_t tiles = (n + kTileP - 1) / kTileP;
-    const int64_t grid_ctas = std::min<int64_t>(tiles, (int64_t)c->sm_count * (TRAIN ? 2 : 4));
+    const int64_t grid_ctas = std::min<int64_t>(tiles, (int64_t)c->sm_count * (TRAIN ? kCtasTrain : kCtasInfer));
     codec_kernel<TRAIN><<<(unsigned)grid_ctas, kTileP, smem, st>>>(make_net(c), pts, grid, tgt, n, out, g, c->err);
     return codec_cuda(cudaGetLastError());
 }
