@@ -321,11 +321,13 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
             if (pts) {
                 pt = pts[idx];
             } else {
+                // one 64-bit division for the brick, 32-bit arithmetic inside it
                 const int64_t V = (int64_t)grid.dims[0] * grid.dims[1] * grid.dims[2];
-                const int64_t q = idx % V;
-                pt = make_float4((float)(q % grid.dims[0]), (float)((q / grid.dims[0]) % grid.dims[1]),
-                                 (float)(q / ((int64_t)grid.dims[0] * grid.dims[1])),
-                                 __int_as_float(grid.bricks[idx / V]));
+                const int64_t k = idx / V;
+                const int q = (int)(idx - k * V);
+                const int qy = q / grid.dims[0];
+                pt = make_float4((float)(q - qy * grid.dims[0]), (float)(qy % grid.dims[1]),
+                                 (float)(qy / grid.dims[1]), __int_as_float(grid.bricks[k]));
             }
         }
         int brick = 0;
@@ -382,7 +384,8 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
                 int64_t o = idx;
                 if (!pts && grid.slots) {
                     const int64_t V = (int64_t)grid.dims[0] * grid.dims[1] * grid.dims[2];
-                    o = (int64_t)grid.slots[idx / V] * V + idx % V;
+                    const int64_t k = idx / V;
+                    o = (int64_t)grid.slots[k] * V + (idx - k * V);
                 }
                 out[o] = v;
             }
