@@ -166,9 +166,27 @@ constexpr uint32_t kOffW1 = 0, kOffW2 = 4096, kOffIN = 12288, kOffH1 = 20480, kO
                    kOffZ1 = 69632, kSmemInfer = 28672, kSmemTrain = 102400;
 constexpr int kCtasInfer = 7, kCtasTrain = 2;
 
-// SiLU with the hardware exponential (relative error ~2^-21, far below the BF16
-// rounding the MLP's operands take).
-__device__ __forceinline__ float silu(float t) { return __fdividef(t, 1.0f + __expf(-t)); }
+// SiLU with the hardware base-2 exponential and reciprocal (relative errors ~2^-22,
+// far below the BF16 rounding the MLP's operands take): t / (1 + 2^(-t log2 e)).
+// Very negative t gives 2^(+big) = inf and a reciprocal of 0, i.e. silu = -0.
+__device__ __forceinline__ float silu(float t) {
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(t * -1.4426950408889634f));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+    return t * r;
+}
+// The same on two values, the multiplications and additions as packed FP32x2
+// operations (each lane rounded like the scalar operation).
+__device__ __forceinline__ float2 silu2(float2 t) {
+    const float2 a = __fmul2_rn(t, make_float2(-1.4426950408889634f, -1.4426950408889634f));
+    float2 e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.x) : "f"(a.x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e.y) : "f"(a.y));
+    const float2 d = __fadd2_rn(e, make_float2(1.0f, 1.0f));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(d.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(d.y));
+    return __fmul2_rn(t, r);
+}
 __device__ __forceinline__ float silu_grad(float t) {
     const float s = __fdividef(1.0f, 1.0f + __expf(-t));
     return s * (1.0f + t * (1.0f - s));
@@ -176,6 +194,14 @@ __device__ __forceinline__ float silu_grad(float t) {
 
 __device__ __forceinline__ void store_bf16(unsigned char* base, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+// Eight consecutive K elements of one operand row: one core-matrix row, 16 bytes.
+__device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v) {
+    __nv_bfloat162 h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
 }
 
 // Point p: brick (bits of .w) and local voxel position (.x, .y, .z) in [0, B].
@@ -188,6 +214,7 @@ struct Corner {
 __device__ __forceinline__ void build_input(const Net& net, float4 pt, bool valid, int row, unsigned char* in_s,
                                             int& brick, Corner& cr) {
     float in[kIn];
+    float2* in2 = reinterpret_cast<float2*>(in);
 #pragma unroll
     for (int i = 0; i < kIn; ++i) in[i] = 0.0f;
     brick = __float_as_int(pt.w);
@@ -213,27 +240,26 @@ __device__ __forceinline__ void build_input(const Net& net, float4 pt, bool vali
             const uint4 q0 = __ldg(src), q1 = __ldg(src + 1);
             const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&q0);
             const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&q1);
+            const float2 w2 = make_float2(w, w);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float2 a0 = __bfloat1622float2(h0[k]), a1 = __bfloat1622float2(h1[k]);
-                in[2 * k] = fmaf(w, a0.x, in[2 * k]);
-                in[2 * k + 1] = fmaf(w, a0.y, in[2 * k + 1]);
-                in[8 + 2 * k] = fmaf(w, a1.x, in[8 + 2 * k]);
-                in[8 + 2 * k + 1] = fmaf(w, a1.y, in[8 + 2 * k + 1]);
+                in2[k] = __ffma2_rn(w2, __bfloat1622float2(h0[k]), in2[k]);
+                in2[4 + k] = __ffma2_rn(w2, __bfloat1622float2(h1[k]), in2[4 + k]);
             }
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            in[16 + 4 * a] = sinpif(x[a]);
-            in[17 + 4 * a] = cospif(x[a]);
-            in[18 + 4 * a] = sinpif(2.0f * x[a]);
-            in[19 + 4 * a] = cospif(2.0f * x[a]);
+            // sin(2 pi x) = 2 sin cos, cos(2 pi x) = (cos - sin)(cos + sin)
+            float sn, cs;
+            sincospif(x[a], &sn, &cs);
+            in[16 + 4 * a] = sn;
+            in[17 + 4 * a] = cs;
+            in[18 + 4 * a] = 2.0f * sn * cs;
+            in[19 + 4 * a] = (cs - sn) * (cs + sn);
         }
     }
 #pragma unroll
-    for (int i = 0; i < kIn; i += 2)
-        *reinterpret_cast<__nv_bfloat162*>(in_s + tc::kmajor_offset(row, i, kIn)) =
-            __floats2bfloat162_rn(in[i], in[i + 1]);
+    for (int i = 0; i < kIn; i += 8) store_bf16x8(in_s + tc::kmajor_offset(row, i, kIn), in + i);
 }
 
 // Issue a chain of K = 16 MMAs (nk of them) and leave the commit to the caller.
@@ -267,6 +293,7 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_slot;
     __shared__ float s_db1[kHidden], s_db2[kHidden], s_dw3[kHidden], s_db3;
+    __shared__ __align__(16) float s_b1[kHidden], s_b2[kHidden], s_w3[kHidden];
     __shared__ double s_loss;
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t tcols = TRAIN ? 256 : 64;
@@ -277,6 +304,11 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
     for (int i = tid; i < kHidden * kHidden; i += kTileP)
         *reinterpret_cast<__nv_bfloat16*>(sm + kOffW2 + tc::kmajor_offset(i / kHidden, i % kHidden, kHidden)) =
             net.W2[i];
+    for (int i = tid; i < kHidden; i += kTileP) {
+        s_b1[i] = net.b1[i];
+        s_b2[i] = net.b2[i];
+        s_w3[i] = net.w3[i];
+    }
     if (TRAIN) {
         for (int i = tid; i < kHidden; i += kTileP) s_db1[i] = s_db2[i] = s_dw3[i] = 0.0f;
         // the bytes the padded gradient products read beyond G1 must be initialised
@@ -303,10 +335,13 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
     uint32_t phase = 0;
     bool ok = true;
     int tiles_done = 0;
-    // every thread waits for the MMAs; the block then agrees on the outcome, so that
-    // a wait that gave up in one thread stops the whole block at the same point
+    // the issuing thread waits for the MMAs (the others sleep at the block barrier
+    // instead of polling); the block then agrees on the outcome, so that a wait that
+    // gave up stops the whole block at the same point.  The mbarrier's completion
+    // (acquire), the barrier and the fence order every thread's tensor-memory reads
+    // after the products.
     auto wait_mma = [&]() {
-        const bool mine = tc::bar_wait(&bar, phase, kWaitLimit);
+        const bool mine = tid != 0 || tc::bar_wait(&bar, phase, kWaitLimit);
         phase ^= 1u;
         ok = __syncthreads_and(mine ? 1 : 0) != 0;
         if (!ok && tid == 0) atomicOr(err, 1);
@@ -317,17 +352,22 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
         const int64_t idx = t * kTileP + tid;
         const bool valid = idx < n_points;
         float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
+        int64_t gk = 0, gq = 0;  // grid points: list entry and voxel within the brick
         if (valid) {
             if (pts) {
                 pt = pts[idx];
             } else {
-                // one 64-bit division for the brick, 32-bit arithmetic inside it
                 const int64_t V = (int64_t)grid.dims[0] * grid.dims[1] * grid.dims[2];
-                const int64_t k = idx / V;
-                const int q = (int)(idx - k * V);
+                if (n_points <= 0x7FFFFFFF) {  // block-uniform: 32-bit division
+                    gk = (uint32_t)idx / (uint32_t)V;
+                } else {
+                    gk = idx / V;
+                }
+                const int q = (int)(idx - gk * V);
+                gq = q;
                 const int qy = q / grid.dims[0];
                 pt = make_float4((float)(q - qy * grid.dims[0]), (float)(qy % grid.dims[1]),
-                                 (float)(qy / grid.dims[1]), __int_as_float(grid.bricks[k]));
+                                 (float)(qy / grid.dims[1]), __int_as_float(grid.bricks[gk]));
             }
         }
         int brick = 0;
@@ -348,15 +388,23 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
             float d[32];
             tc::tmem_ld32(T_D1 + lane_base + c, d);
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-                const float z0 = d[i] + net.b1[c + i], z1 = d[i + 1] + net.b1[c + i + 1];
-                if (TRAIN) {
-                    float* zr = reinterpret_cast<float*>(sm + kOffZ1) + tid * kHidden + c + i;
-                    zr[0] = z0;
-                    zr[1] = z1;
+            for (int i = 0; i < 32; i += 8) {
+                float h[8];
+#pragma unroll
+                for (int e = 0; e < 8; e += 4) {
+                    const float4 b = *reinterpret_cast<const float4*>(s_b1 + c + i + e);
+                    const float2 za = __fadd2_rn(make_float2(d[i + e], d[i + e + 1]), make_float2(b.x, b.y));
+                    const float2 zb = __fadd2_rn(make_float2(d[i + e + 2], d[i + e + 3]), make_float2(b.z, b.w));
+                    if (TRAIN)
+                        *reinterpret_cast<float4*>(reinterpret_cast<float*>(sm + kOffZ1) + tid * kHidden + c + i +
+                                                   e) = make_float4(za.x, za.y, zb.x, zb.y);
+                    const float2 ha = silu2(za), hb = silu2(zb);
+                    h[e] = ha.x;
+                    h[e + 1] = ha.y;
+                    h[e + 2] = hb.x;
+                    h[e + 3] = hb.y;
                 }
-                *reinterpret_cast<__nv_bfloat162*>(sm + kH1 + tc::kmajor_offset(tid, c + i, kHidden)) =
-                    __floats2bfloat162_rn(silu(z0), silu(z1));
+                store_bf16x8(sm + kH1 + tc::kmajor_offset(tid, c + i, kHidden), h);
             }
         }
         tc::fence_smem_to_async();
@@ -369,24 +417,30 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
             tc::mma_commit(&bar);
         }
         wait_mma();
-        float y = net.b3[0];
+        // two partial sums (even and odd units) in one packed register pair
+        float2 y2 = make_float2(net.b3[0], 0.0f);
 #pragma unroll 1
         for (int c = 0; c < kHidden; c += 32) {
             float d[32];
             tc::tmem_ld32(T_D2 + lane_base + c, d);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) y = fmaf(silu(d[i] + net.b2[c + i]), net.w3[c + i], y);
+            for (int i = 0; i < 32; i += 4) {
+                const float4 b = *reinterpret_cast<const float4*>(s_b2 + c + i);
+                const float4 w = *reinterpret_cast<const float4*>(s_w3 + c + i);
+                y2 = __ffma2_rn(silu2(__fadd2_rn(make_float2(d[i], d[i + 1]), make_float2(b.x, b.y))),
+                                make_float2(w.x, w.y), y2);
+                y2 = __ffma2_rn(silu2(__fadd2_rn(make_float2(d[i + 2], d[i + 3]), make_float2(b.z, b.w))),
+                                make_float2(w.z, w.w), y2);
+            }
         }
+        const float y = y2.x + y2.y;
         const float sb = valid ? net.s[brick] : 0.0f;
         const float v = valid ? fmaf(y, sb, net.m[brick]) : 0.0f;
         if (!TRAIN) {
             if (valid) {
                 int64_t o = idx;
-                if (!pts && grid.slots) {
-                    const int64_t V = (int64_t)grid.dims[0] * grid.dims[1] * grid.dims[2];
-                    const int64_t k = idx / V;
-                    o = (int64_t)grid.slots[k] * V + (idx - k * V);
-                }
+                if (!pts && grid.slots)
+                    o = (int64_t)grid.slots[gk] * ((int64_t)grid.dims[0] * grid.dims[1] * grid.dims[2]) + gq;
                 out[o] = v;
             }
             tc::fence_before_sync();
@@ -415,8 +469,8 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
                 float gg[2];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const float z2 = d[i + e] + net.b2[c + i + e];
-                    gg[e] = dy * net.w3[c + i + e] * silu_grad(z2);
+                    const float z2 = d[i + e] + s_b2[c + i + e];
+                    gg[e] = dy * s_w3[c + i + e] * silu_grad(z2);
                     if (dy != 0.0f) {
                         atomicAdd(&s_db2[c + i + e], gg[e]);
                         atomicAdd(&s_dw3[c + i + e], dy * silu(z2));
