@@ -73,9 +73,13 @@ def parse():
     ap.add_argument("--train-lr", type=float, default=3e-3)
     ap.add_argument("--psnr-poses", type=int, default=12)
     ap.add_argument("--codec-brick", type=int, default=0,
-                    help="--learned: brick edge of the codec and of the learned render (0: the workload's)")
+                    help="--learned: brick edge of the codec and of the learned render; --ooc: brick edge "
+                         "of the streamed bricks (0: the workload's)")
     ap.add_argument("--active-frac", type=float, default=0.5,
                     help="--learned: share of training points drawn from voxels the transfer function can show")
+    ap.add_argument("--fallback-bound", type=float, default=None,
+                    help="--learned: bricks whose decode error (above the TF floor, in data units) exceeds "
+                         "this are copied from pinned plain blocks instead of decoded")
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -90,6 +94,9 @@ def workload(args):
         spec["width"], spec["height"] = W, H
         poses = [dict(c, width=W, height=H) for c in poses]
         desc += f", image overridden to {W}x{H}"
+    if args.ooc and args.codec_brick:
+        spec["brick"] = (args.codec_brick,) * 3
+        desc += f", bricks overridden to {args.codec_brick}^3"
     return spec, tf, poses, desc
 
 
@@ -638,12 +645,23 @@ def run_learned(args):
     del dcube
     torch.cuda.empty_cache()
 
+    fb = {}
+
     def render_learned(budget_gib, steps):
         r = vrm.VolumeRenderer(0)
         r.load_cube_codec(codec, shape)
         if budget_gib > 0:
             r.set_option(vrm.VR_OPT_DEVICE_BUDGET, int(budget_gib * 2 ** 30))
+        if args.fallback_bound is not None:
+            r.set_codec_fallback(cube, args.fallback_bound, floor)
+        t_scan = time.perf_counter()
         r.brick(*brick)
+        if args.fallback_bound is not None:
+            err, n_plain = r.codec_brick_errors()
+            fb.update({"bound": args.fallback_bound, "bricks_plain": n_plain, "bricks": nb,
+                       "pinned_gib": n_plain * V * 4 / 2 ** 30, "scan_and_store_s": time.perf_counter() - t_scan,
+                       "brick_error_p50_p90_max": [float(np.percentile(err, 50)), float(np.percentile(err, 90)),
+                                                   float(err.max())]})
         r.set_transfer_function(tf)
         imgs = []
         for cam in psnr_poses:
@@ -692,7 +710,9 @@ def run_learned(args):
                         "decode_ms_all_bricks": dec_ms, "decode_points_per_s": points / (dec_ms * 1e-3),
                         "decode_tensor_tflops": dec_tflops,
                         "bricks_decoded_per_frame": st["bricks_uploaded"] / max(st["frames"], 1),
-                        "bricks_cached_per_frame": st["bricks_cached"] / max(st["frames"], 1)},
+                        "bricks_cached_per_frame": st["bricks_cached"] / max(st["frames"], 1),
+                        "h2d_gb_per_frame": st["h2d_bytes"] / max(st["frames"], 1) / 1e9,
+                        "fallback": fb or None},
             "roofline": {"bound": "tensor", "kernel": "codec_kernel (decode)", "achieved": dec_tflops,
                          "peak": json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
                          if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0,

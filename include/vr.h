@@ -498,6 +498,28 @@ int vr_codec_decode_bricks(vr_codec* codec, const int32_t* bricks, const int32_t
 int vr_load_cube_codec(vr_ctx* ctx, vr_codec* codec, int64_t nx, int64_t ny, int64_t nz);
 
 /*
+ * Per-brick fallback of a learned context to the plain voxels (no counterpart in
+ * the paper): at the next vr_brick every brick is decoded and compared with its
+ * block of the plain cube `data` (host memory, float32[nz][ny][nx] of the sizes
+ * given to vr_load_cube_codec; read during that vr_brick only, the caller keeps
+ * ownership).  The error of a brick is the largest |max(d, floor_v) -
+ * max(v, floor_v)| over the voxels of its (bx+1)(by+1)(bz+1) block that lie
+ * inside the cube (d decoded, v plain): values at or below floor_v, where the
+ * transfer function is transparent, count as floor_v.  A brick whose error
+ * exceeds `bound` keeps a pinned host copy of its plain block and is copied into
+ * its cache slot (as vr_load_cube_host does) instead of decoded.  bound < 0: every
+ * brick falls back; bound = +inf: none.  data = NULL turns the fallback off.
+ * Errors: VR_ESTATE (not a learned context), VR_EINVAL (NaN bound or floor); the
+ * scan's own errors (VR_ENOMEM, VR_ECUDA) are reported by vr_brick.
+ */
+int vr_set_codec_fallback(vr_ctx* ctx, const float* data, float bound, float floor_v);
+
+/* The per-brick errors measured by the last vr_brick's fallback scan (host
+ * float32[n_bricks], may be NULL) and the number of bricks that fall back (may be
+ * NULL).  Errors: VR_ESTATE (no scan since the last load). */
+int vr_codec_brick_errors(vr_ctx* ctx, float* err, int64_t* n_plain);
+
+/*
  * Allocation-free render (the paper has no counterpart; this serves callers that
  * may not allocate device memory while rendering: an application or plugin that
  * owns the device-memory budget, a real-time loop that cannot take the implicit

@@ -238,6 +238,14 @@ struct vr_ctx {
     bool ooc = false;
     const float* h_src = nullptr;      // the caller's cube
     vr_codec* codec = nullptr;         // learned residency: slots are filled by decoding
+    // learned residency's fallback: bricks whose decode error exceeds fb_bound are
+    // copied from plain blocks in h_store (block plain_index[b]) instead
+    const float* fb_src = nullptr;     // the caller's plain cube, read at vr_brick
+    float fb_bound = 0.0f, fb_floor = 0.0f;
+    bool fb_measured = false;          // brick_err holds the last vr_brick's errors
+    std::vector<float> brick_err;
+    std::vector<int64_t> plain_index;  // per brick: its block in h_store, or -1 (decoded)
+    int64_t n_plain = 0;
     float* h_store = nullptr;          // pinned brick store, brick b at b * slot_floats
     size_t store_bytes = 0;
     int64_t slot_floats = 0;           // (Bx+1)(By+1)(Bz+1)

@@ -80,6 +80,11 @@ void free_ooc(vr_ctx* c) {
     c->res = vr::Residency();
     c->h_src = nullptr;
     c->codec = nullptr;
+    c->fb_src = nullptr;
+    c->fb_measured = false;
+    c->brick_err.clear();
+    c->plain_index.clear();
+    c->n_plain = 0;
     c->ooc = false;
 }
 
@@ -97,6 +102,83 @@ int ensure_ooc_streams(vr_ctx* c) {
     VR_CUDA(c, cudaStreamCreateWithPriority(&c->ring_stream, cudaStreamNonBlocking, hi_prio));
     VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_start, cudaEventDisableTiming));
     VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_end, cudaEventDisableTiming));
+    return VR_OK;
+}
+
+// Learned residency's fallback (at vr_brick): decode every brick, compare it with
+// its plain block, and keep pinned plain blocks of the bricks over the bound.
+int codec_fallback_scan(vr_ctx* c) {
+    const int64_t nb = c->n_bricks;
+    c->brick_err.assign(nb, 0.0f);
+    c->plain_index.assign(nb, -1);
+    c->n_plain = 0;
+    c->fb_measured = false;
+    if (!c->fb_src) return VR_OK;
+    const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nb, ((int64_t)256 << 20) / (int64_t)slot_bytes));
+    float *d_dec = nullptr, *d_plain = nullptr, *h_stage = nullptr;
+    int32_t *d_ids = nullptr, *h_ids = nullptr;
+    uint32_t* d_err = nullptr;
+    int rc = VR_OK;
+    if (cudaMalloc((void**)&d_dec, chunk * slot_bytes) != cudaSuccess ||
+        cudaMalloc((void**)&d_plain, chunk * slot_bytes) != cudaSuccess ||
+        cudaMalloc((void**)&d_ids, chunk * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc((void**)&d_err, nb * sizeof(uint32_t)) != cudaSuccess ||
+        cudaHostAlloc((void**)&h_stage, chunk * slot_bytes, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void**)&h_ids, chunk * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(c, VR_ENOMEM, "cannot allocate the fallback scan's buffers");
+    }
+    if (!rc && cudaMemsetAsync(d_err, 0, nb * sizeof(uint32_t), c->copy_stream) != cudaSuccess)
+        rc = fail(c, VR_ECUDA, "fallback scan: memset failed");
+    for (int64_t b0 = 0; !rc && b0 < nb; b0 += chunk) {
+        const int32_t k = (int32_t)std::min<int64_t>(chunk, nb - b0);
+        for (int32_t i = 0; i < k; ++i) h_ids[i] = (int32_t)(b0 + i);
+        vr::build_brick_blocks(c->fb_src, c->n, c->B, c->nb, h_ids, k, h_stage, c->slot_floats);
+        if (cudaMemcpyAsync(d_ids, h_ids, k * sizeof(int32_t), cudaMemcpyHostToDevice, c->copy_stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(d_plain, h_stage, k * slot_bytes, cudaMemcpyHostToDevice, c->copy_stream) != cudaSuccess) {
+            rc = fail(c, VR_ECUDA, "fallback scan: copy failed");
+            break;
+        }
+        if ((rc = vr_codec_decode_bricks(c->codec, d_ids, nullptr, k, d_dec, c->copy_stream))) {
+            rc = fail(c, rc, "fallback scan: brick decode failed");
+            break;
+        }
+        if (vr::launch_brick_error(d_dec, d_plain, b0, k, c->n, c->B, c->nb, c->fb_floor, d_err + b0,
+                                   c->copy_stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->copy_stream) != cudaSuccess) {  // the staging buffers are reused
+            rc = fail(c, VR_ECUDA, "fallback scan: comparison failed");
+            break;
+        }
+    }
+    if (!rc && cudaMemcpy(c->brick_err.data(), d_err, nb * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = fail(c, VR_ECUDA, "fallback scan: cannot read the errors");
+    cudaFree(d_dec);
+    cudaFree(d_plain);
+    cudaFree(d_ids);
+    cudaFree(d_err);
+    if (h_stage) cudaFreeHost(h_stage);
+    if (h_ids) cudaFreeHost(h_ids);
+    if (rc) return rc;
+    std::vector<int32_t> plain;
+    for (int64_t b = 0; b < nb; ++b)
+        if (c->brick_err[b] > c->fb_bound) {
+            c->plain_index[b] = (int64_t)plain.size();
+            plain.push_back((int32_t)b);
+        }
+    c->n_plain = (int64_t)plain.size();
+    c->fb_measured = true;
+    if (plain.empty()) return VR_OK;
+    c->store_bytes = slot_bytes * plain.size();
+    if (cudaHostAlloc((void**)&c->h_store, c->store_bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_store = nullptr;
+        c->store_bytes = 0;
+        return fail(c, VR_ENOMEM, "cannot allocate the pinned store of the fallback bricks");
+    }
+    vr::build_brick_blocks(c->fb_src, c->n, c->B, c->nb, plain.data(), (int64_t)plain.size(), c->h_store,
+                           c->slot_floats);
     return VR_OK;
 }
 
@@ -135,7 +217,7 @@ int build_ooc_store(vr_ctx* c) {
     c->res.slot_of_brick.assign(c->n_bricks, -1);
     c->res.brick_in_slot.assign(slots, -1);
     c->res.last_used.assign(slots, -1);
-    return VR_OK;
+    return c->codec ? codec_fallback_scan(c) : VR_OK;
 }
 
 int64_t precision_bytes(int precision) {
@@ -441,6 +523,25 @@ int vr_load_cube_codec(vr_ctx* c, vr_codec* codec, int64_t nx, int64_t ny, int64
     c->n[0] = nx;
     c->n[1] = ny;
     c->n[2] = nz;
+    return VR_OK;
+}
+
+int vr_set_codec_fallback(vr_ctx* c, const float* data, float bound, float floor_v) {
+    if (!c) return VR_EINVAL;
+    if (!c->codec) return fail(c, VR_ESTATE, "the fallback needs a learned context (vr_load_cube_codec)");
+    if (std::isnan(bound) || std::isnan(floor_v)) return fail(c, VR_EINVAL, "NaN bound or floor");
+    c->fb_src = data;
+    c->fb_bound = bound;
+    c->fb_floor = floor_v;
+    return VR_OK;
+}
+
+int vr_codec_brick_errors(vr_ctx* c, float* err, int64_t* n_plain) {
+    if (!c) return VR_EINVAL;
+    if (!c->codec || !c->bricked || !c->fb_measured)
+        return fail(c, VR_ESTATE, "no fallback scan: vr_set_codec_fallback, then vr_brick, on a learned context");
+    if (err) std::copy(c->brick_err.begin(), c->brick_err.end(), err);
+    if (n_plain) *n_plain = c->n_plain;
     return VR_OK;
 }
 
@@ -822,14 +923,31 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocL
 // Fill the bricks' cache slots on the copy stream: copy them from the pinned
 // store, or decode them (learned residency; list_off: where this launch's
 // (brick, slot) lists sit in the frame's list buffers).
-int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off) {
+// Returns the bytes copied from host memory in *copied.
+int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off, size_t* copied) {
     const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
+    *copied = 0;
     if (c->codec) {
-        const size_t n = L.up.size();
-        std::memcpy(s.h_decode + list_off, L.up.data(), n * sizeof(int32_t));
-        std::memcpy(s.h_decode + list_off + n, L.slot.data(), n * sizeof(int32_t));
-        VR_CUDA(c, cudaMemcpyAsync(s.d_decode + list_off, s.h_decode + list_off, 2 * n * sizeof(int32_t),
-                                   cudaMemcpyHostToDevice, c->copy_stream));
+        // fallback bricks are copied from their plain blocks, the others decoded
+        int32_t* lb = s.h_decode + list_off;
+        size_t n = 0;
+        for (size_t k = 0; k < L.up.size(); ++k) {
+            const int64_t pi = c->plain_index.empty() ? -1 : c->plain_index[L.up[k]];
+            if (pi >= 0) {
+                VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
+                                           c->h_store + (size_t)pi * c->slot_floats, slot_bytes,
+                                           cudaMemcpyHostToDevice, c->copy_stream));
+                *copied += slot_bytes;
+            } else {
+                lb[n++] = L.up[k];
+            }
+        }
+        if (n == 0) return VR_OK;
+        size_t m = 0;
+        for (size_t k = 0; k < L.up.size(); ++k)
+            if (c->plain_index.empty() || c->plain_index[L.up[k]] < 0) lb[n + m++] = L.slot[k];
+        VR_CUDA(c, cudaMemcpyAsync(s.d_decode + list_off, lb, 2 * n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   c->copy_stream));
         const int rc = vr_codec_decode_bricks(c->codec, s.d_decode + list_off, s.d_decode + list_off + n, (int32_t)n,
                                               c->d_pool, c->copy_stream);
         if (rc) return fail(c, rc, "brick decode failed");
@@ -839,6 +957,7 @@ int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off) {
         VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
                                    c->h_store + (size_t)L.up[k] * c->slot_floats, slot_bytes,
                                    cudaMemcpyHostToDevice, c->copy_stream));
+    *copied = L.up.size() * slot_bytes;
     return VR_OK;
 }
 
@@ -969,9 +1088,10 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
             // a ring half is refilled once its last reader has marched (host issue
             // order puts that reader's event record before this wait)
             if (L.half >= 0) VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_half_read[L.half], 0));
-            int r = ooc_upload(c, s, L, list_off[k]);
+            size_t copied = 0;
+            int r = ooc_upload(c, s, L, list_off[k], &copied);
             if (r) return r;
-            if (!c->codec) upload_bytes += L.up.size() * (size_t)c->slot_floats * sizeof(float);
+            upload_bytes += copied;
             VR_CUDA(c, cudaEventRecord(c->ev_chunk[k], c->copy_stream));
             VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));
             return VR_OK;

@@ -160,6 +160,16 @@ struct Residency {
 };
 void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
                        float* store, int64_t slot_floats, float2* minmax);
+// The blocks of the listed bricks ids[0..count) only, block i at store + i * slot_floats.
+void build_brick_blocks(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
+                        const int32_t* ids, int64_t count, float* store, int64_t slot_floats);
+// Decode error of `count` consecutive bricks first, first + 1, ...: decoded and
+// plain hold their (B+1)^3 blocks back to back; err_bits[k] (zeroed by the caller)
+// receives the bits of max |max(d, floor) - max(v, floor)| over brick first + k's
+// voxels inside the cube.
+cudaError_t launch_brick_error(const float* decoded, const float* plain, int64_t first, int32_t count,
+                               const int64_t n[3], const int32_t B[3], const int32_t nb[3], float floor_v,
+                               uint32_t* err_bits, cudaStream_t s);
 // Slots for the frame's bricks (in render order).  upload: positions (in
 // `bricks`) of bricks copied into resident slots; ring: positions of bricks that
 // stream through the ring, in order, the j-th into half (first_half + j / H) % 2.

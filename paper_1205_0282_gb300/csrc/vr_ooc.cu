@@ -8,6 +8,10 @@
 //                      apron its samples read), zero beyond the cube, and the
 //                      brick's [min, max] over the same voxels (Section 2.3.1's
 //                      per-sub-cube range, used for empty-space skipping).
+//   build_brick_blocks the same blocks for a list of bricks only (the plain
+//                      copies a learned context keeps for its fallback bricks).
+//   launch_brick_error per brick, the largest difference between its decoded
+//                      and its plain block, both clipped from below at a floor.
 //   plan_residency     assign a device slot to every brick a frame renders:
 //                      resident bricks are reused and missing ones take free or
 //                      least recently used slots; when the frame needs more bricks
@@ -25,18 +29,22 @@
 
 namespace vr {
 
-void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
-                       float* store, int64_t slot_floats, float2* minmax) {
-    const int64_t total = (int64_t)nb[0] * nb[1] * nb[2];
+namespace {
+
+// Blocks of bricks ids[i] (or i when ids is null), i < count, into store + i * slot_floats.
+void build_blocks(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3], const int32_t* ids,
+                  int64_t count, float* store, int64_t slot_floats, float2* minmax) {
+    const int64_t total = count;
     const int64_t sx = B[0] + 1, sy = B[1] + 1;
     auto work = [&](int64_t b0, int64_t b1) {
-        for (int64_t id = b0; id < b1; ++id) {
+        for (int64_t i = b0; i < b1; ++i) {
+            const int64_t id = ids ? ids[i] : i;
             const int64_t ix = id % nb[0], iy = (id / nb[0]) % nb[1], iz = id / ((int64_t)nb[0] * nb[1]);
             const int64_t x0 = ix * B[0], y0 = iy * B[1], z0 = iz * B[2];
             const int64_t x1 = std::min<int64_t>(x0 + B[0], n[0] - 1);
             const int64_t y1 = std::min<int64_t>(y0 + B[1], n[1] - 1);
             const int64_t z1 = std::min<int64_t>(z0 + B[2], n[2] - 1);
-            float* blk = store + id * slot_floats;
+            float* blk = store + i * slot_floats;
             std::memset(blk, 0, (size_t)slot_floats * sizeof(float));
             float mn = FLT_MAX, mx = -FLT_MAX;
             for (int64_t z = z0; z <= z1; ++z)
@@ -50,7 +58,7 @@ void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3],
                         mx = std::max(mx, row[x]);
                     }
                 }
-            minmax[id] = make_float2(mn, mx);
+            if (minmax) minmax[i] = make_float2(mn, mx);
         }
     };
     const int64_t threads = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), total));
@@ -58,6 +66,53 @@ void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3],
     for (int64_t t = 0; t < threads; ++t)
         pool.emplace_back(work, total * t / threads, total * (t + 1) / threads);
     for (auto& th : pool) th.join();
+}
+
+// One block of threads per (part of a) brick: the largest clipped difference over
+// the brick's voxels inside the cube, folded into err_bits (non-negative floats
+// order like their bit patterns).
+__global__ void brick_error_kernel(const float* __restrict__ decoded, const float* __restrict__ plain, int64_t first,
+                                   int3 n, int3 B, int3 nb, float floor_v, uint32_t* err_bits) {
+    const int k = blockIdx.y;
+    const int64_t id = first + k;
+    const int ix = (int)(id % nb.x), iy = (int)((id / nb.x) % nb.y), iz = (int)(id / ((int64_t)nb.x * nb.y));
+    // extent of the brick's block inside the cube, per axis: voxels 0 .. e
+    const int ex = min(B.x, n.x - 1 - ix * B.x), ey = min(B.y, n.y - 1 - iy * B.y), ez = min(B.z, n.z - 1 - iz * B.z);
+    const int sx = B.x + 1, sy = B.y + 1;
+    const int64_t V = (int64_t)sx * sy * (B.z + 1);
+    const float* d = decoded + (int64_t)k * V;
+    const float* p = plain + (int64_t)k * V;
+    float m = 0.0f;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < V; q += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(q % sx), y = (int)((q / sx) % sy), z = (int)(q / ((int64_t)sx * sy));
+        if (x <= ex && y <= ey && z <= ez) m = fmaxf(m, fabsf(fmaxf(d[q], floor_v) - fmaxf(p[q], floor_v)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(err_bits + k, __float_as_uint(m));
+}
+
+}  // namespace
+
+void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
+                       float* store, int64_t slot_floats, float2* minmax) {
+    build_blocks(src, n, B, nb, nullptr, (int64_t)nb[0] * nb[1] * nb[2], store, slot_floats, minmax);
+}
+
+void build_brick_blocks(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
+                        const int32_t* ids, int64_t count, float* store, int64_t slot_floats) {
+    build_blocks(src, n, B, nb, ids, count, store, slot_floats, nullptr);
+}
+
+cudaError_t launch_brick_error(const float* decoded, const float* plain, int64_t first, int32_t count,
+                               const int64_t n[3], const int32_t B[3], const int32_t nb[3], float floor_v,
+                               uint32_t* err_bits, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t V = (int64_t)(B[0] + 1) * (B[1] + 1) * (B[2] + 1);
+    const int per_brick = (int)std::min<int64_t>(64, (V + 255) / 256);
+    brick_error_kernel<<<dim3(per_brick, count), 256, 0, s>>>(
+        decoded, plain, first, make_int3((int)n[0], (int)n[1], (int)n[2]), make_int3(B[0], B[1], B[2]),
+        make_int3(nb[0], nb[1], nb[2]), floor_v, err_bits);
+    return cudaGetLastError();
 }
 
 int plan_residency(Residency& r, const std::vector<int32_t>& bricks, int64_t frame, int32_t first_half,

@@ -78,7 +78,8 @@ EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_b
            "vr_codec_destroy", "vr_codec_param_count", "vr_codec_set_params", "vr_codec_get_params",
            "vr_codec_forward", "vr_codec_gradient", "vr_codec_fit_stats", "vr_codec_train",
            "vr_codec_decode_bricks", "vr_codec_get_minmax", "vr_codec_brick_count", "vr_codec_brick_size",
-           "vr_load_cube_codec", "vr_render_noalloc", "vr_last_error"]
+           "vr_load_cube_codec", "vr_set_codec_fallback", "vr_codec_brick_errors", "vr_render_noalloc",
+           "vr_last_error"]
 
 
 class vr_server_stats(ctypes.Structure):
@@ -138,6 +139,8 @@ def _load():
     lib.vr_codec_brick_size.argtypes = [P, P]
     lib.vr_codec_brick_size.restype = None
     lib.vr_load_cube_codec.argtypes = [P, P, I64, I64, I64]
+    lib.vr_set_codec_fallback.argtypes = [P, P, ctypes.c_float, ctypes.c_float]
+    lib.vr_codec_brick_errors.argtypes = [P, P, ctypes.POINTER(I64)]
     lib.vr_codec_train.argtypes = [P, P, I64, I64, I64, I32, I32, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_double)]
     lib.vr_codec_decode_bricks.argtypes = [P, P, P, I32, P, P]
@@ -632,6 +635,28 @@ class VolumeRenderer:
         _check(self.ctx, _lib.vr_load_cube_codec(self.ctx, codec.h, *shape_xyz))
         self.shape_xyz = tuple(int(v) for v in shape_xyz)
         self._host_cube = codec
+
+    def set_codec_fallback(self, cube, bound, floor=-3.4e38):
+        """Bricks of a learned context whose decode error exceeds `bound` are copied
+        from the plain host cube (float32 (nz, ny, nx), kept referenced until the
+        next brick()) instead of decoded; cube=None turns the fallback off."""
+        if cube is None:
+            _check(self.ctx, _lib.vr_set_codec_fallback(self.ctx, None, float(bound), float(floor)))
+            self._fallback_cube = None
+            return
+        if not isinstance(cube, np.ndarray) or cube.dtype != np.float32 or not cube.flags.c_contiguous:
+            raise TypeError("cube must be a C-contiguous float32 numpy array")
+        if tuple(cube.shape[::-1]) != tuple(self.shape_xyz):
+            raise ValueError("the cube's shape differs from the learned context's")
+        _check(self.ctx, _lib.vr_set_codec_fallback(self.ctx, cube.ctypes.data, float(bound), float(floor)))
+        self._fallback_cube = cube
+
+    def codec_brick_errors(self):
+        """(per-brick decode errors, number of bricks that fall back) of the last brick()."""
+        err = np.zeros(self.n_bricks, dtype=np.float32)
+        n = ctypes.c_int64(0)
+        _check(self.ctx, _lib.vr_codec_brick_errors(self.ctx, err.ctypes.data, ctypes.byref(n)))
+        return err, int(n.value)
 
     def load_cube_host(self, cube):
         """Out-of-core: the cube stays in host memory (a reference is kept)."""

@@ -213,3 +213,157 @@ def _render_incore(vr, torch, cube, tf, cam, brick):
         r.set_camera(cam)
         r.set_option(vr.VR_OPT_KERNEL, vr.VR_KERNEL_DIRECT)
         return r.render().cpu().numpy()
+
+
+# ------------------------------------------------ per-brick fallback to plain voxels
+
+def _fallback_case(vr, torch):
+    """A ragged cube (3 x 2 x 2 bricks of 16, the last ones partial) and a codec
+    trained briefly on it, so that the bricks' decode errors spread."""
+    import synth
+    shape, brick = (40, 33, 29), (16, 16, 16)
+    cube = np.zeros(shape[::-1], np.float32)
+    synth.add_sources(cube, synth.line_sources(np.random.default_rng(33), 9, shape, (2.0, 8.0),
+                                               (3.0, 8.0), (3.0, 10.0)))
+    cube += np.random.default_rng(34).normal(0, 0.05, cube.shape).astype(np.float32)
+    nb = 3 * 2 * 2
+    p, lat = ref.init_params(nb, seed=4)
+    c = vr.Codec(nb, brick)
+    c.set_params(c.pack(p, lat), np.zeros(nb), np.ones(nb))
+    dev = torch.from_numpy(cube).cuda()
+    c.fit_stats(dev)
+    th, m, s = c.get_params()
+    c.set_params(th, m, s)
+    c.train(dev, steps=150, batch=4096, lr=3e-3, seed=2)
+    tf = synth.make_tf([0.0, 0.02, 0.05, 0.1, 0.15, 0.2, 0.3, 0.4], lo=0.0, hi=8.0)
+    cam = synth.pose(shape, 0.9, 0.35, 72, 56)
+    return cube, shape, brick, c, tf, cam
+
+
+def _ctx(vr, shape, brick, tf, cam, codec=None, cube=None, fallback=None, budget=0, floor=-3.4e38):
+    r = vr.VolumeRenderer(0)
+    if codec is not None:
+        r.load_cube_codec(codec, shape)
+        if fallback is not None:
+            r.set_codec_fallback(cube, fallback, floor)
+    else:
+        r.load_cube_host(cube)
+    if budget:
+        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget * 17 ** 3 * 4)
+    r.set_option(vr.VR_OPT_SKIP_EMPTY, 0)   # codec and plain ranges may differ
+    r.brick(*brick)
+    r.set_transfer_function(tf)
+    r.set_camera(cam)
+    return r
+
+
+def test_fallback_errors_are_the_decoded_blocks_errors(vr):
+    """The scan's per-brick error is max |max(d, f) - max(v, f)| over the brick's
+    block inside the cube, d from vr_codec_decode_bricks, v the plain cube."""
+    import torch
+    cube, shape, brick, c, tf, cam = _fallback_case(vr, torch)
+    nb = 12
+    ids = torch.arange(nb, dtype=torch.int32, device="cuda")
+    blocks = torch.zeros(nb * 17 ** 3, dtype=torch.float32, device="cuda")
+    c.decode_bricks(ids, blocks)
+    torch.cuda.synchronize()
+    blk = blocks.cpu().numpy().reshape(nb, 17, 17, 17)
+    for floor in (np.float32(-3.4e38), np.float32(0.7)):
+        want = np.zeros(nb, np.float32)
+        for b in range(nb):
+            ix, iy, iz = b % 3, (b // 3) % 2, b // 6
+            x0, y0, z0 = 16 * ix, 16 * iy, 16 * iz
+            v = cube[z0:z0 + 17, y0:y0 + 17, x0:x0 + 17]
+            d = blk[b, :v.shape[0], :v.shape[1], :v.shape[2]]
+            want[b] = np.abs(np.maximum(d, floor) - np.maximum(v, floor)).max()
+        with _ctx(vr, shape, brick, tf, cam, codec=c, cube=cube, fallback=float(np.median(want)),
+                  floor=float(floor)) as r:
+            got, n_plain = r.codec_brick_errors()
+        assert np.array_equal(got, want), (got, want)
+        assert n_plain == int(np.sum(want > np.float32(np.median(want))))
+        assert want.max() > 0
+    c.close()
+
+
+def test_fallback_extremes_equal_plain_streaming_and_pure_decoding(vr):
+    """bound < 0: every brick is copied from its plain block, the image is the
+    out-of-core plain render's bit for bit; bound = inf: the pure learned render."""
+    import torch
+    cube, shape, brick, c, tf, cam = _fallback_case(vr, torch)
+    for budget in (0, 3):
+        with _ctx(vr, shape, brick, tf, cam, cube=cube, budget=budget) as r:
+            plain = r.render().cpu().numpy()
+        with _ctx(vr, shape, brick, tf, cam, codec=c, budget=budget) as r:
+            learned = r.render().cpu().numpy()
+        with _ctx(vr, shape, brick, tf, cam, codec=c, cube=cube, fallback=-1.0, budget=budget) as r:
+            every = r.render().cpu().numpy()
+            assert r.codec_brick_errors()[1] == 12
+            st = r.stats()
+        assert st["device_errors"] == 0 and st["bricks_uploaded"] > 0
+        with _ctx(vr, shape, brick, tf, cam, codec=c, cube=cube, fallback=float("inf"), budget=budget) as r:
+            none = r.render().cpu().numpy()
+            assert r.codec_brick_errors()[1] == 0
+        assert np.array_equal(every, plain)
+        assert np.array_equal(none, learned)
+        assert not np.array_equal(plain, learned)
+        assert plain[..., 3].max() > 0.3
+    c.close()
+
+
+def test_fallback_routes_each_brick(vr):
+    """With the bound at the median error, each brick alone (a one-brick region)
+    renders as the plain render if its error exceeds the bound and as the learned
+    render otherwise; the whole frame is the same with every brick resident and
+    streamed through a 3-slot cache, and closer to the plain image than the pure
+    learned one."""
+    import torch
+    cube, shape, brick, c, tf, cam = _fallback_case(vr, torch)
+    with _ctx(vr, shape, brick, tf, cam, codec=c, cube=cube, fallback=float("inf")) as r:
+        err, _ = r.codec_brick_errors()
+    bound = float(np.median(err))
+    flagged = err > np.float32(bound)
+    assert 0 < flagged.sum() < 12
+    mixed = _ctx(vr, shape, brick, tf, cam, codec=c, cube=cube, fallback=bound)
+    plain = _ctx(vr, shape, brick, tf, cam, cube=cube)
+    learned = _ctx(vr, shape, brick, tf, cam, codec=c)
+    seen = 0
+    for b in range(12):
+        ix, iy, iz = b % 3, (b // 3) % 2, b // 6
+        lo, hi = (ix, iy, iz), (ix + 1, iy + 1, iz + 1)
+        imgs = []
+        for r in (mixed, plain, learned):
+            r.set_region(lo, hi)
+            imgs.append(r.render().cpu().numpy())
+        want = imgs[1] if flagged[b] else imgs[2]
+        assert np.array_equal(imgs[0], want), b
+        seen += int(imgs[0][..., 3].max() > 0)
+    assert seen >= 6
+    full = []
+    for r in (mixed, plain, learned):
+        r.set_region((0, 0, 0), (3, 2, 2))
+        full.append(r.render().cpu().numpy())
+    for r in (mixed, plain, learned):
+        r.close()
+    with _ctx(vr, shape, brick, tf, cam, codec=c, cube=cube, fallback=bound, budget=3) as r:
+        streamed = r.render().cpu().numpy()
+        assert r.stats()["bricks_uploaded"] > 0
+    assert np.array_equal(streamed, full[0])
+    mse = lambda a: float(np.mean((a.astype(np.float64) - full[1]) ** 2))
+    assert mse(full[0]) < mse(full[2])
+    c.close()
+
+
+def test_fallback_errors(vr):
+    import torch
+    cube = np.zeros((20, 20, 20), np.float32)
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(cube).cuda())
+        with pytest.raises(vr.VRError, match="VR_ESTATE"):
+            r.set_codec_fallback(cube, 1.0)
+    with vr.Codec(8, (10, 10, 10)) as c, vr.VolumeRenderer(0) as r:
+        r.load_cube_codec(c, (20, 20, 20))
+        with pytest.raises(vr.VRError, match="VR_EINVAL"):
+            r.set_codec_fallback(cube, float("nan"))
+        r.brick(10, 10, 10)
+        with pytest.raises(vr.VRError, match="VR_ESTATE"):
+            r.codec_brick_errors()     # no fallback was set
