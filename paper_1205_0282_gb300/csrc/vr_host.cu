@@ -91,14 +91,16 @@ void free_ooc(vr_ctx* c) {
 // Side streams and events of the out-of-core pipeline (created once per context).
 int ensure_ooc_streams(vr_ctx* c) {
     if (c->copy_stream) return VR_OK;
-    VR_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    int lo_prio = 0, hi_prio = 0;
+    VR_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    // high priority: a learned context's decodes (kernels on this stream) feed the
+    // ring and should not queue behind the resident bricks' long march
+    VR_CUDA(c, cudaStreamCreateWithPriority(&c->copy_stream, cudaStreamNonBlocking, hi_prio));
     VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_march_done, cudaEventDisableTiming));
     VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_copy_done, cudaEventDisableTiming));
     for (cudaEvent_t& ev : c->ev_half_read) VR_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     // the ring's marches free its halves for the next copies: schedule their
     // blocks ahead of the resident bricks' long launch
-    int lo_prio = 0, hi_prio = 0;
-    VR_CUDA(c, cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
     VR_CUDA(c, cudaStreamCreateWithPriority(&c->ring_stream, cudaStreamNonBlocking, hi_prio));
     VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_start, cudaEventDisableTiming));
     VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_end, cudaEventDisableTiming));
