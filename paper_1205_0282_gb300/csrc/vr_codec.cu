@@ -192,6 +192,28 @@ __device__ __forceinline__ float silu_grad(float t) {
     return s * (1.0f + t * (1.0f - s));
 }
 
+// Column sums of a 32 x 16 block held one row per lane (v = this lane's row):
+// after halving exchanges lane l holds the sum of column colsum16_index(l), each
+// column held by the lane pair (l, l ^ 1).  16 shuffles instead of 16 atomic
+// additions per lane to the same 16 addresses.
+__device__ __forceinline__ int colsum16_index(int lane) {
+    return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+__device__ __forceinline__ float warp_colsum16(float v[16], int lane) {
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const int m = 2 * h;
+        const bool hi = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float keep = hi ? v[i + h] : v[i];
+            const float send = hi ? v[i] : v[i + h];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 __device__ __forceinline__ void store_bf16(unsigned char* base, uint32_t off, float v) {
     *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
 }
@@ -460,24 +482,24 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
             for (int o = 16; o > 0; o >>= 1) d3 += __shfl_xor_sync(0xffffffffu, d3, o);
             if ((tid & 31) == 0 && d3 != 0.0f) atomicAdd(&s_db3, d3);
         }
+        const int lane = tid & 31, col = colsum16_index(lane);
 #pragma unroll 1
         for (int c = 0; c < kHidden; c += 16) {
-            float d[16];
+            float d[16], gg[16];
             tc::tmem_ld16(T_D2 + lane_base + c, d);
 #pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-                float gg[2];
+            for (int i = 0; i < 16; ++i) {
+                const float z2 = d[i] + s_b2[c + i];
+                gg[i] = dy * s_w3[c + i] * silu_grad(z2);
+                d[i] = dy * silu(z2);  // this point's term of dL/dw3
+            }
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const float z2 = d[i + e] + s_b2[c + i + e];
-                    gg[e] = dy * s_w3[c + i + e] * silu_grad(z2);
-                    if (dy != 0.0f) {
-                        atomicAdd(&s_db2[c + i + e], gg[e]);
-                        atomicAdd(&s_dw3[c + i + e], dy * silu(z2));
-                    }
-                }
-                *reinterpret_cast<__nv_bfloat162*>(sm + kOffG2 + tc::kmajor_offset(tid, c + i, kHidden)) =
-                    __floats2bfloat162_rn(gg[0], gg[1]);
+            for (int i = 0; i < 16; i += 8)
+                store_bf16x8(sm + kOffG2 + tc::kmajor_offset(tid, c + i, kHidden), gg + i);
+            const float sb2 = warp_colsum16(gg, lane), sw3 = warp_colsum16(d, lane);
+            if ((lane & 1) == 0) {
+                atomicAdd(&s_db2[c + col], sb2);
+                atomicAdd(&s_dw3[c + col], sw3);
             }
         }
         tc::fence_smem_to_async();
@@ -499,18 +521,20 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
         for (int c = 0; c < kHidden; c += 16) {
             float d[16];
             tc::tmem_ld16(T_D1 + lane_base + c, d);
+            const float* zr = reinterpret_cast<const float*>(sm + kOffZ1) + tid * kHidden + c;
 #pragma unroll
-            for (int i = 0; i < 16; i += 2) {
-                float gg[2];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const float z1 = reinterpret_cast<const float*>(sm + kOffZ1)[tid * kHidden + c + i + e];
-                    gg[e] = d[i + e] * silu_grad(z1);
-                    if (dy != 0.0f) atomicAdd(&s_db1[c + i + e], gg[e]);
-                }
-                *reinterpret_cast<__nv_bfloat162*>(sm + kOffG1 + tc::kmajor_offset(tid, c + i, kHidden)) =
-                    __floats2bfloat162_rn(gg[0], gg[1]);
+            for (int i = 0; i < 16; i += 4) {
+                const float4 z = *reinterpret_cast<const float4*>(zr + i);
+                d[i] *= silu_grad(z.x);
+                d[i + 1] *= silu_grad(z.y);
+                d[i + 2] *= silu_grad(z.z);
+                d[i + 3] *= silu_grad(z.w);
             }
+#pragma unroll
+            for (int i = 0; i < 16; i += 8)
+                store_bf16x8(sm + kOffG1 + tc::kmajor_offset(tid, c + i, kHidden), d + i);
+            const float sb1 = warp_colsum16(d, lane);
+            if ((lane & 1) == 0) atomicAdd(&s_db1[c + col], sb1);
         }
         tc::fence_smem_to_async();
         tc::fence_before_sync();
@@ -533,9 +557,13 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
                 float* gl = g.lat + (int64_t)brick * kNodes * kNodes * kNodes * kLatent;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    float* dst = gl + cr.node[k] * kLatent;
+                    // 16-byte aligned: the latent gradients start on 16 bytes, 16 channels per node
+                    float4* dst = reinterpret_cast<float4*>(gl + cr.node[k] * kLatent);
+                    const float w = cr.w[k];
 #pragma unroll
-                    for (int ch = 0; ch < kLatent; ++ch) atomicAdd(dst + ch, cr.w[k] * d[ch]);
+                    for (int q = 0; q < kLatent / 4; ++q)
+                        atomicAdd(dst + q, make_float4(w * d[4 * q], w * d[4 * q + 1], w * d[4 * q + 2],
+                                                       w * d[4 * q + 3]));
                 }
             }
         }
@@ -594,6 +622,9 @@ namespace codec {
 constexpr int64_t kOfsW1 = 0, kOfsB1 = kOfsW1 + kHidden * kIn, kOfsW2 = kOfsB1 + kHidden,
                   kOfsB2 = kOfsW2 + kHidden * kHidden, kOfsW3 = kOfsB2 + kHidden, kOfsB3 = kOfsW3 + kHidden,
                   kOfsLat = kOfsB3 + 1;
+// floats in front of the gradient vector so that its latent part starts on 16 bytes
+// (the latent gradients are accumulated four channels at a time)
+constexpr int64_t kGradPad = (4 - kOfsLat % 4) % 4;
 constexpr int64_t kLatPerBrick = (int64_t)kNodes * kNodes * kNodes * kLatent;
 
 __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
@@ -741,7 +772,8 @@ struct vr_codec {
     int32_t B[3] = {0, 0, 0};
     int64_t n_params = 0;
     float* theta = nullptr;  // FP32 parameters
-    float* grad = nullptr;
+    float* grad = nullptr;       // grad_mem + kGradPad: the latents' gradients 16-byte aligned
+    float* grad_mem = nullptr;
     float* adam1 = nullptr;
     float* adam2 = nullptr;
     __nv_bfloat16* W1h = nullptr;
@@ -875,7 +907,8 @@ int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
     for (int a = 0; a < 3; ++a) c->B[a] = B[a];
     c->n_params = kOfsLat + (int64_t)n_bricks * kLatPerBrick;
     const size_t pb = (size_t)c->n_params * sizeof(float);
-    bool ok = cudaMalloc(&c->theta, pb) == cudaSuccess && cudaMalloc(&c->grad, pb) == cudaSuccess &&
+    bool ok = cudaMalloc(&c->theta, pb) == cudaSuccess &&
+              cudaMalloc(&c->grad_mem, pb + kGradPad * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&c->adam1, pb) == cudaSuccess && cudaMalloc(&c->adam2, pb) == cudaSuccess &&
               cudaMalloc(&c->W1h, kHidden * kIn * 2) == cudaSuccess &&
               cudaMalloc(&c->W2h, kHidden * kHidden * 2) == cudaSuccess &&
@@ -884,6 +917,7 @@ int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
               cudaMalloc(&c->s, n_bricks * 4) == cudaSuccess && cudaMalloc(&c->minmax, n_bricks * 8) == cudaSuccess &&
               cudaMalloc(&c->loss, sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->err, sizeof(int)) == cudaSuccess;
+    if (ok) c->grad = c->grad_mem + kGradPad;
     if (ok) ok = cudaMemset(c->theta, 0, pb) == cudaSuccess && cudaMemset(c->adam1, 0, pb) == cudaSuccess &&
                  cudaMemset(c->adam2, 0, pb) == cudaSuccess && cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
@@ -897,7 +931,7 @@ int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
 
 void vr_codec_destroy(vr_codec* c) {
     if (!c) return;
-    for (void* p : {(void*)c->theta, (void*)c->grad, (void*)c->adam1, (void*)c->adam2, (void*)c->W1h, (void*)c->W2h,
+    for (void* p : {(void*)c->theta, (void*)c->grad_mem, (void*)c->adam1, (void*)c->adam2, (void*)c->W1h, (void*)c->W2h,
                     (void*)c->lath, (void*)c->w3r, (void*)c->m, (void*)c->s, (void*)c->minmax, (void*)c->loss,
                     (void*)c->err, (void*)c->active, (void*)c->d_count, (void*)c->shown,
                     (void*)c->pts, (void*)c->tgt})
