@@ -22,9 +22,32 @@ namespace vr {
 
 namespace texm {
 
-// resident CTAs per SM the kernels are compiled for: 20 (48 registers a thread)
-// for FP32/FP16 storage, 16 (64 registers) for FP8, whose decode needs a few more
-constexpr int tex_blocks_per_sm(int prec) { return prec == kPrecF8 ? 16 : 20; }
+#ifndef VR_TEX_DEPTH_F32
+#define VR_TEX_DEPTH_F32 2
+#endif
+#ifndef VR_TEX_BLOCKS_F32
+#define VR_TEX_BLOCKS_F32 14
+#endif
+#ifndef VR_TEX_DEPTH_F16
+#define VR_TEX_DEPTH_F16 1
+#endif
+#ifndef VR_TEX_BLOCKS_F16
+#define VR_TEX_BLOCKS_F16 20
+#endif
+#ifndef VR_TEX_DEPTH_F8
+#define VR_TEX_DEPTH_F8 1
+#endif
+#ifndef VR_TEX_BLOCKS_F8
+#define VR_TEX_BLOCKS_F8 16
+#endif
+// samples whose gathers are in flight ahead of the one being composited
+__host__ __device__ constexpr int tex_depth(int prec) {
+    return prec == kPrecF8 ? VR_TEX_DEPTH_F8 : (prec == kPrecF16 ? VR_TEX_DEPTH_F16 : VR_TEX_DEPTH_F32);
+}
+// resident CTAs per SM the kernels are compiled for
+__host__ __device__ constexpr int tex_blocks_per_sm(int prec) {
+    return prec == kPrecF8 ? VR_TEX_BLOCKS_F8 : (prec == kPrecF16 ? VR_TEX_BLOCKS_F16 : VR_TEX_BLOCKS_F32);
+}
 
 // Layered texture of the sweep axis S: layer index = coordinate along S, texel
 // (x, y) = coordinates along (U, V) with U < V the two other axes.
@@ -208,11 +231,9 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
             }
         }
     };
-    Corners nxt;
-    if (fk < fn) fetch(fk, nxt);
-    while (fk < fn) {
-        Corners cur = nxt;
-        if (fk + 1.0f < fn) fetch(fk + 1.0f, nxt);
+    // One sample: interpolate the fetched corners, look up and correct the
+    // transfer function, composite, stop at alpha >= tau.
+    auto consume = [&](Corners& cur) {
         decode(cur);
         const float e00 = fmaf(cur.fu, cur.c[1] - cur.c[0], cur.c[0]);
         const float e10 = fmaf(cur.fu, cur.c[3] - cur.c[2], cur.c[2]);
@@ -231,6 +252,40 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         acc.w += w;
         fk += 1.0f;
         if (acc.w >= tau) fn = fk;
+    };
+    // Software pipeline of depth D: the gathers of sample k + D are issued before
+    // sample k is composited, so D samples' texture reads are in flight per ray.
+    // Inside the loop the gathers are unconditional: the last D of a segment read
+    // points up to D steps past its end, which texture addressing clamps (a texture
+    // read never faults), and their values are never used.
+    constexpr int D = tex_depth(PREC);
+    if constexpr (D == 1) {
+        Corners nxt;
+        if (fk < fn) fetch(fk, nxt);
+        while (fk < fn) {
+            Corners cur = nxt;
+            fetch(fk + 1.0f, nxt);
+            consume(cur);
+        }
+    } else {
+        // D + 1 corner buffers in a ring indexed by compile-time constants (the
+        // loop body is unrolled D + 1 times), so that no buffer is copied: a copy
+        // of a buffer whose gathers are still in flight would wait for them.
+        Corners ring[D + 1];
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            if (fk + (float)d < fn) fetch(fk + (float)d, ring[d]);
+        bool live = fk < fn;
+        while (live) {
+#pragma unroll
+            for (int r = 0; r <= D; ++r) {
+                if (live) {
+                    fetch(fk + (float)D, ring[(r + D) % (D + 1)]);
+                    consume(ring[r]);
+                    live = fk < fn;
+                }
+            }
+        }
     }
     p.frags[(int64_t)item.frag * kTilePixels + threadIdx.x] = acc;
     unsigned long long t = (unsigned long long)fk;
@@ -392,7 +447,7 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
     // compiled for (each also reserves 1 KB); the rest of the SM's 256 KB array is
     // L1/texture cache
     auto go = [&](auto kern) {
-        const int blocks = texm::tex_blocks_per_sm(p.precision == kPrecF8 ? kPrecF8 : kPrecF32);
+        const int blocks = texm::tex_blocks_per_sm(p.precision);
         const int pct = (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2;
         static int carveout = -1;
         if (carveout != pct) {
@@ -401,20 +456,21 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
         }
         kern<<<p.n_items, kTilePixels, smem, s>>>(p);
     };
+    auto by_tf = [&](auto uniform_kern, auto general_kern) {
+        if (p.tf_uniform) go(uniform_kern);
+        else go(general_kern);
+    };
+    using namespace texm;
     if (p.step_mode) {  // the dynamic step (any storage; uniform or not)
-        if (p.precision == kPrecF8) {
-            if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF8, true>);
-            else go(texm::march_tex_kernel<false, kPrecF8, true>);
-        } else {
-            if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF32, true>);
-            else go(texm::march_tex_kernel<false, kPrecF32, true>);
-        }
+        if (p.precision == kPrecF8) by_tf(march_tex_kernel<true, kPrecF8, true>, march_tex_kernel<false, kPrecF8, true>);
+        else if (p.precision == kPrecF16) by_tf(march_tex_kernel<true, kPrecF16, true>, march_tex_kernel<false, kPrecF16, true>);
+        else by_tf(march_tex_kernel<true, kPrecF32, true>, march_tex_kernel<false, kPrecF32, true>);
     } else if (p.precision == kPrecF8) {
-        if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF8, false>);
-        else go(texm::march_tex_kernel<false, kPrecF8, false>);
-    } else {  // FP32 and FP16 textures share the kernel
-        if (p.tf_uniform) go(texm::march_tex_kernel<true, kPrecF32, false>);
-        else go(texm::march_tex_kernel<false, kPrecF32, false>);
+        by_tf(march_tex_kernel<true, kPrecF8, false>, march_tex_kernel<false, kPrecF8, false>);
+    } else if (p.precision == kPrecF16) {
+        by_tf(march_tex_kernel<true, kPrecF16, false>, march_tex_kernel<false, kPrecF16, false>);
+    } else {
+        by_tf(march_tex_kernel<true, kPrecF32, false>, march_tex_kernel<false, kPrecF32, false>);
     }
     return cudaGetLastError();
 }
@@ -423,7 +479,7 @@ cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
     const size_t smem = (size_t)(p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
     auto go = [&](auto kern) {
-        const int blocks = texm::tex_blocks_per_sm(p.precision == kPrecF8 ? kPrecF8 : kPrecF32);
+        const int blocks = texm::tex_blocks_per_sm(p.precision);
         const int pct = (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2;
         static int carveout = -1;
         if (carveout != pct) {
@@ -432,12 +488,16 @@ cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
         }
         kern<<<p.n_items, kTilePixels, smem, s>>>(p);
     };
+    using namespace texm;
     if (p.precision == kPrecF8) {
-        if (p.tf_uniform) go(texm::march_tex_batch_kernel<true, kPrecF8>);
-        else go(texm::march_tex_batch_kernel<false, kPrecF8>);
+        if (p.tf_uniform) go(march_tex_batch_kernel<true, kPrecF8>);
+        else go(march_tex_batch_kernel<false, kPrecF8>);
+    } else if (p.precision == kPrecF16) {
+        if (p.tf_uniform) go(march_tex_batch_kernel<true, kPrecF16>);
+        else go(march_tex_batch_kernel<false, kPrecF16>);
     } else {
-        if (p.tf_uniform) go(texm::march_tex_batch_kernel<true, kPrecF32>);
-        else go(texm::march_tex_batch_kernel<false, kPrecF32>);
+        if (p.tf_uniform) go(march_tex_batch_kernel<true, kPrecF32>);
+        else go(march_tex_batch_kernel<false, kPrecF32>);
     }
     return cudaGetLastError();
 }
