@@ -29,10 +29,10 @@ namespace texm {
 #define VR_TEX_BLOCKS_F32 14
 #endif
 #ifndef VR_TEX_DEPTH_F16
-#define VR_TEX_DEPTH_F16 1
+#define VR_TEX_DEPTH_F16 2
 #endif
 #ifndef VR_TEX_BLOCKS_F16
-#define VR_TEX_BLOCKS_F16 20
+#define VR_TEX_BLOCKS_F16 14
 #endif
 #ifndef VR_TEX_DEPTH_F8
 #define VR_TEX_DEPTH_F8 1
@@ -40,11 +40,14 @@ namespace texm {
 #ifndef VR_TEX_BLOCKS_F8
 #define VR_TEX_BLOCKS_F8 16
 #endif
-// samples whose gathers are in flight ahead of the one being composited
+// Samples whose gathers are in flight ahead of the one being composited, and
+// resident CTAs per SM the kernels are compiled for (14: 72 registers a thread;
+// 16: 64).  Measured on the 1080p orbit of the 8 GiB cube: two samples ahead at
+// 14 CTAs beat one ahead at 16-20 for FP32 and FP16 storage; FP8, whose decode
+// needs more registers per buffer, is fastest one ahead at 16.
 __host__ __device__ constexpr int tex_depth(int prec) {
     return prec == kPrecF8 ? VR_TEX_DEPTH_F8 : (prec == kPrecF16 ? VR_TEX_DEPTH_F16 : VR_TEX_DEPTH_F32);
 }
-// resident CTAs per SM the kernels are compiled for
 __host__ __device__ constexpr int tex_blocks_per_sm(int prec) {
     return prec == kPrecF8 ? VR_TEX_BLOCKS_F8 : (prec == kPrecF16 ? VR_TEX_BLOCKS_F16 : VR_TEX_BLOCKS_F32);
 }
@@ -138,7 +141,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         imax[a] = min(p.B[a] - 1, p.n[a] - 2 - O[a]);
     }
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    float fk = 0.0f, fn = 0.0f;
+    float fn = 0.0f;  // samples this ray owes the brick (after termination: those composited)
     float qs[3] = {0, 0, 0}, dq[3] = {0, 0, 0};
     float dt_ray = 0.0f;  // dynamic step: this ray's spacing (voxels)
     {
@@ -231,9 +234,14 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
             }
         }
     };
-    // One sample: interpolate the fetched corners, look up and correct the
-    // transfer function, composite, stop at alpha >= tau.
-    auto consume = [&](Corners& cur) {
+    // Step fi of the march: interpolate the fetched corners, look up and correct
+    // the transfer function and composite sample fi if it is still owed (fi < fn;
+    // fn drops to the terminating sample's index + 1 when alpha reaches tau).  A
+    // step past the end composites with weight 0, which leaves acc unchanged: the
+    // gathered values are finite (clamped texture reads) and the transfer-function
+    // index is clamped, so col and alpha are finite too.
+    float fi = 0.0f;
+    auto step = [&](Corners& cur) {
         decode(cur);
         const float e00 = fmaf(cur.fu, cur.c[1] - cur.c[0], cur.c[0]);
         const float e10 = fmaf(cur.fu, cur.c[3] - cur.c[2], cur.c[2]);
@@ -245,50 +253,36 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         if (PREC == kPrecF8) val *= k0;
         const float4 col = tf_lookup<UNIFORM>(p, s_rgba, s_v, val);
         const float alpha = DYN ? opacity_correct_dt(col.w, dt_ray) : opacity_correct(p, col.w);
-        const float w = (1.0f - acc.w) * alpha;
+        const bool owed = fi < fn;
+        const float w = owed ? (1.0f - acc.w) * alpha : 0.0f;
         acc.x = fmaf(w, col.x, acc.x);
         acc.y = fmaf(w, col.y, acc.y);
         acc.z = fmaf(w, col.z, acc.z);
         acc.w += w;
-        fk += 1.0f;
-        if (acc.w >= tau) fn = fk;
+        if (owed && acc.w >= tau) fn = fi + 1.0f;
+        fi += 1.0f;
     };
     // Software pipeline of depth D: the gathers of sample k + D are issued before
     // sample k is composited, so D samples' texture reads are in flight per ray.
-    // Inside the loop the gathers are unconditional: the last D of a segment read
-    // points up to D steps past its end, which texture addressing clamps (a texture
-    // read never faults), and their values are never used.
+    // The D + 1 corner buffers form a ring indexed by compile-time constants: the
+    // loop body is D + 1 straight-line steps, so that no buffer is copied (a copy of
+    // a buffer whose gathers are in flight would wait for them) and the steps'
+    // independent arithmetic can overlap.  The gathers are unconditional: those
+    // past a segment's end read points up to 2D steps beyond it, which texture
+    // addressing clamps (a texture read never faults).
     constexpr int D = tex_depth(PREC);
-    if constexpr (D == 1) {
-        Corners nxt;
-        if (fk < fn) fetch(fk, nxt);
-        while (fk < fn) {
-            Corners cur = nxt;
-            fetch(fk + 1.0f, nxt);
-            consume(cur);
-        }
-    } else {
-        // D + 1 corner buffers in a ring indexed by compile-time constants (the
-        // loop body is unrolled D + 1 times), so that no buffer is copied: a copy
-        // of a buffer whose gathers are still in flight would wait for them.
-        Corners ring[D + 1];
+    Corners ring[D + 1];
 #pragma unroll
-        for (int d = 0; d < D; ++d)
-            if (fk + (float)d < fn) fetch(fk + (float)d, ring[d]);
-        bool live = fk < fn;
-        while (live) {
+    for (int d = 0; d < D; ++d) fetch((float)d, ring[d]);
+    while (fi < fn) {
 #pragma unroll
-            for (int r = 0; r <= D; ++r) {
-                if (live) {
-                    fetch(fk + (float)D, ring[(r + D) % (D + 1)]);
-                    consume(ring[r]);
-                    live = fk < fn;
-                }
-            }
+        for (int r = 0; r <= D; ++r) {
+            fetch(fi + (float)D, ring[(r + D) % (D + 1)]);
+            step(ring[r]);
         }
     }
     p.frags[(int64_t)item.frag * kTilePixels + threadIdx.x] = acc;
-    unsigned long long t = (unsigned long long)fk;
+    unsigned long long t = (unsigned long long)fn;
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if ((threadIdx.x & 31) == 0 && t) atomicAdd(&p.stats->samples, t);
 }
