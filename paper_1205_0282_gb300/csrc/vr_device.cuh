@@ -10,9 +10,11 @@ namespace vr {
 
 // ------------------------------------------------------------------ ray set-up
 
-// Ray of pixel (i, j) in double-float: unit direction d, entry point pe and the
-// sample count n = #{k >= 0 : k dt < t1 - t0}.  Returns false if the ray misses
-// the domain [0, n-1]^3.
+// Ray of pixel (i, j) in double-float: unit direction d, entry point pe, the
+// sample count n = #{k >= 0 : k dt < t1 - t0} and inv_D[a] = 1 / (dt d[a]) (0 where
+// d[a] = 0), which brick_range multiplies by instead of dividing.  Returns false if
+// the ray misses the domain [0, n-1]^3.  Four df divisions per ray (1 / |d| and one
+// reciprocal per axis); every other quotient is a product with a reciprocal.
 // Cam: FrameParams (one frame) or FrameCam (a frame of a batch): eye, f, r, u, qx, qy.
 // dt: the ray's sample spacing, p.dt, or with the dynamic step (DYN, Section
 // 2.3.2's discrete ray casting) p.dt / max_a |d_a|, so that successive samples
@@ -20,13 +22,17 @@ namespace vr {
 // after the entry.
 template <bool DYN = false, class Cam = FrameParams>
 __device__ __forceinline__ bool setup_ray(const FrameParams& p, const Cam& cam, int i, int j, df d[3], df pe[3],
-                                          int& n_samples, df& dt) {
+                                          int& n_samples, df& dt, df inv_D[3]) {
     const df qx = cam.qx[i], qy = cam.qy[j];
     df dun[3];
     for (int a = 0; a < 3; ++a) dun[a] = df_add(df_add(cam.f[a], df_mul(qx, cam.r[a])), df_mul(qy, cam.u[a]));
     df n2 = df_add(df_add(df_mul(dun[0], dun[0]), df_mul(dun[1], dun[1])), df_mul(dun[2], dun[2]));
-    df len = df_sqrt(n2);
-    for (int a = 0; a < 3; ++a) d[a] = df_div(dun[a], len);
+    const df inv_len = df_div(df_make(1.0f), df_sqrt(n2));
+    df inv_d[3];
+    for (int a = 0; a < 3; ++a) {
+        d[a] = df_mul(dun[a], inv_len);
+        inv_d[a] = df_is_zero(d[a]) ? df_make(0.0f) : df_div(df_make(1.0f), d[a]);
+    }
 
     df tn = df_make(-FLT_MAX), tf = df_make(FLT_MAX);
     for (int a = 0; a < 3; ++a) {
@@ -35,59 +41,67 @@ __device__ __forceinline__ bool setup_ray(const FrameParams& p, const Cam& cam, 
             if (df_lt(cam.eye[a], df_make(0.0f)) || df_gt(cam.eye[a], hi)) return false;
             continue;
         }
-        df ta = df_div(df_neg(cam.eye[a]), d[a]);
-        df tb = df_div(df_sub(hi, cam.eye[a]), d[a]);
+        df ta = df_mul(df_neg(cam.eye[a]), inv_d[a]);
+        df tb = df_mul(df_sub(hi, cam.eye[a]), inv_d[a]);
         tn = df_max(tn, df_min(ta, tb));
         tf = df_min(tf, df_max(ta, tb));
     }
     df t0 = df_max(tn, df_make(0.0f));
     if (!df_gt(tf, t0)) return false;
     dt = p.dt;
+    df inv_dt = p.inv_dt;
     if (DYN) {
         // |d| along the dominant axis (selects, no indexed access); the first
         // sample sits half a step after the entry
-        df dm = d[0];
-        if (fabsf(d[1].hi) > fabsf(dm.hi)) dm = d[1];
-        if (fabsf(d[2].hi) > fabsf(dm.hi)) dm = d[2];
-        dt = df_div(p.dt, dm.hi < 0.0f ? df_neg(dm) : dm);
+        df dm = d[0], inv_dm = inv_d[0];
+        if (fabsf(d[1].hi) > fabsf(dm.hi)) { dm = d[1]; inv_dm = inv_d[1]; }
+        if (fabsf(d[2].hi) > fabsf(dm.hi)) { dm = d[2]; inv_dm = inv_d[2]; }
+        if (dm.hi < 0.0f) { dm = df_neg(dm); inv_dm = df_neg(inv_dm); }
+        dt = df_mul(p.dt, inv_dm);
+        inv_dt = df_mul(dm, p.inv_dt);
         t0 = df_add(t0, df_mul_f(dt, 0.5f));
         if (!df_gt(tf, t0)) return false;
     }
     const df L = df_sub(tf, t0);
-    n_samples = (int)df_ceil(df_div(L, dt));
-    for (int a = 0; a < 3; ++a) pe[a] = df_add(cam.eye[a], df_mul(t0, d[a]));
+    n_samples = (int)df_ceil(df_mul(L, inv_dt));
+    for (int a = 0; a < 3; ++a) {
+        pe[a] = df_add(cam.eye[a], df_mul(t0, d[a]));
+        inv_D[a] = df_mul(inv_d[a], inv_dt);
+    }
     return n_samples > 0;
 }
 
 template <bool DYN = false>
 __device__ __forceinline__ bool setup_ray(const FrameParams& p, int i, int j, df d[3], df pe[3], int& n_samples,
-                                          df& dt) {
-    return setup_ray<DYN>(p, p, i, j, d, pe, n_samples, dt);
+                                          df& dt, df inv_D[3]) {
+    return setup_ray<DYN>(p, p, i, j, d, pe, n_samples, dt, inv_D);
 }
 
 // Sample range [klo, khi) owned by brick bidx (sample p_k = pe + k dt d belongs to
 // brick floor(p/B) per axis, first and last bricks open towards the outside).
+// The crossing index of the plane x_a = O is (O - pe_a) / (dt d_a), formed as a
+// product with inv_D[a]; a face shared by two bricks gives both the same value.
 __device__ __forceinline__ void brick_range(const FrameParams& p, const int bidx[3], const df d[3], const df pe[3],
-                            int n_samples, const df& dt, int& klo, int& khi) {
+                                            int n_samples, const df inv_D[3], int& klo, int& khi) {
     float lo = 0.0f, hi = (float)n_samples;
     for (int a = 0; a < 3; ++a) {
-        const df D = df_mul(dt, d[a]);
+        const float dir = d[a].hi;
         const float O = (float)(bidx[a] * p.B[a]);
         const float OB = (float)(bidx[a] * p.B[a] + p.B[a]);
         if (bidx[a] > 0) {
-            if (D.hi > 0.0f) {
-                lo = fmaxf(lo, df_ceil(df_div(df_sub(df_make(O), pe[a]), D)));
-            } else if (D.hi < 0.0f) {
-                hi = fminf(hi, df_floor(df_div(df_sub(df_make(O), pe[a]), D)) + 1.0f);
+            if (dir > 0.0f) {
+                lo = fmaxf(lo, df_ceil(df_mul(df_sub(df_make(O), pe[a]), inv_D[a])));
+            } else if (dir < 0.0f) {
+                hi = fminf(hi, df_floor(df_mul(df_sub(df_make(O), pe[a]), inv_D[a])) + 1.0f);
             } else if (df_lt(pe[a], df_make(O))) {
                 hi = -1.0f;
             }
         }
         if (bidx[a] < p.nb[a] - 1) {
-            if (D.hi > 0.0f) {
-                hi = fminf(hi, df_ceil(df_div(df_sub(df_make(OB), pe[a]), D)));
-            } else if (D.hi < 0.0f) {
-                lo = fmaxf(lo, df_floor(df_div(df_sub(df_make(OB), pe[a]), D)) + 1.0f);
+            if (dir > 0.0f) {
+                hi = fminf(hi, df_ceil(df_mul(df_sub(df_make(OB), pe[a]), inv_D[a])));
+            } else if (dir < 0.0f) {
+                lo = fmaxf(lo, df_floor(df_mul(df_sub(df_make(OB), pe[a]), inv_D[a])) + 1.0f);
             } else if (!df_lt(pe[a], df_make(OB))) {
                 hi = -1.0f;
             }

@@ -818,6 +818,7 @@ void fill_common_params(vr_ctx* c, vr::FrameParams& p) {
         p.nb[a] = c->nb[a];
     }
     p.dt = vr::df_from_double(c->cam.step);
+    p.inv_dt = vr::df_from_double(1.0 / c->cam.step);
     p.dt_f = (float)c->cam.step;
     p.step_mode = c->step_mode;
     p.tau = (float)c->cam.term_alpha;

@@ -64,6 +64,7 @@ struct FrameParams {
     int32_t width, height, tiles_x, tiles_y;
     int32_t tile;   // tile edge in pixels (fragments hold tile*tile pixels)
     df dt;          // step (voxels)
+    df inv_dt;      // 1 / dt
     int32_t step_mode;  // 0: fixed step dt; 1: dynamic (dt along the ray's dominant axis)
     float dt_f;
     float tau;      // termination opacity

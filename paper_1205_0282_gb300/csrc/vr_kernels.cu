@@ -89,11 +89,11 @@ __global__ void __launch_bounds__(kTilePixels) march_kernel(const FrameParams p)
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float vmax = -FLT_MAX;
     int taken = 0;
-    df d[3], pe[3], dt;
+    df d[3], pe[3], dt, inv_D[3];
     int n_samples = 0;
-    if (i < p.width && j < p.height && setup_ray<DYN>(p, i, j, d, pe, n_samples, dt)) {
+    if (i < p.width && j < p.height && setup_ray<DYN>(p, i, j, d, pe, n_samples, dt, inv_D)) {
         int klo, khi;
-        brick_range(p, bidx, d, pe, n_samples, dt, klo, khi);
+        brick_range(p, bidx, d, pe, n_samples, inv_D, klo, khi);
         const float dt_ray = df_to_float(dt);
         if (khi > klo) {
             int O[3], imax[3];

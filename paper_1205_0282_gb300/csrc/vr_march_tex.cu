@@ -52,6 +52,37 @@ __host__ __device__ constexpr int tex_blocks_per_sm(int prec) {
     return prec == kPrecF8 ? VR_TEX_BLOCKS_F8 : (prec == kPrecF16 ? VR_TEX_BLOCKS_F16 : VR_TEX_BLOCKS_F32);
 }
 
+// Transfer-function colour at v from the control points rgba[] and their forward
+// differences drgba[k] = rgba[k + 1] - rgba[k] (formed in FP32 once per CTA, so
+// rgba[k] + w drgba[k] rounds exactly like the per-sample lerp of two points).
+template <bool UNIFORM>
+__device__ __forceinline__ float4 tf_lerp(const FrameParams& p, const float4* __restrict__ rgba,
+                                          const float4* __restrict__ drgba, const float* __restrict__ vals,
+                                          float v) {
+    int seg;
+    float w;
+    if (UNIFORM) {
+        // drgba[tf_n - 1] = 0 (rgba[tf_n] repeats the last point): x = tf_n - 1 needs
+        // no segment clamp
+        float x = (v - p.tf_v0) * p.tf_inv_dv;
+        x = fminf(fmaxf(x, 0.0f), (float)(p.tf_n - 1));
+        seg = __float2int_rz(x);
+        w = x - (float)seg;
+    } else {
+        int lo = 0, hi = p.tf_n - 1;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (v >= vals[mid]) lo = mid;
+            else hi = mid;
+        }
+        seg = lo;
+        w = (v - vals[seg]) / (vals[seg + 1] - vals[seg]);
+        w = fminf(fmaxf(w, 0.0f), 1.0f);
+    }
+    const float4 c0 = rgba[seg], d = drgba[seg];
+    return make_float4(fmaf(w, d.x, c0.x), fmaf(w, d.y, c0.y), fmaf(w, d.z, c0.z), fmaf(w, d.w, c0.w));
+}
+
 // Layered texture of the sweep axis S: layer index = coordinate along S, texel
 // (x, y) = coordinates along (U, V) with U < V the two other axes.
 template <int S>
@@ -125,7 +156,7 @@ __device__ __forceinline__ int step_of(const FrameParams& p, int a) {
 
 template <int S, bool UNIFORM, int PREC, bool DYN, class Cam>
 __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam, const Item& item,
-                                           const float4* s_rgba, const float* s_v) {
+                                           const float4* s_rgba, const float4* s_drgba, const float* s_v) {
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
     const cudaTextureObject_t tex = p.tex[S];
     const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
@@ -145,11 +176,11 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
     float qs[3] = {0, 0, 0}, dq[3] = {0, 0, 0};
     float dt_ray = 0.0f;  // dynamic step: this ray's spacing (voxels)
     {
-        df d[3], pe[3], dt;
+        df d[3], pe[3], dt, inv_D[3];
         int n_samples = 0;
-        if (i < cam.width && j < cam.height && setup_ray<DYN>(p, cam, i, j, d, pe, n_samples, dt)) {
+        if (i < cam.width && j < cam.height && setup_ray<DYN>(p, cam, i, j, d, pe, n_samples, dt, inv_D)) {
             int klo, khi;
-            brick_range(p, bidx, d, pe, n_samples, dt, klo, khi);
+            brick_range(p, bidx, d, pe, n_samples, inv_D, klo, khi);
             if (DYN) dt_ray = df_to_float(dt);
             if (khi > klo) {
                 fn = (float)(khi - klo);
@@ -196,11 +227,15 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         const float qS = fmaf(f, dq[S], qs[S]);
         const float qU = fmaf(f, dq[U], qs[U]);
         const float qV = fmaf(f, dq[V], qs[V]);
-        // samples sit inside the brick up to rounding: truncation is the floor for
-        // q > -1; the lattice clamp matters only at the far face
-        const int ps = min(__float2int_rz(qS), imax[S]);
-        const int iu = min(__float2int_rz(qU), imax[U]);
-        const int iv = min(__float2int_rz(qV), imax[V]);
+        // Samples sit inside the brick up to rounding: truncation is the floor for
+        // q > -1.  A sample on the brick's far face (q = B: the cube's far face, or
+        // rounding) has cell index B and weight 0 on its +1 corners, which FP32 and
+        // FP16 read from the global texture (at a clamped coordinate beyond the
+        // cube).  FP8 clamps the index to the lattice instead, since its +1 corners
+        // are rescaled by the scale of the brick that owns them.
+        const int ps = PREC == kPrecF8 ? min(__float2int_rz(qS), imax[S]) : __float2int_rz(qS);
+        const int iu = PREC == kPrecF8 ? min(__float2int_rz(qU), imax[U]) : __float2int_rz(qU);
+        const int iv = PREC == kPrecF8 ? min(__float2int_rz(qV), imax[V]) : __float2int_rz(qV);
         s.fs = qS - (float)ps;
         s.fu = qU - (float)iu;
         s.fv = qV - (float)iv;
@@ -251,7 +286,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         const float e1 = fmaf(cur.fv, e11 - e01, e01);
         float val = fmaf(cur.fs, e1 - e0, e0);
         if (PREC == kPrecF8) val *= k0;
-        const float4 col = tf_lookup<UNIFORM>(p, s_rgba, s_v, val);
+        const float4 col = tf_lerp<UNIFORM>(p, s_rgba, s_drgba, s_v, val);
         const float alpha = DYN ? opacity_correct_dt(col.w, dt_ray) : opacity_correct(p, col.w);
         const bool owed = fi < fn;
         const float w = owed ? (1.0f - acc.w) * alpha : 0.0f;
@@ -293,17 +328,23 @@ template <bool UNIFORM, int PREC, bool DYN>
 __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_kernel(const FrameParams p) {
     extern __shared__ float4 s_dyn[];
     float4* s_rgba = s_dyn;
-    float* s_v = reinterpret_cast<float*>(s_dyn + p.tf_n + 1);
+    float4* s_drgba = s_dyn + p.tf_n + 1;
+    float* s_v = reinterpret_cast<float*>(s_drgba + p.tf_n);
     for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
-        s_rgba[k] = p.tf_rgba[k];
-        if (k < p.tf_n) s_v[k] = p.tf_v[k];
+        const float4 c = p.tf_rgba[k];
+        s_rgba[k] = c;
+        if (k < p.tf_n) {
+            const float4 c1 = p.tf_rgba[k + 1];
+            s_drgba[k] = make_float4(c1.x - c.x, c1.y - c.y, c1.z - c.z, c1.w - c.w);
+            s_v[k] = p.tf_v[k];
+        }
     }
     __syncthreads();
     const Item item = p.items[blockIdx.x];
     switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_v); break;
-        case 1: march_item<1, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_v); break;
-        default: march_item<2, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_v); break;
+        case 0: march_item<0, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v); break;
+        case 1: march_item<1, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v); break;
+        default: march_item<2, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v); break;
     }
 }
 
@@ -313,18 +354,24 @@ template <bool UNIFORM, int PREC>
 __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_batch_kernel(const FrameParams p) {
     extern __shared__ float4 s_dyn[];
     float4* s_rgba = s_dyn;
-    float* s_v = reinterpret_cast<float*>(s_dyn + p.tf_n + 1);
+    float4* s_drgba = s_dyn + p.tf_n + 1;
+    float* s_v = reinterpret_cast<float*>(s_drgba + p.tf_n);
     for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
-        s_rgba[k] = p.tf_rgba[k];
-        if (k < p.tf_n) s_v[k] = p.tf_v[k];
+        const float4 c = p.tf_rgba[k];
+        s_rgba[k] = c;
+        if (k < p.tf_n) {
+            const float4 c1 = p.tf_rgba[k + 1];
+            s_drgba[k] = make_float4(c1.x - c.x, c1.y - c.y, c1.z - c.z, c1.w - c.w);
+            s_v[k] = p.tf_v[k];
+        }
     }
     __syncthreads();
     const Item item = p.items[blockIdx.x];
     const FrameCam& cam = p.cams[item.sweep >> 3];
     switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_v); break;
-        case 1: march_item<1, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_v); break;
-        default: march_item<2, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_v); break;
+        case 0: march_item<0, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v); break;
+        case 1: march_item<1, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v); break;
+        default: march_item<2, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v); break;
     }
 }
 
@@ -436,7 +483,7 @@ __global__ void stored_minmax_kernel(const float* __restrict__ a, int64_t pitch,
 
 cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
-    const size_t smem = (size_t)(p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
+    const size_t smem = (size_t)(2 * p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
     // shared-memory carveout just large enough for the resident CTAs the kernel is
     // compiled for (each also reserves 1 KB); the rest of the SM's 256 KB array is
     // L1/texture cache
@@ -471,7 +518,7 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
 
 cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
     if (p.n_items == 0) return cudaSuccess;
-    const size_t smem = (size_t)(p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
+    const size_t smem = (size_t)(2 * p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
     auto go = [&](auto kern) {
         const int blocks = texm::tex_blocks_per_sm(p.precision);
         const int pct = (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2;

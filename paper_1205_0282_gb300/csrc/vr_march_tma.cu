@@ -162,12 +162,12 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Item& ite
     float qs[3] = {0, 0, 0}, dq[3] = {0, 0, 0};
     int nk = 0;
     {
-        df d[3], pe[3];
+        df d[3], pe[3], inv_D[3];
         int n_samples = 0;
         df dt;
-        if (i < p.width && j < p.height && setup_ray(p, i, j, d, pe, n_samples, dt)) {
+        if (i < p.width && j < p.height && setup_ray(p, i, j, d, pe, n_samples, dt, inv_D)) {
             int klo, khi;
-            brick_range(p, bidx, d, pe, n_samples, dt, klo, khi);
+            brick_range(p, bidx, d, pe, n_samples, inv_D, klo, khi);
             nk = khi - klo;
             if (nk > 0) {
 #pragma unroll

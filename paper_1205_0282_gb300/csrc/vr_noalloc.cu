@@ -270,6 +270,7 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
     p.tiles_y = tiles_y;
     p.tile = kTileSide;
     p.dt = vr::df_from_double(cam->step);
+    p.inv_dt = vr::df_from_double(1.0 / cam->step);
     p.dt_f = (float)cam->step;
     p.tau = (float)cam->term_alpha;
     p.cube = cube;
