@@ -276,6 +276,7 @@ struct vr_ctx {
 
     // planner scratch (host)
     std::vector<int32_t> plan_count, plan_fill, plan_sweep;
+    std::vector<double> plan_qx, plan_qy;  // view-plane offsets of tile-centre columns and rows
     struct PB {
         int32_t key, id, rect[4];
     };

@@ -249,18 +249,34 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
     // through the tile's centre pixel, and its sign
     c->plan_sweep.assign(n_tiles, 0);
     if (use_tma(c) || use_tex(c)) {
-        for (int ty = 0; ty < tiles_y; ++ty)
+        // view-plane offsets of the tile centres' columns and rows, then per tile
+        // d = f + qx r + qy u (no division in the tile loop)
+        c->plan_qx.resize(tiles_x);
+        c->plan_qy.resize(tiles_y);
+        for (int tx = 0; tx < tiles_x; ++tx) {
+            const int i = std::min(tx * T + T / 2, cam.width - 1);
+            c->plan_qx[tx] = (2.0 * (i + 0.5) / cam.width - 1.0) * c->basis.tan_half * c->basis.aspect;
+        }
+        for (int ty = 0; ty < tiles_y; ++ty) {
+            const int j = std::min(ty * T + T / 2, cam.height - 1);
+            c->plan_qy[ty] = (1.0 - 2.0 * (j + 0.5) / cam.height) * c->basis.tan_half;
+        }
+        const double* f = c->basis.f;
+        const double* r = c->basis.r;
+        const double* u = c->basis.u;
+        for (int ty = 0; ty < tiles_y; ++ty) {
+            const double qy = c->plan_qy[ty];
+            const double g0 = f[0] + qy * u[0], g1 = f[1] + qy * u[1], g2 = f[2] + qy * u[2];
+            int32_t* sweep = c->plan_sweep.data() + (int64_t)ty * tiles_x;
             for (int tx = 0; tx < tiles_x; ++tx) {
-                const int i = std::min(tx * T + T / 2, cam.width - 1), j = std::min(ty * T + T / 2, cam.height - 1);
-                const double qx = (2.0 * (i + 0.5) / cam.width - 1.0) * c->basis.tan_half * c->basis.aspect;
-                const double qy = (1.0 - 2.0 * (j + 0.5) / cam.height) * c->basis.tan_half;
-                double d[3];
-                for (int a = 0; a < 3; ++a) d[a] = c->basis.f[a] + qx * c->basis.r[a] + qy * c->basis.u[a];
+                const double qx = c->plan_qx[tx];
+                const double d[3] = {g0 + qx * r[0], g1 + qx * r[1], g2 + qx * r[2]};
                 int ax = 0;
                 for (int a = 1; a < 3; ++a)
                     if (std::fabs(d[a]) > std::fabs(d[ax])) ax = a;
-                c->plan_sweep[(int64_t)ty * tiles_x + tx] = ax | (d[ax] < 0.0 ? 4 : 0);
+                sweep[tx] = ax | (d[ax] < 0.0 ? 4 : 0);
             }
+        }
     }
 
     // eye's brick index per axis, -1 / nb when outside (view-order key, see below)
