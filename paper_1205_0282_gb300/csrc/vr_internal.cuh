@@ -36,7 +36,7 @@ struct Stats {
     unsigned long long chunks_staged;  // TMA march: chunks read from shared memory
     unsigned long long chunks_direct;  // TMA march: chunks that fell back to global loads
     int errors;
-    int pad;
+    int work_next;  // texture march: next half item (32 rays) for a warp to take
 };
 
 // One frame of a batch (the serving loop): its camera, tiles and image.  The

@@ -13,6 +13,7 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cstdint>
 
@@ -156,10 +157,11 @@ __device__ __forceinline__ int step_of(const FrameParams& p, int a) {
 
 template <int S, bool UNIFORM, int PREC, bool DYN, class Cam>
 __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam, const Item& item,
-                                           const float4* s_rgba, const float4* s_drgba, const float* s_v) {
+                                           const float4* s_rgba, const float4* s_drgba, const float* s_v,
+                                           int t) {
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
     const cudaTextureObject_t tex = p.tex[S];
-    const int lx = threadIdx.x % kTile, ly = threadIdx.x / kTile;
+    const int lx = t % kTile, ly = t / kTile;  // pixel t of the item's tile
     const int tx = item.tile % cam.tiles_x, ty = item.tile / cam.tiles_x;
     const int i = tx * kTile + lx, j = ty * kTile + ly;
     int bidx[3], O[3], imax[3];
@@ -316,20 +318,20 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
             step(ring[r]);
         }
     }
-    p.frags[(int64_t)item.frag * kTilePixels + threadIdx.x] = acc;
-    unsigned long long t = (unsigned long long)fn;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if ((threadIdx.x & 31) == 0 && t) atomicAdd(&p.stats->samples, t);
+    p.frags[(int64_t)item.frag * kTilePixels + t] = acc;
+    unsigned long long ns = (unsigned long long)fn;
+    for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    if ((threadIdx.x & 31) == 0 && ns) atomicAdd(&p.stats->samples, ns);
 }
 
-// The transfer function lives in dynamic shared memory sized to the control points,
-// so that almost all of the SM's L1/shared array stays texture cache.
-template <bool UNIFORM, int PREC, bool DYN>
-__global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_kernel(const FrameParams p) {
+// Copy the transfer function into dynamic shared memory sized to its control
+// points (so that almost all of the SM's L1/shared array stays texture cache):
+// the points, their forward differences and their values.
+__device__ __forceinline__ void load_tf(const FrameParams& p, float4*& s_rgba, float4*& s_drgba, float*& s_v) {
     extern __shared__ float4 s_dyn[];
-    float4* s_rgba = s_dyn;
-    float4* s_drgba = s_dyn + p.tf_n + 1;
-    float* s_v = reinterpret_cast<float*>(s_drgba + p.tf_n);
+    s_rgba = s_dyn;
+    s_drgba = s_dyn + p.tf_n + 1;
+    s_v = reinterpret_cast<float*>(s_drgba + p.tf_n);
     for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
         const float4 c = p.tf_rgba[k];
         s_rgba[k] = c;
@@ -340,11 +342,31 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
         }
     }
     __syncthreads();
-    const Item item = p.items[blockIdx.x];
-    switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v); break;
-        case 1: march_item<1, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v); break;
-        default: march_item<2, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v); break;
+}
+
+// Persistent CTAs (as many as are resident), each warp taking half items (the 32
+// rays of an 8x4 half tile) in list order from a counter: a warp that finishes
+// its rays starts the next half item at once instead of waiting for the other
+// warp of its CTA, and the list order (brick-major, front to back) is kept.
+template <bool UNIFORM, int PREC, bool DYN>
+__global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_kernel(const FrameParams p) {
+    float4 *s_rgba, *s_drgba;
+    float* s_v;
+    load_tf(p, s_rgba, s_drgba, s_v);
+    const int lane = threadIdx.x & 31;
+    const int total = 2 * p.n_items;
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(&p.stats->work_next, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const Item item = p.items[w >> 1];
+        const int t = (w & 1) * 32 + lane;
+        switch (item.sweep & 3) {
+            case 0: march_item<0, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+            case 1: march_item<1, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+            default: march_item<2, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+        }
     }
 }
 
@@ -352,26 +374,16 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
 // from the frame it belongs to (item.sweep >> 3).
 template <bool UNIFORM, int PREC>
 __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_batch_kernel(const FrameParams p) {
-    extern __shared__ float4 s_dyn[];
-    float4* s_rgba = s_dyn;
-    float4* s_drgba = s_dyn + p.tf_n + 1;
-    float* s_v = reinterpret_cast<float*>(s_drgba + p.tf_n);
-    for (int k = threadIdx.x; k <= p.tf_n; k += blockDim.x) {
-        const float4 c = p.tf_rgba[k];
-        s_rgba[k] = c;
-        if (k < p.tf_n) {
-            const float4 c1 = p.tf_rgba[k + 1];
-            s_drgba[k] = make_float4(c1.x - c.x, c1.y - c.y, c1.z - c.z, c1.w - c.w);
-            s_v[k] = p.tf_v[k];
-        }
-    }
-    __syncthreads();
+    float4 *s_rgba, *s_drgba;
+    float* s_v;
+    load_tf(p, s_rgba, s_drgba, s_v);
     const Item item = p.items[blockIdx.x];
     const FrameCam& cam = p.cams[item.sweep >> 3];
+    const int t = threadIdx.x;
     switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v); break;
-        case 1: march_item<1, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v); break;
-        default: march_item<2, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v); break;
+        case 0: march_item<0, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
+        case 1: march_item<1, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
+        default: march_item<2, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
     }
 }
 
@@ -495,7 +507,12 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
             carveout = pct;
         }
-        kern<<<p.n_items, kTilePixels, smem, s>>>(p);
+        // one wave of persistent CTAs (no more than there are items)
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t grid = std::min<int64_t>((int64_t)sms * blocks, (int64_t)p.n_items);
+        kern<<<(unsigned)grid, kTilePixels, smem, s>>>(p);
     };
     auto by_tf = [&](auto uniform_kern, auto general_kern) {
         if (p.tf_uniform) go(uniform_kern);
