@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--kernel", choices=["auto", "tma", "direct", "tex"], default="auto")
     ap.add_argument("--precision", choices=["f32", "f16", "f8"], default="f32",
                     help="storage of the texture march's cube copies (FP32, FP16, FP8 E4M3 per-brick scale)")
+    ap.add_argument("--mip", action="store_true",
+                    help="maximum intensity projection + colour map (the paper's mode, Section 2.3.3)")
     ap.add_argument("--dynamic-step", action="store_true",
                     help="dynamic step: samples `step` voxels apart along each ray's dominant axis")
     ap.add_argument("--shard", type=int, default=1,
@@ -227,7 +229,7 @@ def recorded_traffic(kernel, workload_name):
 
 # ------------------------------------------------------------------ CPU oracle timing
 
-def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False, regions=None, step_mode=0):
+def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False, regions=None, step_mode=0, mode="ea"):
     """Samples/s of the FP64 oracle on centre crops of successive poses, for
     about `seconds` of wall time (at least one crop).  With keep, also returns
     the crops as (camera, pixel indices, RGBA) for the image-quality check.
@@ -246,7 +248,7 @@ def oracle_rate(cube, tf, poses, brick, seconds, crop=64, keep=False, regions=No
         pix = (jj * W + ii).reshape(-1)
         ref, amb, ns = oracle.render(cube, tf, cam, brick=brick, pixels=pix,
                                      amb_alpha=QUALITY_AMB_ALPHA, amb_steps=QUALITY_AMB_STEPS,
-                                     regions=regions, step_mode=step_mode)
+                                     regions=regions, step_mode=step_mode, mode=mode)
         total += int(ns.sum())
         crops.append((cam, pix, ref, amb) if keep else None)
         k += 7
@@ -384,6 +386,7 @@ def run_ours(args):
     r.set_option(vrmod.VR_OPT_PRECISION, {"f32": vrmod.VR_PRECISION_F32, "f16": vrmod.VR_PRECISION_F16,
                                           "f8": vrmod.VR_PRECISION_F8}[args.precision])
     r.set_option(vrmod.VR_OPT_STEP_MODE, 1 if args.dynamic_step else 0)
+    r.set_option(vrmod.VR_OPT_MODE, 1 if args.mip else 0)
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -510,7 +513,8 @@ def run_ours(args):
             for j, lf in enumerate(leaves):
                 regions[((idx >= lf[:3]) & (idx < lf[3:])).all(axis=1)] = j
         rate, secs, n_crops, crops = oracle_rate(cube, tf, poses, spec["brick"], args.cpu_seconds, keep=True,
-                                                 regions=regions, step_mode=1 if args.dynamic_step else 0)
+                                                 regions=regions, step_mode=1 if args.dynamic_step else 0,
+                                                 mode="mip" if args.mip else "ea")
         cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{n_crops} centre crops of 64x64 pixels on successive orbit poses, "
                          f"{secs:.1f} s of FP64 CPU work"}
@@ -526,6 +530,7 @@ def run_ours(args):
                        "brick": list(spec["brick"]), "image": [W, H], "step": 0.5,
                        "tf": args.tf.upper(), "term_alpha": 0.99,
                        "step_mode": "dynamic (step along the dominant axis)" if args.dynamic_step else "fixed",
+                       "mode": "MIP + colour map" if args.mip else "emission-absorption",
                        "storage": {"f32": "FP32", "f16": "FP16",
                                    "f8": "FP8 E4M3, per-brick absmax/448 scale"}[args.precision],
                        "residency": ("out-of-core: pinned host brick store, device brick cache of "

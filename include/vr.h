@@ -106,8 +106,9 @@ typedef struct {
                                 VR_KERNEL_TMA: 16x16-pixel items, voxel boxes staged in shared
                                 memory by TMA (one transposed copy extra); VR_KERNEL_DIRECT:
                                 8x8-pixel items, corners read through the L1 cache.  MIP frames
-                                always use the direct kernel.  All give the same image up to
-                                FP32 rounding. */
+                                use the texture march under VR_KERNEL_AUTO (cube within the
+                                limits) or VR_KERNEL_TEX with FP32 storage, else the direct
+                                kernel.  All give the same image up to FP32 rounding. */
 #define VR_KERNEL_TMA 0
 #define VR_KERNEL_DIRECT 1
 #define VR_KERNEL_TEX 2

@@ -65,7 +65,9 @@ bool tex_fits(vr_ctx* c) {
     return c->tex_fits == 1;
 }
 bool use_tex(vr_ctx* c) {
-    return !c->ooc && c->mode == 0 && (c->kernel == VR_KERNEL_TEX || (c->kernel == VR_KERNEL_AUTO && tex_fits(c)));
+    // MIP frames run on the texture march with FP32 storage only
+    return !c->ooc && (c->mode == 0 || c->precision == VR_PRECISION_F32) &&
+           (c->kernel == VR_KERNEL_TEX || (c->kernel == VR_KERNEL_AUTO && tex_fits(c)));
 }
 bool use_tma(vr_ctx* c) {
     return !c->ooc && c->mode == 0 && c->step_mode == 0 && (c->kernel == VR_KERNEL_TMA || (c->kernel == VR_KERNEL_AUTO && !tex_fits(c)));

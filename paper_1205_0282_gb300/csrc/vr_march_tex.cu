@@ -155,7 +155,9 @@ __device__ __forceinline__ int step_of(const FrameParams& p, int a) {
     return a == 0 ? 1 : (a == 1 ? p.nb[0] : p.nb[0] * p.nb[1]);
 }
 
-template <int S, bool UNIFORM, int PREC, bool DYN, class Cam>
+// MODE 0: emission-absorption compositing; MODE 1: maximum intensity projection
+// (Section 2.3.2; the colour map is applied by the composite), FP32 storage only.
+template <int S, bool UNIFORM, int PREC, bool DYN, class Cam, int MODE = 0>
 __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam, const Item& item,
                                            const float4* s_rgba, const float4* s_drgba, const float* s_v,
                                            int t) {
@@ -174,6 +176,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         imax[a] = min(p.B[a] - 1, p.n[a] - 2 - O[a]);
     }
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float vmax = -FLT_MAX;  // MIP: running maximum
     float fn = 0.0f;  // samples this ray owes the brick (after termination: those composited)
     float qs[3] = {0, 0, 0}, dq[3] = {0, 0, 0};
     float dt_ray = 0.0f;  // dynamic step: this ray's spacing (voxels)
@@ -288,6 +291,15 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         const float e1 = fmaf(cur.fv, e11 - e01, e01);
         float val = fmaf(cur.fs, e1 - e0, e0);
         if (PREC == kPrecF8) val *= k0;
+        if constexpr (MODE == 1) {
+            // a MIP ray stops once it reaches the data's global maximum (Section
+            // 2.3.2): no later sample can exceed it
+            const bool owed = fi < fn;
+            if (owed) vmax = fmaxf(vmax, val);
+            if (owed && vmax >= p.gmax) fn = fi + 1.0f;
+            fi += 1.0f;
+            return;
+        }
         const float4 col = tf_lerp<UNIFORM>(p, s_rgba, s_drgba, s_v, val);
         const float alpha = DYN ? opacity_correct_dt(col.w, dt_ray) : opacity_correct(p, col.w);
         const bool owed = fi < fn;
@@ -318,6 +330,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
             step(ring[r]);
         }
     }
+    if (MODE == 1) acc = make_float4(vmax, fn > 0.0f ? 1.0f : 0.0f, 0.0f, 0.0f);
     p.frags[(int64_t)item.frag * kTilePixels + t] = acc;
     unsigned long long ns = (unsigned long long)fn;
     for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
@@ -348,7 +361,7 @@ __device__ __forceinline__ void load_tf(const FrameParams& p, float4*& s_rgba, f
 // rays of an 8x4 half tile) in list order from a counter: a warp that finishes
 // its rays starts the next half item at once instead of waiting for the other
 // warp of its CTA, and the list order (brick-major, front to back) is kept.
-template <bool UNIFORM, int PREC, bool DYN>
+template <bool UNIFORM, int PREC, bool DYN, int MODE = 0>
 __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_kernel(const FrameParams p) {
     float4 *s_rgba, *s_drgba;
     float* s_v;
@@ -363,9 +376,9 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
         const Item item = p.items[w >> 1];
         const int t = (w & 1) * 32 + lane;
         switch (item.sweep & 3) {
-            case 0: march_item<0, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v, t); break;
-            case 1: march_item<1, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v, t); break;
-            default: march_item<2, UNIFORM, PREC, DYN>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+            case 0: march_item<0, UNIFORM, PREC, DYN, FrameParams, MODE>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+            case 1: march_item<1, UNIFORM, PREC, DYN, FrameParams, MODE>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+            default: march_item<2, UNIFORM, PREC, DYN, FrameParams, MODE>(p, p, item, s_rgba, s_drgba, s_v, t); break;
         }
     }
 }
@@ -519,7 +532,10 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
         else go(general_kern);
     };
     using namespace texm;
-    if (p.step_mode) {  // the dynamic step (any storage; uniform or not)
+    if (p.mode == 1) {  // MIP (FP32 storage; the march does not read the transfer function)
+        if (p.step_mode) go(march_tex_kernel<true, kPrecF32, true, 1>);
+        else go(march_tex_kernel<true, kPrecF32, false, 1>);
+    } else if (p.step_mode) {  // the dynamic step (any storage; uniform or not)
         if (p.precision == kPrecF8) by_tf(march_tex_kernel<true, kPrecF8, true>, march_tex_kernel<false, kPrecF8, true>);
         else if (p.precision == kPrecF16) by_tf(march_tex_kernel<true, kPrecF16, true>, march_tex_kernel<false, kPrecF16, true>);
         else by_tf(march_tex_kernel<true, kPrecF32, true>, march_tex_kernel<false, kPrecF32, true>);

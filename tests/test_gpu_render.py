@@ -125,11 +125,26 @@ def test_nonuniform_tf(vr, torch, tiny):
     assert_parity(img, ref, amb)
 
 
-def test_mip_mode(vr, torch, tiny):
+@pytest.mark.parametrize("kernel", ["auto", "tex", "direct"])
+def test_mip_mode(vr, torch, tiny, kernel):
+    """MIP + colour map (Section 2.3.3) on the texture march (the default for a cube
+    within the texture limits) and on the direct march."""
     cube, tf = tiny
     cam = synth.tiny_views(width=128, height=128)[2]
-    img, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_MODE: 1})
+    k = {"auto": vr.VR_KERNEL_AUTO, "tex": vr.VR_KERNEL_TEX, "direct": vr.VR_KERNEL_DIRECT}[kernel]
+    img, _ = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_MODE: 1, vr.VR_OPT_KERNEL: k})
     ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32), mode="mip")
+    assert_parity(img, ref, amb)
+
+
+@pytest.mark.parametrize("shape,brick,camk,step,tau", RAGGED[:2])
+def test_mip_texture_march_ragged(vr, torch, shape, brick, camk, step, tau):
+    """MIP on the texture march over ragged cubes and bricks, against the oracle."""
+    cube = synth.random_cube(shape, seed=17)
+    tf = synth.make_tf([0.1, 0.2, 0.4, 0.6, 0.8, 0.9, 1.0, 1.0], lo=-2.0, hi=6.0)
+    cam = synth.pose(shape, camk["az"], camk["el"], camk["W"], camk["H"], step=step, term_alpha=tau)
+    img, _ = gpu_render(vr, torch, cube, tf, cam, brick, {vr.VR_OPT_MODE: 1, vr.VR_OPT_KERNEL: vr.VR_KERNEL_TEX})
+    ref, amb, _ = oracle_render(cube, tf, cam, brick, mode="mip")
     assert_parity(img, ref, amb)
 
 
@@ -309,10 +324,11 @@ def test_mip_stops_at_the_global_maximum(vr, torch):
     cube = np.minimum(cube, np.percentile(cube, 30)).astype(np.float32)
     tf = synth.make_tf([0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8], lo=float(cube.min()), hi=float(cube.max()))
     cam = synth.tiny_views(width=96, height=96)[1]
-    img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_MODE: 1})
     ref, amb, ns = oracle_render(cube, tf, cam, (32, 32, 32), mode="mip")
-    assert_parity(img, ref, amb, min_signal=0.0)
-    assert st["samples"] < 0.7 * ns.sum()
+    for kernel in (vr.VR_KERNEL_TEX, vr.VR_KERNEL_DIRECT):
+        img, st = gpu_render(vr, torch, cube, tf, cam, (32, 32, 32), {vr.VR_OPT_MODE: 1, vr.VR_OPT_KERNEL: kernel})
+        assert_parity(img, ref, amb, min_signal=0.0)
+        assert st["samples"] < 0.7 * ns.sum()
 
 
 # ------------------------------------------------------------------ dynamic step
@@ -331,7 +347,7 @@ def test_dynamic_step_texture_march(vr, torch, tiny, view):
     assert np.abs(ref - fixed).max() > 1e-3      # the variant does change the image
 
 
-@pytest.mark.parametrize("kernel,mode", [(1, 0), (1, 1)])
+@pytest.mark.parametrize("kernel,mode", [(1, 0), (1, 1), (2, 1)])
 def test_dynamic_step_direct_march_and_mip(vr, torch, tiny, kernel, mode):
     cube, tf = tiny
     cam = synth.tiny_views(width=120, height=100)[2]
