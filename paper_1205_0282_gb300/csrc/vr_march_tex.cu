@@ -383,20 +383,28 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
     }
 }
 
-// Batch of frames (the serving loop): the same march, each item's camera read
-// from the frame it belongs to (item.sweep >> 3).
+// Batch of frames (the serving loop): the same persistent march, each item's
+// camera read from the frame it belongs to (item.sweep >> 3).
 template <bool UNIFORM, int PREC>
 __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_batch_kernel(const FrameParams p) {
     float4 *s_rgba, *s_drgba;
     float* s_v;
     load_tf(p, s_rgba, s_drgba, s_v);
-    const Item item = p.items[blockIdx.x];
-    const FrameCam& cam = p.cams[item.sweep >> 3];
-    const int t = threadIdx.x;
-    switch (item.sweep & 3) {
-        case 0: march_item<0, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
-        case 1: march_item<1, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
-        default: march_item<2, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
+    const int lane = threadIdx.x & 31;
+    const int total = 2 * p.n_items;
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(&p.stats->work_next, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const Item item = p.items[w >> 1];
+        const FrameCam& cam = p.cams[item.sweep >> 3];
+        const int t = (w & 1) * 32 + lane;
+        switch (item.sweep & 3) {
+            case 0: march_item<0, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
+            case 1: march_item<1, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
+            default: march_item<2, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
+        }
     }
 }
 
@@ -504,6 +512,14 @@ __global__ void stored_minmax_kernel(const float* __restrict__ a, int64_t pitch,
     }
 }
 
+// One wave of persistent CTAs (no more than there are items).
+inline unsigned persistent_grid(const FrameParams& p, int blocks_per_sm) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (unsigned)std::min<int64_t>((int64_t)sms * blocks_per_sm, (int64_t)p.n_items);
+}
+
 }  // namespace texm
 
 cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
@@ -520,12 +536,7 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
             carveout = pct;
         }
-        // one wave of persistent CTAs (no more than there are items)
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int64_t grid = std::min<int64_t>((int64_t)sms * blocks, (int64_t)p.n_items);
-        kern<<<(unsigned)grid, kTilePixels, smem, s>>>(p);
+        kern<<<texm::persistent_grid(p, blocks), kTilePixels, smem, s>>>(p);
     };
     auto by_tf = [&](auto uniform_kern, auto general_kern) {
         if (p.tf_uniform) go(uniform_kern);
@@ -560,7 +571,7 @@ cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
             carveout = pct;
         }
-        kern<<<p.n_items, kTilePixels, smem, s>>>(p);
+        kern<<<texm::persistent_grid(p, blocks), kTilePixels, smem, s>>>(p);
     };
     using namespace texm;
     if (p.precision == kPrecF8) {
