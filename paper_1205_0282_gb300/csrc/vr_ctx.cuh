@@ -153,6 +153,70 @@ inline bool box_rect(const vr_camera& c, const Basis& b, const double lo[3], con
     return true;
 }
 
+// A box corner seen from the camera: depth along the view axis and, for
+// corners in front of the eye, its pixel coordinates (box_rect's arithmetic).
+struct CornerProj {
+    double zc, pi, pj;
+};
+inline CornerProj project_corner(const vr_camera& c, const Basis& b, const double P[3]) {
+    CornerProj q;
+    const double v[3] = {P[0] - c.eye[0], P[1] - c.eye[1], P[2] - c.eye[2]};
+    q.zc = v[0] * b.f[0] + v[1] * b.f[1] + v[2] * b.f[2];
+    q.pi = q.pj = 0.0;
+    if (q.zc > 1e-9) {
+        const double xc = v[0] * b.r[0] + v[1] * b.r[1] + v[2] * b.r[2];
+        const double yc = v[0] * b.u[0] + v[1] * b.u[1] + v[2] * b.u[2];
+        const double sx = xc / (q.zc * b.tan_half * b.aspect), sy = yc / (q.zc * b.tan_half);
+        q.pi = (sx + 1.0) * 0.5 * c.width - 0.5;
+        q.pj = (1.0 - sy) * 0.5 * c.height - 0.5;
+    }
+    return q;
+}
+// box_rect from the eight corners' projections (the same result as box_rect on
+// the box they span).
+inline bool rect_from_corners(const vr_camera& c, const CornerProj* const q[8], int32_t rect[4]) {
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    bool behind = false;
+    int back = 0;
+    for (int k = 0; k < 8; ++k) {
+        if (q[k]->zc < -1e-6) ++back;
+        if (!(q[k]->zc > 1e-9)) behind = true;
+        if (behind) continue;
+        xmin = std::min(xmin, q[k]->pi);
+        xmax = std::max(xmax, q[k]->pi);
+        ymin = std::min(ymin, q[k]->pj);
+        ymax = std::max(ymax, q[k]->pj);
+    }
+    if (back == 8) {
+        rect[0] = rect[1] = 0;
+        rect[2] = rect[3] = -1;
+        return false;
+    }
+    if (behind) {
+        rect[0] = 0;
+        rect[1] = 0;
+        rect[2] = c.width - 1;
+        rect[3] = c.height - 1;
+        return true;
+    }
+    double x0 = std::floor(xmin) - 1, x1 = std::ceil(xmax) + 1;
+    double y0 = std::floor(ymin) - 1, y1 = std::ceil(ymax) + 1;
+    x0 = std::max(x0, 0.0);
+    y0 = std::max(y0, 0.0);
+    x1 = std::min(x1, (double)c.width - 1);
+    y1 = std::min(y1, (double)c.height - 1);
+    if (x1 < x0 || y1 < y0) {
+        rect[0] = rect[1] = 0;
+        rect[2] = rect[3] = -1;
+        return false;
+    }
+    rect[0] = (int32_t)x0;
+    rect[1] = (int32_t)y0;
+    rect[2] = (int32_t)x1;
+    rect[3] = (int32_t)y1;
+    return true;
+}
+
 // Sampling region of brick (ix, iy, iz): [b*B, min((b+1)*B, n-1)] per axis.
 inline void brick_box(const int64_t n[3], const int32_t B[3], const int64_t idx[3], double lo[3],
                double hi[3]) {
@@ -277,6 +341,8 @@ struct vr_ctx {
     // planner scratch (host)
     std::vector<int32_t> plan_count, plan_fill, plan_sweep;
     std::vector<double> plan_qx, plan_qy;  // view-plane offsets of tile-centre columns and rows
+    std::vector<vrh::CornerProj> plan_proj;  // projections of the brick grid's corner points
+    std::vector<int32_t> plan_diff;         // per-tile item counts as a 2D difference array
     struct PB {
         int32_t key, id, rect[4];
     };

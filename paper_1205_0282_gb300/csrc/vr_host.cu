@@ -290,6 +290,21 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
         else e[a] = std::min<int64_t>((int64_t)std::floor(E / c->B[a]), c->nb[a] - 1);
     }
 
+    // projections of the brick grid's corner points x_i = min(i B, n - 1): each
+    // brick box spans eight of them, so each is projected once, not per brick
+    const int64_t g[3] = {c->nb[0] + 1, c->nb[1] + 1, c->nb[2] + 1};
+    if (c->rect_cull) {
+        c->plan_proj.resize((size_t)(g[0] * g[1] * g[2]));
+        for (int64_t k = 0; k < g[2]; ++k)
+            for (int64_t j = 0; j < g[1]; ++j)
+                for (int64_t i = 0; i < g[0]; ++i) {
+                    const double P[3] = {(double)std::min<int64_t>(i * c->B[0], c->n[0] - 1),
+                                         (double)std::min<int64_t>(j * c->B[1], c->n[1] - 1),
+                                         (double)std::min<int64_t>(k * c->B[2], c->n[2] - 1)};
+                    c->plan_proj[(size_t)((k * g[1] + j) * g[0] + i)] = project_corner(cam, c->basis, P);
+                }
+    }
+
     c->plan_bricks.clear();
     s.bricks_skipped = 0;
     s.touched_bytes = 0;
@@ -308,9 +323,12 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
         vr_ctx::PB pb;
         pb.id = (int32_t)id;
         if (c->rect_cull) {
-            double lo[3], hi[3];
-            brick_box(c->n, c->B, idx, lo, hi);
-            if (!box_rect(cam, c->basis, lo, hi, pb.rect)) continue;
+            const CornerProj* q[8];
+            for (int k = 0; k < 8; ++k) {
+                const int64_t gi = idx[0] + (k & 1), gj = idx[1] + ((k >> 1) & 1), gk = idx[2] + ((k >> 2) & 1);
+                q[k] = &c->plan_proj[(size_t)((gk * g[1] + gj) * g[0] + gi)];
+            }
+            if (!rect_from_corners(cam, q, pb.rect)) continue;
         } else {
             pb.rect[0] = pb.rect[1] = 0;
             pb.rect[2] = cam.width - 1;
@@ -336,14 +354,28 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
                      [](const vr_ctx::PB& x, const vr_ctx::PB& y) { return x.key < y.key; });
     s.bricks_rendered = (int64_t)c->plan_bricks.size();
 
-    c->plan_count.assign(n_tiles + 1, 0);
+    // items per tile: each brick adds 1 over its rectangle of tiles, summed as a 2D
+    // difference array and its prefix sums
+    const int64_t dw = tiles_x + 1;
+    c->plan_diff.assign((size_t)(dw * (tiles_y + 1)), 0);
     n_items = 0;
     for (const auto& pb : c->plan_bricks) {
         const int tx0 = pb.rect[0] / T, tx1 = pb.rect[2] / T;
         const int ty0 = pb.rect[1] / T, ty1 = pb.rect[3] / T;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) c->plan_count[(int64_t)ty * tiles_x + tx]++;
+        c->plan_diff[(size_t)(ty0 * dw + tx0)] += 1;
+        c->plan_diff[(size_t)(ty0 * dw + tx1 + 1)] -= 1;
+        c->plan_diff[(size_t)((ty1 + 1) * dw + tx0)] -= 1;
+        c->plan_diff[(size_t)((ty1 + 1) * dw + tx1 + 1)] += 1;
         n_items += (int64_t)(tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    }
+    c->plan_count.assign(n_tiles + 1, 0);
+    for (int ty = 0; ty < tiles_y; ++ty) {
+        int32_t run = 0;
+        for (int tx = 0; tx < tiles_x; ++tx) {
+            run += c->plan_diff[(size_t)(ty * dw + tx)];
+            const int32_t above = ty > 0 ? c->plan_count[(int64_t)(ty - 1) * tiles_x + tx] : 0;
+            c->plan_count[(int64_t)ty * tiles_x + tx] = run + above;
+        }
     }
     if (n_items > (int64_t)INT32_MAX / (T * T)) return fail(c, VR_ENOMEM, "frame too large");
     int rc = grow_pinned(c, s.h_items, s.cap_items, (size_t)n_items);
