@@ -214,6 +214,19 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def recorded_inst_per_sample(kernel, workload_name):
+    """Thread instructions per composited sample of the march kernel from a
+    committed ncu capture (smsp__thread_inst_executed.sum over the frame's
+    samples), only if the kernel source is unchanged since that capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    e = json.load(open(p)).get(kernel, {}).get(workload_name)
+    if not e or e.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return e.get("thread_inst_per_sample")
+
+
 def recorded_traffic(kernel, workload_name):
     """DRAM bytes per launch from a committed ncu capture, only if the kernel
     source is unchanged since that capture."""
@@ -500,6 +513,22 @@ def run_ours(args):
                 "frame_bytes_per_step": bytes_per_launch + W * H * 16,
                 "frame_frac": (bytes_per_launch + W * H * 16) / (elapsed_ms / args.steps * 1e-3) / 1e9 / peak}
 
+    # secondary (ALU) roofline: lane instructions per second during the march
+    # against the issue peak, 128 lanes per SM per cycle at the sampled SM clock
+    ips = recorded_inst_per_sample(kname, spec["name"] + ("" if args.precision == "f32"
+                                                         else "_" + args.precision))
+    roofline_alu = None
+    if ips and not args.mip and not args.dynamic_step:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.summary().get("sm_mhz") or 0.0
+        if mhz:
+            alu_peak = sms * 128 * mhz * 1e6
+            alu_ach = samples / max(frames, 1) * ips / (avg_march_ms * 1e-3)
+            roofline_alu = {"bound": "alu", "kernel": kname, "achieved": alu_ach / 1e12, "peak": alu_peak / 1e12,
+                            "unit": "T lane-instructions/s", "frac": alu_ach / alu_peak,
+                            "thread_instructions_per_sample": ips,
+                            "peak_kind": f"{sms} SMs x 128 lanes x median SM clock under load ({mhz:.0f} MHz)"}
+
     cpu = quality = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -549,7 +578,7 @@ def run_ours(args):
             "bricks_skipped_per_frame": st["bricks_skipped"] / per_frame,
             "plan_ms_per_frame": st["plan_ms"] / per_frame,
             "composite_ms_per_frame": st["composite_ms"] / per_frame,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "roofline_alu": roofline_alu, "cpu_baseline": cpu, "e2e": e2e,
             "quality": quality,
             "march_kernel": args.kernel,
             "chunks_staged_per_frame": st["chunks_staged"] / per_frame,
