@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--kernel", choices=["auto", "tma", "direct", "tex"], default="auto")
     ap.add_argument("--precision", choices=["f32", "f16", "f8"], default="f32",
                     help="storage of the texture march's cube copies (FP32, FP16, FP8 E4M3 per-brick scale)")
+    ap.add_argument("--tex-slab-layers", type=int, default=0,
+                    help="texture march: layers per slab of the layered copies (0: the device limit)")
     ap.add_argument("--mip", action="store_true",
                     help="maximum intensity projection + colour map (the paper's mode, Section 2.3.3)")
     ap.add_argument("--dynamic-step", action="store_true",
@@ -400,6 +402,8 @@ def run_ours(args):
                                           "f8": vrmod.VR_PRECISION_F8}[args.precision])
     r.set_option(vrmod.VR_OPT_STEP_MODE, 1 if args.dynamic_step else 0)
     r.set_option(vrmod.VR_OPT_MODE, 1 if args.mip else 0)
+    if args.tex_slab_layers > 0:
+        r.set_option(vrmod.VR_OPT_TEX_SLAB_LAYERS, args.tex_slab_layers)
     out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -560,6 +564,7 @@ def run_ours(args):
                        "tf": args.tf.upper(), "term_alpha": 0.99,
                        "step_mode": "dynamic (step along the dominant axis)" if args.dynamic_step else "fixed",
                        "mode": "MIP + colour map" if args.mip else "emission-absorption",
+                       "tex_slab_layers": args.tex_slab_layers or "device limit",
                        "storage": {"f32": "FP32", "f16": "FP16",
                                    "f8": "FP8 E4M3, per-brick absmax/448 scale"}[args.precision],
                        "residency": ("out-of-core: pinned host brick store, device brick cache of "

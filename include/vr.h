@@ -156,6 +156,15 @@ typedef struct {
                                 middles, never their faces).
                                 Rendered by the texture or the direct march (VR_KERNEL_TMA
                                 with it: VR_EINVAL at render time). */
+#define VR_OPT_TEX_SLAB_LAYERS 8 /* texture march: the layered copies are split along their
+                                layer axis into slabs of whole bricks plus one apron layer,
+                                each a layered texture of at most this many layers (0,
+                                default: the device's layer limit, 2048 on this GPU), so
+                                that cubes longer than that limit along any axis keep the
+                                texture march (memory permitting; up to 16 slabs per axis).
+                                Values below B + 1 make the texture march unavailable
+                                (VR_KERNEL_AUTO then picks VR_KERNEL_TMA).  Changing it drops
+                                the current copies (rebuilt at the next render). */
 #define VR_PRECISION_F32 0
 #define VR_PRECISION_F16 1
 #define VR_PRECISION_F8 2

@@ -260,8 +260,10 @@ struct vr_ctx {
     float* d_cube_xzy = nullptr; // transposed copy [x][z][y], row pitch ny_pad (sweeps along x)
     int64_t ny_pad = 0;
     CUtensorMap* d_tmaps = nullptr;  // tensor maps of the TMA march (device memory)
-    cudaArray_t tex_arr[3] = {nullptr, nullptr, nullptr};  // texture march: layered copies
-    cudaTextureObject_t tex_obj[3] = {0, 0, 0};
+    cudaArray_t tex_arr[3][vr::kMaxTexSlabs] = {};  // texture march: layered copies, by slab
+    cudaTextureObject_t tex_obj[3][vr::kMaxTexSlabs] = {};
+    int32_t tex_slab_bricks[3] = {0, 0, 0};         // bricks per slab along each layer axis
+    int64_t tex_slab_layers = 0;                     // VR_OPT_TEX_SLAB_LAYERS (0: device limit)
     bool tex_ready = false;
     int precision = VR_PRECISION_F32;  // storage of the layered copies
     float* d_brick_scale = nullptr;    // FP8 storage: per-brick scale

@@ -49,6 +49,13 @@ int retire_all(vr_ctx* c) {
 // Kernel selection for emission-absorption frames: VR_KERNEL_AUTO takes the
 // texture-gather march when the cube fits the device's layered-texture limits and
 // the TMA-staged march otherwise.
+// Bricks per slab of the layered copy whose layers run along axis S: as many as
+// fit the device's layer limit (or VR_OPT_TEX_SLAB_LAYERS) with their apron layer.
+int32_t tex_slab_bricks(vr_ctx* c, int S, int max_layers) {
+    int64_t lim = max_layers;
+    if (c->tex_slab_layers > 0) lim = std::min<int64_t>(lim, c->tex_slab_layers);
+    return (int32_t)std::max<int64_t>((lim - 1) / c->B[S], 0);
+}
 bool tex_fits(vr_ctx* c) {
     if (c->tex_fits < 0) {
         int maxw = 0, maxh = 0, maxl = 0;
@@ -58,7 +65,9 @@ bool tex_fits(vr_ctx* c) {
         bool ok = c->n[1] <= 65535 && c->n[2] <= 65535;
         for (int S = 0; S < 3; ++S) {
             const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
-            ok = ok && c->n[U] <= maxw && c->n[V] <= maxh && c->n[S] <= maxl;
+            const int32_t K = tex_slab_bricks(c, S, maxl);
+            ok = ok && c->n[U] <= maxw && c->n[V] <= maxh && K > 0 &&
+                 (c->nb[S] + K - 1) / K <= vr::kMaxTexSlabs;
         }
         c->tex_fits = ok ? 1 : 0;
     }
@@ -230,10 +239,13 @@ int64_t precision_bytes(int precision) {
 
 void free_tex(vr_ctx* c) {
     for (int a = 0; a < 3; ++a) {
-        if (c->tex_obj[a]) cudaDestroyTextureObject(c->tex_obj[a]);
-        if (c->tex_arr[a]) cudaFreeArray(c->tex_arr[a]);
-        c->tex_obj[a] = 0;
-        c->tex_arr[a] = nullptr;
+        for (int j = 0; j < vr::kMaxTexSlabs; ++j) {
+            if (c->tex_obj[a][j]) cudaDestroyTextureObject(c->tex_obj[a][j]);
+            if (c->tex_arr[a][j]) cudaFreeArray(c->tex_arr[a][j]);
+            c->tex_obj[a][j] = 0;
+            c->tex_arr[a][j] = nullptr;
+        }
+        c->tex_slab_bricks[a] = 0;
     }
     cudaFree(c->d_brick_scale);
     c->d_brick_scale = nullptr;
@@ -684,7 +696,8 @@ int prepare_tex(vr_ctx* c) {
     if (n[1] > 65535 || n[2] > 65535) return fail(c, VR_EINVAL, "cube too large for the texture march");
     for (int S = 0; S < 3; ++S) {
         const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
-        if (n[U] > maxw || n[V] > maxh || n[S] > maxl)
+        const int32_t K = tex_slab_bricks(c, S, maxl);
+        if (n[U] > maxw || n[V] > maxh || K == 0 || (c->nb[S] + K - 1) / K > vr::kMaxTexSlabs)
             return fail(c, VR_EINVAL, "cube exceeds the layered-texture limits of this device");
     }
     if (c->precision == VR_PRECISION_F16)
@@ -706,30 +719,38 @@ int prepare_tex(vr_ctx* c) {
         cudaChannelFormatDesc ch = c->precision == VR_PRECISION_F16 ? cudaCreateChannelDescHalf()
                                    : c->precision == VR_PRECISION_F8 ? cudaCreateChannelDesc<signed char>()
                                                                      : cudaCreateChannelDesc<float>();
-        if (cudaMalloc3DArray(&c->tex_arr[S], &ch, make_cudaExtent((size_t)n[U], (size_t)n[V], (size_t)n[S]),
-                              cudaArrayLayered | cudaArraySurfaceLoadStore) != cudaSuccess) {
-            cudaGetLastError();
-            free_tex(c);
-            return fail(c, VR_ENOMEM, "cannot allocate the layered textures");
+        const int32_t K = tex_slab_bricks(c, S, maxl);
+        c->tex_slab_bricks[S] = K;
+        const int64_t n_slabs = (c->nb[S] + K - 1) / K;
+        for (int64_t j = 0; j < n_slabs; ++j) {
+            const int64_t l0 = j * K * c->B[S];
+            const int64_t l1 = std::min<int64_t>((j + 1) * K * c->B[S], n[S] - 1);  // apron included
+            if (cudaMalloc3DArray(&c->tex_arr[S][j], &ch,
+                                  make_cudaExtent((size_t)n[U], (size_t)n[V], (size_t)(l1 - l0 + 1)),
+                                  cudaArrayLayered | cudaArraySurfaceLoadStore) != cudaSuccess) {
+                cudaGetLastError();
+                free_tex(c);
+                return fail(c, VR_ENOMEM, "cannot allocate the layered textures");
+            }
+            cudaResourceDesc rd;
+            std::memset(&rd, 0, sizeof(rd));
+            rd.resType = cudaResourceTypeArray;
+            rd.res.array.array = c->tex_arr[S][j];
+            cudaSurfaceObject_t surf = 0;
+            VR_CUDA(c, cudaCreateSurfaceObject(&surf, &rd));
+            cudaError_t e = vr::fill_tex_layers(c->d_cube, n[0], n[1], n[2], c->nx_pad, S, l0, l1 - l0 + 1, prec,
+                                                surf, c->d_brick_scale, c->B, c->nb, 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            cudaDestroySurfaceObject(surf);
+            if (e != cudaSuccess) return cuda_fail(c, e, "fill_tex_layers");
+            cudaTextureDesc td;
+            std::memset(&td, 0, sizeof(td));
+            td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+            td.filterMode = cudaFilterModePoint;
+            td.readMode = cudaReadModeElementType;
+            td.normalizedCoords = 0;
+            VR_CUDA(c, cudaCreateTextureObject(&c->tex_obj[S][j], &rd, &td, nullptr));
         }
-        cudaResourceDesc rd;
-        std::memset(&rd, 0, sizeof(rd));
-        rd.resType = cudaResourceTypeArray;
-        rd.res.array.array = c->tex_arr[S];
-        cudaSurfaceObject_t surf = 0;
-        VR_CUDA(c, cudaCreateSurfaceObject(&surf, &rd));
-        cudaError_t e = vr::fill_tex_layers(c->d_cube, n[0], n[1], n[2], c->nx_pad, S, prec, surf,
-                                            c->d_brick_scale, c->B, c->nb, 0);
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        cudaDestroySurfaceObject(surf);
-        if (e != cudaSuccess) return cuda_fail(c, e, "fill_tex_layers");
-        cudaTextureDesc td;
-        std::memset(&td, 0, sizeof(td));
-        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
-        td.filterMode = cudaFilterModePoint;
-        td.readMode = cudaReadModeElementType;
-        td.normalizedCoords = 0;
-        VR_CUDA(c, cudaCreateTextureObject(&c->tex_obj[S], &rd, &td, nullptr));
     }
     if (c->precision != VR_PRECISION_F32) {
         float2* d_mm = nullptr;
@@ -835,6 +856,16 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
             c->kernel = (int)value;
             return VR_OK;
         case VR_OPT_DEVICE_BUDGET: c->budget = value; return VR_OK;
+        case VR_OPT_TEX_SLAB_LAYERS:
+            if (value < 0) return fail(c, VR_EINVAL, "layers per texture slab must be >= 0");
+            if (value != c->tex_slab_layers) {
+                int rc = retire_all(c);  // frames in flight may read the old textures
+                if (rc) return rc;
+                free_tex(c);
+                c->tex_slab_layers = value;
+                c->tex_fits = -1;
+            }
+            return VR_OK;
         case VR_OPT_STEP_MODE:
             if (value != 0 && value != 1) return fail(c, VR_EINVAL, "step mode must be 0 or 1");
             c->step_mode = (int)value;
@@ -892,7 +923,10 @@ void fill_common_params(vr_ctx* c, vr::FrameParams& p) {
     for (const float2& mm : c->h_minmax) p.gmax = p.gmax == FLT_MAX ? mm.y : std::max(p.gmax, mm.y);
     p.tmaps = c->d_tmaps;
     p.tmaps_per_brick = c->tmaps_per_brick;
-    for (int a = 0; a < 3; ++a) p.tex[a] = c->tex_obj[a];
+    for (int a = 0; a < 3; ++a) {
+        for (int j = 0; j < vr::kMaxTexSlabs; ++j) p.tex[a][j] = c->tex_obj[a][j];
+        p.tex_slab_bricks[a] = c->tex_slab_bricks[a];
+    }
     p.precision = c->precision == VR_PRECISION_F8 ? vr::kPrecF8
                   : c->precision == VR_PRECISION_F16 ? vr::kPrecF16 : vr::kPrecF32;
     p.brick_scale = c->d_brick_scale;

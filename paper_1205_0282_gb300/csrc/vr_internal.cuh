@@ -14,6 +14,7 @@ constexpr int kTilePixels = kTile * kTile;  // 64 rays per item, one per thread
 constexpr int kTileTma = 16;                // tile edge of the TMA-staged march (16x16 items)
 constexpr int kTmaClasses = 8;              // staged-box classes of the TMA march
 constexpr int kPrecF32 = 0, kPrecF16 = 1, kPrecF8 = 2;  // texture storage precisions
+constexpr int kMaxTexSlabs = 16;  // texture march: slabs per layered copy at most
 constexpr int kMaxTfPoints = 256;
 constexpr int kAlphaPolyTerms = 11;         // coefficients of the opacity-correction polynomial
 constexpr int kAlphaSmallTerms = 6;         // ... and of its short form for small opacities
@@ -99,7 +100,11 @@ struct FrameParams {
     int32_t n_items;
     const CUtensorMap* tmaps;   // TMA march: tensor maps in device memory
     int32_t tmaps_per_brick;    // 1: one set per brick (brick-local coordinates)
-    cudaTextureObject_t tex[3]; // texture march: layered copies with layers along x, y, z
+    // texture march: layered copies with layers along x, y, z, each split into slabs
+    // of tex_slab_bricks[S] bricks along its layer axis (slab j holds layers
+    // [j K B_S, min((j + 1) K B_S, n_S - 1)], its last one the apron of the next)
+    cudaTextureObject_t tex[3][kMaxTexSlabs];
+    int32_t tex_slab_bricks[3];
     int32_t precision;          // texture storage: kPrecF32, kPrecF16, kPrecF8
     const float* brick_scale;   // FP8: per-brick scale (value = code * scale)
     const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
@@ -138,9 +143,11 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s);
 // composite of every tile of every frame (p.n_cams frames, total_tiles blocks).
 cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_composite_batch(const FrameParams& p, int32_t total_tiles, cudaStream_t s);
+// Layers [l0, l0 + nl) along axis S of the cube into the layered array behind surf
+// (its layer 0 = coordinate l0).
 cudaError_t fill_tex_layers(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch, int S,
-                            int precision, cudaSurfaceObject_t surf, const float* scale, const int32_t B[3],
-                            const int32_t nb[3], cudaStream_t s);
+                            int64_t l0, int64_t nl, int precision, cudaSurfaceObject_t surf, const float* scale,
+                            const int32_t B[3], const int32_t nb[3], cudaStream_t s);
 cudaError_t launch_brick_scale(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch,
                                const int32_t B[3], const int32_t nb[3], float* scale, cudaStream_t s);
 cudaError_t launch_stored_minmax(const float* a, int64_t pitch, const int32_t n[3], const int32_t B[3],

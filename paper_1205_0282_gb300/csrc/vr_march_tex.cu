@@ -162,7 +162,6 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
                                            const float4* s_rgba, const float4* s_drgba, const float* s_v,
                                            int t) {
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
-    const cudaTextureObject_t tex = p.tex[S];
     const int lx = t % kTile, ly = t / kTile;  // pixel t of the item's tile
     const int tx = item.tile % cam.tiles_x, ty = item.tile / cam.tiles_x;
     const int i = tx * kTile + lx, j = ty * kTile + ly;
@@ -175,6 +174,11 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         O[a] = bidx[a] * p.B[a];
         imax[a] = min(p.B[a] - 1, p.n[a] - 2 - O[a]);
     }
+    // the slab of the layered copy that holds this brick, and the brick's first
+    // layer in it
+    const int slab = bidx[S] / p.tex_slab_bricks[S];
+    const cudaTextureObject_t tex = p.tex[S][slab];
+    const int lay0 = O[S] - slab * p.tex_slab_bricks[S] * p.B[S];
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float vmax = -FLT_MAX;  // MIP: running maximum
     float fn = 0.0f;  // samples this ray owes the brick (after termination: those composited)
@@ -247,12 +251,12 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         const float x = ou + (float)iu, y = ov + (float)iv;
         if (PREC != kPrecF8) {
             // FP32 and FP16 textures both return FP32 values
-            gather4(tex, O[S] + ps, x, y, s.c[0], s.c[1], s.c[2], s.c[3]);
-            gather4(tex, O[S] + ps + 1, x, y, s.c[4], s.c[5], s.c[6], s.c[7]);
+            gather4(tex, lay0 + ps, x, y, s.c[0], s.c[1], s.c[2], s.c[3]);
+            gather4(tex, lay0 + ps + 1, x, y, s.c[4], s.c[5], s.c[6], s.c[7]);
         } else {
             int k[8];
-            gather4_codes(tex, O[S] + ps, x, y, k[0], k[1], k[2], k[3]);
-            gather4_codes(tex, O[S] + ps + 1, x, y, k[4], k[5], k[6], k[7]);
+            gather4_codes(tex, lay0 + ps, x, y, k[0], k[1], k[2], k[3]);
+            gather4_codes(tex, lay0 + ps + 1, x, y, k[4], k[5], k[6], k[7]);
 #pragma unroll
             for (int c = 0; c < 8; ++c) s.c[c] = __int_as_float(k[c]);
             s.halo = (iu == lim_u ? 1 : 0) | (iv == lim_v ? 2 : 0) | (ps == lim_s ? 4 : 0);
@@ -408,31 +412,34 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
     }
 }
 
-// Copy the stored cube a[z][y][x] (row pitch a_pitch floats) into the layered
-// array of sweep axis S through its surface: layer = coordinate along S.  FP16
-// stores the nearest half; FP8 stores the E4M3 code of v / scale, the scale of the
-// brick that owns the voxel (voxel g belongs to brick min(g / B, nb - 1)).
+// Copy layers [l0, l0 + nl) along axis S of the stored cube a[z][y][x] (row pitch
+// a_pitch floats) into the layered array of sweep axis S through its surface:
+// layer = coordinate along S - l0.  FP16 stores the nearest half; FP8 stores the
+// E4M3 code of v / scale, the scale of the brick that owns the voxel (voxel g
+// belongs to brick min(g / B, nb - 1)).  The grid covers (x, y, z) of the slab:
+// x in [x0, x0 + gridDim.x * blockDim.x), y = y0 + blockIdx.y, z = z0 + blockIdx.z.
 template <int S, int PREC>
 __global__ void fill_layers_kernel(const float* __restrict__ a, int64_t nx, int64_t ny, int64_t nz,
-                                   int64_t a_pitch, cudaSurfaceObject_t surf, const float* __restrict__ scale,
-                                   int3 B, int3 nb) {
-    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t y = blockIdx.y;
-    const int64_t z = blockIdx.z;
-    if (x >= nx) return;
+                                   int64_t a_pitch, int64_t l0, int64_t x_end, cudaSurfaceObject_t surf,
+                                   const float* __restrict__ scale, int3 B, int3 nb) {
+    const int64_t x = (S == 0 ? l0 : 0) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t y = (S == 1 ? l0 : 0) + blockIdx.y;
+    const int64_t z = (S == 2 ? l0 : 0) + blockIdx.z;
+    if (x >= x_end) return;
     const float v = a[(z * ny + y) * a_pitch + x];
     const int64_t c[3] = {x, y, z};
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
     const int cx = (int)(c[U] * (PREC == kPrecF32 ? 4 : (PREC == kPrecF16 ? 2 : 1)));
+    const int layer = (int)(c[S] - l0);
     if (PREC == kPrecF32) {
-        surf2DLayeredwrite(v, surf, cx, (int)c[V], (int)c[S]);
+        surf2DLayeredwrite(v, surf, cx, (int)c[V], layer);
     } else if (PREC == kPrecF16) {
-        surf2DLayeredwrite(__half_as_ushort(__float2half_rn(v)), surf, cx, (int)c[V], (int)c[S]);
+        surf2DLayeredwrite(__half_as_ushort(__float2half_rn(v)), surf, cx, (int)c[V], layer);
     } else {
         const int bx = min((int)(x / B.x), nb.x - 1), by = min((int)(y / B.y), nb.y - 1);
         const int bz = min((int)(z / B.z), nb.z - 1);
         const float sc = scale[bx + nb.x * (by + nb.y * bz)];
-        surf2DLayeredwrite((signed char)e4m3_code(v / sc), surf, cx, (int)c[V], (int)c[S]);
+        surf2DLayeredwrite((signed char)e4m3_code(v / sc), surf, cx, (int)c[V], layer);
     }
 }
 
@@ -588,11 +595,14 @@ cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
 }
 
 cudaError_t fill_tex_layers(const float* a, int64_t nx, int64_t ny, int64_t nz, int64_t a_pitch, int S,
-                            int precision, cudaSurfaceObject_t surf, const float* scale, const int32_t B[3],
-                            const int32_t nb[3], cudaStream_t s) {
-    dim3 grid((unsigned)((nx + 255) / 256), (unsigned)ny, (unsigned)nz);
+                            int64_t l0, int64_t nl, int precision, cudaSurfaceObject_t surf, const float* scale,
+                            const int32_t B[3], const int32_t nb[3], cudaStream_t s) {
+    // the slab's extent along each axis (S restricted to [l0, l0 + nl))
+    const int64_t ex = S == 0 ? nl : nx, ey = S == 1 ? nl : ny, ez = S == 2 ? nl : nz;
+    const int64_t x_end = S == 0 ? l0 + nl : nx;
+    dim3 grid((unsigned)((ex + 255) / 256), (unsigned)ey, (unsigned)ez);
     const int3 b3 = make_int3(B[0], B[1], B[2]), n3 = make_int3(nb[0], nb[1], nb[2]);
-    auto go = [&](auto kern) { kern<<<grid, 256, 0, s>>>(a, nx, ny, nz, a_pitch, surf, scale, b3, n3); };
+    auto go = [&](auto kern) { kern<<<grid, 256, 0, s>>>(a, nx, ny, nz, a_pitch, l0, x_end, surf, scale, b3, n3); };
     if (precision == kPrecF16) {
         if (S == 0) go(texm::fill_layers_kernel<0, kPrecF16>);
         else if (S == 1) go(texm::fill_layers_kernel<1, kPrecF16>);
