@@ -217,6 +217,34 @@ inline bool rect_from_corners(const vr_camera& c, const CornerProj* const q[8], 
     return true;
 }
 
+// Projections of the brick grid's corner points x_i = min(i B, n - 1), i = 0..nb
+// per axis (x fastest): every brick box spans eight of them.
+inline void project_brick_grid(const vr_camera& cam, const Basis& b, const int64_t n[3], const int32_t B[3],
+                               const int64_t nb[3], std::vector<CornerProj>& proj) {
+    const int64_t g[3] = {nb[0] + 1, nb[1] + 1, nb[2] + 1};
+    proj.resize((size_t)(g[0] * g[1] * g[2]));
+    for (int64_t k = 0; k < g[2]; ++k)
+        for (int64_t j = 0; j < g[1]; ++j)
+            for (int64_t i = 0; i < g[0]; ++i) {
+                const double P[3] = {(double)std::min<int64_t>(i * B[0], n[0] - 1),
+                                     (double)std::min<int64_t>(j * B[1], n[1] - 1),
+                                     (double)std::min<int64_t>(k * B[2], n[2] - 1)};
+                proj[(size_t)((k * g[1] + j) * g[0] + i)] = project_corner(cam, b, P);
+            }
+}
+
+// Rendering rectangle of brick idx from the grid projections (box_rect of its box).
+inline bool brick_rect_from_grid(const vr_camera& cam, const std::vector<CornerProj>& proj, const int64_t nb[3],
+                                 const int64_t idx[3], int32_t rect[4]) {
+    const int64_t g0 = nb[0] + 1, g1 = nb[1] + 1;
+    const CornerProj* q[8];
+    for (int k = 0; k < 8; ++k) {
+        const int64_t gi = idx[0] + (k & 1), gj = idx[1] + ((k >> 1) & 1), gk = idx[2] + ((k >> 2) & 1);
+        q[k] = &proj[(size_t)((gk * g1 + gj) * g0 + gi)];
+    }
+    return rect_from_corners(cam, q, rect);
+}
+
 // Sampling region of brick (ix, iy, iz): [b*B, min((b+1)*B, n-1)] per axis.
 inline void brick_box(const int64_t n[3], const int32_t B[3], const int64_t idx[3], double lo[3],
                double hi[3]) {

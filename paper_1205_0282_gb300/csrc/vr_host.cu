@@ -302,20 +302,10 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
         else e[a] = std::min<int64_t>((int64_t)std::floor(E / c->B[a]), c->nb[a] - 1);
     }
 
-    // projections of the brick grid's corner points x_i = min(i B, n - 1): each
-    // brick box spans eight of them, so each is projected once, not per brick
-    const int64_t g[3] = {c->nb[0] + 1, c->nb[1] + 1, c->nb[2] + 1};
-    if (c->rect_cull) {
-        c->plan_proj.resize((size_t)(g[0] * g[1] * g[2]));
-        for (int64_t k = 0; k < g[2]; ++k)
-            for (int64_t j = 0; j < g[1]; ++j)
-                for (int64_t i = 0; i < g[0]; ++i) {
-                    const double P[3] = {(double)std::min<int64_t>(i * c->B[0], c->n[0] - 1),
-                                         (double)std::min<int64_t>(j * c->B[1], c->n[1] - 1),
-                                         (double)std::min<int64_t>(k * c->B[2], c->n[2] - 1)};
-                    c->plan_proj[(size_t)((k * g[1] + j) * g[0] + i)] = project_corner(cam, c->basis, P);
-                }
-    }
+    // projections of the brick grid's corner points: each brick box spans eight
+    // of them, so each is projected once, not per brick
+    const int64_t nb64[3] = {c->nb[0], c->nb[1], c->nb[2]};
+    if (c->rect_cull) project_brick_grid(cam, c->basis, c->n, c->B, nb64, c->plan_proj);
 
     c->plan_bricks.clear();
     s.bricks_skipped = 0;
@@ -335,12 +325,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
         vr_ctx::PB pb;
         pb.id = (int32_t)id;
         if (c->rect_cull) {
-            const CornerProj* q[8];
-            for (int k = 0; k < 8; ++k) {
-                const int64_t gi = idx[0] + (k & 1), gj = idx[1] + ((k >> 1) & 1), gk = idx[2] + ((k >> 2) & 1);
-                q[k] = &c->plan_proj[(size_t)((gk * g[1] + gj) * g[0] + gi)];
-            }
-            if (!rect_from_corners(cam, q, pb.rect)) continue;
+            if (!brick_rect_from_grid(cam, c->plan_proj, nb64, idx, pb.rect)) continue;
         } else {
             pb.rect[0] = pb.rect[1] = 0;
             pb.rect[2] = cam.width - 1;
@@ -1429,11 +1414,12 @@ int vr_plan_brick_rects(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz
     const int32_t B[3] = {bx, by, bz};
     const int64_t nb[3] = {bricks_along(nx, bx), bricks_along(ny, by), bricks_along(nz, bz)};
     if (nb[0] * nb[1] * nb[2] != n_bricks) return VR_EINVAL;
+    // the planner's computation (grid-corner projections, then each brick's box)
+    std::vector<CornerProj> proj;
+    project_brick_grid(*cam, b, n, B, nb, proj);
     for (int64_t id = 0; id < n_bricks; ++id) {
         int64_t idx[3] = {id % nb[0], (id / nb[0]) % nb[1], id / (nb[0] * nb[1])};
-        double lo[3], hi[3];
-        brick_box(n, B, idx, lo, hi);
-        box_rect(*cam, b, lo, hi, rects + 4 * id);
+        brick_rect_from_grid(*cam, proj, nb, idx, rects + 4 * id);
     }
     return VR_OK;
 }
