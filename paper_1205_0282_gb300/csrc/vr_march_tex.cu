@@ -6,7 +6,8 @@
 // interpolate; here the texture unit only gathers: tld4 returns the four texels of
 // a 2x2 footprint unchanged, and the interpolation weights are applied in FP32 as
 // in the other kernels, so no reduced-precision filtering enters the result.  The
-// cube is held three times, as layered textures whose layers run along x, y and z;
+// cube is held three times, as layered textures whose layers run along x, y and z
+// (each split along its layers into slabs of whole bricks plus one apron layer);
 // an item reads the copy whose layers run along its dominant ray axis, so the 32
 // rays of a warp sample one or two layers at a time and the gathers stay local in
 // the texture cache.
@@ -205,9 +206,8 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
     const float tau = p.tau;
     // brick origin along U, V plus one: gather coordinate of texel (u, v) is (u + 1, v + 1)
     const float ou = (float)(O[U] + 1), ov = (float)(O[V] + 1);
-    // Sample k's eight corners and weights.  The loop is software-pipelined: the
-    // gathers of sample k + 1 are issued before sample k is interpolated and
-    // composited, so texture latency overlaps the arithmetic.
+    // Sample k's eight corners and weights, gathered D samples ahead of their use
+    // (the software pipeline below).
     struct Corners {
         float c[8];  // (u, v, s) corners: c[0..3] in plane ps, c[4..7] in plane ps + 1
                      // (FP8: the raw codes, decoded when the sample is used, so that the
