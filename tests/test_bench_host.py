@@ -1,0 +1,36 @@
+"""bench.py host logic: recorded ncu figures are reported only for the sources
+they were captured on."""
+import json
+
+import bench
+
+
+def _record(tmp_path, sha):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps({"march_tex_kernel": {"hi": {
+        "kernel_source_sha": sha, "dram_bytes_per_launch": 9.0e9, "thread_inst_per_sample": 98.5}}}))
+
+
+def test_records_follow_the_source_hash(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
+    _record(tmp_path, "abc")
+    assert bench.recorded_traffic("march_tex_kernel", "hi") == 9.0e9
+    assert bench.recorded_inst_per_sample("march_tex_kernel", "hi") == 98.5
+    assert bench.recorded_traffic("march_tex_kernel", "hi_f16") is None
+    assert bench.recorded_inst_per_sample("march_kernel", "hi") is None
+
+
+def test_stale_records_are_not_reported(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "changed")
+    _record(tmp_path, "abc")
+    assert bench.recorded_traffic("march_tex_kernel", "hi") is None
+    assert bench.recorded_inst_per_sample("march_tex_kernel", "hi") is None
+
+
+def test_no_record_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic("march_tex_kernel", "hi") is None
+    assert bench.recorded_inst_per_sample("march_tex_kernel", "hi") is None
