@@ -37,6 +37,17 @@ def test_header_symbols_exported(vrmod):
     assert sorted(vrmod.EXPORTS) == names
 
 
+def test_header_constants_match_the_binding(vrmod):
+    """Every VR_* integer constant of include/vr.h has the same value in the
+    Python binding (error codes, options, kernels, precisions)."""
+    text = open(os.path.join(ROOT, "include", "vr.h")).read()
+    consts = {m[0]: m[1] or m[2] for m in
+              re.findall(r"^#define\s+(VR_[A-Z0-9_]+)\s+(?:\((-?\d+)\)|(-?\d+))(?:\s|$)", text, flags=re.M)}
+    assert len(consts) >= 21 and "VR_EINVAL" in consts and "VR_OPT_TEX_SLAB_LAYERS" in consts
+    for name, value in consts.items():
+        assert getattr(vrmod, name, None) == int(value), name
+
+
 def test_create_without_gpu_fails_cleanly(vrmod):
     import torch
     if torch.cuda.is_available():
