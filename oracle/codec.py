@@ -14,7 +14,9 @@ decoded by a shared MLP).  Definition, used by the GPU kernels and restated here
   h2 = silu(z2), y = w3 . h2 + b3;  silu(t) = t / (1 + exp(-t)).
 * Decoded value: v = y s_b + m_b (per-brick scale and offset).
 
-The tensor-core kernels take their operands in BF16 (round to nearest even):
+The latent grid is held in BF16 (the values interpolated are the BF16 roundings
+of the FP32 master latents that training updates), and the tensor-core kernels
+take their operands in BF16 (round to nearest even):
 the input row, W1, W2, w3, h1 (layer 2's input) and, in the backward pass, the
 layer gradients g2 = dL/dz2 and g1 = dL/dz1 where they enter a product (the
 bias gradients sum them unrounded).  With
@@ -87,7 +89,7 @@ def latent_interp(lat, brick, x):
 
 
 def input_rows(lat, brick, x, bf=True):
-    z = latent_interp(lat, brick, x)
+    z = latent_interp(bf16(lat) if bf else lat, brick, x)
     row = np.concatenate([z, fourier(x), np.zeros((len(brick), K_IN - LATENT - 12))], axis=1)
     return bf16(row) if bf else row
 
@@ -106,9 +108,11 @@ def forward(params, lat, brick, x, bf=True):
     return v, dict(IN=IN, z1=z1, h1=h1, z2=z2, h2=h2, y=y)
 
 
-def backward(params, lat, brick, x, target, bf=True):
+def backward(params, lat, brick, x, target, bf=True, cache=None):
     """Loss mean((v - t)^2) and its gradients with respect to W1, b1, W2, b2, w3,
-    b3 and the latent grid (same shape as lat)."""
+    b3 and the latent grid (same shape as lat).  If ``cache`` is a dict it
+    receives the intermediate values (forward pass, dy, the layer gradients
+    before and after rounding, dh1, din, the interpolation nodes and weights)."""
     W1, W2, w3, s = params["W1"], params["W2"], params["w3"], params["s"]
     q = bf16 if bf else (lambda a: np.asarray(a, dtype=np.float64))
     v, c = forward(params, lat, brick, x, bf)
@@ -135,6 +139,9 @@ def backward(params, lat, brick, x, target, bf=True):
     for k in range(8):
         np.add.at(dlat, (brick, idx[:, k, 2], idx[:, k, 1], idx[:, k, 0]), w[:, k:k + 1] * dz)
     g["lat"] = dlat
+    if cache is not None:
+        cache.update(c)
+        cache.update(v=v, dy=dy, g2f=g2f, g2=g2, dh1=dh1, g1f=g1f, g1=g1, din=din, idx=idx, w=w)
     return loss, g
 
 

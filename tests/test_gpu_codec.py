@@ -51,46 +51,72 @@ def _setup(vr, n_bricks=3, brick=(16, 16, 16), seed=5):
 
 
 def _points(rng, n, n_bricks, brick):
+    """Seeded points; the positions are rounded to FP32 (what the kernel is given)."""
     bricks = rng.integers(0, n_bricks, n)
     u = rng.uniform(0, 1, (n, 3)) * np.array(brick)
     u[: n // 8] = np.round(u[: n // 8])          # lattice points too
-    return bricks, u
+    return bricks, u.astype(np.float32).astype(np.float64)
 
 
 def test_codec_forward_matches_the_oracle(vr):
-    """Values of the tensor-core MLP against the FP64 definition with the same
-    BF16 rounding points.  The tensor cores accumulate in FP32 but not with one
-    IEEE rounding per addition, and the GPU forms the pre-rounding values in FP32,
-    so a BF16 rounding decision can land one step away from the FP64 one: 99% of
-    points agree to 5e-4, all to 1e-2 (relative to 1 + |v|; measured median
-    1.5e-5)."""
+    """Every decoded value against the FP64 definition with the same BF16
+    rounding points, within its own bound from the FP32/BF16 rounding model
+    (tests/codec_bounds.py): FP32 accumulation and approximate SiLU everywhere,
+    plus one BF16 step wherever the oracle's value lies within the GPU's error
+    of a rounding boundary, propagated to the output."""
+    from codec_bounds import forward_bound, forward_terms
     c, p, lat, rng = _setup(vr)
     bricks, u = _points(rng, 3000, 3, (16, 16, 16))
     got = c.forward(c.points(bricks, u)).astype(np.float64)
-    want, _ = ref.forward(p, lat, bricks, u / 16.0, bf=True)
+    x = u / 16.0
+    want, _ = ref.forward(p, lat, bricks, x, bf=True)
+    bound = forward_bound(p, lat, bricks, x)
     c.close()
-    e = np.abs(got - want) / (1.0 + np.abs(want))
-    assert np.quantile(e, 0.99) < 5e-4, np.quantile(e, [0.5, 0.99, 1.0])
-    assert np.median(e) < 1e-4
-    assert e.max() < 1e-2
+    err = np.abs(got - want)
+    bad = np.flatnonzero(err > bound)
+    assert bad.size == 0, (bad[:5], err[bad[:5]], bound[bad[:5]])
     assert np.std(want) > 0.1
+    # the bound is tight where no rounding decision can amplify an error
+    clean = ~forward_terms(p, lat, bricks, x)["ambiguous"]
+    assert clean.mean() > 0.4
+    assert np.median(bound[clean] / (1.0 + np.abs(want[clean]))) < 1e-4
 
 
 def test_codec_gradient_matches_the_oracle(vr):
+    """Loss and every gradient element (W1, b1, W2, b2, w3, b3, each latent
+    channel of each node) of a training step against the FP64 oracle, each
+    within its own bound from the rounding model (tests/codec_bounds.py).  The
+    batch keeps the points whose forward pass has no rounding decision that may
+    go the other way by an amplifying step (the backward pass's decisions stay
+    in the bound)."""
+    import torch
+
+    from codec_bounds import gradient_bounds, unambiguous_points
     c, p, lat, rng = _setup(vr)
-    bricks, u = _points(rng, 4096, 3, (16, 16, 16))
-    targets = rng.normal(size=len(bricks))
+    bricks, u = _points(rng, 6144, 3, (16, 16, 16))
+    keep = unambiguous_points(p, lat, bricks, u / 16.0)
+    bricks, u = bricks[keep], u[keep]
+    assert len(bricks) > 2000
+    targets = rng.normal(size=len(bricks)).astype(np.float32).astype(np.float64)
     loss, g = c.gradient(c.points(bricks, u), targets)
-    want_loss, want = ref.backward(p, lat, bricks, u / 16.0, targets, bf=True)
+    x = u / 16.0
+    want_loss, want = ref.backward(p, lat, bricks, x, targets, bf=True)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n_tiles = (len(bricks) + 127) // 128
+    bounds = gradient_bounds(p, lat, bricks, x, targets, grid=min(n_tiles, 2 * sms))
     c.close()
     got = c.unpack(g.astype(np.float64))
-    assert abs(loss - want_loss) <= 1e-4 * want_loss
+    assert abs(loss - want_loss) <= bounds["loss"], (loss, want_loss, bounds["loss"])
     for name in ("W1", "b1", "W2", "b2", "w3", "b3", "lat"):
-        a, b = got[name].reshape(-1), np.asarray(want[name]).reshape(-1)
+        a, b, e = got[name], np.asarray(want[name]), bounds[name]
         if name == "W1":
-            a, b = got[name][:, :28].reshape(-1), want[name][:, :28].reshape(-1)
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        assert rel < 2e-3, (name, rel)
+            a, b, e = a[:, :28], b[:, :28], e[:, :28]
+        a, b, e = a.reshape(-1), b.reshape(-1), e.reshape(-1)
+        bad = np.flatnonzero(np.abs(a - b) > e)
+        assert bad.size == 0, (name, bad[:5], a[bad[:5]], b[bad[:5]], e[bad[:5]])
+        # the largest element of each block is pinned to well under 1%
+        k = int(np.argmax(np.abs(b)))
+        assert e[k] < 1e-2 * abs(b[k]), (name, e[k], b[k])
     assert np.abs(got["W1"][:, 28:]).max() == 0.0   # the padded inputs are zero
 
 
