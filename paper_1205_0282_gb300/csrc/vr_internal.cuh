@@ -76,7 +76,7 @@ struct FrameParams {
     int32_t B[3];          // brick size
     int32_t nb[3];         // bricks per axis
     int64_t stride_y, stride_z;
-    int32_t offsets32;     // 1: (B+1) * stride_z < 2^31, brick-local offsets fit in 32 bits
+    int32_t offsets32;     // 1: (B+1) * stride_z < 2^32, brick-local offsets fit in uint32_t
 
     // transfer function: control points (r,g,b,a) and their values; tf_rgba has
     // tf_n + 1 entries, the last one repeating point tf_n - 1

@@ -6,14 +6,22 @@
 // implicit device synchronisation of cudaMalloc/cudaFree, or an embedding whose
 // allocator is not CUDA's.  For them this file keeps all of the frame's scratch
 // (frame constants, work list, per-brick sub-image fragments, counters) in one
-// file-scope static device array, and the planner's host-side lists in static
-// host arrays.  The caller passes the cube (device memory), the transfer
-// function, the camera and the output image (device memory).
+// file-scope static device array, and the planner's lists in static host
+// arrays.  The caller passes the cube (device memory), the transfer function,
+// the camera and the output image (device memory).
 //
-// The kernels are the library's ray-march and sort-last composite kernels; only
-// where their scratch lives differs.  Every call shares the same scratch: calls
-// that overlap on the GPU (for example on two streams) race, and the host-side
-// lists make the function unsafe to call from two host threads at once.
+// The kernels are the library's direct-gather ray march and sort-last composite
+// kernels; only where their scratch lives differs.  Every call shares the same
+// device scratch: calls that overlap on the GPU (for example on two streams)
+// race, and the host-side lists make the function unsafe to call from two host
+// threads at once.
+//
+// Set-up, done by the first call on each device (and once per process): the
+// device address of the scratch array (cudaGetSymbolAddress), two events that
+// mark when each of the two host staging sets has been uploaded, and the
+// page-locking of those sets (cudaHostRegister, which pins the existing static
+// arrays and allocates nothing), so that the uploads are asynchronous copies.
+// Call n fills staging set n % 2 after waiting for the uploads of call n - 2.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -45,19 +53,54 @@ constexpr size_t kMaxItems =
     (kScratchBytes - kStatsBytes - kConstBytes - ((size_t)kMaxTiles + 1) * sizeof(int32_t)) /
     (kFragBytesPerItem + sizeof(vr::Item));
 
-static vr::Item h_items[kMaxItems];
-static int32_t h_tile_start[kMaxTiles + 1];
+// Host staging of what each call uploads (two sets, page-locked at set-up).
+struct alignas(4096) HostStage {
+    vr::Item items[kMaxItems];
+    int32_t tile_start[kMaxTiles + 1];
+    unsigned char cst[kConstBytes];
+};
+static HostStage g_stage[2];
+static int g_stage_pinned = -1;          // -1: not tried; 0: pageable; 1: page-locked
+static unsigned long long g_calls = 0;   // calls that uploaded (picks the staging set)
+static int g_stage_dev[2] = {-1, -1};    // device whose event marks each set's last upload
+static cudaEvent_t g_stage_done[kMaxDevices][2];
+static bool g_events_made[kMaxDevices];
+
+// Planner lists that stay on the host.
 static int32_t h_fill[kMaxTiles];
-static unsigned char h_const[kConstBytes];
 struct PlanBrick {
     int32_t key, id, rect[4];
 };
 static PlanBrick h_bricks[kMaxBricks];
+static PlanBrick h_sorted[kMaxBricks];
+// View-order keys sum |b_a - e_a| over the axes, with 0 <= b_a < nb_a and
+// -1 <= e_a <= nb_a, so a key is at most nb_x + nb_y + nb_z <= 3 * kMaxBricks.
+constexpr int kMaxKey = 3 * kMaxBricks;
+static int32_t h_key_start[kMaxKey + 2];
 
 // Set-up, once per device, with that device current: the device address of the
-// scratch array.  Returns nullptr on failure.
+// scratch array and the staging events; once per process: the page-locking of
+// the staging sets (if that fails they stay pageable: still correct, but the
+// copies may then wait for the stream).  Returns nullptr on failure.
 void* scratch_on_current_device(int dev) {
     if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    if (!g_events_made[dev]) {
+        if (cudaEventCreateWithFlags(&g_stage_done[dev][0], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaEventCreateWithFlags(&g_stage_done[dev][1], cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventDestroy(g_stage_done[dev][0]);
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_events_made[dev] = true;
+    }
+    if (g_stage_pinned < 0) {
+        g_stage_pinned =
+            cudaHostRegister(g_stage, sizeof(g_stage), cudaHostRegisterPortable) == cudaSuccess ? 1 : 0;
+        cudaGetLastError();
+    }
     if (g_scratch_ptr[dev]) return g_scratch_ptr[dev];
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess) {
@@ -154,14 +197,19 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
     if (n_bricks > kMaxBricks) return VR_EINVAL;
     Basis b;
     if (!basis_of(*cam, b)) return VR_EINVAL;
-    cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, out_rgba) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
-        cudaPointerGetAttributes(&attr, cube) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
-        cudaGetLastError();
-        return VR_EINVAL;  // both the cube and the image must be device memory
-    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return VR_ECUDA;
+    // both the cube and the image must be device memory of the current device
+    // (the kernels run there and read and write them without peer access)
+    cudaPointerAttributes a_out, a_cube;
+    if (cudaPointerGetAttributes(&a_out, out_rgba) != cudaSuccess ||
+        cudaPointerGetAttributes(&a_cube, cube) != cudaSuccess) {
+        cudaGetLastError();
+        return VR_EINVAL;
+    }
+    if (a_out.type != cudaMemoryTypeDevice || a_cube.type != cudaMemoryTypeDevice || a_out.device != dev ||
+        a_cube.device != dev)
+        return VR_EINVAL;
     unsigned char* scratch = static_cast<unsigned char*>(scratch_on_current_device(dev));
     if (!scratch) return VR_ECUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -189,33 +237,45 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
         for (int a = 0; a < 3; ++a) pb.key += (int32_t)std::llabs(idx[a] - e[a]);
         h_bricks[n_pb++] = pb;
     }
-    std::stable_sort(h_bricks, h_bricks + n_pb, [](const PlanBrick& x, const PlanBrick& y) { return x.key < y.key; });
+    // front-to-back order: a stable counting sort on the view-order key
+    std::memset(h_key_start, 0, sizeof(h_key_start));
+    for (int q = 0; q < n_pb; ++q) h_key_start[h_bricks[q].key + 1]++;
+    for (int k = 0; k <= kMaxKey; ++k) h_key_start[k + 1] += h_key_start[k];
+    for (int q = 0; q < n_pb; ++q) h_sorted[h_key_start[h_bricks[q].key]++] = h_bricks[q];
     const int tiles_x = (cam->width + kTileSide - 1) / kTileSide, tiles_y = (cam->height + kTileSide - 1) / kTileSide;
     const int n_tiles = tiles_x * tiles_y;
     std::memset(h_fill, 0, sizeof(int32_t) * n_tiles);
     int64_t n_items = 0;
     for (int q = 0; q < n_pb; ++q) {
-        const PlanBrick& pb = h_bricks[q];
+        const PlanBrick& pb = h_sorted[q];
         for (int ty = pb.rect[1] / kTileSide; ty <= pb.rect[3] / kTileSide; ++ty)
             for (int tx = pb.rect[0] / kTileSide; tx <= pb.rect[2] / kTileSide; ++tx) h_fill[ty * tiles_x + tx]++;
         n_items += (int64_t)(pb.rect[2] / kTileSide - pb.rect[0] / kTileSide + 1) *
                    (pb.rect[3] / kTileSide - pb.rect[1] / kTileSide + 1);
     }
     if (n_items > (int64_t)kMaxItems) return VR_EINVAL;  // frame needs more scratch than the array holds
+    // the staging set of this call: wait until the call that used it last has
+    // uploaded it (two calls back; normally long done)
+    const int set = (int)(g_calls & 1);
+    if (g_stage_dev[set] >= 0 && cudaEventSynchronize(g_stage_done[g_stage_dev[set]][set]) != cudaSuccess) {
+        cudaGetLastError();
+        return VR_ECUDA;
+    }
+    HostStage& hs = g_stage[set];
     int32_t run = 0;
     for (int t = 0; t < n_tiles; ++t) {
-        h_tile_start[t] = run;
+        hs.tile_start[t] = run;
         run += h_fill[t];
         h_fill[t] = 0;
     }
-    h_tile_start[n_tiles] = run;
+    hs.tile_start[n_tiles] = run;
     int64_t k = 0;
     for (int q = 0; q < n_pb; ++q) {
-        const PlanBrick& pb = h_bricks[q];
+        const PlanBrick& pb = h_sorted[q];
         for (int ty = pb.rect[1] / kTileSide; ty <= pb.rect[3] / kTileSide; ++ty)
             for (int tx = pb.rect[0] / kTileSide; tx <= pb.rect[2] / kTileSide; ++tx) {
                 const int t = ty * tiles_x + tx;
-                h_items[k++] = vr::Item{pb.id, t, h_tile_start[t] + h_fill[t]++, 0};
+                hs.items[k++] = vr::Item{pb.id, t, hs.tile_start[t] + h_fill[t]++, 0};
             }
     }
 
@@ -225,13 +285,13 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
     const size_t tf_v_off = tf_rgba_off + (size_t)(n_tf + 1) * sizeof(float4);
     const size_t const_bytes = tf_v_off + (size_t)n_tf * sizeof(float);
     if (const_bytes > kConstBytes) return VR_EINVAL;
-    vr::df* hq = reinterpret_cast<vr::df*>(h_const);
+    vr::df* hq = reinterpret_cast<vr::df*>(hs.cst);
     for (int i = 0; i < cam->width; ++i)
         hq[i] = vr::df_from_double((2.0 * (i + 0.5) / cam->width - 1.0) * b.tan_half * b.aspect);
     for (int j = 0; j < cam->height; ++j)
         hq[cam->width + j] = vr::df_from_double((1.0 - 2.0 * (j + 0.5) / cam->height) * b.tan_half);
-    float4* hrgba = reinterpret_cast<float4*>(h_const + tf_rgba_off);
-    float* hv = reinterpret_cast<float*>(h_const + tf_v_off);
+    float4* hrgba = reinterpret_cast<float4*>(hs.cst + tf_rgba_off);
+    float* hv = reinterpret_cast<float*>(hs.cst + tf_v_off);
     for (int i = 0; i < n_tf; ++i) {
         hrgba[i] = make_float4((float)tf[5 * i + 1], (float)tf[5 * i + 2], (float)tf[5 * i + 3], (float)tf[5 * i + 4]);
         hv[i] = (float)tf[5 * i];
@@ -303,11 +363,24 @@ extern "C" int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int6
     p.stats = reinterpret_cast<vr::Stats*>(d_stats);
 
     // The counters must start at zero; the rest of the scratch is fully rewritten.
+    // The staging set is marked in use by this call from its first copy on.
+    g_stage_dev[set] = -1;
     if (cudaMemsetAsync(d_stats, 0, sizeof(vr::Stats), st) != cudaSuccess ||
-        cudaMemcpyAsync(d_const, h_const, const_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(d_tiles, h_tile_start, ((size_t)n_tiles + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(d_items, h_items, (size_t)n_items * sizeof(vr::Item), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        vr::launch_march(p, st) != cudaSuccess || vr::launch_composite(p, st) != cudaSuccess) {
+        cudaMemcpyAsync(d_const, hs.cst, const_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_tiles, hs.tile_start, ((size_t)n_tiles + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(d_items, hs.items, (size_t)n_items * sizeof(vr::Item), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaEventRecord(g_stage_done[dev][set], st) != cudaSuccess) {
+        // copies may be in flight: wait for the stream before the set is reused
+        cudaGetLastError();
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        return VR_ECUDA;
+    }
+    g_stage_dev[set] = dev;
+    ++g_calls;
+    if (vr::launch_march(p, st) != cudaSuccess || vr::launch_composite(p, st) != cudaSuccess) {
         cudaGetLastError();
         return VR_ECUDA;
     }

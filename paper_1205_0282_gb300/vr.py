@@ -579,9 +579,21 @@ class Server:
 
 
 def vr_render_noalloc(cube, brick, points, cam: dict, out, stream=None) -> None:
-    """Allocation-free render: ``cube`` and ``out`` are CUDA tensors (float32
-    (nz, ny, nx) and (H, W, 4)); scratch lives in the library's static device
-    array, so calls that overlap on the GPU race."""
+    """Allocation-free render: ``cube`` and ``out`` are float32 CUDA tensors of
+    shapes (nz, ny, nx) and (H, W, 4) on the current device; scratch lives in
+    the library's static device array, so calls that overlap on the GPU race.
+    Raises ValueError for any other shape, dtype or device before calling the
+    library (the library reads and writes by the sizes it is given)."""
+    import torch
+    for name, t in (("cube", cube), ("out", out)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32:
+            raise ValueError(f"{name} must be a float32 torch tensor")
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device")
+    if cube.dim() != 3:
+        raise ValueError("cube must have shape (nz, ny, nx)")
+    if tuple(out.shape) != (int(cam["height"]), int(cam["width"]), 4):
+        raise ValueError(f"out must have shape ({cam['height']}, {cam['width']}, 4)")
     nz, ny, nx = cube.shape
     caddr, ckeep = _ptr(cube)
     oaddr, okeep = _ptr(out)
