@@ -221,20 +221,31 @@ int vr_brick(vr_ctx* ctx, int32_t bx, int32_t by, int32_t bz);
  * r, g, b, a in [0, 1]; a is the opacity per unit voxel of path.  Values
  * between points are interpolated linearly, values outside take the end
  * points.  Per sample alpha = 1 - (1 - a)^(step / 1 voxel).  n <= 256.
- * Host-side only: takes effect for the next vr_render.  Errors: VR_EINVAL.
+ * The rows are doubles (the camera is given in doubles too): the kernels use
+ * each value rounded to FP32, the difference lying far below the image
+ * tolerance.  Host-side only: takes effect for the next vr_render.
+ * Errors: VR_EINVAL.
  */
 int vr_set_transfer_function(vr_ctx* ctx, const double* points, int32_t n);
 
-/* Set the camera; see vr_camera.  width, height in [1, 16384].  Host-side
- * only: takes effect for the next vr_render, frames already enqueued are not
- * affected.  Errors: VR_EINVAL (degenerate basis, bad sizes). */
+/* Set the camera (Section 2.3.2: the viewer's projection and view transforms
+ * fix every pixel's ray; see vr_camera for the equivalent look-at form).
+ * width, height in [1, 16384].  Host-side only: takes effect for the next
+ * vr_render, frames already enqueued are not affected.
+ * Errors: VR_EINVAL (degenerate basis, bad sizes). */
 int vr_set_camera(vr_ctx* ctx, const vr_camera* cam);
 
 /* Set an option (VR_OPT_*).  Errors: VR_EINVAL. */
 int vr_set_option(vr_ctx* ctx, int32_t option, int64_t value);
 
 /*
- * Render one frame into out_rgba: float32[height][width][4], premultiplied
+ * Render one frame (Section 2.3.2, ray casting: for every brick that is not
+ * empty for the transfer function, the pixels of its rendering rectangle cast
+ * rays through it, sampling tri-linearly from the ray's entry into the cube and
+ * stopping at the brick's exit or once the opacity reaches term_alpha;
+ * Section 2.3.3, composition: the per-brick sub-images are folded front to back
+ * with the associative 'over' operator, stopping once a pixel's opacity reaches
+ * term_alpha) into out_rgba: float32[height][width][4], premultiplied
  * (r, g, b, alpha), row 0 at the top, no background.  out_rgba may be device
  * memory (written asynchronously on `cuda_stream`, a cudaStream_t or NULL for
  * the legacy default stream) or host memory (the call then copies the image
@@ -545,14 +556,23 @@ int vr_codec_brick_errors(vr_ctx* ctx, float* err, int64_t* n_plain);
  *   tf_points: host memory, n_tf rows (v, r, g, b, a) as for vr_set_transfer_function.
  *   cam:       as for vr_set_camera, with width and height <= 1024.
  *   out_rgba:  device memory, float32[height][width][4], written on cuda_stream.
- * Runs on the current CUDA device.  The first call on each device looks up the
- * scratch array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the scratch, which keeps the last
- * call's contents (the counters are cleared by each call, everything else is
+ * Runs on the current CUDA device; cube and out_rgba must be device memory of
+ * that device.  The frame is marched by the direct-gather kernel (corners read
+ * through the L1 cache), which gives the same image as vr_render's other
+ * kernels up to FP32 rounding.  Set-up: the first call on each device looks up
+ * the scratch array's device address (cudaGetSymbolAddress) and creates two
+ * events, and the first call in the process page-locks the library's two static
+ * host staging sets of the plan (cudaHostRegister, which allocates nothing);
+ * make that first call before any stream capture.  Each call's plan uploads are
+ * then asynchronous copies from one staging set; a call waits (on the host)
+ * until the uploads of the call two before it, which used the same set, are
+ * done.  All calls share the device scratch, which keeps the last call's
+ * contents (the counters are cleared by each call, everything else is
  * rewritten): calls that overlap on the GPU race, and the function must not be
  * called from two host threads at once.
- * Errors: VR_EINVAL (bad argument, host-memory cube or image, or a frame whose
- * work list needs more than VR_NOALLOC_SCRATCH_BYTES), VR_ECUDA.
+ * Errors: VR_EINVAL (bad argument, a cube or image that is host memory or
+ * memory of another device, or a frame whose work list needs more than
+ * VR_NOALLOC_SCRATCH_BYTES), VR_ECUDA.
  */
 #define VR_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
 int vr_render_noalloc(const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t bx, int32_t by,
