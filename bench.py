@@ -1,9 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the bricked ray caster on the HI-survey workload.
 
-One step = one frame of the whole hot path at the next pose of a 120-pose orbit
-about the y axis: host plan (rendering rectangles, empty-space skipping, view
-order), ray march of every (brick, tile) item, sort-last 'over' composite.
+One step = one frame of the whole hot path at a pose of a 120-pose orbit about
+the y axis: host plan (rendering rectangles, empty-space skipping, view order),
+ray march of every (brick, tile) item, sort-last 'over' composite.  K timed
+steps visit K poses evenly spaced over the orbit (all 120 when K = 120), so the
+frame rate is an orbit mean; warm-up frames render poses spread over the orbit
+too.
 
 Workload (default): float32 cube 1024 x 1024 x 2048 (8 GiB; noise + 2000 line
 sources + 50 continuum sources), 128^3 bricks, 1920 x 1080 image, step 0.5
@@ -318,6 +321,13 @@ def my_share(items, rank: int, world: int):
     return list(items[rank::world]) if world > 1 else list(items)
 
 
+def orbit_index(k: int, count: int, n: int) -> int:
+    """Pose of frame k of `count` frames over an orbit of n poses: evenly spaced
+    (floor(k n / count)) when count < n, else every pose in turn, so that the
+    timed frames cover the whole orbit whatever the step count."""
+    return (k * n) // count % n if count < n else k % n
+
+
 def job_totals(dist, elapsed: float, counts, device="cpu"):
     """Whole-job numbers over ranks: the slowest rank's time (max) and the summed
     counts (samples, frames, launches ...).  dist is torch.distributed or None."""
@@ -413,8 +423,11 @@ def run_ours(args):
         leaf_streams = [torch.cuda.Stream() for _ in range(args.shard)]
         leaf_bufs = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(args.shard)]
 
+    def orbit_pose(k, count):
+        return my_poses[orbit_index(k, count, len(my_poses))]
+
     def frame(k):
-        draw(my_poses[k % len(my_poses)])
+        draw(orbit_pose(k, args.steps))
 
     def draw(cam):
         r.set_camera(cam)
@@ -442,7 +455,7 @@ def run_ours(args):
                                    stream)
 
     for k in range(args.warmup):
-        frame(k)
+        draw(orbit_pose(2 * k + 1, 2 * max(args.warmup, 1)))   # spread over the orbit
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -576,6 +589,11 @@ def run_ours(args):
                                       + (f"; each frame as {args.shard} virtual ranks (k-d leaves) on one GPU"
                                          if args.shard > 1 else "")},
             "fps": frames / (elapsed_ms * 1e-3),
+            "orbit": {"poses": len(poses), "timed_poses": min(args.steps, len(my_poses)),
+                      "rule": "timed frame k renders pose floor(k * poses / steps) (evenly spaced over "
+                              "the orbit; each pose once when steps is a multiple of the pose count)",
+                      "mean_fps": frames / (elapsed_ms * 1e-3),
+                      "frame_ms_p75": float(np.percentile(frame_ms, 75))},
             "frame_ms_p50": float(np.percentile(frame_ms, 50)),
             "frame_ms_p75": float(np.percentile(frame_ms, 75)),
             "samples_per_frame": samples / max(frames, 1),

@@ -1,5 +1,5 @@
 """bench.py host logic: recorded ncu figures are reported only for the sources
-they were captured on."""
+they were captured on; timed frames cover the whole orbit."""
 import json
 
 import bench
@@ -34,3 +34,11 @@ def test_no_record_file(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.recorded_traffic("march_tex_kernel", "hi") is None
     assert bench.recorded_inst_per_sample("march_tex_kernel", "hi") is None
+
+
+def test_timed_frames_span_the_orbit():
+    idx = [bench.orbit_index(k, 20, 120) for k in range(20)]
+    assert idx == list(range(0, 120, 6))
+    assert sorted(bench.orbit_index(k, 120, 120) for k in range(120)) == list(range(120))
+    assert [bench.orbit_index(k, 240, 120) for k in (0, 119, 120, 239)] == [0, 119, 0, 119]
+    assert [bench.orbit_index(2 * k + 1, 10, 120) for k in range(5)] == [12, 36, 60, 84, 108]
