@@ -196,7 +196,87 @@ cudaError_t launch_march(const FrameParams& p, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ composite
+//
+// Sort-last composition (Section 2.3.3): a pixel's fragments, one per brick in
+// view order, are folded front to back with the associative 'over' operator
+// until the accumulated opacity reaches tau.  A warp folds eight pixels at a
+// time: lane l holds fragment j = l / 8 of a chunk of four fragments of pixel
+// l % 8 (the eight pixels' fragments of one brick are contiguous, so each load
+// is coalesced).  An inclusive scan over the four lanes of a pixel (shuffles up
+// by 8 and 16 lanes) gives every prefix of the chunk, the prefix of the earlier
+// chunks is put in front, and the first prefix whose opacity reaches tau is the
+// pixel's value, as in the serial fold that stops after that fragment.
 
+// 'over' of a front and a back fragment (premultiplied RGBA)
+__device__ __forceinline__ float4 over(const float4 f, const float4 b) {
+    const float tr = 1.0f - f.w;
+    return make_float4(fmaf(tr, b.x, f.x), fmaf(tr, b.y, f.y), fmaf(tr, b.z, f.z), fmaf(tr, b.w, f.w));
+}
+
+__device__ __forceinline__ float4 shfl_up4(const float4 v, int d) {
+    return make_float4(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d),
+                       __shfl_up_sync(0xffffffffu, v.z, d), __shfl_up_sync(0xffffffffu, v.w, d));
+}
+
+__device__ __forceinline__ float4 shfl4(const float4 v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
+// Front-to-back fold of the fragments [f0, f1) of pixel group g (pixels 8g..8g+7
+// of a tile of TT pixels; fragment f of pixel q at frags[f TT + q]).  Called by
+// a whole warp; lanes l and l + 8, l + 16, l + 24 return pixel 8g + l % 8's value.
+__device__ __forceinline__ float4 fold_over_warp(const float4* __restrict__ frags, int TT, int g, int f0, int f1,
+                                                 float tau) {
+    const int lane = threadIdx.x & 31, q = lane & 7, j = lane >> 3;
+    const int pix = g * 8 + q;
+    float4 carry = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    bool done = false;
+    for (int c = f0; c < f1; c += 4) {
+        const int f = c + j;
+        float4 v = f < f1 ? frags[(int64_t)f * TT + pix] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        // inclusive 'over' scan of the chunk across the four lanes of each pixel
+        float4 u = shfl_up4(v, 8);
+        if (j >= 1) v = over(u, v);
+        u = shfl_up4(v, 16);
+        if (j >= 2) v = over(u, v);
+        const float4 total = over(carry, v);
+        // first fragment of the chunk at which the pixel's opacity reaches tau
+        const unsigned hit = __ballot_sync(0xffffffffu, !done && f < f1 && total.w >= tau);
+        const unsigned mine = (hit >> q) & 0x01010101u;
+        const int src = mine ? (__ffs(mine) - 1) + q : 24 + q;
+        const float4 pick = shfl4(total, src);
+        if (!done) carry = pick;
+        done = done || mine != 0;
+        if (__all_sync(0xffffffffu, done)) break;
+    }
+    return carry;
+}
+
+// Maximum intensity projection: the colour map of the largest value over the
+// fragments that saw samples (fragment = (max, 1 if any sample, 0, 0)).
+__device__ __forceinline__ float fold_max_warp(const float4* __restrict__ frags, int TT, int g, int f0, int f1,
+                                               bool& any) {
+    const int lane = threadIdx.x & 31, q = lane & 7, j = lane >> 3;
+    const int pix = g * 8 + q;
+    float vmax = -FLT_MAX;
+    int seen = 0;
+    for (int f = f0 + j; f < f1; f += 4) {
+        const float4 fr = frags[(int64_t)f * TT + pix];
+        if (fr.y > 0.0f) {
+            vmax = fmaxf(vmax, fr.x);
+            seen = 1;
+        }
+    }
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 8));
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, 16));
+    seen |= __shfl_xor_sync(0xffffffffu, seen, 8);
+    seen |= __shfl_xor_sync(0xffffffffu, seen, 16);
+    any = seen != 0;
+    return vmax;
+}
+
+// One CTA of 256 threads (8 warps) per tile; warp w folds pixel groups w, w + 8, ...
 __global__ void __launch_bounds__(256) composite_kernel(const FrameParams p) {
     __shared__ TfShared s_tf;
     if (p.mode == 1) {
@@ -209,71 +289,52 @@ __global__ void __launch_bounds__(256) composite_kernel(const FrameParams p) {
     const int t = blockIdx.x;
     const int T = p.tile, TT = p.tile * p.tile;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
-    const int i = tx * T + threadIdx.x % T, j = ty * T + threadIdx.x / T;
-    if (i >= p.width || j >= p.height) return;
     const int f0 = p.tile_start[t], f1 = p.tile_start[t + 1];
-    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (p.mode == 0) {
-        for (int f = f0; f < f1; ++f) {
-            if (acc.w >= p.tau) break;
-            const float4 fr = p.frags[(int64_t)f * TT + threadIdx.x];
-            const float tr = 1.0f - acc.w;
-            acc.x = fmaf(tr, fr.x, acc.x);
-            acc.y = fmaf(tr, fr.y, acc.y);
-            acc.z = fmaf(tr, fr.z, acc.z);
-            acc.w = fmaf(tr, fr.w, acc.w);
-        }
-    } else {
-        float vmax = -FLT_MAX;
-        bool any = false;
-        for (int f = f0; f < f1; ++f) {
-            const float4 fr = p.frags[(int64_t)f * TT + threadIdx.x];
-            if (fr.y > 0.0f) {
-                vmax = fmaxf(vmax, fr.x);
-                any = true;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int g = warp; g < TT / 8; g += 8) {
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (p.mode == 0) {
+            acc = fold_over_warp(p.frags, TT, g, f0, f1, p.tau);
+        } else {
+            bool any;
+            const float vmax = fold_max_warp(p.frags, TT, g, f0, f1, any);
+            if (any) {
+                const float4 c = p.tf_uniform ? tf_lookup<true>(p, s_tf.rgba, s_tf.v, vmax)
+                                             : tf_lookup<false>(p, s_tf.rgba, s_tf.v, vmax);
+                acc = make_float4(c.x * c.w, c.y * c.w, c.z * c.w, c.w);
             }
         }
-        if (any) {
-            const float4 c = p.tf_uniform ? tf_lookup<true>(p, s_tf.rgba, s_tf.v, vmax)
-                                         : tf_lookup<false>(p, s_tf.rgba, s_tf.v, vmax);
-            acc = make_float4(c.x * c.w, c.y * c.w, c.z * c.w, c.w);
-        }
+        const int pix = g * 8 + (lane & 7);
+        const int i = tx * T + pix % T, j = ty * T + pix / T;
+        const int wi = i - p.out_x0, wj = j - p.out_y0;
+        if (lane < 8 && i < p.width && j < p.height && wi >= 0 && wi < p.out_w && wj >= 0 && wj < p.out_h)
+            p.out[(int64_t)wj * p.out_w + wi] = acc;
     }
-    const int wi = i - p.out_x0, wj = j - p.out_y0;
-    if (wi >= 0 && wi < p.out_w && wj >= 0 && wj < p.out_h) p.out[(int64_t)wj * p.out_w + wi] = acc;
 }
 
-// Batch composite: block b is tile b - cams[k].tile_base of the frame k whose
-// blocks contain b (emission-absorption, 8x8 tiles).
-__global__ void __launch_bounds__(kTilePixels) composite_batch_kernel(const FrameParams p) {
+// Batch composite (emission-absorption, 8x8 tiles): block b is tile
+// b - cams[k].tile_base of the frame k whose blocks contain b.
+__global__ void __launch_bounds__(256) composite_batch_kernel(const FrameParams p) {
     int k = 0;
     while (k + 1 < p.n_cams && (int)blockIdx.x >= p.cams[k + 1].tile_base) ++k;
     const FrameCam& cam = p.cams[k];
     const int t = blockIdx.x - cam.tile_base;
     const int tx = t % cam.tiles_x, ty = t / cam.tiles_x;
-    const int i = tx * kTile + threadIdx.x % kTile, j = ty * kTile + threadIdx.x / kTile;
-    if (i >= cam.width || j >= cam.height) return;
     const int f0 = cam.tile_start[t], f1 = cam.tile_start[t + 1];
-    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int f = f0; f < f1; ++f) {
-        if (acc.w >= p.tau) break;
-        const float4 fr = p.frags[(int64_t)f * kTilePixels + threadIdx.x];
-        const float tr = 1.0f - acc.w;
-        acc.x = fmaf(tr, fr.x, acc.x);
-        acc.y = fmaf(tr, fr.y, acc.y);
-        acc.z = fmaf(tr, fr.z, acc.z);
-        acc.w = fmaf(tr, fr.w, acc.w);
-    }
-    cam.out[(int64_t)j * cam.width + i] = acc;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;  // 8 warps, one pixel group each
+    const float4 acc = fold_over_warp(p.frags, kTilePixels, g, f0, f1, p.tau);
+    const int pix = g * 8 + (lane & 7);
+    const int i = tx * kTile + pix % kTile, j = ty * kTile + pix / kTile;
+    if (lane < 8 && i < cam.width && j < cam.height) cam.out[(int64_t)j * cam.width + i] = acc;
 }
 
 cudaError_t launch_composite_batch(const FrameParams& p, int32_t total_tiles, cudaStream_t s) {
-    if (total_tiles > 0) composite_batch_kernel<<<total_tiles, kTilePixels, 0, s>>>(p);
+    if (total_tiles > 0) composite_batch_kernel<<<total_tiles, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_composite(const FrameParams& p, cudaStream_t s) {
-    composite_kernel<<<p.tiles_x * p.tiles_y, p.tile * p.tile, 0, s>>>(p);
+    composite_kernel<<<p.tiles_x * p.tiles_y, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -159,8 +159,11 @@ def test_skip_and_cull_do_not_change_the_image(vr, torch):
     noskip, st2 = gpu_render(vr, torch, cube, tf, cam, (16, 16, 16), {vr.VR_OPT_SKIP_EMPTY: 0})
     nocull, st3 = gpu_render(vr, torch, cube, tf, cam, (16, 16, 16), {vr.VR_OPT_RECT_CULL: 0})
     assert st2["bricks_skipped"] == 0 and st3["items"] > st["items"]
-    np.testing.assert_array_equal(base, nocull)
-    np.testing.assert_allclose(base, noskip, rtol=0, atol=1e-7)
+    # the dropped fragments are exactly zero; the composite's shuffle scan groups a
+    # pixel's fragments in fours, so extra zero fragments can regroup the 'over'
+    # products: equal up to FP32 rounding (one ulp of values <= 1)
+    np.testing.assert_allclose(base, nocull, rtol=0, atol=1.2e-7)
+    np.testing.assert_allclose(base, noskip, rtol=0, atol=1.2e-7)
     ref, amb, _ = oracle_render(cube, tf, cam, (16, 16, 16))
     assert_parity(base, ref, amb, min_signal=0.01)
 

@@ -57,7 +57,10 @@ def test_render_rect_is_the_crop_of_the_full_render(vr, torch, kernel):
         for rect in [(0, 0, 100, 76), (3, 5, 50, 41), (17, 9, 17, 60), (90, 70, 100, 76), (40, 0, 99, 0)]:
             x0, y0, x1, y1 = rect
             sub = r.render_rect(rect).cpu().numpy()
-            assert np.array_equal(sub, full[y0:y1 + 1, x0:x1 + 1]), rect
+            # a rectangle can drop bricks whose fragments are exactly zero; the
+            # composite's shuffle scan groups fragments in fours, so the 'over'
+            # products may regroup: equal up to one FP32 ulp of values <= 1
+            assert np.abs(sub - full[y0:y1 + 1, x0:x1 + 1]).max() <= 1.2e-7, rect
             host = np.zeros_like(sub)
             vr.vr_render_rect(r.ctx, rect, host)
             assert np.array_equal(host, sub)
