@@ -187,6 +187,17 @@ __device__ __forceinline__ float2 silu2(float2 t) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(d.y));
     return __fmul2_rn(t, r);
 }
+// Rendering decode: silu(t) = h + h tanh(h) with h = t / 2 (the same function,
+// t sigmoid(t) = t (1 + tanh(t / 2)) / 2), one hardware tanh (relative error
+// about 2^-11) instead of an exponential and a reciprocal, on two values with
+// packed FP32x2 multiplication and FMA.
+__device__ __forceinline__ float2 silu2_fast(float2 t) {
+    const float2 h = __fmul2_rn(t, make_float2(0.5f, 0.5f));
+    float2 r;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r.x) : "f"(h.x));
+    asm("tanh.approx.f32 %0, %1;" : "=f"(r.y) : "f"(h.y));
+    return __ffma2_rn(h, r, h);
+}
 __device__ __forceinline__ float silu_grad(float t) {
     const float s = __fdividef(1.0f, 1.0f + __expf(-t));
     return s * (1.0f + t * (1.0f - s));
@@ -306,7 +317,10 @@ struct Grid {
     int32_t dims[3];       // B + 1 per axis
 };
 
-template <bool TRAIN>
+// FAST (inference only): SiLU through the hardware tanh (silu2_fast), used when
+// bricks are decoded for rendering; the point queries and training use the
+// exponential form.
+template <bool TRAIN, bool FAST = false>
 __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const float4* __restrict__ pts,
                                                        const Grid grid, const float* __restrict__ tgt,
                                                        int64_t n_points, float* __restrict__ out, const Grads g,
@@ -420,7 +434,7 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
                     if (TRAIN)
                         *reinterpret_cast<float4*>(reinterpret_cast<float*>(sm + kOffZ1) + tid * kHidden + c + i +
                                                    e) = make_float4(za.x, za.y, zb.x, zb.y);
-                    const float2 ha = silu2(za), hb = silu2(zb);
+                    const float2 ha = FAST ? silu2_fast(za) : silu2(za), hb = FAST ? silu2_fast(zb) : silu2(zb);
                     h[e] = ha.x;
                     h[e + 1] = ha.y;
                     h[e + 2] = hb.x;
@@ -449,10 +463,10 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
             for (int i = 0; i < 32; i += 4) {
                 const float4 b = *reinterpret_cast<const float4*>(s_b2 + c + i);
                 const float4 w = *reinterpret_cast<const float4*>(s_w3 + c + i);
-                y2 = __ffma2_rn(silu2(__fadd2_rn(make_float2(d[i], d[i + 1]), make_float2(b.x, b.y))),
-                                make_float2(w.x, w.y), y2);
-                y2 = __ffma2_rn(silu2(__fadd2_rn(make_float2(d[i + 2], d[i + 3]), make_float2(b.z, b.w))),
-                                make_float2(w.z, w.w), y2);
+                const float2 za = __fadd2_rn(make_float2(d[i], d[i + 1]), make_float2(b.x, b.y));
+                const float2 zb = __fadd2_rn(make_float2(d[i + 2], d[i + 3]), make_float2(b.z, b.w));
+                y2 = __ffma2_rn(FAST ? silu2_fast(za) : silu2(za), make_float2(w.x, w.y), y2);
+                y2 = __ffma2_rn(FAST ? silu2_fast(zb) : silu2(zb), make_float2(w.z, w.w), y2);
             }
         }
         const float y = y2.x + y2.y;
@@ -857,7 +871,7 @@ int grow_points(vr_codec* c, int64_t n) {
     return VR_OK;
 }
 
-template <bool TRAIN>
+template <bool TRAIN, bool FAST = false>
 int launch_codec(vr_codec* c, const float4* pts, vr::codec::Grid grid, const float* tgt, int64_t n, float* out,
                  cudaStream_t st) {
     using namespace vr::codec;
@@ -865,7 +879,7 @@ int launch_codec(vr_codec* c, const float4* pts, vr::codec::Grid grid, const flo
     const int smem = TRAIN ? (int)kSmemTrain : (int)kSmemInfer;
     static bool attr = false;
     if (!attr) {
-        CODEC_CUDA(cudaFuncSetAttribute(codec_kernel<TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        CODEC_CUDA(cudaFuncSetAttribute(codec_kernel<TRAIN, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         attr = true;
     }
     Grads g{};
@@ -882,7 +896,7 @@ int launch_codec(vr_codec* c, const float4* pts, vr::codec::Grid grid, const flo
     }
     const int64_t tiles = (n + kTileP - 1) / kTileP;
     const int64_t grid_ctas = std::min<int64_t>(tiles, (int64_t)c->sm_count * (TRAIN ? kCtasTrain : kCtasInfer));
-    codec_kernel<TRAIN><<<(unsigned)grid_ctas, kTileP, smem, st>>>(make_net(c), pts, grid, tgt, n, out, g, c->err);
+    codec_kernel<TRAIN, FAST><<<(unsigned)grid_ctas, kTileP, smem, st>>>(make_net(c), pts, grid, tgt, n, out, g, c->err);
     return codec_cuda(cudaGetLastError());
 }
 
@@ -1099,7 +1113,7 @@ int vr_codec_decode_bricks(vr_codec* c, const int32_t* bricks, const int32_t* sl
     grid.slots = slots;
     for (int a = 0; a < 3; ++a) grid.dims[a] = c->B[a] + 1;
     const int64_t pts = (int64_t)n * grid.dims[0] * grid.dims[1] * grid.dims[2];
-    return launch_codec<false>(c, nullptr, grid, nullptr, pts, out, (cudaStream_t)stream);
+    return launch_codec<false, true>(c, nullptr, grid, nullptr, pts, out, (cudaStream_t)stream);
 }
 
 int32_t vr_codec_brick_count(const vr_codec* c) { return c ? c->n_bricks : -1; }

@@ -64,6 +64,17 @@ def _silu_approx_err(t, value):
     return (np.abs(t) + 8.0) * 4.0 * U * np.abs(value) + TINY
 
 
+TANH_REL = 2.0 ** -10.5   # hardware tanh.approx.f32: relative error about 2^-11, with margin
+
+
+def _silu_fast_err(t, value):
+    """silu(t) = h + h tanh(h), h = t / 2, with the hardware tanh (rendering
+    decode): |h| times the tanh's relative error times |tanh(h)|, plus the
+    roundings of h and of the FMA."""
+    h = 0.5 * np.abs(t)
+    return h * TANH_REL * np.abs(np.tanh(0.5 * t)) + 4.0 * U * np.abs(value) + TINY
+
+
 def _tc_err(S, K):
     """Tensor-core product over K (FP32 accumulation, K / 16 steps)."""
     return 4.0 * (K / 16.0 + 1.0) * U_ACC * S
@@ -109,11 +120,13 @@ def _input_eps(latq, brick, x, B):
     return eps
 
 
-def forward_terms(p, lat, brick, x, B=(16, 16, 16)):
+def forward_terms(p, lat, brick, x, B=(16, 16, 16), fast_silu=False):
     """Error terms of the forward pass (before the factor C): a dict with the
     per-point bound 'v' and the intermediate bounds the backward pass needs.
     Values come from the oracle's forward pass; only magnitudes and error terms
-    are formed here.  x = u / B with u the FP32 positions the GPU was given."""
+    are formed here.  x = u / B with u the FP32 positions the GPU was given;
+    fast_silu: the SiLU of the rendering decode (hardware tanh)."""
+    silu_err = _silu_fast_err if fast_silu else _silu_approx_err
     q = ref.bf16
     W1q, W2q, w3q = q(p["W1"]), q(p["W2"]), q(p["w3"])
     b1, b2, b3 = np.asarray(p["b1"]), np.asarray(p["b2"]), float(p["b3"])
@@ -133,7 +146,7 @@ def forward_terms(p, lat, brick, x, B=(16, 16, 16)):
     dz1 = dIN @ np.abs(W1q).T + _tc_err(S1, 32) + U * (np.abs(z1) + np.abs(b1))
     _, _, sg1, sgg1 = _silu_parts(z1)
     h1_pre = ref.silu(z1)
-    eh1 = np.abs(sg1) * dz1 + _silu_approx_err(z1, h1_pre)
+    eh1 = np.abs(sg1) * dz1 + silu_err(z1, h1_pre)
     h1 = fc["h1"]
     dh1 = bf16_delta(h1_pre, eh1)
     # layer 2 (K = 64), SiLU in FP32, the output unit on the CUDA cores
@@ -142,7 +155,7 @@ def forward_terms(p, lat, brick, x, B=(16, 16, 16)):
     dz2 = dh1 @ np.abs(W2q).T + _tc_err(S2, 64) + U * (np.abs(z2) + np.abs(b2))
     _, _, sg2, sgg2 = _silu_parts(z2)
     h2 = fc["h2"]
-    dh2 = np.abs(sg2) * dz2 + _silu_approx_err(z2, h2)
+    dh2 = np.abs(sg2) * dz2 + silu_err(z2, h2)
     y = fc["y"]
     Sy = np.abs(h2) @ np.abs(w3q) + abs(b3)
     dy_ = dh2 @ np.abs(w3q) + 2.0 * 34.0 * U * Sy
@@ -153,9 +166,9 @@ def forward_terms(p, lat, brick, x, B=(16, 16, 16)):
                 ambiguous=big_flip(dIN, eps_in).any(axis=1) | big_flip(dh1, eh1).any(axis=1))
 
 
-def forward_bound(p, lat, brick, x, B=(16, 16, 16)):
+def forward_bound(p, lat, brick, x, B=(16, 16, 16), fast_silu=False):
     """Per-point bound on |v_gpu - v_oracle| (bf16=True)."""
-    return C * forward_terms(p, lat, brick, x, B)["v"]
+    return C * forward_terms(p, lat, brick, x, B, fast_silu)["v"]
 
 
 def _cta_of_points(P, grid, tile=128):
