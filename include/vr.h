@@ -165,6 +165,17 @@ typedef struct {
                                 Values below B + 1 make the texture march unavailable
                                 (VR_KERNEL_AUTO then picks VR_KERNEL_TMA).  Changing it drops
                                 the current copies (rebuilt at the next render). */
+#define VR_OPT_OOC_MARCH 9     /* out-of-core and learned contexts: 1: the texture march
+                                (VR_KERNEL_TEX's gathers) on three layered copies of the
+                                device cache's slots, one per sweep axis, refilled from
+                                each slot's block after it is copied or decoded; each slot
+                                then takes four times its block's bytes of
+                                VR_OPT_DEVICE_BUDGET (block plus copies).  If the device's
+                                layered-texture limits cannot tile the slots, the direct
+                                march is used.  0: the direct march on the blocks.  2
+                                (default): 1 when every brick fits the budget with its
+                                copies, else 0 (a streaming cache keeps four times the
+                                slots).  Takes effect at the next vr_brick. */
 #define VR_PRECISION_F32 0
 #define VR_PRECISION_F16 1
 #define VR_PRECISION_F8 2
@@ -198,8 +209,9 @@ int vr_load_cube(vr_ctx* ctx, const float* data, int64_t nx, int64_t ny, int64_t
  * and computes the brick ranges on the host; vr_render copies the bricks a frame
  * needs into a device cache (VR_OPT_DEVICE_BUDGET) with cudaMemcpyAsync on a side
  * stream, overlapped with the ray march of bricks already resident, and marches
- * them with the direct kernel (the texture and TMA paths need the whole cube on
- * the device).  Images are those of vr_load_cube with the same data.
+ * them with the texture march on layered copies of the cache's slots
+ * (VR_OPT_OOC_MARCH).  Images are those of vr_load_cube with the same data (up
+ * to FP32 rounding between march kernels).
  * Errors: VR_EINVAL (bad sizes, device memory), VR_ECUDA.
  */
 int vr_load_cube_host(vr_ctx* ctx, const float* data, int64_t nx, int64_t ny, int64_t nz);
@@ -510,7 +522,7 @@ int vr_codec_decode_bricks(vr_codec* codec, const int32_t* bricks, const int32_t
 /*
  * Render from a codec instead of a cube (no counterpart in the paper): like
  * vr_load_cube_host, the context keeps a device brick cache (VR_OPT_DEVICE_BUDGET)
- * and marches bricks from it with the direct kernel, but fills a slot by decoding
+ * and marches bricks from it (VR_OPT_OOC_MARCH), but fills a slot by decoding
  * the brick on the tensor cores instead of copying it from host memory.  Empty-
  * space skipping uses the ranges recorded by vr_codec_fit_stats.  The codec must
  * outlive the context's use of it; vr_brick must give the codec's brick size.

@@ -40,6 +40,11 @@ struct Slot {
     int32_t* h_slot_of = nullptr;  // out-of-core: cache slot of each brick (pinned)
     int32_t* d_slot_of = nullptr;
     size_t cap_slot_of = 0, dcap_slot_of = 0;
+    int32_t* h_fill = nullptr;    // out-of-core texture march: slots whose layered copies are refilled
+    int32_t* d_fill = nullptr;
+    size_t cap_fill = 0, dcap_fill = 0;
+    int32_t* d_work = nullptr;    // out-of-core texture march: one half-item counter per launch
+    size_t dcap_work = 0;
     int32_t* h_decode = nullptr;  // learned residency: (brick, slot) lists of the frame's decodes
     int32_t* d_decode = nullptr;
     size_t cap_decode = 0, dcap_decode = 0;
@@ -345,6 +350,12 @@ struct vr_ctx {
     int64_t slot_floats = 0;           // (Bx+1)(By+1)(Bz+1)
     int64_t budget = 0;                // VR_OPT_DEVICE_BUDGET (<= 0: every brick)
     float* d_pool = nullptr;           // device brick cache
+    int ooc_march = 2;                 // VR_OPT_OOC_MARCH: 2 auto, 1 texture march on layered slot copies, 0 direct
+    bool pool_tex_on = false;          // the current cache has its layered copies
+    cudaArray_t pool_arr[3] = {nullptr, nullptr, nullptr};  // by sweep axis
+    cudaTextureObject_t pool_tex[3] = {0, 0, 0};
+    cudaSurfaceObject_t pool_surf[3] = {0, 0, 0};
+    int32_t pool_cols[3] = {0, 0, 0};  // slots per row of each copy's texel tiling
     vr::Residency res;
     int64_t ooc_frame = 0;
     cudaStream_t copy_stream = nullptr;

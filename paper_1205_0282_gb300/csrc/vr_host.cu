@@ -82,7 +82,24 @@ bool use_tma(vr_ctx* c) {
     return !c->ooc && c->mode == 0 && c->step_mode == 0 && (c->kernel == VR_KERNEL_TMA || (c->kernel == VR_KERNEL_AUTO && !tex_fits(c)));
 }
 
+// The layered copies of the out-of-core cache (texture march).
+void free_pool_tex(vr_ctx* c) {
+    for (int a = 0; a < 3; ++a) {
+        if (c->pool_tex[a]) cudaDestroyTextureObject(c->pool_tex[a]);
+        if (c->pool_surf[a]) cudaDestroySurfaceObject(c->pool_surf[a]);
+        if (c->pool_arr[a]) cudaFreeArray(c->pool_arr[a]);
+        c->pool_tex[a] = 0;
+        c->pool_surf[a] = 0;
+        c->pool_arr[a] = nullptr;
+        c->pool_cols[a] = 0;
+    }
+    c->pool_tex_on = false;
+}
+
+bool use_pool_tex(vr_ctx* c) { return c->ooc && c->pool_tex_on; }
+
 void free_ooc(vr_ctx* c) {
+    free_pool_tex(c);
     if (c->h_store) cudaFreeHost(c->h_store);
     cudaFree(c->d_pool);
     c->h_store = nullptr;
@@ -195,8 +212,59 @@ int codec_fallback_scan(vr_ctx* c) {
     return VR_OK;
 }
 
+// Layered copies of the cache's slots for the texture march: for sweep axis S a
+// layered array with layers along S (B_S + 1 of them) and the slots' (U, V)
+// faces tiled pool_cols[S] per row.  If the device's layered-texture limits do
+// not admit the tiling, the context keeps the direct march.
+int make_pool_tex(vr_ctx* c, int64_t slots) {
+    int maxw = 0, maxh = 0, maxl = 0;
+    VR_CUDA(c, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, c->device));
+    VR_CUDA(c, cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, c->device));
+    VR_CUDA(c, cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, c->device));
+    int64_t cols[3], rows[3];
+    for (int S = 0; S < 3; ++S) {
+        const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
+        cols[S] = std::min<int64_t>(slots, maxw / (c->B[U] + 1));
+        if (cols[S] < 1) return VR_OK;
+        rows[S] = (slots + cols[S] - 1) / cols[S];
+        if (rows[S] * (c->B[V] + 1) > maxh || c->B[S] + 1 > maxl) return VR_OK;
+    }
+    cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
+    for (int S = 0; S < 3; ++S) {
+        const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
+        if (cudaMalloc3DArray(&c->pool_arr[S], &ch,
+                              make_cudaExtent((size_t)(cols[S] * (c->B[U] + 1)), (size_t)(rows[S] * (c->B[V] + 1)),
+                                              (size_t)(c->B[S] + 1)),
+                              cudaArrayLayered | cudaArraySurfaceLoadStore) != cudaSuccess) {
+            cudaGetLastError();
+            free_pool_tex(c);
+            return fail(c, VR_ENOMEM, "cannot allocate the layered copies of the brick cache");
+        }
+        cudaResourceDesc rd;
+        std::memset(&rd, 0, sizeof(rd));
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = c->pool_arr[S];
+        cudaTextureDesc td;
+        std::memset(&td, 0, sizeof(td));
+        td.addressMode[0] = td.addressMode[1] = td.addressMode[2] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        if (cudaCreateTextureObject(&c->pool_tex[S], &rd, &td, nullptr) != cudaSuccess ||
+            cudaCreateSurfaceObject(&c->pool_surf[S], &rd) != cudaSuccess) {
+            cudaGetLastError();
+            free_pool_tex(c);
+            return fail(c, VR_ECUDA, "cannot create the brick cache's texture objects");
+        }
+        c->pool_cols[S] = (int32_t)cols[S];
+    }
+    c->pool_tex_on = true;
+    return VR_OK;
+}
+
 // Brick store and device cache of an out-of-core context (at vr_brick).
 int build_ooc_store(vr_ctx* c) {
+    free_pool_tex(c);
     if (c->h_store) cudaFreeHost(c->h_store);
     cudaFree(c->d_pool);
     c->h_store = nullptr;
@@ -219,13 +287,22 @@ int build_ooc_store(vr_ctx* c) {
         }
         vr::build_brick_store(c->h_src, c->n, c->B, c->nb, c->h_store, c->slot_floats, c->h_minmax.data());
     }
+    // the texture march keeps each slot four times: its block and three layered
+    // copies; automatically chosen when every brick fits the budget that way
+    const bool tex_march = c->ooc_march == 1 ||
+                           (c->ooc_march == 2 && (c->budget <= 0 || c->budget / ((int64_t)slot_bytes * 4) >= c->n_bricks));
+    const int copies = tex_march ? 4 : 1;
     int64_t slots = c->n_bricks;
-    if (c->budget > 0) slots = std::min<int64_t>(slots, c->budget / (int64_t)slot_bytes);
+    if (c->budget > 0) slots = std::min<int64_t>(slots, c->budget / ((int64_t)slot_bytes * copies));
     if (slots < 2) return fail(c, VR_EINVAL, "VR_OPT_DEVICE_BUDGET holds fewer than 2 bricks");
     if (cudaMalloc((void**)&c->d_pool, slot_bytes * (size_t)slots) != cudaSuccess) {
         cudaGetLastError();
         c->d_pool = nullptr;
         return fail(c, VR_ENOMEM, "cannot allocate the device brick cache");
+    }
+    if (tex_march) {
+        int rc = make_pool_tex(c, slots);
+        if (rc) return rc;
     }
     c->res.slot_of_brick.assign(c->n_bricks, -1);
     c->res.brick_in_slot.assign(slots, -1);
@@ -262,7 +339,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
     // sweep axis of each tile for the TMA march: the dominant axis of the ray
     // through the tile's centre pixel, and its sign
     c->plan_sweep.assign(n_tiles, 0);
-    if (use_tma(c) || use_tex(c)) {
+    if (use_tma(c) || use_tex(c) || use_pool_tex(c)) {
         // view-plane offsets of the tile centres' columns and rows, then per tile
         // d = f + qx r + qy u (no division in the tile loop)
         c->plan_qx.resize(tiles_x);
@@ -451,6 +528,9 @@ void vr_destroy(vr_ctx* c) {
         cudaFree(s.d_slot_of);
         if (s.h_decode) cudaFreeHost(s.h_decode);
         cudaFree(s.d_decode);
+        if (s.h_fill) cudaFreeHost(s.h_fill);
+        cudaFree(s.d_fill);
+        cudaFree(s.d_work);
         cudaFree(s.d_frame);
         cudaFree(s.d_items);
         cudaFree(s.d_tile_start);
@@ -841,6 +921,10 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
             c->kernel = (int)value;
             return VR_OK;
         case VR_OPT_DEVICE_BUDGET: c->budget = value; return VR_OK;
+        case VR_OPT_OOC_MARCH:
+            if (value < 0 || value > 2) return fail(c, VR_EINVAL, "out-of-core march must be 0, 1 or 2");
+            c->ooc_march = (int)value;
+            return VR_OK;
         case VR_OPT_TEX_SLAB_LAYERS:
             if (value < 0) return fail(c, VR_EINVAL, "layers per texture slab must be >= 0");
             if (value != c->tex_slab_layers) {
@@ -1115,6 +1199,10 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
         p.slot_stride = c->slot_floats;
         p.pool_sy = c->B[0] + 1;
         p.pool_sz = (c->B[0] + 1) * (c->B[1] + 1);
+        for (int a = 0; a < 3; ++a) {
+            p.pool_tex[a] = c->pool_tex[a];
+            p.pool_cols[a] = c->pool_cols[a];
+        }
     }
     p.tf_rgba = reinterpret_cast<const float4*>(s.d_frame + tf_rgba_off);
     p.tf_v = reinterpret_cast<const float*>(s.d_frame + tf_v_off);
@@ -1154,6 +1242,14 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
             if ((rc2 = grow_pinned(c, s.h_decode, s.cap_decode, std::max<size_t>(list_off[nl], 1)))) return rc2;
             if ((rc2 = grow_device(c, s.d_decode, s.dcap_decode, std::max<size_t>(list_off[nl], 1)))) return rc2;
         }
+        // texture march: each launch's refilled slots, and one half-item counter per launch
+        const bool pool_tex = use_pool_tex(c);
+        if (pool_tex) {
+            if ((rc2 = grow_pinned(c, s.h_fill, s.cap_fill, std::max<size_t>(list_off[nl] / 2, 1)))) return rc2;
+            if ((rc2 = grow_device(c, s.d_fill, s.dcap_fill, std::max<size_t>(list_off[nl] / 2, 1)))) return rc2;
+            if ((rc2 = grow_device(c, s.d_work, s.dcap_work, std::max<size_t>(nl, 1)))) return rc2;
+            VR_CUDA(c, cudaMemsetAsync(s.d_work, 0, nl * sizeof(int32_t), st));
+        }
         auto issue_upload = [&](size_t k) -> int {
             const OocLaunch& L = ooc_launches[k];
             if (L.up.empty()) return VR_OK;
@@ -1164,6 +1260,16 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
             int r = ooc_upload(c, s, L, list_off[k], &copied);
             if (r) return r;
             upload_bytes += copied;
+            if (pool_tex) {
+                // the slots' layered copies, from their blocks
+                int32_t* hf = s.h_fill + list_off[k] / 2;
+                std::copy(L.slot.begin(), L.slot.end(), hf);
+                VR_CUDA(c, cudaMemcpyAsync(s.d_fill + list_off[k] / 2, hf, L.slot.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, c->copy_stream));
+                VR_CUDA(c, vr::fill_pool_tex(c->d_pool, c->slot_floats, s.d_fill + list_off[k] / 2,
+                                             (int32_t)L.slot.size(), c->B, c->pool_surf, c->pool_cols,
+                                             c->copy_stream));
+            }
             VR_CUDA(c, cudaEventRecord(c->ev_chunk[k], c->copy_stream));
             VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));
             return VR_OK;
@@ -1201,7 +1307,12 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
                 vr::FrameParams q = p;
                 q.items = s.d_items + L.lo;
                 q.n_items = (int32_t)(L.hi - L.lo);
-                VR_CUDA(c, vr::launch_march(q, ms));
+                if (pool_tex) {
+                    q.work_next = s.d_work + k;
+                    VR_CUDA(c, vr::launch_march_tex(q, ms));
+                } else {
+                    VR_CUDA(c, vr::launch_march(q, ms));
+                }
                 ++march_launches;
             }
             if (L.half >= 0) {

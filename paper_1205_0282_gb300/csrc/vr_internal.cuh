@@ -109,6 +109,12 @@ struct FrameParams {
     const float* brick_scale;   // FP8: per-brick scale (value = code * scale)
     const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
     const float* pool;          // out-of-core: device brick cache, or nullptr (read `cube`)
+    // out-of-core texture march: the cache's slots as layered copies, one per sweep
+    // axis S (slot k's block at texel (k % pool_cols[S], k / pool_cols[S]) x (B+1)
+    // across, layers = its coordinate along S), or 0
+    cudaTextureObject_t pool_tex[3];
+    int32_t pool_cols[3];
+    int32_t* work_next;         // texture march: the launch's half-item counter (nullptr: stats->work_next)
     const int32_t* slot_of;     // out-of-core: cache slot of each brick rendered this frame
     int64_t slot_stride;        // floats per slot, (Bx+1)(By+1)(Bz+1)
     int32_t pool_sy, pool_sz;   // row and plane strides inside a slot
@@ -139,6 +145,12 @@ cudaError_t launch_brick_minmax(const float* cube, int64_t pitch, const int32_t 
 cudaError_t launch_march(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tma(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s);
+// Out-of-core texture march: copy the blocks of the cache slots slots[0..count)
+// (device list) into the three layered copies of the slot pool (surfaces by
+// sweep axis, slot k at texel (k % cols[S], k / cols[S]) x (B+1)).
+cudaError_t fill_pool_tex(const float* pool, int64_t slot_floats, const int32_t* slots, int32_t count,
+                          const int32_t B[3], const cudaSurfaceObject_t surf[3], const int32_t cols[3],
+                          cudaStream_t s);
 // Batch (vr_serve.cu): the texture march over items of several frames, and the
 // composite of every tile of every frame (p.n_cams frames, total_tiles blocks).
 cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s);

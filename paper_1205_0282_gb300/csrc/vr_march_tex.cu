@@ -158,7 +158,8 @@ __device__ __forceinline__ int step_of(const FrameParams& p, int a) {
 
 // MODE 0: emission-absorption compositing; MODE 1: maximum intensity projection
 // (Section 2.3.2; the colour map is applied by the composite), FP32 storage only.
-template <int S, bool UNIFORM, int PREC, bool DYN, class Cam, int MODE = 0>
+// POOL: the brick is read from its out-of-core cache slot's layered copy (FP32).
+template <int S, bool UNIFORM, int PREC, bool DYN, class Cam, int MODE = 0, bool POOL = false>
 __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam, const Item& item,
                                            const float4* s_rgba, const float4* s_drgba, const float* s_v,
                                            int t) {
@@ -176,10 +177,22 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         imax[a] = min(p.B[a] - 1, p.n[a] - 2 - O[a]);
     }
     // the slab of the layered copy that holds this brick, and the brick's first
-    // layer in it
-    const int slab = bidx[S] / p.tex_slab_bricks[S];
-    const cudaTextureObject_t tex = p.tex[S][slab];
-    const int lay0 = O[S] - slab * p.tex_slab_bricks[S] * p.B[S];
+    // layer in it (out-of-core: the brick's slot in the pool's layered copy, its
+    // layers 0..B)
+    cudaTextureObject_t tex;
+    int lay0;
+    int slot_u = 0, slot_v = 0;
+    if constexpr (POOL) {
+        const int slot = p.slot_of[item.brick];
+        tex = p.pool_tex[S];
+        lay0 = 0;
+        slot_u = (slot % p.pool_cols[S]) * (p.B[U] + 1) - O[U];
+        slot_v = (slot / p.pool_cols[S]) * (p.B[V] + 1) - O[V];
+    } else {
+        const int slab = bidx[S] / p.tex_slab_bricks[S];
+        tex = p.tex[S][slab];
+        lay0 = O[S] - slab * p.tex_slab_bricks[S] * p.B[S];
+    }
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float vmax = -FLT_MAX;  // MIP: running maximum
     float fn = 0.0f;  // samples this ray owes the brick (after termination: those composited)
@@ -205,7 +218,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
     }
     const float tau = p.tau;
     // brick origin along U, V plus one: gather coordinate of texel (u, v) is (u + 1, v + 1)
-    const float ou = (float)(O[U] + 1), ov = (float)(O[V] + 1);
+    const float ou = (float)(O[U] + slot_u + 1), ov = (float)(O[V] + slot_v + 1);
     // Sample k's eight corners and weights, gathered D samples ahead of their use
     // (the software pipeline below).
     struct Corners {
@@ -232,7 +245,26 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
         if (bidx[V] + 1 < p.nb[V]) lim_v = p.B[V] - 1;
         if (bidx[S] + 1 < p.nb[S]) lim_s = p.B[S] - 1;
     }
+    const float2 dqUV = make_float2(dq[U], dq[V]), qsUV = make_float2(qs[U], qs[V]);
+    const float2 oUV = make_float2(ou, ov);
     auto fetch = [&](float f, Corners& s) {
+        if constexpr (PREC != kPrecF8) {
+            // positions, fractions and texel coordinates along (U, V) as packed
+            // FP32x2 operations (each lane rounds like the scalar one)
+            const float qS = fmaf(f, dq[S], qs[S]);
+            const float2 qUV = __ffma2_rn(make_float2(f, f), dqUV, qsUV);
+            const int ps = __float2int_rz(qS), iu = __float2int_rz(qUV.x), iv = __float2int_rz(qUV.y);
+            const float2 fUV = make_float2((float)iu, (float)iv);
+            s.fs = qS - (float)ps;
+            const float2 fr = __fadd2_rn(qUV, make_float2(-fUV.x, -fUV.y));
+            s.fu = fr.x;
+            s.fv = fr.y;
+            const float2 xy = __fadd2_rn(oUV, fUV);
+            // FP32 and FP16 textures both return FP32 values
+            gather4(tex, lay0 + ps, xy.x, xy.y, s.c[0], s.c[1], s.c[2], s.c[3]);
+            gather4(tex, lay0 + ps + 1, xy.x, xy.y, s.c[4], s.c[5], s.c[6], s.c[7]);
+            return;
+        }
         const float qS = fmaf(f, dq[S], qs[S]);
         const float qU = fmaf(f, dq[U], qs[U]);
         const float qV = fmaf(f, dq[V], qs[V]);
@@ -287,13 +319,27 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
     float fi = 0.0f;
     auto step = [&](Corners& cur) {
         decode(cur);
-        const float e00 = fmaf(cur.fu, cur.c[1] - cur.c[0], cur.c[0]);
-        const float e10 = fmaf(cur.fu, cur.c[3] - cur.c[2], cur.c[2]);
-        const float e01 = fmaf(cur.fu, cur.c[5] - cur.c[4], cur.c[4]);
-        const float e11 = fmaf(cur.fu, cur.c[7] - cur.c[6], cur.c[6]);
-        const float e0 = fmaf(cur.fv, e10 - e00, e00);
-        const float e1 = fmaf(cur.fv, e11 - e01, e01);
-        float val = fmaf(cur.fs, e1 - e0, e0);
+        float val;
+        if constexpr (PREC != kPrecF8) {
+            // along S first, two corners per packed FP32x2 operation: the gather
+            // leaves (c[2], c[3]) and (c[1], c[0]) in register pairs
+            const float2 fs2 = make_float2(cur.fs, cur.fs);
+            const float2 a10 = make_float2(cur.c[1], cur.c[0]), a23 = make_float2(cur.c[2], cur.c[3]);
+            const float2 b10 = make_float2(cur.c[5], cur.c[4]), b23 = make_float2(cur.c[6], cur.c[7]);
+            const float2 s10 = __ffma2_rn(fs2, __fadd2_rn(b10, make_float2(-a10.x, -a10.y)), a10);
+            const float2 s23 = __ffma2_rn(fs2, __fadd2_rn(b23, make_float2(-a23.x, -a23.y)), a23);
+            const float e0 = fmaf(cur.fu, s10.x - s10.y, s10.y);   // row v
+            const float e1 = fmaf(cur.fu, s23.y - s23.x, s23.x);   // row v + 1
+            val = fmaf(cur.fv, e1 - e0, e0);
+        } else {
+            const float e00 = fmaf(cur.fu, cur.c[1] - cur.c[0], cur.c[0]);
+            const float e10 = fmaf(cur.fu, cur.c[3] - cur.c[2], cur.c[2]);
+            const float e01 = fmaf(cur.fu, cur.c[5] - cur.c[4], cur.c[4]);
+            const float e11 = fmaf(cur.fu, cur.c[7] - cur.c[6], cur.c[6]);
+            const float e0 = fmaf(cur.fv, e10 - e00, e00);
+            const float e1 = fmaf(cur.fv, e11 - e01, e01);
+            val = fmaf(cur.fs, e1 - e0, e0);
+        }
         if (PREC == kPrecF8) val *= k0;
         if constexpr (MODE == 1) {
             // a MIP ray stops once it reaches the data's global maximum (Section
@@ -365,24 +411,25 @@ __device__ __forceinline__ void load_tf(const FrameParams& p, float4*& s_rgba, f
 // rays of an 8x4 half tile) in list order from a counter: a warp that finishes
 // its rays starts the next half item at once instead of waiting for the other
 // warp of its CTA, and the list order (brick-major, front to back) is kept.
-template <bool UNIFORM, int PREC, bool DYN, int MODE = 0>
+template <bool UNIFORM, int PREC, bool DYN, int MODE = 0, bool POOL = false>
 __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_kernel(const FrameParams p) {
     float4 *s_rgba, *s_drgba;
     float* s_v;
     load_tf(p, s_rgba, s_drgba, s_v);
     const int lane = threadIdx.x & 31;
     const int total = 2 * p.n_items;
+    int* counter = p.work_next ? p.work_next : &p.stats->work_next;
     for (;;) {
         int w = 0;
-        if (lane == 0) w = atomicAdd(&p.stats->work_next, 1);
+        if (lane == 0) w = atomicAdd(counter, 1);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= total) break;
         const Item item = p.items[w >> 1];
         const int t = (w & 1) * 32 + lane;
         switch (item.sweep & 3) {
-            case 0: march_item<0, UNIFORM, PREC, DYN, FrameParams, MODE>(p, p, item, s_rgba, s_drgba, s_v, t); break;
-            case 1: march_item<1, UNIFORM, PREC, DYN, FrameParams, MODE>(p, p, item, s_rgba, s_drgba, s_v, t); break;
-            default: march_item<2, UNIFORM, PREC, DYN, FrameParams, MODE>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+            case 0: march_item<0, UNIFORM, PREC, DYN, FrameParams, MODE, POOL>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+            case 1: march_item<1, UNIFORM, PREC, DYN, FrameParams, MODE, POOL>(p, p, item, s_rgba, s_drgba, s_v, t); break;
+            default: march_item<2, UNIFORM, PREC, DYN, FrameParams, MODE, POOL>(p, p, item, s_rgba, s_drgba, s_v, t); break;
         }
     }
 }
@@ -519,6 +566,27 @@ __global__ void stored_minmax_kernel(const float* __restrict__ a, int64_t pitch,
     }
 }
 
+// Out-of-core texture pool: slot slots[blockIdx.z]'s block (B+1)^3, x fastest,
+// into the layered copy of sweep axis S: layer = coordinate along S, texel =
+// (coordinates along U, V) + the slot's tile origin.  The grid covers (x, y) of
+// the block with (z) in a loop.
+template <int S>
+__global__ void fill_pool_kernel(const float* __restrict__ pool, int64_t slot_floats, const int32_t* slots, int3 B1,
+                                 cudaSurfaceObject_t surf, int32_t cols) {
+    constexpr int U = Axes<S>::U, V = Axes<S>::V;
+    const int k = slots[blockIdx.z];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= B1.x) return;
+    const int n1[3] = {B1.x, B1.y, B1.z};
+    const int tu = (k % cols) * n1[U], tv = (k / cols) * n1[V];
+    const float* blk = pool + (int64_t)k * slot_floats;
+    for (int z = 0; z < B1.z; ++z) {
+        const float v = blk[((int64_t)z * B1.y + y) * B1.x + x];
+        const int c[3] = {x, y, z};
+        surf2DLayeredwrite(v, surf, (tu + c[U]) * 4, tv + c[V], c[S]);
+    }
+}
+
 // One wave of persistent CTAs (no more than there are items).
 inline unsigned persistent_grid(const FrameParams& p, int blocks_per_sm) {
     int dev = 0, sms = 0;
@@ -550,6 +618,17 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
         else go(general_kern);
     };
     using namespace texm;
+    if (p.pool) {  // out-of-core texture march (FP32 slots)
+        if (p.mode == 1) {
+            if (p.step_mode) go(march_tex_kernel<true, kPrecF32, true, 1, true>);
+            else go(march_tex_kernel<true, kPrecF32, false, 1, true>);
+        } else if (p.step_mode) {
+            by_tf(march_tex_kernel<true, kPrecF32, true, 0, true>, march_tex_kernel<false, kPrecF32, true, 0, true>);
+        } else {
+            by_tf(march_tex_kernel<true, kPrecF32, false, 0, true>, march_tex_kernel<false, kPrecF32, false, 0, true>);
+        }
+        return cudaGetLastError();
+    }
     if (p.mode == 1) {  // MIP (FP32 storage; the march does not read the transfer function)
         if (p.step_mode) go(march_tex_kernel<true, kPrecF32, true, 1>);
         else go(march_tex_kernel<true, kPrecF32, false, 1>);
@@ -591,6 +670,18 @@ cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
         if (p.tf_uniform) go(march_tex_batch_kernel<true, kPrecF32>);
         else go(march_tex_batch_kernel<false, kPrecF32>);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t fill_pool_tex(const float* pool, int64_t slot_floats, const int32_t* slots, int32_t count,
+                          const int32_t B[3], const cudaSurfaceObject_t surf[3], const int32_t cols[3],
+                          cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int3 b1 = make_int3(B[0] + 1, B[1] + 1, B[2] + 1);
+    const dim3 grid((unsigned)((b1.x + 127) / 128), (unsigned)b1.y, (unsigned)count);
+    texm::fill_pool_kernel<0><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[0], cols[0]);
+    texm::fill_pool_kernel<1><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[1], cols[1]);
+    texm::fill_pool_kernel<2><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[2], cols[2]);
     return cudaGetLastError();
 }
 

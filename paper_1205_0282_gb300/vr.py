@@ -34,6 +34,7 @@ VR_OPT_PRECISION = 5
 VR_OPT_DEVICE_BUDGET = 6
 VR_OPT_STEP_MODE = 7
 VR_OPT_TEX_SLAB_LAYERS = 8
+VR_OPT_OOC_MARCH = 9
 VR_PRECISION_F32 = 0
 VR_PRECISION_F16 = 1
 VR_PRECISION_F8 = 2

@@ -279,7 +279,10 @@ def _fallback_case(vr, torch):
     return cube, shape, brick, c, tf, cam
 
 
-def _ctx(vr, shape, brick, tf, cam, codec=None, cube=None, fallback=None, budget=0, floor=-3.4e38):
+def _ctx(vr, shape, brick, tf, cam, codec=None, cube=None, fallback=None, budget=0, floor=-3.4e38, march=1):
+    """A plain or learned context on the texture march (march=1: each slot takes
+    four blocks of the budget, its block and three layered copies) or on the
+    direct march (march=0), with a cache of `budget` slots (0: every brick)."""
     r = vr.VolumeRenderer(0)
     if codec is not None:
         r.load_cube_codec(codec, shape)
@@ -287,8 +290,9 @@ def _ctx(vr, shape, brick, tf, cam, codec=None, cube=None, fallback=None, budget
             r.set_codec_fallback(cube, fallback, floor)
     else:
         r.load_cube_host(cube)
+    r.set_option(vr.VR_OPT_OOC_MARCH, march)
     if budget:
-        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget * 17 ** 3 * 4)
+        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget * 17 ** 3 * 4 * (4 if march else 1))
     r.set_option(vr.VR_OPT_SKIP_EMPTY, 0)   # codec and plain ranges may differ
     r.brick(*brick)
     r.set_transfer_function(tf)

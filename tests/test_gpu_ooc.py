@@ -1,13 +1,16 @@
 """GPU parity of the out-of-core path (vr_load_cube_host): the cube stays in host
 memory, bricks are copied into a device cache under a memory budget and marched
-from there.  Its images must equal the in-core direct march bit for bit (same
+from there, by the texture march on layered copies of the cache's slots
+(VR_OPT_OOC_MARCH 1, the default) or by the direct march on the blocks (0).
+Its images must equal the in-core march of the same kernel bit for bit (same
 voxels, same arithmetic) and match the FP64 oracle; the residency counters must
 show reuse when the frame fits the cache and streaming when it does not."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from parity_util import assert_parity
+from parity_util import AMB_ALPHA, AMB_STEPS, assert_parity
 from test_gpu_render import RAGGED, oracle_render
 
 pytestmark = pytest.mark.gpu
@@ -25,22 +28,26 @@ def vr():
     return vr
 
 
-def _incore(vr, torch, cube, tf, cam, brick, mode=0):
+def _incore(vr, torch, cube, tf, cam, brick, mode=0, march=1):
+    """In-core render with the kernel the out-of-core march mirrors."""
     with vr.VolumeRenderer(0) as r:
         r.load_cube(torch.from_numpy(np.ascontiguousarray(cube)).cuda())
         r.brick(*brick)
         r.set_transfer_function(tf)
         r.set_camera(cam)
-        r.set_option(vr.VR_OPT_KERNEL, vr.VR_KERNEL_DIRECT)
+        r.set_option(vr.VR_OPT_KERNEL, vr.VR_KERNEL_TEX if march else vr.VR_KERNEL_DIRECT)
         r.set_option(vr.VR_OPT_MODE, mode)
         return r.render().cpu().numpy()
 
 
-def _ooc(vr, cube, tf, brick, budget_bricks=0, mode=0):
+def _ooc(vr, cube, tf, brick, budget_bricks=0, mode=0, march=1):
+    """Out-of-core context whose cache holds budget_bricks slots (the texture march
+    keeps each slot's block and three layered copies: four blocks' bytes)."""
     r = vr.VolumeRenderer(0)
     r.load_cube_host(cube)
+    r.set_option(vr.VR_OPT_OOC_MARCH, march)
     if budget_bricks:
-        slot = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1) * 4
+        slot = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1) * 4 * (4 if march else 1)
         r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_bricks * slot)
     r.brick(*brick)
     r.set_transfer_function(tf)
@@ -48,18 +55,20 @@ def _ooc(vr, cube, tf, brick, budget_bricks=0, mode=0):
     return r
 
 
+@pytest.mark.parametrize("march", [1, 0])
 @pytest.mark.parametrize("budget", [0, 20, 9, 2])
 @pytest.mark.parametrize("view", [0, 2])
-def test_out_of_core_equals_in_core(vr, torch, budget, view):
-    """Same image as the in-core direct march, frame after frame.  A frame whose
-    bricks fit uploads them once; a larger one keeps S - 2H bricks resident (S
-    slots, H = clamp(S / 8, 1, 32)) and streams the rest through the ring."""
+def test_out_of_core_equals_in_core(vr, torch, budget, view, march):
+    """Same image as the in-core march of the same kernel, frame after frame.  A
+    frame whose bricks fit uploads them once; a larger one keeps S - 2H bricks
+    resident (S slots, H = clamp(S / 8, 1, 32)) and streams the rest through the
+    ring."""
     cube, tf = synth.tiny_cube(), synth.tf_tiny()
     brick = (16, 16, 16)    # 64 bricks
     cam = synth.tiny_views(width=96, height=80)[view]
-    ref = _incore(vr, torch, cube, tf, cam, brick)
+    ref = _incore(vr, torch, cube, tf, cam, brick, march=march)
     ups = []
-    with _ooc(vr, cube, tf, brick, budget) as r:
+    with _ooc(vr, cube, tf, brick, budget, march=march) as r:
         r.set_camera(cam)
         for _ in range(3):
             r.reset_stats()
@@ -137,13 +146,38 @@ def test_out_of_core_ragged(vr, shape, brick, camk, step, tau):
     assert_parity(img, ref, amb)
 
 
-def test_out_of_core_mip(vr, torch):
+@pytest.mark.parametrize("march", [1, 0])
+def test_out_of_core_mip(vr, torch, march):
     cube, tf = synth.tiny_cube(), synth.tf_tiny()
     cam = synth.tiny_views(width=80, height=72)[1]
-    ref = _incore(vr, torch, cube, tf, cam, (16, 16, 16), mode=1)
-    with _ooc(vr, cube, tf, (16, 16, 16), 6, mode=1) as r:
+    ref = _incore(vr, torch, cube, tf, cam, (16, 16, 16), mode=1, march=march)
+    with _ooc(vr, cube, tf, (16, 16, 16), 6, mode=1, march=march) as r:
         r.set_camera(cam)
         assert np.array_equal(r.render().cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("shape,brick,camk,step,tau", RAGGED[:2])
+def test_out_of_core_texture_march_dynamic_step(vr, torch, shape, brick, camk, step, tau):
+    """The dynamic step on the slot copies: the in-core texture march's image, and
+    the oracle's."""
+    cube = synth.hi_cube(seed=11, shape_xyz=shape, n_line=12, n_cont=2)
+    tf = synth.tf_tiny()
+    cam = synth.pose(shape, camk["az"], camk["el"], camk["W"], camk["H"], step=step, term_alpha=tau)
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(np.ascontiguousarray(cube)).cuda())
+        r.set_option(vr.VR_OPT_KERNEL, vr.VR_KERNEL_TEX)
+        r.set_option(vr.VR_OPT_STEP_MODE, 1)
+        r.brick(*brick)
+        r.set_transfer_function(tf)
+        r.set_camera(cam)
+        ref_gpu = r.render().cpu().numpy()
+    with _ooc(vr, cube, tf, brick, 4) as r:
+        r.set_option(vr.VR_OPT_STEP_MODE, 1)
+        r.set_camera(cam)
+        img = r.render().cpu().numpy()
+    assert np.array_equal(img, ref_gpu)
+    ref, amb, _ = oracle.render(cube, tf, cam, brick=brick, amb_alpha=AMB_ALPHA, amb_steps=AMB_STEPS, step_mode=1)
+    assert_parity(img.astype(np.float64), ref, amb)
 
 
 def test_out_of_core_errors(vr, torch):
