@@ -134,6 +134,10 @@ constexpr int kLatent = 16, kNodes = 8, kHidden = 64, kIn = 32, kTileP = 128;
 // Device state of the codec's MLP and latents.
 struct Net {
     const __nv_bfloat16* lat;  // [brick][z][y][x][16] BF16
+    const float* latf;         // the same BF16 values in FP32 (brick decode for rendering)
+    const float4* four;        // brick decode: Fourier features of grid coordinate u along
+                               // axis a at four[four_off[a] + u], u = 0..B_a
+    int32_t four_off[3];
     const __nv_bfloat16* W1;   // [64][32] BF16 (inputs 28..31 zero)
     const __nv_bfloat16* W2;   // [64][64] BF16
     const float* b1;           // [64]
@@ -244,6 +248,9 @@ struct Corner {
     float w[8];
 };
 
+// GRID: pt is a voxel of the brick's grid (integer u): latents read in FP32 and the
+// Fourier features from the per-axis table (the rendering decode).
+template <bool GRID = false>
 __device__ __forceinline__ void build_input(const Net& net, float4 pt, bool valid, int row, unsigned char* in_s,
                                             int& brick, Corner& cr) {
     float in[kIn];
@@ -269,26 +276,49 @@ __device__ __forceinline__ void build_input(const Net& net, float4 pt, bool vali
             const int node = ((i0[2] + cz) * kNodes + (i0[1] + cy)) * kNodes + (i0[0] + cx);
             cr.node[c] = node;
             cr.w[c] = w;
-            const uint4* src = reinterpret_cast<const uint4*>(L + node * kLatent);
-            const uint4 q0 = __ldg(src), q1 = __ldg(src + 1);
-            const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&q0);
-            const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&q1);
             const float2 w2 = make_float2(w, w);
+            if (GRID) {
+                const float4* src = reinterpret_cast<const float4*>(
+                    net.latf + ((int64_t)brick * kNodes * kNodes * kNodes + node) * kLatent);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                in2[k] = __ffma2_rn(w2, __bfloat1622float2(h0[k]), in2[k]);
-                in2[4 + k] = __ffma2_rn(w2, __bfloat1622float2(h1[k]), in2[4 + k]);
+                for (int k = 0; k < 4; ++k) {
+                    const float4 q = __ldg(src + k);
+                    in2[2 * k] = __ffma2_rn(w2, make_float2(q.x, q.y), in2[2 * k]);
+                    in2[2 * k + 1] = __ffma2_rn(w2, make_float2(q.z, q.w), in2[2 * k + 1]);
+                }
+            } else {
+                const uint4* src = reinterpret_cast<const uint4*>(L + node * kLatent);
+                const uint4 q0 = __ldg(src), q1 = __ldg(src + 1);
+                const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&q0);
+                const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&q1);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    in2[k] = __ffma2_rn(w2, __bfloat1622float2(h0[k]), in2[k]);
+                    in2[4 + k] = __ffma2_rn(w2, __bfloat1622float2(h1[k]), in2[4 + k]);
+                }
             }
         }
+        if (GRID) {
+            const float u[3] = {pt.x, pt.y, pt.z};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            // sin(2 pi x) = 2 sin cos, cos(2 pi x) = (cos - sin)(cos + sin)
-            float sn, cs;
-            sincospif(x[a], &sn, &cs);
-            in[16 + 4 * a] = sn;
-            in[17 + 4 * a] = cs;
-            in[18 + 4 * a] = 2.0f * sn * cs;
-            in[19 + 4 * a] = (cs - sn) * (cs + sn);
+            for (int a = 0; a < 3; ++a) {
+                const float4 f4 = __ldg(net.four + net.four_off[a] + (int)u[a]);
+                in[16 + 4 * a] = f4.x;
+                in[17 + 4 * a] = f4.y;
+                in[18 + 4 * a] = f4.z;
+                in[19 + 4 * a] = f4.w;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                // sin(2 pi x) = 2 sin cos, cos(2 pi x) = (cos - sin)(cos + sin)
+                float sn, cs;
+                sincospif(x[a], &sn, &cs);
+                in[16 + 4 * a] = sn;
+                in[17 + 4 * a] = cs;
+                in[18 + 4 * a] = 2.0f * sn * cs;
+                in[19 + 4 * a] = (cs - sn) * (cs + sn);
+            }
         }
     }
 #pragma unroll
@@ -408,7 +438,7 @@ __global__ void __launch_bounds__(kTileP) codec_kernel(const Net net, const floa
         }
         int brick = 0;
         Corner cr;
-        build_input(net, pt, valid, tid, sm + kOffIN, brick, cr);
+        build_input<FAST>(net, pt, valid, tid, sm + kOffIN, brick, cr);
         tc::fence_smem_to_async();
         tc::fence_before_sync();
         __syncthreads();
@@ -793,6 +823,8 @@ struct vr_codec {
     __nv_bfloat16* W1h = nullptr;
     __nv_bfloat16* W2h = nullptr;
     __nv_bfloat16* lath = nullptr;
+    float* latf = nullptr;   // the BF16 latents as FP32 values (brick decode)
+    float4* four = nullptr;  // Fourier features of the grid coordinates (brick decode)
     float* w3r = nullptr;  // w3 rounded to BF16 values
     float* m = nullptr;
     float* s = nullptr;
@@ -837,6 +869,7 @@ int sync_bf16(vr_codec* c) {
     to_bf16_kernel<<<64, 256>>>(c->theta + kOfsW2, c->W2h, kHidden * kHidden);
     round_bf16_kernel<<<1, 64>>>(c->theta + kOfsW3, c->w3r, kHidden);
     to_bf16_kernel<<<1024, 256>>>(c->theta + kOfsLat, c->lath, (int64_t)c->n_bricks * kLatPerBrick);
+    round_bf16_kernel<<<1024, 256>>>(c->theta + kOfsLat, c->latf, (int64_t)c->n_bricks * kLatPerBrick);
     return codec_cuda(cudaGetLastError());
 }
 
@@ -844,6 +877,11 @@ Net make_net(const vr_codec* c) {
     using namespace vr::codec;
     Net n;
     n.lat = c->lath;
+    n.latf = c->latf;
+    n.four = c->four;
+    n.four_off[0] = 0;
+    n.four_off[1] = c->B[0] + 1;
+    n.four_off[2] = c->B[0] + c->B[1] + 2;
     n.W1 = c->W1h;
     n.W2 = c->W2h;
     n.b1 = c->theta + kOfsB1;
@@ -927,11 +965,25 @@ int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
               cudaMalloc(&c->W1h, kHidden * kIn * 2) == cudaSuccess &&
               cudaMalloc(&c->W2h, kHidden * kHidden * 2) == cudaSuccess &&
               cudaMalloc(&c->lath, (size_t)n_bricks * kLatPerBrick * 2) == cudaSuccess &&
+              cudaMalloc(&c->latf, (size_t)n_bricks * kLatPerBrick * 4) == cudaSuccess &&
+              cudaMalloc(&c->four, (size_t)(B[0] + B[1] + B[2] + 3) * sizeof(float4)) == cudaSuccess &&
               cudaMalloc(&c->w3r, kHidden * 4) == cudaSuccess && cudaMalloc(&c->m, n_bricks * 4) == cudaSuccess &&
               cudaMalloc(&c->s, n_bricks * 4) == cudaSuccess && cudaMalloc(&c->minmax, n_bricks * 8) == cudaSuccess &&
               cudaMalloc(&c->loss, sizeof(double)) == cudaSuccess &&
               cudaMalloc(&c->err, sizeof(int)) == cudaSuccess;
     if (ok) c->grad = c->grad_mem + kGradPad;
+    if (ok) {
+        // Fourier features of the grid coordinates x = u / B_a (u = 0..B_a) along each
+        // axis: sin(pi x), cos(pi x), sin(2 pi x), cos(2 pi x), rounded from FP64
+        std::vector<float4> tab;
+        for (int a = 0; a < 3; ++a)
+            for (int u = 0; u <= B[a]; ++u) {
+                const double x = (double)u / (double)B[a];
+                tab.push_back(make_float4((float)std::sin(M_PI * x), (float)std::cos(M_PI * x),
+                                          (float)std::sin(2.0 * M_PI * x), (float)std::cos(2.0 * M_PI * x)));
+            }
+        ok = cudaMemcpy(c->four, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     if (ok) ok = cudaMemset(c->theta, 0, pb) == cudaSuccess && cudaMemset(c->adam1, 0, pb) == cudaSuccess &&
                  cudaMemset(c->adam2, 0, pb) == cudaSuccess && cudaMemset(c->err, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
@@ -946,7 +998,8 @@ int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
 void vr_codec_destroy(vr_codec* c) {
     if (!c) return;
     for (void* p : {(void*)c->theta, (void*)c->grad_mem, (void*)c->adam1, (void*)c->adam2, (void*)c->W1h, (void*)c->W2h,
-                    (void*)c->lath, (void*)c->w3r, (void*)c->m, (void*)c->s, (void*)c->minmax, (void*)c->loss,
+                    (void*)c->lath, (void*)c->latf, (void*)c->four, (void*)c->w3r, (void*)c->m, (void*)c->s,
+                    (void*)c->minmax, (void*)c->loss,
                     (void*)c->err, (void*)c->active, (void*)c->d_count, (void*)c->shown,
                     (void*)c->pts, (void*)c->tgt})
         cudaFree(p);

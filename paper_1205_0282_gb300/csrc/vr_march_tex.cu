@@ -248,47 +248,36 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
     const float2 dqUV = make_float2(dq[U], dq[V]), qsUV = make_float2(qs[U], qs[V]);
     const float2 oUV = make_float2(ou, ov);
     auto fetch = [&](float f, Corners& s) {
-        if constexpr (PREC != kPrecF8) {
-            // positions, fractions and texel coordinates along (U, V) as packed
-            // FP32x2 operations (each lane rounds like the scalar one)
-            const float qS = fmaf(f, dq[S], qs[S]);
-            const float2 qUV = __ffma2_rn(make_float2(f, f), dqUV, qsUV);
-            const int ps = __float2int_rz(qS), iu = __float2int_rz(qUV.x), iv = __float2int_rz(qUV.y);
-            const float2 fUV = make_float2((float)iu, (float)iv);
-            s.fs = qS - (float)ps;
-            const float2 fr = __fadd2_rn(qUV, make_float2(-fUV.x, -fUV.y));
-            s.fu = fr.x;
-            s.fv = fr.y;
-            const float2 xy = __fadd2_rn(oUV, fUV);
-            // FP32 and FP16 textures both return FP32 values
-            gather4(tex, lay0 + ps, xy.x, xy.y, s.c[0], s.c[1], s.c[2], s.c[3]);
-            gather4(tex, lay0 + ps + 1, xy.x, xy.y, s.c[4], s.c[5], s.c[6], s.c[7]);
-            return;
-        }
+        // positions, fractions and texel coordinates along (U, V) as packed FP32x2
+        // operations (each lane rounds like the scalar one)
         const float qS = fmaf(f, dq[S], qs[S]);
-        const float qU = fmaf(f, dq[U], qs[U]);
-        const float qV = fmaf(f, dq[V], qs[V]);
+        const float2 qUV = __ffma2_rn(make_float2(f, f), dqUV, qsUV);
         // Samples sit inside the brick up to rounding: truncation is the floor for
         // q > -1.  A sample on the brick's far face (q = B: the cube's far face, or
         // rounding) has cell index B and weight 0 on its +1 corners, which FP32 and
         // FP16 read from the global texture (at a clamped coordinate beyond the
         // cube).  FP8 clamps the index to the lattice instead, since its +1 corners
         // are rescaled by the scale of the brick that owns them.
-        const int ps = PREC == kPrecF8 ? min(__float2int_rz(qS), imax[S]) : __float2int_rz(qS);
-        const int iu = PREC == kPrecF8 ? min(__float2int_rz(qU), imax[U]) : __float2int_rz(qU);
-        const int iv = PREC == kPrecF8 ? min(__float2int_rz(qV), imax[V]) : __float2int_rz(qV);
+        int ps = __float2int_rz(qS), iu = __float2int_rz(qUV.x), iv = __float2int_rz(qUV.y);
+        if (PREC == kPrecF8) {
+            ps = min(ps, imax[S]);
+            iu = min(iu, imax[U]);
+            iv = min(iv, imax[V]);
+        }
+        const float2 fUV = make_float2((float)iu, (float)iv);
         s.fs = qS - (float)ps;
-        s.fu = qU - (float)iu;
-        s.fv = qV - (float)iv;
-        const float x = ou + (float)iu, y = ov + (float)iv;
+        const float2 fr = __fadd2_rn(qUV, make_float2(-fUV.x, -fUV.y));
+        s.fu = fr.x;
+        s.fv = fr.y;
+        const float2 xy = __fadd2_rn(oUV, fUV);
         if (PREC != kPrecF8) {
             // FP32 and FP16 textures both return FP32 values
-            gather4(tex, lay0 + ps, x, y, s.c[0], s.c[1], s.c[2], s.c[3]);
-            gather4(tex, lay0 + ps + 1, x, y, s.c[4], s.c[5], s.c[6], s.c[7]);
+            gather4(tex, lay0 + ps, xy.x, xy.y, s.c[0], s.c[1], s.c[2], s.c[3]);
+            gather4(tex, lay0 + ps + 1, xy.x, xy.y, s.c[4], s.c[5], s.c[6], s.c[7]);
         } else {
             int k[8];
-            gather4_codes(tex, lay0 + ps, x, y, k[0], k[1], k[2], k[3]);
-            gather4_codes(tex, lay0 + ps + 1, x, y, k[4], k[5], k[6], k[7]);
+            gather4_codes(tex, lay0 + ps, xy.x, xy.y, k[0], k[1], k[2], k[3]);
+            gather4_codes(tex, lay0 + ps + 1, xy.x, xy.y, k[4], k[5], k[6], k[7]);
 #pragma unroll
             for (int c = 0; c < 8; ++c) s.c[c] = __int_as_float(k[c]);
             s.halo = (iu == lim_u ? 1 : 0) | (iv == lim_v ? 2 : 0) | (ps == lim_s ? 4 : 0);
@@ -319,27 +308,16 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
     float fi = 0.0f;
     auto step = [&](Corners& cur) {
         decode(cur);
-        float val;
-        if constexpr (PREC != kPrecF8) {
-            // along S first, two corners per packed FP32x2 operation: the gather
-            // leaves (c[2], c[3]) and (c[1], c[0]) in register pairs
-            const float2 fs2 = make_float2(cur.fs, cur.fs);
-            const float2 a10 = make_float2(cur.c[1], cur.c[0]), a23 = make_float2(cur.c[2], cur.c[3]);
-            const float2 b10 = make_float2(cur.c[5], cur.c[4]), b23 = make_float2(cur.c[6], cur.c[7]);
-            const float2 s10 = __ffma2_rn(fs2, __fadd2_rn(b10, make_float2(-a10.x, -a10.y)), a10);
-            const float2 s23 = __ffma2_rn(fs2, __fadd2_rn(b23, make_float2(-a23.x, -a23.y)), a23);
-            const float e0 = fmaf(cur.fu, s10.x - s10.y, s10.y);   // row v
-            const float e1 = fmaf(cur.fu, s23.y - s23.x, s23.x);   // row v + 1
-            val = fmaf(cur.fv, e1 - e0, e0);
-        } else {
-            const float e00 = fmaf(cur.fu, cur.c[1] - cur.c[0], cur.c[0]);
-            const float e10 = fmaf(cur.fu, cur.c[3] - cur.c[2], cur.c[2]);
-            const float e01 = fmaf(cur.fu, cur.c[5] - cur.c[4], cur.c[4]);
-            const float e11 = fmaf(cur.fu, cur.c[7] - cur.c[6], cur.c[6]);
-            const float e0 = fmaf(cur.fv, e10 - e00, e00);
-            const float e1 = fmaf(cur.fv, e11 - e01, e01);
-            val = fmaf(cur.fs, e1 - e0, e0);
-        }
+        // along S first, two corners per packed FP32x2 operation: the gather leaves
+        // (c[2], c[3]) and (c[1], c[0]) in register pairs (FP8: the decoded values)
+        const float2 fs2 = make_float2(cur.fs, cur.fs);
+        const float2 a10 = make_float2(cur.c[1], cur.c[0]), a23 = make_float2(cur.c[2], cur.c[3]);
+        const float2 b10 = make_float2(cur.c[5], cur.c[4]), b23 = make_float2(cur.c[6], cur.c[7]);
+        const float2 s10 = __ffma2_rn(fs2, __fadd2_rn(b10, make_float2(-a10.x, -a10.y)), a10);
+        const float2 s23 = __ffma2_rn(fs2, __fadd2_rn(b23, make_float2(-a23.x, -a23.y)), a23);
+        const float e0 = fmaf(cur.fu, s10.x - s10.y, s10.y);   // row v
+        const float e1 = fmaf(cur.fu, s23.y - s23.x, s23.x);   // row v + 1
+        float val = fmaf(cur.fv, e1 - e0, e0);
         if (PREC == kPrecF8) val *= k0;
         if constexpr (MODE == 1) {
             // a MIP ray stops once it reaches the data's global maximum (Section
