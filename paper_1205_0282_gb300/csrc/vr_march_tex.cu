@@ -25,10 +25,10 @@ namespace vr {
 namespace texm {
 
 #ifndef VR_TEX_DEPTH_F32
-#define VR_TEX_DEPTH_F32 2
+#define VR_TEX_DEPTH_F32 3
 #endif
 #ifndef VR_TEX_BLOCKS_F32
-#define VR_TEX_BLOCKS_F32 14
+#define VR_TEX_BLOCKS_F32 12
 #endif
 #ifndef VR_TEX_DEPTH_F16
 #define VR_TEX_DEPTH_F16 2
@@ -43,10 +43,11 @@ namespace texm {
 #define VR_TEX_BLOCKS_F8 16
 #endif
 // Samples whose gathers are in flight ahead of the one being composited, and
-// resident CTAs per SM the kernels are compiled for (14: 72 registers a thread;
-// 16: 64).  Measured on the 1080p orbit of the 8 GiB cube: two samples ahead at
-// 14 CTAs beat one ahead at 16-20 for FP32 and FP16 storage; FP8, whose decode
-// needs more registers per buffer, is fastest one ahead at 16.
+// resident CTAs per SM the kernels are compiled for (12: 80 registers a thread;
+// 14: 72; 16: 64).  Measured on the 1080p orbit of the 8 GiB cube: for FP32, three
+// samples ahead at 12 CTAs (1.5% faster than two ahead at 14, which beat one
+// ahead at 16-20 and four ahead at 10); FP16 two ahead at 14; FP8, whose decode
+// makes it ALU-bound, is fastest one ahead at 16 (two ahead: 10% slower).
 __host__ __device__ constexpr int tex_depth(int prec) {
     return prec == kPrecF8 ? VR_TEX_DEPTH_F8 : (prec == kPrecF16 ? VR_TEX_DEPTH_F16 : VR_TEX_DEPTH_F32);
 }
