@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["hi", "mid", "tiny"], default="hi")
+    ap.add_argument("--config", choices=["hi", "mid", "tiny", "xl"], default="hi",
+                    help="xl (with --learned): the 4096x4096x3200 (~200 GiB) cube, generated brick by brick "
+                         "on request, learned against plain out-of-core at the same device budgets")
     ap.add_argument("--tf", choices=["a", "b"], default="a")
     ap.add_argument("--width", type=int, default=0, help="override the image width")
     ap.add_argument("--height", type=int, default=0, help="override the image height")
@@ -87,6 +89,17 @@ def parse():
     ap.add_argument("--fallback-bound", type=float, default=None,
                     help="--learned: bricks whose decode error (above the TF floor, in data units) exceeds "
                          "this are copied from pinned plain blocks instead of decoded")
+    ap.add_argument("--xl-budgets-gib", default="32,96",
+                    help="--config xl: device brick-cache budgets (GiB) at which both forms render")
+    ap.add_argument("--xl-frames", type=int, default=4, help="--config xl: timed frames per form and budget")
+    ap.add_argument("--xl-slab-layers", type=int, default=4,
+                    help="--config xl: brick layers per training slab (generated on the host, copied to the device)")
+    ap.add_argument("--xl-decoder-slabs", type=int, default=3,
+                    help="--config xl: slabs the shared decoder is trained on (--train-steps each)")
+    ap.add_argument("--xl-slab-steps", type=int, default=1500,
+                    help="--config xl: steps fitting each slab's latents to the trained decoder")
+    ap.add_argument("--xl-scale", type=int, default=1,
+                    help="--config xl: divide each axis by this and the source counts by its cube (quick checks)")
     ap.add_argument("--e2e-steps", type=int, default=120)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -779,6 +792,194 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def xl_slabs(nbz: int, layers: int):
+    """Brick-layer ranges [bz0, bz1) of the training slabs, in order."""
+    return [(b, min(b + layers, nbz)) for b in range(0, nbz, layers)]
+
+
+def spread(items, k: int):
+    """k items evenly spaced over the list (all of them when k >= len)."""
+    if k >= len(items):
+        return list(items)
+    return [items[(i * len(items)) // k + len(items) // (2 * k)] for i in range(k)]
+
+
+def run_learned_xl(args):
+    """The learned form on the 4096x4096x3200 (~200 GiB) cube, which never exists
+    whole: its bricks are generated on request by the seeded block source.  The
+    codec is trained slab by slab (a slab of brick layers generated on the host
+    into pinned memory and copied to the device): first the shared decoder with
+    the latents of a few slabs, then every slab's latents fitted to the fixed
+    decoder.  Learned (latents on the device, fallback bricks' plain blocks in
+    pinned host memory) and plain out-of-core (every missing brick from the
+    provider) render the same orbit poses at each device budget; PSNR of the
+    learned frames against the plain ones."""
+    import torch
+
+    from paper_1205_0282_gb300 import vr as vrm
+
+    torch.cuda.set_device(0)
+    k = max(1, args.xl_scale)
+    spec = dict(synth.XL)
+    shape = tuple(n // k for n in spec["shape_xyz"])
+    n_line, n_cont = spec["n_line"] // k ** 3, max(1, spec["n_cont"] // k ** 3)
+    src = synth.BlockSource(shape, spec["seed"], synth.hi_sources(spec["seed"], shape, n_line, n_cont))
+    brick = (args.codec_brick or 64,) * 3
+    tf = synth.tf_hi_a() if args.tf == "a" else synth.tf_hi_b()
+    floor = tf_floor(tf)
+    W = args.width or spec["width"]
+    H = args.height or spec["height"]
+    poses = synth.orbit(shape, 60, 15.0, W, H)
+    nbs = [(n - 2 + b) // b for n, b in zip(shape, brick)]
+    nb = int(np.prod(nbs))
+    V = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1)
+    cube_bytes = 4 * int(np.prod(shape))
+    bound = 2.0 if args.fallback_bound is None else args.fallback_bound
+    desc = (f"XL cube {shape[0]}x{shape[1]}x{shape[2]} f32 ({cube_bytes / 2 ** 30:.0f} GiB; noise + {n_line} line + "
+            f"{n_cont} continuum sources), generated brick by brick on request, {brick[0]}^3 bricks, {W}x{H}, "
+            f"step 0.5, 16-point TF-{args.tf.upper()}, tau 0.99, 60-pose orbit")
+
+    # ---- codec training, slab by slab
+    codec = vrm.Codec(nb, brick)
+    rng = np.random.default_rng(3)
+    H_, K_ = vrm.Codec.HIDDEN, vrm.Codec.K_IN
+    W1 = rng.uniform(-1, 1, (H_, K_)) / np.sqrt(28.0)
+    W1[:, 28:] = 0.0
+    params = {"W1": W1, "b1": np.zeros(H_), "W2": rng.uniform(-1, 1, (H_, H_)) / np.sqrt(H_),
+              "b2": np.zeros(H_), "w3": rng.uniform(-1, 1, H_) / np.sqrt(H_), "b3": np.zeros(1)}
+    lat = rng.standard_normal((nb, 8, 8, 8, 16), dtype=np.float32) * np.float32(0.1)
+    codec.set_params(codec.pack(params, lat), np.zeros(nb), np.ones(nb))
+    del lat
+    slabs = xl_slabs(nbs[2], args.xl_slab_layers)
+    max_planes = min(args.xl_slab_layers * brick[2], shape[2] - 1) + 1
+    host = torch.empty((max_planes, shape[1], shape[0]), dtype=torch.float32, pin_memory=True)
+    dev = torch.empty((max_planes, shape[1], shape[0]), dtype=torch.float32, device="cuda")
+    t_gen = 0.0
+
+    def load(bz0, bz1):
+        nonlocal t_gen
+        z0, z1 = bz0 * brick[2], min(bz1 * brick[2], shape[2] - 1)
+        t = time.perf_counter()
+        src.fill_planes(host.data_ptr(), z0, z1)
+        t_gen += time.perf_counter() - t
+        d = dev[: z1 - z0 + 1]
+        d.copy_(host[: z1 - z0 + 1])
+        return d
+
+    t0 = time.perf_counter()
+    losses_a, losses_b = [], []
+    fitted = set()
+    for i, (bz0, bz1) in enumerate(spread(slabs, args.xl_decoder_slabs)):
+        d = load(bz0, bz1)
+        codec.fit_stats_slab(d, shape, bz0, bz1, floor)
+        fitted.add((bz0, bz1))
+        done = 0
+        while done < args.train_steps:
+            n = min(250, args.train_steps - done)
+            lr = args.train_lr * (0.1 if done >= 0.8 * args.train_steps else 1.0)
+            losses_a.append(codec.train_slab(d, shape, bz0, bz1, n, args.train_batch, lr, lr,
+                                             seed=7919 * i + done))
+            done += n
+    for j, (bz0, bz1) in enumerate(slabs):
+        d = load(bz0, bz1)
+        codec.fit_stats_slab(d, shape, bz0, bz1, floor)
+        done = 0
+        while done < args.xl_slab_steps:
+            n = min(500, args.xl_slab_steps - done)
+            lr = args.train_lr * (0.1 if done >= 0.8 * args.xl_slab_steps else 1.0)
+            last = codec.train_slab(d, shape, bz0, bz1, n, args.train_batch, lr, 0.0, seed=104729 + 7919 * j + done)
+            done += n
+        losses_b.append(last)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del host, dev, d
+    torch.cuda.empty_cache()
+
+    # ---- both forms at each budget
+    budgets = [float(b) for b in args.xl_budgets_gib.split(",") if b.strip()]
+    frame_poses = [poses[(i * len(poses)) // args.xl_frames] for i in range(args.xl_frames)]
+    results = []
+    learned_line = None
+
+    def timed(r, cam, out):
+        r.set_camera(cam)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r.render(out)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t
+
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(0).uuid)
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    with ClockSampler(gpu_id) as clocks:
+        for budget in budgets:
+            row = {"budget_gib": budget}
+            for form in ("plain", "learned"):
+                r = vrm.VolumeRenderer(0)
+                if form == "plain":
+                    r.load_cube_provider(src, shape)
+                else:
+                    r.load_cube_codec(codec, shape)
+                    r.set_codec_fallback_provider(src, bound, floor)
+                r.set_option(vrm.VR_OPT_DEVICE_BUDGET, int(budget * 2 ** 30))
+                t = time.perf_counter()
+                r.brick(*brick)
+                setup_s = time.perf_counter() - t
+                r.set_transfer_function(tf)
+                info = {"setup_s": setup_s}
+                if form == "learned":
+                    err, n_plain = r.codec_brick_errors()
+                    info.update(bricks_plain=n_plain, bricks=nb, pinned_gib=n_plain * V * 4 / 2 ** 30,
+                                bound=bound)
+                cold = timed(r, frame_poses[0], out)
+                r.reset_stats()
+                secs, imgs = [], []
+                for cam in frame_poses:
+                    secs.append(timed(r, cam, out))
+                    imgs.append(out.cpu().numpy())
+                st = r.stats()
+                r.close()
+                info.update(cold_first_frame_s=cold, frame_s=secs, fps=len(secs) / sum(secs),
+                            samples_per_s=st["samples"] / sum(secs),
+                            bricks_rendered_per_frame=st["bricks_rendered"] / max(st["frames"], 1),
+                            bricks_filled_per_frame=st["bricks_uploaded"] / max(st["frames"], 1),
+                            launches=st["launches"], device_errors=st["device_errors"])
+                row[form] = info
+                row[form + "_imgs"] = imgs
+            a = np.stack(row.pop("learned_imgs")).astype(np.float64)
+            b = np.stack(row.pop("plain_imgs")).astype(np.float64)
+            mse = float(np.mean((a - b) ** 2))
+            row["psnr_db_learned_vs_plain"] = 10 * np.log10(1.0 / mse) if mse > 0 else None
+            row["max_abs_learned_vs_plain"] = float(np.abs(a - b).max())
+            results.append(row)
+            print(json.dumps({"xl_budget": row}), flush=True)
+            if learned_line is None:
+                learned_line = row
+    codec.close()
+    L = learned_line["learned"]
+    line = {"metric": METRIC, "value": L["samples_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.xl_frames,
+            "warmup": 1, "ms_per_step": 1e3 / L["fps"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (decoder bf16 x bf16 -> f32)", "data": "synthetic",
+            "config": {"workload": desc, "codec_brick": list(brick),
+                       "form": "learned: 8^3 x 16 BF16 latents per brick + shared MLP (28 -> 64 -> 64 -> 1, SiLU), "
+                               "bricks over the error bound from pinned plain blocks; plain: out-of-core, every "
+                               "missing brick generated on request (no host copy of the cube)",
+                       "train": {"decoder_slabs": args.xl_decoder_slabs, "decoder_steps_per_slab": args.train_steps,
+                                 "latent_steps_per_slab": args.xl_slab_steps, "slab_layers": args.xl_slab_layers,
+                                 "batch": args.train_batch, "lr": args.train_lr, "floor": floor},
+                       "timing": "wall clock per frame with a device synchronise on both sides (host generation "
+                                 "and uploads included); the first frame after vr_brick fills the cache (cold)"},
+            "fps": L["fps"],
+            "xl": {"cube_bytes": cube_bytes, "latent_bytes": nb * 8 * 8 * 8 * 16 * 2, "bricks": nb,
+                   "train_s": train_s, "host_generation_s_in_training": t_gen,
+                   "loss_decoder_last": losses_a[-1] if losses_a else None,
+                   "loss_latents_last_per_slab": losses_b,
+                   "budgets": results},
+            "gpu_launches": L["launches"], "clocks": clocks.summary(), "roofline": None, "cpu_baseline": None,
+            "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 SERVE_RESOLUTIONS = [(512, 512), (1280, 720), (1920, 1080), (3840, 2160)]
 
 
@@ -894,7 +1095,9 @@ def main():
     if args.serve and args.impl == "ours":
         return run_serve(args)
     if args.learned and args.impl == "ours":
-        return run_learned(args)
+        return run_learned_xl(args) if args.config == "xl" else run_learned(args)
+    if args.config == "xl":
+        raise SystemExit("--config xl runs with --learned (the cube never exists whole in host or device memory)")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -42,6 +42,7 @@ extern "C" {
 #define VR_ECUDA (-3)    /* a CUDA runtime/driver call failed */
 #define VR_ESTATE (-4)   /* call out of order (e.g. render before cube/brick/TF/camera) */
 #define VR_ETIMEOUT (-5) /* a bounded device wait gave up; the frame is invalid */
+#define VR_ESOURCE (-6)  /* a brick provider (vr_block_provider) reported a failure */
 
 typedef struct vr_ctx vr_ctx;
 
@@ -176,6 +177,9 @@ typedef struct {
                                 (default): 1 when every brick fits the budget with its
                                 copies, else 0 (a streaming cache keeps four times the
                                 slots).  Takes effect at the next vr_brick. */
+#define VR_OPT_PROVIDER_THREADS 10 /* host threads that call a brick provider (and copy a
+                                host cube into the brick store) at once; <= 0 (default):
+                                the machine's hardware threads. */
 #define VR_PRECISION_F32 0
 #define VR_PRECISION_F16 1
 #define VR_PRECISION_F8 2
@@ -215,6 +219,38 @@ int vr_load_cube(vr_ctx* ctx, const float* data, int64_t nx, int64_t ny, int64_t
  * Errors: VR_EINVAL (bad sizes, device memory), VR_ECUDA.
  */
 int vr_load_cube_host(vr_ctx* ctx, const float* data, int64_t nx, int64_t ny, int64_t nz);
+
+/*
+ * A brick provider: fills one box of the cube on request, for cubes that exist only
+ * as a function (read from storage, received, or generated).  The paper's render
+ * nodes likewise load their sub-cubes from a file server on request (Sections 2.2
+ * and 2.3.1).  Voxel (origin[0] + i, origin[1] + j, origin[2] + k), i < extent[0],
+ * j < extent[1], k < extent[2], goes to dst[k * slice_stride + j * row_stride + i]
+ * (strides in floats, row_stride >= extent[0], slice_stride >= row_stride *
+ * extent[1]); the box always lies inside the cube and dst is host memory the
+ * library owns.  Returns 0 on success, anything else on failure.  The library
+ * calls it from up to VR_OPT_PROVIDER_THREADS host threads at once, so it must be
+ * thread-safe, and it must return the same values for a voxel every time.
+ */
+typedef int (*vr_block_provider)(void* user, const int64_t origin[3], const int32_t extent[3], float* dst,
+                                 int64_t row_stride, int64_t slice_stride);
+
+/*
+ * Out-of-core load from a provider (no counterpart in the paper): like
+ * vr_load_cube_host, but no host copy of the cube or of its bricks is kept.
+ * vr_brick calls the provider once for every brick's block (its voxels plus the
+ * one-voxel apron, clipped to the cube) to compute the bricks' ranges; vr_render
+ * calls it for every brick the frame needs that is not in the device cache
+ * (VR_OPT_DEVICE_BUDGET), into pinned staging buffers the library owns, copies the
+ * blocks into their cache slots with cudaMemcpyAsync on a side stream, and marches
+ * them as vr_load_cube_host does, while the bricks already resident march.  fn and
+ * user must stay valid until the context is destroyed or another cube is loaded.
+ * Images are those of vr_load_cube_host with the same values, bit for bit.
+ * Errors: VR_EINVAL (null fn, bad sizes), VR_ECUDA; a failing provider makes
+ * vr_brick or vr_render return VR_ESOURCE (vr_last_error names the brick; a frame
+ * that fails leaves the cache's failed slots empty and can be rendered again).
+ */
+int vr_load_cube_provider(vr_ctx* ctx, vr_block_provider fn, void* user, int64_t nx, int64_t ny, int64_t nz);
 
 /*
  * Partition the loaded cube into bricks of bx x by x bz voxels (Section 2.3.1;
@@ -512,6 +548,27 @@ void vr_codec_brick_size(const vr_codec* codec, int32_t B[3]);
 int vr_codec_train(vr_codec* codec, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps,
                    int32_t batch, float lr, float active_frac, uint64_t seed, double* last_loss);
 
+/* The same two steps for a cube that does not fit the device, one slab of brick
+ * layers at a time.  slab: device float32[z1 - z0 + 1][ny][nx], the planes z0 =
+ * bz0 * bz .. z1 = min(bz1 * bz, nz - 1) of the (nx, ny, nz) cube (bz the codec's
+ * brick depth), holding the bricks whose z index lies in [bz0, bz1) with their
+ * aprons (brick ids bz0 * nbx * nby .. bz1 * nbx * nby - 1, x fastest).
+ * vr_codec_fit_stats_slab fits those bricks' offset, scale and range as
+ * vr_codec_fit_stats does.  vr_codec_train_slab takes `steps` Adam steps on
+ * `batch` voxels drawn from the slab's bricks above the floor (uniform brick, then
+ * uniform voxel of its block; all bricks when the floor is -FLT_MAX; no step when
+ * none is above it): the shared network at rate mlp_lr (0: kept as it is, e.g.
+ * to fit latents to a trained decoder), the slab's latents at rate lr; other
+ * bricks' latents, gradients and moments are not touched.  A slab's latents count
+ * their own Adam steps (bias correction), the network its own.  Training over all
+ * layers at once with mlp_lr = lr is vr_codec_train with active_frac 0.
+ * Errors: VR_EINVAL (sizes, layers), VR_ENOMEM, VR_ECUDA, VR_ETIMEOUT. */
+int vr_codec_fit_stats_slab(vr_codec* codec, const float* slab, int64_t nx, int64_t ny, int64_t nz, int32_t bz0,
+                            int32_t bz1, float floor_v);
+int vr_codec_train_slab(vr_codec* codec, const float* slab, int64_t nx, int64_t ny, int64_t nz, int32_t bz0,
+                        int32_t bz1, int32_t steps, int32_t batch, float lr, float mlp_lr, uint64_t seed,
+                        double* last_loss);
+
 /* Decode the blocks of n bricks (device list of valid brick indices) into device
  * memory: brick k's V = (bx+1)(by+1)(bz+1) values (x fastest) go to out + k V, or
  * to out + slots[k] V when slots (device) is not NULL; on `stream`.
@@ -546,6 +603,16 @@ int vr_load_cube_codec(vr_ctx* ctx, vr_codec* codec, int64_t nx, int64_t ny, int
  * scan's own errors (VR_ENOMEM, VR_ECUDA) are reported by vr_brick.
  */
 int vr_set_codec_fallback(vr_ctx* ctx, const float* data, float bound, float floor_v);
+
+/*
+ * The same fallback with the plain blocks taken from a brick provider (see
+ * vr_load_cube_provider) instead of a host cube: the scan at vr_brick calls fn for
+ * every brick's block, and the bricks over the bound keep pinned host copies of
+ * their blocks.  fn = NULL turns the fallback off.  fn and user are used during
+ * vr_brick only.  Errors: as vr_set_codec_fallback; a failing provider makes
+ * vr_brick return VR_ESOURCE.
+ */
+int vr_set_codec_fallback_provider(vr_ctx* ctx, vr_block_provider fn, void* user, float bound, float floor_v);
 
 /* The per-brick errors measured by the last vr_brick's fallback scan (host
  * float32[n_bricks], may be NULL) and the number of bricks that fall back (may be

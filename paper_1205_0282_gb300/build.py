@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libvr.so")
 SOURCES = ["vr_host.cu", "vr_kernels.cu", "vr_march_tma.cu", "vr_march_tex.cu", "vr_noalloc.cu", "vr_shard.cu", "vr_ooc.cu", "vr_serve.cu", "vr_codec.cu"]
-HEADERS = ["df.cuh", "vr_internal.cuh", "vr_device.cuh", "vr_alpha_fit.h", "vr_ctx.cuh", "tc.cuh"]
+HEADERS = ["df.cuh", "vr_blocks.h", "vr_internal.cuh", "vr_device.cuh", "vr_alpha_fit.h", "vr_ctx.cuh", "tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -701,11 +701,14 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 }
 
 // Training points: uniform brick, uniform voxel of its (B+1)^3 block clipped to
-// the cube; target = the cube's value there.
-__global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, int64_t n_points,
-                              uint64_t seed, float floor_v, const uint32_t* __restrict__ active, uint64_t n_active,
-                              float active_frac, const int32_t* __restrict__ shown, int32_t n_shown,
-                              float4* __restrict__ pts, float* __restrict__ tgt) {
+// the cube; target = the cube's value there.  cube holds the planes from z = zoff
+// on (the whole cube when zoff = 0); without a list of shown bricks the brick is
+// uniform among [b_lo, b_hi).
+__global__ void sample_kernel(const float* __restrict__ cube, int64_t zoff, int3 n, int3 B, int3 nb,
+                              int32_t b_lo, int32_t b_hi, int64_t n_points, uint64_t seed, float floor_v,
+                              const uint32_t* __restrict__ active, uint64_t n_active, float active_frac,
+                              const int32_t* __restrict__ shown, int32_t n_shown, float4* __restrict__ pts,
+                              float* __restrict__ tgt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_points) return;
     const uint64_t r0 = mix64(seed ^ (uint64_t)(3 * i)), r1 = mix64(seed ^ (uint64_t)(3 * i + 1));
@@ -724,8 +727,7 @@ __global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, in
     } else {
         // a uniform brick among those the transfer function can show (all bricks
         // when none is listed), then a uniform voxel of its block
-        const int nbt = nb.x * nb.y * nb.z;
-        b = n_shown > 0 ? shown[r0 % (uint64_t)n_shown] : (int)(r0 % (uint64_t)nbt);
+        b = n_shown > 0 ? shown[r0 % (uint64_t)n_shown] : b_lo + (int)(r0 % (uint64_t)(b_hi - b_lo));
         bx = b % nb.x;
         by = (b / nb.x) % nb.y;
         bz = b / (nb.x * nb.y);
@@ -737,7 +739,7 @@ __global__ void sample_kernel(const float* __restrict__ cube, int3 n, int3 B, in
         gz = min(bz * B.z + uz, n.z - 1);
     }
     pts[i] = make_float4((float)(gx - bx * B.x), (float)(gy - by * B.y), (float)(gz - bz * B.z), __int_as_float(b));
-    tgt[i] = fmaxf(cube[((int64_t)gz * n.y + gy) * n.x + gx], floor_v);
+    tgt[i] = fmaxf(cube[(((int64_t)gz - zoff) * n.y + gy) * n.x + gx], floor_v);
 }
 
 // Voxels above the floor (the ones the transfer function can show): count, then
@@ -762,9 +764,9 @@ __global__ void active_kernel(const float* __restrict__ cube, int64_t n, float f
 
 // Per-brick offset and scale: mean and standard deviation (at least 1e-3) over
 // the brick's voxels and apron.
-__global__ void brick_stats_kernel(const float* __restrict__ cube, int3 n, int3 B, int3 nb, float floor_v, float* m,
-                                   float* s, float2* mm) {
-    const int b = blockIdx.x;
+__global__ void brick_stats_kernel(const float* __restrict__ cube, int64_t zoff, int3 n, int3 B, int3 nb, int32_t b0,
+                                   float floor_v, float* m, float* s, float2* mm) {
+    const int b = b0 + (int)blockIdx.x;
     const int bx = b % nb.x, by = (b / nb.x) % nb.y, bz = b / (nb.x * nb.y);
     const int x0 = bx * B.x, y0 = by * B.y, z0 = bz * B.z;
     const int x1 = min(x0 + B.x, n.x - 1), y1 = min(y0 + B.y, n.y - 1), z1 = min(z0 + B.z, n.z - 1);
@@ -775,7 +777,7 @@ __global__ void brick_stats_kernel(const float* __restrict__ cube, int3 n, int3 
         const int x = x0 + (int)(q % (x1 - x0 + 1));
         const int y = y0 + (int)((q / (x1 - x0 + 1)) % (y1 - y0 + 1));
         const int z = z0 + (int)(q / ((int64_t)(x1 - x0 + 1) * (y1 - y0 + 1)));
-        const float raw = cube[((int64_t)z * n.y + y) * n.x + x];
+        const float raw = cube[(((int64_t)z - zoff) * n.y + y) * n.x + x];
         lo = fminf(lo, raw);
         hi = fmaxf(hi, raw);
         const double v = fmaxf(raw, floor_v);
@@ -840,7 +842,11 @@ struct vr_codec {
     float4* pts = nullptr;
     float* tgt = nullptr;
     int64_t cap_pts = 0;
-    int64_t adam_t = 0;
+    int64_t adam_t = 0;               // Adam steps of the shared network
+    std::vector<int64_t> lat_t;       // per brick: Adam steps of its latents
+    std::vector<float2> h_minmax;     // host copy of minmax
+    int32_t* shown_range = nullptr;   // shown bricks of the last slab trained
+    int32_t cap_shown_range = 0;
     int sm_count = 0;
 };
 
@@ -862,14 +868,19 @@ int codec_cuda(cudaError_t e) { return e == cudaSuccess ? VR_OK : (cudaGetLastEr
         if (_rc) return _rc;                    \
     } while (0)
 
-// Refresh the BF16 operand copies from the FP32 parameters.
-int sync_bf16(vr_codec* c) {
+// Refresh the BF16 operand copies from the FP32 parameters (the latents of
+// bricks [b0, b1) only; b1 < 0: every brick).
+int sync_bf16(vr_codec* c, int32_t b0 = 0, int32_t b1 = -1) {
     using namespace vr::codec;
+    if (b1 < 0) b1 = c->n_bricks;
     to_bf16_kernel<<<64, 256>>>(c->theta + kOfsW1, c->W1h, kHidden * kIn);
     to_bf16_kernel<<<64, 256>>>(c->theta + kOfsW2, c->W2h, kHidden * kHidden);
     round_bf16_kernel<<<1, 64>>>(c->theta + kOfsW3, c->w3r, kHidden);
-    to_bf16_kernel<<<1024, 256>>>(c->theta + kOfsLat, c->lath, (int64_t)c->n_bricks * kLatPerBrick);
-    round_bf16_kernel<<<1024, 256>>>(c->theta + kOfsLat, c->latf, (int64_t)c->n_bricks * kLatPerBrick);
+    const int64_t o = (int64_t)b0 * kLatPerBrick, k = (int64_t)(b1 - b0) * kLatPerBrick;
+    if (k > 0) {
+        to_bf16_kernel<<<1024, 256>>>(c->theta + kOfsLat + o, c->lath + o, k);
+        round_bf16_kernel<<<1024, 256>>>(c->theta + kOfsLat + o, c->latf + o, k);
+    }
     return codec_cuda(cudaGetLastError());
 }
 
@@ -944,6 +955,74 @@ int check_err(vr_codec* c) {
     return h ? VR_ETIMEOUT : VR_OK;
 }
 
+// Bricks per axis of an (nx, ny, nz) cube bricked by the codec's B; false when
+// the count differs from the codec's.
+bool codec_grid(const vr_codec* c, int64_t nx, int64_t ny, int64_t nz, int3& n, int3& B, int3& nb) {
+    if (nx < 2 || ny < 2 || nz < 2 || nx > 65536 || ny > 65536 || nz > 65536) return false;
+    n = make_int3((int)nx, (int)ny, (int)nz);
+    B = make_int3(c->B[0], c->B[1], c->B[2]);
+    nb = make_int3((int)((nx - 2 + B.x) / B.x), (int)((ny - 2 + B.y) / B.y), (int)((nz - 2 + B.z) / B.z));
+    return (int64_t)nb.x * nb.y * nb.z == c->n_bricks;
+}
+
+// Offset, scale and range of bricks [b0, b1) from cube planes zoff on.
+int fit_range(vr_codec* c, const float* cube, int64_t zoff, int3 n, int3 B, int3 nb, int32_t b0, int32_t b1,
+              float floor_v) {
+    using namespace vr::codec;
+    c->floor_v = floor_v;
+    if (b1 <= b0) return VR_OK;
+    brick_stats_kernel<<<b1 - b0, 256>>>(cube, zoff, n, B, nb, b0, floor_v, c->m, c->s, c->minmax);
+    CODEC_CUDA(cudaGetLastError());
+    CODEC_CUDA(cudaMemcpy(c->h_minmax.data() + b0, c->minmax + b0, (size_t)(b1 - b0) * sizeof(float2),
+                          cudaMemcpyDeviceToHost));
+    return VR_OK;
+}
+
+// `steps` Adam steps on points of bricks [b0, b1) (from `shown` when listed) read
+// from cube planes zoff on: the shared network at rate mlp_lr (0: unchanged), the
+// latents of bricks [b0, b1) at rate lr; gradients, moments and BF16 copies of
+// other bricks' latents are not touched.
+int train_range(vr_codec* c, const float* cube, int64_t zoff, int3 n, int3 B, int3 nb, int32_t b0, int32_t b1,
+                const int32_t* shown, int32_t n_shown, float active_frac, int32_t steps, int32_t batch, float lr,
+                float mlp_lr, uint64_t seed, double* last_loss) {
+    using namespace vr::codec;
+    int rc = grow_points(c, batch);
+    if (rc) return rc;
+    const int64_t lo = kOfsLat + (int64_t)b0 * kLatPerBrick, cnt = (int64_t)(b1 - b0) * kLatPerBrick;
+    const bool whole = zoff == 0 && b0 == 0 && b1 == c->n_bricks;
+    int64_t t_lat = 0;
+    for (int32_t b = b0; b < b1; ++b) t_lat = std::max(t_lat, c->lat_t[b]);
+    for (int32_t it = 0; it < steps; ++it) {
+        sample_kernel<<<(batch + 255) / 256, 256>>>(cube, zoff, n, B, nb, b0, b1, batch, mix64_host(seed, it),
+                                                    c->floor_v, whole ? c->active : nullptr, whole ? c->n_active : 0,
+                                                    active_frac, shown, n_shown, c->pts, c->tgt);
+        CODEC_CUDA(cudaMemsetAsync(c->grad, 0, (size_t)kOfsLat * 4));
+        CODEC_CUDA(cudaMemsetAsync(c->grad + lo, 0, (size_t)cnt * 4));
+        CODEC_CUDA(cudaMemsetAsync(c->loss, 0, sizeof(double)));
+        if ((rc = launch_codec<true>(c, c->pts, Grid{}, c->tgt, batch, nullptr, 0))) return rc;
+        if (mlp_lr > 0.0f) {
+            ++c->adam_t;
+            const float c1 = 1.0f / (1.0f - powf(0.9f, (float)c->adam_t));
+            const float c2 = 1.0f / (1.0f - powf(0.999f, (float)c->adam_t));
+            adam_kernel<<<64, 256>>>(c->theta, c->grad, c->adam1, c->adam2, kOfsLat, mlp_lr, c1, c2);
+        }
+        ++t_lat;
+        const float c1 = 1.0f / (1.0f - powf(0.9f, (float)t_lat));
+        const float c2 = 1.0f / (1.0f - powf(0.999f, (float)t_lat));
+        adam_kernel<<<1024, 256>>>(c->theta + lo, c->grad + lo, c->adam1 + lo, c->adam2 + lo, cnt, lr, c1, c2);
+        if ((rc = sync_bf16(c, b0, b1))) return rc;
+    }
+    for (int32_t b = b0; b < b1; ++b) c->lat_t[b] = t_lat;
+    CODEC_CUDA(cudaDeviceSynchronize());
+    if ((rc = check_err(c))) return rc;
+    if (last_loss) {
+        double l = 0;
+        CODEC_CUDA(cudaMemcpy(&l, c->loss, sizeof(double), cudaMemcpyDeviceToHost));
+        *last_loss = l / (double)batch;
+    }
+    return VR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -958,6 +1037,8 @@ int vr_codec_create(int32_t n_bricks, const int32_t B[3], vr_codec** out) {
     c->n_bricks = n_bricks;
     for (int a = 0; a < 3; ++a) c->B[a] = B[a];
     c->n_params = kOfsLat + (int64_t)n_bricks * kLatPerBrick;
+    c->lat_t.assign(n_bricks, 0);
+    c->h_minmax.assign(n_bricks, make_float2(0.0f, 0.0f));
     const size_t pb = (size_t)c->n_params * sizeof(float);
     bool ok = cudaMalloc(&c->theta, pb) == cudaSuccess &&
               cudaMalloc(&c->grad_mem, pb + kGradPad * sizeof(float)) == cudaSuccess &&
@@ -1000,7 +1081,7 @@ void vr_codec_destroy(vr_codec* c) {
     for (void* p : {(void*)c->theta, (void*)c->grad_mem, (void*)c->adam1, (void*)c->adam2, (void*)c->W1h, (void*)c->W2h,
                     (void*)c->lath, (void*)c->latf, (void*)c->four, (void*)c->w3r, (void*)c->m, (void*)c->s,
                     (void*)c->minmax, (void*)c->loss,
-                    (void*)c->err, (void*)c->active, (void*)c->d_count, (void*)c->shown,
+                    (void*)c->err, (void*)c->active, (void*)c->d_count, (void*)c->shown, (void*)c->shown_range,
                     (void*)c->pts, (void*)c->tgt})
         cudaFree(p);
     delete c;
@@ -1014,6 +1095,7 @@ int vr_codec_set_params(vr_codec* c, const float* theta, const float* m, const f
     CODEC_CUDA(cudaMemcpy(c->m, m, (size_t)c->n_bricks * 4, cudaMemcpyHostToDevice));
     CODEC_CUDA(cudaMemcpy(c->s, s, (size_t)c->n_bricks * 4, cudaMemcpyHostToDevice));
     c->adam_t = 0;
+    std::fill(c->lat_t.begin(), c->lat_t.end(), 0);
     CODEC_CUDA(cudaMemset(c->adam1, 0, (size_t)c->n_params * 4));
     CODEC_CUDA(cudaMemset(c->adam2, 0, (size_t)c->n_params * 4));
     return sync_bf16(c);
@@ -1073,18 +1155,15 @@ int vr_codec_gradient(vr_codec* c, const float* points, const float* targets, in
 int vr_codec_fit_stats(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64_t nz, float floor_v) {
     using namespace vr::codec;
     if (!c || !cube) return VR_EINVAL;
-    const int3 n = make_int3((int)nx, (int)ny, (int)nz), B = make_int3(c->B[0], c->B[1], c->B[2]);
-    const int3 nb = make_int3((int)((nx - 2 + B.x) / B.x), (int)((ny - 2 + B.y) / B.y), (int)((nz - 2 + B.z) / B.z));
-    if ((int64_t)nb.x * nb.y * nb.z != c->n_bricks) return VR_EINVAL;
-    c->floor_v = floor_v;
-    brick_stats_kernel<<<c->n_bricks, 256>>>(cube, n, B, nb, floor_v, c->m, c->s, c->minmax);
-    CODEC_CUDA(cudaGetLastError());
+    int3 n, B, nb;
+    if (!codec_grid(c, nx, ny, nz, n, B, nb)) return VR_EINVAL;
+    int rc = fit_range(c, cube, 0, n, B, nb, 0, c->n_bricks, floor_v);
+    if (rc) return rc;
     // the bricks with values above the floor: training samples only those (the
     // others are skipped by the renderer's empty-space test whenever the transfer
     // function is transparent up to the floor)
     {
-        std::vector<float2> mm(c->n_bricks);
-        CODEC_CUDA(cudaMemcpy(mm.data(), c->minmax, (size_t)c->n_bricks * 8, cudaMemcpyDeviceToHost));
+        const std::vector<float2>& mm = c->h_minmax;
         std::vector<int32_t> shown;
         for (int32_t b = 0; b < c->n_bricks; ++b)
             if (mm[b].y > floor_v) shown.push_back(b);
@@ -1126,34 +1205,53 @@ int vr_codec_get_minmax(vr_codec* c, float* out) {
 
 int vr_codec_train(vr_codec* c, const float* cube, int64_t nx, int64_t ny, int64_t nz, int32_t steps, int32_t batch,
                    float lr, float active_frac, uint64_t seed, double* last_loss) {
-    using namespace vr::codec;
     if (!c || !cube || steps < 0 || batch < 1) return VR_EINVAL;
-    const int3 n = make_int3((int)nx, (int)ny, (int)nz), B = make_int3(c->B[0], c->B[1], c->B[2]);
-    const int3 nb = make_int3((int)((nx - 2 + B.x) / B.x), (int)((ny - 2 + B.y) / B.y), (int)((nz - 2 + B.z) / B.z));
-    if ((int64_t)nb.x * nb.y * nb.z != c->n_bricks) return VR_EINVAL;
-    int rc = grow_points(c, batch);
+    int3 n, B, nb;
+    if (!codec_grid(c, nx, ny, nz, n, B, nb)) return VR_EINVAL;
+    return train_range(c, cube, 0, n, B, nb, 0, c->n_bricks, c->shown, c->n_shown, active_frac, steps, batch, lr, lr,
+                       seed, last_loss);
+}
+
+int vr_codec_fit_stats_slab(vr_codec* c, const float* slab, int64_t nx, int64_t ny, int64_t nz, int32_t bz0,
+                            int32_t bz1, float floor_v) {
+    if (!c || !slab) return VR_EINVAL;
+    int3 n, B, nb;
+    if (!codec_grid(c, nx, ny, nz, n, B, nb) || bz0 < 0 || bz1 > nb.z || bz0 >= bz1) return VR_EINVAL;
+    const int32_t layer = nb.x * nb.y;
+    int rc = fit_range(c, slab, (int64_t)bz0 * B.z, n, B, nb, bz0 * layer, bz1 * layer, floor_v);
     if (rc) return rc;
-    for (int32_t it = 0; it < steps; ++it) {
-        sample_kernel<<<(batch + 255) / 256, 256>>>(cube, n, B, nb, batch, mix64_host(seed, it), c->floor_v,
-                                                    c->active, c->n_active, active_frac, c->shown, c->n_shown,
-                                                    c->pts, c->tgt);
-        CODEC_CUDA(cudaMemsetAsync(c->grad, 0, (size_t)c->n_params * 4));
-        CODEC_CUDA(cudaMemsetAsync(c->loss, 0, sizeof(double)));
-        if ((rc = launch_codec<true>(c, c->pts, Grid{}, c->tgt, batch, nullptr, 0))) return rc;
-        ++c->adam_t;
-        const float c1 = 1.0f / (1.0f - powf(0.9f, (float)c->adam_t));
-        const float c2 = 1.0f / (1.0f - powf(0.999f, (float)c->adam_t));
-        adam_kernel<<<1024, 256>>>(c->theta, c->grad, c->adam1, c->adam2, c->n_params, lr, c1, c2);
-        if ((rc = sync_bf16(c))) return rc;
+    return codec_cuda(cudaDeviceSynchronize());
+}
+
+int vr_codec_train_slab(vr_codec* c, const float* slab, int64_t nx, int64_t ny, int64_t nz, int32_t bz0, int32_t bz1,
+                        int32_t steps, int32_t batch, float lr, float mlp_lr, uint64_t seed, double* last_loss) {
+    if (!c || !slab || steps < 0 || batch < 1 || !(lr >= 0.0f) || !(mlp_lr >= 0.0f)) return VR_EINVAL;
+    int3 n, B, nb;
+    if (!codec_grid(c, nx, ny, nz, n, B, nb) || bz0 < 0 || bz1 > nb.z || bz0 >= bz1) return VR_EINVAL;
+    const int32_t layer = nb.x * nb.y, b0 = bz0 * layer, b1 = bz1 * layer;
+    // the slab's bricks with values above the floor (all of them when none has)
+    std::vector<int32_t> shown;
+    if (c->floor_v > -FLT_MAX)
+        for (int32_t b = b0; b < b1; ++b)
+            if (c->h_minmax[b].y > c->floor_v) shown.push_back(b);
+    if (shown.empty() && c->floor_v > -FLT_MAX) {   // nothing to learn: the renderer skips these bricks
+        if (last_loss) *last_loss = 0.0;
+        return VR_OK;
     }
-    CODEC_CUDA(cudaDeviceSynchronize());
-    if ((rc = check_err(c))) return rc;
-    if (last_loss) {
-        double l = 0;
-        CODEC_CUDA(cudaMemcpy(&l, c->loss, sizeof(double), cudaMemcpyDeviceToHost));
-        *last_loss = l / (double)batch;
+    if ((int32_t)shown.size() > c->cap_shown_range) {
+        cudaFree(c->shown_range);
+        c->shown_range = nullptr;
+        c->cap_shown_range = 0;
+        if (cudaMalloc(&c->shown_range, shown.size() * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return VR_ENOMEM;
+        }
+        c->cap_shown_range = (int32_t)shown.size();
     }
-    return VR_OK;
+    if (!shown.empty())
+        CODEC_CUDA(cudaMemcpy(c->shown_range, shown.data(), shown.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return train_range(c, slab, (int64_t)bz0 * B.z, n, B, nb, b0, b1, shown.empty() ? nullptr : c->shown_range,
+                       (int32_t)shown.size(), 0.0f, steps, batch, lr, mlp_lr, seed, last_loss);
 }
 
 int vr_codec_decode_bricks(vr_codec* c, const int32_t* bricks, const int32_t* slots, int32_t n, float* out,

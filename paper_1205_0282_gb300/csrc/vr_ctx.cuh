@@ -13,6 +13,7 @@
 
 #include "../../include/vr.h"
 #include "vr_alpha_fit.h"
+#include "vr_blocks.h"
 #include "vr_internal.cuh"
 
 using vr::df;
@@ -336,10 +337,22 @@ struct vr_ctx {
     // out-of-core mode (vr_load_cube_host): cube in host memory, bricks cached on the device
     bool ooc = false;
     const float* h_src = nullptr;      // the caller's cube
+    vr_block_provider prov_fn = nullptr;  // vr_load_cube_provider: bricks come from the provider
+    void* prov_user = nullptr;
+    int prov_threads = 0;              // VR_OPT_PROVIDER_THREADS
+    // provider contexts: pinned staging for the blocks of one upload launch, the
+    // buffers taken in turn (a buffer is refilled once its copies have finished)
+    static constexpr int kStage = 3;
+    float* h_stage[kStage] = {nullptr, nullptr, nullptr};
+    size_t stage_cap = 0;              // bytes of each staging buffer
+    cudaEvent_t ev_stage[kStage] = {nullptr, nullptr, nullptr};
+    int stage_next = 0;
     vr_codec* codec = nullptr;         // learned residency: slots are filled by decoding
     // learned residency's fallback: bricks whose decode error exceeds fb_bound are
     // copied from plain blocks in h_store (block plain_index[b]) instead
     const float* fb_src = nullptr;     // the caller's plain cube, read at vr_brick
+    vr_block_provider fb_fn = nullptr; // or a provider of the plain blocks
+    void* fb_user = nullptr;
     float fb_bound = 0.0f, fb_floor = 0.0f;
     bool fb_measured = false;          // brick_err holds the last vr_brick's errors
     std::vector<float> brick_err;

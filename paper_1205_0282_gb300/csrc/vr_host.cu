@@ -106,9 +106,19 @@ void free_ooc(vr_ctx* c) {
     c->d_pool = nullptr;
     c->store_bytes = 0;
     c->res = vr::Residency();
+    for (int j = 0; j < vr_ctx::kStage; ++j) {
+        if (c->ev_stage[j]) cudaEventSynchronize(c->ev_stage[j]);
+        if (c->h_stage[j]) cudaFreeHost(c->h_stage[j]);
+        c->h_stage[j] = nullptr;
+    }
+    c->stage_cap = 0;
     c->h_src = nullptr;
+    c->prov_fn = nullptr;
+    c->prov_user = nullptr;
     c->codec = nullptr;
     c->fb_src = nullptr;
+    c->fb_fn = nullptr;
+    c->fb_user = nullptr;
     c->fb_measured = false;
     c->brick_err.clear();
     c->plain_index.clear();
@@ -132,7 +142,21 @@ int ensure_ooc_streams(vr_ctx* c) {
     VR_CUDA(c, cudaStreamCreateWithPriority(&c->ring_stream, cudaStreamNonBlocking, hi_prio));
     VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_start, cudaEventDisableTiming));
     VR_CUDA(c, cudaEventCreateWithFlags(&c->ev_ring_end, cudaEventDisableTiming));
+    for (cudaEvent_t& ev : c->ev_stage) VR_CUDA(c, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     return VR_OK;
+}
+
+vr::BlockSource brick_source(vr_ctx* c) {
+    vr::BlockSource bs;
+    bs.cube = c->h_src;
+    bs.fn = c->prov_fn;
+    bs.user = c->prov_user;
+    bs.threads = c->prov_threads;
+    return bs;
+}
+
+int source_fail(vr_ctx* c, int64_t brick) {
+    return fail(c, VR_ESOURCE, "the brick provider failed for brick " + std::to_string(brick));
 }
 
 // Learned residency's fallback (at vr_brick): decode every brick, compare it with
@@ -143,7 +167,12 @@ int codec_fallback_scan(vr_ctx* c) {
     c->plain_index.assign(nb, -1);
     c->n_plain = 0;
     c->fb_measured = false;
-    if (!c->fb_src) return VR_OK;
+    vr::BlockSource fb;
+    fb.cube = c->fb_src;
+    fb.fn = c->fb_fn;
+    fb.user = c->fb_user;
+    fb.threads = c->prov_threads;
+    if (!fb.valid()) return VR_OK;
     const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
     const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nb, ((int64_t)256 << 20) / (int64_t)slot_bytes));
     float *d_dec = nullptr, *d_plain = nullptr, *h_stage = nullptr;
@@ -164,7 +193,11 @@ int codec_fallback_scan(vr_ctx* c) {
     for (int64_t b0 = 0; !rc && b0 < nb; b0 += chunk) {
         const int32_t k = (int32_t)std::min<int64_t>(chunk, nb - b0);
         for (int32_t i = 0; i < k; ++i) h_ids[i] = (int32_t)(b0 + i);
-        vr::build_brick_blocks(c->fb_src, c->n, c->B, c->nb, h_ids, k, h_stage, c->slot_floats);
+        int64_t bad = -1;
+        if (vr::read_blocks(fb, c->n, c->B, c->nb, h_ids, k, h_stage, c->slot_floats, nullptr, &bad)) {
+            rc = source_fail(c, bad);
+            break;
+        }
         if (cudaMemcpyAsync(d_ids, h_ids, k * sizeof(int32_t), cudaMemcpyHostToDevice, c->copy_stream) !=
                 cudaSuccess ||
             cudaMemcpyAsync(d_plain, h_stage, k * slot_bytes, cudaMemcpyHostToDevice, c->copy_stream) != cudaSuccess) {
@@ -207,8 +240,10 @@ int codec_fallback_scan(vr_ctx* c) {
         c->store_bytes = 0;
         return fail(c, VR_ENOMEM, "cannot allocate the pinned store of the fallback bricks");
     }
-    vr::build_brick_blocks(c->fb_src, c->n, c->B, c->nb, plain.data(), (int64_t)plain.size(), c->h_store,
-                           c->slot_floats);
+    int64_t bad = -1;
+    if (vr::read_blocks(fb, c->n, c->B, c->nb, plain.data(), (int64_t)plain.size(), c->h_store, c->slot_floats,
+                        nullptr, &bad))
+        return source_fail(c, bad);
     return VR_OK;
 }
 
@@ -265,6 +300,12 @@ int make_pool_tex(vr_ctx* c, int64_t slots) {
 // Brick store and device cache of an out-of-core context (at vr_brick).
 int build_ooc_store(vr_ctx* c) {
     free_pool_tex(c);
+    for (int j = 0; j < vr_ctx::kStage; ++j) {
+        if (c->ev_stage[j]) cudaEventSynchronize(c->ev_stage[j]);
+        if (c->h_stage[j]) cudaFreeHost(c->h_stage[j]);
+        c->h_stage[j] = nullptr;
+    }
+    c->stage_cap = 0;
     if (c->h_store) cudaFreeHost(c->h_store);
     cudaFree(c->d_pool);
     c->h_store = nullptr;
@@ -278,6 +319,29 @@ int build_ooc_store(vr_ctx* c) {
             return fail(c, VR_EINVAL, "the bricking does not match the codec's");
         if (vr_codec_get_minmax(c->codec, reinterpret_cast<float*>(c->h_minmax.data())))
             return fail(c, VR_ECUDA, "cannot read the codec's brick ranges");
+    } else if (c->prov_fn) {
+        // no store: every brick once through the provider for its range, then the
+        // pinned staging the uploads go through (one launch's bricks per buffer:
+        // at most a 64 MiB group of resident uploads or a 32-brick ring half)
+        const int64_t per_chunk = std::max<int64_t>(1, ((int64_t)256 << 20) / (int64_t)slot_bytes);
+        std::vector<float> buf((size_t)(std::min<int64_t>(per_chunk, c->n_bricks) * c->slot_floats));
+        for (int64_t b0 = 0; b0 < c->n_bricks; b0 += per_chunk) {
+            const int64_t k = std::min<int64_t>(per_chunk, c->n_bricks - b0);
+            std::vector<int32_t> ids(k);
+            for (int64_t i = 0; i < k; ++i) ids[i] = (int32_t)(b0 + i);
+            int64_t bad = -1;
+            if (vr::read_blocks(brick_source(c), c->n, c->B, c->nb, ids.data(), k, buf.data(), c->slot_floats,
+                                c->h_minmax.data() + b0, &bad))
+                return source_fail(c, bad);
+        }
+        const size_t group = std::max<size_t>(1, ((size_t)64 << 20) / slot_bytes);
+        c->stage_cap = std::max<size_t>(group, 32) * slot_bytes;
+        for (int j = 0; j < vr_ctx::kStage; ++j)
+            if (cudaHostAlloc((void**)&c->h_stage[j], c->stage_cap, cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                c->h_stage[j] = nullptr;
+                return fail(c, VR_ENOMEM, "cannot allocate the provider's pinned staging");
+            }
     } else {
         c->store_bytes = slot_bytes * (size_t)c->n_bricks;
         if (cudaHostAlloc((void**)&c->h_store, c->store_bytes, cudaHostAllocDefault) != cudaSuccess) {
@@ -285,7 +349,8 @@ int build_ooc_store(vr_ctx* c) {
             c->h_store = nullptr;
             return fail(c, VR_ENOMEM, "cannot allocate the pinned brick store");
         }
-        vr::build_brick_store(c->h_src, c->n, c->B, c->nb, c->h_store, c->slot_floats, c->h_minmax.data());
+        vr::read_blocks(brick_source(c), c->n, c->B, c->nb, nullptr, c->n_bricks, c->h_store, c->slot_floats,
+                        c->h_minmax.data(), nullptr);
     }
     // the texture march keeps each slot four times: its block and three layered
     // copies; automatically chosen when every brick fits the budget that way
@@ -554,6 +619,8 @@ void vr_destroy(vr_ctx* c) {
     for (cudaEvent_t ev : c->ev_chunk) cudaEventDestroy(ev);
     for (cudaEvent_t ev : c->ev_half_read)
         if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->ev_stage)
+        if (ev) cudaEventDestroy(ev);
     delete c;
 }
 
@@ -628,6 +695,34 @@ int vr_load_cube_host(vr_ctx* c, const float* data, int64_t nx, int64_t ny, int6
     return VR_OK;
 }
 
+int vr_load_cube_provider(vr_ctx* c, vr_block_provider fn, void* user, int64_t nx, int64_t ny, int64_t nz) {
+    if (!c) return VR_EINVAL;
+    if (!fn) return fail(c, VR_EINVAL, "null brick provider");
+    if (nx < 2 || ny < 2 || nz < 2 || nx > 65536 || ny > 65536 || nz > 65536)
+        return fail(c, VR_EINVAL, "cube sizes must be in [2, 65536]");
+    VR_CUDA(c, cudaSetDevice(c->device));
+    int rc = retire_all(c);
+    if (rc) return rc;
+    cudaFree(c->d_cube);
+    cudaFree(c->d_cube_xzy);
+    c->d_cube = nullptr;
+    c->d_cube_xzy = nullptr;
+    c->bricked = false;
+    c->tma_ready = false;
+    c->tex_fits = -1;
+    free_tex(c);
+    free_ooc(c);
+    if ((rc = ensure_ooc_streams(c))) return rc;
+    c->ooc = true;
+    c->prov_fn = fn;
+    c->prov_user = user;
+    c->nx_pad = nx;
+    c->n[0] = nx;
+    c->n[1] = ny;
+    c->n[2] = nz;
+    return VR_OK;
+}
+
 int vr_load_cube_codec(vr_ctx* c, vr_codec* codec, int64_t nx, int64_t ny, int64_t nz) {
     if (!c) return VR_EINVAL;
     if (!codec) return fail(c, VR_EINVAL, "null codec");
@@ -660,6 +755,20 @@ int vr_set_codec_fallback(vr_ctx* c, const float* data, float bound, float floor
     if (!c->codec) return fail(c, VR_ESTATE, "the fallback needs a learned context (vr_load_cube_codec)");
     if (std::isnan(bound) || std::isnan(floor_v)) return fail(c, VR_EINVAL, "NaN bound or floor");
     c->fb_src = data;
+    c->fb_fn = nullptr;
+    c->fb_user = nullptr;
+    c->fb_bound = bound;
+    c->fb_floor = floor_v;
+    return VR_OK;
+}
+
+int vr_set_codec_fallback_provider(vr_ctx* c, vr_block_provider fn, void* user, float bound, float floor_v) {
+    if (!c) return VR_EINVAL;
+    if (!c->codec) return fail(c, VR_ESTATE, "the fallback needs a learned context (vr_load_cube_codec)");
+    if (std::isnan(bound) || std::isnan(floor_v)) return fail(c, VR_EINVAL, "NaN bound or floor");
+    c->fb_src = nullptr;
+    c->fb_fn = fn;
+    c->fb_user = fn ? user : nullptr;
     c->fb_bound = bound;
     c->fb_floor = floor_v;
     return VR_OK;
@@ -921,6 +1030,7 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
             c->kernel = (int)value;
             return VR_OK;
         case VR_OPT_DEVICE_BUDGET: c->budget = value; return VR_OK;
+        case VR_OPT_PROVIDER_THREADS: c->prov_threads = (int)std::max<int64_t>(0, std::min<int64_t>(value, 4096)); return VR_OK;
         case VR_OPT_OOC_MARCH:
             if (value < 0 || value > 2) return fail(c, VR_EINVAL, "out-of-core march must be 0, 1 or 2");
             c->ooc_march = (int)value;
@@ -1109,12 +1219,47 @@ int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off, size_t* 
         if (rc) return fail(c, rc, "brick decode failed");
         return VR_OK;
     }
+    if (c->prov_fn) {
+        // the provider fills a staging buffer whose earlier copies have finished
+        const int j = c->stage_next;
+        c->stage_next = (j + 1) % vr_ctx::kStage;
+        if (L.up.size() * slot_bytes > c->stage_cap) return fail(c, VR_EINVAL, "internal: upload group too large");
+        VR_CUDA(c, cudaEventSynchronize(c->ev_stage[j]));
+        int64_t bad = -1;
+        if (vr::read_blocks(brick_source(c), c->n, c->B, c->nb, L.up.data(), (int64_t)L.up.size(), c->h_stage[j],
+                            c->slot_floats, nullptr, &bad))
+            return source_fail(c, bad);
+        for (size_t k = 0; k < L.up.size(); ++k)
+            VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
+                                       c->h_stage[j] + k * c->slot_floats, slot_bytes, cudaMemcpyHostToDevice,
+                                       c->copy_stream));
+        VR_CUDA(c, cudaEventRecord(c->ev_stage[j], c->copy_stream));
+        *copied = L.up.size() * slot_bytes;
+        return VR_OK;
+    }
     for (size_t k = 0; k < L.up.size(); ++k)
         VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
                                    c->h_store + (size_t)L.up[k] * c->slot_floats, slot_bytes,
                                    cudaMemcpyHostToDevice, c->copy_stream));
     *copied = L.up.size() * slot_bytes;
     return VR_OK;
+}
+
+// A frame whose provider failed: let the work already issued finish (it reads the
+// frame's buffers), and forget the resident slots this frame was to fill, so
+// that the next frame asks for those bricks again.
+int abort_frame(vr_ctx* c, cudaStream_t st, const std::vector<OocLaunch>& launches, int rc) {
+    cudaStreamSynchronize(st);
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamSynchronize(c->ring_stream);
+    for (const OocLaunch& L : launches)
+        if (L.half < 0)
+            for (size_t k = 0; k < L.up.size(); ++k) {
+                const int32_t b = L.up[k], sl = L.slot[k];
+                if (c->res.slot_of_brick[b] == sl) c->res.slot_of_brick[b] = -1;
+                if (c->res.brick_in_slot[sl] == b) c->res.brick_in_slot[sl] = -1;
+            }
+    return rc;
 }
 
 int ensure_events(vr_ctx* c, std::vector<cudaEvent_t>& ev, size_t n) {
@@ -1278,18 +1423,21 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
         bool resident_uploads = false;
         for (const OocLaunch& L : ooc_launches) resident_uploads = resident_uploads || (L.half < 0 && !L.up.empty());
         if (resident_uploads) VR_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_march_done, 0));
-        // every resident upload at once; the ring two launches ahead of the march
+        // every resident upload at once (with a provider, each just before its own
+        // launch, so that the host fills a group while the earlier ones march); the
+        // ring two launches ahead of the march
+        const bool lazy = c->prov_fn != nullptr;
         std::vector<size_t> ring_launches;
         for (size_t k = 0; k < nl; ++k) {
             if (ooc_launches[k].half < 0) {
-                if ((rc2 = issue_upload(k))) return rc2;
+                if (!lazy && (rc2 = issue_upload(k))) return abort_frame(c, st, ooc_launches, rc2);
             } else {
                 ring_launches.push_back(k);
             }
         }
         size_t ring_issued = 0;
         while (ring_issued < std::min<size_t>(2, ring_launches.size()))
-            if ((rc2 = issue_upload(ring_launches[ring_issued++]))) return rc2;
+            if ((rc2 = issue_upload(ring_launches[ring_issued++]))) return abort_frame(c, st, ooc_launches, rc2);
         VR_CUDA(c, cudaEventRecord(s.ev_march0, st));
         // the streamed bricks march on their own stream, beside the resident ones,
         // so that waiting for a ring half never holds back the resident work
@@ -1302,6 +1450,7 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
         for (size_t k = 0; k < nl; ++k) {
             const OocLaunch& L = ooc_launches[k];
             cudaStream_t ms = L.half >= 0 ? c->ring_stream : st;
+            if (lazy && L.half < 0 && (rc2 = issue_upload(k))) return abort_frame(c, st, ooc_launches, rc2);
             if (!L.up.empty()) VR_CUDA(c, cudaStreamWaitEvent(ms, c->ev_chunk[k], 0));
             if (L.hi > L.lo) {
                 vr::FrameParams q = p;
@@ -1318,7 +1467,8 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
             if (L.half >= 0) {
                 VR_CUDA(c, cudaEventRecord(c->ev_half_read[L.half], ms));
                 if (ring_issued < ring_launches.size())
-                    if ((rc2 = issue_upload(ring_launches[ring_issued++]))) return rc2;
+                    if ((rc2 = issue_upload(ring_launches[ring_issued++])))
+                        return abort_frame(c, st, ooc_launches, rc2);
             }
         }
         if (ring) {

@@ -10,6 +10,9 @@
 //                      per-sub-cube range, used for empty-space skipping).
 //   build_brick_blocks the same blocks for a list of bricks only (the plain
 //                      copies a learned context keeps for its fallback bricks).
+//   read_blocks        blocks of a list of bricks from the host cube or from a
+//                      provider callback (cubes that exist only as a function:
+//                      generated, or read from storage on request).
 //   launch_brick_error per brick, the largest difference between its decoded
 //                      and its plain block, both clipped from below at a floor.
 //   plan_residency     assign a device slot to every brick a frame renders:
@@ -20,24 +23,31 @@
 //                      across frames, and the bricks left over stream through the
 //                      ring.
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
+#include <climits>
 #include <cstring>
 #include <thread>
 #include <vector>
 
+#include "vr_blocks.h"
 #include "vr_internal.cuh"
 
 namespace vr {
 
 namespace {
 
-// Blocks of bricks ids[i] (or i when ids is null), i < count, into store + i * slot_floats.
-void build_blocks(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3], const int32_t* ids,
-                  int64_t count, float* store, int64_t slot_floats, float2* minmax) {
-    const int64_t total = count;
+// Blocks of bricks ids[i] (or i when ids is null), i < count, into store + i *
+// slot_floats, from the host cube or the provider; bricks are dealt to the threads
+// one at a time (a provider's cost per brick can vary).
+int build_blocks(const BlockSource& src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
+                 const int32_t* ids, int64_t count, float* store, int64_t slot_floats, float2* minmax,
+                 int64_t* bad_brick) {
     const int64_t sx = B[0] + 1, sy = B[1] + 1;
-    auto work = [&](int64_t b0, int64_t b1) {
-        for (int64_t i = b0; i < b1; ++i) {
+    std::atomic<int64_t> next{0};
+    std::atomic<int64_t> bad{INT64_MAX};
+    auto work = [&]() {
+        for (int64_t i = next++; i < count && bad.load() == INT64_MAX; i = next++) {
             const int64_t id = ids ? ids[i] : i;
             const int64_t ix = id % nb[0], iy = (id / nb[0]) % nb[1], iz = id / ((int64_t)nb[0] * nb[1]);
             const int64_t x0 = ix * B[0], y0 = iy * B[1], z0 = iz * B[2];
@@ -45,27 +55,53 @@ void build_blocks(const float* src, const int64_t n[3], const int32_t B[3], cons
             const int64_t y1 = std::min<int64_t>(y0 + B[1], n[1] - 1);
             const int64_t z1 = std::min<int64_t>(z0 + B[2], n[2] - 1);
             float* blk = store + i * slot_floats;
-            std::memset(blk, 0, (size_t)slot_floats * sizeof(float));
-            float mn = FLT_MAX, mx = -FLT_MAX;
-            for (int64_t z = z0; z <= z1; ++z)
-                for (int64_t y = y0; y <= y1; ++y) {
-                    const float* row = src + (z * n[1] + y) * n[0] + x0;
-                    float* dst = blk + ((z - z0) * sy + (y - y0)) * sx;
-                    const int64_t len = x1 - x0 + 1;
-                    std::memcpy(dst, row, (size_t)len * sizeof(float));
-                    for (int64_t x = 0; x < len; ++x) {
-                        mn = std::min(mn, row[x]);
-                        mx = std::max(mx, row[x]);
+            // zero the part of the block beyond the cube (all of it when clipped)
+            if (x1 - x0 < B[0] || y1 - y0 < B[1] || z1 - z0 < B[2])
+                std::memset(blk, 0, (size_t)slot_floats * sizeof(float));
+            const int64_t len = x1 - x0 + 1;
+            if (src.fn) {
+                const int64_t origin[3] = {x0, y0, z0};
+                const int32_t extent[3] = {(int32_t)len, (int32_t)(y1 - y0 + 1), (int32_t)(z1 - z0 + 1)};
+                if (src.fn(src.user, origin, extent, blk, sx, sx * sy) != 0) {
+                    int64_t cur = bad.load();
+                    while (id < cur && !bad.compare_exchange_weak(cur, id)) {
                     }
+                    break;
                 }
-            if (minmax) minmax[i] = make_float2(mn, mx);
+            } else {
+                for (int64_t z = z0; z <= z1; ++z)
+                    for (int64_t y = y0; y <= y1; ++y)
+                        std::memcpy(blk + ((z - z0) * sy + (y - y0)) * sx, src.cube + (z * n[1] + y) * n[0] + x0,
+                                    (size_t)len * sizeof(float));
+            }
+            if (minmax) {
+                float mn = FLT_MAX, mx = -FLT_MAX;
+                for (int64_t z = 0; z <= z1 - z0; ++z)
+                    for (int64_t y = 0; y <= y1 - y0; ++y) {
+                        const float* row = blk + (z * sy + y) * sx;
+                        for (int64_t x = 0; x < len; ++x) {
+                            mn = std::min(mn, row[x]);
+                            mx = std::max(mx, row[x]);
+                        }
+                    }
+                minmax[i] = make_float2(mn, mx);
+            }
         }
     };
-    const int64_t threads = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), total));
-    std::vector<std::thread> pool;
-    for (int64_t t = 0; t < threads; ++t)
-        pool.emplace_back(work, total * t / threads, total * (t + 1) / threads);
-    for (auto& th : pool) th.join();
+    const int64_t hw = src.threads > 0 ? src.threads : (int64_t)std::max(1u, std::thread::hardware_concurrency());
+    const int64_t threads = std::max<int64_t>(1, std::min<int64_t>(hw, count));
+    if (threads == 1) {
+        work();
+    } else {
+        std::vector<std::thread> pool;
+        for (int64_t t = 0; t < threads; ++t) pool.emplace_back(work);
+        for (auto& th : pool) th.join();
+    }
+    if (bad.load() != INT64_MAX) {
+        if (bad_brick) *bad_brick = bad.load();
+        return VR_ESOURCE;
+    }
+    return VR_OK;
 }
 
 // One block of threads per (part of a) brick: the largest clipped difference over
@@ -93,14 +129,25 @@ __global__ void brick_error_kernel(const float* __restrict__ decoded, const floa
 
 }  // namespace
 
+int read_blocks(const BlockSource& src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
+                const int32_t* ids, int64_t count, float* store, int64_t slot_floats, float2* minmax,
+                int64_t* bad_brick) {
+    if (count <= 0) return VR_OK;
+    return build_blocks(src, n, B, nb, ids, count, store, slot_floats, minmax, bad_brick);
+}
+
 void build_brick_store(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
                        float* store, int64_t slot_floats, float2* minmax) {
-    build_blocks(src, n, B, nb, nullptr, (int64_t)nb[0] * nb[1] * nb[2], store, slot_floats, minmax);
+    BlockSource bs;
+    bs.cube = src;
+    build_blocks(bs, n, B, nb, nullptr, (int64_t)nb[0] * nb[1] * nb[2], store, slot_floats, minmax, nullptr);
 }
 
 void build_brick_blocks(const float* src, const int64_t n[3], const int32_t B[3], const int32_t nb[3],
                         const int32_t* ids, int64_t count, float* store, int64_t slot_floats) {
-    build_blocks(src, n, B, nb, ids, count, store, slot_floats, nullptr);
+    BlockSource bs;
+    bs.cube = src;
+    build_blocks(bs, n, B, nb, ids, count, store, slot_floats, nullptr, nullptr);
 }
 
 cudaError_t launch_brick_error(const float* decoded, const float* plain, int64_t first, int32_t count,

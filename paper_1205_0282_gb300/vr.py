@@ -21,6 +21,7 @@ VR_ENOMEM = -2
 VR_ECUDA = -3
 VR_ESTATE = -4
 VR_ETIMEOUT = -5
+VR_ESOURCE = -6
 
 VR_OPT_SKIP_EMPTY = 1
 VR_OPT_RECT_CULL = 2
@@ -35,12 +36,13 @@ VR_OPT_DEVICE_BUDGET = 6
 VR_OPT_STEP_MODE = 7
 VR_OPT_TEX_SLAB_LAYERS = 8
 VR_OPT_OOC_MARCH = 9
+VR_OPT_PROVIDER_THREADS = 10
 VR_PRECISION_F32 = 0
 VR_PRECISION_F16 = 1
 VR_PRECISION_F8 = 2
 
 _ERR_NAMES = {VR_EINVAL: "VR_EINVAL", VR_ENOMEM: "VR_ENOMEM", VR_ECUDA: "VR_ECUDA",
-              VR_ESTATE: "VR_ESTATE", VR_ETIMEOUT: "VR_ETIMEOUT"}
+              VR_ESTATE: "VR_ESTATE", VR_ETIMEOUT: "VR_ETIMEOUT", VR_ESOURCE: "VR_ESOURCE"}
 
 
 class VRError(RuntimeError):
@@ -71,16 +73,17 @@ class vr_stats(ctypes.Structure):
 
 
 # The exported symbols, in header order (tests check them against include/vr.h).
-EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_brick", "vr_set_transfer_function",
+EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_load_cube_provider", "vr_brick", "vr_set_transfer_function",
            "vr_set_camera", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
            "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_kd_partition", "vr_kd_order",
            "vr_set_region", "vr_region_rect", "vr_plan_region_rect", "vr_render_rect",
            "vr_composite_subimages", "vr_server_create", "vr_server_submit", "vr_server_wait",
            "vr_server_get_stats", "vr_server_destroy", "vr_codec_gemm_check", "vr_codec_create",
            "vr_codec_destroy", "vr_codec_param_count", "vr_codec_set_params", "vr_codec_get_params",
-           "vr_codec_forward", "vr_codec_gradient", "vr_codec_fit_stats", "vr_codec_train",
+           "vr_codec_forward", "vr_codec_gradient", "vr_codec_fit_stats", "vr_codec_train", "vr_codec_fit_stats_slab",
+           "vr_codec_train_slab",
            "vr_codec_decode_bricks", "vr_codec_get_minmax", "vr_codec_brick_count", "vr_codec_brick_size",
-           "vr_load_cube_codec", "vr_set_codec_fallback", "vr_codec_brick_errors", "vr_render_noalloc",
+           "vr_load_cube_codec", "vr_set_codec_fallback", "vr_set_codec_fallback_provider", "vr_codec_brick_errors", "vr_render_noalloc",
            "vr_last_error"]
 
 
@@ -103,6 +106,7 @@ def _load():
     lib.vr_codec_param_count.restype = ctypes.c_int64
     lib.vr_load_cube.argtypes = [P, P, I64, I64, I64]
     lib.vr_load_cube_host.argtypes = [P, P, I64, I64, I64]
+    lib.vr_load_cube_provider.argtypes = [P, P, P, I64, I64, I64]
     lib.vr_brick.argtypes = [P, I32, I32, I32]
     lib.vr_set_transfer_function.argtypes = [P, P, I32]
     lib.vr_set_camera.argtypes = [P, ctypes.POINTER(vr_camera)]
@@ -142,10 +146,14 @@ def _load():
     lib.vr_codec_brick_size.restype = None
     lib.vr_load_cube_codec.argtypes = [P, P, I64, I64, I64]
     lib.vr_set_codec_fallback.argtypes = [P, P, ctypes.c_float, ctypes.c_float]
+    lib.vr_set_codec_fallback_provider.argtypes = [P, P, P, ctypes.c_float, ctypes.c_float]
     lib.vr_codec_brick_errors.argtypes = [P, P, ctypes.POINTER(I64)]
     lib.vr_codec_train.argtypes = [P, P, I64, I64, I64, I32, I32, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
                                    ctypes.POINTER(ctypes.c_double)]
     lib.vr_codec_decode_bricks.argtypes = [P, P, P, I32, P, P]
+    lib.vr_codec_fit_stats_slab.argtypes = [P, P, I64, I64, I64, I32, I32, ctypes.c_float]
+    lib.vr_codec_train_slab.argtypes = [P, P, I64, I64, I64, I32, I32, I32, I32, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
     lib.vr_render_noalloc.argtypes = [P, I64, I64, I64, I32, I32, I32, P, I32,
                                       ctypes.POINTER(vr_camera), P, P]
     lib.vr_last_error.argtypes = [P]
@@ -237,6 +245,52 @@ def vr_load_cube_host(ctx, cube) -> None:
     nz, ny, nx = cube.shape
     addr, keep = _ptr(cube)
     _check(ctx, _lib.vr_load_cube_host(ctx, addr, nx, ny, nz))
+
+
+# int provider(void* user, const int64_t origin[3], const int32_t extent[3], float* dst,
+#              int64_t row_stride, int64_t slice_stride)
+BLOCK_PROVIDER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.c_int64, ctypes.c_int64)
+
+
+def block_provider(provider):
+    """(fn, user, keep) for the C ABI from either a native provider (an object
+    with integer ``fn`` and ``user`` addresses, e.g. ``synth.BlockSource``) or a
+    Python callable ``provider(origin_xyz, extent_xyz) -> float32 (ez, ey, ex)``
+    (any thread may call it; an exception or a wrong shape reports a failure).
+    Keep ``keep`` alive while the library may call the provider."""
+    if hasattr(provider, "fn") and hasattr(provider, "user"):
+        return provider.fn, provider.user, provider
+    if not callable(provider):
+        raise TypeError("provider must be callable or have native fn/user addresses")
+
+    def cb(user, origin, extent, dst, row, slc):
+        try:
+            o = (int(origin[0]), int(origin[1]), int(origin[2]))
+            e = (int(extent[0]), int(extent[1]), int(extent[2]))
+            blk = np.asarray(provider(o, e), dtype=np.float32)
+            if blk.shape != (e[2], e[1], e[0]):
+                return 1
+            n = (e[2] - 1) * slc + (e[1] - 1) * row + e[0]
+            buf = np.ctypeslib.as_array(dst, shape=(n,))
+            view = np.lib.stride_tricks.as_strided(buf, shape=(e[2], e[1], e[0]), strides=(slc * 4, row * 4, 4))
+            view[...] = blk
+            return 0
+        except Exception:
+            return 1
+
+    f = BLOCK_PROVIDER(cb)
+    return ctypes.cast(f, ctypes.c_void_p).value, None, f
+
+
+def vr_load_cube_provider(ctx, provider, shape_xyz):
+    """Out-of-core load from a brick provider (see ``block_provider``); returns
+    the object to keep alive while the context uses the provider."""
+    fn, user, keep = block_provider(provider)
+    nx, ny, nz = (int(v) for v in shape_xyz)
+    _check(ctx, _lib.vr_load_cube_provider(ctx, fn, user, nx, ny, nz))
+    return keep
 
 
 def vr_brick(ctx, bx: int, by: int, bz: int) -> None:
@@ -544,6 +598,30 @@ class Codec:
                                      float(active_frac), int(seed), ctypes.byref(loss)), "vr_codec_train")
         return loss.value
 
+    def _slab_args(self, slab_dev, shape_xyz, bz0, bz1):
+        nx, ny, nz = (int(v) for v in shape_xyz)
+        bz = self.brick[2]
+        planes = min(bz1 * bz, nz - 1) - bz0 * bz + 1
+        if tuple(slab_dev.shape) != (planes, ny, nx) or not slab_dev.is_contiguous():
+            raise ValueError(f"slab must be a contiguous ({planes}, {ny}, {nx}) device tensor")
+        return slab_dev.data_ptr(), nx, ny, nz, int(bz0), int(bz1)
+
+    def fit_stats_slab(self, slab_dev, shape_xyz, bz0: int, bz1: int, floor=-3.4e38):
+        """fit_stats for the bricks of layers [bz0, bz1) from the slab of the cube's
+        planes bz0*Bz .. min(bz1*Bz, nz-1)."""
+        self._rc(_lib.vr_codec_fit_stats_slab(self.h, *self._slab_args(slab_dev, shape_xyz, bz0, bz1), float(floor)),
+                 "vr_codec_fit_stats_slab")
+
+    def train_slab(self, slab_dev, shape_xyz, bz0: int, bz1: int, steps: int, batch: int, lr: float,
+                   mlp_lr: float = None, seed: int = 1) -> float:
+        """Adam steps on the slab's bricks: their latents at lr, the shared network
+        at mlp_lr (default lr; 0 keeps it)."""
+        loss = ctypes.c_double()
+        self._rc(_lib.vr_codec_train_slab(self.h, *self._slab_args(slab_dev, shape_xyz, bz0, bz1), int(steps),
+                                          int(batch), float(lr), float(lr if mlp_lr is None else mlp_lr), int(seed),
+                                          ctypes.byref(loss)), "vr_codec_train_slab")
+        return loss.value
+
     def decode_bricks(self, bricks_dev, out_dev, slots_dev=None, stream=None):
         self._rc(_lib.vr_codec_decode_bricks(self.h, bricks_dev.data_ptr(),
                                              None if slots_dev is None else slots_dev.data_ptr(),
@@ -665,6 +743,17 @@ class VolumeRenderer:
         _check(self.ctx, _lib.vr_set_codec_fallback(self.ctx, cube.ctypes.data, float(bound), float(floor)))
         self._fallback_cube = cube
 
+    def set_codec_fallback_provider(self, provider, bound, floor=-3.4e38):
+        """As set_codec_fallback, with the plain blocks from a brick provider
+        (see ``block_provider``; used during the next brick() only)."""
+        if provider is None:
+            _check(self.ctx, _lib.vr_set_codec_fallback_provider(self.ctx, None, None, float(bound), float(floor)))
+            self._fallback_cube = None
+            return
+        fn, user, keep = block_provider(provider)
+        _check(self.ctx, _lib.vr_set_codec_fallback_provider(self.ctx, fn, user, float(bound), float(floor)))
+        self._fallback_cube = keep
+
     def codec_brick_errors(self):
         """(per-brick decode errors, number of bricks that fall back) of the last brick()."""
         err = np.zeros(self.n_bricks, dtype=np.float32)
@@ -679,6 +768,12 @@ class VolumeRenderer:
         nz, ny, nx = cube.shape
         self.shape_xyz = (nx, ny, nz)
         self._host_cube = cube
+
+    def load_cube_provider(self, provider, shape_xyz):
+        """Out-of-core from a brick provider (see ``block_provider``): no host
+        copy of the cube is kept; bricks are requested as frames need them."""
+        self._host_cube = vr_load_cube_provider(self.ctx, provider, shape_xyz)
+        self.shape_xyz = tuple(int(v) for v in shape_xyz)
 
     def brick(self, bx, by, bz):
         vr_brick(self.ctx, bx, by, bz)

@@ -17,6 +17,9 @@ available; the axes follow an HI spectral cube, Section 1.1):
   continuum sources extended along the whole spectral axis, 128^3 bricks,
   1920x1080 images, step 0.5, 16-point transfer functions, a 120-pose orbit
   about the y axis (the paper rotates its cubes about Y, Section 3.1).
+* ``xl``: 4096x4096x3200 cube (~200 GiB) = noise + 100,000 line sources + 500
+  continuum sources (the HI recipe), generated block by block on demand
+  (``BlockSource``), never whole.
 
 A camera is a plain dict with keys ``eye, target, up`` (3-tuples of float),
 ``fovy_deg``, ``width``, ``height``, ``step``, ``term_alpha``.  A transfer
@@ -50,7 +53,7 @@ def build(force: bool = False) -> str:
         return _LIB
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
     os.close(fd)
-    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+    cmd = ["gcc", "-O3", "-fno-math-errno", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
            "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
@@ -68,6 +71,10 @@ def _load():
             lib.synth_add_sources.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                               ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64]
             lib.synth_add_sources.restype = None
+            lib.synth_block.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64]
+            lib.synth_block.restype = None
             _lib = lib
     return _lib
 
@@ -126,6 +133,18 @@ def tiny_cube(seed: int = 1) -> np.ndarray:
     return add_sources(cube, src)
 
 
+def hi_sources(seed: int = 3, shape_xyz=(1024, 1024, 2048), n_line: int = 2000,
+               n_cont: int = 50) -> np.ndarray:
+    """The source list of an HI-survey-like cube: line sources (amplitude
+    log-uniform 1-20 sigma, spatial FWHM 2-6, spectral FWHM 3-40 channels), then
+    continuum sources (amplitude log-uniform 1-20 sigma, spatial FWHM 2-6)."""
+    rng = np.random.default_rng(seed)
+    lines = line_sources(rng, n_line, shape_xyz, (1.0, 20.0), (2.0, 6.0), (3.0, 40.0),
+                         log_amp=True)
+    cont = continuum_sources(rng, n_cont, shape_xyz, (1.0, 20.0), (2.0, 6.0))
+    return np.concatenate([lines, cont], axis=0)
+
+
 def hi_cube(seed: int = 3, shape_xyz=(1024, 1024, 2048), n_line: int = 2000,
             n_cont: int = 50) -> np.ndarray:
     """HI-survey-like cube: noise + line sources + continuum sources.
@@ -134,11 +153,75 @@ def hi_cube(seed: int = 3, shape_xyz=(1024, 1024, 2048), n_line: int = 2000,
     proportionally fewer sources serve tests."""
     nx, ny, nz = shape_xyz
     cube = noise_cube(nx, ny, nz, seed)
-    rng = np.random.default_rng(seed)
-    lines = line_sources(rng, n_line, shape_xyz, (1.0, 20.0), (2.0, 6.0), (3.0, 40.0),
-                         log_amp=True)
-    cont = continuum_sources(rng, n_cont, shape_xyz, (1.0, 20.0), (2.0, 6.0))
-    return add_sources(cube, np.concatenate([lines, cont], axis=0))
+    return add_sources(cube, hi_sources(seed, shape_xyz, n_line, n_cont))
+
+
+def cube_block(shape_xyz, seed: int, sources: np.ndarray, origin, extent,
+               sigma: float = 1.0) -> np.ndarray:
+    """float32[ez][ey][ex] block at ``origin`` of the cube noise_cube(*shape_xyz,
+    seed, sigma) + add_sources(sources), generated without the rest of the cube
+    (bit for bit the same values)."""
+    nx, ny, nz = shape_xyz
+    o = np.ascontiguousarray(origin, dtype=np.int64)
+    e = np.ascontiguousarray(extent, dtype=np.int32)
+    assert all(o >= 0) and all(e >= 1) and all(o + e <= np.array(shape_xyz))
+    src = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 7)
+    out = np.empty((int(e[2]), int(e[1]), int(e[0])), dtype=np.float32)
+    _load().synth_block(out.ctypes.data, int(e[0]), int(e[0]) * int(e[1]), o.ctypes.data, e.ctypes.data,
+                        nx, ny, nz, seed, sigma, src.ctypes.data, len(src))
+    return out
+
+
+class _CubeDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64 * 3), ("seed", ctypes.c_uint64), ("sigma", ctypes.c_double),
+                ("src", ctypes.c_void_p), ("n_src", ctypes.c_int64)]
+
+
+class BlockSource:
+    """A procedural cube as a native block source: ``fn`` is the address of a C
+    function with the renderer library's brick-provider signature (origin,
+    extent, destination, row and slice strides) and ``user`` the address of its
+    cube description; both stay valid while this object lives.  Any thread may
+    call it; nothing is held in memory but the source list."""
+
+    def __init__(self, shape_xyz, seed: int, sources: np.ndarray, sigma: float = 1.0):
+        lib = _load()
+        self.shape_xyz = tuple(int(v) for v in shape_xyz)
+        self.seed = int(seed)
+        self.sources = np.ascontiguousarray(sources, dtype=np.float64).reshape(-1, 7)
+        self._desc = _CubeDesc((ctypes.c_int64 * 3)(*self.shape_xyz), self.seed, float(sigma),
+                               self.sources.ctypes.data, len(self.sources))
+        self.fn = ctypes.cast(lib.synth_cube_block, ctypes.c_void_p).value
+        self.user = ctypes.addressof(self._desc)
+        self._lib = lib
+
+    def block(self, origin, extent) -> np.ndarray:
+        return cube_block(self.shape_xyz, self.seed, self.sources, origin, extent, self._desc.sigma)
+
+    def fill_planes(self, dst_ptr: int, z0: int, z1: int, threads: int = 0) -> None:
+        """Write the planes z0..z1 (inclusive) of the cube, float32[z1-z0+1][ny][nx],
+        to host memory at dst_ptr, split over threads (0: one per CPU)."""
+        from concurrent.futures import ThreadPoolExecutor
+        nx, ny, _ = self.shape_xyz
+        fn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int64,
+                              ctypes.c_int64)(self.fn)
+        plane = nx * ny
+        # tasks of a quarter plane (rows), so that a thin slab still spreads over the threads
+        rows = max(1, ny // 4)
+        tasks = [(z, y) for z in range(z0, z1 + 1) for y in range(0, ny, rows)]
+
+        def one(t):
+            z, y = t
+            h = min(rows, ny - y)
+            o = (ctypes.c_int64 * 3)(0, y, z)
+            e = (ctypes.c_int32 * 3)(nx, h, 1)
+            rc = fn(self.user, o, e, dst_ptr + 4 * ((z - z0) * plane + y * nx), nx, plane)
+            if rc:
+                raise RuntimeError(f"block source failed ({rc})")
+
+        with ThreadPoolExecutor(threads or os.cpu_count()) as ex:
+            list(ex.map(one, tasks))
 
 
 def random_cube(shape_xyz, seed: int, lo: float = -2.0, hi: float = 6.0) -> np.ndarray:
@@ -233,3 +316,13 @@ MID = {"name": "mid", "shape_xyz": (512, 512, 1024), "brick": (128, 128, 128),
        "width": 1920, "height": 1080}
 HI = {"name": "hi", "shape_xyz": (1024, 1024, 2048), "brick": (128, 128, 128),
       "width": 1920, "height": 1080}
+# ~200 GiB: never held whole in host memory; blocks come from BlockSource(XL ...)
+XL = {"name": "xl", "shape_xyz": (4096, 4096, 3200), "brick": (128, 128, 128),
+      "width": 1920, "height": 1080, "n_line": 100_000, "n_cont": 500, "seed": 7}
+
+
+def xl_source() -> "BlockSource":
+    """The 4096x4096x3200 cube (noise + 100k line + 500 continuum sources) as a
+    block source."""
+    return BlockSource(XL["shape_xyz"], XL["seed"],
+                       hi_sources(XL["seed"], XL["shape_xyz"], XL["n_line"], XL["n_cont"]))

@@ -458,3 +458,99 @@ def test_what_training_and_the_fallback_gain(vr):
     assert trained >= untrained + 10.0, (untrained, trained)
     assert 0 < n_plain < nb
     assert mixed > trained, (trained, mixed)
+
+
+# ------------------------------------------------ slab-by-slab fitting and training
+
+def _slab_case(vr, n_codecs=2):
+    """A ragged cube of 3 x 2 x 3 bricks of 16 (layers bz = 0, 1, 2, the last ones
+    partial) and codecs with the same initial parameters."""
+    import torch
+
+    import synth
+    shape, brick = (40, 33, 45), (16, 16, 16)
+    cube = np.zeros(shape[::-1], np.float32)
+    synth.add_sources(cube, synth.line_sources(np.random.default_rng(41), 12, shape, (2.0, 8.0),
+                                               (3.0, 8.0), (3.0, 10.0)))
+    cube += np.random.default_rng(42).normal(0, 0.05, cube.shape).astype(np.float32)
+    nb = 3 * 2 * 3
+    p, lat = ref.init_params(nb, seed=6)
+    codecs = []
+    for _ in range(n_codecs):
+        c = vr.Codec(nb, brick)
+        c.set_params(c.pack(p, lat), np.zeros(nb), np.ones(nb))
+        codecs.append(c)
+    return torch.from_numpy(cube).cuda(), shape, brick, nb, codecs
+
+
+def _slab(dev, bz0, bz1, bz=16):
+    return dev[bz0 * bz: min(bz1 * bz, dev.shape[0] - 1) + 1].contiguous()
+
+
+@pytest.mark.parametrize("floor", [-3.4e38, 0.5])
+def test_slab_fitting_and_training_equal_the_whole_cube(vr, floor):
+    """fit_stats slab by slab gives every brick's offset, scale and range of the
+    whole-cube fit bit for bit.  Training over all layers at once (slab = the
+    cube) draws the same points as vr_codec_train: the two agree to within the
+    run-to-run spread of vr_codec_train itself (its gradient sums use atomics, so
+    two runs differ in rounding), far closer than a run with another seed."""
+    dev, shape, brick, nb, (a, a2, b, c) = _slab_case(vr, 4)
+    for x in (a, a2):
+        x.fit_stats(dev, floor)
+    for x in (b, c):
+        for bz0, bz1 in ((0, 1), (1, 3)):
+            x.fit_stats_slab(_slab(dev, bz0, bz1), shape, bz0, bz1, floor)
+    ta, ma, sa = a.get_params()
+    tb, mb, sb = b.get_params()
+    assert np.array_equal(a.minmax(), b.minmax())
+    assert np.array_equal(ma, mb) and np.array_equal(sa, sb)
+    la = a.train(dev, steps=25, batch=4096, lr=3e-3, seed=3)
+    a2.train(dev, steps=25, batch=4096, lr=3e-3, seed=3)
+    lb = b.train_slab(dev, shape, 0, 3, steps=25, batch=4096, lr=3e-3, seed=3)
+    c.train_slab(dev, shape, 0, 3, steps=25, batch=4096, lr=3e-3, seed=4)
+    ta, ta2, tb, tc = (x.get_params()[0].astype(np.float64) for x in (a, a2, b, c))
+    spread = max(3 * np.mean(np.abs(ta - ta2)), 1e-5)
+    assert abs(la - lb) <= 1e-4 * abs(la)
+    assert np.mean(np.abs(ta - tb)) <= spread
+    assert np.mean(np.abs(ta - tc)) > 10 * spread
+    for x in (a, a2, b, c):
+        x.close()
+
+
+def test_slab_training_touches_only_its_latents(vr):
+    """Training slab [1, 2): the other layers' latents stay bit for bit; with
+    mlp_lr = 0 the shared network stays too, and the slab's loss falls."""
+    import torch
+    dev, shape, brick, nb, (a, b) = _slab_case(vr)
+    for bz0, bz1 in ((0, 1), (1, 2), (2, 3)):
+        a.fit_stats_slab(_slab(dev, bz0, bz1), shape, bz0, bz1)
+    th0 = a.get_params()[0]
+    n_mlp = a.n_params - nb * 8 ** 3 * 16
+    lat_of = lambda th, b0, b1: th[n_mlp + b0 * 8192: n_mlp + b1 * 8192]   # noqa: E731
+    slab = _slab(dev, 1, 2)
+    first = a.train_slab(slab, shape, 1, 2, steps=1, batch=8192, lr=3e-3, mlp_lr=0.0, seed=4)
+    last = a.train_slab(slab, shape, 1, 2, steps=200, batch=8192, lr=3e-3, mlp_lr=0.0, seed=5)
+    th1 = a.get_params()[0]
+    assert np.array_equal(th1[:n_mlp], th0[:n_mlp])
+    assert np.array_equal(lat_of(th1, 0, 6), lat_of(th0, 0, 6))
+    assert np.array_equal(lat_of(th1, 12, 18), lat_of(th0, 12, 18))
+    assert not np.array_equal(lat_of(th1, 6, 12), lat_of(th0, 6, 12))
+    assert last < 0.7 * first, (first, last)
+    # with the network's rate on, the network moves and the other latents still stay
+    a.train_slab(slab, shape, 1, 2, steps=5, batch=4096, lr=3e-3, mlp_lr=1e-3, seed=6)
+    th2 = a.get_params()[0]
+    assert not np.array_equal(th2[:n_mlp], th1[:n_mlp])
+    assert np.array_equal(lat_of(th2, 0, 6), lat_of(th0, 0, 6))
+    # decoding reflects the slab's latents only: bricks of layer 0 decode as before
+    ids = torch.arange(6, dtype=torch.int32, device="cuda")
+    out = torch.empty(6 * 17 ** 3, device="cuda")
+    b.set_params(*a.get_params())
+    with pytest.raises(vr.VRError):
+        b.train_slab(dev[32:].contiguous(), shape, 2, 4, steps=1, batch=16, lr=1e-3)   # layers beyond the cube
+    with pytest.raises(ValueError):
+        b.train_slab(_slab(dev, 0, 1), shape, 1, 2, steps=1, batch=16, lr=1e-3)   # wrong planes
+    b.decode_bricks(ids, out)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    a.close()
+    b.close()
