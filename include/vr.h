@@ -180,6 +180,15 @@ typedef struct {
 #define VR_OPT_PROVIDER_THREADS 10 /* host threads that call a brick provider (and copy a
                                 host cube into the brick store) at once; <= 0 (default):
                                 the machine's hardware threads. */
+#define VR_OPT_HOST_OUTPUT_ASYNC 11 /* 0 (default): vr_render into host memory returns with
+                                the image there.  1: a page-locked host buffer (cudaHostAlloc
+                                or cudaHostRegister) is filled by a copy enqueued on the
+                                call's stream after the frame's kernels, and the call returns
+                                without waiting, so that the host plans the next frame while
+                                this one renders; the image is there once the stream has
+                                reached that point (synchronise it or wait on an event
+                                recorded after the call).  Pageable host memory is then
+                                refused (VR_EINVAL). */
 #define VR_PRECISION_F32 0
 #define VR_PRECISION_F16 1
 #define VR_PRECISION_F8 2
@@ -297,8 +306,9 @@ int vr_set_option(vr_ctx* ctx, int32_t option, int64_t value);
  * (r, g, b, alpha), row 0 at the top, no background.  out_rgba may be device
  * memory (written asynchronously on `cuda_stream`, a cudaStream_t or NULL for
  * the legacy default stream) or host memory (the call then copies the image
- * back and synchronises the stream).  Stream-ordered: the call returns after
- * enqueueing work unless out_rgba is host memory.  Calls on different streams
+ * back and synchronises the stream, or only enqueues the copy with
+ * VR_OPT_HOST_OUTPUT_ASYNC).  Stream-ordered: the call returns after enqueueing
+ * work unless out_rgba is host memory and VR_OPT_HOST_OUTPUT_ASYNC is 0.  Calls on different streams
  * with one context must not overlap in time on the device.
  * Errors: VR_ESTATE (missing cube/brick/TF/camera), VR_EINVAL, VR_ENOMEM,
  * VR_ECUDA.

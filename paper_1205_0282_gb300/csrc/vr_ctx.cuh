@@ -340,6 +340,7 @@ struct vr_ctx {
     vr_block_provider prov_fn = nullptr;  // vr_load_cube_provider: bricks come from the provider
     void* prov_user = nullptr;
     int prov_threads = 0;              // VR_OPT_PROVIDER_THREADS
+    bool host_async = false;           // VR_OPT_HOST_OUTPUT_ASYNC
     // provider contexts: pinned staging for the blocks of one upload launch, the
     // buffers taken in turn (a buffer is refilled once its copies have finished)
     static constexpr int kStage = 3;

@@ -1030,6 +1030,10 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
             c->kernel = (int)value;
             return VR_OK;
         case VR_OPT_DEVICE_BUDGET: c->budget = value; return VR_OK;
+        case VR_OPT_HOST_OUTPUT_ASYNC:
+            if (value != 0 && value != 1) return fail(c, VR_EINVAL, "asynchronous host output must be 0 or 1");
+            c->host_async = value != 0;
+            return VR_OK;
         case VR_OPT_PROVIDER_THREADS: c->prov_threads = (int)std::max<int64_t>(0, std::min<int64_t>(value, 4096)); return VR_OK;
         case VR_OPT_OOC_MARCH:
             if (value < 0 || value > 2) return fail(c, VR_EINVAL, "out-of-core march must be 0, 1 or 2");
@@ -1277,11 +1281,15 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     VR_CUDA(c, cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream_ptr;
     cudaPointerAttributes attr;
-    bool out_on_device = false;
-    if (cudaPointerGetAttributes(&attr, out_rgba) == cudaSuccess)
+    bool out_on_device = false, out_pinned = false;
+    if (cudaPointerGetAttributes(&attr, out_rgba) == cudaSuccess) {
         out_on_device = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
-    else
+        out_pinned = attr.type == cudaMemoryTypeHost;
+    } else {
         cudaGetLastError();
+    }
+    if (c->host_async && !out_on_device && !out_pinned)
+        return fail(c, VR_EINVAL, "asynchronous host output needs page-locked host memory");
 
     Slot& s = c->slots[c->next_slot];
     c->next_slot = (c->next_slot + 1) % kSlots;
@@ -1499,7 +1507,7 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
     s.d2h_bytes = (int64_t)sizeof(vr::Stats) + (out_on_device ? 0 : (int64_t)(img_px * sizeof(float4)));
     if (!out_on_device) {
         VR_CUDA(c, cudaMemcpyAsync(out_rgba, s.d_img, img_px * sizeof(float4), cudaMemcpyDeviceToHost, st));
-        VR_CUDA(c, cudaStreamSynchronize(st));
+        if (!c->host_async) VR_CUDA(c, cudaStreamSynchronize(st));
     }
     return VR_OK;
 }

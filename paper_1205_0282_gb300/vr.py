@@ -37,6 +37,7 @@ VR_OPT_STEP_MODE = 7
 VR_OPT_TEX_SLAB_LAYERS = 8
 VR_OPT_OOC_MARCH = 9
 VR_OPT_PROVIDER_THREADS = 10
+VR_OPT_HOST_OUTPUT_ASYNC = 11
 VR_PRECISION_F32 = 0
 VR_PRECISION_F16 = 1
 VR_PRECISION_F8 = 2

@@ -519,14 +519,19 @@ def test_slab_fitting_and_training_equal_the_whole_cube(vr, floor):
 
 def test_slab_training_touches_only_its_latents(vr):
     """Training slab [1, 2): the other layers' latents stay bit for bit; with
-    mlp_lr = 0 the shared network stays too, and the slab's loss falls."""
+    mlp_lr = 0 the shared network stays too, and the slab's loss falls as its
+    latents (reset to noise) are fitted again to the trained decoder."""
     import torch
     dev, shape, brick, nb, (a, b) = _slab_case(vr)
     for bz0, bz1 in ((0, 1), (1, 2), (2, 3)):
         a.fit_stats_slab(_slab(dev, bz0, bz1), shape, bz0, bz1)
-    th0 = a.get_params()[0]
+    a.train_slab(dev, shape, 0, 3, steps=300, batch=8192, lr=3e-3, seed=2)     # decoder and latents
+    th, m, s = a.get_params()
     n_mlp = a.n_params - nb * 8 ** 3 * 16
     lat_of = lambda th, b0, b1: th[n_mlp + b0 * 8192: n_mlp + b1 * 8192]   # noqa: E731
+    lat_of(th, 6, 12)[:] = np.random.default_rng(8).normal(0, 0.1, 6 * 8192)
+    a.set_params(th, m, s)
+    th0 = a.get_params()[0]
     slab = _slab(dev, 1, 2)
     first = a.train_slab(slab, shape, 1, 2, steps=1, batch=8192, lr=3e-3, mlp_lr=0.0, seed=4)
     last = a.train_slab(slab, shape, 1, 2, steps=200, batch=8192, lr=3e-3, mlp_lr=0.0, seed=5)
@@ -548,7 +553,7 @@ def test_slab_training_touches_only_its_latents(vr):
     with pytest.raises(vr.VRError):
         b.train_slab(dev[32:].contiguous(), shape, 2, 4, steps=1, batch=16, lr=1e-3)   # layers beyond the cube
     with pytest.raises(ValueError):
-        b.train_slab(_slab(dev, 0, 1), shape, 1, 2, steps=1, batch=16, lr=1e-3)   # wrong planes
+        b.train_slab(_slab(dev, 0, 2), shape, 1, 2, steps=1, batch=16, lr=1e-3)   # wrong plane count
     b.decode_bricks(ids, out)
     torch.cuda.synchronize()
     assert torch.isfinite(out).all()

@@ -389,3 +389,34 @@ def test_dynamic_step_errors(vr, torch, tiny):
         r.render()
         with pytest.raises(vr.VRError, match="VR_EINVAL"):
             vr.Server(r, 128 << 20)
+
+
+def test_asynchronous_host_output():
+    """VR_OPT_HOST_OUTPUT_ASYNC: frames rendered into page-locked host buffers
+    without waiting (several in flight) hold the synchronous images once the
+    stream is synchronised; pageable memory is refused."""
+    import torch
+    from paper_1205_0282_gb300 import vr
+    cube = synth.tiny_cube()
+    tf = synth.tf_tiny()
+    cams = synth.tiny_views(width=120, height=90)
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(cube).cuda())
+        r.brick(32, 32, 32)
+        r.set_transfer_function(tf)
+        want = []
+        for cam in cams:
+            r.set_camera(cam)
+            want.append(r.render(np.zeros((90, 120, 4), np.float32)).copy())
+        r.set_option(vr.VR_OPT_HOST_OUTPUT_ASYNC, 1)
+        bufs = [torch.full((90, 120, 4), -1.0, pin_memory=True).numpy() for _ in cams]
+        for cam, b in zip(cams, bufs):
+            r.set_camera(cam)
+            r.render(b)
+        torch.cuda.synchronize()
+        for b, w in zip(bufs, want):
+            assert np.array_equal(b, w)
+        assert want[0][..., 3].max() > 0.1
+        with pytest.raises(vr.VRError) as e:
+            r.render(np.zeros((90, 120, 4), np.float32))
+        assert e.value.code == vr.VR_EINVAL
