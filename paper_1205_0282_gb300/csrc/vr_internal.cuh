@@ -52,7 +52,11 @@ struct FrameCam {
     const int32_t* tile_start;  // fragments of tile t: [tile_start[t], tile_start[t+1])
     float4* out;                // float4[height][width]
     int32_t tile_base;          // first composite block of this frame in the batch
-    int32_t pad;
+    int32_t tf_off;             // the frame's transfer function: entries [tf_off, tf_off + tf_n]
+    int32_t tf_n;               // of the batch's tables (control points, the last repeated)
+    float tf_v0, tf_inv_dv;     // uniform control points: v_i = v0 + i / inv_dv
+    float tau;                  // termination threshold
+    int32_t tf_uniform;         // 1: look the transfer function up by its uniform spacing
 };
 
 // Everything a frame's kernels need, passed by value.

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(256) composite_batch_kernel(const FrameParams 
     const int tx = t % cam.tiles_x, ty = t / cam.tiles_x;
     const int f0 = cam.tile_start[t], f1 = cam.tile_start[t + 1];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;  // 8 warps, one pixel group each
-    const float4 acc = fold_over_warp(p.frags, kTilePixels, g, f0, f1, p.tau);
+    const float4 acc = fold_over_warp(p.frags, kTilePixels, g, f0, f1, cam.tau);
     const int pix = g * 8 + (lane & 7);
     const int i = tx * kTile + pix % kTile, j = ty * kTile + pix / kTile;
     if (lane < 8 && i < cam.width && j < cam.height) cam.out[(int64_t)j * cam.width + i] = acc;

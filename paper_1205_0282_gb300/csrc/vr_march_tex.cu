@@ -58,21 +58,36 @@ __host__ __device__ constexpr int tex_blocks_per_sm(int prec) {
 // Transfer-function colour at v from the control points rgba[] and their forward
 // differences drgba[k] = rgba[k + 1] - rgba[k] (formed in FP32 once per CTA, so
 // rgba[k] + w drgba[k] rounds exactly like the per-sample lerp of two points).
+// The transfer function and termination an item composites with: the launch's
+// (single frames), or its frame's own (a serving batch that mixes transfer
+// functions and termination thresholds; its control points sit at offset tf_off
+// of the batch's shared-memory arrays).
+struct TfView {
+    float v0, inv_dv, tau;
+    int n;
+};
+__device__ __forceinline__ TfView tf_view(const FrameParams& p, const FrameParams&) {
+    return TfView{p.tf_v0, p.tf_inv_dv, p.tau, p.tf_n};
+}
+__device__ __forceinline__ TfView tf_view(const FrameParams&, const FrameCam& c) {
+    return TfView{c.tf_v0, c.tf_inv_dv, c.tau, c.tf_n};
+}
+
 template <bool UNIFORM>
-__device__ __forceinline__ float4 tf_lerp(const FrameParams& p, const float4* __restrict__ rgba,
+__device__ __forceinline__ float4 tf_lerp(const TfView& p, const float4* __restrict__ rgba,
                                           const float4* __restrict__ drgba, const float* __restrict__ vals,
                                           float v) {
     int seg;
     float w;
     if (UNIFORM) {
-        // drgba[tf_n - 1] = 0 (rgba[tf_n] repeats the last point): x = tf_n - 1 needs
-        // no segment clamp
-        float x = (v - p.tf_v0) * p.tf_inv_dv;
-        x = fminf(fmaxf(x, 0.0f), (float)(p.tf_n - 1));
+        // drgba[n - 1] = 0 (rgba[n] repeats the last point): x = n - 1 needs no
+        // segment clamp
+        float x = (v - p.v0) * p.inv_dv;
+        x = fminf(fmaxf(x, 0.0f), (float)(p.n - 1));
         seg = __float2int_rz(x);
         w = x - (float)seg;
     } else {
-        int lo = 0, hi = p.tf_n - 1;
+        int lo = 0, hi = p.n - 1;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (v >= vals[mid]) lo = mid;
@@ -217,7 +232,8 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
             }
         }
     }
-    const float tau = p.tau;
+    const TfView tfv = tf_view(p, cam);
+    const float tau = tfv.tau;
     // brick origin along U, V plus one: gather coordinate of texel (u, v) is (u + 1, v + 1)
     const float ou = (float)(O[U] + slot_u + 1), ov = (float)(O[V] + slot_v + 1);
     // Sample k's eight corners and weights, gathered D samples ahead of their use
@@ -329,7 +345,7 @@ __device__ __forceinline__ void march_item(const FrameParams& p, const Cam& cam,
             fi += 1.0f;
             return;
         }
-        const float4 col = tf_lerp<UNIFORM>(p, s_rgba, s_drgba, s_v, val);
+        const float4 col = tf_lerp<UNIFORM>(tfv, s_rgba, s_drgba, s_v, val);
         const float alpha = DYN ? opacity_correct_dt(col.w, dt_ray) : opacity_correct(p, col.w);
         const bool owed = fi < fn;
         const float w = owed ? (1.0f - acc.w) * alpha : 0.0f;
@@ -414,8 +430,10 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
 }
 
 // Batch of frames (the serving loop): the same persistent march, each item's
-// camera read from the frame it belongs to (item.sweep >> 3).
-template <bool UNIFORM, int PREC>
+// camera, transfer function and termination threshold read from the frame it
+// belongs to (item.sweep >> 3).  The batch's transfer functions are concatenated
+// (tf_n + 1 entries each, the last point repeated), p.tf_n = their total - 1.
+template <int PREC>
 __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_tex_batch_kernel(const FrameParams p) {
     float4 *s_rgba, *s_drgba;
     float* s_v;
@@ -430,10 +448,24 @@ __global__ void __launch_bounds__(kTilePixels, tex_blocks_per_sm(PREC)) march_te
         const Item item = p.items[w >> 1];
         const FrameCam& cam = p.cams[item.sweep >> 3];
         const int t = (w & 1) * 32 + lane;
-        switch (item.sweep & 3) {
-            case 0: march_item<0, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
-            case 1: march_item<1, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
-            default: march_item<2, UNIFORM, PREC, false>(p, cam, item, s_rgba, s_drgba, s_v, t); break;
+        // the frame's transfer function within the batch's concatenated tables
+        const float4* rgba = s_rgba + cam.tf_off;
+        const float4* drgba = s_drgba + cam.tf_off;
+        const float* vals = s_v + cam.tf_off;
+        // the lookup each frame's own vr_render would use (uniform spacing or
+        // search), so that its image is the same alone and in the batch
+        if (cam.tf_uniform) {
+            switch (item.sweep & 3) {
+                case 0: march_item<0, true, PREC, false>(p, cam, item, rgba, drgba, vals, t); break;
+                case 1: march_item<1, true, PREC, false>(p, cam, item, rgba, drgba, vals, t); break;
+                default: march_item<2, true, PREC, false>(p, cam, item, rgba, drgba, vals, t); break;
+            }
+        } else {
+            switch (item.sweep & 3) {
+                case 0: march_item<0, false, PREC, false>(p, cam, item, rgba, drgba, vals, t); break;
+                case 1: march_item<1, false, PREC, false>(p, cam, item, rgba, drgba, vals, t); break;
+                default: march_item<2, false, PREC, false>(p, cam, item, rgba, drgba, vals, t); break;
+            }
         }
     }
 }
@@ -640,14 +672,11 @@ cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
     };
     using namespace texm;
     if (p.precision == kPrecF8) {
-        if (p.tf_uniform) go(march_tex_batch_kernel<true, kPrecF8>);
-        else go(march_tex_batch_kernel<false, kPrecF8>);
+        go(march_tex_batch_kernel<kPrecF8>);
     } else if (p.precision == kPrecF16) {
-        if (p.tf_uniform) go(march_tex_batch_kernel<true, kPrecF16>);
-        else go(march_tex_batch_kernel<false, kPrecF16>);
+        go(march_tex_batch_kernel<kPrecF16>);
     } else {
-        if (p.tf_uniform) go(march_tex_batch_kernel<true, kPrecF32>);
-        else go(march_tex_batch_kernel<false, kPrecF32>);
+        go(march_tex_batch_kernel<kPrecF32>);
     }
     return cudaGetLastError();
 }

@@ -8,7 +8,9 @@
 // uploads the next batch while the GPU renders the current one.  A completion
 // thread waits for each batch's event and stamps its requests done.
 #include <condition_variable>
+#include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -25,6 +27,23 @@ double now_ms() {
 
 enum ReqState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
 
+// A transfer function as the march reads it: control points with the last one
+// repeated, their values (the last repeated too), and the uniform spacing if any.
+struct TfTable {
+    std::vector<float4> rgba;
+    std::vector<float> v;
+    int32_t n = 0;
+    bool uniform = false;
+    float v0 = 0.0f, inv_dv = 0.0f;
+    bool same(const TfTable& o) const {
+        return n == o.n && std::memcmp(rgba.data(), o.rgba.data(), rgba.size() * sizeof(float4)) == 0 &&
+               std::memcmp(v.data(), o.v.data(), v.size() * sizeof(float)) == 0;
+    }
+};
+
+// Entries of all the transfer functions of one batch (shared memory of the march)
+constexpr int32_t kBatchTfEntries = 512;
+
 struct Req {
     int64_t id = 0;
     vr_camera cam{};
@@ -39,12 +58,17 @@ struct Req {
     std::vector<df> q;
     double f[3], r[3], u[3];
     int32_t tiles_x = 0, tiles_y = 0;
+    std::shared_ptr<const TfTable> tft;  // the transfer function it was planned with
+    int32_t tf_slot = -1;                // its table in the batch
 };
 
 struct Batch {
     int half = -1;
     std::vector<Req*> reqs;
     int64_t items = 0;
+    std::vector<const TfTable*> tfs;  // distinct transfer functions, in order of first use
+    std::vector<int32_t> tf_off;      // their first entries in the concatenated tables
+    int32_t tf_entries = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -76,10 +100,23 @@ struct vr_server {
 
     Slot plan;  // planner scratch (host arrays)
     std::vector<double> tf_now;
+    std::shared_ptr<const TfTable> tf_table;  // tf_now as the march reads it
     vr_server_stats st{};
 };
 
 namespace {
+
+std::shared_ptr<const TfTable> table_of(const vr_ctx* c) {
+    auto t = std::make_shared<TfTable>();
+    t->n = (int32_t)c->tf_v.size();
+    t->rgba = c->tf_rgba;
+    t->v = c->tf_v;
+    t->v.push_back(c->tf_v.back());
+    t->uniform = c->tf_uniform != 0;
+    t->v0 = c->tf_v0;
+    t->inv_dv = c->tf_inv_dv;
+    return t;
+}
 
 // Device bytes a planned frame takes in the arena.
 size_t frame_bytes(const vr_camera& cam, int64_t n_items, int64_t n_tiles) {
@@ -103,21 +140,25 @@ int run_batch(vr_server* S, Batch& b) {
     const int h = b.half;
     char* stage = S->h_stage[h];
     char* arena = S->d_arena[h];
-    // layout: [TF rgba][TF v][cams][all items][per frame: q tables, tile_start][frags]
-    const int32_t tf_n = (int32_t)(c->tf.size() / 5);
+    // layout: [TF rgba][TF v][cams][all items][per frame: q tables, tile_start][frags];
+    // the batch's transfer functions concatenated (n + 1 entries each)
     int64_t n_items = 0;
     for (Req* r : b.reqs) n_items += (int64_t)r->items.size();
     size_t off = 0;
     const size_t o_rgba = off;
-    off += align256(c->tf_rgba.size() * sizeof(float4));
+    off += align256((size_t)b.tf_entries * sizeof(float4));
     const size_t o_v = off;
-    off += align256(c->tf_v.size() * sizeof(float));
+    off += align256((size_t)b.tf_entries * sizeof(float));
     const size_t o_cams = off;
     off += align256(b.reqs.size() * sizeof(vr::FrameCam));
     const size_t o_items = off;
     off += align256((size_t)n_items * sizeof(vr::Item));
-    std::memcpy(stage + o_rgba, c->tf_rgba.data(), c->tf_rgba.size() * sizeof(float4));
-    std::memcpy(stage + o_v, c->tf_v.data(), c->tf_v.size() * sizeof(float));
+    for (size_t k = 0; k < b.tfs.size(); ++k) {
+        const TfTable* t = b.tfs[k];
+        std::memcpy(stage + o_rgba + (size_t)b.tf_off[k] * sizeof(float4), t->rgba.data(),
+                    t->rgba.size() * sizeof(float4));
+        std::memcpy(stage + o_v + (size_t)b.tf_off[k] * sizeof(float), t->v.data(), t->v.size() * sizeof(float));
+    }
     vr::FrameCam* cams = reinterpret_cast<vr::FrameCam*>(stage + o_cams);
     vr::Item* items = reinterpret_cast<vr::Item*>(stage + o_items);
     int64_t frag_base = 0, tile_base = 0;
@@ -154,6 +195,12 @@ int run_batch(vr_server* S, Batch& b) {
         fc.tile_start = reinterpret_cast<const int32_t*>(arena + o_tiles);
         fc.out = reinterpret_cast<float4*>(r->out);
         fc.tile_base = (int32_t)tile_base;
+        fc.tf_off = b.tf_off[r->tf_slot];
+        fc.tf_n = r->tft->n;
+        fc.tf_v0 = r->tft->v0;
+        fc.tf_inv_dv = r->tft->inv_dv;
+        fc.tau = (float)r->cam.term_alpha;
+        fc.tf_uniform = r->tft->uniform ? 1 : 0;
         frag_base += (int64_t)r->items.size();
         tile_base += n_tiles;
     }
@@ -168,7 +215,7 @@ int run_batch(vr_server* S, Batch& b) {
     p.tile = vr::kTile;
     p.tf_rgba = reinterpret_cast<const float4*>(arena + o_rgba);
     p.tf_v = reinterpret_cast<const float*>(arena + o_v);
-    p.tf_n = tf_n;
+    p.tf_n = b.tf_entries - 1;  // the shared-memory copy takes every entry
     p.cams = reinterpret_cast<const vr::FrameCam*>(arena + o_cams);
     p.n_cams = (int32_t)b.reqs.size();
     p.items = reinterpret_cast<const vr::Item*>(arena + o_items);
@@ -210,8 +257,21 @@ int plan_request(vr_server* S, Req* r, size_t& bytes) {
     return VR_OK;
 }
 
-bool same_group(const Req* a, const Req* b) {
-    return a->cam.step == b->cam.step && a->cam.term_alpha == b->cam.term_alpha;
+// Frames of one batch share the step (its opacity-correction fit is per launch);
+// transfer functions and termination thresholds may differ.
+bool same_group(const Req* a, const Req* b) { return a->cam.step == b->cam.step; }
+
+// The request's table in the batch (added if no equal one is there).
+void use_table(Batch& b, Req* r) {
+    for (size_t k = 0; k < b.tfs.size(); ++k)
+        if (b.tfs[k]->same(*r->tft)) {
+            r->tf_slot = (int32_t)k;
+            return;
+        }
+    r->tf_slot = (int32_t)b.tfs.size();
+    b.tfs.push_back(r->tft.get());
+    b.tf_off.push_back(b.tf_entries);
+    b.tf_entries += (int32_t)r->tft->rgba.size();
 }
 
 void worker_main(vr_server* S) {
@@ -229,9 +289,10 @@ void worker_main(vr_server* S) {
             b.half = S->half_busy[0] ? 1 : 0;
             S->half_busy[b.half] = true;
         }
-        // admit in arrival order while the frames share the transfer function, step
-        // and termination, number at most max_batch and fit half the arena
-        size_t bytes = 4096 + 2 * (size_t)vr::kMaxTfPoints * sizeof(float4);
+        // admit in arrival order while the frames share the step, number at most
+        // max_batch, their transfer functions fit the batch's tables and their
+        // plans fit half the arena
+        size_t bytes = 4096 + align256((size_t)kBatchTfEntries * sizeof(float4)) + align256((size_t)kBatchTfEntries * sizeof(float));
         for (;;) {
             Req* r = nullptr;
             {
@@ -239,15 +300,21 @@ void worker_main(vr_server* S) {
                 if (S->queue.empty() || (int32_t)b.reqs.size() >= S->max_batch) break;
                 r = S->queue.front();
                 const bool tf_change = !r->tf.empty() && r->tf != S->tf_now;
-                if (!b.reqs.empty() && (tf_change || !same_group(r, b.reqs[0]))) break;
+                const int32_t tf_new = tf_change ? (int32_t)(r->tf.size() / 5) + 1 : 0;
+                if (!b.reqs.empty() && (!same_group(r, b.reqs[0]) || b.tf_entries + tf_new > kBatchTfEntries))
+                    break;
                 S->queue.pop_front();
                 r->state = kRunning;
             }
             int rc = VR_OK;
             if (!r->tf.empty() && r->tf != S->tf_now) {
                 rc = vr_set_transfer_function(c, r->tf.data(), (int32_t)(r->tf.size() / 5));
-                if (!rc) S->tf_now = r->tf;
+                if (!rc) {
+                    S->tf_now = r->tf;
+                    S->tf_table = table_of(c);
+                }
             }
+            r->tft = S->tf_table;
             size_t need = 0;
             if (!rc) rc = plan_request(S, r, need);
             std::lock_guard<std::mutex> lk(S->mu);
@@ -265,6 +332,7 @@ void worker_main(vr_server* S) {
                 break;
             }
             bytes += need;
+            use_table(b, r);
             b.reqs.push_back(r);
         }
         const int rc = b.reqs.empty() ? VR_OK : run_batch(S, b);
@@ -346,6 +414,7 @@ int vr_server_create(vr_ctx* c, int64_t arena_bytes, int32_t max_batch, vr_serve
     S->max_batch = max_batch;
     S->half_bytes = (size_t)arena_bytes / 2 / 256 * 256;
     S->tf_now = c->tf;
+    S->tf_table = table_of(c);
     bool ok = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess;
     for (int h = 0; h < 2 && ok; ++h) {
         ok = cudaMalloc((void**)&S->d_arena[h], S->half_bytes) == cudaSuccess &&

@@ -119,6 +119,46 @@ def test_admission_by_memory(vr, torch):
     assert np.array_equal(o1.cpu().numpy(), o3.cpu().numpy())
 
 
+def test_transfer_functions_and_thresholds_mix_in_a_batch(vr, torch):
+    """Every request switching transfer function (uniform and non-uniform control
+    points) and termination threshold: the frames still share batches, and each
+    image is vr_render's for its own transfer function and threshold, bit for
+    bit."""
+    shape, brick = (64, 64, 64), (16, 16, 16)
+    cube = synth.tiny_cube()
+    tfs = [synth.tf_tiny(),
+           synth.make_tf([0.0, 0.0, 0.01, 0.04, 0.1, 0.2, 0.3, 0.5], lo=-3.0, hi=10.0),
+           np.array([[-3.0, 0.0, 0.0, 1.0, 0.0], [0.8, 0.1, 0.2, 0.9, 0.0], [1.1, 0.2, 0.6, 0.8, 0.03],
+                     [2.9, 0.9, 0.9, 0.9, 0.1], [4.0, 1.0, 0.5, 0.1, 0.3], [9.5, 1.0, 0.0, 0.0, 0.8]])]
+    rng = np.random.default_rng(9)
+    reqs = []
+    for k in range(18):
+        cam = synth.pose(shape, rng.uniform(0, 2 * np.pi), rng.uniform(-1.0, 1.0), *RESOLUTIONS[k % 5],
+                         term_alpha=(0.99, 0.9, 0.6)[k % 3])
+        reqs.append((cam, tfs[(k // 2) % 3]))
+    alone = []
+    with _renderer(vr, torch, cube, tfs[0], reqs[0][0], brick) as r:
+        for cam, tf in reqs:
+            r.set_transfer_function(tf)
+            r.set_camera(cam)
+            alone.append(r.render().cpu().numpy())
+    r = _renderer(vr, torch, cube, tfs[0], reqs[0][0], brick)
+    outs = [torch.empty((c["height"], c["width"], 4), dtype=torch.float32, device="cuda") for c, _ in reqs]
+    with vr.Server(r, 256 << 20, max_batch=8) as srv:
+        tickets = [srv.submit(cam, out, tf) for (cam, tf), out in zip(reqs, outs)]
+        for t in tickets:
+            srv.wait(t, 60.0)
+        st = srv.stats()
+    r.close()
+    for k, (a, o) in enumerate(zip(alone, outs)):
+        assert np.array_equal(a, o.cpu().numpy()), k
+    assert st["completed"] == len(reqs)
+    # thresholds differ between any two consecutive requests (and transfer
+    # functions every second one): batches of more than one frame mix them
+    assert st["batches"] < len(reqs)
+    assert len({float(a[..., 3].max()) for a in alone}) > 3
+
+
 def test_requests_of_different_steps_are_not_batched_together(vr, torch):
     shape, brick = (64, 64, 64), (16, 16, 16)
     cube, tf = synth.tiny_cube(), synth.tf_tiny()
