@@ -69,6 +69,9 @@ def parse():
                     help="out-of-core: the cube stays in host memory, bricks stream into a device cache")
     ap.add_argument("--budget-gib", type=float, default=0.0,
                     help="device brick-cache budget for --ooc in GiB (0: every brick)")
+    ap.add_argument("--ooc-march", choices=["auto", "direct", "tex", "texz"], default="auto",
+                    help="out-of-core and learned marches: direct on the blocks, texture march on three "
+                         "layered copies of the slots, or on one copy along z (VR_OPT_OOC_MARCH)")
     ap.add_argument("--serve", action="store_true",
                     help="serving loop: Poisson arrivals of camera/TF/resolution requests, p50/p99 latency")
     ap.add_argument("--rate", type=float, default=200.0, help="--serve: mean arrivals per second")
@@ -408,6 +411,7 @@ def run_ours(args):
     t_load = time.perf_counter()
     if args.ooc:
         r.load_cube_host(cube)
+        r.set_option(vrmod.VR_OPT_OOC_MARCH, OOC_MARCH[args.ooc_march])
         if args.budget_gib > 0:
             r.set_option(vrmod.VR_OPT_DEVICE_BUDGET, int(args.budget_gib * 2 ** 30))
     else:
@@ -736,6 +740,7 @@ def run_learned(args):
     def render_learned(budget_gib, steps):
         r = vrm.VolumeRenderer(0)
         r.load_cube_codec(codec, shape)
+        r.set_option(vrm.VR_OPT_OOC_MARCH, OOC_MARCH[args.ooc_march])
         if budget_gib > 0:
             r.set_option(vrm.VR_OPT_DEVICE_BUDGET, int(budget_gib * 2 ** 30))
         if args.fallback_bound is not None:
@@ -806,6 +811,9 @@ def run_learned(args):
             "gpu_launches": st["launches"], "clocks": clocks.summary(), "cpu_baseline": None, "e2e": None}
     line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     print(json.dumps(line), flush=True)
+
+
+OOC_MARCH = {"direct": 0, "tex": 1, "auto": 2, "texz": 3}
 
 
 def xl_slabs(nbz: int, layers: int):
@@ -938,6 +946,7 @@ def run_learned_xl(args):
                     r.load_cube_codec(codec, shape)
                     r.set_codec_fallback_provider(src, bound, floor)
                 r.set_option(vrm.VR_OPT_DEVICE_BUDGET, int(budget * 2 ** 30))
+                r.set_option(vrm.VR_OPT_OOC_MARCH, OOC_MARCH[args.ooc_march])
                 t = time.perf_counter()
                 r.brick(*brick)
                 setup_s = time.perf_counter() - t
@@ -983,6 +992,7 @@ def run_learned_xl(args):
                        "train": {"decoder_slabs": args.xl_decoder_slabs, "decoder_steps_per_slab": args.train_steps,
                                  "latent_steps_per_slab": args.xl_slab_steps, "slab_layers": args.xl_slab_layers,
                                  "batch": args.train_batch, "lr": args.train_lr, "floor": floor},
+                       "ooc_march": args.ooc_march,
                        "timing": "wall clock per frame with a device synchronise on both sides (host generation "
                                  "and uploads included); the first frame after vr_brick fills the cache (cold)"},
             "fps": L["fps"],

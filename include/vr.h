@@ -173,10 +173,14 @@ typedef struct {
                                 then takes four times its block's bytes of
                                 VR_OPT_DEVICE_BUDGET (block plus copies).  If the device's
                                 layered-texture limits cannot tile the slots, the direct
-                                march is used.  0: the direct march on the blocks.  2
-                                (default): 1 when every brick fits the budget with its
-                                copies, else 0 (a streaming cache keeps four times the
-                                slots).  Takes effect at the next vr_brick. */
+                                march is used.  3: the same march on one layered copy,
+                                layers along z (every ray sweeps along z, about 17% slower
+                                than with the ray's dominant axis), each slot taking twice
+                                its block's bytes.  0: the direct march on the blocks.  2
+                                (default): 1 when every brick fits the budget with three
+                                copies, else 3 when every brick fits it with one, else 0
+                                (a streaming cache keeps up to four times the slots).
+                                Takes effect at the next vr_brick. */
 #define VR_OPT_PROVIDER_THREADS 10 /* host threads that call a brick provider (and copy a
                                 host cube into the brick store) at once; <= 0 (default):
                                 the machine's hardware threads. */

@@ -364,8 +364,10 @@ struct vr_ctx {
     int64_t slot_floats = 0;           // (Bx+1)(By+1)(Bz+1)
     int64_t budget = 0;                // VR_OPT_DEVICE_BUDGET (<= 0: every brick)
     float* d_pool = nullptr;           // device brick cache
-    int ooc_march = 2;                 // VR_OPT_OOC_MARCH: 2 auto, 1 texture march on layered slot copies, 0 direct
+    int ooc_march = 2;                 // VR_OPT_OOC_MARCH: 2 auto, 1 texture march on three layered slot
+                                       // copies, 3 on one (along z), 0 direct
     bool pool_tex_on = false;          // the current cache has its layered copies
+    bool pool_single = false;          // only the copy along z (VR_OPT_OOC_MARCH 3)
     cudaArray_t pool_arr[3] = {nullptr, nullptr, nullptr};  // by sweep axis
     cudaTextureObject_t pool_tex[3] = {0, 0, 0};
     cudaSurfaceObject_t pool_surf[3] = {0, 0, 0};

@@ -94,6 +94,7 @@ void free_pool_tex(vr_ctx* c) {
         c->pool_cols[a] = 0;
     }
     c->pool_tex_on = false;
+    c->pool_single = false;
 }
 
 bool use_pool_tex(vr_ctx* c) { return c->ooc && c->pool_tex_on; }
@@ -249,15 +250,17 @@ int codec_fallback_scan(vr_ctx* c) {
 
 // Layered copies of the cache's slots for the texture march: for sweep axis S a
 // layered array with layers along S (B_S + 1 of them) and the slots' (U, V)
-// faces tiled pool_cols[S] per row.  If the device's layered-texture limits do
-// not admit the tiling, the context keeps the direct march.
-int make_pool_tex(vr_ctx* c, int64_t slots) {
+// faces tiled pool_cols[S] per row; single: the copy along z only (every item
+// then sweeps along z).  If the device's layered-texture limits do not admit the
+// tiling, the context keeps the direct march.
+int make_pool_tex(vr_ctx* c, int64_t slots, bool single) {
     int maxw = 0, maxh = 0, maxl = 0;
     VR_CUDA(c, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, c->device));
     VR_CUDA(c, cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, c->device));
     VR_CUDA(c, cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, c->device));
     int64_t cols[3], rows[3];
-    for (int S = 0; S < 3; ++S) {
+    const int S0 = single ? 2 : 0;
+    for (int S = S0; S < 3; ++S) {
         const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
         cols[S] = std::min<int64_t>(slots, maxw / (c->B[U] + 1));
         if (cols[S] < 1) return VR_OK;
@@ -265,7 +268,7 @@ int make_pool_tex(vr_ctx* c, int64_t slots) {
         if (rows[S] * (c->B[V] + 1) > maxh || c->B[S] + 1 > maxl) return VR_OK;
     }
     cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
-    for (int S = 0; S < 3; ++S) {
+    for (int S = S0; S < 3; ++S) {
         const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
         if (cudaMalloc3DArray(&c->pool_arr[S], &ch,
                               make_cudaExtent((size_t)(cols[S] * (c->B[U] + 1)), (size_t)(rows[S] * (c->B[V] + 1)),
@@ -294,6 +297,7 @@ int make_pool_tex(vr_ctx* c, int64_t slots) {
         c->pool_cols[S] = (int32_t)cols[S];
     }
     c->pool_tex_on = true;
+    c->pool_single = single;
     return VR_OK;
 }
 
@@ -352,11 +356,13 @@ int build_ooc_store(vr_ctx* c) {
         vr::read_blocks(brick_source(c), c->n, c->B, c->nb, nullptr, c->n_bricks, c->h_store, c->slot_floats,
                         c->h_minmax.data(), nullptr);
     }
-    // the texture march keeps each slot four times: its block and three layered
-    // copies; automatically chosen when every brick fits the budget that way
-    const bool tex_march = c->ooc_march == 1 ||
-                           (c->ooc_march == 2 && (c->budget <= 0 || c->budget / ((int64_t)slot_bytes * 4) >= c->n_bricks));
-    const int copies = tex_march ? 4 : 1;
+    // the texture march keeps each slot four times (its block and three layered
+    // copies) or twice (its block and the copy along z); automatically chosen, in
+    // that order, when every brick fits the budget that way
+    auto fits = [&](int64_t k) { return c->budget <= 0 || c->budget / ((int64_t)slot_bytes * k) >= c->n_bricks; };
+    const bool single = c->ooc_march == 3 || (c->ooc_march == 2 && !fits(4) && fits(2));
+    const bool tex_march = single || c->ooc_march == 1 || (c->ooc_march == 2 && fits(4));
+    const int copies = single ? 2 : (tex_march ? 4 : 1);
     int64_t slots = c->n_bricks;
     if (c->budget > 0) slots = std::min<int64_t>(slots, c->budget / ((int64_t)slot_bytes * copies));
     if (slots < 2) return fail(c, VR_EINVAL, "VR_OPT_DEVICE_BUDGET holds fewer than 2 bricks");
@@ -366,7 +372,7 @@ int build_ooc_store(vr_ctx* c) {
         return fail(c, VR_ENOMEM, "cannot allocate the device brick cache");
     }
     if (tex_march) {
-        int rc = make_pool_tex(c, slots);
+        int rc = make_pool_tex(c, slots, single);
         if (rc) return rc;
     }
     c->res.slot_of_brick.assign(c->n_bricks, -1);
@@ -420,6 +426,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
         const double* f = c->basis.f;
         const double* r = c->basis.r;
         const double* u = c->basis.u;
+        const bool pool_z = use_pool_tex(c) && c->pool_single;
         for (int ty = 0; ty < tiles_y; ++ty) {
             const double qy = c->plan_qy[ty];
             const double g0 = f[0] + qy * u[0], g1 = f[1] + qy * u[1], g2 = f[2] + qy * u[2];
@@ -430,6 +437,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
                 int ax = 0;
                 for (int a = 1; a < 3; ++a)
                     if (std::fabs(d[a]) > std::fabs(d[ax])) ax = a;
+                if (pool_z) ax = 2;  // the cache keeps only the copy along z
                 sweep[tx] = ax | (d[ax] < 0.0 ? 4 : 0);
             }
         }
@@ -1036,7 +1044,7 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
             return VR_OK;
         case VR_OPT_PROVIDER_THREADS: c->prov_threads = (int)std::max<int64_t>(0, std::min<int64_t>(value, 4096)); return VR_OK;
         case VR_OPT_OOC_MARCH:
-            if (value < 0 || value > 2) return fail(c, VR_EINVAL, "out-of-core march must be 0, 1 or 2");
+            if (value < 0 || value > 3) return fail(c, VR_EINVAL, "out-of-core march must be 0, 1, 2 or 3");
             c->ooc_march = (int)value;
             return VR_OK;
         case VR_OPT_TEX_SLAB_LAYERS:

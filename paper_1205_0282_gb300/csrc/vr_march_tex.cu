@@ -687,9 +687,10 @@ cudaError_t fill_pool_tex(const float* pool, int64_t slot_floats, const int32_t*
     if (count <= 0) return cudaSuccess;
     const int3 b1 = make_int3(B[0] + 1, B[1] + 1, B[2] + 1);
     const dim3 grid((unsigned)((b1.x + 127) / 128), (unsigned)b1.y, (unsigned)count);
-    texm::fill_pool_kernel<0><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[0], cols[0]);
-    texm::fill_pool_kernel<1><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[1], cols[1]);
-    texm::fill_pool_kernel<2><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[2], cols[2]);
+    // the copies the pool keeps (all three, or the one along z)
+    if (surf[0]) texm::fill_pool_kernel<0><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[0], cols[0]);
+    if (surf[1]) texm::fill_pool_kernel<1><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[1], cols[1]);
+    if (surf[2]) texm::fill_pool_kernel<2><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[2], cols[2]);
     return cudaGetLastError();
 }
 

@@ -42,12 +42,13 @@ def _incore(vr, torch, cube, tf, cam, brick, mode=0, march=1):
 
 def _ooc(vr, cube, tf, brick, budget_bricks=0, mode=0, march=1):
     """Out-of-core context whose cache holds budget_bricks slots (the texture march
-    keeps each slot's block and three layered copies: four blocks' bytes)."""
+    keeps each slot's block and three layered copies: four blocks' bytes; with one
+    copy along z, march 3, two)."""
     r = vr.VolumeRenderer(0)
     r.load_cube_host(cube)
     r.set_option(vr.VR_OPT_OOC_MARCH, march)
     if budget_bricks:
-        slot = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1) * 4 * (4 if march else 1)
+        slot = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1) * 4 * {0: 1, 1: 4, 3: 2}[march]
         r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_bricks * slot)
     r.brick(*brick)
     r.set_transfer_function(tf)
@@ -178,6 +179,40 @@ def test_out_of_core_texture_march_dynamic_step(vr, torch, shape, brick, camk, s
     assert np.array_equal(img, ref_gpu)
     ref, amb, _ = oracle.render(cube, tf, cam, brick=brick, amb_alpha=AMB_ALPHA, amb_steps=AMB_STEPS, step_mode=1)
     assert_parity(img.astype(np.float64), ref, amb)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("budget", [0, 20, 5])
+def test_out_of_core_single_copy_march(vr, budget, mode):
+    """VR_OPT_OOC_MARCH 3: the texture march on one layered copy of the slots,
+    layers along z.  The same samples as the three-copy march, gathered in
+    another plane: within FP32 rounding of its image (emission-absorption and
+    MIP), frame after frame with every brick resident or streamed, and oracle
+    parity."""
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    brick = (16, 16, 16)
+    for view in (0, 2):
+        cam = synth.tiny_views(width=96, height=80)[view]
+        with _ooc(vr, cube, tf, brick, budget, mode=mode, march=1) as r:
+            r.set_camera(cam)
+            want = r.render().cpu().numpy().astype(np.float64)
+        with _ooc(vr, cube, tf, brick, budget, mode=mode, march=3) as r:
+            r.set_camera(cam)
+            for k in range(3):
+                r.reset_stats()
+                img = r.render().cpu().numpy().astype(np.float64)
+                assert np.abs(img - want).max() <= 2e-6
+                st = r.stats()
+                assert st["device_errors"] == 0
+                assert st["bricks_uploaded"] + st["bricks_cached"] == st["bricks_rendered"]
+                if budget == 5 and k > 0:
+                    assert st["bricks_uploaded"] > 0       # streamed through the ring
+                if budget == 0 and k > 0:
+                    assert st["bricks_uploaded"] == 0      # every brick resident
+        if mode == 0:
+            ref, amb, _ = oracle_render(cube, tf, cam, brick)
+            assert_parity(img, ref, amb)
+        assert want.max() > 0.2     # not an empty frame
 
 
 def test_out_of_core_errors(vr, torch):
