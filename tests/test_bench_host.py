@@ -42,3 +42,22 @@ def test_timed_frames_span_the_orbit():
     assert sorted(bench.orbit_index(k, 120, 120) for k in range(120)) == list(range(120))
     assert [bench.orbit_index(k, 240, 120) for k in (0, 119, 120, 239)] == [0, 119, 0, 119]
     assert [bench.orbit_index(2 * k + 1, 10, 120) for k in range(5)] == [12, 36, 60, 84, 108]
+
+
+def test_xl_training_slabs_cover_every_brick_layer_once():
+    """The ~200 GiB cube's training slabs: consecutive layer ranges covering all
+    layers (the last one shorter), and the decoder slabs spread over them."""
+    for nbz, layers in ((50, 4), (50, 7), (3, 4), (1, 1)):
+        slabs = bench.xl_slabs(nbz, layers)
+        assert slabs[0][0] == 0 and slabs[-1][1] == nbz
+        assert all(b1 - b0 <= layers and b1 > b0 for b0, b1 in slabs)
+        assert all(a[1] == b[0] for a, b in zip(slabs, slabs[1:]))
+    slabs = bench.xl_slabs(50, 4)
+    picked = bench.spread(slabs, 3)
+    assert len(picked) == 3 and len(set(picked)) == 3 and all(p in slabs for p in picked)
+    assert picked[0][0] < 20 and picked[-1][0] > 30          # from both ends of the cube
+    assert bench.spread(slabs[:2], 3) == slabs[:2]
+
+
+def test_out_of_core_march_names():
+    assert bench.OOC_MARCH == {"direct": 0, "tex": 1, "auto": 2, "texz": 3}
