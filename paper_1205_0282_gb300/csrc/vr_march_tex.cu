@@ -616,7 +616,7 @@ cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s) {
     // L1/texture cache
     auto go = [&](auto kern) {
         const int blocks = texm::tex_blocks_per_sm(p.precision);
-        const int pct = (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2;
+        const int pct = std::min(100, (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2);
         static int carveout = -1;
         if (carveout != pct) {
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
@@ -662,7 +662,7 @@ cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
     const size_t smem = (size_t)(2 * p.tf_n + 1) * sizeof(float4) + (size_t)p.tf_n * sizeof(float);
     auto go = [&](auto kern) {
         const int blocks = texm::tex_blocks_per_sm(p.precision);
-        const int pct = (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2;
+        const int pct = std::min(100, (int)((blocks * (smem + 1024) * 100 + 233471) / 233472) + 2);
         static int carveout = -1;
         if (carveout != pct) {
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);

@@ -159,6 +159,40 @@ def test_transfer_functions_and_thresholds_mix_in_a_batch(vr, torch):
     assert len({float(a[..., 3].max()) for a in alone}) > 3
 
 
+def test_a_batch_with_many_transfer_functions(vr, torch):
+    """Twelve requests with twelve different 40-point transfer functions: the
+    batch tables hold up to 512 control points (12 x 41 here, a large shared-memory
+    table), and each image is still vr_render's."""
+    shape, brick = (64, 64, 64), (16, 16, 16)
+    cube = synth.tiny_cube()
+    rng = np.random.default_rng(12)
+    reqs = []
+    for k in range(12):
+        alpha = np.sort(rng.uniform(0.0, 0.3, 40))
+        alpha[:10] = 0.0
+        tf = synth.make_tf(alpha, lo=-3.0 + 0.1 * k, hi=10.0)
+        cam = synth.pose(shape, rng.uniform(0, 2 * np.pi), rng.uniform(-1.0, 1.0), 72, 56)
+        reqs.append((cam, tf))
+    alone = []
+    with _renderer(vr, torch, cube, reqs[0][1], reqs[0][0], brick) as r:
+        for cam, tf in reqs:
+            r.set_transfer_function(tf)
+            r.set_camera(cam)
+            alone.append(r.render().cpu().numpy())
+    r = _renderer(vr, torch, cube, reqs[0][1], reqs[0][0], brick)
+    outs = [torch.empty((56, 72, 4), dtype=torch.float32, device="cuda") for _ in reqs]
+    with vr.Server(r, 256 << 20, max_batch=16) as srv:
+        tickets = [srv.submit(cam, out, tf) for (cam, tf), out in zip(reqs, outs)]
+        for t in tickets:
+            srv.wait(t, 60.0)
+        st = srv.stats()
+    r.close()
+    assert st["completed"] == 12 and st["failed"] == 0
+    for k, (a, o) in enumerate(zip(alone, outs)):
+        assert np.array_equal(a, o.cpu().numpy()), k
+    assert max(a[..., 3].max() for a in alone) > 0.1
+
+
 def test_requests_of_different_steps_are_not_batched_together(vr, torch):
     shape, brick = (64, 64, 64), (16, 16, 16)
     cube, tf = synth.tiny_cube(), synth.tf_tiny()
