@@ -394,6 +394,11 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    local_world = int(os.environ.get("LOCAL_WORLD_SIZE", str(world)))
+    if local_world > 1:
+        # the replicas generate their cubes at once: share the host cores (the
+        # launcher's default of one thread per process would leave most idle)
+        os.environ["OMP_NUM_THREADS"] = str(max(1, (os.cpu_count() or 1) // local_world))
     dist = None
     if world > 1:
         import torch.distributed as dist
