@@ -449,8 +449,10 @@ typedef struct {
  * may use ctx meanwhile.  It allocates arena_bytes of device memory (>= 64 MiB)
  * in two halves, one per batch in flight, and pinned staging of the same size.
  * A worker thread admits queued requests in arrival order into a batch while
- * they share the transfer function, step and term_alpha, number at most
- * max_batch, and their work lists and fragments fit one half; it plans the next
+ * they share the step, number at most max_batch, their transfer functions fit
+ * the batch's tables (512 control points in all) and their work lists and
+ * fragments fit one half; frames of one batch may differ in transfer function
+ * and term_alpha, each rendered as vr_render renders it.  It plans the next
  * batch while the GPU renders the current one.  A completion thread marks
  * requests done when their batch's event fires.
  * Errors: VR_EINVAL, VR_ESTATE, VR_ENOMEM, VR_ECUDA.

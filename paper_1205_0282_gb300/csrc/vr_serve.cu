@@ -133,8 +133,9 @@ void finish(vr_server* S, Req* r, int state, int err) {
     else ++S->st.failed;
 }
 
-// Render one admitted batch (every frame planned, same transfer function, step
-// and termination) into arena half b.half.  Returns VR_OK or a CUDA error.
+// Render one admitted batch (every frame planned, one step; each frame with its
+// own transfer function and termination) into arena half b.half.  Returns VR_OK
+// or a CUDA error.
 int run_batch(vr_server* S, Batch& b) {
     vr_ctx* c = S->c;
     const int h = b.half;
