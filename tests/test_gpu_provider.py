@@ -204,3 +204,34 @@ def test_learned_fallback_from_a_provider(vr):
         assert np.array_equal(got_err, want_err) and got_n == want_n and 0 < got_n < 12
         assert np.array_equal(got, want)
     c.close()
+
+
+@pytest.mark.parametrize("march", [1, 3, 0])
+def test_provider_mip_and_dynamic_step(vr, source, cube, march):
+    """MIP with the dynamic step through a provider-backed cache (every march
+    of the out-of-core path): the host-cube context's image bit for bit, and the
+    oracle's."""
+    brick = (24, 16, 20)
+    tf = synth.tf_tiny()
+    cam = synth.pose(SHAPE, 0.7, 0.4, 90, 70, step=0.4)
+
+    def ctx(load):
+        r = vr.VolumeRenderer(0)
+        load(r)
+        r.set_option(vr.VR_OPT_OOC_MARCH, march)
+        r.set_option(vr.VR_OPT_MODE, 1)
+        r.set_option(vr.VR_OPT_STEP_MODE, 1)
+        r.brick(*brick)
+        r.set_transfer_function(tf)
+        r.set_camera(cam)
+        return r
+
+    with ctx(lambda r: r.load_cube_host(cube)) as r:
+        want = r.render().cpu().numpy()
+    with ctx(lambda r: r.load_cube_provider(source, SHAPE)) as r:
+        got = r.render().cpu().numpy()
+    assert np.array_equal(got, want) and got.max() > 0.2
+    ref, amb, _ = oracle.render(cube, tf, cam, brick=brick, mode="mip", amb_alpha=AMB_ALPHA, amb_steps=AMB_STEPS,
+                                step_mode=1)
+    assert_parity(got.astype(np.float64), ref, amb)
+

@@ -51,7 +51,7 @@ def _requests(shape, n, seed=4):
     return out, tfs
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_each_result_is_the_same_alone_and_in_the_mix(vr, torch, precision):
     shape, brick = (64, 64, 64), (16, 16, 16)
     cube = synth.tiny_cube()
