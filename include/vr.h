@@ -296,6 +296,26 @@ int vr_set_transfer_function(vr_ctx* ctx, const double* points, int32_t n);
  * Errors: VR_EINVAL (degenerate basis, bad sizes). */
 int vr_set_camera(vr_ctx* ctx, const vr_camera* cam);
 
+/*
+ * The camera from the viewer's OpenGL matrices (Section 2.3.2: the viewer sends
+ * its projection and transformation matrices and the rendering threads project
+ * with them).  view: the modelview matrix (world -> eye, a rotation and a
+ * translation), proj: a symmetric perspective projection, both 16 doubles in
+ * OpenGL's column-major order (element (row r, column c) at [4 c + r]).  The eye
+ * is -R^T t, the viewing direction minus the third row of R, up its second row;
+ * fovy = 2 atan(1 / proj[5]).  The aspect proj[5] / proj[0] must equal width /
+ * height (square pixels) within 1e-6, R must be orthonormal within 1e-6, and
+ * the projection must have no skew or off-centre terms (proj[4], proj[8],
+ * proj[9] zero, proj[11] = -1, proj[15] = 0).  width, height, step and
+ * term_alpha as in vr_camera.  vr_camera_from_matrices only fills *out (host
+ * code, no context); vr_set_camera_matrices then sets it as vr_set_camera does.
+ * Errors: VR_EINVAL.
+ */
+int vr_camera_from_matrices(const double view[16], const double proj[16], int32_t width, int32_t height,
+                            double step, double term_alpha, vr_camera* out);
+int vr_set_camera_matrices(vr_ctx* ctx, const double view[16], const double proj[16], int32_t width,
+                           int32_t height, double step, double term_alpha);
+
 /* Set an option (VR_OPT_*).  Errors: VR_EINVAL. */
 int vr_set_option(vr_ctx* ctx, int32_t option, int64_t value);
 

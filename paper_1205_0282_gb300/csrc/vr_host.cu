@@ -1022,6 +1022,56 @@ int vr_set_camera(vr_ctx* c, const vr_camera* cam) {
     return VR_OK;
 }
 
+int vr_camera_from_matrices(const double view[16], const double proj[16], int32_t width, int32_t height,
+                            double step, double term_alpha, vr_camera* out) {
+    if (!view || !proj || !out || width < 1 || height < 1) return VR_EINVAL;
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(view[k]) || !std::isfinite(proj[k])) return VR_EINVAL;
+    // rows of the rotation R (column-major: element (r, c) at [4c + r]) and t
+    double R[3][3], t[3];
+    for (int r = 0; r < 3; ++r) {
+        for (int cc = 0; cc < 3; ++cc) R[r][cc] = view[4 * cc + r];
+        t[r] = view[12 + r];
+    }
+    if (view[3] != 0.0 || view[7] != 0.0 || view[11] != 0.0 || view[15] != 1.0) return VR_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double dot = R[a][0] * R[b][0] + R[a][1] * R[b][1] + R[a][2] * R[b][2];
+            if (std::fabs(dot - (a == b ? 1.0 : 0.0)) > 1e-6) return VR_EINVAL;
+        }
+    // a symmetric perspective projection with square pixels
+    const double p0 = proj[0], p5 = proj[5];
+    if (!(p0 > 0.0) || !(p5 > 0.0) || proj[1] != 0.0 || proj[4] != 0.0 || proj[8] != 0.0 || proj[9] != 0.0 ||
+        proj[11] != -1.0 || proj[15] != 0.0 || proj[3] != 0.0 || proj[7] != 0.0 || proj[2] != 0.0 ||
+        proj[6] != 0.0)
+        return VR_EINVAL;
+    const double aspect = p5 / p0;
+    if (std::fabs(aspect - (double)width / height) > 1e-6 * ((double)width / height)) return VR_EINVAL;
+    vr_camera cam{};
+    for (int a = 0; a < 3; ++a) {
+        // eye = -R^T t; forward = -(third row), up = second row
+        cam.eye[a] = -(R[0][a] * t[0] + R[1][a] * t[1] + R[2][a] * t[2]);
+        cam.target[a] = cam.eye[a] - R[2][a];
+        cam.up[a] = R[1][a];
+    }
+    cam.fovy_deg = 2.0 * std::atan(1.0 / p5) * (180.0 / M_PI);
+    cam.width = width;
+    cam.height = height;
+    cam.step = step;
+    cam.term_alpha = term_alpha;
+    *out = cam;
+    return VR_OK;
+}
+
+int vr_set_camera_matrices(vr_ctx* c, const double view[16], const double proj[16], int32_t width, int32_t height,
+                           double step, double term_alpha) {
+    if (!c) return VR_EINVAL;
+    vr_camera cam;
+    if (vr_camera_from_matrices(view, proj, width, height, step, term_alpha, &cam))
+        return fail(c, VR_EINVAL, "the matrices are not a rigid view and a symmetric perspective with square pixels");
+    return vr_set_camera(c, &cam);
+}
+
 int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
     if (!c) return VR_EINVAL;
     switch (option) {

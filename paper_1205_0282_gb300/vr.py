@@ -75,7 +75,7 @@ class vr_stats(ctypes.Structure):
 
 # The exported symbols, in header order (tests check them against include/vr.h).
 EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_load_cube_provider", "vr_brick", "vr_set_transfer_function",
-           "vr_set_camera", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
+           "vr_set_camera", "vr_camera_from_matrices", "vr_set_camera_matrices", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
            "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_kd_partition", "vr_kd_order",
            "vr_set_region", "vr_region_rect", "vr_plan_region_rect", "vr_render_rect",
            "vr_composite_subimages", "vr_server_create", "vr_server_submit", "vr_server_wait",
@@ -111,6 +111,9 @@ def _load():
     lib.vr_brick.argtypes = [P, I32, I32, I32]
     lib.vr_set_transfer_function.argtypes = [P, P, I32]
     lib.vr_set_camera.argtypes = [P, ctypes.POINTER(vr_camera)]
+    D = ctypes.c_double
+    lib.vr_camera_from_matrices.argtypes = [P, P, I32, I32, D, D, ctypes.POINTER(vr_camera)]
+    lib.vr_set_camera_matrices.argtypes = [P, P, P, I32, I32, D, D]
     lib.vr_set_option.argtypes = [P, I32, I64]
     lib.vr_render.argtypes = [P, P, P]
     lib.vr_get_stats.argtypes = [P, ctypes.POINTER(vr_stats)]
@@ -306,6 +309,35 @@ def vr_set_transfer_function(ctx, points) -> None:
 def vr_set_camera(ctx, cam: dict) -> None:
     c = make_camera(cam)
     _check(ctx, _lib.vr_set_camera(ctx, ctypes.byref(c)))
+
+
+def _mat16(m):
+    """A 4x4 matrix (numpy, row r column c) as OpenGL's column-major 16 doubles."""
+    a = np.asarray(m, dtype=np.float64)
+    if a.shape == (4, 4):
+        a = a.T
+    return np.ascontiguousarray(a.reshape(16), dtype=np.float64)
+
+
+def vr_camera_from_matrices(view, proj, width: int, height: int, step: float = 0.5,
+                            term_alpha: float = 0.99) -> dict:
+    """The camera dict equivalent to an OpenGL modelview and projection matrix
+    (4x4 arrays, row r column c, or 16 column-major values)."""
+    v, p = _mat16(view), _mat16(proj)
+    cam = vr_camera()
+    rc = _lib.vr_camera_from_matrices(v.ctypes.data, p.ctypes.data, int(width), int(height), float(step),
+                                      float(term_alpha), ctypes.byref(cam))
+    if rc != VR_OK:
+        raise VRError(rc, "vr_camera_from_matrices")
+    return {"eye": tuple(cam.eye), "target": tuple(cam.target), "up": tuple(cam.up), "fovy_deg": cam.fovy_deg,
+            "width": cam.width, "height": cam.height, "step": cam.step, "term_alpha": cam.term_alpha}
+
+
+def vr_set_camera_matrices(ctx, view, proj, width: int, height: int, step: float = 0.5,
+                           term_alpha: float = 0.99) -> None:
+    v, p = _mat16(view), _mat16(proj)
+    _check(ctx, _lib.vr_set_camera_matrices(ctx, v.ctypes.data, p.ctypes.data, int(width), int(height),
+                                            float(step), float(term_alpha)))
 
 
 def vr_set_option(ctx, option: int, value: int) -> None:
@@ -791,6 +823,11 @@ class VolumeRenderer:
     def set_camera(self, cam):
         vr_set_camera(self.ctx, cam)
         self.camera = dict(cam)
+
+    def set_camera_matrices(self, view, proj, width, height, step=0.5, term_alpha=0.99):
+        """Camera from the viewer's OpenGL modelview and projection matrices."""
+        vr_set_camera_matrices(self.ctx, view, proj, width, height, step, term_alpha)
+        self.camera = vr_camera_from_matrices(view, proj, width, height, step, term_alpha)
 
     def set_option(self, option, value):
         vr_set_option(self.ctx, option, value)

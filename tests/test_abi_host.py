@@ -106,3 +106,77 @@ def test_rectangles_are_tight_enough(vrmod):
     rects = vrmod.vr_plan_brick_rects(cam, (64, 64, 64), (16, 16, 16))
     area = ((rects[:, 2] - rects[:, 0] + 1) * (rects[:, 3] - rects[:, 1] + 1)).mean()
     assert area < 0.1 * 256 * 256
+
+
+# ------------------------------------------------ the camera as OpenGL matrices
+
+def _look_at(eye, target, up):
+    """gluLookAt's modelview matrix (row r, column c)."""
+    eye, target, up = (np.asarray(v, np.float64) for v in (eye, target, up))
+    f = (target - eye) / np.linalg.norm(target - eye)
+    s = np.cross(f, up)
+    s /= np.linalg.norm(s)
+    u = np.cross(s, f)
+    m = np.eye(4)
+    m[0, :3], m[1, :3], m[2, :3] = s, u, -f
+    m[:3, 3] = -m[:3, :3] @ eye
+    return m
+
+
+def _perspective(fovy_deg, aspect, near=1.0, far=1e5):
+    """gluPerspective's projection matrix (row r, column c)."""
+    g = 1.0 / np.tan(np.radians(fovy_deg) / 2.0)
+    p = np.zeros((4, 4))
+    p[0, 0], p[1, 1] = g / aspect, g
+    p[2, 2], p[2, 3] = (far + near) / (near - far), 2.0 * far * near / (near - far)
+    p[3, 2] = -1.0
+    return p
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_camera_from_opengl_matrices(vrmod, k):
+    """The viewer's modelview and projection matrices give the camera they were
+    built from: the same eye, viewing direction, up and field of view, so the
+    same rays (the planner's rendering rectangles agree to the pixel)."""
+    shape, brick = (61, 47, 53), (16, 16, 16)
+    cam = synth.tiny_views(seed=7 + k, width=(160, 96, 200, 64)[k], height=(90, 96, 150, 120)[k])[0]
+    cam = dict(cam, eye=tuple(np.asarray(cam["eye"]) * (0.9 + 0.1 * k)))
+    view = _look_at(cam["eye"], cam["target"], cam["up"])
+    proj = _perspective(cam["fovy_deg"], cam["width"] / cam["height"])
+    got = vrmod.vr_camera_from_matrices(view, proj, cam["width"], cam["height"], cam["step"], cam["term_alpha"])
+    np.testing.assert_allclose(got["eye"], cam["eye"], rtol=1e-12, atol=1e-9)
+    f0 = np.subtract(cam["target"], cam["eye"])
+    f1 = np.subtract(got["target"], got["eye"])
+    np.testing.assert_allclose(f1 / np.linalg.norm(f1), f0 / np.linalg.norm(f0), atol=1e-12)
+    assert abs(got["fovy_deg"] - cam["fovy_deg"]) < 1e-9
+    assert np.dot(got["up"], f1) == pytest.approx(0.0, abs=1e-12)
+    assert np.dot(got["up"], cam["up"]) > 0.0
+    want = vrmod.vr_plan_brick_rects(cam, (61, 47, 53), brick)
+    assert np.array_equal(vrmod.vr_plan_brick_rects(got, shape, brick), want)
+    # the column-major form is accepted as 16 values too
+    got16 = vrmod.vr_camera_from_matrices(view.T.reshape(16), proj.T.reshape(16), cam["width"], cam["height"])
+    np.testing.assert_allclose(got16["eye"], got["eye"], rtol=0, atol=0)
+
+
+def test_camera_matrices_are_checked(vrmod):
+    view = _look_at((100.0, 40.0, -80.0), (30.0, 20.0, 25.0), (0.0, 1.0, 0.0))
+    proj = _perspective(35.0, 4.0 / 3.0)
+    vrmod.vr_camera_from_matrices(view, proj, 640, 480)
+    bad = []
+    v = view.copy()
+    v[0, :3] *= 1.01                      # not a rotation
+    bad.append((v, proj, 640, 480))
+    p = proj.copy()
+    p[0, 2] = 0.1                         # off-centre frustum
+    bad.append((view, p, 640, 480))
+    bad.append((view, proj, 640, 640))    # aspect differs from the image's
+    p = proj.copy()
+    p[3, 3] = 1.0                         # orthographic-like, not a perspective
+    bad.append((view, p, 640, 480))
+    v = view.copy()
+    v[3, 0] = 0.5                         # not affine
+    bad.append((v, proj, 640, 480))
+    for v, p, w, h in bad:
+        with pytest.raises(vrmod.VRError) as e:
+            vrmod.vr_camera_from_matrices(v, p, w, h)
+        assert e.value.code == vrmod.VR_EINVAL

@@ -420,3 +420,27 @@ def test_asynchronous_host_output():
         with pytest.raises(vr.VRError) as e:
             r.render(np.zeros((90, 120, 4), np.float32))
         assert e.value.code == vr.VR_EINVAL
+
+
+def test_camera_from_opengl_matrices_renders_the_same_image():
+    """vr_set_camera_matrices with the viewer's modelview and projection (the
+    paper's interface) renders the image of the equivalent look-at camera, and
+    the oracle's."""
+    import torch
+    from paper_1205_0282_gb300 import vr
+    from test_abi_host import _look_at, _perspective
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    cam = synth.tiny_views(width=120, height=90)[1]
+    view = _look_at(cam["eye"], cam["target"], cam["up"])
+    proj = _perspective(cam["fovy_deg"], 120 / 90)
+    with vr.VolumeRenderer(0) as r:
+        r.load_cube(torch.from_numpy(cube).cuda())
+        r.brick(32, 32, 32)
+        r.set_transfer_function(tf)
+        r.set_camera(cam)
+        want = r.render().cpu().numpy().astype(np.float64)
+        r.set_camera_matrices(view, proj, 120, 90, cam["step"], cam["term_alpha"])
+        got = r.render().cpu().numpy().astype(np.float64)
+    assert np.abs(got - want).max() <= 1e-6
+    ref, amb, _ = oracle_render(cube, tf, cam, (32, 32, 32))
+    assert_parity(got, ref, amb)
