@@ -629,7 +629,7 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{n_crops} centre crops of 64x64 pixels on successive orbit poses, "
                          f"{secs:.1f} s of FP64 CPU work"}
-        # the same crops judge the GPU image (per-pixel error, PSNR)
+        # the GPU image's error on the same crops (per-pixel error, PSNR)
         quality = image_quality(render_pose, crops)
 
     value = samples / (elapsed_ms * 1e-3)
