@@ -362,6 +362,16 @@ int vr_get_brick_minmax(vr_ctx* ctx, float* out, int64_t n_bricks);
 int vr_plan_brick_rects(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz,
                         int32_t bx, int32_t by, int32_t bz, int32_t* rects, int64_t n_bricks);
 
+/* Host-only, like vr_plan_brick_rects: the (brick, 8x8 tile) work items the
+ * planner emits for every brick (no empty-space skipping), as mask[brick *
+ * n_tiles + tile] = 1 (tiles row-major, ceil(width / 8) per row).  A brick's
+ * items are the tiles of its rendering rectangle that its silhouette reaches:
+ * with all eight box corners in front of the eye, the convex hull of their
+ * projections widened by one pixel; otherwise the whole rectangle.
+ * Errors: VR_EINVAL. */
+int vr_plan_brick_tiles(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz, int32_t bx, int32_t by,
+                        int32_t bz, uint8_t* mask, int64_t n_bricks, int64_t n_tiles);
+
 /* ---------------------------------------------------------------------------
  * Sort-last distribution over ranks (Sections 2.3.1, 2.3.3, 2.3.4).  Each rank
  * renders the bricks of its k-d leaf into a sub-image clipped to the leaf's

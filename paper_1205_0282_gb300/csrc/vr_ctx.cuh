@@ -240,15 +240,114 @@ inline void project_brick_grid(const vr_camera& cam, const Basis& b, const int64
 }
 
 // Rendering rectangle of brick idx from the grid projections (box_rect of its box).
-inline bool brick_rect_from_grid(const vr_camera& cam, const std::vector<CornerProj>& proj, const int64_t nb[3],
-                                 const int64_t idx[3], int32_t rect[4]) {
+inline void grid_corners(const std::vector<CornerProj>& proj, const int64_t nb[3], const int64_t idx[3],
+                         const CornerProj* q[8]) {
     const int64_t g0 = nb[0] + 1, g1 = nb[1] + 1;
-    const CornerProj* q[8];
     for (int k = 0; k < 8; ++k) {
         const int64_t gi = idx[0] + (k & 1), gj = idx[1] + ((k >> 1) & 1), gk = idx[2] + ((k >> 2) & 1);
         q[k] = &proj[(size_t)((gk * g1 + gj) * g0 + gi)];
     }
+}
+inline bool brick_rect_from_grid(const vr_camera& cam, const std::vector<CornerProj>& proj, const int64_t nb[3],
+                                 const int64_t idx[3], int32_t rect[4]) {
+    const CornerProj* q[8];
+    grid_corners(proj, nb, idx, q);
     return rect_from_corners(cam, q, rect);
+}
+
+// Tiles of T x T pixels that brick idx's silhouette reaches, as one span [tx0, tx1]
+// per tile row ty.  With all eight corners in front of the eye, the silhouette is
+// the convex hull of their projections; a tile is kept if a pixel centre of it lies
+// within one pixel of the hull (the rectangle's margin), so every pixel whose ray
+// crosses the brick keeps its tile.  Otherwise (a corner at or behind the eye
+// plane) every tile of the rendering rectangle is kept.  Spans are clipped to the
+// rectangle rect (the brick's rendering rectangle within the output window).
+struct Span {
+    int32_t ty, tx0, tx1;
+};
+inline void brick_spans(const CornerProj* const q[8], const int32_t rect[4], int T, std::vector<Span>& out) {
+    const int tx_lo = rect[0] / T, tx_hi = rect[2] / T, ty_lo = rect[1] / T, ty_hi = rect[3] / T;
+    bool front = true;
+    for (int k = 0; k < 8; ++k) front = front && q[k]->zc > 1e-9;
+    if (!front) {
+        for (int ty = ty_lo; ty <= ty_hi; ++ty) out.push_back(Span{ty, tx_lo, tx_hi});
+        return;
+    }
+    // convex hull (monotone chain) of the projected corners, counter-clockwise
+    double px[8], py[8];
+    int ord[8];
+    for (int k = 0; k < 8; ++k) {
+        px[k] = q[k]->pi;
+        py[k] = q[k]->pj;
+        ord[k] = k;
+    }
+    for (int i = 1; i < 8; ++i)  // insertion sort by (x, y)
+        for (int j = i; j > 0 && (px[ord[j]] < px[ord[j - 1]] ||
+                                  (px[ord[j]] == px[ord[j - 1]] && py[ord[j]] < py[ord[j - 1]]));
+             --j)
+            std::swap(ord[j], ord[j - 1]);
+    int hull[16], h = 0;
+    auto cross = [&](int o, int a, int b) {
+        return (px[a] - px[o]) * (py[b] - py[o]) - (py[a] - py[o]) * (px[b] - px[o]);
+    };
+    for (int i = 0; i < 8; ++i) {
+        while (h >= 2 && cross(hull[h - 2], hull[h - 1], ord[i]) <= 0.0) --h;
+        hull[h++] = ord[i];
+    }
+    for (int i = 6, lo = h + 1; i >= 0; --i) {
+        while (h >= lo && cross(hull[h - 2], hull[h - 1], ord[i]) <= 0.0) --h;
+        hull[h++] = ord[i];
+    }
+    const int nh = h - 1;  // the last point repeats the first
+    const double m = 1.0;  // margin in pixels
+    const double inv_t = 1.0 / T;  // exact for the power-of-two tiles; columns are integers < 2^24
+    // x-extent of the silhouette within each tile row's band of pixel-centre rows
+    // (widened by the margin): the extremes lie on its edges, so each edge updates
+    // the rows its y-range overlaps, clipped to each band
+    const int nrows = ty_hi - ty_lo + 1;
+    constexpr int kRows = 2048;  // image heights up to 16384 pixels in tiles of 8 or more
+    double xmn[kRows], xmx[kRows];
+    for (int k = 0; k < nrows; ++k) {
+        xmn[k] = 1e300;
+        xmx[k] = -1e300;
+    }
+    auto band_lo = [&](int ty) { return std::max((double)(ty * T), (double)rect[1]) - m; };
+    auto band_hi = [&](int ty) { return std::min((double)(ty * T + T - 1), (double)rect[3]) + m; };
+    auto add_segment = [&](double xa, double ya, double xb, double yb) {
+        if (ya > yb) {
+            std::swap(xa, xb);
+            std::swap(ya, yb);
+        }
+        const int r0 = std::max(ty_lo, (int)std::floor((ya - m - (T - 1)) / T));
+        const int r1 = std::min(ty_hi, (int)std::floor((yb + m) / T));
+        const double slope = yb > ya ? (xb - xa) / (yb - ya) : 0.0;
+        for (int ty = r0; ty <= r1; ++ty) {
+            const double lo = std::max(ya, band_lo(ty)), hi = std::min(yb, band_hi(ty));
+            if (lo > hi) continue;
+            double x0 = xa, x1 = xb;
+            if (yb > ya) {
+                x0 = xa + (lo - ya) * slope;
+                x1 = xa + (hi - ya) * slope;
+            }
+            const int k = ty - ty_lo;
+            xmn[k] = std::min(xmn[k], std::min(x0, x1));
+            xmx[k] = std::max(xmx[k], std::max(x0, x1));
+        }
+    };
+    if (nh >= 1) {
+        for (int e = 0; e < nh; ++e) add_segment(px[hull[e]], py[hull[e]], px[hull[e + 1]], py[hull[e + 1]]);
+    } else {
+        for (int k = 0; k < 8; ++k) add_segment(px[k], py[k], px[k], py[k]);
+    }
+    for (int ty = ty_lo; ty <= ty_hi; ++ty) {
+        const int k = ty - ty_lo;
+        if (xmx[k] < xmn[k]) continue;  // the band misses the silhouette
+        const double c0 = std::ceil(xmn[k] - m), c1 = std::floor(xmx[k] + m);
+        if (c1 < c0) continue;
+        const int tx0 = std::max(tx_lo, (int)(std::max(c0, 0.0) * inv_t));
+        const int tx1 = std::min(tx_hi, (int)(std::max(c1, 0.0) * inv_t));
+        if (tx0 <= tx1) out.push_back(Span{ty, tx0, tx1});
+    }
 }
 
 // Sampling region of brick (ix, iy, iz): [b*B, min((b+1)*B, n-1)] per axis.
@@ -402,8 +501,11 @@ struct vr_ctx {
     std::vector<int32_t> plan_diff;         // per-tile item counts as a 2D difference array
     struct PB {
         int32_t key, id, rect[4];
+        int32_t span0, nspan;  // its tile spans in plan_spans
+        int32_t n_items;       // tiles it covers
     };
     std::vector<PB> plan_bricks;
+    std::vector<vrh::Span> plan_spans;
 };
 
 namespace vrh {

@@ -458,6 +458,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
     if (c->rect_cull) project_brick_grid(cam, c->basis, c->n, c->B, nb64, c->plan_proj);
 
     c->plan_bricks.clear();
+    c->plan_spans.clear();
     s.bricks_skipped = 0;
     s.touched_bytes = 0;
     for (int64_t id = 0; id < c->n_bricks; ++id) {
@@ -487,6 +488,22 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
         pb.rect[2] = std::min(pb.rect[2], win[2]);
         pb.rect[3] = std::min(pb.rect[3], win[3]);
         if (pb.rect[2] < pb.rect[0] || pb.rect[3] < pb.rect[1]) continue;
+        // the tiles its silhouette reaches, row by row (the rectangle's in full
+        // without culling)
+        pb.span0 = (int32_t)c->plan_spans.size();
+        if (c->rect_cull) {
+            const CornerProj* q[8];
+            grid_corners(c->plan_proj, nb64, idx, q);
+            brick_spans(q, pb.rect, T, c->plan_spans);
+        } else {
+            for (int ty = pb.rect[1] / T; ty <= pb.rect[3] / T; ++ty)
+                c->plan_spans.push_back(Span{ty, pb.rect[0] / T, pb.rect[2] / T});
+        }
+        pb.nspan = (int32_t)c->plan_spans.size() - pb.span0;
+        pb.n_items = 0;
+        for (int32_t k = pb.span0; k < pb.span0 + pb.nspan; ++k)
+            pb.n_items += c->plan_spans[k].tx1 - c->plan_spans[k].tx0 + 1;
+        if (pb.n_items == 0) continue;
         // Along any ray from the eye each axis index moves monotonically away from
         // the eye's index, so sum |b - e| strictly increases from one brick to the
         // next: sorting by it is a valid front-to-back order for every ray.
@@ -501,27 +518,25 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
                      [](const vr_ctx::PB& x, const vr_ctx::PB& y) { return x.key < y.key; });
     s.bricks_rendered = (int64_t)c->plan_bricks.size();
 
-    // items per tile: each brick adds 1 over its rectangle of tiles, summed as a 2D
-    // difference array and its prefix sums
+    // items per tile: each span adds 1 over its tiles of one row, summed as a
+    // difference array per row and its prefix sums
     const int64_t dw = tiles_x + 1;
-    c->plan_diff.assign((size_t)(dw * (tiles_y + 1)), 0);
+    c->plan_diff.assign((size_t)(dw * tiles_y), 0);
     n_items = 0;
     for (const auto& pb : c->plan_bricks) {
-        const int tx0 = pb.rect[0] / T, tx1 = pb.rect[2] / T;
-        const int ty0 = pb.rect[1] / T, ty1 = pb.rect[3] / T;
-        c->plan_diff[(size_t)(ty0 * dw + tx0)] += 1;
-        c->plan_diff[(size_t)(ty0 * dw + tx1 + 1)] -= 1;
-        c->plan_diff[(size_t)((ty1 + 1) * dw + tx0)] -= 1;
-        c->plan_diff[(size_t)((ty1 + 1) * dw + tx1 + 1)] += 1;
-        n_items += (int64_t)(tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+        for (int32_t k = pb.span0; k < pb.span0 + pb.nspan; ++k) {
+            const Span& sp = c->plan_spans[k];
+            c->plan_diff[(size_t)(sp.ty * dw + sp.tx0)] += 1;
+            c->plan_diff[(size_t)(sp.ty * dw + sp.tx1 + 1)] -= 1;
+        }
+        n_items += pb.n_items;
     }
     c->plan_count.assign(n_tiles + 1, 0);
     for (int ty = 0; ty < tiles_y; ++ty) {
         int32_t run = 0;
         for (int tx = 0; tx < tiles_x; ++tx) {
             run += c->plan_diff[(size_t)(ty * dw + tx)];
-            const int32_t above = ty > 0 ? c->plan_count[(int64_t)(ty - 1) * tiles_x + tx] : 0;
-            c->plan_count[(int64_t)ty * tiles_x + tx] = run + above;
+            c->plan_count[(int64_t)ty * tiles_x + tx] = run;
         }
     }
     if (n_items > (int64_t)INT32_MAX / (T * T)) return fail(c, VR_ENOMEM, "frame too large");
@@ -538,11 +553,10 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
     c->plan_fill.assign(n_tiles, 0);
     int64_t k = 0;
     for (const auto& pb : c->plan_bricks) {
-        const int tx0 = pb.rect[0] / T, tx1 = pb.rect[2] / T;
-        const int ty0 = pb.rect[1] / T, ty1 = pb.rect[3] / T;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                const int64_t t = (int64_t)ty * tiles_x + tx;
+        for (int32_t sk = pb.span0; sk < pb.span0 + pb.nspan; ++sk) {
+            const Span& sp = c->plan_spans[sk];
+            for (int tx = sp.tx0; tx <= sp.tx1; ++tx) {
+                const int64_t t = (int64_t)sp.ty * tiles_x + tx;
                 vr::Item it;
                 it.brick = pb.id;
                 it.tile = (int32_t)t;
@@ -550,6 +564,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
                 it.sweep = c->plan_sweep[t];
                 s.h_items[k++] = it;
             }
+        }
     }
     s.items = n_items;
     return VR_OK;
@@ -1192,8 +1207,7 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocL
     for (int32_t k = 0; k < P; ++k) {
         const auto& pb = c->plan_bricks[k];
         c->ooc_bricks[k] = pb.id;
-        const int64_t cnt = (int64_t)(pb.rect[2] / T - pb.rect[0] / T + 1) * (pb.rect[3] / T - pb.rect[1] / T + 1);
-        c->ooc_item_off[k + 1] = c->ooc_item_off[k] + (int32_t)cnt;
+        c->ooc_item_off[k + 1] = c->ooc_item_off[k] + pb.n_items;
     }
     if (c->ooc_item_off[P] != n_items) return fail(c, VR_EINVAL, "internal: out-of-core item count mismatch");
     const int32_t H = vr::plan_residency(c->res, c->ooc_bricks, c->ooc_frame++, c->ring_first_half, c->ooc_slot,
@@ -1747,6 +1761,37 @@ int vr_plan_brick_rects(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz
     for (int64_t id = 0; id < n_bricks; ++id) {
         int64_t idx[3] = {id % nb[0], (id / nb[0]) % nb[1], id / (nb[0] * nb[1])};
         brick_rect_from_grid(*cam, proj, nb, idx, rects + 4 * id);
+    }
+    return VR_OK;
+}
+
+int vr_plan_brick_tiles(const vr_camera* cam, int64_t nx, int64_t ny, int64_t nz, int32_t bx, int32_t by,
+                        int32_t bz, uint8_t* mask, int64_t n_bricks, int64_t n_tiles) {
+    if (!cam || !mask || !camera_valid(*cam)) return VR_EINVAL;
+    if (nx < 2 || ny < 2 || nz < 2 || bx < 1 || by < 1 || bz < 1) return VR_EINVAL;
+    Basis b;
+    if (!make_basis(*cam, b)) return VR_EINVAL;
+    const int64_t n[3] = {nx, ny, nz};
+    const int32_t B[3] = {bx, by, bz};
+    const int64_t nb[3] = {bricks_along(nx, bx), bricks_along(ny, by), bricks_along(nz, bz)};
+    const int T = vr::kTile;
+    const int64_t tiles_x = (cam->width + T - 1) / T, tiles_y = (cam->height + T - 1) / T;
+    if (nb[0] * nb[1] * nb[2] != n_bricks || tiles_x * tiles_y != n_tiles) return VR_EINVAL;
+    std::memset(mask, 0, (size_t)(n_bricks * n_tiles));
+    // the planner's computation: grid-corner projections, rectangle, silhouette spans
+    std::vector<CornerProj> proj;
+    project_brick_grid(*cam, b, n, B, nb, proj);
+    std::vector<Span> spans;
+    for (int64_t id = 0; id < n_bricks; ++id) {
+        const int64_t idx[3] = {id % nb[0], (id / nb[0]) % nb[1], id / (nb[0] * nb[1])};
+        int32_t rect[4];
+        if (!brick_rect_from_grid(*cam, proj, nb, idx, rect)) continue;
+        const CornerProj* q[8];
+        grid_corners(proj, nb, idx, q);
+        spans.clear();
+        brick_spans(q, rect, T, spans);
+        for (const Span& sp : spans)
+            for (int tx = sp.tx0; tx <= sp.tx1; ++tx) mask[id * n_tiles + (int64_t)sp.ty * tiles_x + tx] = 1;
     }
     return VR_OK;
 }

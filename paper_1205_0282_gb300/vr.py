@@ -76,7 +76,7 @@ class vr_stats(ctypes.Structure):
 # The exported symbols, in header order (tests check them against include/vr.h).
 EXPORTS = ["vr_create", "vr_destroy", "vr_load_cube", "vr_load_cube_host", "vr_load_cube_provider", "vr_brick", "vr_set_transfer_function",
            "vr_set_camera", "vr_camera_from_matrices", "vr_set_camera_matrices", "vr_set_option", "vr_render", "vr_get_stats", "vr_reset_stats",
-           "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_kd_partition", "vr_kd_order",
+           "vr_get_brick_minmax", "vr_plan_brick_rects", "vr_plan_brick_tiles", "vr_kd_partition", "vr_kd_order",
            "vr_set_region", "vr_region_rect", "vr_plan_region_rect", "vr_render_rect",
            "vr_composite_subimages", "vr_server_create", "vr_server_submit", "vr_server_wait",
            "vr_server_get_stats", "vr_server_destroy", "vr_codec_gemm_check", "vr_codec_create",
@@ -121,6 +121,7 @@ def _load():
     lib.vr_get_brick_minmax.argtypes = [P, P, I64]
     lib.vr_plan_brick_rects.argtypes = [ctypes.POINTER(vr_camera), I64, I64, I64, I32, I32, I32,
                                         P, I64]
+    lib.vr_plan_brick_tiles.argtypes = [ctypes.POINTER(vr_camera), I64, I64, I64, I32, I32, I32, P, I64, I64]
     lib.vr_kd_partition.argtypes = [I64, I64, I64, P, I32, P]
     lib.vr_kd_order.argtypes = [I64, I64, I64, P, I32, P, P]
     lib.vr_set_region.argtypes = [P, P, P]
@@ -379,6 +380,20 @@ def vr_plan_brick_rects(cam: dict, shape_xyz, brick) -> np.ndarray:
     if rc != VR_OK:
         raise VRError(rc, "vr_plan_brick_rects rejected its arguments")
     return rects
+
+
+def vr_plan_brick_tiles(cam: dict, shape_xyz, brick) -> np.ndarray:
+    """Host-only: bool (n_bricks, n_tiles) of the (brick, 8x8 tile) items the
+    planner emits (tiles row-major)."""
+    nb = [(n - 1 + b - 1) // b for n, b in zip(shape_xyz, brick)]
+    n_bricks = nb[0] * nb[1] * nb[2]
+    n_tiles = ((cam["width"] + 7) // 8) * ((cam["height"] + 7) // 8)
+    mask = np.zeros((n_bricks, n_tiles), dtype=np.uint8)
+    c = make_camera(cam)
+    rc = _lib.vr_plan_brick_tiles(ctypes.byref(c), *shape_xyz, *brick, mask.ctypes.data, n_bricks, n_tiles)
+    if rc != VR_OK:
+        raise VRError(rc, "vr_plan_brick_tiles rejected its arguments")
+    return mask.astype(bool)
 
 
 def _i32(v, n):

@@ -100,6 +100,62 @@ def test_rendering_rectangles_are_sound(vrmod, shape, brick, cam):
         assert np.all(inside[hit]), f"brick {b}: pixel with samples outside its rectangle"
 
 
+@pytest.mark.parametrize("shape,brick,cam", CASES)
+def test_planned_tiles_are_sound(vrmod, shape, brick, cam):
+    """Every pixel whose ray has samples in a brick (the oracle's ownership) lies
+    in a tile the planner emits for that brick: culling tiles outside the brick's
+    silhouette never drops work."""
+    tiles = vrmod.vr_plan_brick_tiles(cam, shape, brick)
+    rects = vrmod.vr_plan_brick_rects(cam, shape, brick)
+    W, H = cam["width"], cam["height"]
+    pixels = np.arange(W * H)
+    owns = oracle.pixel_bricks(cam, shape, brick, pixels)
+    tile = (pixels // W // 8) * ((W + 7) // 8) + (pixels % W) // 8
+    for b in range(owns.shape[1]):
+        hit = owns[:, b]
+        assert np.all(tiles[b, tile[hit]]), f"brick {b}: a pixel with samples in a dropped tile"
+        # and the tiles lie within the brick's rendering rectangle
+        x0, y0, x1, y1 = rects[b]
+        ty, tx = np.divmod(np.flatnonzero(tiles[b]), (W + 7) // 8)
+        assert np.all((tx >= x0 // 8) & (tx <= x1 // 8) & (ty >= y0 // 8) & (ty <= y1 // 8))
+
+
+def test_planned_tiles_drop_what_the_silhouette_misses(vrmod):
+    """On the HI workload's 1080p orbit the silhouette test drops about a fifth of
+    the rectangles' tiles (their corners), and keeps every tile a ray of the
+    brick passes through (checked by exact ray-box tests of every pixel)."""
+    shape, brick = (1024, 1024, 2048), (128, 128, 128)
+    cam = synth.orbit(shape, 120, 15.0, 1920, 1080)[17]
+    tiles = vrmod.vr_plan_brick_tiles(cam, shape, brick)
+    rects = vrmod.vr_plan_brick_rects(cam, shape, brick)
+    valid = rects[:, 2] >= rects[:, 0]
+    rect_tiles = ((rects[:, 2] // 8 - rects[:, 0] // 8 + 1) * (rects[:, 3] // 8 - rects[:, 1] // 8 + 1))[valid].sum()
+    kept = tiles.sum()
+    assert kept < 0.9 * rect_tiles
+    # exact check on a sample of bricks: every pixel whose ray meets the box keeps its tile
+    eye, tgt, up = (np.asarray(cam[k], np.float64) for k in ("eye", "target", "up"))
+    f = (tgt - eye) / np.linalg.norm(tgt - eye)
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    W, H = cam["width"], cam["height"]
+    th = np.tan(np.radians(cam["fovy_deg"]) / 2)
+    jj, ii = np.mgrid[0:H, 0:W]
+    d = f + ((2 * (ii + 0.5) / W - 1) * th * W / H)[..., None] * r + ((1 - 2 * (jj + 0.5) / H) * th)[..., None] * u
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    tile = (jj // 8) * ((W + 7) // 8) + ii // 8
+    nb = [(n - 2 + b) // b for n, b in zip(shape, brick)]
+    for b in np.random.default_rng(0).choice(np.flatnonzero(valid), 24, replace=False):
+        ix, iy, iz = b % nb[0], (b // nb[0]) % nb[1], b // (nb[0] * nb[1])
+        lo = np.array([ix, iy, iz], np.float64) * 128
+        hi = np.minimum(lo + 128, np.array(shape) - 1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1, t2 = (lo - eye) / d, (hi - eye) / d
+        tn, tf = np.minimum(t1, t2).max(-1), np.maximum(t1, t2).min(-1)
+        hit = tf > np.maximum(tn, 0.0)
+        assert np.all(tiles[b, tile[hit]]), b
+
+
 def test_rectangles_are_tight_enough(vrmod):
     """Rectangles are not the whole screen: the planner actually culls."""
     cam = synth.tiny_views(width=256, height=256)[0]
