@@ -2,6 +2,8 @@
 // function and camera state, the per-frame planner (rendering rectangles, exact
 // empty-space skipping, view-order sort, work-list build; Sections 2.3.1-2.3.3 of
 // arXiv:1205.0282) and the stream-ordered frame pipeline.
+#include <thread>
+
 #include "vr_ctx.cuh"
 
 using namespace vrh;
@@ -457,62 +459,99 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
     const int64_t nb64[3] = {c->nb[0], c->nb[1], c->nb[2]};
     if (c->rect_cull) project_brick_grid(cam, c->basis, c->n, c->B, nb64, c->plan_proj);
 
+    // per brick: region, empty-space test, rectangle, silhouette spans.  Chunks of
+    // bricks run on host threads and are joined in brick order, so the plan is the
+    // same whatever the thread count.
+    const bool lowp = use_tex(c) && c->precision != VR_PRECISION_F32;
+    const int64_t vox_bytes = use_tex(c) ? precision_bytes(c->precision) : (int64_t)sizeof(float);
+    struct Part {
+        std::vector<vr_ctx::PB> bricks;
+        std::vector<Span> spans;
+        int64_t skipped = 0, touched = 0;
+    };
+    auto plan_range = [&](int64_t id0, int64_t id1, Part& out) {
+        for (int64_t id = id0; id < id1; ++id) {
+            int64_t idx[3] = {id % c->nb[0], (id / c->nb[0]) % c->nb[1], id / ((int64_t)c->nb[0] * c->nb[1])};
+            bool inside = true;
+            for (int a = 0; a < 3; ++a) inside = inside && idx[a] >= c->region_lo[a] && idx[a] < c->region_hi[a];
+            if (!inside) continue;
+            if (c->skip_empty && c->mode == 0) {
+                const float2 mm = lowp ? c->h_minmax_q[id] : c->h_minmax[id];
+                if (tf_alpha_max(c->tf, mm.x, mm.y) == 0.0) {
+                    ++out.skipped;
+                    continue;
+                }
+            }
+            vr_ctx::PB pb;
+            pb.id = (int32_t)id;
+            if (c->rect_cull) {
+                if (!brick_rect_from_grid(cam, c->plan_proj, nb64, idx, pb.rect)) continue;
+            } else {
+                pb.rect[0] = pb.rect[1] = 0;
+                pb.rect[2] = cam.width - 1;
+                pb.rect[3] = cam.height - 1;
+            }
+            // only the output window's pixels are computed
+            pb.rect[0] = std::max(pb.rect[0], win[0]);
+            pb.rect[1] = std::max(pb.rect[1], win[1]);
+            pb.rect[2] = std::min(pb.rect[2], win[2]);
+            pb.rect[3] = std::min(pb.rect[3], win[3]);
+            if (pb.rect[2] < pb.rect[0] || pb.rect[3] < pb.rect[1]) continue;
+            // the tiles its silhouette reaches, row by row (the rectangle's in full
+            // without culling)
+            pb.span0 = (int32_t)out.spans.size();
+            if (c->rect_cull) {
+                const CornerProj* q[8];
+                grid_corners(c->plan_proj, nb64, idx, q);
+                brick_spans(q, pb.rect, T, out.spans);
+            } else {
+                for (int ty = pb.rect[1] / T; ty <= pb.rect[3] / T; ++ty)
+                    out.spans.push_back(Span{ty, pb.rect[0] / T, pb.rect[2] / T});
+            }
+            pb.nspan = (int32_t)out.spans.size() - pb.span0;
+            pb.n_items = 0;
+            for (int32_t k = pb.span0; k < pb.span0 + pb.nspan; ++k)
+                pb.n_items += out.spans[k].tx1 - out.spans[k].tx0 + 1;
+            if (pb.n_items == 0) {
+                out.spans.resize(pb.span0);
+                continue;
+            }
+            // Along any ray from the eye each axis index moves monotonically away from
+            // the eye's index, so sum |b - e| strictly increases from one brick to the
+            // next: sorting by it is a valid front-to-back order for every ray.
+            pb.key = 0;
+            for (int a = 0; a < 3; ++a) pb.key += (int32_t)std::llabs(idx[a] - e[a]);
+            out.bricks.push_back(pb);
+            int64_t vox = 1;
+            for (int a = 0; a < 3; ++a) vox *= std::min<int64_t>(c->B[a], c->n[a] - idx[a] * c->B[a]);
+            out.touched += vox * vox_bytes;
+        }
+    };
+    const int64_t hw = (int64_t)std::max(1u, std::thread::hardware_concurrency());
+    const int64_t n_parts = std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)8, c->n_bricks / 256}));
+    std::vector<Part> parts(n_parts);
+    if (n_parts == 1) {
+        plan_range(0, c->n_bricks, parts[0]);
+    } else {
+        std::vector<std::thread> pool;
+        for (int64_t t = 1; t < n_parts; ++t)
+            pool.emplace_back(plan_range, c->n_bricks * t / n_parts, c->n_bricks * (t + 1) / n_parts, std::ref(parts[t]));
+        plan_range(0, c->n_bricks / n_parts, parts[0]);
+        for (auto& th : pool) th.join();
+    }
     c->plan_bricks.clear();
     c->plan_spans.clear();
     s.bricks_skipped = 0;
     s.touched_bytes = 0;
-    for (int64_t id = 0; id < c->n_bricks; ++id) {
-        int64_t idx[3] = {id % c->nb[0], (id / c->nb[0]) % c->nb[1], id / ((int64_t)c->nb[0] * c->nb[1])};
-        bool inside = true;
-        for (int a = 0; a < 3; ++a) inside = inside && idx[a] >= c->region_lo[a] && idx[a] < c->region_hi[a];
-        if (!inside) continue;
-        if (c->skip_empty && c->mode == 0) {
-            const float2 mm = (use_tex(c) && c->precision != VR_PRECISION_F32) ? c->h_minmax_q[id] : c->h_minmax[id];
-            if (tf_alpha_max(c->tf, mm.x, mm.y) == 0.0) {
-                ++s.bricks_skipped;
-                continue;
-            }
+    for (Part& pt : parts) {
+        const int32_t base = (int32_t)c->plan_spans.size();
+        c->plan_spans.insert(c->plan_spans.end(), pt.spans.begin(), pt.spans.end());
+        for (vr_ctx::PB pb : pt.bricks) {
+            pb.span0 += base;
+            c->plan_bricks.push_back(pb);
         }
-        vr_ctx::PB pb;
-        pb.id = (int32_t)id;
-        if (c->rect_cull) {
-            if (!brick_rect_from_grid(cam, c->plan_proj, nb64, idx, pb.rect)) continue;
-        } else {
-            pb.rect[0] = pb.rect[1] = 0;
-            pb.rect[2] = cam.width - 1;
-            pb.rect[3] = cam.height - 1;
-        }
-        // only the output window's pixels are computed
-        pb.rect[0] = std::max(pb.rect[0], win[0]);
-        pb.rect[1] = std::max(pb.rect[1], win[1]);
-        pb.rect[2] = std::min(pb.rect[2], win[2]);
-        pb.rect[3] = std::min(pb.rect[3], win[3]);
-        if (pb.rect[2] < pb.rect[0] || pb.rect[3] < pb.rect[1]) continue;
-        // the tiles its silhouette reaches, row by row (the rectangle's in full
-        // without culling)
-        pb.span0 = (int32_t)c->plan_spans.size();
-        if (c->rect_cull) {
-            const CornerProj* q[8];
-            grid_corners(c->plan_proj, nb64, idx, q);
-            brick_spans(q, pb.rect, T, c->plan_spans);
-        } else {
-            for (int ty = pb.rect[1] / T; ty <= pb.rect[3] / T; ++ty)
-                c->plan_spans.push_back(Span{ty, pb.rect[0] / T, pb.rect[2] / T});
-        }
-        pb.nspan = (int32_t)c->plan_spans.size() - pb.span0;
-        pb.n_items = 0;
-        for (int32_t k = pb.span0; k < pb.span0 + pb.nspan; ++k)
-            pb.n_items += c->plan_spans[k].tx1 - c->plan_spans[k].tx0 + 1;
-        if (pb.n_items == 0) continue;
-        // Along any ray from the eye each axis index moves monotonically away from
-        // the eye's index, so sum |b - e| strictly increases from one brick to the
-        // next: sorting by it is a valid front-to-back order for every ray.
-        pb.key = 0;
-        for (int a = 0; a < 3; ++a) pb.key += (int32_t)std::llabs(idx[a] - e[a]);
-        c->plan_bricks.push_back(pb);
-        int64_t vox = 1;
-        for (int a = 0; a < 3; ++a) vox *= std::min<int64_t>(c->B[a], c->n[a] - idx[a] * c->B[a]);
-        s.touched_bytes += vox * (use_tex(c) ? precision_bytes(c->precision) : (int64_t)sizeof(float));
+        s.bricks_skipped += pt.skipped;
+        s.touched_bytes += pt.touched;
     }
     std::stable_sort(c->plan_bricks.begin(), c->plan_bricks.end(),
                      [](const vr_ctx::PB& x, const vr_ctx::PB& y) { return x.key < y.key; });
