@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/vr.h"
@@ -229,14 +230,26 @@ inline void project_brick_grid(const vr_camera& cam, const Basis& b, const int64
                                const int64_t nb[3], std::vector<CornerProj>& proj) {
     const int64_t g[3] = {nb[0] + 1, nb[1] + 1, nb[2] + 1};
     proj.resize((size_t)(g[0] * g[1] * g[2]));
-    for (int64_t k = 0; k < g[2]; ++k)
-        for (int64_t j = 0; j < g[1]; ++j)
-            for (int64_t i = 0; i < g[0]; ++i) {
-                const double P[3] = {(double)std::min<int64_t>(i * B[0], n[0] - 1),
-                                     (double)std::min<int64_t>(j * B[1], n[1] - 1),
-                                     (double)std::min<int64_t>(k * B[2], n[2] - 1)};
-                proj[(size_t)((k * g[1] + j) * g[0] + i)] = project_corner(cam, b, P);
-            }
+    auto planes = [&](int64_t k0, int64_t k1) {
+        for (int64_t k = k0; k < k1; ++k)
+            for (int64_t j = 0; j < g[1]; ++j)
+                for (int64_t i = 0; i < g[0]; ++i) {
+                    const double P[3] = {(double)std::min<int64_t>(i * B[0], n[0] - 1),
+                                         (double)std::min<int64_t>(j * B[1], n[1] - 1),
+                                         (double)std::min<int64_t>(k * B[2], n[2] - 1)};
+                    proj[(size_t)((k * g[1] + j) * g[0] + i)] = project_corner(cam, b, P);
+                }
+    };
+    // large grids (tens of thousands of points) on a few host threads, by planes
+    const int64_t parts = std::min<int64_t>({g[2], (int64_t)8, g[0] * g[1] * g[2] / 16384 + 1});
+    if (parts <= 1) {
+        planes(0, g[2]);
+        return;
+    }
+    std::vector<std::thread> pool;
+    for (int64_t t = 1; t < parts; ++t) pool.emplace_back(planes, g[2] * t / parts, g[2] * (t + 1) / parts);
+    planes(0, g[2] / parts);
+    for (auto& th : pool) th.join();
 }
 
 // Rendering rectangle of brick idx from the grid projections (box_rect of its box).
