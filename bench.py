@@ -1001,6 +1001,8 @@ def run_learned_xl(args):
                             samples_per_s=st["samples"] / sum(secs),
                             bricks_rendered_per_frame=st["bricks_rendered"] / max(st["frames"], 1),
                             bricks_filled_per_frame=st["bricks_uploaded"] / max(st["frames"], 1),
+                            plan_ms_per_frame=st["plan_ms"] / max(st["frames"], 1),
+                            items_per_frame=st["items"] / max(st["frames"], 1),
                             launches=st["launches"], device_errors=st["device_errors"])
                 row[form] = info
                 row[form + "_imgs"] = imgs
