@@ -95,7 +95,8 @@ typedef struct {
 /* Options for vr_set_option. */
 #define VR_OPT_SKIP_EMPTY 1  /* 1 (default): drop bricks whose TF opacity is 0 on [min,max] */
 #define VR_OPT_RECT_CULL 2   /* 1 (default): items only for tiles inside a brick's rendering
-                                rectangle (Section 2.3.2); 0: every tile for every brick */
+                                rectangle (Section 2.3.2) that its silhouette reaches (see
+                                vr_plan_brick_tiles); 0: every tile for every brick */
 #define VR_OPT_MODE 3        /* 0 (default): emission-absorption compositing;
                                 1: maximum intensity projection + colour map (Section 2.3.3) */
 #define VR_OPT_KERNEL 4      /* ray-march kernel for emission-absorption frames:
