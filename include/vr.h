@@ -18,9 +18,12 @@
  *   - Return value: VR_OK (0) or a negative VR_E* code; no exception crosses the
  *     ABI.  vr_last_error() gives a message for the last failing call on a context.
  *   - The library owns all device memory it allocates (released by vr_destroy).
- *     Callers own every buffer they pass; the library never keeps a pointer to a
- *     caller buffer after a call returns, except that a device output buffer
- *     given to vr_render is written asynchronously on the given stream.
+ *     Callers own every buffer they pass; the library keeps no pointer to a
+ *     caller buffer after a call returns, except where the call says so: an
+ *     output buffer written asynchronously on the given stream (device memory,
+ *     or page-locked host memory with VR_OPT_HOST_OUTPUT_ASYNC), the host cube
+ *     of vr_load_cube_host, a brick provider and its user data, and a learned
+ *     context's fallback cube or provider (read at the next vr_brick).
  *   - Pointers may be host or device (CUDA unified addressing decides).
  *   - Coordinates: voxel (i,j,k) of a cube float32[nz][ny][nx] (x fastest) sits
  *     at the point (i,j,k); the domain is [0,nx-1] x [0,ny-1] x [0,nz-1]; all
