@@ -313,7 +313,7 @@ inline void brick_spans(const CornerProj* const q[8], const int32_t rect[4], int
     }
     const int nh = h - 1;  // the last point repeats the first
     const double m = 1.0;  // margin in pixels
-    const double inv_t = 1.0 / T;  // exact for the power-of-two tiles; columns are integers < 2^24
+    const double inv_t = 1.0 / T;  // x / T exactly for the power-of-two tiles (columns are integers < 2^24)
     // x-extent of the silhouette within each tile row's band of pixel-centre rows
     // (widened by the margin): the extremes lie on its edges, so each edge updates
     // the rows its y-range overlaps, clipped to each band
@@ -331,8 +331,8 @@ inline void brick_spans(const CornerProj* const q[8], const int32_t rect[4], int
             std::swap(xa, xb);
             std::swap(ya, yb);
         }
-        const int r0 = std::max(ty_lo, (int)std::floor((ya - m - (T - 1)) / T));
-        const int r1 = std::min(ty_hi, (int)std::floor((yb + m) / T));
+        const int r0 = std::max(ty_lo, (int)std::floor((ya - m - (T - 1)) * inv_t));
+        const int r1 = std::min(ty_hi, (int)std::floor((yb + m) * inv_t));
         const double slope = yb > ya ? (xb - xa) / (yb - ya) : 0.0;
         for (int ty = r0; ty <= r1; ++ty) {
             const double lo = std::max(ya, band_lo(ty)), hi = std::min(yb, band_hi(ty));
@@ -495,8 +495,7 @@ struct vr_ctx {
     cudaEvent_t ev_half_read[2] = {nullptr, nullptr};  // last march that read each ring half
     int32_t ring_first_half = 0;                       // ring half the next frame starts in
     std::vector<int32_t> ooc_ring;
-    std::vector<int32_t> ooc_bricks, ooc_slot, ooc_up, ooc_item_off;
-    std::vector<vr::Item> ooc_items;
+    std::vector<int32_t> ooc_bricks, ooc_slot, ooc_up;
 
     // sort-last distribution: the bricks this context renders, [region_lo, region_hi)
     int32_t region_lo[3] = {0, 0, 0}, region_hi[3] = {0, 0, 0};
@@ -511,14 +510,23 @@ struct vr_ctx {
     std::vector<int32_t> plan_count, plan_fill, plan_sweep;
     std::vector<double> plan_qx, plan_qy;  // view-plane offsets of tile-centre columns and rows
     std::vector<vrh::CornerProj> plan_proj;  // projections of the brick grid's corner points
-    std::vector<int32_t> plan_diff;         // per-tile item counts as a 2D difference array
+    std::vector<int64_t> plan_dst;          // per planned brick: where its items start in the frame's list
     struct PB {
-        int32_t key, id, rect[4];
-        int32_t span0, nspan;  // its tile spans in plan_spans
+        int32_t id;
+        int32_t part;          // the host thread's share that planned it (plan_parts)
+        int32_t span0, nspan;  // its tile spans there
         int32_t n_items;       // tiles it covers
     };
-    std::vector<PB> plan_bricks;
-    std::vector<vrh::Span> plan_spans;
+    std::vector<PB> plan_bricks;  // in view order
+    struct PlanPart {  // one host thread's share of the bricks, kept from frame to frame
+        std::vector<PB> bricks;
+        std::vector<int32_t> keys;       // their view-order keys
+        std::vector<int32_t> key_count;  // bricks per key, then where the first of each goes
+        std::vector<vrh::Span> spans;
+        std::vector<int32_t> diff;  // items per tile as a difference array per tile row
+        int64_t skipped = 0, touched = 0, items = 0;
+    };
+    std::vector<PlanPart> plan_parts;
 };
 
 namespace vrh {
@@ -581,7 +589,8 @@ bool use_tma(vr_ctx* c);
 int prepare_tex(vr_ctx* c);
 int64_t precision_bytes(int precision);
 int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32_t& tiles_y, int32_t& T,
-               int64_t& n_items);
+               int64_t& n_items, bool emit = true);
+void emit_items(vr_ctx* c, Slot& s, int32_t tiles_x, int32_t tiles_y, int64_t n_items);
 void fill_common_params(vr_ctx* c, vr::FrameParams& p);
 
 }  // namespace vrh

@@ -403,7 +403,7 @@ void free_tex(vr_ctx* c) {
 }
 
 int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32_t& tiles_y, int32_t& T,
-               int64_t& n_items) {
+               int64_t& n_items, bool emit) {
     const vr_camera& cam = c->cam;
     T = use_tma(c) ? vr::kTileTma : vr::kTile;  // the direct and texture marches use 8x8 tiles
     tiles_x = (cam.width + T - 1) / T;
@@ -459,122 +459,166 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
     const int64_t nb64[3] = {c->nb[0], c->nb[1], c->nb[2]};
     if (c->rect_cull) project_brick_grid(cam, c->basis, c->n, c->B, nb64, c->plan_proj);
 
-    // per brick: region, empty-space test, rectangle, silhouette spans.  Chunks of
-    // bricks run on host threads and are joined in brick order, so the plan is the
-    // same whatever the thread count.
+    // Opacity runs of the TF that reach its first or its last control point: a brick
+    // whose value range lies within one has zero opacity, the empty-space test's
+    // answer without evaluating the TF (its other bricks go through tf_alpha_max).
+    const std::vector<double>& tf = c->tf;
+    const int n_tf = (int)(tf.size() / 5);
+    double zero_to = -INFINITY, zero_from = INFINITY;
+    {
+        int z = -1, w = n_tf;
+        while (z + 1 < n_tf && tf[5 * (z + 1) + 4] == 0.0) ++z;
+        while (w > 0 && tf[5 * (w - 1) + 4] == 0.0) --w;
+        if (z >= 0) zero_to = tf[5 * z];
+        if (w < n_tf) zero_from = tf[5 * w];
+    }
+
+    // Per brick: region, empty-space test, rectangle, silhouette spans and the
+    // per-tile item counts.  Host threads take consecutive chunks of bricks.
     const bool lowp = use_tex(c) && c->precision != VR_PRECISION_F32;
     const int64_t vox_bytes = use_tex(c) ? precision_bytes(c->precision) : (int64_t)sizeof(float);
-    struct Part {
-        std::vector<vr_ctx::PB> bricks;
-        std::vector<Span> spans;
-        int64_t skipped = 0, touched = 0;
-    };
-    auto plan_range = [&](int64_t id0, int64_t id1, Part& out) {
-        for (int64_t id = id0; id < id1; ++id) {
-            int64_t idx[3] = {id % c->nb[0], (id / c->nb[0]) % c->nb[1], id / ((int64_t)c->nb[0] * c->nb[1])};
+    const int64_t dw = tiles_x + 1;
+    const int32_t n_keys = c->nb[0] + c->nb[1] + c->nb[2] + 1;  // keys are at most the sum of the brick counts
+    using Part = vr_ctx::PlanPart;
+    auto plan_range = [&](int64_t id0, int64_t id1, int32_t part) {
+        Part& out = c->plan_parts[part];
+        out.bricks.clear();
+        out.keys.clear();
+        out.spans.clear();
+        out.diff.assign((size_t)(dw * tiles_y), 0);
+        out.key_count.assign((size_t)n_keys, 0);
+        out.skipped = out.touched = out.items = 0;
+        int64_t idx[3] = {id0 % c->nb[0], (id0 / c->nb[0]) % c->nb[1], id0 / ((int64_t)c->nb[0] * c->nb[1])};
+        auto next = [&]() {
+            if (++idx[0] < c->nb[0]) return;
+            idx[0] = 0;
+            if (++idx[1] < c->nb[1]) return;
+            idx[1] = 0;
+            ++idx[2];
+        };
+        for (int64_t id = id0; id < id1; ++id, next()) {
             bool inside = true;
             for (int a = 0; a < 3; ++a) inside = inside && idx[a] >= c->region_lo[a] && idx[a] < c->region_hi[a];
             if (!inside) continue;
             if (c->skip_empty && c->mode == 0) {
                 const float2 mm = lowp ? c->h_minmax_q[id] : c->h_minmax[id];
-                if (tf_alpha_max(c->tf, mm.x, mm.y) == 0.0) {
+                if ((double)mm.y <= zero_to || (double)mm.x >= zero_from || tf_alpha_max(tf, mm.x, mm.y) == 0.0) {
                     ++out.skipped;
                     continue;
                 }
             }
-            vr_ctx::PB pb;
-            pb.id = (int32_t)id;
+            int32_t rect[4];
             if (c->rect_cull) {
-                if (!brick_rect_from_grid(cam, c->plan_proj, nb64, idx, pb.rect)) continue;
+                if (!brick_rect_from_grid(cam, c->plan_proj, nb64, idx, rect)) continue;
             } else {
-                pb.rect[0] = pb.rect[1] = 0;
-                pb.rect[2] = cam.width - 1;
-                pb.rect[3] = cam.height - 1;
+                rect[0] = rect[1] = 0;
+                rect[2] = cam.width - 1;
+                rect[3] = cam.height - 1;
             }
             // only the output window's pixels are computed
-            pb.rect[0] = std::max(pb.rect[0], win[0]);
-            pb.rect[1] = std::max(pb.rect[1], win[1]);
-            pb.rect[2] = std::min(pb.rect[2], win[2]);
-            pb.rect[3] = std::min(pb.rect[3], win[3]);
-            if (pb.rect[2] < pb.rect[0] || pb.rect[3] < pb.rect[1]) continue;
+            rect[0] = std::max(rect[0], win[0]);
+            rect[1] = std::max(rect[1], win[1]);
+            rect[2] = std::min(rect[2], win[2]);
+            rect[3] = std::min(rect[3], win[3]);
+            if (rect[2] < rect[0] || rect[3] < rect[1]) continue;
             // the tiles its silhouette reaches, row by row (the rectangle's in full
-            // without culling)
+            // without culling), rows ascending
+            vr_ctx::PB pb;
+            pb.id = (int32_t)id;
+            pb.part = part;
             pb.span0 = (int32_t)out.spans.size();
             if (c->rect_cull) {
                 const CornerProj* q[8];
                 grid_corners(c->plan_proj, nb64, idx, q);
-                brick_spans(q, pb.rect, T, out.spans);
+                brick_spans(q, rect, T, out.spans);
             } else {
-                for (int ty = pb.rect[1] / T; ty <= pb.rect[3] / T; ++ty)
-                    out.spans.push_back(Span{ty, pb.rect[0] / T, pb.rect[2] / T});
+                for (int ty = rect[1] / T; ty <= rect[3] / T; ++ty)
+                    out.spans.push_back(Span{ty, rect[0] / T, rect[2] / T});
             }
             pb.nspan = (int32_t)out.spans.size() - pb.span0;
             pb.n_items = 0;
-            for (int32_t k = pb.span0; k < pb.span0 + pb.nspan; ++k)
-                pb.n_items += out.spans[k].tx1 - out.spans[k].tx0 + 1;
+            for (int32_t k = pb.span0; k < pb.span0 + pb.nspan; ++k) {
+                const Span& sp = out.spans[k];
+                pb.n_items += sp.tx1 - sp.tx0 + 1;
+                out.diff[(size_t)(sp.ty * dw + sp.tx0)] += 1;
+                out.diff[(size_t)(sp.ty * dw + sp.tx1 + 1)] -= 1;
+            }
             if (pb.n_items == 0) {
                 out.spans.resize(pb.span0);
                 continue;
             }
+            out.items += pb.n_items;
             // Along any ray from the eye each axis index moves monotonically away from
             // the eye's index, so sum |b - e| strictly increases from one brick to the
-            // next: sorting by it is a valid front-to-back order for every ray.
-            pb.key = 0;
-            for (int a = 0; a < 3; ++a) pb.key += (int32_t)std::llabs(idx[a] - e[a]);
+            // next: ordering by it is a valid front-to-back order for every ray.
+            int32_t key = 0;
+            for (int a = 0; a < 3; ++a) key += (int32_t)std::llabs(idx[a] - e[a]);
             out.bricks.push_back(pb);
+            out.keys.push_back(key);
+            ++out.key_count[key];
             int64_t vox = 1;
             for (int a = 0; a < 3; ++a) vox *= std::min<int64_t>(c->B[a], c->n[a] - idx[a] * c->B[a]);
             out.touched += vox * vox_bytes;
         }
     };
     const int64_t hw = (int64_t)std::max(1u, std::thread::hardware_concurrency());
-    const int64_t n_parts = std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)8, c->n_bricks / 256}));
-    std::vector<Part> parts(n_parts);
-    if (n_parts == 1) {
-        plan_range(0, c->n_bricks, parts[0]);
-    } else {
+    const int32_t n_parts = (int32_t)std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)8, c->n_bricks / 256}));
+    if ((int32_t)c->plan_parts.size() < n_parts) c->plan_parts.resize(n_parts);
+    auto run_parts = [&](auto&& fn) {
+        if (n_parts == 1) {
+            fn(0);
+            return;
+        }
         std::vector<std::thread> pool;
-        for (int64_t t = 1; t < n_parts; ++t)
-            pool.emplace_back(plan_range, c->n_bricks * t / n_parts, c->n_bricks * (t + 1) / n_parts, std::ref(parts[t]));
-        plan_range(0, c->n_bricks / n_parts, parts[0]);
+        for (int32_t t = 1; t < n_parts; ++t) pool.emplace_back(fn, t);
+        fn(0);
         for (auto& th : pool) th.join();
-    }
-    c->plan_bricks.clear();
-    c->plan_spans.clear();
+    };
+    run_parts([&](int32_t t) { plan_range(c->n_bricks * t / n_parts, c->n_bricks * (t + 1) / n_parts, t); });
+
+    // the bricks in view order: a stable counting sort by key.  Bricks of one key
+    // go part after part, each part's in brick order (the chunks are consecutive),
+    // so the order is the same whatever the thread count; each part scatters its
+    // own bricks.
+    size_t n_bricks = 0;
     s.bricks_skipped = 0;
     s.touched_bytes = 0;
-    for (Part& pt : parts) {
-        const int32_t base = (int32_t)c->plan_spans.size();
-        c->plan_spans.insert(c->plan_spans.end(), pt.spans.begin(), pt.spans.end());
-        for (vr_ctx::PB pb : pt.bricks) {
-            pb.span0 += base;
-            c->plan_bricks.push_back(pb);
-        }
+    n_items = 0;
+    for (int32_t t = 0; t < n_parts; ++t) {
+        const Part& pt = c->plan_parts[t];
+        n_bricks += pt.bricks.size();
         s.bricks_skipped += pt.skipped;
         s.touched_bytes += pt.touched;
+        n_items += pt.items;
     }
-    std::stable_sort(c->plan_bricks.begin(), c->plan_bricks.end(),
-                     [](const vr_ctx::PB& x, const vr_ctx::PB& y) { return x.key < y.key; });
-    s.bricks_rendered = (int64_t)c->plan_bricks.size();
+    {
+        int64_t run = 0;
+        for (int32_t k = 0; k < n_keys; ++k)
+            for (int32_t t = 0; t < n_parts; ++t) {
+                int32_t& cnt = c->plan_parts[t].key_count[k];
+                const int32_t here = cnt;
+                cnt = (int32_t)run;  // where the part's first brick of key k goes
+                run += here;
+            }
+    }
+    c->plan_bricks.resize(n_bricks);
+    run_parts([&](int32_t t) {
+        Part& pt = c->plan_parts[t];
+        for (size_t i = 0; i < pt.bricks.size(); ++i) c->plan_bricks[(size_t)pt.key_count[pt.keys[i]]++] = pt.bricks[i];
+    });
+    s.bricks_rendered = (int64_t)n_bricks;
 
-    // items per tile: each span adds 1 over its tiles of one row, summed as a
-    // difference array per row and its prefix sums
-    const int64_t dw = tiles_x + 1;
-    c->plan_diff.assign((size_t)(dw * tiles_y), 0);
-    n_items = 0;
-    for (const auto& pb : c->plan_bricks) {
-        for (int32_t k = pb.span0; k < pb.span0 + pb.nspan; ++k) {
-            const Span& sp = c->plan_spans[k];
-            c->plan_diff[(size_t)(sp.ty * dw + sp.tx0)] += 1;
-            c->plan_diff[(size_t)(sp.ty * dw + sp.tx1 + 1)] -= 1;
-        }
-        n_items += pb.n_items;
+    // items per tile: the parts' difference arrays summed, then prefix sums per row
+    std::vector<int32_t>& diff = c->plan_parts[0].diff;
+    for (int64_t t = 1; t < n_parts; ++t) {
+        const int32_t* d = c->plan_parts[t].diff.data();
+        for (size_t i = 0; i < diff.size(); ++i) diff[i] += d[i];
     }
     c->plan_count.assign(n_tiles + 1, 0);
     for (int ty = 0; ty < tiles_y; ++ty) {
         int32_t run = 0;
         for (int tx = 0; tx < tiles_x; ++tx) {
-            run += c->plan_diff[(size_t)(ty * dw + tx)];
+            run += diff[(size_t)(ty * dw + tx)];
             c->plan_count[(int64_t)ty * tiles_x + tx] = run;
         }
     }
@@ -589,24 +633,65 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
         run += c->plan_count[t];
     }
     s.h_tile_start[n_tiles] = run;
-    c->plan_fill.assign(n_tiles, 0);
-    int64_t k = 0;
-    for (const auto& pb : c->plan_bricks) {
-        for (int32_t sk = pb.span0; sk < pb.span0 + pb.nspan; ++sk) {
-            const Span& sp = c->plan_spans[sk];
-            for (int tx = sp.tx0; tx <= sp.tx1; ++tx) {
-                const int64_t t = (int64_t)sp.ty * tiles_x + tx;
-                vr::Item it;
-                it.brick = pb.id;
-                it.tile = (int32_t)t;
-                it.frag = s.h_tile_start[t] + c->plan_fill[t]++;
-                it.sweep = c->plan_sweep[t];
-                s.h_items[k++] = it;
+    s.items = n_items;
+    if (emit) {
+        // the items brick after brick in view order
+        c->plan_dst.resize(n_bricks);
+        int64_t w = 0;
+        for (size_t k = 0; k < n_bricks; ++k) {
+            c->plan_dst[k] = w;
+            w += c->plan_bricks[k].n_items;
+        }
+        emit_items(c, s, tiles_x, tiles_y, n_items);
+    }
+    return VR_OK;
+}
+
+// The frame's items: brick k's items, one per tile of its spans, start at
+// plan_dst[k] of the list; each gets its tile's next fragment slot in view order
+// of the bricks, so every tile's fragments run front to back.  Rows of tiles are
+// split among host threads by their item counts, each thread filling its rows'
+// items wherever they sit in the list (the same list whatever the thread count).
+void emit_items(vr_ctx* c, Slot& s, int32_t tiles_x, int32_t tiles_y, int64_t n_items) {
+    const int64_t P = (int64_t)c->plan_bricks.size();
+    c->plan_fill.assign((size_t)tiles_x * tiles_y, 0);
+    auto rows = [&](int32_t ty0, int32_t ty1) {
+        for (int64_t k = 0; k < P; ++k) {
+            const vr_ctx::PB& pb = c->plan_bricks[k];
+            const Span* sp = c->plan_parts[pb.part].spans.data() + pb.span0;
+            if (sp[pb.nspan - 1].ty < ty0 || sp[0].ty >= ty1) continue;
+            int64_t w = c->plan_dst[k];
+            for (int32_t j = 0; j < pb.nspan; ++j) {
+                const Span& q = sp[j];
+                if (q.ty >= ty0 && q.ty < ty1) {
+                    const int64_t t0 = (int64_t)q.ty * tiles_x;
+                    for (int32_t tx = q.tx0; tx <= q.tx1; ++tx) {
+                        const int64_t t = t0 + tx;
+                        s.h_items[w + (tx - q.tx0)] =
+                            vr::Item{pb.id, (int32_t)t, s.h_tile_start[t] + c->plan_fill[t]++, c->plan_sweep[t]};
+                    }
+                }
+                w += q.tx1 - q.tx0 + 1;
             }
         }
+    };
+    const int64_t hw = (int64_t)std::max(1u, std::thread::hardware_concurrency());
+    const int64_t n_parts = std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)8, n_items / 65536, (int64_t)tiles_y}));
+    if (n_parts == 1) {
+        rows(0, tiles_y);
+        return;
     }
-    s.items = n_items;
-    return VR_OK;
+    // row boundaries at about equal item counts
+    std::vector<int32_t> cut(1, 0);
+    for (int32_t ty = 0; ty < tiles_y && (int64_t)cut.size() < n_parts; ++ty) {
+        const int64_t upto = s.h_tile_start[(int64_t)(ty + 1) * tiles_x];
+        if (upto * n_parts >= n_items * (int64_t)cut.size()) cut.push_back(ty + 1);
+    }
+    cut.push_back(tiles_y);
+    std::vector<std::thread> pool;
+    for (size_t p = 1; p + 1 < cut.size(); ++p) pool.emplace_back(rows, cut[p], cut[p + 1]);
+    rows(cut[0], cut[1]);
+    for (auto& th : pool) th.join();
 }
 
 }  // namespace vrh
@@ -1227,11 +1312,11 @@ void fill_common_params(vr_ctx* c, vr::FrameParams& p) {
     p.brick_scale = c->d_brick_scale;
 }
 
-// Out-of-core frame: cache slots for the frame's bricks, the slot table, and the
+// Out-of-core frame: cache slots for the frame's bricks, the slot table, the
 // march launches, each a contiguous range of items with the bricks it must wait
 // for: first the items of resident bricks (no wait), then bricks copied into
 // resident slots in groups of about 64 MiB, then bricks streamed through the ring,
-// one launch per half-ring.
+// one launch per half-ring; and the items, written straight into that order.
 struct OocLaunch {
     int64_t lo, hi;             // items [lo, hi)
     std::vector<int32_t> up;    // bricks (ids) to copy before the launch
@@ -1239,16 +1324,16 @@ struct OocLaunch {
     int32_t half = -1;          // ring half the bricks go to (-1: resident slots)
 };
 
-int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocLaunch>& launches) {
+int ooc_prepare(vr_ctx* c, Slot& s, int32_t tiles_x, int32_t tiles_y, int64_t n_items,
+                std::vector<OocLaunch>& launches) {
     const int32_t P = (int32_t)c->plan_bricks.size();
     c->ooc_bricks.resize(P);
-    c->ooc_item_off.assign(P + 1, 0);
+    int64_t total = 0;
     for (int32_t k = 0; k < P; ++k) {
-        const auto& pb = c->plan_bricks[k];
-        c->ooc_bricks[k] = pb.id;
-        c->ooc_item_off[k + 1] = c->ooc_item_off[k] + pb.n_items;
+        c->ooc_bricks[k] = c->plan_bricks[k].id;
+        total += c->plan_bricks[k].n_items;
     }
-    if (c->ooc_item_off[P] != n_items) return fail(c, VR_EINVAL, "internal: out-of-core item count mismatch");
+    if (total != n_items) return fail(c, VR_EINVAL, "internal: out-of-core item count mismatch");
     const int32_t H = vr::plan_residency(c->res, c->ooc_bricks, c->ooc_frame++, c->ring_first_half, c->ooc_slot,
                                          c->ooc_up, c->ooc_ring);
     int rc = grow_pinned(c, s.h_slot_of, s.cap_slot_of, (size_t)c->n_bricks);
@@ -1256,14 +1341,14 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocL
     if ((rc = grow_device(c, s.d_slot_of, s.dcap_slot_of, (size_t)c->n_bricks))) return rc;
     std::fill(s.h_slot_of, s.h_slot_of + c->n_bricks, -1);
     for (int32_t k = 0; k < P; ++k) s.h_slot_of[c->ooc_bricks[k]] = c->ooc_slot[k];
-    // reorder the items: resident hits, then the uploads, then the ring
-    std::vector<char> moved(P, 0);
-    for (int32_t k : c->ooc_up) moved[k] = 1;
-    for (int32_t k : c->ooc_ring) moved[k] = 1;
-    c->ooc_items.resize((size_t)n_items);
+    // where each brick's items go: resident hits, then the uploads, then the ring
+    c->plan_dst.assign(P, -1);
+    for (int32_t k : c->ooc_up) c->plan_dst[k] = -2;
+    for (int32_t k : c->ooc_ring) c->plan_dst[k] = -2;
     int64_t w = 0;
     auto take = [&](int32_t k, OocLaunch* L) {
-        for (int64_t i = c->ooc_item_off[k]; i < c->ooc_item_off[k + 1]; ++i) c->ooc_items[w++] = s.h_items[i];
+        c->plan_dst[k] = w;
+        w += c->plan_bricks[k].n_items;
         if (L) {
             L->up.push_back(c->ooc_bricks[k]);
             L->slot.push_back(c->ooc_slot[k]);
@@ -1273,7 +1358,7 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocL
     OocLaunch hits;
     hits.lo = 0;
     for (int32_t k = 0; k < P; ++k)
-        if (!moved[k]) take(k, nullptr);
+        if (c->plan_dst[k] == -1) take(k, nullptr);
     hits.hi = w;
     launches.push_back(std::move(hits));
     const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
@@ -1295,7 +1380,7 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t T, int64_t n_items, std::vector<OocL
         launches.push_back(std::move(L));
     }
     c->ring_first_half = (c->ring_first_half + halves) % 2;
-    std::copy(c->ooc_items.begin(), c->ooc_items.end(), s.h_items);
+    emit_items(c, s, tiles_x, tiles_y, n_items);
     s.bricks_uploaded = (int64_t)(c->ooc_up.size() + c->ooc_ring.size());
     s.bricks_cached = P - s.bricks_uploaded;
     return VR_OK;
@@ -1417,11 +1502,11 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
                                   "VR_KERNEL_TEX or VR_KERNEL_AUTO on a cube within the texture limits)");
     if (use_tma(c) && (rc = prepare_tma(c))) return rc;
     if (use_tex(c) && (rc = prepare_tex(c))) return rc;
-    rc = plan_frame(c, s, win, tiles_x, tiles_y, T, n_items);
+    rc = plan_frame(c, s, win, tiles_x, tiles_y, T, n_items, !c->ooc);
     if (rc) return rc;
     std::vector<OocLaunch> ooc_launches;
     s.bricks_uploaded = s.bricks_cached = 0;
-    if (c->ooc && (rc = ooc_prepare(c, s, T, n_items, ooc_launches))) return rc;
+    if (c->ooc && (rc = ooc_prepare(c, s, tiles_x, tiles_y, n_items, ooc_launches))) return rc;
     s.plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     const int64_t n_tiles = (int64_t)tiles_x * tiles_y;
     const size_t img_px = (size_t)(win[2] - win[0] + 1) * (size_t)(win[3] - win[1] + 1);

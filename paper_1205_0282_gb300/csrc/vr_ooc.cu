@@ -181,23 +181,45 @@ int plan_residency(Residency& r, const std::vector<int32_t>& bricks, int64_t fra
             r.brick_in_slot[s] = -1;
         }
     // resident hits, then free or least recently used resident slots for the rest
+    // (each brick is listed once, so the hits of different threads touch different
+    // slots)
     std::vector<char> needed(R, 0);
-    for (int32_t k = 0; k < P; ++k) {
-        const int32_t s = r.slot_of_brick[bricks[k]];
-        if (s >= 0) {
-            slot[k] = s;
-            needed[s] = 1;
-            r.last_used[s] = frame;
+    const int32_t hw = (int32_t)std::max(1u, std::thread::hardware_concurrency());
+    const int32_t n_th = std::max(1, std::min({hw, 8, P / 16384}));
+    std::vector<int32_t> miss(n_th, 0);
+    auto hits = [&](int32_t t) {
+        for (int32_t k = (int32_t)((int64_t)P * t / n_th); k < (int32_t)((int64_t)P * (t + 1) / n_th); ++k) {
+            const int32_t s = r.slot_of_brick[bricks[k]];
+            if (s >= 0) {
+                slot[k] = s;
+                needed[s] = 1;
+                r.last_used[s] = frame;
+            } else {
+                ++miss[t];
+            }
         }
-    }
+    };
+    std::vector<std::thread> pool;
+    for (int32_t t = 1; t < n_th; ++t) pool.emplace_back(hits, t);
+    hits(0);
+    for (auto& th : pool) th.join();
+    int32_t misses = 0;
+    for (int32_t m : miss) misses += m;
+    // the misses' slots: free ones first, then the least recently used (ties by
+    // slot), found without ordering the whole cache
     std::vector<int32_t> victims;
-    for (int32_t s = 0; s < R; ++s)
-        if (!needed[s]) victims.push_back(s);
-    std::sort(victims.begin(), victims.end(), [&](int32_t a, int32_t b) {
-        const bool fa = r.brick_in_slot[a] < 0, fb = r.brick_in_slot[b] < 0;
-        if (fa != fb) return fa;
-        return r.last_used[a] < r.last_used[b];
-    });
+    if (misses > 0) {
+        for (int32_t s = 0; s < R; ++s)
+            if (!needed[s]) victims.push_back(s);
+        const size_t m = std::min<size_t>((size_t)misses, victims.size());
+        std::partial_sort(victims.begin(), victims.begin() + m, victims.end(), [&](int32_t a, int32_t b) {
+            const bool fa = r.brick_in_slot[a] < 0, fb = r.brick_in_slot[b] < 0;
+            if (fa != fb) return fa;
+            if (r.last_used[a] != r.last_used[b]) return r.last_used[a] < r.last_used[b];
+            return a < b;
+        });
+        victims.resize(m);
+    }
     size_t v = 0;
     int32_t streamed = 0;
     for (int32_t k = 0; k < P; ++k) {
