@@ -140,9 +140,14 @@ typedef struct {
                                 for frames in flight and rebuilds the copies on the next
                                 render (F8 also after vr_brick). */
 #define VR_OPT_DEVICE_BUDGET 6 /* out-of-core contexts (vr_load_cube_host): bytes of device
-                                memory for the brick cache, each brick taking
-                                (bx+1)(by+1)(bz+1) floats; default (and any value <= 0):
-                                room for every brick.  A frame whose rendered bricks fit
+                                memory for the brick cache, a brick's block being
+                                (bx+1)(by+1)(bz+1) floats: with the direct march one block
+                                per slot; with the texture march (VR_OPT_OOC_MARCH) one
+                                block's bytes per layered copy of a slot, plus a staging
+                                area of max(min(64 MiB of blocks, S0/8), H0) blocks (S0:
+                                the slots the budget holds without it, H0 its ring half)
+                                through which the blocks are copied or decoded.  Default
+                                (and any value <= 0): room for every brick.  A frame whose rendered bricks fit
                                 keeps bricks resident across frames (least recently used
                                 evicted); in a larger frame the last 2H slots (H = S/8
                                 clamped to [1, 32], S slots) form a ring of two halves that
@@ -172,19 +177,20 @@ typedef struct {
                                 the current copies (rebuilt at the next render). */
 #define VR_OPT_OOC_MARCH 9     /* out-of-core and learned contexts: 1: the texture march
                                 (VR_KERNEL_TEX's gathers) on three layered copies of the
-                                device cache's slots, one per sweep axis, refilled from
-                                each slot's block after it is copied or decoded; each slot
-                                then takes four times its block's bytes of
-                                VR_OPT_DEVICE_BUDGET (block plus copies).  If the device's
+                                device cache's slots, one per sweep axis, filled from each
+                                brick's block after it is copied or decoded into the
+                                staging area; each slot takes three times its block's
+                                bytes of VR_OPT_DEVICE_BUDGET.  If the device's
                                 layered-texture limits cannot tile the slots, the direct
                                 march is used.  3: the same march on one layered copy,
                                 layers along z (every ray sweeps along z, about 17% slower
-                                than with the ray's dominant axis), each slot taking twice
-                                its block's bytes.  0: the direct march on the blocks.  2
-                                (default): 1 when every brick fits the budget with three
-                                copies, else 3 when every brick fits it with one, else 0
-                                (a streaming cache keeps up to four times the slots).
-                                Takes effect at the next vr_brick. */
+                                than with the ray's dominant axis), each slot taking its
+                                block's bytes.  0: the direct march on blocks kept in the
+                                slots (a block per slot).  2 (default): 1 when every brick
+                                fits the budget with three copies, else 3 when every brick
+                                fits it with one, else 0 (a cache that streams is bound by
+                                its uploads, which the direct march does not follow with
+                                fills).  Takes effect at the next vr_brick. */
 #define VR_OPT_PROVIDER_THREADS 10 /* host threads that call a brick provider (and copy a
                                 host cube into the brick store) at once; <= 0 (default):
                                 the machine's hardware threads. */

@@ -480,6 +480,9 @@ struct vr_ctx {
                                        // copies, 3 on one (along z), 0 direct
     bool pool_tex_on = false;          // the current cache has its layered copies
     bool pool_single = false;          // only the copy along z (VR_OPT_OOC_MARCH 3)
+    int64_t pool_stage = 0;            // texture march: d_pool holds this many blocks, one
+                                       // launch's uploads on their way into the layered
+                                       // copies (0: d_pool is the cache, a block per slot)
     cudaArray_t pool_arr[3] = {nullptr, nullptr, nullptr};  // by sweep axis
     cudaTextureObject_t pool_tex[3] = {0, 0, 0};
     cudaSurfaceObject_t pool_surf[3] = {0, 0, 0};

@@ -303,6 +303,17 @@ int make_pool_tex(vr_ctx* c, int64_t slots, bool single) {
     return VR_OK;
 }
 
+// Blocks of the texture march's staging area for a cache of `slots` slots: one
+// launch's uploads, i.e. a group of resident uploads (about 64 MiB, and no more
+// than an eighth of the cache) or a ring half (max(1, min(slots / 8, 32))
+// bricks), whichever is larger.
+int64_t ooc_stage_blocks(int64_t slots, size_t slot_bytes) {
+    const int64_t group = std::max<int64_t>(1, ((int64_t)64 << 20) / (int64_t)slot_bytes);
+    const int64_t eighth = std::max<int64_t>(1, slots / 8);
+    const int64_t half = std::max<int64_t>(1, std::min<int64_t>(slots / 8, 32));
+    return std::max(std::min(group, eighth), half);
+}
+
 // Brick store and device cache of an out-of-core context (at vr_brick).
 int build_ooc_store(vr_ctx* c) {
     free_pool_tex(c);
@@ -358,24 +369,45 @@ int build_ooc_store(vr_ctx* c) {
         vr::read_blocks(brick_source(c), c->n, c->B, c->nb, nullptr, c->n_bricks, c->h_store, c->slot_floats,
                         c->h_minmax.data(), nullptr);
     }
-    // the texture march keeps each slot four times (its block and three layered
-    // copies) or twice (its block and the copy along z); automatically chosen, in
-    // that order, when every brick fits the budget that way
-    auto fits = [&](int64_t k) { return c->budget <= 0 || c->budget / ((int64_t)slot_bytes * k) >= c->n_bricks; };
-    const bool single = c->ooc_march == 3 || (c->ooc_march == 2 && !fits(4) && fits(2));
-    const bool tex_march = single || c->ooc_march == 1 || (c->ooc_march == 2 && fits(4));
-    const int copies = single ? 2 : (tex_march ? 4 : 1);
-    int64_t slots = c->n_bricks;
-    if (c->budget > 0) slots = std::min<int64_t>(slots, c->budget / ((int64_t)slot_bytes * copies));
-    if (slots < 2) return fail(c, VR_EINVAL, "VR_OPT_DEVICE_BUDGET holds fewer than 2 bricks");
-    if (cudaMalloc((void**)&c->d_pool, slot_bytes * (size_t)slots) != cudaSuccess) {
-        cudaGetLastError();
-        c->d_pool = nullptr;
-        return fail(c, VR_ENOMEM, "cannot allocate the device brick cache");
-    }
+    // The texture march keeps each slot as layered copies only, three (one per
+    // sweep axis) or the one along z, and the blocks pass through a staging area
+    // that holds one launch's uploads.  The direct march keeps a block per slot.
+    // Automatically: the three copies when every brick fits the budget that way,
+    // else the one copy when every brick fits with it, else the direct march (a
+    // streaming cache is bound by its uploads, which the direct march does not
+    // follow with fills).
+    const int64_t budget_blocks = c->budget > 0 ? c->budget / (int64_t)slot_bytes : -1;
+    auto fits = [&](int64_t copies) {
+        return budget_blocks < 0 ||
+               (budget_blocks - ooc_stage_blocks(budget_blocks / copies, slot_bytes)) / copies >= c->n_bricks;
+    };
+    const bool single = c->ooc_march == 3 || (c->ooc_march == 2 && !fits(3) && fits(1));
+    const bool tex_march = single || c->ooc_march == 1 || (c->ooc_march == 2 && fits(3));
+    int64_t slots = 0;
+    c->pool_stage = 0;
     if (tex_march) {
+        const int64_t copies = single ? 1 : 3;
+        int64_t stage = ooc_stage_blocks(c->n_bricks, slot_bytes);
+        slots = c->n_bricks;
+        if (budget_blocks >= 0) {
+            stage = ooc_stage_blocks(budget_blocks / copies, slot_bytes);
+            slots = std::min<int64_t>(slots, (budget_blocks - stage) / copies);
+        }
+        if (slots < 2) return fail(c, VR_EINVAL, "VR_OPT_DEVICE_BUDGET holds fewer than 2 bricks");
         int rc = make_pool_tex(c, slots, single);
         if (rc) return rc;
+        if (c->pool_tex_on) c->pool_stage = stage;
+    }
+    if (!c->pool_tex_on) {
+        slots = budget_blocks >= 0 ? std::min<int64_t>(c->n_bricks, budget_blocks) : c->n_bricks;
+        if (slots < 2) return fail(c, VR_EINVAL, "VR_OPT_DEVICE_BUDGET holds fewer than 2 bricks");
+    }
+    const int64_t blocks = c->pool_stage > 0 ? c->pool_stage : slots;
+    if (cudaMalloc((void**)&c->d_pool, slot_bytes * (size_t)blocks) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_pool = nullptr;
+        free_pool_tex(c);
+        return fail(c, VR_ENOMEM, "cannot allocate the device brick cache");
     }
     c->res.slot_of_brick.assign(c->n_bricks, -1);
     c->res.brick_in_slot.assign(slots, -1);
@@ -1362,7 +1394,9 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t tiles_x, int32_t tiles_y, int64_t n_
     hits.hi = w;
     launches.push_back(std::move(hits));
     const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
-    const size_t group = std::max<size_t>(1, ((size_t)64 << 20) / slot_bytes);
+    size_t group = std::max<size_t>(1, ((size_t)64 << 20) / slot_bytes);
+    if (c->pool_stage > 0) group = std::min(group, (size_t)c->pool_stage);  // one staging area's blocks
+    if (c->pool_stage > 0 && H > c->pool_stage) return fail(c, VR_EINVAL, "internal: ring half larger than the staging");
     for (size_t g0 = 0; g0 < c->ooc_up.size(); g0 += group) {
         OocLaunch L;
         L.lo = w;
@@ -1393,6 +1427,11 @@ int ooc_prepare(vr_ctx* c, Slot& s, int32_t tiles_x, int32_t tiles_y, int64_t n_
 int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off, size_t* copied) {
     const size_t slot_bytes = (size_t)c->slot_floats * sizeof(float);
     *copied = 0;
+    // where brick k of the launch lands: its slot's block, or (texture march) block
+    // k of the staging area, from which its layered copies are filled
+    if (c->pool_stage > 0 && (int64_t)L.up.size() > c->pool_stage)
+        return fail(c, VR_EINVAL, "internal: upload group larger than the staging");
+    auto dst = [&](size_t k) -> int32_t { return c->pool_stage > 0 ? (int32_t)k : L.slot[k]; };
     if (c->codec) {
         // fallback bricks are copied from their plain blocks, the others decoded
         int32_t* lb = s.h_decode + list_off;
@@ -1400,7 +1439,7 @@ int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off, size_t* 
         for (size_t k = 0; k < L.up.size(); ++k) {
             const int64_t pi = c->plain_index.empty() ? -1 : c->plain_index[L.up[k]];
             if (pi >= 0) {
-                VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
+                VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)dst(k) * c->slot_floats,
                                            c->h_store + (size_t)pi * c->slot_floats, slot_bytes,
                                            cudaMemcpyHostToDevice, c->copy_stream));
                 *copied += slot_bytes;
@@ -1411,7 +1450,7 @@ int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off, size_t* 
         if (n == 0) return VR_OK;
         size_t m = 0;
         for (size_t k = 0; k < L.up.size(); ++k)
-            if (c->plain_index.empty() || c->plain_index[L.up[k]] < 0) lb[n + m++] = L.slot[k];
+            if (c->plain_index.empty() || c->plain_index[L.up[k]] < 0) lb[n + m++] = dst(k);
         VR_CUDA(c, cudaMemcpyAsync(s.d_decode + list_off, lb, 2 * n * sizeof(int32_t), cudaMemcpyHostToDevice,
                                    c->copy_stream));
         const int rc = vr_codec_decode_bricks(c->codec, s.d_decode + list_off, s.d_decode + list_off + n, (int32_t)n,
@@ -1430,7 +1469,7 @@ int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off, size_t* 
                             c->slot_floats, nullptr, &bad))
             return source_fail(c, bad);
         for (size_t k = 0; k < L.up.size(); ++k)
-            VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
+            VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)dst(k) * c->slot_floats,
                                        c->h_stage[j] + k * c->slot_floats, slot_bytes, cudaMemcpyHostToDevice,
                                        c->copy_stream));
         VR_CUDA(c, cudaEventRecord(c->ev_stage[j], c->copy_stream));
@@ -1438,7 +1477,7 @@ int ooc_upload(vr_ctx* c, Slot& s, const OocLaunch& L, size_t list_off, size_t* 
         return VR_OK;
     }
     for (size_t k = 0; k < L.up.size(); ++k)
-        VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)L.slot[k] * c->slot_floats,
+        VR_CUDA(c, cudaMemcpyAsync(c->d_pool + (size_t)dst(k) * c->slot_floats,
                                    c->h_store + (size_t)L.up[k] * c->slot_floats, slot_bytes,
                                    cudaMemcpyHostToDevice, c->copy_stream));
     *copied = L.up.size() * slot_bytes;
@@ -1615,9 +1654,11 @@ int render_impl(vr_ctx* c, float* out_rgba, void* stream_ptr, const int32_t win[
                 std::copy(L.slot.begin(), L.slot.end(), hf);
                 VR_CUDA(c, cudaMemcpyAsync(s.d_fill + list_off[k] / 2, hf, L.slot.size() * sizeof(int32_t),
                                            cudaMemcpyHostToDevice, c->copy_stream));
+                // (from the staging area, in launch order, on the copy stream: the next
+                // launch's blocks overwrite it only after this fill)
                 VR_CUDA(c, vr::fill_pool_tex(c->d_pool, c->slot_floats, s.d_fill + list_off[k] / 2,
-                                             (int32_t)L.slot.size(), c->B, c->pool_surf, c->pool_cols,
-                                             c->copy_stream));
+                                             (int32_t)L.slot.size(), c->pool_stage > 0, c->B, c->pool_surf,
+                                             c->pool_cols, c->copy_stream));
             }
             VR_CUDA(c, cudaEventRecord(c->ev_chunk[k], c->copy_stream));
             VR_CUDA(c, cudaEventRecord(c->ev_copy_done, c->copy_stream));

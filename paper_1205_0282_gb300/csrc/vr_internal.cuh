@@ -150,9 +150,11 @@ cudaError_t launch_march(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tma(const FrameParams& p, cudaStream_t s);
 cudaError_t launch_march_tex(const FrameParams& p, cudaStream_t s);
 // Out-of-core texture march: copy the blocks of the cache slots slots[0..count)
-// (device list) into the three layered copies of the slot pool (surfaces by
-// sweep axis, slot k at texel (k % cols[S], k / cols[S]) x (B+1)).
-cudaError_t fill_pool_tex(const float* pool, int64_t slot_floats, const int32_t* slots, int32_t count,
+// (device list) into the layered copies of the slot pool (surfaces by sweep axis,
+// null for a copy the pool does not keep; slot k at texel (k % cols[S], k / cols[S])
+// x (B+1)).  staged: slot slots[i]'s block is block i of `pool` (the staging area);
+// otherwise block slots[i].
+cudaError_t fill_pool_tex(const float* pool, int64_t slot_floats, const int32_t* slots, int32_t count, bool staged,
                           const int32_t B[3], const cudaSurfaceObject_t surf[3], const int32_t cols[3],
                           cudaStream_t s);
 // Batch (vr_serve.cu): the texture march over items of several frames, and the

@@ -582,15 +582,15 @@ __global__ void stored_minmax_kernel(const float* __restrict__ a, int64_t pitch,
 // (coordinates along U, V) + the slot's tile origin.  The grid covers (x, y) of
 // the block with (z) in a loop.
 template <int S>
-__global__ void fill_pool_kernel(const float* __restrict__ pool, int64_t slot_floats, const int32_t* slots, int3 B1,
-                                 cudaSurfaceObject_t surf, int32_t cols) {
+__global__ void fill_pool_kernel(const float* __restrict__ pool, int64_t slot_floats, const int32_t* slots,
+                                 bool staged, int3 B1, cudaSurfaceObject_t surf, int32_t cols) {
     constexpr int U = Axes<S>::U, V = Axes<S>::V;
     const int k = slots[blockIdx.z];
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= B1.x) return;
     const int n1[3] = {B1.x, B1.y, B1.z};
     const int tu = (k % cols) * n1[U], tv = (k / cols) * n1[V];
-    const float* blk = pool + (int64_t)k * slot_floats;
+    const float* blk = pool + (int64_t)(staged ? (int)blockIdx.z : k) * slot_floats;
     for (int z = 0; z < B1.z; ++z) {
         const float v = blk[((int64_t)z * B1.y + y) * B1.x + x];
         const int c[3] = {x, y, z};
@@ -681,16 +681,19 @@ cudaError_t launch_march_tex_batch(const FrameParams& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t fill_pool_tex(const float* pool, int64_t slot_floats, const int32_t* slots, int32_t count,
+cudaError_t fill_pool_tex(const float* pool, int64_t slot_floats, const int32_t* slots, int32_t count, bool staged,
                           const int32_t B[3], const cudaSurfaceObject_t surf[3], const int32_t cols[3],
                           cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const int3 b1 = make_int3(B[0] + 1, B[1] + 1, B[2] + 1);
     const dim3 grid((unsigned)((b1.x + 127) / 128), (unsigned)b1.y, (unsigned)count);
     // the copies the pool keeps (all three, or the one along z)
-    if (surf[0]) texm::fill_pool_kernel<0><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[0], cols[0]);
-    if (surf[1]) texm::fill_pool_kernel<1><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[1], cols[1]);
-    if (surf[2]) texm::fill_pool_kernel<2><<<grid, 128, 0, s>>>(pool, slot_floats, slots, b1, surf[2], cols[2]);
+    if (surf[0])
+        texm::fill_pool_kernel<0><<<grid, 128, 0, s>>>(pool, slot_floats, slots, staged, b1, surf[0], cols[0]);
+    if (surf[1])
+        texm::fill_pool_kernel<1><<<grid, 128, 0, s>>>(pool, slot_floats, slots, staged, b1, surf[1], cols[1]);
+    if (surf[2])
+        texm::fill_pool_kernel<2><<<grid, 128, 0, s>>>(pool, slot_floats, slots, staged, b1, surf[2], cols[2]);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,8 @@ numpy in FP64 on the same BF16 values."""
 import numpy as np
 import pytest
 
+from ooc_budget import budget_for
+
 pytestmark = pytest.mark.gpu
 
 
@@ -225,7 +227,7 @@ def test_codec_decodes_into_slots_and_renders(vr):
             with vr.VolumeRenderer(0) as r:
                 r.load_cube_codec(c, shape)
                 if budget:
-                    r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget * 17 ** 3 * 4)
+                    r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget * 17 ** 3 * 4)   # 3 blocks: a 2-slot cache
                 r.brick(*brick)
                 r.set_transfer_function(tf)
                 r.set_camera(cam)
@@ -280,9 +282,9 @@ def _fallback_case(vr, torch):
 
 
 def _ctx(vr, shape, brick, tf, cam, codec=None, cube=None, fallback=None, budget=0, floor=-3.4e38, march=1):
-    """A plain or learned context on the texture march (march=1: each slot takes
-    four blocks of the budget, its block and three layered copies) or on the
-    direct march (march=0), with a cache of `budget` slots (0: every brick)."""
+    """A plain or learned context on the texture march (march=1: three layered
+    copies per slot plus a staging area) or on the direct march (march=0: a block
+    per slot), with a cache of `budget` slots (0: every brick)."""
     r = vr.VolumeRenderer(0)
     if codec is not None:
         r.load_cube_codec(codec, shape)
@@ -292,7 +294,7 @@ def _ctx(vr, shape, brick, tf, cam, codec=None, cube=None, fallback=None, budget
         r.load_cube_host(cube)
     r.set_option(vr.VR_OPT_OOC_MARCH, march)
     if budget:
-        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget * 17 ** 3 * 4 * (4 if march else 1))
+        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_for(budget, brick, march))
     r.set_option(vr.VR_OPT_SKIP_EMPTY, 0)   # codec and plain ranges may differ
     r.brick(*brick)
     r.set_transfer_function(tf)

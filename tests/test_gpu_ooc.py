@@ -11,6 +11,7 @@ import pytest
 import oracle
 import synth
 from parity_util import AMB_ALPHA, AMB_STEPS, assert_parity
+from ooc_budget import budget_for
 from test_gpu_render import RAGGED, oracle_render
 
 pytestmark = pytest.mark.gpu
@@ -42,14 +43,13 @@ def _incore(vr, torch, cube, tf, cam, brick, mode=0, march=1):
 
 def _ooc(vr, cube, tf, brick, budget_bricks=0, mode=0, march=1):
     """Out-of-core context whose cache holds budget_bricks slots (the texture march
-    keeps each slot's block and three layered copies: four blocks' bytes; with one
-    copy along z, march 3, two)."""
+    keeps three layered copies of each slot, or with march 3 the one along z, plus
+    a staging area for one launch's blocks)."""
     r = vr.VolumeRenderer(0)
     r.load_cube_host(cube)
     r.set_option(vr.VR_OPT_OOC_MARCH, march)
     if budget_bricks:
-        slot = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1) * 4 * {0: 1, 1: 4, 3: 2}[march]
-        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_bricks * slot)
+        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_for(budget_bricks, brick, march))
     r.brick(*brick)
     r.set_transfer_function(tf)
     r.set_option(vr.VR_OPT_MODE, mode)

@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 import synth
+from ooc_budget import budget_for
 from parity_util import AMB_ALPHA, AMB_STEPS, assert_parity
 
 pytestmark = pytest.mark.gpu
@@ -44,8 +45,7 @@ def _ctx(vr, load, brick, tf, cam, march, budget_bricks=0):
     load(r)
     r.set_option(vr.VR_OPT_OOC_MARCH, march)
     if budget_bricks:
-        slot = (brick[0] + 1) * (brick[1] + 1) * (brick[2] + 1) * 4 * (4 if march else 1)
-        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_bricks * slot)
+        r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_for(budget_bricks, brick, march))
     r.brick(*brick)
     r.set_transfer_function(tf)
     r.set_camera(cam)
@@ -193,7 +193,7 @@ def test_learned_fallback_from_a_provider(vr):
         r.set_codec_fallback_provider(provide, bound)
         r.set_option(vr.VR_OPT_OOC_MARCH, 1)      # as the host-cube context: the texture march
         if budget:
-            r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget * 17 ** 3 * 4 * 4)
+            r.set_option(vr.VR_OPT_DEVICE_BUDGET, budget_for(budget, brick, 1))
         r.set_option(vr.VR_OPT_SKIP_EMPTY, 0)
         r.brick(*brick)
         r.set_transfer_function(tf)
