@@ -996,18 +996,21 @@ def run_learned_xl(args):
                     secs.append(timed(r, cam, out))
                     imgs.append(out.cpu().numpy())
                 st = r.stats()
-                # the same poses back to back, one synchronisation at the end: the
-                # planning of a frame overlaps the device work of the ones before it
+                # the same poses back to back (repeated to at least 16 frames, so that
+                # the first frame's planning, which nothing overlaps, weighs little),
+                # one synchronisation at the end: the planning of a frame overlaps the
+                # device work of the ones before it
+                piped = frame_poses * max(1, -(-16 // len(frame_poses)))
                 torch.cuda.synchronize()
                 t = time.perf_counter()
-                for cam in frame_poses:
+                for cam in piped:
                     r.set_camera(cam)
                     r.render(out)
                 torch.cuda.synchronize()
-                fps_pipelined = len(frame_poses) / (time.perf_counter() - t)
+                fps_pipelined = len(piped) / (time.perf_counter() - t)
                 r.close()
                 info.update(cold_first_frame_s=cold, frame_s=secs, fps=len(secs) / sum(secs),
-                            fps_pipelined=fps_pipelined,
+                            fps_pipelined=fps_pipelined, frames_pipelined=len(piped),
                             samples_per_s=st["samples"] / sum(secs),
                             bricks_rendered_per_frame=st["bricks_rendered"] / max(st["frames"], 1),
                             bricks_filled_per_frame=st["bricks_uploaded"] / max(st["frames"], 1),

@@ -224,6 +224,13 @@ inline bool rect_from_corners(const vr_camera& c, const CornerProj* const q[8], 
     return true;
 }
 
+// Host threads the planner splits its loops over (no more than the machine has);
+// the plan is the same whatever the count.
+constexpr int64_t kPlanThreads = 16;
+inline int64_t plan_threads() {
+    return std::max<int64_t>(1, std::min<int64_t>((int64_t)std::thread::hardware_concurrency(), kPlanThreads));
+}
+
 // Projections of the brick grid's corner points x_i = min(i B, n - 1), i = 0..nb
 // per axis (x fastest): every brick box spans eight of them.
 inline void project_brick_grid(const vr_camera& cam, const Basis& b, const int64_t n[3], const int32_t B[3],
@@ -241,7 +248,7 @@ inline void project_brick_grid(const vr_camera& cam, const Basis& b, const int64
                 }
     };
     // large grids (tens of thousands of points) on a few host threads, by planes
-    const int64_t parts = std::min<int64_t>({g[2], (int64_t)8, g[0] * g[1] * g[2] / 16384 + 1});
+    const int64_t parts = std::min<int64_t>({g[2], plan_threads(), g[0] * g[1] * g[2] / 16384 + 1});
     if (parts <= 1) {
         planes(0, g[2]);
         return;

@@ -97,6 +97,7 @@ void free_pool_tex(vr_ctx* c) {
     }
     c->pool_tex_on = false;
     c->pool_single = false;
+    c->pool_stage = 0;
 }
 
 bool use_pool_tex(vr_ctx* c) { return c->ooc && c->pool_tex_on; }
@@ -593,8 +594,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
             out.touched += vox * vox_bytes;
         }
     };
-    const int64_t hw = (int64_t)std::max(1u, std::thread::hardware_concurrency());
-    const int32_t n_parts = (int32_t)std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)8, c->n_bricks / 256}));
+    const int32_t n_parts = (int32_t)std::max<int64_t>(1, std::min<int64_t>(plan_threads(), c->n_bricks / 256));
     if ((int32_t)c->plan_parts.size() < n_parts) c->plan_parts.resize(n_parts);
     auto run_parts = [&](auto&& fn) {
         if (n_parts == 1) {
@@ -707,8 +707,7 @@ void emit_items(vr_ctx* c, Slot& s, int32_t tiles_x, int32_t tiles_y, int64_t n_
             }
         }
     };
-    const int64_t hw = (int64_t)std::max(1u, std::thread::hardware_concurrency());
-    const int64_t n_parts = std::max<int64_t>(1, std::min<int64_t>({hw, (int64_t)8, n_items / 65536, (int64_t)tiles_y}));
+    const int64_t n_parts = std::max<int64_t>(1, std::min<int64_t>({plan_threads(), n_items / 65536, (int64_t)tiles_y}));
     if (n_parts == 1) {
         rows(0, tiles_y);
         return;

@@ -185,7 +185,7 @@ int plan_residency(Residency& r, const std::vector<int32_t>& bricks, int64_t fra
     // slots)
     std::vector<char> needed(R, 0);
     const int32_t hw = (int32_t)std::max(1u, std::thread::hardware_concurrency());
-    const int32_t n_th = std::max(1, std::min({hw, 8, P / 16384}));
+    const int32_t n_th = std::max(1, std::min({hw, 16, P / 16384}));
     std::vector<int32_t> miss(n_th, 0);
     auto hits = [&](int32_t t) {
         for (int32_t k = (int32_t)((int64_t)P * t / n_th); k < (int32_t)((int64_t)P * (t + 1) / n_th); ++k) {
