@@ -69,9 +69,10 @@ def parse():
                     help="out-of-core: the cube stays in host memory, bricks stream into a device cache")
     ap.add_argument("--budget-gib", type=float, default=0.0,
                     help="device brick-cache budget for --ooc in GiB (0: every brick)")
-    ap.add_argument("--ooc-march", choices=["auto", "direct", "tex", "texz"], default="auto",
+    ap.add_argument("--ooc-march", choices=["auto", "direct", "tex", "texz", "texxz"], default="auto",
                     help="out-of-core and learned marches: direct on the blocks, texture march on three "
-                         "layered copies of the slots, or on one copy along z (VR_OPT_OOC_MARCH)")
+                         "layered copies of the slots, on one copy along z, or on the copies along x and z "
+                         "(VR_OPT_OOC_MARCH)")
     ap.add_argument("--serve", action="store_true",
                     help="serving loop: Poisson arrivals of camera/TF/resolution requests, p50/p99 latency")
     ap.add_argument("--rate", type=float, default=200.0, help="--serve: mean arrivals per second")
@@ -846,7 +847,7 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
-OOC_MARCH = {"direct": 0, "tex": 1, "auto": 2, "texz": 3}
+OOC_MARCH = {"direct": 0, "tex": 1, "auto": 2, "texz": 3, "texxz": 4}
 
 
 def xl_slabs(nbz: int, layers: int):

@@ -185,7 +185,11 @@ typedef struct {
                                 march is used.  3: the same march on one layered copy,
                                 layers along z (every ray sweeps along z, about 17% slower
                                 than with the ray's dominant axis), each slot taking its
-                                block's bytes.  0: the direct march on blocks kept in the
+                                block's bytes.  4: two layered copies, layers along x and
+                                along z (each ray sweeps along the larger of |d_x|, |d_z|:
+                                for camera paths about the y axis, the paper's orbit, as
+                                fast as three copies), each slot taking twice its block's
+                                bytes.  0: the direct march on blocks kept in the
                                 slots (a block per slot).  2 (default): 1 when every brick
                                 fits the budget with three copies, else 3 when every brick
                                 fits it with one, else 0 (a cache that streams is bound by

@@ -486,7 +486,7 @@ struct vr_ctx {
     int ooc_march = 2;                 // VR_OPT_OOC_MARCH: 2 auto, 1 texture march on three layered slot
                                        // copies, 3 on one (along z), 0 direct
     bool pool_tex_on = false;          // the current cache has its layered copies
-    bool pool_single = false;          // only the copy along z (VR_OPT_OOC_MARCH 3)
+    int pool_axes = 0;                 // bit S: the cache keeps the copy along axis S
     int64_t pool_stage = 0;            // texture march: d_pool holds this many blocks, one
                                        // launch's uploads on their way into the layered
                                        // copies (0: d_pool is the cache, a block per slot)

@@ -96,7 +96,7 @@ void free_pool_tex(vr_ctx* c) {
         c->pool_cols[a] = 0;
     }
     c->pool_tex_on = false;
-    c->pool_single = false;
+    c->pool_axes = 0;
     c->pool_stage = 0;
 }
 
@@ -251,19 +251,19 @@ int codec_fallback_scan(vr_ctx* c) {
     return VR_OK;
 }
 
-// Layered copies of the cache's slots for the texture march: for sweep axis S a
-// layered array with layers along S (B_S + 1 of them) and the slots' (U, V)
-// faces tiled pool_cols[S] per row; single: the copy along z only (every item
-// then sweeps along z).  If the device's layered-texture limits do not admit the
-// tiling, the context keeps the direct march.
-int make_pool_tex(vr_ctx* c, int64_t slots, bool single) {
+// Layered copies of the cache's slots for the texture march: for each sweep axis S
+// in `axes` (bit S) a layered array with layers along S (B_S + 1 of them) and the
+// slots' (U, V) faces tiled pool_cols[S] per row (an item then sweeps along the
+// ray's dominant axis among those kept).  If the device's layered-texture limits
+// do not admit the tiling, the context keeps the direct march.
+int make_pool_tex(vr_ctx* c, int64_t slots, int axes) {
     int maxw = 0, maxh = 0, maxl = 0;
     VR_CUDA(c, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture2DLayeredWidth, c->device));
     VR_CUDA(c, cudaDeviceGetAttribute(&maxh, cudaDevAttrMaxTexture2DLayeredHeight, c->device));
     VR_CUDA(c, cudaDeviceGetAttribute(&maxl, cudaDevAttrMaxTexture2DLayeredLayers, c->device));
     int64_t cols[3], rows[3];
-    const int S0 = single ? 2 : 0;
-    for (int S = S0; S < 3; ++S) {
+    for (int S = 0; S < 3; ++S) {
+        if (!(axes >> S & 1)) continue;
         const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
         cols[S] = std::min<int64_t>(slots, maxw / (c->B[U] + 1));
         if (cols[S] < 1) return VR_OK;
@@ -271,7 +271,8 @@ int make_pool_tex(vr_ctx* c, int64_t slots, bool single) {
         if (rows[S] * (c->B[V] + 1) > maxh || c->B[S] + 1 > maxl) return VR_OK;
     }
     cudaChannelFormatDesc ch = cudaCreateChannelDesc<float>();
-    for (int S = S0; S < 3; ++S) {
+    for (int S = 0; S < 3; ++S) {
+        if (!(axes >> S & 1)) continue;
         const int U = S == 0 ? 1 : 0, V = S == 2 ? 1 : 2;
         if (cudaMalloc3DArray(&c->pool_arr[S], &ch,
                               make_cudaExtent((size_t)(cols[S] * (c->B[U] + 1)), (size_t)(rows[S] * (c->B[V] + 1)),
@@ -300,7 +301,7 @@ int make_pool_tex(vr_ctx* c, int64_t slots, bool single) {
         c->pool_cols[S] = (int32_t)cols[S];
     }
     c->pool_tex_on = true;
-    c->pool_single = single;
+    c->pool_axes = axes;
     return VR_OK;
 }
 
@@ -371,8 +372,9 @@ int build_ooc_store(vr_ctx* c) {
                         c->h_minmax.data(), nullptr);
     }
     // The texture march keeps each slot as layered copies only, three (one per
-    // sweep axis) or the one along z, and the blocks pass through a staging area
-    // that holds one launch's uploads.  The direct march keeps a block per slot.
+    // sweep axis), the ones along x and z, or the one along z, and the blocks pass
+    // through a staging area
+    // holding one launch's uploads.  The direct march keeps a block per slot.
     // Automatically: the three copies when every brick fits the budget that way,
     // else the one copy when every brick fits with it, else the direct march (a
     // streaming cache is bound by its uploads, which the direct march does not
@@ -383,11 +385,12 @@ int build_ooc_store(vr_ctx* c) {
                (budget_blocks - ooc_stage_blocks(budget_blocks / copies, slot_bytes)) / copies >= c->n_bricks;
     };
     const bool single = c->ooc_march == 3 || (c->ooc_march == 2 && !fits(3) && fits(1));
-    const bool tex_march = single || c->ooc_march == 1 || (c->ooc_march == 2 && fits(3));
+    const bool tex_march = single || c->ooc_march == 1 || c->ooc_march == 4 || (c->ooc_march == 2 && fits(3));
+    const int axes = single ? 4 : (c->ooc_march == 4 ? 5 : 7);  // bit S: the copy along axis S
     int64_t slots = 0;
     c->pool_stage = 0;
     if (tex_march) {
-        const int64_t copies = single ? 1 : 3;
+        const int64_t copies = (axes & 1) + (axes >> 1 & 1) + (axes >> 2 & 1);
         int64_t stage = ooc_stage_blocks(c->n_bricks, slot_bytes);
         slots = c->n_bricks;
         if (budget_blocks >= 0) {
@@ -395,7 +398,7 @@ int build_ooc_store(vr_ctx* c) {
             slots = std::min<int64_t>(slots, (budget_blocks - stage) / copies);
         }
         if (slots < 2) return fail(c, VR_EINVAL, "VR_OPT_DEVICE_BUDGET holds fewer than 2 bricks");
-        int rc = make_pool_tex(c, slots, single);
+        int rc = make_pool_tex(c, slots, axes);
         if (rc) return rc;
         if (c->pool_tex_on) c->pool_stage = stage;
     }
@@ -461,7 +464,7 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
         const double* f = c->basis.f;
         const double* r = c->basis.r;
         const double* u = c->basis.u;
-        const bool pool_z = use_pool_tex(c) && c->pool_single;
+        const int axes = use_pool_tex(c) ? c->pool_axes : 7;  // the cache's copies
         for (int ty = 0; ty < tiles_y; ++ty) {
             const double qy = c->plan_qy[ty];
             const double g0 = f[0] + qy * u[0], g1 = f[1] + qy * u[1], g2 = f[2] + qy * u[2];
@@ -469,10 +472,10 @@ int plan_frame(vr_ctx* c, Slot& s, const int32_t win[4], int32_t& tiles_x, int32
             for (int tx = 0; tx < tiles_x; ++tx) {
                 const double qx = c->plan_qx[tx];
                 const double d[3] = {g0 + qx * r[0], g1 + qx * r[1], g2 + qx * r[2]};
-                int ax = 0;
-                for (int a = 1; a < 3; ++a)
-                    if (std::fabs(d[a]) > std::fabs(d[ax])) ax = a;
-                if (pool_z) ax = 2;  // the cache keeps only the copy along z
+                // the dominant axis among those with a copy (ties to the lower axis)
+                int ax = -1;
+                for (int a = 0; a < 3; ++a)
+                    if ((axes >> a & 1) && (ax < 0 || std::fabs(d[a]) > std::fabs(d[ax]))) ax = a;
                 sweep[tx] = ax | (d[ax] < 0.0 ? 4 : 0);
             }
         }
@@ -1264,7 +1267,7 @@ int vr_set_option(vr_ctx* c, int32_t option, int64_t value) {
             return VR_OK;
         case VR_OPT_PROVIDER_THREADS: c->prov_threads = (int)std::max<int64_t>(0, std::min<int64_t>(value, 4096)); return VR_OK;
         case VR_OPT_OOC_MARCH:
-            if (value < 0 || value > 3) return fail(c, VR_EINVAL, "out-of-core march must be 0, 1, 2 or 3");
+            if (value < 0 || value > 4) return fail(c, VR_EINVAL, "out-of-core march must be 0, 1, 2, 3 or 4");
             c->ooc_march = (int)value;
             return VR_OK;
         case VR_OPT_TEX_SLAB_LAYERS:

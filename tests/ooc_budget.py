@@ -1,6 +1,6 @@
 """Device budgets for out-of-core test contexts, by the rule VR_OPT_DEVICE_BUDGET
 documents: the direct march takes one block of (bx+1)(by+1)(bz+1) floats per cache
-slot; the texture march takes its layered copies per slot (three, or one along z)
+slot; the texture march takes its layered copies per slot (three, two along x and z, or one along z)
 plus a staging area of max(min(64 MiB of blocks, slots / 8), ring half) blocks,
 sized for the slots the budget would hold without it."""
 
@@ -17,11 +17,12 @@ def stage_blocks(slots, brick):
 
 
 def slots_of(budget, brick, march, n_bricks):
-    """Cache slots that a budget gives (march 0: direct, 1: three copies, 3: one)."""
+    """Cache slots that a budget gives (march 0: direct, 1: three copies, 3: one,
+    4: two)."""
     blocks = budget // block_bytes(brick)
     if march == 0:
         return min(n_bricks, blocks)
-    copies = 3 if march == 1 else 1
+    copies = {1: 3, 3: 1, 4: 2}[march]
     return min(n_bricks, (blocks - stage_blocks(blocks // copies, brick)) // copies)
 
 

@@ -1,6 +1,7 @@
 """bench.py host logic: recorded ncu figures are reported only for the sources
 they were captured on; timed frames cover the whole orbit."""
 import json
+import os
 
 import bench
 
@@ -60,4 +61,10 @@ def test_xl_training_slabs_cover_every_brick_layer_once():
 
 
 def test_out_of_core_march_names():
-    assert bench.OOC_MARCH == {"direct": 0, "tex": 1, "auto": 2, "texz": 3}
+    """The bench's names for VR_OPT_OOC_MARCH values, against the header."""
+    import re
+    assert bench.OOC_MARCH == {"direct": 0, "tex": 1, "auto": 2, "texz": 3, "texxz": 4}
+    header = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "vr.h")).read()
+    doc = header[header.index("#define VR_OPT_OOC_MARCH"):header.index("#define VR_OPT_PROVIDER_THREADS")]
+    for v in (0, 1, 2, 3, 4):
+        assert re.search(rf"\b{v}( \(default\))?:", doc), v

@@ -181,14 +181,15 @@ def test_out_of_core_texture_march_dynamic_step(vr, torch, shape, brick, camk, s
     assert_parity(img.astype(np.float64), ref, amb)
 
 
+@pytest.mark.parametrize("march", [3, 4])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("budget", [0, 20, 5])
-def test_out_of_core_single_copy_march(vr, budget, mode):
+def test_out_of_core_single_copy_march(vr, budget, mode, march):
     """VR_OPT_OOC_MARCH 3: the texture march on one layered copy of the slots,
-    layers along z.  The same samples as the three-copy march, gathered in
-    another plane: within FP32 rounding of its image (emission-absorption and
-    MIP), frame after frame with every brick resident or streamed, and oracle
-    parity."""
+    layers along z; 4: on the two copies along x and z.  The same samples as the
+    three-copy march, gathered in another plane where a ray's dominant axis has no
+    copy: within FP32 rounding of its image (emission-absorption and MIP), frame
+    after frame with every brick resident or streamed, and oracle parity."""
     cube, tf = synth.tiny_cube(), synth.tf_tiny()
     brick = (16, 16, 16)
     for view in (0, 2):
@@ -196,7 +197,7 @@ def test_out_of_core_single_copy_march(vr, budget, mode):
         with _ooc(vr, cube, tf, brick, budget, mode=mode, march=1) as r:
             r.set_camera(cam)
             want = r.render().cpu().numpy().astype(np.float64)
-        with _ooc(vr, cube, tf, brick, budget, mode=mode, march=3) as r:
+        with _ooc(vr, cube, tf, brick, budget, mode=mode, march=march) as r:
             r.set_camera(cam)
             for k in range(3):
                 r.reset_stats()
@@ -213,6 +214,27 @@ def test_out_of_core_single_copy_march(vr, budget, mode):
             ref, amb, _ = oracle_render(cube, tf, cam, brick)
             assert_parity(img, ref, amb)
         assert want.max() > 0.2     # not an empty frame
+
+
+def test_two_copy_march_equals_three_on_an_orbit(vr):
+    """VR_OPT_OOC_MARCH 4 on the paper's kind of camera path (an orbit about y at
+    15 degrees of elevation, 30 degree field of view): no ray is dominated by y,
+    so every item sweeps along the axis the three-copy march picks and the images
+    are the same bit for bit, resident and streamed, with half the copies' bytes."""
+    cube, tf = synth.tiny_cube(), synth.tf_tiny()
+    brick = (16, 16, 16)
+    for cam in synth.orbit((64, 64, 64), 8, 15.0, 96, 80)[::3]:
+        for budget in (0, 6):
+            with _ooc(vr, cube, tf, brick, budget, march=1) as r:
+                r.set_camera(cam)
+                want = r.render().cpu().numpy()
+            with _ooc(vr, cube, tf, brick, budget, march=4) as r:
+                r.set_camera(cam)
+                for _ in range(2):
+                    got = r.render().cpu().numpy()
+                    assert np.array_equal(got, want)
+                    assert r.stats()["device_errors"] == 0
+        assert want[..., 3].max() > 0.05
 
 
 def test_out_of_core_errors(vr, torch):
