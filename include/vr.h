@@ -191,10 +191,11 @@ typedef struct {
                                 fast as three copies), each slot taking twice its block's
                                 bytes.  0: the direct march on blocks kept in the
                                 slots (a block per slot).  2 (default): 1 when every brick
-                                fits the budget with three copies, else 3 when every brick
-                                fits it with one, else 0 (a cache that streams is bound by
-                                its uploads, which the direct march does not follow with
-                                fills).  Takes effect at the next vr_brick. */
+                                fits the budget with three copies, else 4 when every brick
+                                fits it with two, else 3 when every brick fits it with one,
+                                else 0 (a cache that streams is bound by its uploads, which
+                                the direct march does not follow with fills).  Takes effect
+                                at the next vr_brick. */
 #define VR_OPT_PROVIDER_THREADS 10 /* host threads that call a brick provider (and copy a
                                 host cube into the brick store) at once; <= 0 (default):
                                 the machine's hardware threads. */

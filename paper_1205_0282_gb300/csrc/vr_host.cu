@@ -375,18 +375,21 @@ int build_ooc_store(vr_ctx* c) {
     // sweep axis), the ones along x and z, or the one along z, and the blocks pass
     // through a staging area
     // holding one launch's uploads.  The direct march keeps a block per slot.
-    // Automatically: the three copies when every brick fits the budget that way,
-    // else the one copy when every brick fits with it, else the direct march (a
-    // streaming cache is bound by its uploads, which the direct march does not
-    // follow with fills).
+    // Automatically: as many copies (three, the two along x and z, the one along
+    // z) as let every brick fit the budget, else the direct march (a streaming
+    // cache is bound by its uploads, which the direct march does not follow with
+    // fills).
     const int64_t budget_blocks = c->budget > 0 ? c->budget / (int64_t)slot_bytes : -1;
     auto fits = [&](int64_t copies) {
         return budget_blocks < 0 ||
                (budget_blocks - ooc_stage_blocks(budget_blocks / copies, slot_bytes)) / copies >= c->n_bricks;
     };
-    const bool single = c->ooc_march == 3 || (c->ooc_march == 2 && !fits(3) && fits(1));
-    const bool tex_march = single || c->ooc_march == 1 || c->ooc_march == 4 || (c->ooc_march == 2 && fits(3));
-    const int axes = single ? 4 : (c->ooc_march == 4 ? 5 : 7);  // bit S: the copy along axis S
+    int axes = 0;  // bit S: the copy along axis S (0: the direct march)
+    if (c->ooc_march == 1) axes = 7;
+    else if (c->ooc_march == 4) axes = 5;
+    else if (c->ooc_march == 3) axes = 4;
+    else if (c->ooc_march == 2) axes = fits(3) ? 7 : (fits(2) ? 5 : (fits(1) ? 4 : 0));
+    const bool tex_march = axes != 0;
     int64_t slots = 0;
     c->pool_stage = 0;
     if (tex_march) {
